@@ -1,0 +1,278 @@
+"""Benchmark of the exhaustive k-SNP MI search on one GB300.
+
+One step = one whole search (enumerate every combination, count its
+contingency table, score it, keep the exact top-N) over a resident dataset.
+Prints one JSON line.
+
+    python bench.py [--steps K] [--warmup W] [--workload NAME] [--path popc|tc|auto]
+    python bench.py --impl reference ...   # the CPU oracle on the host cores
+
+Under torchrun with N > 1 each rank runs the same search on its own GPU
+(independent replicas, weak scaling); the reported value sums the ranks' work
+over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "combination-samples/sec at orders 2-4 (INT8-TC vs popcount path); top-N recall at k=5"
+UNIT = "combination-samples/s"
+DEFAULT_WORKLOAD = "order3_2000snp_4000"
+POPC_PER_SM_CLK = 16          # 32-bit POPC results per SM per clock (integer pipe)
+N_SMS = 152
+SM_MAX_MHZ = 2070.0
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def workload_desc(name, d, k, top_n):
+    return dict(workload=name, order=k, n_snps=d.n_snps, n_samples=d.n_samples, n_cases=d.n_cases,
+                n_controls=d.n_samples - d.n_cases, top_n=top_n, data="synthetic HWE, seeded")
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", str(self.gpu), "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if not self.path or not os.path.exists(self.path):
+            return out
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        loaded = [s for s in sm if s > 0.5 * max(sm)] if sm else []
+        out.update(sm_mhz=statistics.median(loaded) if loaded else None, sm_max_mhz=max(mx) if mx else None,
+                   reasons=sorted(reasons), samples=len(rows))
+        return out
+
+
+def cpu_baseline(d, k, target_s=15.0):
+    """The oracle, as it stands, on a bounded rank range of the same workload."""
+    from oracle import oracle as O
+    total = O.binom(d.n_snps, k)
+    threads = O.max_threads()
+    r = min(total, 20000)
+    t0 = time.perf_counter()
+    O.search(d.geno, d.pheno, k, 100, rank_begin=0, rank_end=r, with_counts=False)
+    dt = time.perf_counter() - t0
+    if dt < target_s / 4 and r < total:
+        r = min(total, int(r * target_s / max(dt, 1e-3)))
+        t0 = time.perf_counter()
+        O.search(d.geno, d.pheno, k, 100, rank_begin=0, rank_end=r, with_counts=False)
+        dt = time.perf_counter() - t0
+    return dict(value=r * d.n_samples / dt, unit=UNIT, cores=threads, kind="oracle",
+                sample=f"lexicographic ranks [0, {r}) of the {total} combinations, {dt:.1f} s",
+                seconds=dt)
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle timed on this host's cores."""
+    rank = _env_int("RANK", 0)
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    from paper_2201_02460_gb300 import synth
+    d, k, top_n = synth.make_workload(args.workload)
+    total = O.binom(d.n_snps, k)
+    threads = O.max_threads()
+    # size each step to about 10 s of CPU work
+    r = min(total, 20000)
+    t0 = time.perf_counter()
+    O.search(d.geno, d.pheno, k, top_n, rank_begin=0, rank_end=r, with_counts=False)
+    dt = time.perf_counter() - t0
+    r = min(total, max(r, int(r * 10.0 / max(dt, 1e-3))))
+    for _ in range(args.warmup):
+        O.search(d.geno, d.pheno, k, top_n, rank_begin=0, rank_end=min(total, r // 10 + 1), with_counts=False)
+    times = []
+    for s in range(args.steps):
+        r0 = (s * r) % max(1, total - r + 1)
+        t0 = time.perf_counter()
+        O.search(d.geno, d.pheno, k, top_n, rank_begin=r0, rank_end=r0 + r, with_counts=False)
+        times.append(time.perf_counter() - t0)
+    t = sum(times)
+    value = args.steps * r * d.n_samples / t
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
+                ms_per_step=1e3 * t / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="u32", data="synthetic", impl="reference",
+                config=workload_desc(args.workload, d, k, top_n),
+                cpu_baseline=dict(value=value, unit=UNIT, cores=threads, kind="oracle",
+                                  sample=f"each step: {r} consecutive lexicographic ranks of {total}"),
+                e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local = _env_int("LOCAL_RANK", 0)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+
+    from paper_2201_02460_gb300 import build as B
+    B.build()
+    from paper_2201_02460_gb300 import epi, synth
+
+    d, k, top_n = synth.make_workload(args.workload)
+    ctx = epi.Context(local)
+    ds = epi.Dataset(ctx, d.geno, d.pheno)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    total = math.comb(d.n_snps, k)
+    units = total * d.n_samples
+
+    for _ in range(args.warmup):
+        epi.search(ds, k, top_n, path=args.path)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = ctx.kernel_launches()
+    ctx.profile_begin()
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for s in range(args.steps):
+            flush.fill_(s & 0xFF)            # evict the L2 between steps (not timed)
+            ev[s][0].record(stream)
+            res = epi.search(ds, k, top_n, path=args.path)
+            ev[s][1].record(stream)
+        torch.cuda.synchronize()
+    kern_ms, kern_n = ctx.profile_end()
+    launches = ctx.kernel_launches() - launches0
+    t_ms = sum(a.elapsed_time(b) for a, b in ev)
+    if world > 1:
+        tt = torch.tensor([t_ms], dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    value = world * units * args.steps / (t_ms / 1e3)
+
+    # end to end: host genotypes in, host results out, through the C-ABI
+    e2e_times = []
+    for s in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ds2 = epi.Dataset(ctx, d.geno, d.pheno)
+        epi.search(ds2, k, top_n, path=args.path)
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+        ds2.close()
+    e2e_t = statistics.median(e2e_times)
+    h2d = int(d.geno.nbytes + d.pheno.nbytes)
+    d2h = int(top_n * epi.RESULT_DTYPE.itemsize + top_n * 2 * 3 ** k * 4)
+
+    clocks = clk.summary()
+    # roofline of the counting kernel: algorithmic 32-bit AND+POPC word
+    # operations = C(n,k) * 3^k cells * (W1 + W0) words per launch
+    W = ((d.n_cases + 127) // 128 + (d.n_samples - d.n_cases + 127) // 128) * 4
+    alg_ops = total * (3 ** k) * W
+    kern_avg_s = (kern_ms / max(kern_n, 1)) / 1e3
+    achieved = alg_ops / kern_avg_s / 1e12
+    peak = N_SMS * POPC_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
+    roof = dict(bound="alu", achieved=achieved, peak=peak, unit="Tops/s", frac=achieved / peak, traffic=None,
+                kernel="popc_search_kernel", kernel_ms=kern_avg_s * 1e3,
+                ops_note="paper work: 3^k cells x (W1+W0) 32-bit AND+POPC per combination; "
+                         "peak = 152 SMs x 16 POPC/clk x 2070 MHz")
+
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+                ms_per_step=t_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="u32", data="synthetic",
+                config=dict(**workload_desc(args.workload, d, k, top_n), path=args.path,
+                            l2="flushed between steps (256 MiB write)", parallelism="replicas"),
+                e2e=dict(value=units / e2e_t, unit=UNIT, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h,
+                         seconds=e2e_t),
+                roofline=roof, gpu_launches=int(launches), clocks=clocks,
+                top1=dict(snps=[int(x) for x in res.combs[0]], mi=float(res.mi[0]), planted=list(d.planted)))
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline(d, k)
+        cb.pop("seconds", None)
+        line["cpu_baseline"] = cb
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--path", default="popc", choices=["popc", "tc", "auto"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

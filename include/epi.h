@@ -1,0 +1,153 @@
+/*
+ * libepi -- exhaustive k-SNP epistasis search on one GB300 GPU (sm_103a).
+ *
+ * The method is that of Ponte-Fernandez et al., "A SIMD algorithm for the
+ * detection of epistatic interactions of any order" (arXiv 2201.02460):
+ * for every k-subset S of SNPs, build the 3^k x 2 genotype/phenotype
+ * contingency table from bit-packed genotype tables (Section 2.1, Fig. 2),
+ * the last combination level fused with the population count (Section 2.2),
+ * score it by mutual information (Section 2.3, Eq. 1-3) and keep the best N
+ * (Section 2.4, Algorithm 1).
+ *
+ * Conventions shared by every call:
+ *   - Genotypes are uint8 in {0, 1, 2} (row g of a genotype table marks
+ *     genotype g), stored [n_snps][n_samples] row-major.  Phenotypes are uint8
+ *     in {0 = control, 1 = case}.  Missing genotypes are not supported.
+ *   - A combination is a strictly increasing tuple s_1 < ... < s_k of SNP
+ *     indices.  Its cell x = sum_t g_t 3^(k-t) (first SNP most significant,
+ *     the row order of a combined genotype table, Section 2.1).
+ *   - Tables are uint32 [2][3^k]: index 0 = cases, 1 = controls.
+ *   - MI is in nats with probabilities count / m over all m individuals and
+ *     0 log 0 = 0 (Eq. 1-3).  mi_f32 is the single-precision screening score;
+ *     mi is the double-precision re-score of the same table.
+ *   - Results are ordered by mi descending, equal mi broken by the
+ *     lexicographically smaller tuple.  n_out = min(top_n, C(n, k)).
+ *   - Host pointers are read or written during the call only; the caller
+ *     owns every buffer it passes.  Device pointers must be memory of the
+ *     context's device.
+ *   - Every call runs on the stream given to epi_create and returns after the
+ *     stream has finished the call's work, unless its name ends in _async.
+ *   - Errors: a call returns a status != EPI_OK, writes no output it has not
+ *     documented as partially written, and leaves a message for
+ *     epi_last_error() (per thread).  Device-side failures (a watchdog that
+ *     expired, a candidate pool that was too small) come back as status codes;
+ *     no kernel of the library traps.
+ */
+#ifndef EPI_H
+#define EPI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    EPI_OK = 0,
+    EPI_EINVAL = 1,        /* bad argument (value, size, pointer, order) */
+    EPI_ENOMEM = 2,        /* device or host allocation failed */
+    EPI_ECUDA = 3,         /* a CUDA runtime call failed */
+    EPI_EUNSUPPORTED = 4,  /* valid request this build cannot run */
+    EPI_ETIMEOUT = 5,      /* a bounded device wait gave up */
+    EPI_EOVERFLOW = 6      /* exact top-N not guaranteed even after retries */
+} epi_status;
+
+/* Counting path of the search. */
+typedef enum {
+    EPI_PATH_AUTO = 0,     /* fastest exact path for the order and sizes */
+    EPI_PATH_POPC = 1,     /* bitwise AND + POPC on the integer pipe */
+    EPI_PATH_TC = 2        /* exact 0/1 GEMM on tcgen05 tensor cores */
+} epi_path;
+
+#define EPI_MAX_ORDER 8    /* highest order the API accepts (Table 2 goes to 8) */
+
+typedef struct epi_ctx epi_ctx;
+typedef struct epi_dataset epi_dataset;
+
+/* One retained combination. */
+typedef struct {
+    uint32_t snp[EPI_MAX_ORDER];  /* s_1 < ... < s_k; entries k.. are 0 */
+    double mi;                    /* double-precision MI (nats) */
+    float mi_f32;                 /* single-precision screening MI (nats) */
+    uint32_t order;               /* k */
+    uint64_t rank;                /* lexicographic rank among the k-subsets */
+} epi_result;
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *epi_last_error(void);
+
+/* Context on CUDA device `device`; all work is queued on `cuda_stream` (a
+ * cudaStream_t, NULL = the legacy default stream).  The context owns its
+ * device scratch memory, allocated on first use and grown as needed. */
+epi_status epi_create(int device, void *cuda_stream, epi_ctx **out);
+void epi_destroy(epi_ctx *ctx);
+
+/* Genotype tables of a dataset (Section 2.1).  geno [n_snps][n_samples] and
+ * pheno [n_samples] are host memory when inputs_on_device = 0, device memory
+ * otherwise; they are read during the call only.  The library packs them on
+ * the device into per-SNP case and control bit rows.  Fails with EPI_EINVAL
+ * for n_snps < 1, n_samples < 1, n_samples > 2^24 - 1 or a value outside
+ * {0,1,2} / {0,1} (checked on the device for device inputs).  Device inputs
+ * that are not device memory of the context's device fail with EPI_EINVAL. */
+epi_status epi_dataset_create(epi_ctx *ctx, const uint8_t *geno, const uint8_t *pheno,
+                              int64_t n_snps, int64_t n_samples, int inputs_on_device,
+                              epi_dataset **out);
+void epi_dataset_destroy(epi_dataset *ds);
+
+/* Sizes of a dataset: n_snps, n_samples, n_cases, n_controls. */
+epi_status epi_dataset_info(const epi_dataset *ds, int64_t *n_snps, int64_t *n_samples,
+                            int64_t *n_cases, int64_t *n_controls);
+
+/* Exhaustive search of every k-subset (Algorithm 1), keeping the best top_n
+ * (Section 2.4).  out: host array of top_n records; counts (optional, may be
+ * NULL): host array [top_n][2][3^k]; *n_out receives min(top_n, C(n,k)).
+ * Orders 1..5 run on the GPU (EPI_EUNSUPPORTED above); top_n in [1, 1024]. */
+epi_status epi_search(epi_dataset *ds, int order, int top_n, int path, epi_result *out,
+                      uint32_t *counts, int *n_out);
+
+/* The same restricted to combinations of lexicographic rank in
+ * [rank_begin, rank_end) (rank_end clipped to C(n,k)): the resumable and
+ * shardable form of the search. */
+epi_status epi_search_range(epi_dataset *ds, int order, int top_n, int path,
+                            uint64_t rank_begin, uint64_t rank_end, epi_result *out,
+                            uint32_t *counts, int *n_out);
+
+/* Device-side form of epi_search: results are written to device memory
+ * (out_dev [top_n] records, counts_dev [top_n][2][3^k] or NULL, n_out_dev one
+ * int32) and status_dev (one int32, device) receives EPI_OK or the device
+ * status of the search.  Returns after queueing the work; the host does not
+ * wait.  A search that needs a larger candidate pool reports EPI_EOVERFLOW in
+ * status_dev instead of retrying. */
+epi_status epi_search_async(epi_dataset *ds, int order, int top_n, int path,
+                            epi_result *out_dev, uint32_t *counts_dev, int32_t *n_out_dev,
+                            int32_t *status_dev);
+
+/* Contingency tables (Section 2.2) of `count` given combinations.  combs:
+ * host [count][order] uint32, each strictly increasing and < n_snps;
+ * out: host [count][2][3^order].  order in 1..8. */
+epi_status epi_tables(epi_dataset *ds, int order, const uint32_t *combs, int64_t count,
+                      uint32_t *out);
+
+/* Single-precision and double-precision MI of `count` host tables
+ * [count][2][3^order] with the dataset's class sizes (Eq. 1-3); either
+ * output may be NULL. */
+epi_status epi_score_tables(epi_dataset *ds, int order, const uint32_t *tables, int64_t count,
+                            float *mi_f32, double *mi_f64);
+
+/* Number of kernels the library launched on this context since creation
+ * (a diagnostic counter). */
+uint64_t epi_kernel_launches(const epi_ctx *ctx);
+
+/* Timing of the dominant counting kernel.  After epi_profile_begin, every
+ * launch of a search's counting kernel is bracketed by CUDA events on the
+ * context's stream; epi_profile_end waits for those events and returns their
+ * summed duration in milliseconds and the number of bracketed launches. */
+epi_status epi_profile_begin(epi_ctx *ctx);
+epi_status epi_profile_end(epi_ctx *ctx, double *kernel_ms, int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EPI_H */

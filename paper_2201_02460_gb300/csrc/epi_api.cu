@@ -1,0 +1,591 @@
+// C-ABI of libepi: contexts, datasets and the search orchestration.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "epi_host.h"
+#include "epi_internal.cuh"
+
+using namespace epi;
+
+struct epi_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    size_t smem_optin = 0;
+    void *scratch = nullptr;
+    size_t scratch_bytes = 0;
+    uint64_t launches = 0;
+    bool profiling = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
+};
+
+struct epi_dataset {
+    epi_ctx *ctx = nullptr;
+    int64_t n = 0, m = 0, m1 = 0, m0 = 0;
+    int32_t W1 = 0, W0 = 0, Wt = 0;
+    uint32_t *masks = nullptr;
+    uint64_t *binom = nullptr;
+    DevData dev() const
+    {
+        DevData d;
+        d.n = n; d.m = m; d.m1 = m1; d.m0 = m0;
+        d.W1 = W1; d.W0 = W0; d.Wt = Wt;
+        d.masks = masks;
+        d.binom = binom;
+        return d;
+    }
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+epi_status fail(epi_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return fail(e_ == cudaErrorMemoryAllocation ? EPI_ENOMEM : EPI_ECUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                        \
+    } while (0)
+
+// Makes the context's device current for the scope of a call.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+// exact C(n, k) or UINT64_MAX
+uint64_t host_binom(int64_t n, int64_t k)
+{
+    if (k < 0 || n < 0 || k > n) return 0;
+    if (k > n - k) k = n - k;
+    unsigned __int128 r = 1;
+    for (int64_t i = 0; i < k; i++) {
+        r = r * (unsigned __int128)(n - i) / (unsigned __int128)(i + 1);
+        if (r > (unsigned __int128)UINT64_MAX) return UINT64_MAX;
+    }
+    return (uint64_t)r;
+}
+
+// true when p is device (or managed) memory usable on `device`
+bool is_device_ptr(const void *p, int device)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == device;
+}
+
+int pow3i(int k)
+{
+    int r = 1;
+    while (k-- > 0) r *= 3;
+    return r;
+}
+
+// Carves aligned pieces out of the context's scratch arena.
+struct Arena {
+    size_t off = 0;
+    template <typename T>
+    size_t take(size_t count)
+    {
+        off = (off + 255) & ~(size_t)255;
+        const size_t at = off;
+        off += count * sizeof(T);
+        return at;
+    }
+};
+
+epi_status ensure_scratch(epi_ctx *ctx, size_t bytes)
+{
+    if (ctx->scratch_bytes >= bytes) return EPI_OK;
+    if (ctx->scratch) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(ctx->scratch);
+        ctx->scratch = nullptr;
+        ctx->scratch_bytes = 0;
+    }
+    size_t want = std::max(bytes, (size_t)1 << 20);
+    want = (want + ((1u << 20) - 1)) & ~(size_t)((1u << 20) - 1);
+    CK(cudaMalloc(&ctx->scratch, want));
+    ctx->scratch_bytes = want;
+    return EPI_OK;
+}
+
+struct SearchPlan {
+    int k = 0, top_n = 0, pool = 0, tile = 0, slots = 0, cand_p2 = 0, grid = 0;
+    size_t smem = 0;
+    uint64_t rb = 0, re = 0, total = 0;
+};
+
+epi_status plan_popc(const epi_dataset *ds, SearchPlan &p)
+{
+    const epi_ctx *ctx = ds->ctx;
+    const uint64_t span = p.re - p.rb;
+    int tile = 512;
+    const uint64_t want_per_cta = span / ((uint64_t)ctx->num_sms * 2 + 1);
+    while (tile > 128 && (uint64_t)tile > want_per_cta) tile >>= 1;
+    p.tile = tile;
+    p.cand_p2 = next_pow2(p.pool + 2 * tile);
+    const size_t limit = ctx->smem_optin ? ctx->smem_optin : 227 * 1024;
+    int best_slots = 0, best_occ = 0;
+    size_t best_smem = 0;
+    for (int s = 8; s >= 1; s--) {
+        const size_t sm = popc_smem_bytes(p.k, ds->Wt, s, p.cand_p2) + 1024;
+        if (sm > limit) continue;
+        const int occ = popc_max_active(p.k, sm);
+        if (occ <= 0) continue;
+        // prefer two resident CTAs per SM, then more staged prefixes
+        const int score_new = std::min(occ, 2) * 16 + s;
+        const int score_old = std::min(best_occ, 2) * 16 + best_slots;
+        if (best_slots == 0 || score_new > score_old) { best_slots = s; best_occ = occ; best_smem = sm; }
+    }
+    if (best_slots == 0)
+        return fail(EPI_EUNSUPPORTED, "order %d with %lld samples: one prefix table does not fit in shared memory",
+                    p.k, (long long)ds->m);
+    p.slots = best_slots;
+    p.smem = best_smem;
+    uint64_t grid = (uint64_t)ctx->num_sms * (uint64_t)best_occ;
+    const uint64_t by_work = (span + 127) / 128;
+    if (grid > by_work) grid = by_work;
+    if (grid < 1) grid = 1;
+    p.grid = (int)grid;
+    return EPI_OK;
+}
+
+// Queues one search pass with the given plan; results land in device memory.
+epi_status queue_search(epi_dataset *ds, const SearchPlan &p, int path, epi_result *out_dev, uint32_t *counts_dev,
+                        int32_t *n_out_dev, int32_t **status_dev_out)
+{
+    epi_ctx *ctx = ds->ctx;
+    (void)path;
+    const int cells = pow3i(p.k);
+    Arena a;
+    const size_t o_thr = a.take<uint32_t>(1);
+    const size_t o_status = a.take<int32_t>(1);
+    const size_t o_ls = a.take<float>((size_t)p.grid * p.pool);
+    const size_t o_lr = a.take<uint64_t>((size_t)p.grid * p.pool);
+    const size_t o_lc = a.take<int32_t>((size_t)p.grid);
+    const size_t o_cs = a.take<float>((size_t)p.pool);
+    const size_t o_cr = a.take<uint64_t>((size_t)p.pool);
+    const size_t o_cn = a.take<int32_t>(1);
+    const size_t o_ct = a.take<uint32_t>((size_t)p.pool * 2 * cells);
+    const size_t o_mi = a.take<double>((size_t)p.pool);
+    const size_t o_cb = a.take<int32_t>((size_t)p.pool * p.k);
+    epi_status st = ensure_scratch(ctx, a.off);
+    if (st != EPI_OK) return st;
+    char *base = static_cast<char *>(ctx->scratch);
+    uint32_t *thr = reinterpret_cast<uint32_t *>(base + o_thr);
+    int32_t *status = reinterpret_cast<int32_t *>(base + o_status);
+    float *ls = reinterpret_cast<float *>(base + o_ls);
+    uint64_t *lr = reinterpret_cast<uint64_t *>(base + o_lr);
+    int32_t *lc = reinterpret_cast<int32_t *>(base + o_lc);
+    float *cs = reinterpret_cast<float *>(base + o_cs);
+    uint64_t *cr = reinterpret_cast<uint64_t *>(base + o_cr);
+    int32_t *cn = reinterpret_cast<int32_t *>(base + o_cn);
+    uint32_t *ct = reinterpret_cast<uint32_t *>(base + o_ct);
+    double *mi = reinterpret_cast<double *>(base + o_mi);
+    int32_t *cb = reinterpret_cast<int32_t *>(base + o_cb);
+    // threshold word and status word live in the first 512 bytes
+    CK(cudaMemsetAsync(base, 0, 512, ctx->stream));
+    const DevData d = ds->dev();
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (ctx->profiling) {
+        CK(cudaEventCreate(&ev0));
+        CK(cudaEventCreate(&ev1));
+        ctx->prof_events.emplace_back(ev0, ev1);
+        CK(cudaEventRecord(ev0, ctx->stream));
+    }
+    CK(launch_popc_search(d, p.k, p.rb, p.re, p.tile, p.pool, p.slots, p.cand_p2, thr, ls, lr, lc, p.grid, p.smem,
+                          ctx->stream));
+    if (ev1) CK(cudaEventRecord(ev1, ctx->stream));
+    CK(launch_merge(ls, lr, lc, p.grid, p.pool, p.pool, cs, cr, cn, ctx->stream));
+    CK(launch_rescore(d, p.k, p.pool, cr, cn, ct, mi, cb, ctx->stream));
+    CK(launch_finalize(d, p.k, p.top_n, p.pool, cs, cr, cn, mi, cb, ct, thr, p.re - p.rb, out_dev, counts_dev,
+                       n_out_dev, status, ctx->stream));
+    ctx->launches += 4;
+    *status_dev_out = status;
+    return EPI_OK;
+}
+
+epi_status check_search_args(epi_dataset *ds, int order, int top_n, int path, uint64_t rb, uint64_t &re,
+                             uint64_t &total)
+{
+    if (!ds) return fail(EPI_EINVAL, "dataset is NULL");
+    if (order < 1 || order > EPI_MAX_ORDER) return fail(EPI_EINVAL, "order %d outside 1..%d", order, EPI_MAX_ORDER);
+    if (order > ds->n) return fail(EPI_EINVAL, "order %d exceeds the %lld SNPs", order, (long long)ds->n);
+    if (top_n < 1 || top_n > 1024) return fail(EPI_EINVAL, "top_n %d outside 1..1024", top_n);
+    if (path < EPI_PATH_AUTO || path > EPI_PATH_TC) return fail(EPI_EINVAL, "unknown path %d", path);
+    if (order > kMaxOrderGpu) return fail(EPI_EUNSUPPORTED, "order %d: the GPU search covers orders 1..%d", order,
+                                          kMaxOrderGpu);
+    total = host_binom(ds->n, order);
+    if (total >= ((uint64_t)1 << 62)) return fail(EPI_EUNSUPPORTED, "C(%lld, %d) is too large", (long long)ds->n, order);
+    if (re > total) re = total;
+    if (rb > re) rb = re;
+    (void)rb;
+    return EPI_OK;
+}
+
+int initial_pool(int top_n)
+{
+    int p = std::max(top_n + 64, 128);
+    return (p + 31) & ~31;
+}
+
+constexpr int kMaxPool = 4096;
+
+epi_status run_search_sync(epi_dataset *ds, int order, int top_n, int path, uint64_t rb, uint64_t re,
+                           epi_result *out, uint32_t *counts, int *n_out)
+{
+    uint64_t total = 0;
+    epi_status st = check_search_args(ds, order, top_n, path, rb, re, total);
+    if (st != EPI_OK) return st;
+    if (!out || !n_out) return fail(EPI_EINVAL, "out and n_out must not be NULL");
+    epi_ctx *ctx = ds->ctx;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(EPI_ECUDA, "cannot select device %d", ctx->device);
+    *n_out = 0;
+    if (rb >= re) return EPI_OK;
+    const int cells = pow3i(order);
+    int pool = initial_pool(top_n);
+    for (;;) {
+        SearchPlan p;
+        p.k = order; p.top_n = top_n; p.pool = pool; p.rb = rb; p.re = re; p.total = total;
+        st = plan_popc(ds, p);
+        if (st != EPI_OK) return st;
+        // device-side outputs of this pass (stream-ordered allocation)
+        const size_t rec_b = ((size_t)top_n * sizeof(epi_result) + 255) & ~(size_t)255;
+        const size_t cnt_b = ((size_t)top_n * 2 * cells * 4 + 255) & ~(size_t)255;
+        void *dout = nullptr;
+        CK(cudaMallocAsync(&dout, rec_b + cnt_b + 256, ctx->stream));
+        epi_result *out_dev = static_cast<epi_result *>(dout);
+        uint32_t *cnt_dev = reinterpret_cast<uint32_t *>(static_cast<char *>(dout) + rec_b);
+        int32_t *nout_dev = reinterpret_cast<int32_t *>(static_cast<char *>(dout) + rec_b + cnt_b);
+        int32_t *status_dev = nullptr;
+        st = queue_search(ds, p, path, out_dev, counts ? cnt_dev : nullptr, nout_dev, &status_dev);
+        if (st != EPI_OK) { cudaFreeAsync(dout, ctx->stream); return st; }
+        int32_t hst[2] = {0, 0};
+        CK(cudaMemcpyAsync(&hst[0], status_dev, 4, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaMemcpyAsync(&hst[1], nout_dev, 4, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        if (hst[0] & ST_POOL_OVERFLOW) {
+            cudaFreeAsync(dout, ctx->stream);
+            if (pool >= kMaxPool)
+                return fail(EPI_EOVERFLOW, "candidate pool of %d cannot prove the exact top %d (ties)", pool, top_n);
+            pool = std::min(pool * 4, kMaxPool);
+            continue;
+        }
+        if (hst[0] & ST_TIMEOUT) { cudaFreeAsync(dout, ctx->stream); return fail(EPI_ETIMEOUT, "device wait expired"); }
+        if (hst[0] != 0) { cudaFreeAsync(dout, ctx->stream); return fail(EPI_ECUDA, "device status 0x%x", hst[0]); }
+        const int n = hst[1];
+        CK(cudaMemcpyAsync(out, out_dev, (size_t)n * sizeof(epi_result), cudaMemcpyDeviceToHost, ctx->stream));
+        if (counts)
+            CK(cudaMemcpyAsync(counts, cnt_dev, (size_t)n * 2 * cells * 4, cudaMemcpyDeviceToHost, ctx->stream));
+        cudaFreeAsync(dout, ctx->stream);
+        CK(cudaStreamSynchronize(ctx->stream));
+        *n_out = n;
+        return EPI_OK;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *epi_last_error(void) { return g_err.c_str(); }
+
+epi_status epi_create(int device, void *cuda_stream, epi_ctx **out)
+{
+    if (!out) return fail(EPI_EINVAL, "out is NULL");
+    *out = nullptr;
+    int count = 0;
+    CK(cudaGetDeviceCount(&count));
+    if (device < 0 || device >= count) return fail(EPI_EINVAL, "device %d outside 0..%d", device, count - 1);
+    DeviceGuard g(device);
+    if (!g.ok) return fail(EPI_ECUDA, "cannot select device %d", device);
+    cudaDeviceProp prop;
+    CK(cudaGetDeviceProperties(&prop, device));
+    if (prop.major < 10) return fail(EPI_EUNSUPPORTED, "device %d is sm_%d%d; this build targets sm_103a", device,
+                                     prop.major, prop.minor);
+    epi_ctx *c = new epi_ctx();
+    c->device = device;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    c->num_sms = prop.multiProcessorCount;
+    c->smem_optin = prop.sharedMemPerBlockOptin;
+    *out = c;
+    return EPI_OK;
+}
+
+void epi_destroy(epi_ctx *ctx)
+{
+    if (!ctx) return;
+    DeviceGuard g(ctx->device);
+    if (ctx->scratch) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(ctx->scratch);
+    }
+    delete ctx;
+}
+
+epi_status epi_dataset_create(epi_ctx *ctx, const uint8_t *geno, const uint8_t *pheno, int64_t n_snps,
+                              int64_t n_samples, int inputs_on_device, epi_dataset **out)
+{
+    if (!ctx || !geno || !pheno || !out) return fail(EPI_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (n_snps < 1 || n_samples < 1) return fail(EPI_EINVAL, "need at least one SNP and one sample");
+    if (n_samples > (1 << 24) - 1) return fail(EPI_EINVAL, "n_samples %lld above 2^24-1", (long long)n_samples);
+    if (n_snps > (1 << 24)) return fail(EPI_EINVAL, "n_snps %lld above 2^24", (long long)n_snps);
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(EPI_ECUDA, "cannot select device %d", ctx->device);
+    cudaStream_t st = ctx->stream;
+    const int64_t n = n_snps, m = n_samples;
+    uint8_t *dgeno = nullptr, *dpheno = nullptr, *tmp = nullptr;
+    if (inputs_on_device) {
+        if (!is_device_ptr(geno, ctx->device) || !is_device_ptr(pheno, ctx->device))
+            return fail(EPI_EINVAL, "inputs_on_device set but geno/pheno are not device memory of device %d",
+                        ctx->device);
+        dgeno = const_cast<uint8_t *>(geno);
+        dpheno = const_cast<uint8_t *>(pheno);
+    } else {
+        CK(cudaMallocAsync((void **)&tmp, (size_t)(n * m + m), st));
+        dgeno = tmp;
+        dpheno = tmp + n * m;
+        CK(cudaMemcpyAsync(dgeno, geno, (size_t)(n * m), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(dpheno, pheno, (size_t)m, cudaMemcpyHostToDevice, st));
+    }
+    void *work = nullptr;
+    const size_t work_bytes = (size_t)m * 8 + 64;
+    CK(cudaMallocAsync(&work, work_bytes, st));
+    int32_t *case_idx = static_cast<int32_t *>(work);
+    int32_t *ctrl_idx = case_idx + m;
+    int64_t *dm1 = reinterpret_cast<int64_t *>(ctrl_idx + m + (m & 1));
+    int32_t *dstatus = reinterpret_cast<int32_t *>(dm1 + 1);
+    CK(cudaMemsetAsync(dstatus, 0, 4, st));
+    launch_scan_pheno(dpheno, m, case_idx, ctrl_idx, dm1, dstatus, st);
+    CK(cudaGetLastError());
+    int64_t m1 = 0;
+    int32_t hstatus = 0;
+    CK(cudaMemcpyAsync(&m1, dm1, 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&hstatus, dstatus, 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    epi_status ret = EPI_OK;
+    epi_dataset *ds = nullptr;
+    if (hstatus & ST_BAD_PHENO) {
+        ret = fail(EPI_EINVAL, "phenotype values must be 0 or 1");
+    } else {
+        ds = new epi_dataset();
+        ds->ctx = ctx;
+        ds->n = n; ds->m = m; ds->m1 = m1; ds->m0 = m - m1;
+        ds->W1 = (int32_t)(((m1 + 127) / 128) * 4);
+        ds->W0 = (int32_t)(((m - m1 + 127) / 128) * 4);
+        ds->Wt = ds->W1 + ds->W0;
+        cudaError_t e1 = cudaMalloc((void **)&ds->masks, (size_t)n * 3 * ds->Wt * 4);
+        cudaError_t e2 = cudaMalloc((void **)&ds->binom, (size_t)9 * (n + 1) * 8);
+        if (e1 != cudaSuccess || e2 != cudaSuccess) {
+            ret = fail(EPI_ENOMEM, "dataset allocation failed");
+        } else {
+            launch_pack_masks(dgeno, n, m, case_idx, ctrl_idx, m1, ds->W1, ds->Wt, ds->masks, dstatus, ctx->num_sms, st);
+            launch_binom(n, ds->binom, ctx->num_sms, st);
+            ctx->launches += 3;
+            cudaError_t e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&hstatus, dstatus, 4, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) ret = fail(EPI_ECUDA, "packing failed: %s", cudaGetErrorString(e));
+            else if (hstatus & ST_BAD_GENO) ret = fail(EPI_EINVAL, "genotype values must be 0, 1 or 2");
+        }
+    }
+    cudaFreeAsync(work, st);
+    if (tmp) cudaFreeAsync(tmp, st);
+    cudaStreamSynchronize(st);
+    if (ret != EPI_OK) {
+        if (ds) { cudaFree(ds->masks); cudaFree(ds->binom); delete ds; }
+        return ret;
+    }
+    *out = ds;
+    return EPI_OK;
+}
+
+void epi_dataset_destroy(epi_dataset *ds)
+{
+    if (!ds) return;
+    DeviceGuard g(ds->ctx->device);
+    cudaStreamSynchronize(ds->ctx->stream);
+    cudaFree(ds->masks);
+    cudaFree(ds->binom);
+    delete ds;
+}
+
+epi_status epi_dataset_info(const epi_dataset *ds, int64_t *n_snps, int64_t *n_samples, int64_t *n_cases,
+                            int64_t *n_controls)
+{
+    if (!ds) return fail(EPI_EINVAL, "dataset is NULL");
+    if (n_snps) *n_snps = ds->n;
+    if (n_samples) *n_samples = ds->m;
+    if (n_cases) *n_cases = ds->m1;
+    if (n_controls) *n_controls = ds->m0;
+    return EPI_OK;
+}
+
+epi_status epi_search(epi_dataset *ds, int order, int top_n, int path, epi_result *out, uint32_t *counts, int *n_out)
+{
+    return run_search_sync(ds, order, top_n, path, 0, UINT64_MAX, out, counts, n_out);
+}
+
+epi_status epi_search_range(epi_dataset *ds, int order, int top_n, int path, uint64_t rank_begin, uint64_t rank_end,
+                            epi_result *out, uint32_t *counts, int *n_out)
+{
+    return run_search_sync(ds, order, top_n, path, rank_begin, rank_end, out, counts, n_out);
+}
+
+epi_status epi_search_async(epi_dataset *ds, int order, int top_n, int path, epi_result *out_dev,
+                            uint32_t *counts_dev, int32_t *n_out_dev, int32_t *status_dev)
+{
+    uint64_t total = 0, re = UINT64_MAX;
+    epi_status st = check_search_args(ds, order, top_n, path, 0, re, total);
+    if (st != EPI_OK) return st;
+    if (!out_dev || !n_out_dev || !status_dev) return fail(EPI_EINVAL, "NULL output pointer");
+    epi_ctx *ctx = ds->ctx;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(EPI_ECUDA, "cannot select device %d", ctx->device);
+    if (!is_device_ptr(out_dev, ctx->device) || !is_device_ptr(n_out_dev, ctx->device) ||
+        !is_device_ptr(status_dev, ctx->device) || (counts_dev && !is_device_ptr(counts_dev, ctx->device)))
+        return fail(EPI_EINVAL, "epi_search_async outputs must be device memory of device %d", ctx->device);
+    SearchPlan p;
+    p.k = order; p.top_n = top_n; p.pool = initial_pool(top_n); p.rb = 0; p.re = re; p.total = total;
+    st = plan_popc(ds, p);
+    if (st != EPI_OK) return st;
+    int32_t *status = nullptr;
+    st = queue_search(ds, p, path, out_dev, counts_dev, n_out_dev, &status);
+    if (st != EPI_OK) return st;
+    // device status bits to an epi_status code
+    CK(launch_publish_status(status, status_dev, ctx->stream));
+    ctx->launches += 1;
+    return EPI_OK;
+}
+
+epi_status epi_tables(epi_dataset *ds, int order, const uint32_t *combs, int64_t count, uint32_t *out)
+{
+    if (!ds) return fail(EPI_EINVAL, "dataset is NULL");
+    if (order < 1 || order > EPI_MAX_ORDER) return fail(EPI_EINVAL, "order %d outside 1..%d", order, EPI_MAX_ORDER);
+    if (count < 0) return fail(EPI_EINVAL, "negative count");
+    if (count == 0) return EPI_OK;
+    if (!combs || !out) return fail(EPI_EINVAL, "NULL argument");
+    for (int64_t c = 0; c < count; c++)
+        for (int t = 0; t < order; t++) {
+            const uint32_t v = combs[c * order + t];
+            if (v >= (uint64_t)ds->n || (t && v <= combs[c * order + t - 1]))
+                return fail(EPI_EINVAL, "combination %lld is not strictly increasing within 0..%lld", (long long)c,
+                            (long long)ds->n - 1);
+        }
+    epi_ctx *ctx = ds->ctx;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(EPI_ECUDA, "cannot select device %d", ctx->device);
+    const size_t cells = (size_t)pow3i(order);
+    const size_t in_b = (size_t)count * order * 4, out_b = (size_t)count * 2 * cells * 4;
+    void *buf = nullptr;
+    CK(cudaMallocAsync(&buf, in_b + out_b + 256, ctx->stream));
+    uint32_t *dc = static_cast<uint32_t *>(buf);
+    uint32_t *dout = reinterpret_cast<uint32_t *>(static_cast<char *>(buf) + ((in_b + 255) & ~(size_t)255));
+    cudaError_t e = cudaMemcpyAsync(dc, combs, in_b, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = launch_tables(ds->dev(), order, dc, count, dout, ctx->num_sms, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, out_b, cudaMemcpyDeviceToHost, ctx->stream);
+    cudaFreeAsync(buf, ctx->stream);
+    ctx->launches += 1;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return fail(EPI_ECUDA, "tables: %s", cudaGetErrorString(e));
+    return EPI_OK;
+}
+
+epi_status epi_score_tables(epi_dataset *ds, int order, const uint32_t *tables, int64_t count, float *mi_f32,
+                            double *mi_f64)
+{
+    if (!ds) return fail(EPI_EINVAL, "dataset is NULL");
+    if (order < 1 || order > EPI_MAX_ORDER) return fail(EPI_EINVAL, "order %d outside 1..%d", order, EPI_MAX_ORDER);
+    if (count < 0) return fail(EPI_EINVAL, "negative count");
+    if (count == 0) return EPI_OK;
+    if (!tables) return fail(EPI_EINVAL, "NULL tables");
+    epi_ctx *ctx = ds->ctx;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(EPI_ECUDA, "cannot select device %d", ctx->device);
+    const size_t cells = (size_t)pow3i(order);
+    const size_t in_b = (size_t)count * 2 * cells * 4;
+    void *buf = nullptr;
+    CK(cudaMallocAsync(&buf, in_b + (size_t)count * 12 + 512, ctx->stream));
+    uint32_t *dt = static_cast<uint32_t *>(buf);
+    char *p = static_cast<char *>(buf) + ((in_b + 255) & ~(size_t)255);
+    double *d64 = reinterpret_cast<double *>(p);
+    float *d32 = reinterpret_cast<float *>(p + (((size_t)count * 8 + 255) & ~(size_t)255));
+    cudaError_t e = cudaMemcpyAsync(dt, tables, in_b, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = launch_score_tables(ds->dev(), order, dt, count, d32, d64, ctx->num_sms, ctx->stream);
+    if (e == cudaSuccess && mi_f32) e = cudaMemcpyAsync(mi_f32, d32, (size_t)count * 4, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess && mi_f64) e = cudaMemcpyAsync(mi_f64, d64, (size_t)count * 8, cudaMemcpyDeviceToHost, ctx->stream);
+    cudaFreeAsync(buf, ctx->stream);
+    ctx->launches += 1;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return fail(EPI_ECUDA, "score_tables: %s", cudaGetErrorString(e));
+    return EPI_OK;
+}
+
+uint64_t epi_kernel_launches(const epi_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+epi_status epi_profile_begin(epi_ctx *ctx)
+{
+    if (!ctx) return fail(EPI_EINVAL, "context is NULL");
+    DeviceGuard g(ctx->device);
+    for (auto &pr : ctx->prof_events) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
+    ctx->prof_events.clear();
+    ctx->profiling = true;
+    return EPI_OK;
+}
+
+epi_status epi_profile_end(epi_ctx *ctx, double *kernel_ms, int64_t *launches)
+{
+    if (!ctx || !kernel_ms || !launches) return fail(EPI_EINVAL, "NULL argument");
+    DeviceGuard g(ctx->device);
+    double total = 0.0;
+    epi_status st = EPI_OK;
+    for (auto &pr : ctx->prof_events) {
+        float ms = 0.0f;
+        cudaError_t e = cudaEventSynchronize(pr.second);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, pr.first, pr.second);
+        if (e != cudaSuccess && st == EPI_OK) st = fail(EPI_ECUDA, "profile events: %s", cudaGetErrorString(e));
+        total += ms;
+    }
+    *kernel_ms = total;
+    *launches = (int64_t)ctx->prof_events.size();
+    for (auto &pr : ctx->prof_events) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
+    ctx->prof_events.clear();
+    ctx->profiling = false;
+    return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,42 @@
+// Host-side launchers of libepi's kernels (one definition per .cu file).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "epi_internal.cuh"
+
+namespace epi {
+
+// epi_data.cu
+void launch_scan_pheno(const uint8_t *pheno, int64_t m, int32_t *case_idx, int32_t *ctrl_idx, int64_t *m1,
+                       int32_t *status, cudaStream_t st);
+void launch_pack_masks(const uint8_t *geno, int64_t n, int64_t m, const int32_t *case_idx, const int32_t *ctrl_idx,
+                       int64_t m1, int32_t W1, int32_t Wt, uint32_t *masks, int32_t *status, int num_sms,
+                       cudaStream_t st);
+void launch_binom(int64_t n, uint64_t *tab, int num_sms, cudaStream_t st);
+
+// epi_popc.cu
+size_t popc_smem_bytes(int k, int32_t Wt, int slots, int cand_p2);
+int popc_max_active(int k, size_t smem);
+cudaError_t launch_popc_search(const DevData &d, int k, uint64_t rank_begin, uint64_t rank_end, int tile, int pool,
+                               int slots, int cand_p2, uint32_t *global_thr, float *list_score, uint64_t *list_rank,
+                               int32_t *list_count, int grid, size_t smem, cudaStream_t st);
+
+// epi_select.cu
+cudaError_t launch_merge(const float *ls, const uint64_t *lr, const int32_t *lc, int nlists, int stride, int pool,
+                         float *out_s, uint64_t *out_r, int32_t *out_n, cudaStream_t st);
+cudaError_t launch_rescore(const DevData &d, int k, int pool, const uint64_t *cand_r, const int32_t *cand_n,
+                           uint32_t *counts, double *mi64, int32_t *combs, cudaStream_t st);
+cudaError_t launch_finalize(const DevData &d, int k, int top_n, int pool, const float *cand_s, const uint64_t *cand_r,
+                            const int32_t *cand_n, const double *mi64, const int32_t *combs, const uint32_t *counts,
+                            const uint32_t *global_thr, uint64_t total, epi_result *out, uint32_t *out_counts,
+                            int32_t *n_out, int32_t *status, cudaStream_t st);
+cudaError_t launch_tables(const DevData &d, int k, const uint32_t *combs, int64_t count, uint32_t *out, int num_sms,
+                          cudaStream_t st);
+cudaError_t launch_publish_status(const int32_t *bits, int32_t *code, cudaStream_t st);
+cudaError_t launch_score_tables(const DevData &d, int k, const uint32_t *tabs, int64_t count, float *f32, double *f64,
+                                int num_sms, cudaStream_t st);
+
+}  // namespace epi

@@ -1,0 +1,190 @@
+// Internal declarations of libepi shared by its CUDA translation units.
+//
+// Device data layout of a dataset (the genotype tables of Section 2.1):
+//   masks  uint32 [n][3][Wt]  row g of SNP s: bit b of word w is individual
+//                             32 w + b; words [0, W1) hold the cases,
+//                             [W1, Wt) the controls (each subtable in input
+//                             order, zero padded to a multiple of 128 bits)
+//   binom  uint64 [9][n + 1]  C(a, b) for 0 <= a <= n, 0 <= b <= 8
+// A combination's flat index is its lexicographic rank; consecutive ranks
+// share their (k-1)-prefix and differ in the last SNP, as in the
+// depth-first order of Algorithm 1.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/epi.h"
+
+namespace epi {
+
+constexpr int kMaxOrderGpu = 5;          // orders with specialised kernels
+constexpr int kMaxPoolLists = 8192;      // entries of one candidate list
+constexpr uint64_t kBinomSaturated = ~0ull;
+
+// device status bits (OR-ed by kernels, read by the host after a call)
+enum : int32_t {
+    ST_BAD_GENO = 1,
+    ST_BAD_PHENO = 2,
+    ST_POOL_OVERFLOW = 4,
+    ST_TIMEOUT = 8,
+    ST_INTERNAL = 16,
+};
+
+struct DevData {
+    int64_t n, m, m1, m0;
+    int32_t W1, W0, Wt;          // uint32 words per subtable row
+    const uint32_t *masks;       // [n][3][Wt]
+    const uint64_t *binom;       // [9][n+1]
+};
+
+__host__ __device__ inline uint64_t binom_at(const uint64_t *tab, int64_t n, int64_t a, int b)
+{
+    if (b < 0 || a < b || a < 0) return 0;
+    return tab[(int64_t)b * (n + 1) + a];
+}
+
+// Lexicographic unranking of r among the k-subsets of [0, n) (count of
+// subsets whose element t is below c is C(n-start, k-t) - C(n-c, k-t)).
+__device__ inline void unrank_lex(const uint64_t *tab, int64_t n, int k, uint64_t r, int32_t *out)
+{
+    int64_t start = 0;
+    for (int t = 0; t < k; t++) {
+        const int rem = k - t;                       // elements still to place
+        const uint64_t total = binom_at(tab, n, n - start, rem);
+        const uint64_t x = total - r;                // >= 1
+        // smallest c in [start, n-rem] with C(n-1-c, rem) < x
+        int64_t lo = start, hi = n - rem;
+        while (lo < hi) {
+            int64_t mid = (lo + hi) >> 1;
+            if (binom_at(tab, n, n - 1 - mid, rem) < x) hi = mid;
+            else lo = mid + 1;
+        }
+        r -= total - binom_at(tab, n, n - lo, rem);
+        out[t] = (int32_t)lo;
+        start = lo + 1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Mutual information per cell.
+//
+// Eq. 1 written as a sum of non-negative terms: with e = n_x m_y / m the
+// count expected under independence and u = n / e - 1,
+//     m * MI = sum over cells and classes of  e * phi(u),
+//     phi(u) = (1 + u) ln(1 + u) - u  >= 0,
+// because n ln(n/e) = e phi(u) + (n - e) and the (n - e) sum to zero within
+// each cell.  Every term is >= 0, so the sum has no cancellation and the
+// single-precision value keeps a small relative error even when MI is small.
+// phi is evaluated through y = u / (2 + u), ln(1+u) = 2 atanh(y):
+//     phi(u) = u y + 2 (1 + u) y (y^2/3 + y^4/5 + ...)
+// for |y| <= 1/2, and directly as (1+u) log1p(u) - u elsewhere (no
+// cancellation there).  log1p is CUDA's.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float phi_f32(float u)
+{
+    if (u >= -0.6666667f && u <= 2.0f) {
+        const float y = u / (2.0f + u);
+        const float y2 = y * y;
+        float s = 1.0f / 23.0f;
+        s = fmaf(s, y2, 1.0f / 21.0f);
+        s = fmaf(s, y2, 1.0f / 19.0f);
+        s = fmaf(s, y2, 1.0f / 17.0f);
+        s = fmaf(s, y2, 1.0f / 15.0f);
+        s = fmaf(s, y2, 1.0f / 13.0f);
+        s = fmaf(s, y2, 1.0f / 11.0f);
+        s = fmaf(s, y2, 1.0f / 9.0f);
+        s = fmaf(s, y2, 1.0f / 7.0f);
+        s = fmaf(s, y2, 1.0f / 5.0f);
+        s = fmaf(s, y2, 1.0f / 3.0f);
+        s *= y2;
+        return fmaf(2.0f * (1.0f + u) * y, s, u * y);
+    }
+    return fmaf(1.0f + u, log1pf(u), -u);
+}
+
+__device__ __forceinline__ double phi_f64(double u)
+{
+    if (u >= -0.25 && u <= 0.4) {
+        // |y| <= 1/6.9: 14 terms reach double precision
+        const double y = u / (2.0 + u);
+        const double y2 = y * y;
+        double s = 1.0 / 29.0;
+        for (int d = 27; d >= 3; d -= 2) s = fma(s, y2, 1.0 / d);
+        s *= y2;
+        return fma(2.0 * (1.0 + u) * y, s, u * y);
+    }
+    return fma(1.0 + u, log1p(u), -u);
+}
+
+// e * phi(u) for count n of class size my in a cell with total nx.
+__device__ __forceinline__ float mi_term_f32(uint32_t n, uint32_t nx, int64_t my, int64_t m, float inv_m)
+{
+    if (nx == 0 || my == 0) return 0.0f;
+    const int64_t den = (int64_t)nx * my;          // m * e, exact
+    const float e = (float)den * inv_m;
+    if (n == 0) return e;                          // phi(-1) = 1
+    const int64_t num = (int64_t)n * m - den;      // m * (n - e), exact
+    return e * phi_f32((float)num / (float)den);
+}
+
+__device__ __forceinline__ double mi_term_f64(uint32_t n, uint32_t nx, int64_t my, int64_t m)
+{
+    if (nx == 0 || my == 0) return 0.0;
+    const int64_t den = (int64_t)nx * my;
+    const double e = (double)den / (double)m;
+    if (n == 0) return e;
+    const int64_t num = (int64_t)n * m - den;
+    return e * phi_f64((double)num / (double)den);
+}
+
+// Relative bound on |MI_f32 - MI| used to size the exact-top-N margin: each
+// term carries a few roundings, the sum of L = 2 * 3^k non-negative terms at
+// most L more; a factor 2 of headroom.
+__host__ __device__ inline double f32_rel_bound(int k)
+{
+    int64_t cells = 1;
+    for (int t = 0; t < k; t++) cells *= 3;
+    return 2.0 * (double)(2 * cells + 32) * 5.9604644775390625e-8;
+}
+
+// ---------------------------------------------------------------------------
+// Candidate lists: (score, rank) pairs ordered by score descending, then
+// rank ascending.  Kept in shared memory as separate arrays.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool cand_better(float sa, uint64_t ra, float sb, uint64_t rb)
+{
+    return sa > sb || (sa == sb && ra < rb);
+}
+
+// Bitonic sort of size p2 (power of two) over the whole block.  Entries past
+// the live count must already hold the sentinel (-1, ~0).
+__device__ inline void block_sort_cands(float *sc, uint64_t *rk, int p2)
+{
+    for (int kk = 2; kk <= p2; kk <<= 1) {
+        for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+            for (int i = threadIdx.x; i < p2; i += blockDim.x) {
+                const int ixj = i ^ jj;
+                if (ixj > i) {
+                    const bool up = (i & kk) == 0;
+                    const bool sw = up ? cand_better(sc[ixj], rk[ixj], sc[i], rk[i])
+                                       : cand_better(sc[i], rk[i], sc[ixj], rk[ixj]);
+                    if (sw) {
+                        float ts = sc[i]; sc[i] = sc[ixj]; sc[ixj] = ts;
+                        uint64_t tr = rk[i]; rk[i] = rk[ixj]; rk[ixj] = tr;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__host__ __device__ inline int next_pow2(int x)
+{
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+}  // namespace epi

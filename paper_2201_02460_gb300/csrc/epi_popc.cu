@@ -1,0 +1,370 @@
+// Popcount counting path of the exhaustive search.
+//
+// Section 2.4 / Algorithm 1: combinations are visited prefix by prefix; the
+// genotype table of the (k-1)-prefix (Section 2.1, Listing A.1 semantics:
+// row-wise AND) is built once into shared memory and reused for every last
+// SNP j; the last level is never stored but fused with the population count
+// (Section 2.2, Listing A.2 semantics).  The score is the single-precision MI
+// of Eq. 1-3 (Section 2.3) and only the best candidates are kept
+// (Section 2.4).
+//
+// GPU mapping:
+//   * persistent grid; CTA b owns the contiguous lexicographic rank range
+//     [R_b, R_{b+1}) (every combination costs the same, so a static split
+//     balances); it unranks R_b once and then steps prefixes in lex order;
+//   * a sub-tile is up to T consecutive ranks spanning at most `slots`
+//     prefixes; their tables are staged in shared memory as uint4 rows;
+//   * one thread per combination: 128-bit loads of the last SNP's rows for
+//     genotypes 0 and 1, AND + POPC against every prefix row; genotype 2 is
+//     the prefix row's total minus the other two (exact, saves a third of
+//     the work);
+//   * the counts never leave registers: MI is evaluated in the same thread
+//     and compared against the CTA's current threshold; survivors go to a
+//     shared-memory buffer that is merged into the CTA's sorted list.
+#include "epi_internal.cuh"
+#include "epi_host.h"
+
+namespace epi {
+
+__host__ __device__ constexpr int ipow3(int k) { return k <= 0 ? 1 : 3 * ipow3(k - 1); }
+
+struct PopcParams {
+    DevData d;
+    uint64_t rank_begin, rank_end;  // lexicographic range searched
+    int32_t tile;                   // combinations per sub-tile (T)
+    int32_t pool;                   // list entries kept per CTA
+    int32_t slots;                  // prefixes staged per sub-tile
+    int32_t cand_p2;                // shared candidate arrays (power of two)
+    uint32_t *global_thr;           // float bits of max over CTAs of their pool-th score
+    float *list_score;              // [grid][pool]
+    uint64_t *list_rank;            // [grid][pool]
+    int32_t *list_count;            // [grid]
+};
+
+struct SlotInfo {
+    int64_t base;     // rank of the prefix's first combination (j = s_last + 1)
+    int32_t s_last;   // last prefix SNP (-1 for order 1)
+    int32_t N;        // number of last SNPs: n - 1 - s_last
+    int32_t snp[kMaxOrderGpu];
+};
+
+struct SubtileState {
+    int64_t F, F_end;              // current sub-tile [F, F_end)
+    int64_t cur_base;
+    int32_t cur_prefix[kMaxOrderGpu];
+    int32_t nslots;
+    int32_t list_len, nbuf;
+    float thr;
+    int32_t done;
+};
+
+// next (k-1)-subset of [0, n-1) in lex order; false after the last
+__device__ inline bool next_prefix(int32_t *p, int km1, int64_t n)
+{
+    const int64_t u = n - 1;           // the last SNP needs room after the prefix
+    int t = km1 - 1;
+    while (t >= 0 && p[t] == u - km1 + t) t--;
+    if (t < 0) return false;
+    p[t]++;
+    for (int v = t + 1; v < km1; v++) p[v] = p[v - 1] + 1;
+    return true;
+}
+
+__device__ __forceinline__ uint32_t popc4(uint4 p, uint4 a)
+{
+    return __popc(p.x & a.x) + __popc(p.y & a.y) + __popc(p.z & a.z) + __popc(p.w & a.w);
+}
+
+// Counts of one combination against R staged prefix rows, over words [wb, we).
+template <int R>
+__device__ __forceinline__ void count_rows(const uint32_t *__restrict__ pre, int Wt, const uint32_t *__restrict__ mj,
+                                           int wb, int we, uint32_t (&c0)[R], uint32_t (&c1)[R])
+{
+#pragma unroll
+    for (int r = 0; r < R; r++) { c0[r] = 0; c1[r] = 0; }
+    for (int w = wb; w < we; w += 4) {
+        const uint4 a = __ldg(reinterpret_cast<const uint4 *>(mj + w));
+        const uint4 b = __ldg(reinterpret_cast<const uint4 *>(mj + Wt + w));
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const uint4 p = *reinterpret_cast<const uint4 *>(pre + r * Wt + w);
+            c0[r] += popc4(p, a);
+            c1[r] += popc4(p, b);
+        }
+    }
+}
+
+// single-precision m * MI of one combination (sum of e * phi terms)
+template <int K>
+__device__ __forceinline__ float score_popc(const uint32_t *__restrict__ pre, const uint32_t *__restrict__ tot,
+                                            const uint32_t *__restrict__ mj, const DevData &d, float inv_m)
+{
+    constexpr int PR = ipow3(K - 1);
+    constexpr int R = PR < 27 ? PR : 27;
+    constexpr int G = PR / R;
+    float acc = 0.0f;
+#pragma unroll 1
+    for (int grp = 0; grp < G; grp++) {
+        const uint32_t *pg = pre + grp * R * d.Wt;
+        uint32_t a0[R], a1[R], b0[R], b1[R];
+        count_rows<R>(pg, d.Wt, mj, 0, d.W1, a0, a1);
+        count_rows<R>(pg, d.Wt, mj, d.W1, d.Wt, b0, b1);
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const uint32_t t1 = tot[(grp * R + r) * 2 + 0];
+            const uint32_t t0 = tot[(grp * R + r) * 2 + 1];
+            const uint32_t a2 = t1 - a0[r] - a1[r];
+            const uint32_t b2 = t0 - b0[r] - b1[r];
+            acc += mi_term_f32(a0[r], a0[r] + b0[r], d.m1, d.m, inv_m) +
+                   mi_term_f32(b0[r], a0[r] + b0[r], d.m0, d.m, inv_m);
+            acc += mi_term_f32(a1[r], a1[r] + b1[r], d.m1, d.m, inv_m) +
+                   mi_term_f32(b1[r], a1[r] + b1[r], d.m0, d.m, inv_m);
+            acc += mi_term_f32(a2, a2 + b2, d.m1, d.m, inv_m) + mi_term_f32(b2, a2 + b2, d.m0, d.m, inv_m);
+        }
+    }
+    return acc * inv_m;
+}
+
+// Sort the live list + buffer, keep the best `pool`, refresh the threshold.
+__device__ inline void flush_list(SubtileState &S, float *sc, uint64_t *rk, int pool, int cand_p2,
+                                  uint32_t *global_thr)
+{
+    __syncthreads();
+    const int live = S.list_len + S.nbuf;
+    const int p2 = next_pow2(live < 2 ? 2 : live);
+    for (int i = live + threadIdx.x; i < p2 && i < cand_p2; i += blockDim.x) { sc[i] = -1.0f; rk[i] = ~0ull; }
+    __syncthreads();
+    block_sort_cands(sc, rk, p2);
+    if (threadIdx.x == 0) {
+        S.list_len = live < pool ? live : pool;
+        S.nbuf = 0;
+        if (S.list_len == pool) {
+            const float t = sc[pool - 1];
+            S.thr = t;
+            atomicMax(global_thr, __float_as_uint(t));
+        }
+    }
+    __syncthreads();
+}
+
+template <int K>
+__global__ void __launch_bounds__(128) popc_search_kernel(PopcParams P)
+{
+    constexpr int PR = ipow3(K - 1);
+    const DevData &d = P.d;
+    extern __shared__ __align__(16) unsigned char smem[];
+    // layout: prefix rows | totals | candidate scores | candidate ranks
+    uint32_t *pre = reinterpret_cast<uint32_t *>(smem);
+    const size_t pre_words = (size_t)P.slots * PR * d.Wt;
+    uint32_t *tot = pre + pre_words;
+    uint64_t *rk = reinterpret_cast<uint64_t *>(smem + (((pre_words + (size_t)P.slots * PR * 2) * 4 + 15) & ~(size_t)15));
+    float *sc = reinterpret_cast<float *>(rk + P.cand_p2);
+    __shared__ SlotInfo slot[8];
+    __shared__ SubtileState S;
+
+    const int km1 = K - 1;
+    const float inv_m = 1.0f / (float)d.m;
+    const uint64_t span = P.rank_end - P.rank_begin;
+    const int64_t R_b = (int64_t)(P.rank_begin + (uint64_t)(((unsigned __int128)span * blockIdx.x) / gridDim.x));
+    const int64_t R_e = (int64_t)(P.rank_begin + (uint64_t)(((unsigned __int128)span * (blockIdx.x + 1)) / gridDim.x));
+
+    if (threadIdx.x == 0) {
+        S.list_len = 0; S.nbuf = 0; S.thr = -1.0f; S.done = R_b >= R_e;
+        S.F = R_b;
+        if (!S.done) {
+            int32_t c[kMaxOrderGpu];
+            unrank_lex(d.binom, d.n, K, (uint64_t)R_b, c);
+            const int32_t s_last = K > 1 ? c[K - 2] : -1;
+            for (int t = 0; t < km1; t++) S.cur_prefix[t] = c[t];
+            S.cur_base = R_b - (c[K - 1] - (s_last + 1));
+        }
+    }
+    __syncthreads();
+
+    while (!S.done) {
+        // ---- assemble the sub-tile's prefixes ----------------------------
+        if (threadIdx.x == 0) {
+            const int64_t lim = min((int64_t)S.F + P.tile, R_e);
+            int32_t p[kMaxOrderGpu];
+            for (int t = 0; t < km1; t++) p[t] = S.cur_prefix[t];
+            int64_t base = S.cur_base;
+            int ns = 0;
+            bool more = true;
+            while (true) {
+                SlotInfo &sl = slot[ns];
+                sl.base = base;
+                sl.s_last = km1 > 0 ? p[km1 - 1] : -1;
+                sl.N = (int32_t)(d.n - 1 - sl.s_last);
+                for (int t = 0; t < km1; t++) sl.snp[t] = p[t];
+                ns++;
+                base += sl.N;
+                if (base >= lim || ns == P.slots) break;
+                if (km1 == 0 || !next_prefix(p, km1, d.n)) { more = false; break; }
+            }
+            const SlotInfo &last = slot[ns - 1];
+            const int64_t last_end = last.base + last.N;
+            S.F_end = min(lim, last_end);
+            S.nslots = ns;
+            // prefix containing the next sub-tile's first rank
+            if (S.F_end == last_end && S.F_end < R_e) {
+                for (int t = 0; t < km1; t++) p[t] = last.snp[t];
+                if (km1 > 0) more = next_prefix(p, km1, d.n);
+                for (int t = 0; t < km1; t++) S.cur_prefix[t] = p[t];
+                S.cur_base = last_end;
+                (void)more;
+            } else {
+                for (int t = 0; t < km1; t++) S.cur_prefix[t] = last.snp[t];
+                S.cur_base = last.base;
+            }
+            // stricter of the CTA threshold and the best known global one
+            const float g = __uint_as_float(*(volatile uint32_t *)P.global_thr);
+            if (S.list_len == P.pool || g > 0.0f) S.thr = fmaxf(S.thr, g);
+        }
+        __syncthreads();
+
+        // ---- stage prefix tables: row x' = sum_t g_t 3^(k-2-t) -------------
+        const int ns = S.nslots;
+        const int W4 = d.Wt >> 2;
+        for (int idx = threadIdx.x; idx < ns * PR * W4; idx += blockDim.x) {
+            const int w4 = idx % W4;
+            const int row = (idx / W4) % PR;
+            const int s = idx / (W4 * PR);
+            uint4 acc;
+            if (K == 1) {
+                // the empty prefix: every real individual of each subtable
+                const int w = w4 * 4;
+                uint32_t v[4];
+                for (int q = 0; q < 4; q++) {
+                    const int ww = w + q;
+                    const int64_t first = ww < d.W1 ? (int64_t)ww * 32 : (int64_t)(ww - d.W1) * 32;
+                    const int64_t size = ww < d.W1 ? d.m1 : d.m0;
+                    const int64_t left = size - first;
+                    v[q] = left >= 32 ? 0xffffffffu : (left <= 0 ? 0u : ((1u << left) - 1u));
+                }
+                acc = make_uint4(v[0], v[1], v[2], v[3]);
+            } else {
+                acc = make_uint4(~0u, ~0u, ~0u, ~0u);
+                int rem = row;
+                int div = PR / 3;
+#pragma unroll
+                for (int t = 0; t < km1; t++) {
+                    const int g = rem / div;
+                    rem -= g * div;
+                    div = div > 1 ? div / 3 : 1;
+                    const uint4 v = __ldg(reinterpret_cast<const uint4 *>(
+                        d.masks + ((int64_t)slot[s].snp[t] * 3 + g) * d.Wt) + w4);
+                    acc.x &= v.x; acc.y &= v.y; acc.z &= v.z; acc.w &= v.w;
+                }
+            }
+            reinterpret_cast<uint4 *>(pre + ((size_t)s * PR + row) * d.Wt)[w4] = acc;
+        }
+        __syncthreads();
+        // per-row totals of each subtable (the third genotype by subtraction)
+        for (int idx = threadIdx.x; idx < ns * PR * 2; idx += blockDim.x) {
+            const int half = idx & 1;
+            const int sr = idx >> 1;
+            const uint32_t *row = pre + (size_t)sr * d.Wt;
+            uint32_t c = 0;
+            const int wb = half ? d.W1 : 0, we = half ? d.Wt : d.W1;
+            for (int w = wb; w < we; w++) c += __popc(row[w]);
+            tot[sr * 2 + half] = c;
+        }
+        __syncthreads();
+
+        // ---- count and score: one thread per combination -------------------
+        const int64_t F = S.F, F_end = S.F_end;
+        const int list_len = S.list_len;
+        const float thr = S.thr;
+        for (int64_t f = F + threadIdx.x; f < F_end; f += blockDim.x) {
+            int s = 0;
+            while (s + 1 < ns && f >= slot[s + 1].base) s++;
+            const int32_t j = slot[s].s_last + 1 + (int32_t)(f - slot[s].base);
+            const float score = score_popc<K>(pre + (size_t)s * PR * d.Wt, tot + s * PR * 2,
+                                              d.masks + (int64_t)j * 3 * d.Wt, d, inv_m);
+            if (score >= thr) {
+                const int pos = list_len + atomicAdd(&S.nbuf, 1);
+                sc[pos] = score;
+                rk[pos] = (uint64_t)f;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            S.F = F_end;
+            S.done = F_end >= R_e;
+        }
+        __syncthreads();
+        if (S.nbuf > P.tile || (S.done && S.nbuf > 0)) flush_list(S, sc, rk, P.pool, P.cand_p2, P.global_thr);
+    }
+    __syncthreads();
+    const int L = S.list_len;
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        P.list_score[(size_t)blockIdx.x * P.pool + i] = sc[i];
+        P.list_rank[(size_t)blockIdx.x * P.pool + i] = rk[i];
+    }
+    if (threadIdx.x == 0) P.list_count[blockIdx.x] = L;
+}
+
+template <int K>
+static cudaError_t launch_k(const PopcParams &p, int grid, size_t smem, cudaStream_t st)
+{
+    auto kern = popc_search_kernel<K>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, 128, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+size_t popc_smem_bytes(int k, int32_t Wt, int slots, int cand_p2)
+{
+    const size_t PR = (size_t)ipow3(k - 1);
+    size_t b = (((size_t)slots * PR * Wt + (size_t)slots * PR * 2) * 4 + 15) & ~(size_t)15;
+    return b + (size_t)cand_p2 * 12;
+}
+
+int popc_max_active(int k, size_t smem)
+{
+    int n = 0;
+    cudaError_t e = cudaSuccess;
+    switch (k) {
+    case 1: cudaFuncSetAttribute(popc_search_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, popc_search_kernel<1>, 128, smem); break;
+    case 2: cudaFuncSetAttribute(popc_search_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, popc_search_kernel<2>, 128, smem); break;
+    case 3: cudaFuncSetAttribute(popc_search_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, popc_search_kernel<3>, 128, smem); break;
+    case 4: cudaFuncSetAttribute(popc_search_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, popc_search_kernel<4>, 128, smem); break;
+    case 5: cudaFuncSetAttribute(popc_search_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, popc_search_kernel<5>, 128, smem); break;
+    default: return 0;
+    }
+    return e == cudaSuccess ? n : 0;
+}
+
+cudaError_t launch_popc_search(const DevData &d, int k, uint64_t rank_begin, uint64_t rank_end, int tile, int pool,
+                               int slots, int cand_p2, uint32_t *global_thr, float *list_score, uint64_t *list_rank,
+                               int32_t *list_count, int grid, size_t smem, cudaStream_t st)
+{
+    PopcParams p;
+    p.d = d;
+    p.rank_begin = rank_begin;
+    p.rank_end = rank_end;
+    p.tile = tile;
+    p.pool = pool;
+    p.slots = slots;
+    p.cand_p2 = cand_p2;
+    p.global_thr = global_thr;
+    p.list_score = list_score;
+    p.list_rank = list_rank;
+    p.list_count = list_count;
+    switch (k) {
+    case 1: return launch_k<1>(p, grid, smem, st);
+    case 2: return launch_k<2>(p, grid, smem, st);
+    case 3: return launch_k<3>(p, grid, smem, st);
+    case 4: return launch_k<4>(p, grid, smem, st);
+    case 5: return launch_k<5>(p, grid, smem, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace epi

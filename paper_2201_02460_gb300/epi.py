@@ -1,0 +1,265 @@
+"""Python binding of libepi (ctypes).
+
+Marshalling only: every step of a search runs in the library's CUDA kernels.
+PyTorch provides the CUDA stream (and, for device-resident inputs, the device
+memory); numpy arrays are host buffers.  There is no fallback: if the shared
+library is missing or cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libepi.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "epi.h")
+
+EPI_OK, EPI_EINVAL, EPI_ENOMEM, EPI_ECUDA, EPI_EUNSUPPORTED, EPI_ETIMEOUT, EPI_EOVERFLOW = range(7)
+PATHS = {"auto": 0, "popc": 1, "tc": 2}
+MAX_ORDER = 8
+
+RESULT_DTYPE = np.dtype([("snp", "<u4", (MAX_ORDER,)), ("mi", "<f8"), ("mi_f32", "<f4"),
+                         ("order", "<u4"), ("rank", "<u8")])
+assert RESULT_DTYPE.itemsize == 56
+
+
+class EpiError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"libepi status {status}: {msg}")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def exported_names() -> list[str]:
+    """Function names declared in include/epi.h."""
+    with open(HEADER) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(epi_[a-z0-9_]+)\s*\(",
+                                 text, flags=re.M)))
+
+
+def load(path: str | None = None):
+    """Load libepi (raises if it was not built)."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise OSError(f"libepi is not built ({p} missing); run paper_2201_02460_gb300.build.build()")
+        lib = C.CDLL(p)
+        V, P = C.c_void_p, C.c_void_p
+        i32, i64, u64 = C.c_int, C.c_int64, C.c_uint64
+        lib.epi_last_error.restype = C.c_char_p
+        lib.epi_last_error.argtypes = []
+        lib.epi_create.restype = i32
+        lib.epi_create.argtypes = [i32, V, C.POINTER(V)]
+        lib.epi_destroy.restype = None
+        lib.epi_destroy.argtypes = [V]
+        lib.epi_dataset_create.restype = i32
+        lib.epi_dataset_create.argtypes = [V, P, P, i64, i64, i32, C.POINTER(V)]
+        lib.epi_dataset_destroy.restype = None
+        lib.epi_dataset_destroy.argtypes = [V]
+        lib.epi_dataset_info.restype = i32
+        lib.epi_dataset_info.argtypes = [V, P, P, P, P]
+        lib.epi_search.restype = i32
+        lib.epi_search.argtypes = [V, i32, i32, i32, P, P, P]
+        lib.epi_search_range.restype = i32
+        lib.epi_search_range.argtypes = [V, i32, i32, i32, u64, u64, P, P, P]
+        lib.epi_search_async.restype = i32
+        lib.epi_search_async.argtypes = [V, i32, i32, i32, P, P, P, P]
+        lib.epi_tables.restype = i32
+        lib.epi_tables.argtypes = [V, i32, P, i64, P]
+        lib.epi_score_tables.restype = i32
+        lib.epi_score_tables.argtypes = [V, i32, P, i64, P, P]
+        lib.epi_kernel_launches.restype = u64
+        lib.epi_kernel_launches.argtypes = [V]
+        lib.epi_profile_begin.restype = i32
+        lib.epi_profile_begin.argtypes = [V]
+        lib.epi_profile_end.restype = i32
+        lib.epi_profile_end.argtypes = [V, P, P]
+        if path is None:
+            _lib = lib
+        return lib
+
+
+def _check(rc: int):
+    if rc != EPI_OK:
+        raise EpiError(rc, load().epi_last_error().decode(errors="replace"))
+
+
+def _np_ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _current_stream_handle():
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+class Context:
+    """A libepi context on one CUDA device and stream (torch's current stream
+    by default)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        lib = load()
+        if stream is None:
+            import torch
+            with torch.cuda.device(device):
+                stream = torch.cuda.current_stream().cuda_stream
+        elif hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        self.device = device
+        self.stream = stream
+        h = C.c_void_p()
+        _check(lib.epi_create(device, C.c_void_p(stream), C.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def kernel_launches(self) -> int:
+        return int(load().epi_kernel_launches(self._h))
+
+    def profile_begin(self):
+        _check(load().epi_profile_begin(self._h))
+
+    def profile_end(self) -> tuple[float, int]:
+        """(summed milliseconds, launches) of the counting kernel since
+        profile_begin."""
+        ms = C.c_double(0.0)
+        n = C.c_int64(0)
+        _check(load().epi_profile_end(self._h, C.byref(ms), C.byref(n)))
+        return ms.value, n.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().epi_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Dataset:
+    """Genotype tables of one dataset on the context's device.
+
+    geno [n_snps, n_samples] uint8 in {0,1,2}, pheno [n_samples] uint8 in
+    {0,1}; numpy arrays (host) or torch CUDA tensors (device)."""
+
+    def __init__(self, ctx: Context, geno, pheno):
+        lib = load()
+        self.ctx = ctx
+        on_dev = hasattr(geno, "is_cuda") and geno.is_cuda
+        if on_dev:
+            import torch
+            if geno.dtype != torch.uint8 or pheno.dtype != torch.uint8:
+                raise TypeError("device inputs must be torch.uint8")
+            geno = geno.contiguous()
+            pheno = pheno.contiguous()
+            n, m = geno.shape
+            gp, pp = C.c_void_p(geno.data_ptr()), C.c_void_p(pheno.data_ptr())
+            keep = (geno, pheno)
+        else:
+            geno = np.ascontiguousarray(geno, dtype=np.uint8)
+            pheno = np.ascontiguousarray(pheno, dtype=np.uint8)
+            n, m = geno.shape
+            gp, pp = _np_ptr(geno), _np_ptr(pheno)
+            keep = (geno, pheno)
+        if pheno.shape[0] != m:
+            raise ValueError("pheno length must equal the number of samples")
+        h = C.c_void_p()
+        _check(lib.epi_dataset_create(ctx.handle, gp, pp, n, m, 1 if on_dev else 0, C.byref(h)))
+        del keep
+        self._h = h
+        info = np.zeros(4, dtype=np.int64)
+        _check(lib.epi_dataset_info(h, _np_ptr(info[0:]), _np_ptr(info[1:]), _np_ptr(info[2:]), _np_ptr(info[3:])))
+        self.n_snps, self.n_samples, self.n_cases, self.n_controls = (int(x) for x in info)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().epi_dataset_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class SearchResult:
+    def __init__(self, recs: np.ndarray, counts: np.ndarray | None, order: int):
+        self.records = recs
+        self.order = order
+        self.combs = recs["snp"][:, :order].astype(np.int64)
+        self.mi = recs["mi"].copy()
+        self.mi_f32 = recs["mi_f32"].copy()
+        self.rank = recs["rank"].copy()
+        self.counts = counts
+
+    def __len__(self):
+        return len(self.records)
+
+
+def search(ds: Dataset, order: int, top_n: int, path: str = "auto", rank_range=None,
+           with_counts: bool = True) -> SearchResult:
+    lib = load()
+    out = np.zeros(top_n, dtype=RESULT_DTYPE)
+    counts = np.zeros((top_n, 2, 3 ** order), dtype=np.uint32) if with_counts else None
+    n_out = C.c_int(0)
+    cp = _np_ptr(counts) if with_counts else None
+    if rank_range is None:
+        _check(lib.epi_search(ds.handle, order, top_n, PATHS[path], _np_ptr(out), cp, C.byref(n_out)))
+    else:
+        r0, r1 = rank_range
+        _check(lib.epi_search_range(ds.handle, order, top_n, PATHS[path], int(r0), int(min(r1, 2 ** 64 - 1)),
+                                    _np_ptr(out), cp, C.byref(n_out)))
+    n = n_out.value
+    return SearchResult(out[:n], counts[:n] if with_counts else None, order)
+
+
+def search_async(ds: Dataset, order: int, top_n: int, out_dev, counts_dev, n_out_dev, status_dev,
+                 path: str = "auto"):
+    """Device-side search into torch CUDA tensors (out_dev: uint8 [top_n*56],
+    counts_dev: int32 [top_n, 2, 3^k] or None, n_out_dev / status_dev: int32 [1])."""
+    lib = load()
+    cp = C.c_void_p(counts_dev.data_ptr()) if counts_dev is not None else None
+    _check(lib.epi_search_async(ds.handle, order, top_n, PATHS[path], C.c_void_p(out_dev.data_ptr()), cp,
+                                C.c_void_p(n_out_dev.data_ptr()), C.c_void_p(status_dev.data_ptr())))
+
+
+def tables(ds: Dataset, combs) -> np.ndarray:
+    lib = load()
+    combs = np.ascontiguousarray(combs, dtype=np.uint32)
+    if combs.ndim != 2:
+        raise ValueError("combs must be [count, order]")
+    count, order = combs.shape
+    out = np.zeros((count, 2, 3 ** order), dtype=np.uint32)
+    _check(lib.epi_tables(ds.handle, order, _np_ptr(combs), count, _np_ptr(out)))
+    return out
+
+
+def score_tables(ds: Dataset, order: int, tabs) -> tuple[np.ndarray, np.ndarray]:
+    lib = load()
+    tabs = np.ascontiguousarray(tabs, dtype=np.uint32)
+    count = tabs.shape[0]
+    f32 = np.zeros(count, dtype=np.float32)
+    f64 = np.zeros(count, dtype=np.float64)
+    _check(lib.epi_score_tables(ds.handle, order, _np_ptr(tabs), count, _np_ptr(f32), _np_ptr(f64)))
+    return f32, f64

@@ -1,0 +1,208 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the CPU oracle.
+
+Counts and top-N combinations must match bit for bit; double-precision
+scores within F64_ATOL; the single-precision screening score within 1e-6
+relative of the oracle's double-precision MI.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from oracle import brute
+from oracle import oracle as O
+from tests.helpers import F32_RTOL, F64_ATOL, check_topn, random_data
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def epi():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2201_02460_gb300 import epi as E
+    E.load()
+    return E
+
+
+@pytest.fixture(scope="module")
+def ctx(epi):
+    return epi.Context(0)
+
+
+def _search_both(epi, ctx, geno, pheno, k, top_n, path="popc", rank_range=None):
+    ds = epi.Dataset(ctx, geno, pheno)
+    r = epi.search(ds, k, top_n, path=path, rank_range=rank_range)
+    if rank_range is None:
+        oc, om, ot = O.search(geno, pheno, k, top_n)
+    else:
+        oc, om, ot = O.search(geno, pheno, k, top_n, rank_begin=rank_range[0], rank_end=rank_range[1])
+    return ds, r, oc, om, ot
+
+
+def _check_result(r, geno, pheno, oc, om):
+    check_topn(r.combs, r.mi, oc, om)
+    # every returned table is the oracle's table of that combination
+    if len(r):
+        t = O.tables(geno, pheno, r.combs.astype(np.int32))
+        assert (t == r.counts).all()
+        m = geno.shape[1]
+        want = np.array([O.mi(x[0], x[1], m) for x in t])
+        np.testing.assert_allclose(r.mi, want, rtol=0, atol=F64_ATOL)
+        err = np.abs(r.mi_f32.astype(np.float64) - want)
+        assert (err <= F32_RTOL * want + 1e-12).all(), err.max()
+        # ranks are lexicographic ranks
+        for c, rk in zip(r.combs[:20], r.rank[:20]):
+            assert O.rank(geno.shape[0], r.order, c) == int(rk)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("m", [37, 128, 129, 300])
+def test_tables_match_oracle(epi, ctx, k, m):
+    geno, pheno = random_data(11, m, seed=k * 1000 + m)
+    ds = epi.Dataset(ctx, geno, pheno)
+    combs = np.array(brute.all_combinations(11, k), dtype=np.uint32)
+    got = epi.tables(ds, combs)
+    want = O.tables(geno, pheno, combs.astype(np.int32))
+    assert (got == want).all()
+
+
+def test_tables_high_order(epi, ctx):
+    geno, pheno = random_data(10, 90, seed=8)
+    ds = epi.Dataset(ctx, geno, pheno)
+    for k in (6, 7, 8):
+        combs = np.array(brute.all_combinations(10, k)[:40], dtype=np.uint32)
+        assert (epi.tables(ds, combs) == O.tables(geno, pheno, combs.astype(np.int32))).all()
+
+
+@pytest.mark.parametrize("k,n,m,top_n", [
+    (1, 30, 200, 10), (2, 40, 257, 25), (3, 30, 700, 50), (4, 22, 1100, 40), (5, 16, 450, 30),
+    (2, 12, 64, 66), (3, 9, 33, 200),
+])
+def test_search_small(epi, ctx, k, n, m, top_n):
+    geno, pheno = random_data(n, m, seed=7 * k + n)
+    ds, r, oc, om, _ = _search_both(epi, ctx, geno, pheno, k, top_n)
+    _check_result(r, geno, pheno, oc, om)
+
+
+def test_search_with_exact_ties(epi, ctx):
+    geno, pheno = random_data(24, 301, seed=99)
+    geno[10] = geno[3]
+    geno[17] = geno[5]
+    geno[20] = geno[3]
+    ds, r, oc, om, _ = _search_both(epi, ctx, geno, pheno, 3, 60)
+    _check_result(r, geno, pheno, oc, om)
+
+
+@pytest.mark.parametrize("m1", [0, 1, 299])
+def test_search_single_or_nearly_single_class(epi, ctx, m1):
+    geno, pheno = random_data(15, 300, seed=5, m1=m1)
+    ds, r, oc, om, _ = _search_both(epi, ctx, geno, pheno, 3, 40)
+    _check_result(r, geno, pheno, oc, om)
+
+
+@pytest.mark.parametrize("k", [2, 3, 4])
+def test_search_range(epi, ctx, k):
+    n = {2: 300, 3: 80, 4: 40}[k]
+    geno, pheno = random_data(n, 513, seed=11 + k)
+    total = O.binom(n, k)
+    for r0, r1 in [(0, 1), (17, 5000), (total // 3, total // 3 + 77777), (total - 999, total + 10)]:
+        ds, r, oc, om, _ = _search_both(epi, ctx, geno, pheno, k, 30, rank_range=(r0, r1))
+        _check_result(r, geno, pheno, oc, om)
+        assert all(r0 <= int(x) < r1 for x in r.rank)
+
+
+def test_workload_order2_full(epi, ctx):
+    from paper_2201_02460_gb300 import synth
+    ds_, k, top_n = synth.make_workload("order2_200snp_1600")
+    for N in (top_n, 1000):
+        ds, r, oc, om, _ = _search_both(epi, ctx, ds_.geno, ds_.pheno, k, N)
+        _check_result(r, ds_.geno, ds_.pheno, oc, om)
+    assert tuple(r.combs[0]) == ds_.planted
+
+
+def test_workload_order3_reduced(epi, ctx):
+    """The order-3 workload with 4000 samples at 260 SNPs (2.9M combinations,
+    several tiles per CTA and ragged sub-tiles): full oracle parity."""
+    from paper_2201_02460_gb300 import synth
+    d, k, top_n = synth.make_workload("order3_2000snp_4000", n_snps=260)
+    ds, r, oc, om, _ = _search_both(epi, ctx, d.geno, d.pheno, k, top_n)
+    _check_result(r, d.geno, d.pheno, oc, om)
+
+
+def test_workload_order4_reduced(epi, ctx):
+    from paper_2201_02460_gb300 import synth
+    d, k, top_n = synth.make_workload("order4_500snp_8192", n_snps=48)
+    ds, r, oc, om, _ = _search_both(epi, ctx, d.geno, d.pheno, k, top_n)
+    _check_result(r, d.geno, d.pheno, oc, om)
+
+
+def test_device_inputs_match_host_inputs(epi, ctx):
+    import torch
+    geno, pheno = random_data(40, 999, seed=3)
+    a = epi.search(epi.Dataset(ctx, geno, pheno), 3, 50)
+    b = epi.search(epi.Dataset(ctx, torch.from_numpy(geno).cuda(), torch.from_numpy(pheno).cuda()), 3, 50)
+    assert (a.records == b.records).all()
+
+
+def test_search_async_matches_sync(epi, ctx):
+    import torch
+    geno, pheno = random_data(50, 800, seed=4)
+    ds = epi.Dataset(ctx, geno, pheno)
+    a = epi.search(ds, 3, 64)
+    out = torch.zeros(64 * 56, dtype=torch.uint8, device="cuda")
+    cnt = torch.zeros((64, 2, 27), dtype=torch.int32, device="cuda")
+    n_out = torch.zeros(1, dtype=torch.int32, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    epi.search_async(ds, 3, 64, out, cnt, n_out, st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0 and int(n_out.item()) == 64
+    recs = np.frombuffer(out.cpu().numpy().tobytes(), dtype=epi.RESULT_DTYPE)
+    assert (recs == a.records).all()
+    assert (cnt.cpu().numpy().astype(np.uint32) == a.counts).all()
+
+
+def test_invalid_inputs(epi, ctx):
+    geno, pheno = random_data(8, 50, seed=1)
+    bad = geno.copy()
+    bad[3, 7] = 3
+    with pytest.raises(epi.EpiError) as e:
+        epi.Dataset(ctx, bad, pheno)
+    assert e.value.status == epi.EPI_EINVAL
+    badp = pheno.copy()
+    badp[0] = 2
+    with pytest.raises(epi.EpiError):
+        epi.Dataset(ctx, geno, badp)
+    ds = epi.Dataset(ctx, geno, pheno)
+    for k, n in [(0, 5), (9, 5), (3, 0), (3, 5000)]:
+        with pytest.raises(epi.EpiError) as e:
+            epi.search(ds, k, n)
+        assert e.value.status == epi.EPI_EINVAL
+    with pytest.raises(epi.EpiError) as e:
+        epi.search(ds, 6, 5)
+    assert e.value.status == epi.EPI_EUNSUPPORTED
+    with pytest.raises(epi.EpiError):
+        epi.tables(ds, np.array([[3, 3]], dtype=np.uint32))
+    with pytest.raises(epi.EpiError):
+        epi.tables(ds, np.array([[1, 8]], dtype=np.uint32))
+
+
+def test_score_tables_fp32_accuracy(epi, ctx):
+    """The single-precision screening score on random tables of every order:
+    within 1e-6 relative of the oracle's double-precision MI."""
+    rng = np.random.default_rng(12)
+    geno, pheno = random_data(6, 4096, seed=2, m1=2000)
+    ds = epi.Dataset(ctx, geno, pheno)
+    for k in (1, 2, 3, 4, 5):
+        cells = 3 ** k
+        tabs = []
+        for _ in range(200):
+            a = rng.multinomial(2000, rng.dirichlet(np.ones(cells)))
+            b = rng.multinomial(2096, rng.dirichlet(np.ones(cells)))
+            tabs.append([a, b])
+        tabs = np.array(tabs, dtype=np.uint32)
+        f32, f64 = epi.score_tables(ds, k, tabs)
+        want = np.array([O.mi(t[0], t[1], 4096) for t in tabs])
+        np.testing.assert_allclose(f64, want, rtol=0, atol=F64_ATOL)
+        assert (np.abs(f32 - want) <= F32_RTOL * want + 1e-12).all()
