@@ -387,7 +387,8 @@ epi_status epi_dataset_create(epi_ctx *ctx, const uint8_t *geno, const uint8_t *
     CK(cudaMallocAsync(&work, work_bytes, st));
     int32_t *case_idx = static_cast<int32_t *>(work);
     int32_t *ctrl_idx = case_idx + m;
-    int64_t *dm1 = reinterpret_cast<int64_t *>(ctrl_idx + m + (m & 1));
+    // 2 m int32 entries end on an 8-byte boundary
+    int64_t *dm1 = reinterpret_cast<int64_t *>(case_idx + 2 * m);
     int32_t *dstatus = reinterpret_cast<int32_t *>(dm1 + 1);
     CK(cudaMemsetAsync(dstatus, 0, 4, st));
     launch_scan_pheno(dpheno, m, case_idx, ctrl_idx, dm1, dstatus, st);
