@@ -177,7 +177,8 @@ def run_ours(args):
     B.build()
     from paper_2201_02460_gb300 import epi, synth
 
-    d, k, top_n = synth.make_workload(args.workload)
+    over = {"n_snps": args.n_snps} if args.n_snps else {}
+    d, k, top_n = synth.make_workload(args.workload, **over)
     ctx = epi.Context(local)
     ds = epi.Dataset(ctx, d.geno, d.pheno)
     stream = torch.cuda.current_stream()
@@ -268,6 +269,7 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--path", default="popc", choices=["popc", "tc", "auto"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n-snps", type=int, default=None, help="smaller SNP count (profiling captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
