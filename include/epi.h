@@ -87,7 +87,7 @@ void epi_destroy(epi_ctx *ctx);
  * pheno [n_samples] are host memory when inputs_on_device = 0, device memory
  * otherwise; they are read during the call only.  The library packs them on
  * the device into per-SNP case and control bit rows.  Fails with EPI_EINVAL
- * for n_snps < 1, n_samples < 1, n_samples > 2^24 - 1 or a value outside
+ * for n_snps < 1, n_samples < 1, n_samples > 2^23 - 1 or a value outside
  * {0,1,2} / {0,1} (checked on the device for device inputs).  Device inputs
  * that are not device memory of the context's device fail with EPI_EINVAL. */
 epi_status epi_dataset_create(epi_ctx *ctx, const uint8_t *geno, const uint8_t *pheno,

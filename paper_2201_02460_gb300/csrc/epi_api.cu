@@ -142,39 +142,42 @@ epi_status ensure_scratch(epi_ctx *ctx, size_t bytes)
 }
 
 struct SearchPlan {
-    int k = 0, top_n = 0, pool = 0, tile = 0, slots = 0, cand_p2 = 0, grid = 0;
+    int k = 0, top_n = 0, pool = 0, tile = 0, slots = 0, cand_p2 = 0, grid = 0, R = 0;
     size_t smem = 0;
     uint64_t rb = 0, re = 0, total = 0;
 };
 
-epi_status plan_popc(const epi_dataset *ds, SearchPlan &p)
+// Popcount-path launch shape: row group R (counters per thread), sub-tile T,
+// staged prefixes per sub-tile and CTAs per SM.  Residency first (the POPC
+// pipe needs many warps to hide its latency), then staged prefixes.
+epi_status plan_popc(const epi_dataset *ds, SearchPlan &p, int R_req = 0)
 {
     const epi_ctx *ctx = ds->ctx;
     const uint64_t span = p.re - p.rb;
-    int tile = 512;
-    const uint64_t want_per_cta = span / ((uint64_t)ctx->num_sms * 2 + 1);
-    while (tile > 128 && (uint64_t)tile > want_per_cta) tile >>= 1;
-    p.tile = tile;
-    p.cand_p2 = next_pow2(p.pool + 2 * tile);
+    p.R = R_req ? R_req : popc_default_row_group(p.k);
+    if (!popc_row_group_ok(p.k, p.R)) return fail(EPI_EINVAL, "row group %d invalid for order %d", p.R, p.k);
     const size_t limit = ctx->smem_optin ? ctx->smem_optin : 227 * 1024;
-    int best_slots = 0, best_occ = 0;
-    size_t best_smem = 0;
-    for (int s = 8; s >= 1; s--) {
-        const size_t sm = popc_smem_bytes(p.k, ds->Wt, s, p.cand_p2) + 1024;
-        if (sm > limit) continue;
-        const int occ = popc_max_active(p.k, sm);
-        if (occ <= 0) continue;
-        // prefer two resident CTAs per SM, then more staged prefixes
-        const int score_new = std::min(occ, 2) * 16 + s;
-        const int score_old = std::min(best_occ, 2) * 16 + best_slots;
-        if (best_slots == 0 || score_new > score_old) { best_slots = s; best_occ = occ; best_smem = sm; }
+    int best_score = -1;
+    for (int tile : {512, 256, 128}) {
+        // small searches: keep every CTA busy
+        if (tile > 128 && (uint64_t)tile * ctx->num_sms * 2 > span) continue;
+        const int cand_p2 = next_pow2(p.pool + 2 * tile);
+        for (int s = 8; s >= 1; s--) {
+            const size_t sm = popc_smem_bytes(p.k, ds->Wt, s, cand_p2) + 1024;
+            if (sm > limit) continue;
+            const int occ = popc_max_active(p.k, p.R, sm);
+            if (occ <= 0) continue;
+            const int score = std::min(occ, 8) * 1000 + (tile >= 256 ? 100 : 0) + s * 10 + (tile == 512);
+            if (score > best_score) {
+                best_score = score;
+                p.tile = tile; p.cand_p2 = cand_p2; p.slots = s; p.smem = sm; p.grid = occ;
+            }
+        }
     }
-    if (best_slots == 0)
+    if (best_score < 0)
         return fail(EPI_EUNSUPPORTED, "order %d with %lld samples: one prefix table does not fit in shared memory",
                     p.k, (long long)ds->m);
-    p.slots = best_slots;
-    p.smem = best_smem;
-    uint64_t grid = (uint64_t)ctx->num_sms * (uint64_t)best_occ;
+    uint64_t grid = (uint64_t)ctx->num_sms * (uint64_t)p.grid;
     const uint64_t by_work = (span + 127) / 128;
     if (grid > by_work) grid = by_work;
     if (grid < 1) grid = 1;
@@ -225,8 +228,8 @@ epi_status queue_search(epi_dataset *ds, const SearchPlan &p, int path, epi_resu
         ctx->prof_events.emplace_back(ev0, ev1);
         CK(cudaEventRecord(ev0, ctx->stream));
     }
-    CK(launch_popc_search(d, p.k, p.rb, p.re, p.tile, p.pool, p.slots, p.cand_p2, thr, ls, lr, lc, p.grid, p.smem,
-                          ctx->stream));
+    CK(launch_popc_search(d, p.k, p.R, p.rb, p.re, p.tile, p.pool, p.slots, p.cand_p2, thr, ls, lr, lc, p.grid,
+                          p.smem, ctx->stream));
     if (ev1) CK(cudaEventRecord(ev1, ctx->stream));
     CK(launch_merge(ls, lr, lc, p.grid, p.pool, p.pool, cs, cr, cn, ctx->stream));
     CK(launch_rescore(d, p.k, p.pool, cr, cn, ct, mi, cb, ctx->stream));
@@ -362,7 +365,7 @@ epi_status epi_dataset_create(epi_ctx *ctx, const uint8_t *geno, const uint8_t *
     if (!ctx || !geno || !pheno || !out) return fail(EPI_EINVAL, "NULL argument");
     *out = nullptr;
     if (n_snps < 1 || n_samples < 1) return fail(EPI_EINVAL, "need at least one SNP and one sample");
-    if (n_samples > (1 << 24) - 1) return fail(EPI_EINVAL, "n_samples %lld above 2^24-1", (long long)n_samples);
+    if (n_samples > (1 << 23) - 1) return fail(EPI_EINVAL, "n_samples %lld above 2^23-1", (long long)n_samples);
     if (n_snps > (1 << 24)) return fail(EPI_EINVAL, "n_snps %lld above 2^24", (long long)n_snps);
     DeviceGuard g(ctx->device);
     if (!g.ok) return fail(EPI_ECUDA, "cannot select device %d", ctx->device);

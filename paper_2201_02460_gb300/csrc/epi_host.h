@@ -18,11 +18,14 @@ void launch_pack_masks(const uint8_t *geno, int64_t n, int64_t m, const int32_t 
 void launch_binom(int64_t n, uint64_t *tab, int num_sms, cudaStream_t st);
 
 // epi_popc.cu
+bool popc_row_group_ok(int k, int R);
+int popc_default_row_group(int k);
+int popc_slot_words(int k, int32_t Wt);
 size_t popc_smem_bytes(int k, int32_t Wt, int slots, int cand_p2);
-int popc_max_active(int k, size_t smem);
-cudaError_t launch_popc_search(const DevData &d, int k, uint64_t rank_begin, uint64_t rank_end, int tile, int pool,
-                               int slots, int cand_p2, uint32_t *global_thr, float *list_score, uint64_t *list_rank,
-                               int32_t *list_count, int grid, size_t smem, cudaStream_t st);
+int popc_max_active(int k, int R, size_t smem);
+cudaError_t launch_popc_search(const DevData &d, int k, int R, uint64_t rank_begin, uint64_t rank_end, int tile,
+                               int pool, int slots, int cand_p2, uint32_t *global_thr, float *list_score,
+                               uint64_t *list_rank, int32_t *list_count, int grid, size_t smem, cudaStream_t st);
 
 // epi_select.cu
 cudaError_t launch_merge(const float *ls, const uint64_t *lr, const int32_t *lc, int nlists, int stride, int pool,

@@ -84,7 +84,7 @@ __device__ inline void unrank_lex(const uint64_t *tab, int64_t n, int k, uint64_
 __device__ __forceinline__ float phi_f32(float u)
 {
     if (u >= -0.6666667f && u <= 2.0f) {
-        const float y = u / (2.0f + u);
+        const float y = u * __frcp_rn(2.0f + u);
         const float y2 = y * y;
         float s = 1.0f / 23.0f;
         s = fmaf(s, y2, 1.0f / 21.0f);
@@ -117,15 +117,54 @@ __device__ __forceinline__ double phi_f64(double u)
     return fma(1.0 + u, log1p(u), -u);
 }
 
-// e * phi(u) for count n of class size my in a cell with total nx.
-__device__ __forceinline__ float mi_term_f32(uint32_t n, uint32_t nx, int64_t my, int64_t m, float inv_m)
+// Exact float of an integer below 2^23 without a conversion instruction:
+// 2^23 + v has v as its mantissa.
+__device__ __forceinline__ float u2f_exact(uint32_t v)
 {
-    if (nx == 0 || my == 0) return 0.0f;
-    const int64_t den = (int64_t)nx * my;          // m * e, exact
-    const float e = (float)den * inv_m;
-    if (n == 0) return e;                          // phi(-1) = 1
-    const int64_t num = (int64_t)n * m - den;      // m * (n - e), exact
-    return e * phi_f32((float)num / (float)den);
+    return __int_as_float(0x4B000000u | v) - 8388608.0f;
+}
+
+// Constants of one dataset for the single-precision cell terms.
+struct MiConstF32 {
+    float fm, fm1, fm0;       // class sizes as exact floats (< 2^23)
+    float inv_m, inv_m1, inv_m0;
+};
+
+__device__ __forceinline__ MiConstF32 make_mi_const(int64_t m, int64_t m1, int64_t m0)
+{
+    MiConstF32 c;
+    c.fm = (float)m; c.fm1 = (float)m1; c.fm0 = (float)m0;
+    c.inv_m = 1.0f / c.fm;
+    c.inv_m1 = m1 ? 1.0f / c.fm1 : 0.0f;
+    c.inv_m0 = m0 ? 1.0f / c.fm0 : 0.0f;
+    return c;
+}
+
+// e * phi(u) of one class in a cell: n = count, fx = cell total (float),
+// rx = 1 / fx, fmy / inv_my = class size and its inverse.  With p = fx * fmy
+// and err its exact rounding error (fma), m (n - e) = n m - nx my is
+// fma(n, m, -p) - err to about one ulp however strong the cancellation.
+__device__ __forceinline__ float class_term_f32(uint32_t n, float fx, float rx, float fmy, float inv_my,
+                                                const MiConstF32 &c)
+{
+    if (fmy == 0.0f) return 0.0f;
+    const float p = fx * fmy;
+    const float err = fmaf(fx, fmy, -p);
+    const float e = p * c.inv_m;
+    if (n == 0) return e;                           // phi(-1) = 1
+    const float num = fmaf(u2f_exact(n), c.fm, -p) - err;
+    const float u = num * rx * inv_my;
+    return e * phi_f32(u);
+}
+
+// Both classes of one cell (a cases, b controls).
+__device__ __forceinline__ float cell_terms_f32(uint32_t a, uint32_t b, const MiConstF32 &c)
+{
+    const uint32_t nx = a + b;
+    if (nx == 0) return 0.0f;
+    const float fx = u2f_exact(nx);
+    const float rx = __frcp_rn(fx);
+    return class_term_f32(a, fx, rx, c.fm1, c.inv_m1, c) + class_term_f32(b, fx, rx, c.fm0, c.inv_m0, c);
 }
 
 __device__ __forceinline__ double mi_term_f64(uint32_t n, uint32_t nx, int64_t my, int64_t m)

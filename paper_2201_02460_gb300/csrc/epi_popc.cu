@@ -34,6 +34,7 @@ struct PopcParams {
     int32_t tile;                   // combinations per sub-tile (T)
     int32_t pool;                   // list entries kept per CTA
     int32_t slots;                  // prefixes staged per sub-tile
+    int32_t slot_words;             // words per staged prefix (skewed by 4 words)
     int32_t cand_p2;                // shared candidate arrays (power of two)
     uint32_t *global_thr;           // float bits of max over CTAs of their pool-th score
     float *list_score;              // [grid][pool]
@@ -82,6 +83,7 @@ __device__ __forceinline__ void count_rows(const uint32_t *__restrict__ pre, int
 {
 #pragma unroll
     for (int r = 0; r < R; r++) { c0[r] = 0; c1[r] = 0; }
+#pragma unroll 2
     for (int w = wb; w < we; w += 4) {
         const uint4 a = __ldg(reinterpret_cast<const uint4 *>(mj + w));
         const uint4 b = __ldg(reinterpret_cast<const uint4 *>(mj + Wt + w));
@@ -94,14 +96,16 @@ __device__ __forceinline__ void count_rows(const uint32_t *__restrict__ pre, int
     }
 }
 
-// single-precision m * MI of one combination (sum of e * phi terms)
-template <int K>
+// Single-precision MI of one combination: the prefix rows are taken R at a
+// time (R counters per genotype and class stay in registers); genotype 2 of
+// the last SNP is the prefix row's total minus genotypes 0 and 1.
+template <int K, int R>
 __device__ __forceinline__ float score_popc(const uint32_t *__restrict__ pre, const uint32_t *__restrict__ tot,
-                                            const uint32_t *__restrict__ mj, const DevData &d, float inv_m)
+                                            const uint32_t *__restrict__ mj, const DevData &d, const MiConstF32 &mc)
 {
     constexpr int PR = ipow3(K - 1);
-    constexpr int R = PR < 27 ? PR : 27;
     constexpr int G = PR / R;
+    static_assert(PR % R == 0, "row group must divide the prefix rows");
     float acc = 0.0f;
 #pragma unroll 1
     for (int grp = 0; grp < G; grp++) {
@@ -113,16 +117,12 @@ __device__ __forceinline__ float score_popc(const uint32_t *__restrict__ pre, co
         for (int r = 0; r < R; r++) {
             const uint32_t t1 = tot[(grp * R + r) * 2 + 0];
             const uint32_t t0 = tot[(grp * R + r) * 2 + 1];
-            const uint32_t a2 = t1 - a0[r] - a1[r];
-            const uint32_t b2 = t0 - b0[r] - b1[r];
-            acc += mi_term_f32(a0[r], a0[r] + b0[r], d.m1, d.m, inv_m) +
-                   mi_term_f32(b0[r], a0[r] + b0[r], d.m0, d.m, inv_m);
-            acc += mi_term_f32(a1[r], a1[r] + b1[r], d.m1, d.m, inv_m) +
-                   mi_term_f32(b1[r], a1[r] + b1[r], d.m0, d.m, inv_m);
-            acc += mi_term_f32(a2, a2 + b2, d.m1, d.m, inv_m) + mi_term_f32(b2, a2 + b2, d.m0, d.m, inv_m);
+            acc += cell_terms_f32(a0[r], b0[r], mc);
+            acc += cell_terms_f32(a1[r], b1[r], mc);
+            acc += cell_terms_f32(t1 - a0[r] - a1[r], t0 - b0[r] - b1[r], mc);
         }
     }
-    return acc * inv_m;
+    return acc * mc.inv_m;
 }
 
 // Sort the live list + buffer, keep the best `pool`, refresh the threshold.
@@ -147,7 +147,7 @@ __device__ inline void flush_list(SubtileState &S, float *sc, uint64_t *rk, int 
     __syncthreads();
 }
 
-template <int K>
+template <int K, int R>
 __global__ void __launch_bounds__(128) popc_search_kernel(PopcParams P)
 {
     constexpr int PR = ipow3(K - 1);
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(128) popc_search_kernel(PopcParams P)
     extern __shared__ __align__(16) unsigned char smem[];
     // layout: prefix rows | totals | candidate scores | candidate ranks
     uint32_t *pre = reinterpret_cast<uint32_t *>(smem);
-    const size_t pre_words = (size_t)P.slots * PR * d.Wt;
+    const size_t pre_words = (size_t)P.slots * P.slot_words;
     uint32_t *tot = pre + pre_words;
     uint64_t *rk = reinterpret_cast<uint64_t *>(smem + (((pre_words + (size_t)P.slots * PR * 2) * 4 + 15) & ~(size_t)15));
     float *sc = reinterpret_cast<float *>(rk + P.cand_p2);
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(128) popc_search_kernel(PopcParams P)
     __shared__ SubtileState S;
 
     const int km1 = K - 1;
-    const float inv_m = 1.0f / (float)d.m;
+    const MiConstF32 mc = make_mi_const(d.m, d.m1, d.m0);
     const uint64_t span = P.rank_end - P.rank_begin;
     const int64_t R_b = (int64_t)(P.rank_begin + (uint64_t)(((unsigned __int128)span * blockIdx.x) / gridDim.x));
     const int64_t R_e = (int64_t)(P.rank_begin + (uint64_t)(((unsigned __int128)span * (blockIdx.x + 1)) / gridDim.x));
@@ -256,14 +256,14 @@ __global__ void __launch_bounds__(128) popc_search_kernel(PopcParams P)
                     acc.x &= v.x; acc.y &= v.y; acc.z &= v.z; acc.w &= v.w;
                 }
             }
-            reinterpret_cast<uint4 *>(pre + ((size_t)s * PR + row) * d.Wt)[w4] = acc;
+            reinterpret_cast<uint4 *>(pre + (size_t)s * P.slot_words + (size_t)row * d.Wt)[w4] = acc;
         }
         __syncthreads();
         // per-row totals of each subtable (the third genotype by subtraction)
         for (int idx = threadIdx.x; idx < ns * PR * 2; idx += blockDim.x) {
             const int half = idx & 1;
             const int sr = idx >> 1;
-            const uint32_t *row = pre + (size_t)sr * d.Wt;
+            const uint32_t *row = pre + (size_t)(sr / PR) * P.slot_words + (size_t)(sr % PR) * d.Wt;
             uint32_t c = 0;
             const int wb = half ? d.W1 : 0, we = half ? d.Wt : d.W1;
             for (int w = wb; w < we; w++) c += __popc(row[w]);
@@ -279,8 +279,8 @@ __global__ void __launch_bounds__(128) popc_search_kernel(PopcParams P)
             int s = 0;
             while (s + 1 < ns && f >= slot[s + 1].base) s++;
             const int32_t j = slot[s].s_last + 1 + (int32_t)(f - slot[s].base);
-            const float score = score_popc<K>(pre + (size_t)s * PR * d.Wt, tot + s * PR * 2,
-                                              d.masks + (int64_t)j * 3 * d.Wt, d, inv_m);
+            const float score = score_popc<K, R>(pre + (size_t)s * P.slot_words, tot + s * PR * 2,
+                                                 d.masks + (int64_t)j * 3 * d.Wt, d, mc);
             if (score >= thr) {
                 const int pos = list_len + atomicAdd(&S.nbuf, 1);
                 sc[pos] = score;
@@ -304,46 +304,73 @@ __global__ void __launch_bounds__(128) popc_search_kernel(PopcParams P)
     if (threadIdx.x == 0) P.list_count[blockIdx.x] = L;
 }
 
-template <int K>
-static cudaError_t launch_k(const PopcParams &p, int grid, size_t smem, cudaStream_t st)
+template <int K, int R>
+static cudaError_t launch_kr(const PopcParams &p, int grid, size_t smem, cudaStream_t st)
 {
-    auto kern = popc_search_kernel<K>;
+    auto kern = popc_search_kernel<K, R>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, 128, smem, st>>>(p);
     return cudaGetLastError();
 }
 
+template <int K, int R>
+static int occupancy_kr(size_t smem)
+{
+    auto kern = popc_search_kernel<K, R>;
+    int n = 0;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, 128, smem) != cudaSuccess) return 0;
+    return n;
+}
+
+// Row-group sizes compiled per order: every R divides 3^(k-1).
+bool popc_row_group_ok(int k, int R)
+{
+    switch (k) {
+    case 1: return R == 1;
+    case 2: return R == 3;
+    case 3: return R == 9;
+    case 4: return R == 9 || R == 27;
+    case 5: return R == 9 || R == 27;
+    default: return false;
+    }
+}
+
+int popc_default_row_group(int k)
+{
+    return k == 1 ? 1 : (k == 2 ? 3 : 9);
+}
+
+int popc_slot_words(int k, int32_t Wt)
+{
+    return ipow3(k - 1) * Wt + 4;   // 16-byte skew: slots start on different banks
+}
+
 size_t popc_smem_bytes(int k, int32_t Wt, int slots, int cand_p2)
 {
     const size_t PR = (size_t)ipow3(k - 1);
-    size_t b = (((size_t)slots * PR * Wt + (size_t)slots * PR * 2) * 4 + 15) & ~(size_t)15;
+    size_t b = (((size_t)slots * popc_slot_words(k, Wt) + (size_t)slots * PR * 2) * 4 + 15) & ~(size_t)15;
     return b + (size_t)cand_p2 * 12;
 }
 
-int popc_max_active(int k, size_t smem)
+int popc_max_active(int k, int R, size_t smem)
 {
-    int n = 0;
-    cudaError_t e = cudaSuccess;
-    switch (k) {
-    case 1: cudaFuncSetAttribute(popc_search_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, popc_search_kernel<1>, 128, smem); break;
-    case 2: cudaFuncSetAttribute(popc_search_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, popc_search_kernel<2>, 128, smem); break;
-    case 3: cudaFuncSetAttribute(popc_search_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, popc_search_kernel<3>, 128, smem); break;
-    case 4: cudaFuncSetAttribute(popc_search_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, popc_search_kernel<4>, 128, smem); break;
-    case 5: cudaFuncSetAttribute(popc_search_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, popc_search_kernel<5>, 128, smem); break;
+    switch (k * 100 + R) {
+    case 101: return occupancy_kr<1, 1>(smem);
+    case 203: return occupancy_kr<2, 3>(smem);
+    case 309: return occupancy_kr<3, 9>(smem);
+    case 409: return occupancy_kr<4, 9>(smem);
+    case 427: return occupancy_kr<4, 27>(smem);
+    case 509: return occupancy_kr<5, 9>(smem);
+    case 527: return occupancy_kr<5, 27>(smem);
     default: return 0;
     }
-    return e == cudaSuccess ? n : 0;
 }
 
-cudaError_t launch_popc_search(const DevData &d, int k, uint64_t rank_begin, uint64_t rank_end, int tile, int pool,
-                               int slots, int cand_p2, uint32_t *global_thr, float *list_score, uint64_t *list_rank,
-                               int32_t *list_count, int grid, size_t smem, cudaStream_t st)
+cudaError_t launch_popc_search(const DevData &d, int k, int R, uint64_t rank_begin, uint64_t rank_end, int tile,
+                               int pool, int slots, int cand_p2, uint32_t *global_thr, float *list_score,
+                               uint64_t *list_rank, int32_t *list_count, int grid, size_t smem, cudaStream_t st)
 {
     PopcParams p;
     p.d = d;
@@ -352,17 +379,20 @@ cudaError_t launch_popc_search(const DevData &d, int k, uint64_t rank_begin, uin
     p.tile = tile;
     p.pool = pool;
     p.slots = slots;
+    p.slot_words = popc_slot_words(k, d.Wt);
     p.cand_p2 = cand_p2;
     p.global_thr = global_thr;
     p.list_score = list_score;
     p.list_rank = list_rank;
     p.list_count = list_count;
-    switch (k) {
-    case 1: return launch_k<1>(p, grid, smem, st);
-    case 2: return launch_k<2>(p, grid, smem, st);
-    case 3: return launch_k<3>(p, grid, smem, st);
-    case 4: return launch_k<4>(p, grid, smem, st);
-    case 5: return launch_k<5>(p, grid, smem, st);
+    switch (k * 100 + R) {
+    case 101: return launch_kr<1, 1>(p, grid, smem, st);
+    case 203: return launch_kr<2, 3>(p, grid, smem, st);
+    case 309: return launch_kr<3, 9>(p, grid, smem, st);
+    case 409: return launch_kr<4, 9>(p, grid, smem, st);
+    case 427: return launch_kr<4, 27>(p, grid, smem, st);
+    case 509: return launch_kr<5, 9>(p, grid, smem, st);
+    case 527: return launch_kr<5, 27>(p, grid, smem, st);
     default: return cudaErrorInvalidValue;
     }
 }

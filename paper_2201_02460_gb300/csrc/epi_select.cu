@@ -108,13 +108,10 @@ __device__ inline double table_mi_f64(const DevData &d, const uint32_t *ct, int 
 
 __device__ inline float table_mi_f32(const DevData &d, const uint32_t *ct, int cells)
 {
-    const float inv_m = 1.0f / (float)d.m;
+    const MiConstF32 mc = make_mi_const(d.m, d.m1, d.m0);
     float acc = 0.0f;
-    for (int x = 0; x < cells; x++) {
-        const uint32_t a = ct[x], b = ct[cells + x];
-        acc += mi_term_f32(a, a + b, d.m1, d.m, inv_m) + mi_term_f32(b, a + b, d.m0, d.m, inv_m);
-    }
-    return acc * inv_m;
+    for (int x = 0; x < cells; x++) acc += cell_terms_f32(ct[x], ct[cells + x], mc);
+    return acc * mc.inv_m;
 }
 
 __global__ void __launch_bounds__(256) rescore_kernel(DevData d, int k, const uint64_t *__restrict__ cand_rank,
