@@ -139,6 +139,14 @@ epi_status epi_score_tables(epi_dataset *ds, int order, const uint32_t *tables, 
  * (a diagnostic counter). */
 uint64_t epi_kernel_launches(const epi_ctx *ctx);
 
+/* Validation aid: the contingency table of every combination as the
+ * tensor-core counting path computes it, before any screening.  out: host
+ * [C(n,k)][2][3^order] in lexicographic rank order (at most 2 GiB).  Fails
+ * with EPI_EUNSUPPORTED where the tensor-core path does not apply (see
+ * epi_search).  The paper has no counterpart; the tables equal those of
+ * epi_tables (Section 2.2) when the path is exact. */
+epi_status epi_debug_counts(epi_dataset *ds, int order, uint32_t *out);
+
 /* Timing of the dominant counting kernel.  After epi_profile_begin, every
  * launch of a search's counting kernel is bracketed by CUDA events on the
  * context's stream; epi_profile_end waits for those events and returns their

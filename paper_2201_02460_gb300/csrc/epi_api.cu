@@ -31,6 +31,7 @@ struct epi_dataset {
     int32_t W1 = 0, W0 = 0, Wt = 0;
     uint32_t *masks = nullptr;
     uint64_t *binom = nullptr;
+    unsigned char *b8 = nullptr;   // tensor-core operand, built on first use
     DevData dev() const
     {
         DevData d;
@@ -79,19 +80,6 @@ struct DeviceGuard {
         if (prev >= 0) cudaSetDevice(prev);
     }
 };
-
-// exact C(n, k) or UINT64_MAX
-uint64_t host_binom(int64_t n, int64_t k)
-{
-    if (k < 0 || n < 0 || k > n) return 0;
-    if (k > n - k) k = n - k;
-    unsigned __int128 r = 1;
-    for (int64_t i = 0; i < k; i++) {
-        r = r * (unsigned __int128)(n - i) / (unsigned __int128)(i + 1);
-        if (r > (unsigned __int128)UINT64_MAX) return UINT64_MAX;
-    }
-    return (uint64_t)r;
-}
 
 // true when p is device (or managed) memory usable on `device`
 bool is_device_ptr(const void *p, int device)
@@ -143,6 +131,7 @@ epi_status ensure_scratch(epi_ctx *ctx, size_t bytes)
 
 struct SearchPlan {
     int k = 0, top_n = 0, pool = 0, tile = 0, slots = 0, cand_p2 = 0, grid = 0, R = 0;
+    bool tc = false;
     size_t smem = 0;
     uint64_t rb = 0, re = 0, total = 0;
 };
@@ -185,9 +174,51 @@ epi_status plan_popc(const epi_dataset *ds, SearchPlan &p, int R_req = 0)
     return EPI_OK;
 }
 
+// Tensor-core path conditions: orders 2..4, both classes present, the whole
+// combination range (the tensor tiles follow panel order, not rank order).
+bool tc_applicable(const epi_dataset *ds, int k, uint64_t rb, uint64_t re, uint64_t total)
+{
+    return k >= 2 && k <= 4 && ds->m1 > 0 && ds->m0 > 0 && rb == 0 && re == total && ds->n >= k + 1;
+}
+
+epi_status choose_path(const epi_dataset *ds, int k, int path, uint64_t rb, uint64_t re, uint64_t total, bool &tc)
+{
+    const bool ok = tc_applicable(ds, k, rb, re, total);
+    if (path == EPI_PATH_TC) {
+        if (!ok)
+            return fail(EPI_EUNSUPPORTED,
+                        "tensor-core path needs order 2..4, cases and controls, and the whole combination range");
+        tc = true;
+    } else if (path == EPI_PATH_POPC) {
+        tc = false;
+    } else {
+        tc = ok && k >= 3;
+    }
+    return EPI_OK;
+}
+
+epi_status ensure_b8(epi_dataset *ds)
+{
+    if (ds->b8) return EPI_OK;
+    epi_ctx *ctx = ds->ctx;
+    CK(cudaMalloc((void **)&ds->b8, tc_b8_bytes(ds->dev())));
+    CK(launch_build_b8(ds->dev(), ds->b8, ctx->num_sms, ctx->stream));
+    ctx->launches += 1;
+    return EPI_OK;
+}
+
+epi_status make_plan(const epi_dataset *ds, SearchPlan &p, int path)
+{
+    epi_status st = choose_path(ds, p.k, path, p.rb, p.re, p.total, p.tc);
+    if (st != EPI_OK) return st;
+    if (!p.tc) return plan_popc(ds, p);
+    p.grid = ds->ctx->num_sms;
+    return EPI_OK;
+}
+
 // Queues one search pass with the given plan; results land in device memory.
 epi_status queue_search(epi_dataset *ds, const SearchPlan &p, int path, epi_result *out_dev, uint32_t *counts_dev,
-                        int32_t *n_out_dev, int32_t **status_dev_out)
+                        int32_t *n_out_dev, int32_t **status_dev_out, uint32_t *dump = nullptr)
 {
     epi_ctx *ctx = ds->ctx;
     (void)path;
@@ -204,6 +235,7 @@ epi_status queue_search(epi_dataset *ds, const SearchPlan &p, int path, epi_resu
     const size_t o_ct = a.take<uint32_t>((size_t)p.pool * 2 * cells);
     const size_t o_mi = a.take<double>((size_t)p.pool);
     const size_t o_cb = a.take<int32_t>((size_t)p.pool * p.k);
+    const size_t o_ic = a.take<uint64_t>((size_t)ds->n + 1);
     epi_status st = ensure_scratch(ctx, a.off);
     if (st != EPI_OK) return st;
     char *base = static_cast<char *>(ctx->scratch);
@@ -218,6 +250,11 @@ epi_status queue_search(epi_dataset *ds, const SearchPlan &p, int path, epi_resu
     uint32_t *ct = reinterpret_cast<uint32_t *>(base + o_ct);
     double *mi = reinterpret_cast<double *>(base + o_mi);
     int32_t *cb = reinterpret_cast<int32_t *>(base + o_cb);
+    uint64_t *ic = reinterpret_cast<uint64_t *>(base + o_ic);
+    if (p.tc) {
+        st = ensure_b8(ds);
+        if (st != EPI_OK) return st;
+    }
     // threshold word and status word live in the first 512 bytes
     CK(cudaMemsetAsync(base, 0, 512, ctx->stream));
     const DevData d = ds->dev();
@@ -228,8 +265,15 @@ epi_status queue_search(epi_dataset *ds, const SearchPlan &p, int path, epi_resu
         ctx->prof_events.emplace_back(ev0, ev1);
         CK(cudaEventRecord(ev0, ctx->stream));
     }
-    CK(launch_popc_search(d, p.k, p.R, p.rb, p.re, p.tile, p.pool, p.slots, p.cand_p2, thr, ls, lr, lc, p.grid,
-                          p.smem, ctx->stream));
+    if (p.tc) {
+        int cand_p2 = 0;
+        CK(launch_tc_search(d, p.k, ds->b8, ic, p.pool, thr, ls, lr, lc, status, p.grid, p.total, ctx->stream,
+                            &cand_p2, dump));
+        ctx->launches += 1;   // item table
+    } else {
+        CK(launch_popc_search(d, p.k, p.R, p.rb, p.re, p.tile, p.pool, p.slots, p.cand_p2, thr, ls, lr, lc, p.grid,
+                              p.smem, ctx->stream));
+    }
     if (ev1) CK(cudaEventRecord(ev1, ctx->stream));
     CK(launch_merge(ls, lr, lc, p.grid, p.pool, p.pool, cs, cr, cn, ctx->stream));
     CK(launch_rescore(d, p.k, p.pool, cr, cn, ct, mi, cb, ctx->stream));
@@ -283,7 +327,7 @@ epi_status run_search_sync(epi_dataset *ds, int order, int top_n, int path, uint
     for (;;) {
         SearchPlan p;
         p.k = order; p.top_n = top_n; p.pool = pool; p.rb = rb; p.re = re; p.total = total;
-        st = plan_popc(ds, p);
+        st = make_plan(ds, p, path);
         if (st != EPI_OK) return st;
         // device-side outputs of this pass (stream-ordered allocation)
         const size_t rec_b = ((size_t)top_n * sizeof(epi_result) + 255) & ~(size_t)255;
@@ -445,6 +489,7 @@ void epi_dataset_destroy(epi_dataset *ds)
     cudaStreamSynchronize(ds->ctx->stream);
     cudaFree(ds->masks);
     cudaFree(ds->binom);
+    if (ds->b8) cudaFree(ds->b8);
     delete ds;
 }
 
@@ -485,7 +530,7 @@ epi_status epi_search_async(epi_dataset *ds, int order, int top_n, int path, epi
         return fail(EPI_EINVAL, "epi_search_async outputs must be device memory of device %d", ctx->device);
     SearchPlan p;
     p.k = order; p.top_n = top_n; p.pool = initial_pool(top_n); p.rb = 0; p.re = re; p.total = total;
-    st = plan_popc(ds, p);
+    st = make_plan(ds, p, path);
     if (st != EPI_OK) return st;
     int32_t *status = nullptr;
     st = queue_search(ds, p, path, out_dev, counts_dev, n_out_dev, &status);
@@ -560,6 +605,46 @@ epi_status epi_score_tables(epi_dataset *ds, int order, const uint32_t *tables, 
 }
 
 uint64_t epi_kernel_launches(const epi_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+epi_status epi_debug_counts(epi_dataset *ds, int order, uint32_t *out)
+{
+    uint64_t total = 0, re = UINT64_MAX;
+    epi_status st = check_search_args(ds, order, 1, EPI_PATH_TC, 0, re, total);
+    if (st != EPI_OK) return st;
+    if (!out) return fail(EPI_EINVAL, "out is NULL");
+    if (!tc_applicable(ds, order, 0, total, total))
+        return fail(EPI_EUNSUPPORTED, "the tensor-core path does not apply to this dataset and order");
+    const size_t cells = (size_t)pow3i(order);
+    const size_t bytes = (size_t)total * 2 * cells * 4;
+    if (bytes > ((size_t)1 << 31)) return fail(EPI_EINVAL, "debug table dump limited to 2 GiB");
+    epi_ctx *ctx = ds->ctx;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(EPI_ECUDA, "cannot select device %d", ctx->device);
+    SearchPlan p;
+    p.k = order; p.top_n = 1; p.pool = initial_pool(1); p.rb = 0; p.re = total; p.total = total;
+    st = make_plan(ds, p, EPI_PATH_TC);
+    if (st != EPI_OK) return st;
+    void *buf = nullptr;
+    CK(cudaMallocAsync(&buf, bytes + sizeof(epi_result) + 512, ctx->stream));
+    uint32_t *dump = static_cast<uint32_t *>(buf);
+    epi_result *rec = reinterpret_cast<epi_result *>(static_cast<char *>(buf) + ((bytes + 255) & ~(size_t)255));
+    int32_t *nout = reinterpret_cast<int32_t *>(rec + 1);
+    int32_t *status = nullptr;
+    cudaError_t e = cudaMemsetAsync(dump, 0xff, bytes, ctx->stream);
+    if (e != cudaSuccess) { cudaFreeAsync(buf, ctx->stream); return fail(EPI_ECUDA, "%s", cudaGetErrorString(e)); }
+    st = queue_search(ds, p, EPI_PATH_TC, rec, nullptr, nout, &status, dump);
+    if (st == EPI_OK) {
+        int32_t hs = 0;
+        e = cudaMemcpyAsync(out, dump, bytes, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, status, 4, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) st = fail(EPI_ECUDA, "%s", cudaGetErrorString(e));
+        else if (hs & ST_TIMEOUT) st = fail(EPI_ETIMEOUT, "device wait expired");
+    }
+    cudaFreeAsync(buf, ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
+    return st;
+}
 
 epi_status epi_profile_begin(epi_ctx *ctx)
 {

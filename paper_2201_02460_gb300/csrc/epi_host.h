@@ -9,6 +9,19 @@
 
 namespace epi {
 
+// exact C(n, k), or UINT64_MAX when it does not fit
+inline uint64_t host_binom(int64_t n, int64_t k)
+{
+    if (k < 0 || n < 0 || k > n) return 0;
+    if (k > n - k) k = n - k;
+    unsigned __int128 r = 1;
+    for (int64_t i = 0; i < k; i++) {
+        r = r * (unsigned __int128)(n - i) / (unsigned __int128)(i + 1);
+        if (r > (unsigned __int128)UINT64_MAX) return UINT64_MAX;
+    }
+    return (uint64_t)r;
+}
+
 // epi_data.cu
 void launch_scan_pheno(const uint8_t *pheno, int64_t m, int32_t *case_idx, int32_t *ctrl_idx, int64_t *m1,
                        int32_t *status, cudaStream_t st);
@@ -26,6 +39,16 @@ int popc_max_active(int k, int R, size_t smem);
 cudaError_t launch_popc_search(const DevData &d, int k, int R, uint64_t rank_begin, uint64_t rank_end, int tile,
                                int pool, int slots, int cand_p2, uint32_t *global_thr, float *list_score,
                                uint64_t *list_rank, int32_t *list_count, int grid, size_t smem, cudaStream_t st);
+
+// epi_tc.cu
+size_t tc_b8_bytes(const DevData &d);
+cudaError_t launch_build_b8(const DevData &d, unsigned char *b8, int num_sms, cudaStream_t st);
+uint64_t tc_item_count(int64_t n, int k);
+size_t tc_smem_bytes(int cand_p2);
+cudaError_t launch_tc_search(const DevData &d, int k, const unsigned char *b8, uint64_t *item_cum, int pool,
+                             uint32_t *global_thr, float *list_score, uint64_t *list_rank, int32_t *list_count,
+                             int32_t *status, int grid, uint64_t total, cudaStream_t st, int *cand_p2_out,
+                             uint32_t *dump = nullptr);
 
 // epi_select.cu
 cudaError_t launch_merge(const float *ls, const uint64_t *lr, const int32_t *lc, int nlists, int stride, int pool,

@@ -1,0 +1,847 @@
+// Tensor-core counting path of the exhaustive search (tcgen05, sm_103a).
+//
+// The last combination level of Section 2.2 (AND of the prefix table with
+// the last SNP's table, then popcount) is an exact 0/1 matrix product:
+//     count[(p, x'), (j, g)] = sum over individuals s of A[(p, x')][s] * B[(j, g)][s]
+// with A[(p, x')] the genotype-table row x' of prefix p (Section 2.1) and
+// B[(j, g)] row g of SNP j, summed separately over the case and the control
+// individuals.  Both operands hold 0/1 values as FP8 E4M3 bytes (A: 2^-6,
+// B: 1.0), accumulated in FP32 in tensor memory: every partial sum is an
+// integer multiple of 2^-6 below 2^17, hence exact.  Genotype 2 of the last
+// SNP is obtained by subtraction from the prefix row's total, as in the
+// popcount path.
+//
+// Layout of one tile: M = 128 rows = 4 warps x 32 lanes; each warp holds
+// floor(32 / 3^(k-1)) whole prefixes (prefix rows never straddle a warp, so
+// the epilogue reduces a prefix with warp shuffles); N = 128 columns = 64 last
+// SNPs x genotypes {0, 1}; K = 128 individuals per stage.
+// Prefixes are taken in "panel order" (by their last SNP c ascending) so the
+// last SNPs of a tile, j > c, form one contiguous range.
+//
+// Warp roles (320 threads, one CTA per SM, persistent, a contiguous range of
+// work items per CTA; an item = one M tile x one N tile x the whole K range):
+//   warps 0-3  epilogue: TMEM -> registers, single-precision MI screen,
+//              exact-margin candidate selection, per-CTA candidate list
+//   warps 4-7  A producers: prefix rows = AND of the prefix SNPs' bit rows,
+//              expanded to E4M3 bytes in the 128-byte-swizzled K-major layout
+//   warp 8     TMA producer of B tiles, and writer of the item descriptors
+//   warp 9     TMEM allocator and MMA issuer (one elected thread)
+// Every mbarrier wait is bounded (about 2 s); a wait that gives up sets
+// ST_TIMEOUT and all roles leave their loops, drain their own asynchronous
+// work and free tensor memory.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "epi_host.h"
+#include "epi_internal.cuh"
+
+namespace epi {
+
+namespace tc {
+
+constexpr int kJ = 64;                 // last SNPs per N tile
+constexpr int kN = 2 * kJ;             // accumulator columns per class
+constexpr int kKC = 128;               // individuals (bytes) per K stage
+constexpr int kStages = 4;
+constexpr int kDescDepth = 4;
+constexpr int kThreads = 320;
+constexpr int kStageBytes = 2 * 128 * kKC;   // A and B tiles
+constexpr uint32_t kTxBytes = 128 * kKC;     // B tile bytes per stage
+constexpr int kMaxDescSnps = 40;
+constexpr unsigned long long kTimeoutNs = 2000000000ull;
+
+struct Desc {
+    int32_t j0;          // first last-SNP of the N tile
+    int32_t nvalid;      // real prefixes in the M tile
+    int32_t snp[kMaxDescSnps];   // prefix p occupies snp[p*(k-1) .. p*(k-1)+k-2]
+};
+
+struct Params {
+    DevData d;
+    int k, PR, ppw, ppt;
+    uint64_t n_prefix;         // C(n-1, k-1)
+    uint64_t n_items;
+    const uint64_t *item_cum;  // [n + 1] items of M tiles starting in panels < c
+    int chunks, chunks_case;   // K stages in total / over the cases
+    int pool, cand_p2;
+    float delta;               // screening margin (nats)
+    float tconst;              // T(m) - T(m1) - T(m0), T(c) = c log2 c
+    float ln2_over_m;
+    uint64_t total;            // C(n, k)
+    uint32_t *global_thr;
+    float *list_score;
+    uint64_t *list_rank;
+    int32_t *list_count;
+    int32_t *status;
+    uint32_t *dump;            // optional: every table, [rank][2][3^k] (validation)
+};
+
+// ------------------------------------------------------------------ PTX --
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t now_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase of parity `parity`; false when it gave up (the
+// CTA-wide abort flag is then set).
+__device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag)
+{
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = now_ns();
+    for (;;) {
+        if (mbar_try(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (now_ns() - t0 > kTimeoutNs) {
+            *abort_flag = 1;
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// K-major operand in the 128-byte swizzle: 8-row atoms of 1024 bytes stacked
+// along M/N (stride 1024), descriptor version 1, layout SWIZZLE_128B.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr)
+{
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// kind::f8f6f4, E4M3 x E4M3 -> F32, K-major A and B, M = 128, N = 128
+constexpr uint32_t kIdesc = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(kN >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void mma_f8(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            d_tmem),
+        "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+#define TMEM_LD32(taddr, r)                                                                                        \
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"  \
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"                        \
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), \
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),       \
+                   "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),     \
+                   "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),     \
+                   "=r"(r[29]), "=r"(r[30]), "=r"(r[31])                                                           \
+                 : "r"(taddr))
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// ------------------------------------------------------------ enumeration --
+// Prefixes of order k are the (k-1)-subsets whose last SNP c is <= n-2, in
+// panel order: panel c holds the C(c, k-2) subsets ending in c, ordered
+// colexicographically by their first k-2 SNPs; panel c starts at C(c, k-1).
+struct PrefixIter {
+    int32_t a[kMaxOrderGpu];   // first k-2 SNPs (ascending)
+    int32_t c;                 // last prefix SNP (panel)
+    uint64_t q;                // index in panel order
+};
+
+__device__ inline void prefix_unrank(const DevData &d, int k, uint64_t q, PrefixIter &it)
+{
+    // panel: largest c with C(c, k-1) <= q
+    int64_t lo = k - 2, hi = d.n - 2;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (binom_at(d.binom, d.n, mid, k - 1) <= q) lo = mid;
+        else hi = mid - 1;
+    }
+    it.c = (int32_t)lo;
+    it.q = q;
+    uint64_t r = q - binom_at(d.binom, d.n, lo, k - 1);
+    // colexicographic unranking of the first k-2 SNPs within [0, c)
+    int64_t top = lo - 1;
+    for (int i = k - 3; i >= 0; i--) {
+        int64_t l2 = i, h2 = top;
+        while (l2 < h2) {
+            const int64_t mid = (l2 + h2 + 1) >> 1;
+            if (binom_at(d.binom, d.n, mid, i + 1) <= r) l2 = mid;
+            else h2 = mid - 1;
+        }
+        it.a[i] = (int32_t)l2;
+        r -= binom_at(d.binom, d.n, l2, i + 1);
+        top = l2 - 1;
+    }
+}
+
+__device__ inline void prefix_next(int k, PrefixIter &it)
+{
+    it.q++;
+    const int m2 = k - 2;
+    int i = 0;
+    while (i < m2) {
+        const int32_t lim = (i + 1 < m2) ? it.a[i + 1] : it.c;
+        if (it.a[i] + 1 < lim) break;
+        i++;
+    }
+    if (i < m2) {
+        it.a[i]++;
+        for (int t = 0; t < i; t++) it.a[t] = t;
+        return;
+    }
+    it.c++;
+    for (int t = 0; t < m2; t++) it.a[t] = t;
+}
+
+__device__ __forceinline__ int64_t ntiles_of(const DevData &d, int32_t c) { return (d.n - 1 - c + kJ - 1) / kJ; }
+
+// -------------------------------------------------------------- epilogue --
+__device__ __forceinline__ uint32_t f2count(uint32_t bits)
+{
+    // accumulator = count * 2^-6, exact; back to the integer
+    const float v = __uint_as_float(bits) * 64.0f;
+    return __float_as_uint(v + 8388608.0f) & 0x7FFFFFu;
+}
+
+__device__ __forceinline__ float tlog(float c) { return c * __log2f(fmaxf(c, 1.0f)); }
+
+__device__ __forceinline__ float seg_sum(float v, int pos, int PR)
+{
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const float o = __shfl_down_sync(0xffffffffu, v, off);
+        if ((pos & (2 * off - 1)) == 0 && pos + off < PR) v += o;
+    }
+    return v;
+}
+
+__device__ inline void sort_cands_epi(float *sc, uint64_t *rk, int p2, int tid)
+{
+    for (int kk = 2; kk <= p2; kk <<= 1) {
+        for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+            for (int i = tid; i < p2; i += 128) {
+                const int ixj = i ^ jj;
+                if (ixj > i) {
+                    const bool up = (i & kk) == 0;
+                    const bool sw = up ? cand_better(sc[ixj], rk[ixj], sc[i], rk[i])
+                                       : cand_better(sc[i], rk[i], sc[ixj], rk[ixj]);
+                    if (sw) {
+                        float ts = sc[i]; sc[i] = sc[ixj]; sc[ixj] = ts;
+                        uint64_t tr = rk[i]; rk[i] = rk[ixj]; rk[ixj] = tr;
+                    }
+                }
+            }
+            epi_bar();
+        }
+    }
+}
+
+struct EpiState {
+    int32_t list_len, nbuf, stop;
+    float thr;
+};
+
+__device__ inline void epi_flush(EpiState &S, float *sc, uint64_t *rk, int pool, uint32_t *global_thr, int tid)
+{
+    epi_bar();
+    const int live = S.list_len + S.nbuf;
+    const int p2 = next_pow2(live < 2 ? 2 : live);
+    for (int i = live + tid; i < p2; i += 128) { sc[i] = -1.0f; rk[i] = ~0ull; }
+    epi_bar();
+    sort_cands_epi(sc, rk, p2, tid);
+    if (tid == 0) {
+        S.list_len = live < pool ? live : pool;
+        S.nbuf = 0;
+        if (S.list_len == pool) {
+            S.thr = sc[pool - 1];
+            atomicMax(global_thr, __float_as_uint(S.thr));
+        }
+    }
+    epi_bar();
+}
+
+// ---------------------------------------------------------------- kernel --
+template <int K>
+__global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_constant__ CUtensorMap tmap_b,
+                                                                const Params P)
+{
+    constexpr int kPR = K == 2 ? 3 : (K == 3 ? 9 : 27);
+    constexpr int kPPW = 32 / kPR;
+    constexpr int kPPT = 4 * kPPW;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // 1024-byte aligned stage area first
+    unsigned char *smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
+    unsigned char *stages = smem;
+    float *sc = reinterpret_cast<float *>(stages + kStages * kStageBytes);
+    uint64_t *rk = reinterpret_cast<uint64_t *>(sc + P.cand_p2);
+    uint32_t *tot = reinterpret_cast<uint32_t *>(rk + P.cand_p2);   // [2][128][2]
+    Desc *desc = reinterpret_cast<Desc *>(tot + 2 * 128 * 2);
+
+    __shared__ __align__(8) uint64_t full_a[kStages], full_b[kStages], empty[kStages];
+    __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], tot_full[2];
+    __shared__ __align__(8) uint64_t desc_full[kDescDepth], desc_empty[kDescDepth], drain_bar;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ volatile int abort_flag;
+    __shared__ EpiState ES;
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const DevData &d = P.d;
+    constexpr int km1 = K - 1;
+
+    // contiguous item range of this CTA
+    const uint64_t it_b = (uint64_t)(((unsigned __int128)P.n_items * blockIdx.x) / gridDim.x);
+    const uint64_t it_e = (uint64_t)(((unsigned __int128)P.n_items * (blockIdx.x + 1)) / gridDim.x);
+    const int64_t n_my = (int64_t)(it_e - it_b);
+
+    if (tid == 0) {
+        for (int s = 0; s < kStages; s++) { mbar_init(&full_a[s], 4); mbar_init(&full_b[s], 1); mbar_init(&empty[s], 1); }
+        for (int b = 0; b < 2; b++) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], 4); mbar_init(&tot_full[b], 4); }
+        for (int q = 0; q < kDescDepth; q++) { mbar_init(&desc_full[q], 1); mbar_init(&desc_empty[q], 8); }
+        mbar_init(&drain_bar, 1);
+        abort_flag = 0;
+        ES.list_len = 0; ES.nbuf = 0; ES.stop = 0; ES.thr = -1.0f;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 9) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = tmem_base_sh;
+
+    if (warp == 8) {
+        // ------------------------------------------------ TMA + descriptors
+        if (lane == 0 && n_my > 0) {
+            // decode the first item: panel by binary search, then M tile / N tile
+            const uint64_t w0 = it_b;
+            int64_t lo = 0, hi = d.n - 1;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi + 1) >> 1;
+                if (P.item_cum[mid] <= w0) lo = mid;
+                else hi = mid - 1;
+            }
+            const int32_t c0 = (int32_t)lo;
+            const uint64_t off = w0 - P.item_cum[c0];
+            const int64_t nt0 = ntiles_of(d, c0);
+            const uint64_t tfirst = (binom_at(d.binom, d.n, c0, km1) + kPPT - 1) / kPPT;
+            uint64_t t = tfirst + off / (uint64_t)nt0;
+            int64_t u = (int64_t)(off % (uint64_t)nt0);
+            PrefixIter it;
+            prefix_unrank(d, K, t * (uint64_t)kPPT, it);
+            int32_t tile_snp[kMaxDescSnps];
+            int32_t nvalid = 0, cmin = it.c;
+            auto fill_tile = [&]() {
+                nvalid = 0;
+                cmin = it.c;
+                for (int p = 0; p < kPPT && it.q < P.n_prefix; p++) {
+                    for (int s2 = 0; s2 < km1 - 1; s2++) tile_snp[p * km1 + s2] = it.a[s2];
+                    tile_snp[p * km1 + km1 - 1] = it.c;
+                    nvalid++;
+                    prefix_next(K, it);
+                }
+            };
+            fill_tile();
+            uint64_t g = 0;   // global chunk counter
+            for (int64_t i = 0; i < n_my && !abort_flag; i++) {
+                const int dq = (int)(i % kDescDepth);
+                const uint32_t ud = (uint32_t)(i / kDescDepth);
+                if (!mbar_wait(&desc_empty[dq], (ud & 1) ^ 1, &abort_flag)) break;
+                Desc &D = desc[dq];
+                D.j0 = cmin + 1 + (int32_t)(u * kJ);
+                D.nvalid = nvalid;
+                for (int q = 0; q < nvalid * km1; q++) D.snp[q] = tile_snp[q];
+                mbar_arrive(&desc_full[dq]);
+                const int y = 2 * D.j0;
+                for (int kc = 0; kc < P.chunks; kc++, g++) {
+                    const int s = (int)(g % kStages);
+                    const uint32_t us = (uint32_t)(g / kStages);
+                    if (!mbar_wait(&empty[s], (us & 1) ^ 1, &abort_flag)) break;
+                    mbar_arrive_tx(&full_b[s], kTxBytes);
+                    tma_load_2d(stages + s * kStageBytes + 128 * kKC, &tmap_b, kc * kKC, y, &full_b[s]);
+                }
+                // advance to the next item
+                u++;
+                if (u == ntiles_of(d, cmin)) {
+                    u = 0;
+                    fill_tile();
+                }
+            }
+            // drain: the last load issued into each stage must have landed
+            for (int s = 0; s < kStages; s++) {
+                if (g > (uint64_t)s) {
+                    const uint64_t last = ((g - 1 - s) / kStages) * kStages + s;   // last chunk index in stage s
+                    const uint32_t us = (uint32_t)(last / kStages);
+                    const uint64_t t0 = now_ns();
+                    while (!mbar_try(&full_b[s], us & 1) && now_ns() - t0 < kTimeoutNs) {}
+                }
+            }
+        }
+    } else if (warp == 9) {
+        // ------------------------------------------------------------- MMA
+        if (lane == 0 && n_my > 0) {
+            uint64_t g = 0;
+            const uint32_t a0 = smem_u32(stages);
+            for (int64_t i = 0; i < n_my && !abort_flag; i++) {
+                const int b = (int)(i & 1);
+                const uint32_t ub = (uint32_t)(i >> 1);
+                if (!mbar_wait(&acc_empty[b], (ub & 1) ^ 1, &abort_flag)) break;
+                tc_fence_after();
+                bool ok = true;
+                for (int kc = 0; kc < P.chunks; kc++, g++) {
+                    const int s = (int)(g % kStages);
+                    const uint32_t us = (uint32_t)(g / kStages);
+                    if (!mbar_wait(&full_a[s], us & 1, &abort_flag) || !mbar_wait(&full_b[s], us & 1, &abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t dcol = tmem_base + (uint32_t)(b * 2 * kN) + (kc < P.chunks_case ? 0u : (uint32_t)kN);
+                    const bool first = (kc == 0) || (kc == P.chunks_case);
+                    const uint64_t ad = sdesc(a0 + s * kStageBytes);
+                    const uint64_t bd = sdesc(a0 + s * kStageBytes + 128 * kKC);
+#pragma unroll
+                    for (int kk = 0; kk < kKC / 32; kk++)
+                        mma_f8(dcol, ad + 2 * kk, bd + 2 * kk, (first && kk == 0) ? 0u : 1u);
+                    mma_commit(&empty[s]);
+                }
+                if (!ok) break;
+                mma_commit(&acc_full[b]);
+            }
+            // every issued MMA has completed before tensor memory is freed
+            mma_commit(&drain_bar);
+            const uint64_t t0 = now_ns();
+            while (!mbar_try(&drain_bar, 0) && now_ns() - t0 < kTimeoutNs) {}
+        }
+    } else if (warp >= 4) {
+        // ---------------------------------------------------- A producers
+        const int r = tid - 128;           // tile row
+        const int w = r >> 5, l = r & 31;
+        uint64_t g = 0;
+        for (int64_t i = 0; i < n_my; i++) {
+            if (abort_flag) break;
+            const int dq = (int)(i % kDescDepth);
+            const uint32_t ud = (uint32_t)(i / kDescDepth);
+            if (!mbar_wait(&desc_full[dq], ud & 1, &abort_flag)) break;
+            const Desc &D = desc[dq];
+            // this row: prefix p, genotype digits of x'
+            const uint32_t *rows[kMaxOrderGpu];
+            bool active = false;
+            if (l < kPPW * kPR) {
+                const int p = w * kPPW + l / kPR;
+                if (p < D.nvalid) {
+                    active = true;
+                    int rem = l % kPR, div = kPR / 3;
+                    for (int t = 0; t < km1; t++) {
+                        const int gg = rem / div;
+                        rem -= gg * div;
+                        div = div > 1 ? div / 3 : 1;
+                        rows[t] = d.masks + ((int64_t)D.snp[p * km1 + t] * 3 + gg) * d.Wt;
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&desc_empty[dq]);
+            uint32_t t1 = 0, t0 = 0;
+            bool ok = true;
+            for (int kc = 0; kc < P.chunks; kc++, g++) {
+                const int s = (int)(g % kStages);
+                const uint32_t us = (uint32_t)(g / kStages);
+                if (!mbar_wait(&empty[s], (us & 1) ^ 1, &abort_flag)) { ok = false; break; }
+                unsigned char *arow = stages + s * kStageBytes + r * 128;
+                uint4 bits = make_uint4(0, 0, 0, 0);
+                if (active) {
+                    bits = __ldg(reinterpret_cast<const uint4 *>(rows[0]) + kc);
+                    for (int t = 1; t < km1; t++) {
+                        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(rows[t]) + kc);
+                        bits.x &= v.x; bits.y &= v.y; bits.z &= v.z; bits.w &= v.w;
+                    }
+                    const uint32_t c4 = __popc(bits.x) + __popc(bits.y) + __popc(bits.z) + __popc(bits.w);
+                    if (kc < P.chunks_case) t1 += c4;
+                    else t0 += c4;
+                }
+                const uint32_t wv[4] = {bits.x, bits.y, bits.z, bits.w};
+#pragma unroll
+                for (int cc = 0; cc < 8; cc++) {
+                    const uint32_t h = (wv[cc >> 1] >> ((cc & 1) * 16)) & 0xFFFFu;
+                    uint4 o;
+                    o.x = ((h & 0xFu) * 0x01020408u) & 0x08080808u;
+                    o.y = (((h >> 4) & 0xFu) * 0x01020408u) & 0x08080808u;
+                    o.z = (((h >> 8) & 0xFu) * 0x01020408u) & 0x08080808u;
+                    o.w = (((h >> 12) & 0xFu) * 0x01020408u) & 0x08080808u;
+                    *reinterpret_cast<uint4 *>(arow + ((cc ^ (r & 7)) << 4)) = o;
+                }
+                fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&full_a[s]);
+            }
+            if (!ok) break;
+            // prefix-row totals for the epilogue's third genotype
+            const int b = (int)(i & 1);
+            const uint32_t ub = (uint32_t)(i >> 1);
+            if (!mbar_wait(&acc_empty[b], (ub & 1) ^ 1, &abort_flag)) break;
+            tot[(b * 128 + r) * 2 + 0] = t1;
+            tot[(b * 128 + r) * 2 + 1] = t0;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tot_full[b]);
+        }
+    } else {
+        // -------------------------------------------------------- epilogue
+        const int r = tid;                 // tile row = TMEM lane
+        const int l = lane;
+        const int pos = l % kPR;
+        const int pl = l / kPR;           // prefix within the warp
+        const bool lane_real = l < kPPW * kPR;
+        const MiConstF32 mc = make_mi_const(d.m, d.m1, d.m0);
+        for (int64_t i = 0; i < n_my; i++) {
+            const int dq = (int)(i % kDescDepth);
+            const uint32_t ud = (uint32_t)(i / kDescDepth);
+            const int b = (int)(i & 1);
+            const uint32_t ub = (uint32_t)(i >> 1);
+            bool ok = mbar_wait(&desc_full[dq], ud & 1, &abort_flag);
+            ok = ok && mbar_wait(&acc_full[b], ub & 1, &abort_flag);
+            ok = ok && mbar_wait(&tot_full[b], ub & 1, &abort_flag);
+            ok = __all_sync(0xffffffffu, ok);
+            tc_fence_after();
+            const Desc &D = desc[dq];
+            const int p = warp * kPPW + pl;
+            const bool prow = ok && lane_real && p < D.nvalid;
+            const int32_t cpre = prow ? D.snp[p * km1 + km1 - 1] : 0x7fffffff;
+            int32_t psnp[kMaxOrderGpu];
+            for (int t = 0; t < km1; t++) psnp[t] = prow ? D.snp[p * km1 + t] : 0;
+            const uint32_t T1 = tot[(b * 128 + r) * 2 + 0], T0 = tot[(b * 128 + r) * 2 + 1];
+            const int32_t j0 = D.j0;
+            // threshold: the CTA's and the best known global one
+            if (tid == 0) {
+                const float gthr = __uint_as_float(*(volatile uint32_t *)P.global_thr);
+                if (ES.list_len == P.pool || gthr > 0.0f) ES.thr = fmaxf(ES.thr, gthr);
+            }
+            epi_bar();
+            for (int jc = 0; jc < kJ / 16; jc++) {
+                // list position and threshold as of the last flush
+                const float thr = ES.thr;
+                const float cut = thr - P.delta;
+                const int list_len = ES.list_len;
+                uint32_t cs[32], cn[32];
+                if (ok) {
+                    const uint32_t ta = tmem_base + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * 2 * kN + 32 * jc);
+                    TMEM_LD32(ta, cs);
+                    TMEM_LD32(ta + kN, cn);
+                    tmem_wait_ld();
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 32; q++) { cs[q] = 0; cn[q] = 0; }
+                }
+#pragma unroll
+                for (int jj = 0; jj < 16; jj++) {
+                    const int32_t j = j0 + 16 * jc + jj;
+                    const uint32_t a0 = f2count(cs[2 * jj]), a1 = f2count(cs[2 * jj + 1]);
+                    const uint32_t b0 = f2count(cn[2 * jj]), b1 = f2count(cn[2 * jj + 1]);
+                    const uint32_t a2 = T1 - a0 - a1, b2 = T0 - b0 - b1;
+                    float v = 0.0f;
+                    if (prow) {
+                        const float fa0 = u2f_exact(a0), fa1 = u2f_exact(a1), fa2 = u2f_exact(a2);
+                        const float fb0 = u2f_exact(b0), fb1 = u2f_exact(b1), fb2 = u2f_exact(b2);
+                        v = (tlog(fa0) + tlog(fb0) - tlog(fa0 + fb0)) + (tlog(fa1) + tlog(fb1) - tlog(fa1 + fb1)) +
+                            (tlog(fa2) + tlog(fb2) - tlog(fa2 + fb2));
+                    }
+                    v = seg_sum(v, pos, kPR);
+                    const bool valid = prow && j < d.n && j > cpre;
+                    if (P.dump && valid) {
+                        uint64_t rs = 0;
+                        for (int t = 0; t < km1; t++) rs += binom_at(d.binom, d.n, d.n - 1 - psnp[t], K - t);
+                        rs += binom_at(d.binom, d.n, d.n - 1 - j, 1);
+                        constexpr int cells = kPR * 3;
+                        uint32_t *o = P.dump + (P.total - 1 - rs) * 2 * cells;
+                        o[pos * 3 + 0] = a0; o[pos * 3 + 1] = a1; o[pos * 3 + 2] = a2;
+                        o[cells + pos * 3 + 0] = b0; o[cells + pos * 3 + 1] = b1; o[cells + pos * 3 + 2] = b2;
+                    }
+                    const float approx = (v + P.tconst) * P.ln2_over_m;
+                    const bool cand = valid && pos == 0 && approx >= cut;
+                    uint32_t seg_mask = __ballot_sync(0xffffffffu, cand);
+                    while (seg_mask) {
+                        const int leader = __ffs(seg_mask) - 1;
+                        seg_mask &= seg_mask - 1;
+                        // precise single-precision MI of that (prefix, j)
+                        float e = 0.0f;
+                        if (l / kPR == leader / kPR && lane_real)
+                            e = cell_terms_f32(a0, b0, mc) + cell_terms_f32(a1, b1, mc) + cell_terms_f32(a2, b2, mc);
+                        e = seg_sum(e, pos, kPR);
+                        if (l == leader) {
+                            const float score = e * mc.inv_m;
+                            if (score >= thr) {
+                                // lexicographic rank of (prefix, j)
+                                uint64_t rk_sum = 0;
+                                for (int t = 0; t < km1; t++)
+                                    rk_sum += binom_at(d.binom, d.n, d.n - 1 - psnp[t], K - t);
+                                rk_sum += binom_at(d.binom, d.n, d.n - 1 - j, 1);
+                                const int slot = list_len + atomicAdd(&ES.nbuf, 1);
+                                sc[slot] = score;
+                                rk[slot] = P.total - 1 - rk_sum;
+                            }
+                        }
+                    }
+                }
+                // keep the buffer below its capacity: flush after any 16 last SNPs
+                epi_bar();
+                if (ES.nbuf > 16 * kPPT) epi_flush(ES, sc, rk, P.pool, P.global_thr, tid);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&acc_empty[b]);
+                mbar_arrive(&desc_empty[dq]);
+            }
+            epi_bar();
+            if (tid == 0) ES.stop = abort_flag;
+            epi_bar();
+            if (ES.stop) break;
+        }
+        epi_bar();
+        if (ES.nbuf > 0) epi_flush(ES, sc, rk, P.pool, P.global_thr, tid);
+        const int L = ES.list_len;
+        for (int q = tid; q < L; q += 128) {
+            P.list_score[(size_t)blockIdx.x * P.pool + q] = sc[q];
+            P.list_rank[(size_t)blockIdx.x * P.pool + q] = rk[q];
+        }
+        if (tid == 0) P.list_count[blockIdx.x] = L;
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 9) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(512) : "memory");
+    }
+    if (tid == 0 && abort_flag) atomicOr(P.status, ST_TIMEOUT);
+}
+
+// Items per panel: the M tiles whose first prefix lies in panel c, times the
+// N tiles of that panel; exclusive prefix sum over c (one block).
+__global__ void __launch_bounds__(1024) item_cum_kernel(DevData d, int k, int ppt, uint64_t *cum)
+{
+    __shared__ uint64_t part[1024];
+    const int64_t n = d.n;
+    const int64_t per = (n + 1023) / 1024;
+    const int64_t b = (int64_t)threadIdx.x * per, e = min(n, b + per);
+    auto items = [&](int64_t c) -> uint64_t {
+        if (c < k - 2 || c > n - 2) return 0;
+        const uint64_t t0 = (binom_at(d.binom, n, c, k - 1) + ppt - 1) / ppt;
+        const uint64_t t1 = (binom_at(d.binom, n, c + 1, k - 1) + ppt - 1) / ppt;
+        return (t1 - t0) * (uint64_t)((n - 1 - c + kJ - 1) / kJ);
+    };
+    uint64_t s = 0;
+    for (int64_t c = b; c < e; c++) s += items(c);
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const uint64_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    uint64_t run = part[threadIdx.x] - s;
+    for (int64_t c = b; c < e; c++) {
+        cum[c] = run;
+        run += items(c);
+    }
+    if (threadIdx.x == 1023) cum[n] = part[1023];
+}
+
+// B operand: row 2j+g (g = 0, 1) holds individual s of SNP j as byte s,
+// E4M3 1.0 (0x38) where the genotype is g, else 0.
+__global__ void build_b8_kernel(DevData d, unsigned char *__restrict__ b8)
+{
+    const int64_t Kt = (int64_t)d.Wt * 32;
+    const int64_t per_row = Kt / 16;
+    const int64_t total = 2 * d.n * per_row;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = idx / per_row;
+        const int64_t q = idx - row * per_row;            // 16-byte piece
+        const int64_t j = row >> 1;
+        const int g = (int)(row & 1);
+        const uint32_t word = d.masks[(j * 3 + g) * d.Wt + (q >> 1)];
+        const uint32_t h = (word >> ((q & 1) * 16)) & 0xFFFFu;
+        uint4 o;
+        o.x = ((h & 0xFu) * 0x00204081u) & 0x01010101u;
+        o.y = (((h >> 4) & 0xFu) * 0x00204081u) & 0x01010101u;
+        o.z = (((h >> 8) & 0xFu) * 0x00204081u) & 0x01010101u;
+        o.w = (((h >> 12) & 0xFu) * 0x00204081u) & 0x01010101u;
+        o.x *= 0x38u; o.y *= 0x38u; o.z *= 0x38u; o.w *= 0x38u;
+        reinterpret_cast<uint4 *>(b8)[idx] = o;
+    }
+}
+
+}  // namespace tc
+
+// ----------------------------------------------------------------- host --
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+static cudaError_t get_encode()
+{
+    if (g_encode) return cudaSuccess;
+    cudaDriverEntryPointQueryResult q;
+    void *fn = nullptr;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    return cudaSuccess;
+}
+
+size_t tc_b8_bytes(const DevData &d) { return (size_t)2 * d.n * d.Wt * 32; }
+
+cudaError_t launch_build_b8(const DevData &d, unsigned char *b8, int num_sms, cudaStream_t st)
+{
+    const int64_t total = 2 * d.n * (int64_t)d.Wt * 2;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > (int64_t)num_sms * 16) blocks = (int64_t)num_sms * 16;
+    tc::build_b8_kernel<<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, st>>>(d, b8);
+    return cudaGetLastError();
+}
+
+// Work items of an order-k search (same formula as item_cum_kernel): the
+// host needs the count to split items over the CTAs.
+uint64_t tc_item_count(int64_t n, int k)
+{
+    const int PR = k == 2 ? 3 : (k == 3 ? 9 : 27);
+    const uint64_t ppt = 4 * (32 / PR);
+    uint64_t total = 0;
+    for (int64_t c = k - 2; c <= n - 2; c++) {
+        const uint64_t t0 = (host_binom(c, k - 1) + ppt - 1) / ppt;
+        const uint64_t t1 = (host_binom(c + 1, k - 1) + ppt - 1) / ppt;
+        total += (t1 - t0) * (uint64_t)((n - 1 - c + tc::kJ - 1) / tc::kJ);
+    }
+    return total;
+}
+
+int tc_prefixes_per_warp(int k)
+{
+    const int PR = k == 2 ? 3 : (k == 3 ? 9 : (k == 4 ? 27 : 81));
+    return PR <= 32 ? 32 / PR : 0;
+}
+
+size_t tc_smem_bytes(int cand_p2)
+{
+    return 1024 + (size_t)tc::kStages * tc::kStageBytes + (size_t)cand_p2 * 12 + 2 * 128 * 2 * 4 +
+           tc::kDescDepth * sizeof(tc::Desc) + 64;
+}
+
+cudaError_t launch_tc_search(const DevData &d, int k, const unsigned char *b8, uint64_t *item_cum, int pool,
+                             uint32_t *global_thr, float *list_score, uint64_t *list_rank, int32_t *list_count,
+                             int32_t *status, int grid, uint64_t total, cudaStream_t st, int *cand_p2_out,
+                             uint32_t *dump)
+{
+    cudaError_t e = get_encode();
+    if (e != cudaSuccess) return e;
+    tc::Params P;
+    P.d = d;
+    P.k = k;
+    P.PR = k == 2 ? 3 : (k == 3 ? 9 : 27);
+    P.ppw = 32 / P.PR;
+    P.ppt = 4 * P.ppw;
+    // C(n-1, k-1) prefixes, computed with the same exact arithmetic as the host
+    unsigned __int128 np = 1;
+    for (int t = 0; t < k - 1; t++) np = np * (unsigned __int128)(d.n - 1 - t) / (unsigned __int128)(t + 1);
+    P.n_prefix = (uint64_t)np;
+    P.item_cum = item_cum;
+    tc::item_cum_kernel<<<1, 1024, 0, st>>>(d, k, P.ppt, item_cum);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    P.n_items = tc_item_count(d.n, k);
+    const int64_t Kt = (int64_t)d.Wt * 32;
+    P.chunks = (int)(Kt / tc::kKC);
+    P.chunks_case = (int)((int64_t)d.W1 * 32 / tc::kKC);
+    P.pool = pool;
+    P.cand_p2 = next_pow2(pool + 2 * 16 * P.ppt);
+    *cand_p2_out = P.cand_p2;
+    auto T = [](double c) { return c > 0 ? c * log2(c) : 0.0; };
+    const double tconst = T((double)d.m) - T((double)d.m1) - T((double)d.m0);
+    P.tconst = (float)tconst;
+    P.ln2_over_m = (float)(0.6931471805599453 / (double)d.m);
+    // screening margin: relative errors of the log2 approximation (2^-21)
+    // and of the float sums over (T(m) + T(m1) + T(m0)), doubled
+    const int64_t cells = (int64_t)P.PR * 3;
+    const double mag = T((double)d.m) + T((double)d.m1) + T((double)d.m0);
+    P.delta = (float)(2.0 * (4.0 * 4.76837158203125e-7 + (double)(2 * cells + 40) * 5.9604644775390625e-8) * mag *
+                      0.6931471805599453 / (double)d.m) + 1e-7f;
+    P.total = total;
+    P.global_thr = global_thr;
+    P.list_score = list_score;
+    P.list_rank = list_rank;
+    P.list_count = list_count;
+    P.status = status;
+    P.dump = dump;
+
+    CUtensorMap map;
+    cuuint64_t gdim[2] = {(cuuint64_t)Kt, (cuuint64_t)(2 * d.n)};
+    cuuint64_t gstride[1] = {(cuuint64_t)Kt};
+    cuuint32_t box[2] = {(cuuint32_t)tc::kKC, 128u};
+    cuuint32_t estr[2] = {1u, 1u};
+    CUresult cr = g_encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<unsigned char *>(b8), gdim, gstride, box,
+                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    const size_t smem = tc_smem_bytes(P.cand_p2);
+    auto kern = k == 2 ? tc::tc_search_kernel<2> : (k == 3 ? tc::tc_search_kernel<3> : tc::tc_search_kernel<4>);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, tc::kThreads, smem, st>>>(map, P);
+    return cudaGetLastError();
+}
+
+}  // namespace epi

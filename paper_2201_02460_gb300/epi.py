@@ -81,6 +81,8 @@ def load(path: str | None = None):
         lib.epi_score_tables.argtypes = [V, i32, P, i64, P, P]
         lib.epi_kernel_launches.restype = u64
         lib.epi_kernel_launches.argtypes = [V]
+        lib.epi_debug_counts.restype = i32
+        lib.epi_debug_counts.argtypes = [V, i32, P]
         lib.epi_profile_begin.restype = i32
         lib.epi_profile_begin.argtypes = [V]
         lib.epi_profile_end.restype = i32
@@ -242,6 +244,17 @@ def search_async(ds: Dataset, order: int, top_n: int, out_dev, counts_dev, n_out
     cp = C.c_void_p(counts_dev.data_ptr()) if counts_dev is not None else None
     _check(lib.epi_search_async(ds.handle, order, top_n, PATHS[path], C.c_void_p(out_dev.data_ptr()), cp,
                                 C.c_void_p(n_out_dev.data_ptr()), C.c_void_p(status_dev.data_ptr())))
+
+
+def debug_counts(ds: Dataset, order: int) -> np.ndarray:
+    """Every combination's table as the tensor-core path counts it,
+    [C(n,k), 2, 3^k] in lexicographic rank order (small datasets only)."""
+    import math
+    lib = load()
+    total = math.comb(ds.n_snps, order)
+    out = np.zeros((total, 2, 3 ** order), dtype=np.uint32)
+    _check(lib.epi_debug_counts(ds.handle, order, _np_ptr(out)))
+    return out
 
 
 def tables(ds: Dataset, combs) -> np.ndarray:

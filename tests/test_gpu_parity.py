@@ -206,3 +206,71 @@ def test_score_tables_fp32_accuracy(epi, ctx):
         want = np.array([O.mi(t[0], t[1], 4096) for t in tabs])
         np.testing.assert_allclose(f64, want, rtol=0, atol=F64_ATOL)
         assert (np.abs(f32 - want) <= F32_RTOL * want + 1e-12).all()
+
+
+# ---------------------------------------------------------------------------
+# tensor-core counting path
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("k,n,m", [(2, 50, 300), (3, 24, 700), (3, 40, 129), (4, 14, 1000), (4, 12, 257),
+                                   (3, 70, 2000), (2, 150, 64)])
+def test_tc_counts_bit_exact(epi, ctx, k, n, m):
+    """Every combination's table from the tensor-core kernel equals the
+    popcount table kernel's and the oracle's, bit for bit."""
+    geno, pheno = random_data(n, m, seed=300 * k + n + m)
+    ds = epi.Dataset(ctx, geno, pheno)
+    got = epi.debug_counts(ds, k)
+    combs = np.array(brute.all_combinations(n, k), dtype=np.uint32)
+    want = epi.tables(ds, combs)
+    assert (want == O.tables(geno, pheno, combs.astype(np.int32))).all()
+    bad = np.nonzero((got != want).any(axis=(1, 2)))[0]
+    assert len(bad) == 0, f"{len(bad)} tables differ, first rank {bad[:5]}"
+
+
+@pytest.mark.parametrize("k,n,m,top_n", [(2, 60, 257, 25), (3, 30, 700, 50), (3, 90, 1500, 100),
+                                         (4, 22, 1100, 40), (4, 30, 513, 64)])
+def test_tc_search_small(epi, ctx, k, n, m, top_n):
+    geno, pheno = random_data(n, m, seed=11 * k + n)
+    ds, r, oc, om, _ = _search_both(epi, ctx, geno, pheno, k, top_n, path="tc")
+    _check_result(r, geno, pheno, oc, om)
+
+
+def test_tc_matches_popc(epi, ctx):
+    geno, pheno = random_data(120, 2000, seed=77)
+    geno[50] = geno[7]
+    ds = epi.Dataset(ctx, geno, pheno)
+    a = epi.search(ds, 3, 200, path="popc")
+    b = epi.search(ds, 3, 200, path="tc")
+    assert (a.combs == b.combs).all()
+    assert (a.mi == b.mi).all()
+    assert (a.counts == b.counts).all()
+    np.testing.assert_allclose(a.mi_f32, b.mi_f32, rtol=2e-6)
+
+
+def test_tc_workload_order3_reduced(epi, ctx):
+    from paper_2201_02460_gb300 import synth
+    d, k, top_n = synth.make_workload("order3_2000snp_4000", n_snps=260)
+    ds, r, oc, om, _ = _search_both(epi, ctx, d.geno, d.pheno, k, top_n, path="tc")
+    _check_result(r, d.geno, d.pheno, oc, om)
+
+
+def test_tc_workload_order4_reduced(epi, ctx):
+    from paper_2201_02460_gb300 import synth
+    d, k, top_n = synth.make_workload("order4_500snp_8192", n_snps=48)
+    ds, r, oc, om, _ = _search_both(epi, ctx, d.geno, d.pheno, k, top_n, path="tc")
+    _check_result(r, d.geno, d.pheno, oc, om)
+
+
+def test_tc_unsupported_cases(epi, ctx):
+    geno, pheno = random_data(20, 100, seed=1, m1=0)
+    ds = epi.Dataset(ctx, geno, pheno)
+    with pytest.raises(epi.EpiError) as e:
+        epi.search(ds, 3, 10, path="tc")
+    assert e.value.status == epi.EPI_EUNSUPPORTED
+    geno, pheno = random_data(20, 100, seed=1)
+    ds = epi.Dataset(ctx, geno, pheno)
+    with pytest.raises(epi.EpiError):
+        epi.search(ds, 3, 10, path="tc", rank_range=(0, 100))
+    # auto falls back to the popcount path for a range
+    r = epi.search(ds, 3, 10, path="auto", rank_range=(0, 100))
+    assert len(r) == 10
