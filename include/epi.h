@@ -79,7 +79,10 @@ const char *epi_last_error(void);
 
 /* Context on CUDA device `device`; all work is queued on `cuda_stream` (a
  * cudaStream_t, NULL = the legacy default stream).  The context owns its
- * device scratch memory, allocated on first use and grown as needed. */
+ * device scratch memory, allocated on first use and grown as needed.
+ * epi_destroy may be called while datasets of the context are alive: the
+ * context is then freed by the last epi_dataset_destroy, and no other call
+ * may use it meanwhile. */
 epi_status epi_create(int device, void *cuda_stream, epi_ctx **out);
 void epi_destroy(epi_ctx *ctx);
 

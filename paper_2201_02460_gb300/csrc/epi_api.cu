@@ -23,6 +23,8 @@ struct epi_ctx {
     uint64_t launches = 0;
     bool profiling = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
+    int64_t live_datasets = 0;     // datasets created on this context and not yet destroyed
+    bool destroy_requested = false;
 };
 
 struct epi_dataset {
@@ -392,15 +394,23 @@ epi_status epi_create(int device, void *cuda_stream, epi_ctx **out)
     return EPI_OK;
 }
 
-void epi_destroy(epi_ctx *ctx)
+static void free_ctx(epi_ctx *ctx)
 {
-    if (!ctx) return;
     DeviceGuard g(ctx->device);
     if (ctx->scratch) {
         cudaStreamSynchronize(ctx->stream);
         cudaFree(ctx->scratch);
     }
+    for (auto &pr : ctx->prof_events) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
     delete ctx;
+}
+
+void epi_destroy(epi_ctx *ctx)
+{
+    if (!ctx) return;
+    // a context outlives its datasets: the last epi_dataset_destroy frees it
+    ctx->destroy_requested = true;
+    if (ctx->live_datasets == 0) free_ctx(ctx);
 }
 
 epi_status epi_dataset_create(epi_ctx *ctx, const uint8_t *geno, const uint8_t *pheno, int64_t n_snps,
@@ -478,6 +488,7 @@ epi_status epi_dataset_create(epi_ctx *ctx, const uint8_t *geno, const uint8_t *
         if (ds) { cudaFree(ds->masks); cudaFree(ds->binom); delete ds; }
         return ret;
     }
+    ctx->live_datasets++;
     *out = ds;
     return EPI_OK;
 }
@@ -485,12 +496,17 @@ epi_status epi_dataset_create(epi_ctx *ctx, const uint8_t *geno, const uint8_t *
 void epi_dataset_destroy(epi_dataset *ds)
 {
     if (!ds) return;
-    DeviceGuard g(ds->ctx->device);
-    cudaStreamSynchronize(ds->ctx->stream);
-    cudaFree(ds->masks);
-    cudaFree(ds->binom);
-    if (ds->b8) cudaFree(ds->b8);
+    epi_ctx *ctx = ds->ctx;
+    {
+        DeviceGuard g(ctx->device);
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(ds->masks);
+        cudaFree(ds->binom);
+        if (ds->b8) cudaFree(ds->b8);
+    }
     delete ds;
+    ctx->live_datasets--;
+    if (ctx->destroy_requested && ctx->live_datasets == 0) free_ctx(ctx);
 }
 
 epi_status epi_dataset_info(const epi_dataset *ds, int64_t *n_snps, int64_t *n_samples, int64_t *n_cases,

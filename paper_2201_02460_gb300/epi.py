@@ -7,10 +7,12 @@ library is missing or cannot be loaded, every call raises.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes as C
 import os
 import re
 import threading
+import weakref
 
 import numpy as np
 
@@ -35,6 +37,23 @@ class EpiError(RuntimeError):
 
 _lock = threading.Lock()
 _lib = None
+_live_datasets: "weakref.WeakSet" = weakref.WeakSet()
+_live_contexts: "weakref.WeakSet" = weakref.WeakSet()
+
+
+@atexit.register
+def _close_all():
+    # datasets before their contexts, while the CUDA runtime is still up
+    for ds in list(_live_datasets):
+        try:
+            ds.close()
+        except Exception:
+            pass
+    for ctx in list(_live_contexts):
+        try:
+            ctx.close()
+        except Exception:
+            pass
 
 
 def exported_names() -> list[str]:
@@ -123,6 +142,7 @@ class Context:
         h = C.c_void_p()
         _check(lib.epi_create(device, C.c_void_p(stream), C.byref(h)))
         self._h = h
+        _live_contexts.add(self)
 
     @property
     def handle(self):
@@ -185,6 +205,7 @@ class Dataset:
         _check(lib.epi_dataset_create(ctx.handle, gp, pp, n, m, 1 if on_dev else 0, C.byref(h)))
         del keep
         self._h = h
+        _live_datasets.add(self)
         info = np.zeros(4, dtype=np.int64)
         _check(lib.epi_dataset_info(h, _np_ptr(info[0:]), _np_ptr(info[1:]), _np_ptr(info[2:]), _np_ptr(info[3:])))
         self.n_snps, self.n_samples, self.n_cases, self.n_controls = (int(x) for x in info)
