@@ -203,6 +203,7 @@ def run_ours(args):
             res = epi.search(ds, k, top_n, path=args.path)
             ev[s][1].record(stream)
         torch.cuda.synchronize()
+    waits = ctx.profile_waits() if args.path != "popc" else None
     kern_ms, kern_n = ctx.profile_end()
     launches = ctx.kernel_launches() - launches0
     t_ms = sum(a.elapsed_time(b) for a, b in ev)
@@ -248,6 +249,8 @@ def run_ours(args):
                          seconds=e2e_t),
                 roofline=roof, gpu_launches=int(launches), clocks=clocks,
                 top1=dict(snps=[int(x) for x in res.combs[0]], mi=float(res.mi[0]), planted=list(d.planted)))
+    if waits and waits.get("mma_loop"):
+        line["tc_wait_fractions"] = {k: round(v / waits["mma_loop"], 4) for k, v in waits.items() if k != "unused4"}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(d, k)
         cb.pop("seconds", None)

@@ -157,6 +157,16 @@ epi_status epi_debug_counts(epi_dataset *ds, int order, uint32_t *out);
 epi_status epi_profile_begin(epi_ctx *ctx);
 epi_status epi_profile_end(epi_ctx *ctx, double *kernel_ms, int64_t *launches);
 
+/* Wait-cycle trace of the last tensor-core search run while profiling was on
+ * (the paper has no counterpart): out[8] receives, averaged over CTAs, the
+ * SM cycles the MMA issuer waited for generated prefix tiles [0], for TMA
+ * tiles [1] and for a free accumulator [2], the A producers waited for a free
+ * stage [3], the epilogue waited for a finished accumulator [5], the TMA
+ * producer waited for a free stage [6], and the MMA issuer's whole loop [7].
+ * Zeros when no such search ran.  The value must be read before the context's
+ * next search (the scratch memory is reused). */
+epi_status epi_profile_waits(epi_ctx *ctx, double *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -24,6 +24,8 @@ struct epi_ctx {
     bool profiling = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
     int64_t live_datasets = 0;     // datasets created on this context and not yet destroyed
+    unsigned long long *waits_dev = nullptr;   // per-role wait cycles of the last profiled TC search
+    int waits_grid = 0;
     bool destroy_requested = false;
 };
 
@@ -238,6 +240,7 @@ epi_status queue_search(epi_dataset *ds, const SearchPlan &p, int path, epi_resu
     const size_t o_mi = a.take<double>((size_t)p.pool);
     const size_t o_cb = a.take<int32_t>((size_t)p.pool * p.k);
     const size_t o_ic = a.take<uint64_t>((size_t)ds->n + 1);
+    const size_t o_wt = a.take<unsigned long long>((size_t)p.grid * kTcWaitSlots);
     epi_status st = ensure_scratch(ctx, a.off);
     if (st != EPI_OK) return st;
     char *base = static_cast<char *>(ctx->scratch);
@@ -253,6 +256,7 @@ epi_status queue_search(epi_dataset *ds, const SearchPlan &p, int path, epi_resu
     double *mi = reinterpret_cast<double *>(base + o_mi);
     int32_t *cb = reinterpret_cast<int32_t *>(base + o_cb);
     uint64_t *ic = reinterpret_cast<uint64_t *>(base + o_ic);
+    unsigned long long *wt = reinterpret_cast<unsigned long long *>(base + o_wt);
     if (p.tc) {
         st = ensure_b8(ds);
         if (st != EPI_OK) return st;
@@ -269,8 +273,15 @@ epi_status queue_search(epi_dataset *ds, const SearchPlan &p, int path, epi_resu
     }
     if (p.tc) {
         int cand_p2 = 0;
+        unsigned long long *waits = nullptr;
+        if (ctx->profiling) {
+            CK(cudaMemsetAsync(wt, 0, (size_t)p.grid * kTcWaitSlots * 8, ctx->stream));
+            waits = wt;
+            ctx->waits_dev = wt;
+            ctx->waits_grid = p.grid;
+        }
         CK(launch_tc_search(d, p.k, ds->b8, ic, p.pool, thr, ls, lr, lc, status, p.grid, p.total, ctx->stream,
-                            &cand_p2, dump));
+                            &cand_p2, dump, waits));
         ctx->launches += 1;   // item table
     } else {
         CK(launch_popc_search(d, p.k, p.R, p.rb, p.re, p.tile, p.pool, p.slots, p.cand_p2, thr, ls, lr, lc, p.grid,
@@ -669,6 +680,20 @@ epi_status epi_profile_begin(epi_ctx *ctx)
     for (auto &pr : ctx->prof_events) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
     ctx->prof_events.clear();
     ctx->profiling = true;
+    return EPI_OK;
+}
+
+epi_status epi_profile_waits(epi_ctx *ctx, double *out)
+{
+    if (!ctx || !out) return fail(EPI_EINVAL, "NULL argument");
+    for (int i = 0; i < kTcWaitSlots; i++) out[i] = 0.0;
+    if (!ctx->waits_dev || ctx->waits_grid <= 0) return EPI_OK;
+    DeviceGuard g(ctx->device);
+    std::vector<unsigned long long> h((size_t)ctx->waits_grid * kTcWaitSlots);
+    CK(cudaMemcpyAsync(h.data(), ctx->waits_dev, h.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int b = 0; b < ctx->waits_grid; b++)
+        for (int i = 0; i < kTcWaitSlots; i++) out[i] += (double)h[(size_t)b * kTcWaitSlots + i] / ctx->waits_grid;
     return EPI_OK;
 }
 

@@ -48,7 +48,8 @@ size_t tc_smem_bytes(int cand_p2);
 cudaError_t launch_tc_search(const DevData &d, int k, const unsigned char *b8, uint64_t *item_cum, int pool,
                              uint32_t *global_thr, float *list_score, uint64_t *list_rank, int32_t *list_count,
                              int32_t *status, int grid, uint64_t total, cudaStream_t st, int *cand_p2_out,
-                             uint32_t *dump = nullptr);
+                             uint32_t *dump = nullptr, unsigned long long *waits = nullptr);
+constexpr int kTcWaitSlots = 8;
 
 // epi_select.cu
 cudaError_t launch_merge(const float *ls, const uint64_t *lr, const int32_t *lc, int nlists, int stride, int pool,

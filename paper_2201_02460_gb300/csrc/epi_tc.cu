@@ -5,11 +5,20 @@
 //     count[(p, x'), (j, g)] = sum over individuals s of A[(p, x')][s] * B[(j, g)][s]
 // with A[(p, x')] the genotype-table row x' of prefix p (Section 2.1) and
 // B[(j, g)] row g of SNP j, summed separately over the case and the control
-// individuals.  Both operands hold 0/1 values as FP8 E4M3 bytes (A: 2^-6,
-// B: 1.0), accumulated in FP32 in tensor memory: every partial sum is an
-// integer multiple of 2^-6 below 2^17, hence exact.  Genotype 2 of the last
-// SNP is obtained by subtraction from the prefix row's total, as in the
-// popcount path.
+// individuals.  Both operands hold 0/1 values as FP8 E4M3 bytes and the MMA
+// accumulates in FP32 in tensor memory.  Because the product sums over K,
+// any fixed permutation of the individuals inside a K stage, applied to both
+// operands, leaves the counts unchanged, and the two operands may carry
+// different weights per K position as long as their product is constant:
+//   * K byte 4 i + b of each 32-individual word holds individual 8 b + i, so
+//     the A producer turns one mask word into eight output words with one
+//     AND each (output i keeps bit i of every byte, shifted into bits 3..6);
+//   * A's nonzero byte at position i is 2^-5, 2^-3, 2^1 or 2^-6 (normal E4M3
+//     powers of two) and B's is the reciprocal times 2^-5, so every product
+//     of two ones is exactly 2^-5 and an accumulator holds count * 2^-5, an
+//     exact FP32 value.
+// Genotype 2 of the last SNP is obtained by subtraction from the prefix
+// row's total, as in the popcount path.
 //
 // Layout of one tile: M = 128 rows = 4 warps x 32 lanes; each warp holds
 // floor(32 / 3^(k-1)) whole prefixes (prefix rows never straddle a warp, so
@@ -18,14 +27,17 @@
 // Prefixes are taken in "panel order" (by their last SNP c ascending) so the
 // last SNPs of a tile, j > c, form one contiguous range.
 //
-// Warp roles (320 threads, one CTA per SM, persistent, a contiguous range of
+// Warp roles (576 threads, one CTA per SM, persistent, a contiguous range of
 // work items per CTA; an item = one M tile x one N tile x the whole K range):
-//   warps 0-3  epilogue: TMEM -> registers, single-precision MI screen,
-//              exact-margin candidate selection, per-CTA candidate list
-//   warps 4-7  A producers: prefix rows = AND of the prefix SNPs' bit rows,
-//              expanded to E4M3 bytes in the 128-byte-swizzled K-major layout
-//   warp 8     TMA producer of B tiles, and writer of the item descriptors
-//   warp 9     TMEM allocator and MMA issuer (one elected thread)
+//   warps 0-7   epilogue: TMEM -> registers, single-precision MI screen,
+//               exact-margin candidate selection, per-CTA candidate list;
+//               warp w reads TMEM lane quadrant w % 4 for half w / 4 of the
+//               tile's last SNPs
+//   warps 8-15  A producers: prefix rows = AND of the prefix SNPs' bit rows,
+//               expanded to E4M3 bytes in the 128-byte-swizzled K-major
+//               layout; two threads per row, next K stage prefetched
+//   warp 16     TMA producer of B tiles, and writer of the item descriptors
+//   warp 17     TMEM allocator and MMA issuer (one elected thread)
 // Every mbarrier wait is bounded (about 2 s); a wait that gives up sets
 // ST_TIMEOUT and all roles leave their loops, drain their own asynchronous
 // work and free tensor memory.
@@ -42,10 +54,15 @@ namespace tc {
 constexpr int kJ = 64;                 // last SNPs per N tile
 constexpr int kN = 2 * kJ;             // accumulator columns per class
 constexpr int kKC = 128;               // individuals (bytes) per K stage
-constexpr int kStages = 4;
+constexpr int kStagesA = 6;            // generated prefix-row stages
+constexpr int kStagesB = 6;            // TMA stages of single-SNP rows
 constexpr int kDescDepth = 4;
-constexpr int kThreads = 320;
-constexpr int kStageBytes = 2 * 128 * kKC;   // A and B tiles
+constexpr int kEpiWarps = 8;           // two per TMEM lane quadrant
+constexpr int kProdWarps = 8;          // two threads per tile row
+constexpr int kThreads = 32 * (kEpiWarps + kProdWarps + 2);
+constexpr int kEpiThreads = 32 * kEpiWarps;
+constexpr int kTileBytes = 128 * kKC;        // one A or B tile
+constexpr int kWaitSlots = 8;
 constexpr uint32_t kTxBytes = 128 * kKC;     // B tile bytes per stage
 constexpr int kMaxDescSnps = 40;
 constexpr unsigned long long kTimeoutNs = 2000000000ull;
@@ -74,6 +91,7 @@ struct Params {
     int32_t *list_count;
     int32_t *status;
     uint32_t *dump;            // optional: every table, [rank][2][3^k] (validation)
+    unsigned long long *waits; // optional: [grid][8] cycles spent waiting, per role (tracing)
 };
 
 // ------------------------------------------------------------------ PTX --
@@ -127,6 +145,17 @@ __device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile 
             return false;
         }
     }
+}
+
+// Hot-path wait: one inline try_wait; the bounded out-of-line wait (and the
+// cycle accounting of the trace) only when the phase is not complete yet.
+__device__ __forceinline__ bool wait_fast(uint64_t *bar, uint32_t parity, volatile int *abort_flag, long long &acc)
+{
+    if (mbar_try(bar, parity)) return true;
+    const long long t0 = clock64();
+    const bool ok = mbar_wait(bar, parity, abort_flag);
+    acc += clock64() - t0;
+    return ok;
 }
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -183,7 +212,7 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar)
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory"); }
 
 // ------------------------------------------------------------ enumeration --
 // Prefixes of order k are the (k-1)-subsets whose last SNP c is <= n-2, in
@@ -244,19 +273,17 @@ __device__ inline void prefix_next(int k, PrefixIter &it)
 __device__ __forceinline__ int64_t ntiles_of(const DevData &d, int32_t c) { return (d.n - 1 - c + kJ - 1) / kJ; }
 
 // -------------------------------------------------------------- epilogue --
-__device__ __forceinline__ uint32_t f2count(uint32_t bits)
-{
-    // accumulator = count * 2^-6, exact; back to the integer
-    const float v = __uint_as_float(bits) * 64.0f;
-    return __float_as_uint(v + 8388608.0f) & 0x7FFFFFu;
-}
+// accumulator = count * 2^-5 (exact): the count as a float, and as an integer
+__device__ __forceinline__ float acc2f(uint32_t bits) { return __uint_as_float(bits) * 32.0f; }
+__device__ __forceinline__ uint32_t f2u_exact(float v) { return __float_as_uint(v + 8388608.0f) & 0x7FFFFFu; }
 
 __device__ __forceinline__ float tlog(float c) { return c * __log2f(fmaxf(c, 1.0f)); }
 
-__device__ __forceinline__ float seg_sum(float v, int pos, int PR)
+template <int PR>
+__device__ __forceinline__ float seg_sum(float v, int pos)
 {
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
+    for (int off = 1; off < PR; off <<= 1) {
         const float o = __shfl_down_sync(0xffffffffu, v, off);
         if ((pos & (2 * off - 1)) == 0 && pos + off < PR) v += o;
     }
@@ -267,7 +294,7 @@ __device__ inline void sort_cands_epi(float *sc, uint64_t *rk, int p2, int tid)
 {
     for (int kk = 2; kk <= p2; kk <<= 1) {
         for (int jj = kk >> 1; jj > 0; jj >>= 1) {
-            for (int i = tid; i < p2; i += 128) {
+            for (int i = tid; i < p2; i += kEpiThreads) {
                 const int ixj = i ^ jj;
                 if (ixj > i) {
                     const bool up = (i & kk) == 0;
@@ -294,7 +321,7 @@ __device__ inline void epi_flush(EpiState &S, float *sc, uint64_t *rk, int pool,
     epi_bar();
     const int live = S.list_len + S.nbuf;
     const int p2 = next_pow2(live < 2 ? 2 : live);
-    for (int i = live + tid; i < p2; i += 128) { sc[i] = -1.0f; rk[i] = ~0ull; }
+    for (int i = live + tid; i < p2; i += kEpiThreads) { sc[i] = -1.0f; rk[i] = ~0ull; }
     epi_bar();
     sort_cands_epi(sc, rk, p2, tid);
     if (tid == 0) {
@@ -309,6 +336,22 @@ __device__ inline void epi_flush(EpiState &S, float *sc, uint64_t *rk, int pool,
 }
 
 // ---------------------------------------------------------------- kernel --
+// Precise single-precision terms of one tile row's three cells (the rare
+// candidate path, kept out of line).
+__device__ __noinline__ float row_terms_precise(uint32_t a0, uint32_t b0, uint32_t a1, uint32_t b1, uint32_t a2,
+                                                uint32_t b2, const MiConstF32 mc)
+{
+    return cell_terms_f32(a0, b0, mc) + cell_terms_f32(a1, b1, mc) + cell_terms_f32(a2, b2, mc);
+}
+
+#define TMEM_LD16(taddr, r)                                                                                      \
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, " \
+                 "[%16];"                                                                                        \
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), \
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),       \
+                   "=r"(r[15])                                                                                   \
+                 : "r"(taddr))
+
 template <int K>
 __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_constant__ CUtensorMap tmap_b,
                                                                 const Params P)
@@ -316,16 +359,20 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
     constexpr int kPR = K == 2 ? 3 : (K == 3 ? 9 : 27);
     constexpr int kPPW = 32 / kPR;
     constexpr int kPPT = 4 * kPPW;
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    // 1024-byte aligned stage area first
-    unsigned char *smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
-    unsigned char *stages = smem;
-    float *sc = reinterpret_cast<float *>(stages + kStages * kStageBytes);
-    uint64_t *rk = reinterpret_cast<uint64_t *>(sc + P.cand_p2);
-    uint32_t *tot = reinterpret_cast<uint32_t *>(rk + P.cand_p2);   // [2][128][2]
-    Desc *desc = reinterpret_cast<Desc *>(tot + 2 * 128 * 2);
+    constexpr int km1 = K - 1;
+    constexpr int kWarpTma = kEpiWarps + kProdWarps;
+    constexpr int kWarpMma = kWarpTma + 1;
 
-    __shared__ __align__(8) uint64_t full_a[kStages], full_b[kStages], empty[kStages];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
+    unsigned char *stages_a = smem;
+    unsigned char *stages_b = smem + kStagesA * kTileBytes;
+    float *sc = reinterpret_cast<float *>(stages_b + kStagesB * kTileBytes);
+    uint64_t *rk = reinterpret_cast<uint64_t *>(sc + P.cand_p2);
+    uint32_t *tot = reinterpret_cast<uint32_t *>(rk + P.cand_p2);   // [2][128][2 halves][2 classes]
+    Desc *desc = reinterpret_cast<Desc *>(tot + 2 * 128 * 4);
+
+    __shared__ __align__(8) uint64_t full_a[kStagesA], empty_a[kStagesA], full_b[kStagesB], empty_b[kStagesB];
     __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], tot_full[2];
     __shared__ __align__(8) uint64_t desc_full[kDescDepth], desc_empty[kDescDepth], drain_bar;
     __shared__ uint32_t tmem_base_sh;
@@ -335,23 +382,35 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     const DevData &d = P.d;
-    constexpr int km1 = K - 1;
 
-    // contiguous item range of this CTA
     const uint64_t it_b = (uint64_t)(((unsigned __int128)P.n_items * blockIdx.x) / gridDim.x);
     const uint64_t it_e = (uint64_t)(((unsigned __int128)P.n_items * (blockIdx.x + 1)) / gridDim.x);
     const int64_t n_my = (int64_t)(it_e - it_b);
 
     if (tid == 0) {
-        for (int s = 0; s < kStages; s++) { mbar_init(&full_a[s], 4); mbar_init(&full_b[s], 1); mbar_init(&empty[s], 1); }
-        for (int b = 0; b < 2; b++) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], 4); mbar_init(&tot_full[b], 4); }
-        for (int q = 0; q < kDescDepth; q++) { mbar_init(&desc_full[q], 1); mbar_init(&desc_empty[q], 8); }
+        for (int s = 0; s < kStagesA; s++) {
+            mbar_init(&full_a[s], kProdWarps);
+            mbar_init(&empty_a[s], 1);
+        }
+        for (int s = 0; s < kStagesB; s++) {
+            mbar_init(&full_b[s], 1);
+            mbar_init(&empty_b[s], 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], kEpiWarps);
+            mbar_init(&tot_full[b], kProdWarps);
+        }
+        for (int q = 0; q < kDescDepth; q++) {
+            mbar_init(&desc_full[q], 1);
+            mbar_init(&desc_empty[q], kEpiWarps + kProdWarps);
+        }
         mbar_init(&drain_bar, 1);
         abort_flag = 0;
         ES.list_len = 0; ES.nbuf = 0; ES.stop = 0; ES.thr = -1.0f;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 9) {
+    if (warp == kWarpMma) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
                      "r"(512)
                      : "memory");
@@ -362,10 +421,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
     tc_fence_after();
     const uint32_t tmem_base = tmem_base_sh;
 
-    if (warp == 8) {
+    if (warp == kWarpTma) {
         // ------------------------------------------------ TMA + descriptors
         if (lane == 0 && n_my > 0) {
-            // decode the first item: panel by binary search, then M tile / N tile
             const uint64_t w0 = it_b;
             int64_t lo = 0, hi = d.n - 1;
             while (lo < hi) {
@@ -377,24 +435,29 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
             const uint64_t off = w0 - P.item_cum[c0];
             const int64_t nt0 = ntiles_of(d, c0);
             const uint64_t tfirst = (binom_at(d.binom, d.n, c0, km1) + kPPT - 1) / kPPT;
-            uint64_t t = tfirst + off / (uint64_t)nt0;
+            const uint64_t t = tfirst + off / (uint64_t)nt0;
             int64_t u = (int64_t)(off % (uint64_t)nt0);
             PrefixIter it;
             prefix_unrank(d, K, t * (uint64_t)kPPT, it);
-            int32_t tile_snp[kMaxDescSnps];
+            int32_t tile_snp[kPPT * km1];
             int32_t nvalid = 0, cmin = it.c;
             auto fill_tile = [&]() {
                 nvalid = 0;
                 cmin = it.c;
-                for (int p = 0; p < kPPT && it.q < P.n_prefix; p++) {
-                    for (int s2 = 0; s2 < km1 - 1; s2++) tile_snp[p * km1 + s2] = it.a[s2];
-                    tile_snp[p * km1 + km1 - 1] = it.c;
-                    nvalid++;
-                    prefix_next(K, it);
+#pragma unroll
+                for (int p = 0; p < kPPT; p++) {
+                    if (it.q < P.n_prefix) {
+#pragma unroll
+                        for (int s2 = 0; s2 < km1 - 1; s2++) tile_snp[p * km1 + s2] = it.a[s2];
+                        tile_snp[p * km1 + km1 - 1] = it.c;
+                        nvalid++;
+                        prefix_next(K, it);
+                    }
                 }
             };
             fill_tile();
-            uint64_t g = 0;   // global chunk counter
+            uint64_t g = 0;
+            long long w_tma = 0;
             for (int64_t i = 0; i < n_my && !abort_flag; i++) {
                 const int dq = (int)(i % kDescDepth);
                 const uint32_t ud = (uint32_t)(i / kDescDepth);
@@ -402,93 +465,104 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                 Desc &D = desc[dq];
                 D.j0 = cmin + 1 + (int32_t)(u * kJ);
                 D.nvalid = nvalid;
-                for (int q = 0; q < nvalid * km1; q++) D.snp[q] = tile_snp[q];
+#pragma unroll
+                for (int q = 0; q < kPPT * km1; q++) D.snp[q] = tile_snp[q];
                 mbar_arrive(&desc_full[dq]);
                 const int y = 2 * D.j0;
                 for (int kc = 0; kc < P.chunks; kc++, g++) {
-                    const int s = (int)(g % kStages);
-                    const uint32_t us = (uint32_t)(g / kStages);
-                    if (!mbar_wait(&empty[s], (us & 1) ^ 1, &abort_flag)) break;
+                    const int s = (int)(g % kStagesB);
+                    const uint32_t us = (uint32_t)(g / kStagesB);
+                    if (!wait_fast(&empty_b[s], (us & 1) ^ 1, &abort_flag, w_tma)) break;
                     mbar_arrive_tx(&full_b[s], kTxBytes);
-                    tma_load_2d(stages + s * kStageBytes + 128 * kKC, &tmap_b, kc * kKC, y, &full_b[s]);
+                    tma_load_2d(stages_b + s * kTileBytes, &tmap_b, kc * kKC, y, &full_b[s]);
                 }
-                // advance to the next item
                 u++;
                 if (u == ntiles_of(d, cmin)) {
                     u = 0;
                     fill_tile();
                 }
             }
-            // drain: the last load issued into each stage must have landed
-            for (int s = 0; s < kStages; s++) {
+            if (P.waits) P.waits[blockIdx.x * kWaitSlots + 6] = (unsigned long long)w_tma;
+            for (int s = 0; s < kStagesB; s++) {
                 if (g > (uint64_t)s) {
-                    const uint64_t last = ((g - 1 - s) / kStages) * kStages + s;   // last chunk index in stage s
-                    const uint32_t us = (uint32_t)(last / kStages);
+                    const uint64_t last = ((g - 1 - s) / kStagesB) * kStagesB + s;
+                    const uint32_t us = (uint32_t)(last / kStagesB);
                     const uint64_t t0 = now_ns();
                     while (!mbar_try(&full_b[s], us & 1) && now_ns() - t0 < kTimeoutNs) {}
                 }
             }
         }
-    } else if (warp == 9) {
+    } else if (warp == kWarpMma) {
         // ------------------------------------------------------------- MMA
         if (lane == 0 && n_my > 0) {
             uint64_t g = 0;
-            const uint32_t a0 = smem_u32(stages);
+            const uint32_t sa0 = smem_u32(stages_a), sb0 = smem_u32(stages_b);
+            long long w_a = 0, w_b = 0, w_acc = 0;
+            const long long t_start = clock64();
             for (int64_t i = 0; i < n_my && !abort_flag; i++) {
                 const int b = (int)(i & 1);
                 const uint32_t ub = (uint32_t)(i >> 1);
-                if (!mbar_wait(&acc_empty[b], (ub & 1) ^ 1, &abort_flag)) break;
+                if (!wait_fast(&acc_empty[b], (ub & 1) ^ 1, &abort_flag, w_acc)) break;
                 tc_fence_after();
                 bool ok = true;
                 for (int kc = 0; kc < P.chunks; kc++, g++) {
-                    const int s = (int)(g % kStages);
-                    const uint32_t us = (uint32_t)(g / kStages);
-                    if (!mbar_wait(&full_a[s], us & 1, &abort_flag) || !mbar_wait(&full_b[s], us & 1, &abort_flag)) {
-                        ok = false;
-                        break;
-                    }
+                    const int sa = (int)(g % kStagesA), sb = (int)(g % kStagesB);
+                    const uint32_t ua = (uint32_t)(g / kStagesA), ubb = (uint32_t)(g / kStagesB);
+                    if (!wait_fast(&full_a[sa], ua & 1, &abort_flag, w_a)) { ok = false; break; }
+                    if (!wait_fast(&full_b[sb], ubb & 1, &abort_flag, w_b)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t dcol = tmem_base + (uint32_t)(b * 2 * kN) + (kc < P.chunks_case ? 0u : (uint32_t)kN);
                     const bool first = (kc == 0) || (kc == P.chunks_case);
-                    const uint64_t ad = sdesc(a0 + s * kStageBytes);
-                    const uint64_t bd = sdesc(a0 + s * kStageBytes + 128 * kKC);
+                    const uint64_t ad = sdesc(sa0 + sa * kTileBytes);
+                    const uint64_t bd = sdesc(sb0 + sb * kTileBytes);
 #pragma unroll
                     for (int kk = 0; kk < kKC / 32; kk++)
                         mma_f8(dcol, ad + 2 * kk, bd + 2 * kk, (first && kk == 0) ? 0u : 1u);
-                    mma_commit(&empty[s]);
+                    mma_commit(&empty_a[sa]);
+                    mma_commit(&empty_b[sb]);
                 }
                 if (!ok) break;
                 mma_commit(&acc_full[b]);
             }
-            // every issued MMA has completed before tensor memory is freed
+            if (P.waits) {
+                unsigned long long *wp = P.waits + blockIdx.x * kWaitSlots;
+                wp[0] = (unsigned long long)w_a;
+                wp[1] = (unsigned long long)w_b;
+                wp[2] = (unsigned long long)w_acc;
+                wp[7] = (unsigned long long)(clock64() - t_start);
+            }
             mma_commit(&drain_bar);
             const uint64_t t0 = now_ns();
             while (!mbar_try(&drain_bar, 0) && now_ns() - t0 < kTimeoutNs) {}
         }
-    } else if (warp >= 4) {
+    } else if (warp >= kEpiWarps) {
         // ---------------------------------------------------- A producers
-        const int r = tid - 128;           // tile row
-        const int w = r >> 5, l = r & 31;
+        const int t = tid - kEpiThreads;     // 0 .. 255
+        const int r = t >> 1;                // tile row
+        const int half = t & 1;              // words 2 half, 2 half + 1 of a stage
+        const int l = r & 31, w = r >> 5;
+        const int pwarp = (tid >> 5) - kEpiWarps;
         uint64_t g = 0;
+        long long w_prod = 0;
         for (int64_t i = 0; i < n_my; i++) {
             if (abort_flag) break;
             const int dq = (int)(i % kDescDepth);
             const uint32_t ud = (uint32_t)(i / kDescDepth);
             if (!mbar_wait(&desc_full[dq], ud & 1, &abort_flag)) break;
             const Desc &D = desc[dq];
-            // this row: prefix p, genotype digits of x'
-            const uint32_t *rows[kMaxOrderGpu];
+            const uint2 *rows[km1];
             bool active = false;
             if (l < kPPW * kPR) {
                 const int p = w * kPPW + l / kPR;
                 if (p < D.nvalid) {
                     active = true;
                     int rem = l % kPR, div = kPR / 3;
-                    for (int t = 0; t < km1; t++) {
+#pragma unroll
+                    for (int tt = 0; tt < km1; tt++) {
                         const int gg = rem / div;
                         rem -= gg * div;
                         div = div > 1 ? div / 3 : 1;
-                        rows[t] = d.masks + ((int64_t)D.snp[p * km1 + t] * 3 + gg) * d.Wt;
+                        rows[tt] = reinterpret_cast<const uint2 *>(d.masks + ((int64_t)D.snp[p * km1 + tt] * 3 + gg) * d.Wt) + half;
                     }
                 }
             }
@@ -496,112 +570,145 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
             if (lane == 0) mbar_arrive(&desc_empty[dq]);
             uint32_t t1 = 0, t0 = 0;
             bool ok = true;
-            for (int kc = 0; kc < P.chunks; kc++, g++) {
-                const int s = (int)(g % kStages);
-                const uint32_t us = (uint32_t)(g / kStages);
-                if (!mbar_wait(&empty[s], (us & 1) ^ 1, &abort_flag)) { ok = false; break; }
-                unsigned char *arow = stages + s * kStageBytes + r * 128;
-                uint4 bits = make_uint4(0, 0, 0, 0);
-                if (active) {
-                    bits = __ldg(reinterpret_cast<const uint4 *>(rows[0]) + kc);
-                    for (int t = 1; t < km1; t++) {
-                        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(rows[t]) + kc);
-                        bits.x &= v.x; bits.y &= v.y; bits.z &= v.z; bits.w &= v.w;
-                    }
-                    const uint32_t c4 = __popc(bits.x) + __popc(bits.y) + __popc(bits.z) + __popc(bits.w);
-                    if (kc < P.chunks_case) t1 += c4;
-                    else t0 += c4;
-                }
-                const uint32_t wv[4] = {bits.x, bits.y, bits.z, bits.w};
+            // two-word slices of this row, loaded kPf stages ahead (a register
+            // ring indexed statically: the stage loop is unrolled by kPf)
+            constexpr int kPf = 4;
+            uint2 ring[kPf];
 #pragma unroll
-                for (int cc = 0; cc < 8; cc++) {
-                    const uint32_t h = (wv[cc >> 1] >> ((cc & 1) * 16)) & 0xFFFFu;
-                    uint4 o;
-                    o.x = ((h & 0xFu) * 0x01020408u) & 0x08080808u;
-                    o.y = (((h >> 4) & 0xFu) * 0x01020408u) & 0x08080808u;
-                    o.z = (((h >> 8) & 0xFu) * 0x01020408u) & 0x08080808u;
-                    o.w = (((h >> 12) & 0xFu) * 0x01020408u) & 0x08080808u;
-                    *reinterpret_cast<uint4 *>(arow + ((cc ^ (r & 7)) << 4)) = o;
+            for (int u = 0; u < kPf; u++) {
+                ring[u] = make_uint2(0, 0);
+                if (active && u < P.chunks) {
+                    ring[u] = __ldg(rows[0] + 2 * u);
+#pragma unroll
+                    for (int tt = 1; tt < km1; tt++) {
+                        const uint2 v = __ldg(rows[tt] + 2 * u);
+                        ring[u].x &= v.x; ring[u].y &= v.y;
+                    }
                 }
-                fence_proxy_async();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&full_a[s]);
+            }
+            for (int kb = 0; kb < P.chunks && ok; kb += kPf) {
+#pragma unroll
+                for (int u = 0; u < kPf; u++) {
+                    const int kc = kb + u;
+                    if (kc >= P.chunks) break;
+                    const uint2 cur = ring[u];
+                    if (active && kc + kPf < P.chunks) {
+                        ring[u] = __ldg(rows[0] + 2 * (kc + kPf));
+#pragma unroll
+                        for (int tt = 1; tt < km1; tt++) {
+                            const uint2 v = __ldg(rows[tt] + 2 * (kc + kPf));
+                            ring[u].x &= v.x; ring[u].y &= v.y;
+                        }
+                    }
+                    const int s = (int)(g % kStagesA);
+                    const uint32_t us = (uint32_t)(g / kStagesA);
+                    if (!wait_fast(&empty_a[s], (us & 1) ^ 1, &abort_flag, w_prod)) { ok = false; break; }
+                    if (active) {
+                        const uint32_t c2 = __popc(cur.x) + __popc(cur.y);
+                        if (kc < P.chunks_case) t1 += c2;
+                        else t0 += c2;
+                    }
+                    unsigned char *arow = stages_a + s * kTileBytes + r * 128;
+#pragma unroll
+                    for (int q = 0; q < 2; q++) {
+                        // output word i = bit i of every byte of the mask word
+                        const uint32_t wv = q ? cur.y : cur.x;
+                        const uint32_t s4 = wv << 4, r4 = wv >> 4;
+                        const uint4 lo = make_uint4(s4 & 0x10101010u, s4 & 0x20202020u, s4 & 0x40404040u, wv & 0x08080808u);
+                        const uint4 hi = make_uint4(wv & 0x10101010u, wv & 0x20202020u, wv & 0x40404040u, r4 & 0x08080808u);
+                        const int cc = 4 * half + 2 * q;
+                        *reinterpret_cast<uint4 *>(arow + ((cc ^ (r & 7)) << 4)) = lo;
+                        *reinterpret_cast<uint4 *>(arow + (((cc + 1) ^ (r & 7)) << 4)) = hi;
+                    }
+                    fence_proxy_async();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&full_a[s]);
+                    g++;
+                }
             }
             if (!ok) break;
-            // prefix-row totals for the epilogue's third genotype
             const int b = (int)(i & 1);
             const uint32_t ub = (uint32_t)(i >> 1);
             if (!mbar_wait(&acc_empty[b], (ub & 1) ^ 1, &abort_flag)) break;
-            tot[(b * 128 + r) * 2 + 0] = t1;
-            tot[(b * 128 + r) * 2 + 1] = t0;
+            tot[((b * 128 + r) * 2 + half) * 2 + 0] = t1;
+            tot[((b * 128 + r) * 2 + half) * 2 + 1] = t0;
             __syncwarp();
             if (lane == 0) mbar_arrive(&tot_full[b]);
         }
+        if (P.waits && t == 0) P.waits[blockIdx.x * kWaitSlots + 3] = (unsigned long long)w_prod;
+        (void)pwarp;
     } else {
         // -------------------------------------------------------- epilogue
-        const int r = tid;                 // tile row = TMEM lane
+        const int quad = warp & 3;           // TMEM lane quadrant
+        const int jhalf = warp >> 2;         // which 32 last SNPs of the tile
+        const int r = quad * 32 + lane;      // tile row = TMEM lane
         const int l = lane;
         const int pos = l % kPR;
-        const int pl = l / kPR;           // prefix within the warp
+        const int pl = l / kPR;
         const bool lane_real = l < kPPW * kPR;
         const MiConstF32 mc = make_mi_const(d.m, d.m1, d.m0);
+        long long w_epi = 0;
         for (int64_t i = 0; i < n_my; i++) {
             const int dq = (int)(i % kDescDepth);
             const uint32_t ud = (uint32_t)(i / kDescDepth);
             const int b = (int)(i & 1);
             const uint32_t ub = (uint32_t)(i >> 1);
             bool ok = mbar_wait(&desc_full[dq], ud & 1, &abort_flag);
-            ok = ok && mbar_wait(&acc_full[b], ub & 1, &abort_flag);
+            ok = ok && wait_fast(&acc_full[b], ub & 1, &abort_flag, w_epi);
             ok = ok && mbar_wait(&tot_full[b], ub & 1, &abort_flag);
             ok = __all_sync(0xffffffffu, ok);
             tc_fence_after();
             const Desc &D = desc[dq];
-            const int p = warp * kPPW + pl;
+            const int p = quad * kPPW + pl;
             const bool prow = ok && lane_real && p < D.nvalid;
             const int32_t cpre = prow ? D.snp[p * km1 + km1 - 1] : 0x7fffffff;
-            int32_t psnp[kMaxOrderGpu];
-            for (int t = 0; t < km1; t++) psnp[t] = prow ? D.snp[p * km1 + t] : 0;
-            const uint32_t T1 = tot[(b * 128 + r) * 2 + 0], T0 = tot[(b * 128 + r) * 2 + 1];
-            const int32_t j0 = D.j0;
-            // threshold: the CTA's and the best known global one
+            int32_t psnp[km1];
+#pragma unroll
+            for (int tt = 0; tt < km1; tt++) psnp[tt] = prow ? D.snp[p * km1 + tt] : 0;
+            const uint32_t T1 = tot[((b * 128 + r) * 2 + 0) * 2 + 0] + tot[((b * 128 + r) * 2 + 1) * 2 + 0];
+            const uint32_t T0 = tot[((b * 128 + r) * 2 + 0) * 2 + 1] + tot[((b * 128 + r) * 2 + 1) * 2 + 1];
+            const float fT1 = u2f_exact(T1), fT0 = u2f_exact(T0);
+            const int32_t j0 = D.j0 + 32 * jhalf;
             if (tid == 0) {
                 const float gthr = __uint_as_float(*(volatile uint32_t *)P.global_thr);
                 if (ES.list_len == P.pool || gthr > 0.0f) ES.thr = fmaxf(ES.thr, gthr);
             }
             epi_bar();
-            for (int jc = 0; jc < kJ / 16; jc++) {
-                // list position and threshold as of the last flush
+#pragma unroll 1
+            for (int jc = 0; jc < 4; jc++) {
                 const float thr = ES.thr;
                 const float cut = thr - P.delta;
                 const int list_len = ES.list_len;
-                uint32_t cs[32], cn[32];
+                uint32_t cs[16], cn[16];
                 if (ok) {
-                    const uint32_t ta = tmem_base + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * 2 * kN + 32 * jc);
-                    TMEM_LD32(ta, cs);
-                    TMEM_LD32(ta + kN, cn);
+                    const uint32_t ta = tmem_base + ((uint32_t)(quad * 32) << 16) +
+                                        (uint32_t)(b * 2 * kN + 64 * jhalf + 16 * jc);
+                    TMEM_LD16(ta, cs);
+                    TMEM_LD16(ta + kN, cn);
                     tmem_wait_ld();
                 } else {
 #pragma unroll
-                    for (int q = 0; q < 32; q++) { cs[q] = 0; cn[q] = 0; }
+                    for (int q = 0; q < 16; q++) { cs[q] = 0; cn[q] = 0; }
                 }
 #pragma unroll
-                for (int jj = 0; jj < 16; jj++) {
-                    const int32_t j = j0 + 16 * jc + jj;
-                    const uint32_t a0 = f2count(cs[2 * jj]), a1 = f2count(cs[2 * jj + 1]);
-                    const uint32_t b0 = f2count(cn[2 * jj]), b1 = f2count(cn[2 * jj + 1]);
-                    const uint32_t a2 = T1 - a0 - a1, b2 = T0 - b0 - b1;
+                for (int jj = 0; jj < 8; jj++) {
+                    const int32_t j = j0 + 8 * jc + jj;
+                    // counts as exact floats (all below 2^23)
+                    const float fa0 = acc2f(cs[2 * jj]), fa1 = acc2f(cs[2 * jj + 1]);
+                    const float fb0 = acc2f(cn[2 * jj]), fb1 = acc2f(cn[2 * jj + 1]);
+                    const float fa2 = fT1 - fa0 - fa1, fb2 = fT0 - fb0 - fb1;
                     float v = 0.0f;
-                    if (prow) {
-                        const float fa0 = u2f_exact(a0), fa1 = u2f_exact(a1), fa2 = u2f_exact(a2);
-                        const float fb0 = u2f_exact(b0), fb1 = u2f_exact(b1), fb2 = u2f_exact(b2);
+                    if (prow)
                         v = (tlog(fa0) + tlog(fb0) - tlog(fa0 + fb0)) + (tlog(fa1) + tlog(fb1) - tlog(fa1 + fb1)) +
                             (tlog(fa2) + tlog(fb2) - tlog(fa2 + fb2));
-                    }
-                    v = seg_sum(v, pos, kPR);
+                    v = seg_sum<kPR>(v, pos);
                     const bool valid = prow && j < d.n && j > cpre;
                     if (P.dump && valid) {
+                        const uint32_t a0 = f2u_exact(fa0), a1 = f2u_exact(fa1), a2 = f2u_exact(fa2);
+                        const uint32_t b0 = f2u_exact(fb0), b1 = f2u_exact(fb1), b2 = f2u_exact(fb2);
                         uint64_t rs = 0;
-                        for (int t = 0; t < km1; t++) rs += binom_at(d.binom, d.n, d.n - 1 - psnp[t], K - t);
+#pragma unroll
+                        for (int tt = 0; tt < km1; tt++) rs += binom_at(d.binom, d.n, d.n - 1 - psnp[tt], K - tt);
                         rs += binom_at(d.binom, d.n, d.n - 1 - j, 1);
                         constexpr int cells = kPR * 3;
                         uint32_t *o = P.dump + (P.total - 1 - rs) * 2 * cells;
@@ -614,18 +721,18 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                     while (seg_mask) {
                         const int leader = __ffs(seg_mask) - 1;
                         seg_mask &= seg_mask - 1;
-                        // precise single-precision MI of that (prefix, j)
                         float e = 0.0f;
                         if (l / kPR == leader / kPR && lane_real)
-                            e = cell_terms_f32(a0, b0, mc) + cell_terms_f32(a1, b1, mc) + cell_terms_f32(a2, b2, mc);
-                        e = seg_sum(e, pos, kPR);
+                            e = row_terms_precise(f2u_exact(fa0), f2u_exact(fb0), f2u_exact(fa1), f2u_exact(fb1),
+                                                  f2u_exact(fa2), f2u_exact(fb2), mc);
+                        e = seg_sum<kPR>(e, pos);
                         if (l == leader) {
                             const float score = e * mc.inv_m;
                             if (score >= thr) {
-                                // lexicographic rank of (prefix, j)
                                 uint64_t rk_sum = 0;
-                                for (int t = 0; t < km1; t++)
-                                    rk_sum += binom_at(d.binom, d.n, d.n - 1 - psnp[t], K - t);
+#pragma unroll
+                                for (int tt = 0; tt < km1; tt++)
+                                    rk_sum += binom_at(d.binom, d.n, d.n - 1 - psnp[tt], K - tt);
                                 rk_sum += binom_at(d.binom, d.n, d.n - 1 - j, 1);
                                 const int slot = list_len + atomicAdd(&ES.nbuf, 1);
                                 sc[slot] = score;
@@ -634,7 +741,6 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                         }
                     }
                 }
-                // keep the buffer below its capacity: flush after any 16 last SNPs
                 epi_bar();
                 if (ES.nbuf > 16 * kPPT) epi_flush(ES, sc, rk, P.pool, P.global_thr, tid);
             }
@@ -652,16 +758,17 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
         epi_bar();
         if (ES.nbuf > 0) epi_flush(ES, sc, rk, P.pool, P.global_thr, tid);
         const int L = ES.list_len;
-        for (int q = tid; q < L; q += 128) {
+        for (int q = tid; q < L; q += kEpiThreads) {
             P.list_score[(size_t)blockIdx.x * P.pool + q] = sc[q];
             P.list_rank[(size_t)blockIdx.x * P.pool + q] = rk[q];
         }
         if (tid == 0) P.list_count[blockIdx.x] = L;
+        if (P.waits && tid == 0) P.waits[blockIdx.x * kWaitSlots + 5] = (unsigned long long)w_epi;
     }
 
     tc_fence_before();
     __syncthreads();
-    if (warp == 9) {
+    if (warp == kWarpMma) {
         __syncwarp();
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(512) : "memory");
@@ -701,10 +808,13 @@ __global__ void __launch_bounds__(1024) item_cum_kernel(DevData d, int k, int pp
     if (threadIdx.x == 1023) cum[n] = part[1023];
 }
 
-// B operand: row 2j+g (g = 0, 1) holds individual s of SNP j as byte s,
-// E4M3 1.0 (0x38) where the genotype is g, else 0.
+// B operand: row 2j+g (g = 0, 1) of SNP j, K byte 32 w + 4 i + b = individual
+// 32 w + 8 b + i (the A producer's order); where the genotype is g the byte
+// is 2^-5 divided by A's weight at that position, else 0.
 __global__ void build_b8_kernel(DevData d, unsigned char *__restrict__ b8)
 {
+    // E4M3 bytes of B by bit position i: 1.0, 2^-2, 2^-6, 2^1 (A: 2^-5, 2^-3, 2^1, 2^-6)
+    const uint32_t bval[8] = {0x38u, 0x28u, 0x08u, 0x40u, 0x38u, 0x28u, 0x08u, 0x40u};
     const int64_t Kt = (int64_t)d.Wt * 32;
     const int64_t per_row = Kt / 16;
     const int64_t total = 2 * d.n * per_row;
@@ -715,14 +825,11 @@ __global__ void build_b8_kernel(DevData d, unsigned char *__restrict__ b8)
         const int64_t j = row >> 1;
         const int g = (int)(row & 1);
         const uint32_t word = d.masks[(j * 3 + g) * d.Wt + (q >> 1)];
-        const uint32_t h = (word >> ((q & 1) * 16)) & 0xFFFFu;
-        uint4 o;
-        o.x = ((h & 0xFu) * 0x00204081u) & 0x01010101u;
-        o.y = (((h >> 4) & 0xFu) * 0x00204081u) & 0x01010101u;
-        o.z = (((h >> 8) & 0xFu) * 0x00204081u) & 0x01010101u;
-        o.w = (((h >> 12) & 0xFu) * 0x00204081u) & 0x01010101u;
-        o.x *= 0x38u; o.y *= 0x38u; o.z *= 0x38u; o.w *= 0x38u;
-        reinterpret_cast<uint4 *>(b8)[idx] = o;
+        const int i0 = (int)(q & 1) * 4;
+        uint32_t o[4];
+#pragma unroll
+        for (int t = 0; t < 4; t++) o[t] = ((word >> (i0 + t)) & 0x01010101u) * bval[i0 + t];
+        reinterpret_cast<uint4 *>(b8)[idx] = make_uint4(o[0], o[1], o[2], o[3]);
     }
 }
 
@@ -777,14 +884,14 @@ int tc_prefixes_per_warp(int k)
 
 size_t tc_smem_bytes(int cand_p2)
 {
-    return 1024 + (size_t)tc::kStages * tc::kStageBytes + (size_t)cand_p2 * 12 + 2 * 128 * 2 * 4 +
+    return 1024 + (size_t)(tc::kStagesA + tc::kStagesB) * tc::kTileBytes + (size_t)cand_p2 * 12 + 2 * 128 * 4 * 4 +
            tc::kDescDepth * sizeof(tc::Desc) + 64;
 }
 
 cudaError_t launch_tc_search(const DevData &d, int k, const unsigned char *b8, uint64_t *item_cum, int pool,
                              uint32_t *global_thr, float *list_score, uint64_t *list_rank, int32_t *list_count,
                              int32_t *status, int grid, uint64_t total, cudaStream_t st, int *cand_p2_out,
-                             uint32_t *dump)
+                             uint32_t *dump, unsigned long long *waits)
 {
     cudaError_t e = get_encode();
     if (e != cudaSuccess) return e;
@@ -826,6 +933,7 @@ cudaError_t launch_tc_search(const DevData &d, int k, const unsigned char *b8, u
     P.list_count = list_count;
     P.status = status;
     P.dump = dump;
+    P.waits = waits;
 
     CUtensorMap map;
     cuuint64_t gdim[2] = {(cuuint64_t)Kt, (cuuint64_t)(2 * d.n)};

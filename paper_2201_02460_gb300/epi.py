@@ -106,6 +106,8 @@ def load(path: str | None = None):
         lib.epi_profile_begin.argtypes = [V]
         lib.epi_profile_end.restype = i32
         lib.epi_profile_end.argtypes = [V, P, P]
+        lib.epi_profile_waits.restype = i32
+        lib.epi_profile_waits.argtypes = [V, P]
         if path is None:
             _lib = lib
         return lib
@@ -161,6 +163,14 @@ class Context:
         n = C.c_int64(0)
         _check(load().epi_profile_end(self._h, C.byref(ms), C.byref(n)))
         return ms.value, n.value
+
+    def profile_waits(self) -> dict:
+        """Per-role wait cycles of the last profiled tensor-core search."""
+        out = np.zeros(8, dtype=np.float64)
+        _check(load().epi_profile_waits(self._h, _np_ptr(out)))
+        names = ["mma_wait_a", "mma_wait_b", "mma_wait_acc", "prod_wait_stage", "unused4", "epi_wait_acc",
+                 "tma_wait_stage", "mma_loop"]
+        return {k: float(v) for k, v in zip(names, out)}
 
     def close(self):
         if getattr(self, "_h", None):
