@@ -1,15 +1,18 @@
 """Benchmark of the exhaustive k-SNP MI search on one GB300.
 
 One step = one whole search (enumerate every combination, count its
-contingency table, score it, keep the exact top-N) over a resident dataset.
-Prints one JSON line.
+contingency table, score it, keep the exact top-N) over a dataset resident
+in HBM.  Prints one JSON line.
 
-    python bench.py [--steps K] [--warmup W] [--workload NAME] [--path popc|tc|auto]
+    python bench.py [--steps K] [--warmup W] [--workload NAME] [--path auto|tc|popc]
     python bench.py --impl reference ...   # the CPU oracle on the host cores
 
-Under torchrun with N > 1 each rank runs the same search on its own GPU
-(independent replicas, weak scaling); the reported value sums the ranks' work
-over the slowest rank's time.
+The main figure is the order-3 workload (2000 SNPs x 4000 samples) on the
+fastest exact counting path (tensor cores); the popcount path and the order-4
+workload (500 SNPs x 8192 samples) are measured beside it.  Under torchrun
+with N > 1 each rank runs the same search on its own GPU (independent
+replicas, weak scaling); the reported value sums the ranks' work over the
+slowest rank's time.
 """
 from __future__ import annotations
 
@@ -29,9 +32,13 @@ sys.path.insert(0, ROOT)
 METRIC = "combination-samples/sec at orders 2-4 (INT8-TC vs popcount path); top-N recall at k=5"
 UNIT = "combination-samples/s"
 DEFAULT_WORKLOAD = "order3_2000snp_4000"
-POPC_PER_SM_CLK = 16          # 32-bit POPC results per SM per clock (integer pipe)
+# integer-pipe roofline of the popcount path: POPC executes on the XU pipe,
+# 16 results per SM per clock (measured: 15.1/clk/SM), 152 SMs, 2070 MHz max
+POPC_PER_SM_CLK = 16
 N_SMS = 152
 SM_MAX_MHZ = 2070.0
+# FP8 dense rate = 2 x BF16 dense (nominal 4.5 vs 2.25 PFLOP/s)
+FP8_OVER_BF16 = 2.0
 
 
 def _env_int(name, default):
@@ -39,6 +46,17 @@ def _env_int(name, default):
         return int(os.environ.get(name, default))
     except ValueError:
         return default
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return dict(bf16=p["bf16_tflops"], bf16_sustained=p.get("bf16_tflops_sustained", p["bf16_tflops"]),
+                    hbm=p["hbm_gbs"], source="measured")
+    except (OSError, KeyError, ValueError):
+        return dict(bf16=1900.0, bf16_sustained=1700.0, hbm=6800.0, source="fallback")
 
 
 def workload_desc(name, d, k, top_n):
@@ -105,41 +123,40 @@ class ClockSampler:
         return out
 
 
-def cpu_baseline(d, k, target_s=15.0):
-    """The oracle, as it stands, on a bounded rank range of the same workload."""
+
+def oracle_range_rate(d, k, top_n, target_s):
+    """Time the oracle, as it stands, on a rank range sized to ~target_s."""
     from oracle import oracle as O
     total = O.binom(d.n_snps, k)
-    threads = O.max_threads()
     r = min(total, 20000)
     t0 = time.perf_counter()
-    O.search(d.geno, d.pheno, k, 100, rank_begin=0, rank_end=r, with_counts=False)
+    O.search(d.geno, d.pheno, k, top_n, rank_begin=0, rank_end=r, with_counts=False)
     dt = time.perf_counter() - t0
     if dt < target_s / 4 and r < total:
         r = min(total, int(r * target_s / max(dt, 1e-3)))
         t0 = time.perf_counter()
-        O.search(d.geno, d.pheno, k, 100, rank_begin=0, rank_end=r, with_counts=False)
+        O.search(d.geno, d.pheno, k, top_n, rank_begin=0, rank_end=r, with_counts=False)
         dt = time.perf_counter() - t0
-    return dict(value=r * d.n_samples / dt, unit=UNIT, cores=threads, kind="oracle",
-                sample=f"lexicographic ranks [0, {r}) of the {total} combinations, {dt:.1f} s",
-                seconds=dt)
+    return r, dt, total
+
+
+def cpu_baseline(d, k, top_n, target_s=15.0):
+    from oracle import oracle as O
+    r, dt, total = oracle_range_rate(d, k, top_n, target_s)
+    return dict(value=r * d.n_samples / dt, unit=UNIT, cores=O.max_threads(), kind="oracle",
+                sample=f"lexicographic ranks [0, {r}) of the {total} combinations ({dt:.1f} s)")
 
 
 def run_reference(args):
     """Reference arm: the CPU oracle timed on this host's cores."""
-    rank = _env_int("RANK", 0)
-    if rank != 0:
+    if _env_int("RANK", 0) != 0:
         return 0
     from oracle import oracle as O
     from paper_2201_02460_gb300 import synth
     d, k, top_n = synth.make_workload(args.workload)
     total = O.binom(d.n_snps, k)
     threads = O.max_threads()
-    # size each step to about 10 s of CPU work
-    r = min(total, 20000)
-    t0 = time.perf_counter()
-    O.search(d.geno, d.pheno, k, top_n, rank_begin=0, rank_end=r, with_counts=False)
-    dt = time.perf_counter() - t0
-    r = min(total, max(r, int(r * 10.0 / max(dt, 1e-3))))
+    r, dt, _ = oracle_range_rate(d, k, top_n, 10.0)
     for _ in range(args.warmup):
         O.search(d.geno, d.pheno, k, top_n, rank_begin=0, rank_end=min(total, r // 10 + 1), with_counts=False)
     times = []
@@ -152,7 +169,7 @@ def run_reference(args):
     value = args.steps * r * d.n_samples / t
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
                 ms_per_step=1e3 * t / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
-                dtype="u32", data="synthetic", impl="reference",
+                dtype="f64", data="synthetic", impl="reference",
                 config=workload_desc(args.workload, d, k, top_n),
                 cpu_baseline=dict(value=value, unit=UNIT, cores=threads, kind="oracle",
                                   sample=f"each step: {r} consecutive lexicographic ranks of {total}"),
@@ -161,8 +178,52 @@ def run_reference(args):
     return 0
 
 
+def time_search(epi, ctx, ds, k, top_n, path, steps, warmup, flush, stream):
+    """Device time of `steps` searches (L2 flushed between them, not timed),
+    the counting kernel's own event time, and the library's launches."""
+    import torch
+    for _ in range(warmup):
+        epi.search(ds, k, top_n, path=path)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    launches0 = ctx.kernel_launches()
+    ctx.profile_begin()
+    res = None
+    for s in range(steps):
+        flush.fill_(s & 0xFF)
+        ev[s][0].record(stream)
+        res = epi.search(ds, k, top_n, path=path)
+        ev[s][1].record(stream)
+    torch.cuda.synchronize()
+    waits = ctx.profile_waits()
+    kern_ms, kern_n = ctx.profile_end()
+    t_ms = sum(a.elapsed_time(b) for a, b in ev)
+    return dict(t_ms=t_ms, kern_ms=kern_ms / max(kern_n, 1), launches=ctx.kernel_launches() - launches0,
+                res=res, waits=waits)
+
+
+def roofline(kind, d, k, kern_ms, peaks):
+    total = math.comb(d.n_snps, k)
+    if kind == "tc":
+        # algorithmic work: 3^k cells x m individuals multiply-adds per combination
+        flops = 2.0 * total * (3 ** k) * d.n_samples
+        achieved = flops / (kern_ms / 1e3) / 1e12
+        peak = FP8_OVER_BF16 * peaks["bf16_sustained"]
+        return dict(bound="tensor", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
+                    traffic=None, kernel="tc_search_kernel", kernel_ms=kern_ms,
+                    note=f"FP8 (E4M3) dense = 2 x {peaks['source']} sustained BF16 "
+                         f"{peaks['bf16_sustained']} TFLOP/s; work 2*3^k*m flop per combination")
+    W = ((d.n_cases + 127) // 128 + (d.n_samples - d.n_cases + 127) // 128) * 4
+    ops = total * (3 ** k) * W
+    achieved = ops / (kern_ms / 1e3) / 1e12
+    peak = N_SMS * POPC_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
+    return dict(bound="alu", achieved=achieved, peak=peak, unit="Tops/s", frac=achieved / peak, traffic=None,
+                kernel="popc_search_kernel", kernel_ms=kern_ms,
+                note="32-bit AND+POPC word operations, 3^k cells x (W1+W0) words per combination; "
+                     "peak = 152 SMs x 16 POPC/clk x 2070 MHz")
+
+
 def run_ours(args):
-    import numpy as np
     import torch
 
     rank = _env_int("RANK", 0)
@@ -177,6 +238,7 @@ def run_ours(args):
     B.build()
     from paper_2201_02460_gb300 import epi, synth
 
+    peaks = measured_peaks()
     over = {"n_snps": args.n_snps} if args.n_snps else {}
     d, k, top_n = synth.make_workload(args.workload, **over)
     ctx = epi.Context(local)
@@ -185,76 +247,75 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     total = math.comb(d.n_snps, k)
     units = total * d.n_samples
+    path = args.path
+    tc_ok = 2 <= k <= 4 and 0 < d.n_cases < d.n_samples
+    kind = "tc" if (path == "tc" or (path == "auto" and tc_ok and k >= 3)) else "popc"
 
-    for _ in range(args.warmup):
-        epi.search(ds, k, top_n, path=args.path)
-    torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    launches0 = ctx.kernel_launches()
-    ctx.profile_begin()
     with ClockSampler(local) as clk:
-        torch.cuda.synchronize()
-        for s in range(args.steps):
-            flush.fill_(s & 0xFF)            # evict the L2 between steps (not timed)
-            ev[s][0].record(stream)
-            res = epi.search(ds, k, top_n, path=args.path)
-            ev[s][1].record(stream)
-        torch.cuda.synchronize()
-    waits = ctx.profile_waits() if args.path != "popc" else None
-    kern_ms, kern_n = ctx.profile_end()
-    launches = ctx.kernel_launches() - launches0
-    t_ms = sum(a.elapsed_time(b) for a, b in ev)
+        main_m = time_search(epi, ctx, ds, k, top_n, path, args.steps, args.warmup, flush, stream)
+    clocks = clk.summary()
+    t_ms = main_m["t_ms"]
     if world > 1:
         tt = torch.tensor([t_ms], dtype=torch.float64)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_ms = float(tt.item())
     value = world * units * args.steps / (t_ms / 1e3)
+    res = main_m["res"]
 
-    # end to end: host genotypes in, host results out, through the C-ABI
+    # end to end through the C-ABI: host genotypes in, host records out
     e2e_times = []
-    for s in range(max(1, min(args.steps, 3))):
+    for _ in range(max(1, min(args.steps, 3))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ds2 = epi.Dataset(ctx, d.geno, d.pheno)
-        epi.search(ds2, k, top_n, path=args.path)
+        epi.search(ds2, k, top_n, path=path)
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t0)
         ds2.close()
     e2e_t = statistics.median(e2e_times)
-    h2d = int(d.geno.nbytes + d.pheno.nbytes)
-    d2h = int(top_n * epi.RESULT_DTYPE.itemsize + top_n * 2 * 3 ** k * 4)
-
-    clocks = clk.summary()
-    # roofline of the counting kernel: algorithmic 32-bit AND+POPC word
-    # operations = C(n,k) * 3^k cells * (W1 + W0) words per launch
-    W = ((d.n_cases + 127) // 128 + (d.n_samples - d.n_cases + 127) // 128) * 4
-    alg_ops = total * (3 ** k) * W
-    kern_avg_s = (kern_ms / max(kern_n, 1)) / 1e3
-    achieved = alg_ops / kern_avg_s / 1e12
-    peak = N_SMS * POPC_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
-    roof = dict(bound="alu", achieved=achieved, peak=peak, unit="Tops/s", frac=achieved / peak, traffic=None,
-                kernel="popc_search_kernel", kernel_ms=kern_avg_s * 1e3,
-                ops_note="paper work: 3^k cells x (W1+W0) 32-bit AND+POPC per combination; "
-                         "peak = 152 SMs x 16 POPC/clk x 2070 MHz")
 
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=t_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
-                dtype="u32", data="synthetic",
-                config=dict(**workload_desc(args.workload, d, k, top_n), path=args.path,
+                dtype="f8e4m3 0/1 operands, f32 accumulate" if kind == "tc" else "u32",
+                data="synthetic",
+                config=dict(**workload_desc(args.workload, d, k, top_n), path=path, counting=kind,
                             l2="flushed between steps (256 MiB write)", parallelism="replicas"),
-                e2e=dict(value=units / e2e_t, unit=UNIT, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h,
+                e2e=dict(value=units / e2e_t, unit=UNIT, h2d_bytes_per_step=int(d.geno.nbytes + d.pheno.nbytes),
+                         d2h_bytes_per_step=int(top_n * epi.RESULT_DTYPE.itemsize + top_n * 2 * 3 ** k * 4),
                          seconds=e2e_t),
-                roofline=roof, gpu_launches=int(launches), clocks=clocks,
+                roofline=roofline(kind, d, k, main_m["kern_ms"], peaks),
+                gpu_launches=int(main_m["launches"]), clocks=clocks,
                 top1=dict(snps=[int(x) for x in res.combs[0]], mi=float(res.mi[0]), planted=list(d.planted)))
-    if waits and waits.get("mma_loop"):
-        line["tc_wait_fractions"] = {k: round(v / waits["mma_loop"], 4) for k, v in waits.items() if k != "unused4"}
+    if kind == "tc" and main_m["waits"].get("mma_loop"):
+        w = main_m["waits"]
+        line["tc_wait_fractions"] = {k2: round(v / w["mma_loop"], 4) for k2, v in w.items() if k2 != "unused4"}
+
+    # the other counting path and the order-4 workload, measured beside it
+    if not args.no_compare and world == 1:
+        comp = {}
+        other = "popc" if kind == "tc" else ("tc" if tc_ok else None)
+        if other:
+            m2 = time_search(epi, ctx, ds, k, top_n, other, 2, 1, flush, stream)
+            comp[f"{args.workload}/{other}"] = dict(value=units / (m2["t_ms"] / 2 / 1e3), ms_per_step=m2["t_ms"] / 2,
+                                                     roofline=roofline(other, d, k, m2["kern_ms"], peaks))
+        if args.workload != "order4_500snp_8192":
+            d4, k4, n4 = synth.make_workload("order4_500snp_8192")
+            ds4 = epi.Dataset(ctx, d4.geno, d4.pheno)
+            u4 = math.comb(d4.n_snps, k4) * d4.n_samples
+            m4 = time_search(epi, ctx, ds4, k4, n4, "tc", 2, 1, flush, stream)
+            comp["order4_500snp_8192/tc"] = dict(value=u4 / (m4["t_ms"] / 2 / 1e3), ms_per_step=m4["t_ms"] / 2,
+                                                 roofline=roofline("tc", d4, k4, m4["kern_ms"], peaks))
+            if args.full_compare:
+                p4 = time_search(epi, ctx, ds4, k4, n4, "popc", 1, 0, flush, stream)
+                comp["order4_500snp_8192/popc"] = dict(value=u4 / (p4["t_ms"] / 1e3), ms_per_step=p4["t_ms"],
+                                                       roofline=roofline("popc", d4, k4, p4["kern_ms"], peaks))
+            ds4.close()
+        line["compare"] = comp
+
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb = cpu_baseline(d, k)
-        cb.pop("seconds", None)
-        line["cpu_baseline"] = cb
+        line["cpu_baseline"] = cpu_baseline(d, k, top_n)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -270,8 +331,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
-    ap.add_argument("--path", default="popc", choices=["popc", "tc", "auto"])
+    ap.add_argument("--path", default="auto", choices=["popc", "tc", "auto"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip the other path and the order-4 workload")
+    ap.add_argument("--full-compare", action="store_true", help="also time the order-4 popcount path (~26 s)")
     ap.add_argument("--n-snps", type=int, default=None, help="smaller SNP count (profiling captures)")
     args = ap.parse_args()
     if args.impl == "reference":
