@@ -17,6 +17,7 @@ slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import faulthandler
 import json
 import math
 import os
@@ -132,7 +133,9 @@ def oracle_range_rate(d, k, top_n, target_s):
     t0 = time.perf_counter()
     O.search(d.geno, d.pheno, k, top_n, rank_begin=0, rank_end=r, with_counts=False)
     dt = time.perf_counter() - t0
-    if dt < target_s / 4 and r < total:
+    for _ in range(3):            # grow the range until it takes about target_s
+        if dt >= target_s / 2 or r >= total:
+            break
         r = min(total, int(r * target_s / max(dt, 1e-3)))
         t0 = time.perf_counter()
         O.search(d.geno, d.pheno, k, top_n, rank_begin=0, rank_end=r, with_counts=False)
@@ -325,6 +328,7 @@ def run_ours(args):
 
 
 def main():
+    faulthandler.enable()
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)

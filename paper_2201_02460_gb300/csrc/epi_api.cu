@@ -24,8 +24,8 @@ struct epi_ctx {
     bool profiling = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
     int64_t live_datasets = 0;     // datasets created on this context and not yet destroyed
-    unsigned long long *waits_dev = nullptr;   // per-role wait cycles of the last profiled TC search
-    int waits_grid = 0;
+    unsigned long long *waits_dev = nullptr;   // own buffer: per-role wait cycles of a profiled TC search
+    int waits_grid = 0;                        // CTAs recorded in waits_dev (0: nothing recorded)
     bool destroy_requested = false;
 };
 
@@ -240,7 +240,6 @@ epi_status queue_search(epi_dataset *ds, const SearchPlan &p, int path, epi_resu
     const size_t o_mi = a.take<double>((size_t)p.pool);
     const size_t o_cb = a.take<int32_t>((size_t)p.pool * p.k);
     const size_t o_ic = a.take<uint64_t>((size_t)ds->n + 1);
-    const size_t o_wt = a.take<unsigned long long>((size_t)p.grid * kTcWaitSlots);
     epi_status st = ensure_scratch(ctx, a.off);
     if (st != EPI_OK) return st;
     char *base = static_cast<char *>(ctx->scratch);
@@ -256,7 +255,6 @@ epi_status queue_search(epi_dataset *ds, const SearchPlan &p, int path, epi_resu
     double *mi = reinterpret_cast<double *>(base + o_mi);
     int32_t *cb = reinterpret_cast<int32_t *>(base + o_cb);
     uint64_t *ic = reinterpret_cast<uint64_t *>(base + o_ic);
-    unsigned long long *wt = reinterpret_cast<unsigned long long *>(base + o_wt);
     if (p.tc) {
         st = ensure_b8(ds);
         if (st != EPI_OK) return st;
@@ -275,9 +273,10 @@ epi_status queue_search(epi_dataset *ds, const SearchPlan &p, int path, epi_resu
         int cand_p2 = 0;
         unsigned long long *waits = nullptr;
         if (ctx->profiling) {
-            CK(cudaMemsetAsync(wt, 0, (size_t)p.grid * kTcWaitSlots * 8, ctx->stream));
-            waits = wt;
-            ctx->waits_dev = wt;
+            if (!ctx->waits_dev)
+                CK(cudaMalloc((void **)&ctx->waits_dev, (size_t)ctx->num_sms * kTcWaitSlots * 8));
+            CK(cudaMemsetAsync(ctx->waits_dev, 0, (size_t)p.grid * kTcWaitSlots * 8, ctx->stream));
+            waits = ctx->waits_dev;
             ctx->waits_grid = p.grid;
         }
         CK(launch_tc_search(d, p.k, ds->b8, ic, p.pool, thr, ls, lr, lc, status, p.grid, p.total, ctx->stream,
@@ -413,6 +412,7 @@ static void free_ctx(epi_ctx *ctx)
         cudaFree(ctx->scratch);
     }
     for (auto &pr : ctx->prof_events) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
+    if (ctx->waits_dev) cudaFree(ctx->waits_dev);
     delete ctx;
 }
 
@@ -680,6 +680,7 @@ epi_status epi_profile_begin(epi_ctx *ctx)
     for (auto &pr : ctx->prof_events) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
     ctx->prof_events.clear();
     ctx->profiling = true;
+    ctx->waits_grid = 0;
     return EPI_OK;
 }
 

@@ -274,3 +274,17 @@ def test_tc_unsupported_cases(epi, ctx):
     # auto falls back to the popcount path for a range
     r = epi.search(ds, 3, 10, path="auto", rank_range=(0, 100))
     assert len(r) == 10
+
+
+def test_profile_trace_survives_scratch_growth(epi, ctx):
+    """The wait trace of a tensor-core search stays readable after a later
+    search grew the context's scratch memory."""
+    geno, pheno = random_data(120, 1500, seed=8)
+    ds = epi.Dataset(ctx, geno, pheno)
+    ctx.profile_begin()
+    epi.search(ds, 3, 50, path="tc")
+    epi.search(ds, 3, 1000, path="popc")      # larger candidate lists
+    w = ctx.profile_waits()
+    ms, n = ctx.profile_end()
+    assert n == 2 and ms > 0
+    assert w["mma_loop"] > 0
