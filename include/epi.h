@@ -150,6 +150,38 @@ uint64_t epi_kernel_launches(const epi_ctx *ctx);
  * epi_tables (Section 2.2) when the path is exact. */
 epi_status epi_debug_counts(epi_dataset *ds, int order, uint32_t *out);
 
+/* Allocation-free search, for callers that cannot allocate device memory
+ * (for example a plug-in inside a host framework that owns all device
+ * allocations, or code with a fixed memory budget).  The paper has no
+ * counterpart: this is the popcount-path search of epi_search with every
+ * intermediate buffer (genotype tables, candidate lists, recount tables) in
+ * one 64 MiB array that the library holds in device memory for the life of
+ * the process, on every GPU that loads it.  The call performs no cudaMalloc,
+ * cudaFree or other allocating call.
+ *
+ * Inputs, all device memory of the current device: geno [n_snps][n_samples]
+ * uint8 in {0,1,2}, pheno [n_samples] uint8 in {0,1}; n_cases must equal the
+ * number of ones in pheno.  Outputs, device memory: out_dev [top_n] records,
+ * counts_dev [top_n][2][3^order] (may be NULL), n_out_dev one int32,
+ * status_dev one int32 that receives EPI_OK, EPI_EINVAL (invalid genotype or
+ * phenotype values, or n_cases that does not match), or EPI_EOVERFLOW (the
+ * candidate pool could not prove the exact top N; epi_search retries in that
+ * case, this call does not).  Work is queued on cuda_stream and the call
+ * returns without waiting.  order in 1..5, top_n in 1..1024.  A dataset whose
+ * buffers exceed the 64 MiB array fails with EPI_EINVAL before any work is
+ * queued (the genotype tables take about n_snps * 3 * 2 * ceil(n_samples/128)
+ * * 16 bytes).
+ *
+ * The first call on each device resolves the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call uses the same array and leaves its contents behind; calls whose
+ * work overlaps on the GPU (other streams, other host threads) race on it and
+ * must be serialised by the caller. */
+epi_status epi_search_static(const uint8_t *geno_dev, const uint8_t *pheno_dev, int64_t n_snps,
+                             int64_t n_samples, int64_t n_cases, int order, int top_n,
+                             epi_result *out_dev, uint32_t *counts_dev, int32_t *n_out_dev,
+                             int32_t *status_dev, void *cuda_stream);
+
 /* Timing of the dominant counting kernel.  After epi_profile_begin, every
  * launch of a search's counting kernel is bracketed by CUDA events on the
  * context's stream; epi_profile_end waits for those events and returns their

@@ -378,6 +378,10 @@ epi_status run_search_sync(epi_dataset *ds, int order, int top_n, int path, uint
 
 }  // namespace
 
+namespace epi {
+void set_last_error(const char *msg) { g_err = msg; }
+}  // namespace epi
+
 extern "C" {
 
 const char *epi_last_error(void) { return g_err.c_str(); }
