@@ -126,6 +126,20 @@ epi_status epi_search_async(epi_dataset *ds, int order, int top_n, int path,
                             epi_result *out_dev, uint32_t *counts_dev, int32_t *n_out_dev,
                             int32_t *status_dev);
 
+/* Many independent searches at once (one per dataset, Algorithm 1 each):
+ * datasets of the same order and counting path share one persistent launch
+ * whose CTAs are split among them in proportion to their work, and the whole
+ * batch (counting launches, per-dataset merge, re-score and selection, and
+ * the copies back) is captured once into a CUDA graph that later calls with
+ * the same datasets, orders and top_n replay.  ds[i] must belong to ctx;
+ * orders[i] in 1..5, top_ns[i] in 1..1024; outs[i] host arrays of top_ns[i]
+ * records; counts NULL or counts[i] NULL or a host array [top_ns[i]][2][3^k];
+ * n_outs[i] receives the record count.  Same results as epi_search on each
+ * dataset.  Destroying a dataset invalidates the cached graph. */
+epi_status epi_search_batched(epi_ctx *ctx, epi_dataset *const *ds, const int *orders, const int *top_ns,
+                              int n_ds, int path, epi_result *const *outs, uint32_t *const *counts,
+                              int *n_outs);
+
 /* Contingency tables (Section 2.2) of `count` given combinations.  combs:
  * host [count][order] uint32, each strictly increasing and < n_snps;
  * out: host [count][2][3^order].  order in 1..8. */

@@ -24,6 +24,15 @@ struct epi_ctx {
     bool profiling = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
     int64_t live_datasets = 0;     // datasets created on this context and not yet destroyed
+    // batched searches: device arena, pinned staging, one cached graph
+    void *batch_dev = nullptr;
+    size_t batch_dev_bytes = 0;
+    void *batch_host = nullptr;
+    size_t batch_host_bytes = 0;
+    cudaStream_t capture_stream = nullptr;
+    cudaGraphExec_t batch_exec = nullptr;
+    std::vector<uint64_t> batch_key;
+    uint64_t next_dataset_id = 1;
     unsigned long long *waits_dev = nullptr;   // own buffer: per-role wait cycles of a profiled TC search
     int waits_grid = 0;                        // CTAs recorded in waits_dev (0: nothing recorded)
     bool destroy_requested = false;
@@ -31,6 +40,7 @@ struct epi_ctx {
 
 struct epi_dataset {
     epi_ctx *ctx = nullptr;
+    uint64_t id = 0;               // unique within the context (keys cached batch graphs)
     int64_t n = 0, m = 0, m1 = 0, m0 = 0;
     int32_t W1 = 0, W0 = 0, Wt = 0;
     uint32_t *masks = nullptr;
@@ -382,6 +392,335 @@ namespace epi {
 void set_last_error(const char *msg) { g_err = msg; }
 }  // namespace epi
 
+
+namespace {
+
+// One dataset of a batched search and where its buffers live.
+struct BatchItem {
+    epi_dataset *ds = nullptr;
+    int k = 0, top_n = 0, pool = 0, cells = 0;
+    bool tc = false;
+    uint64_t total = 0;
+    double cost = 0;
+    int group = -1, cta_begin = 0, cta_count = 0;
+    // device offsets in the batch arena
+    size_t o_thr = 0, o_status = 0, o_code = 0, o_nout = 0, o_cs = 0, o_cr = 0, o_cn = 0, o_ct = 0, o_mi = 0,
+           o_cb = 0, o_ic = 0, o_rec = 0, o_cnt = 0, o_ls = 0, o_lr = 0, o_lc = 0;
+    // pinned host offsets of the copied-back results
+    size_t h_rec = 0, h_cnt = 0, h_nout = 0, h_code = 0;
+};
+
+struct BatchGroup {
+    bool tc = false;
+    int k = 0, R = 0, tile = 0, slots = 0, cand_p2 = 0, pool = 0, max_wt = 0, grid = 0;
+    size_t smem = 0;
+    std::vector<int> items;
+    size_t o_desc = 0, o_tmap = 0, o_ctads = 0, o_ls = 0, o_lr = 0, o_lc = 0;
+};
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) & ~(a - 1); }
+
+// Popcount launch shape for a group: residency first, then staged prefixes.
+bool plan_group_popc(const epi_ctx *ctx, BatchGroup &g)
+{
+    const size_t limit = ctx->smem_optin ? ctx->smem_optin : 227 * 1024;
+    g.R = popc_default_row_group(g.k);
+    int best = -1;
+    for (int tile : {512, 256}) {
+        const int cp2 = next_pow2(g.pool + 2 * tile);
+        for (int sl = 8; sl >= 1; sl--) {
+            const size_t sm = popc_smem_bytes(g.k, g.max_wt, sl, cp2) + 1024;
+            if (sm > limit) continue;
+            const int occ = popc_max_active(g.k, g.R, sm);
+            if (occ <= 0) continue;
+            const int score = std::min(occ, 8) * 1000 + sl * 10 + (tile == 512);
+            if (score > best) { best = score; g.tile = tile; g.cand_p2 = cp2; g.slots = sl; g.smem = sm; g.grid = occ; }
+        }
+    }
+    if (best < 0) return false;
+    g.grid *= ctx->num_sms;
+    return true;
+}
+
+// CTAs of a group's grid spread over its datasets in proportion to work.
+void split_ctas(BatchGroup &g, std::vector<BatchItem> &items)
+{
+    const int n = (int)g.items.size();
+    if (g.grid < n) g.grid = n;
+    double total = 0;
+    for (int i : g.items) total += items[i].cost;
+    int used = 0;
+    std::vector<double> frac(n);
+    for (int q = 0; q < n; q++) {
+        BatchItem &it = items[g.items[q]];
+        const double share = total > 0 ? it.cost / total * (double)(g.grid - n) : 0.0;
+        it.cta_count = 1 + (int)share;
+        frac[q] = share - (double)(int)share;
+        used += it.cta_count;
+    }
+    // hand out the remainder by largest fractional share
+    std::vector<int> order(n);
+    for (int q = 0; q < n; q++) order[q] = q;
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return frac[a] > frac[b]; });
+    for (int q = 0; used < g.grid; q = (q + 1) % n, used++) items[g.items[order[q]]].cta_count++;
+    int at = 0;
+    for (int q = 0; q < n; q++) {
+        BatchItem &it = items[g.items[q]];
+        it.cta_begin = at;
+        at += it.cta_count;
+    }
+}
+
+epi_status ensure_batch_buffers(epi_ctx *ctx, size_t dev_bytes, size_t host_bytes)
+{
+    if (ctx->batch_dev_bytes < dev_bytes || ctx->batch_host_bytes < host_bytes) {
+        if (ctx->batch_exec) { cudaGraphExecDestroy(ctx->batch_exec); ctx->batch_exec = nullptr; }
+        ctx->batch_key.clear();
+    }
+    if (ctx->batch_dev_bytes < dev_bytes) {
+        cudaStreamSynchronize(ctx->stream);
+        if (ctx->batch_dev) cudaFree(ctx->batch_dev);
+        ctx->batch_dev = nullptr;
+        ctx->batch_dev_bytes = 0;
+        CK(cudaMalloc(&ctx->batch_dev, dev_bytes));
+        ctx->batch_dev_bytes = dev_bytes;
+    }
+    if (ctx->batch_host_bytes < host_bytes) {
+        cudaStreamSynchronize(ctx->stream);
+        if (ctx->batch_host) cudaFreeHost(ctx->batch_host);
+        ctx->batch_host = nullptr;
+        ctx->batch_host_bytes = 0;
+        CK(cudaMallocHost(&ctx->batch_host, host_bytes));
+        ctx->batch_host_bytes = host_bytes;
+    }
+    if (!ctx->capture_stream) CK(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
+    return EPI_OK;
+}
+
+// Records every step of the batched search on `st` (captured into a graph).
+epi_status record_batch(epi_ctx *ctx, std::vector<BatchItem> &items, std::vector<BatchGroup> &groups, cudaStream_t st)
+{
+    char *dev = static_cast<char *>(ctx->batch_dev);
+    char *host = static_cast<char *>(ctx->batch_host);
+    // thresholds and status words of all datasets sit in one block at offset 0
+    CK(cudaMemsetAsync(dev, 0, items.size() * 256, st));
+    for (auto &g : groups) {
+        if (g.tc)
+            for (int i : g.items) CK(launch_tc_item_cum(items[i].ds->dev(), g.k, reinterpret_cast<uint64_t *>(dev + items[i].o_ic), st));
+        float *ls = reinterpret_cast<float *>(dev + g.o_ls);
+        uint64_t *lr = reinterpret_cast<uint64_t *>(dev + g.o_lr);
+        int32_t *lc = reinterpret_cast<int32_t *>(dev + g.o_lc);
+        int32_t *ctads = reinterpret_cast<int32_t *>(dev + g.o_ctads);
+        // every CTA of a TC group reports a timeout through its dataset's status
+        if (g.tc)
+            CK(launch_tc_batch(dev + g.o_desc, ctads, g.k, g.pool, ls, lr, lc,
+                               reinterpret_cast<int32_t *>(dev + items[g.items[0]].o_status), g.grid, st));
+        else
+            CK(launch_popc_batch(dev + g.o_desc, ctads, g.k, g.R, g.max_wt, g.tile, g.pool, g.slots, g.cand_p2, ls, lr,
+                                 lc, g.grid, g.smem, st));
+        ctx->launches += 1;
+    }
+    for (auto &it : items) {
+        const BatchGroup &g = groups[it.group];
+        const DevData d = it.ds->dev();
+        float *ls = reinterpret_cast<float *>(dev + g.o_ls) + (size_t)it.cta_begin * g.pool;
+        uint64_t *lr = reinterpret_cast<uint64_t *>(dev + g.o_lr) + (size_t)it.cta_begin * g.pool;
+        int32_t *lc = reinterpret_cast<int32_t *>(dev + g.o_lc) + it.cta_begin;
+        float *cs = reinterpret_cast<float *>(dev + it.o_cs);
+        uint64_t *cr = reinterpret_cast<uint64_t *>(dev + it.o_cr);
+        int32_t *cn = reinterpret_cast<int32_t *>(dev + it.o_cn);
+        uint32_t *ct = reinterpret_cast<uint32_t *>(dev + it.o_ct);
+        double *mi = reinterpret_cast<double *>(dev + it.o_mi);
+        int32_t *cb = reinterpret_cast<int32_t *>(dev + it.o_cb);
+        uint32_t *thr = reinterpret_cast<uint32_t *>(dev + it.o_thr);
+        int32_t *status = reinterpret_cast<int32_t *>(dev + it.o_status);
+        epi_result *rec = reinterpret_cast<epi_result *>(dev + it.o_rec);
+        uint32_t *cnt = reinterpret_cast<uint32_t *>(dev + it.o_cnt);
+        int32_t *nout = reinterpret_cast<int32_t *>(dev + it.o_nout);
+        int32_t *code = reinterpret_cast<int32_t *>(dev + it.o_code);
+        CK(launch_merge(ls, lr, lc, it.cta_count, g.pool, it.pool, cs, cr, cn, st));
+        CK(launch_rescore(d, it.k, it.pool, cr, cn, ct, mi, cb, st));
+        CK(launch_finalize(d, it.k, it.top_n, it.pool, cs, cr, cn, mi, cb, ct, thr, it.total, rec, cnt, nout, status,
+                           st));
+        CK(launch_publish_status(status, code, st));
+        ctx->launches += 4;
+        CK(cudaMemcpyAsync(host + it.h_rec, rec, (size_t)it.top_n * sizeof(epi_result), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(host + it.h_cnt, cnt, (size_t)it.top_n * 2 * it.cells * 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(host + it.h_nout, nout, 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(host + it.h_code, code, 4, cudaMemcpyDeviceToHost, st));
+    }
+    return EPI_OK;
+}
+
+}  // namespace
+
+extern "C" epi_status epi_search_batched(epi_ctx *ctx, epi_dataset *const *dss, const int *orders, const int *top_ns,
+                                         int n_ds, int path, epi_result *const *outs, uint32_t *const *counts,
+                                         int *n_outs)
+{
+    if (!ctx || !dss || !orders || !top_ns || !outs || !n_outs) return fail(EPI_EINVAL, "NULL argument");
+    if (n_ds < 1 || n_ds > 4096) return fail(EPI_EINVAL, "n_ds %d outside 1..4096", n_ds);
+    std::vector<BatchItem> items((size_t)n_ds);
+    for (int i = 0; i < n_ds; i++) {
+        BatchItem &it = items[i];
+        it.ds = dss[i];
+        if (!it.ds || it.ds->ctx != ctx) return fail(EPI_EINVAL, "dataset %d is NULL or belongs to another context", i);
+        if (!outs[i]) return fail(EPI_EINVAL, "outs[%d] is NULL", i);
+        uint64_t re = UINT64_MAX, total = 0;
+        epi_status st = check_search_args(it.ds, orders[i], top_ns[i], path, 0, re, total);
+        if (st != EPI_OK) return fail(st, "dataset %d: %s", i, epi_last_error());
+        it.k = orders[i];
+        it.top_n = top_ns[i];
+        it.total = total;
+        it.pool = initial_pool(it.top_n);
+        it.cells = pow3i(it.k);
+        st = choose_path(it.ds, it.k, path, 0, total, total, it.tc);
+        if (st != EPI_OK) return fail(st, "dataset %d: %s", i, epi_last_error());
+        const DevData d = it.ds->dev();
+        it.cost = it.tc ? (double)tc_item_count(d.n, it.k) * (double)(d.Wt / 4)
+                        : (double)total * (double)(it.cells / 3) * (double)d.Wt;
+    }
+    DeviceGuard guard(ctx->device);
+    if (!guard.ok) return fail(EPI_ECUDA, "cannot select device %d", ctx->device);
+    // one group per (path, order)
+    std::vector<BatchGroup> groups;
+    for (int i = 0; i < n_ds; i++) {
+        int gi = -1;
+        for (size_t q = 0; q < groups.size(); q++)
+            if (groups[q].tc == items[i].tc && groups[q].k == items[i].k) gi = (int)q;
+        if (gi < 0) {
+            groups.emplace_back();
+            gi = (int)groups.size() - 1;
+            groups[gi].tc = items[i].tc;
+            groups[gi].k = items[i].k;
+        }
+        items[i].group = gi;
+        BatchGroup &g = groups[gi];
+        g.items.push_back(i);
+        g.pool = std::max(g.pool, items[i].pool);
+        g.max_wt = std::max(g.max_wt, items[i].ds->Wt);
+    }
+    for (auto &g : groups) {
+        if (g.tc) g.grid = ctx->num_sms;
+        else if (!plan_group_popc(ctx, g))
+            return fail(EPI_EUNSUPPORTED, "order %d: a prefix table of the largest dataset does not fit in shared memory", g.k);
+        split_ctas(g, items);
+    }
+    // device arena: per-dataset threshold/status block first, then buffers
+    Arena a;
+    for (auto &it : items) {
+        const size_t base = a.take<char>(256);
+        it.o_thr = base;
+        it.o_status = base + 4;
+        it.o_code = base + 8;
+        it.o_nout = base + 12;
+    }
+    for (auto &g : groups) {
+        g.o_desc = a.take<char>((g.tc ? tc_ds_bytes() : popc_ds_bytes()) * g.items.size());
+        g.o_tmap = a.take<char>((size_t)128 * g.items.size());
+        g.o_ctads = a.take<int32_t>((size_t)g.grid);
+        g.o_ls = a.take<float>((size_t)g.grid * g.pool);
+        g.o_lr = a.take<uint64_t>((size_t)g.grid * g.pool);
+        g.o_lc = a.take<int32_t>((size_t)g.grid);
+    }
+    for (auto &it : items) {
+        it.o_cs = a.take<float>((size_t)it.pool);
+        it.o_cr = a.take<uint64_t>((size_t)it.pool);
+        it.o_cn = a.take<int32_t>(1);
+        it.o_ct = a.take<uint32_t>((size_t)it.pool * 2 * it.cells);
+        it.o_mi = a.take<double>((size_t)it.pool);
+        it.o_cb = a.take<int32_t>((size_t)it.pool * it.k);
+        it.o_ic = a.take<uint64_t>((size_t)it.ds->n + 1);
+        it.o_rec = a.take<epi_result>((size_t)it.top_n);
+        it.o_cnt = a.take<uint32_t>((size_t)it.top_n * 2 * it.cells);
+    }
+    size_t hoff = 0;
+    for (auto &it : items) {
+        it.h_rec = hoff; hoff = align_up(hoff + (size_t)it.top_n * sizeof(epi_result), 64);
+        it.h_cnt = hoff; hoff = align_up(hoff + (size_t)it.top_n * 2 * it.cells * 4, 64);
+        it.h_nout = hoff; hoff += 64;
+        it.h_code = hoff; hoff += 64;
+    }
+    // descriptors are staged after the results in the pinned buffer
+    size_t hdesc = hoff;
+    for (auto &g : groups) hdesc = align_up(hdesc + (g.tc ? tc_ds_bytes() : popc_ds_bytes()) * g.items.size() +
+                                            128 * g.items.size() + (size_t)g.grid * 4, 256);
+    epi_status st = ensure_batch_buffers(ctx, a.off, hdesc + 256);
+    if (st != EPI_OK) return st;
+    for (auto &it : items)
+        if (it.tc) {
+            st = ensure_b8(it.ds);
+            if (st != EPI_OK) return st;
+        }
+    // graph key: datasets, orders, sizes, path
+    std::vector<uint64_t> key;
+    key.push_back((uint64_t)path);
+    for (auto &it : items) {
+        key.push_back(it.ds->id);
+        key.push_back((uint64_t)it.k << 32 | (uint64_t)it.top_n);
+    }
+    char *dev = static_cast<char *>(ctx->batch_dev);
+    char *host = static_cast<char *>(ctx->batch_host);
+    if (!ctx->batch_exec || key != ctx->batch_key) {
+        if (ctx->batch_exec) { cudaGraphExecDestroy(ctx->batch_exec); ctx->batch_exec = nullptr; }
+        // descriptor tables, built once per graph
+        size_t hp = hoff;
+        for (auto &g : groups) {
+            const size_t dsz = g.tc ? tc_ds_bytes() : popc_ds_bytes();
+            char *hd = host + hp;
+            char *hm = hd + dsz * g.items.size();
+            int32_t *hc = reinterpret_cast<int32_t *>(hm + 128 * g.items.size());
+            for (size_t q = 0; q < g.items.size(); q++) {
+                BatchItem &it = items[g.items[q]];
+                const DevData d = it.ds->dev();
+                uint32_t *thr = reinterpret_cast<uint32_t *>(dev + it.o_thr);
+                if (g.tc) {
+                    CK(tc_fill_batch_entry(hd + dsz * q, hm + 128 * q, d, it.k, it.ds->b8,
+                                           reinterpret_cast<uint64_t *>(dev + it.o_ic), thr, it.total,
+                                           dev + g.o_tmap + 128 * q, it.cta_begin, it.cta_count));
+                } else {
+                    popc_fill_ds(hd + dsz * q, d, 0, it.total, it.cta_begin, it.cta_count, thr);
+                }
+                for (int c2 = 0; c2 < it.cta_count; c2++) hc[it.cta_begin + c2] = (int32_t)q;
+            }
+            CK(cudaMemcpyAsync(dev + g.o_desc, hd, dsz * g.items.size(), cudaMemcpyHostToDevice, ctx->stream));
+            CK(cudaMemcpyAsync(dev + g.o_tmap, hm, 128 * g.items.size(), cudaMemcpyHostToDevice, ctx->stream));
+            CK(cudaMemcpyAsync(dev + g.o_ctads, hc, (size_t)g.grid * 4, cudaMemcpyHostToDevice, ctx->stream));
+            hp = align_up(hp + dsz * g.items.size() + 128 * g.items.size() + (size_t)g.grid * 4, 256);
+        }
+        CK(cudaStreamSynchronize(ctx->stream));
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
+        epi_status rs = record_batch(ctx, items, groups, ctx->capture_stream);
+        cudaError_t ec = cudaStreamEndCapture(ctx->capture_stream, &graph);
+        if (rs != EPI_OK) { if (graph) cudaGraphDestroy(graph); return rs; }
+        if (ec != cudaSuccess) return fail(EPI_ECUDA, "graph capture: %s", cudaGetErrorString(ec));
+        ec = cudaGraphInstantiate(&ctx->batch_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ec != cudaSuccess) { ctx->batch_exec = nullptr; return fail(EPI_ECUDA, "graph instantiate: %s", cudaGetErrorString(ec)); }
+        ctx->batch_key = key;
+    }
+    CK(cudaGraphLaunch(ctx->batch_exec, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < n_ds; i++) {
+        BatchItem &it = items[i];
+        const int32_t code = *reinterpret_cast<int32_t *>(host + it.h_code);
+        if (code == EPI_EOVERFLOW) {
+            // ties at the pool boundary: this dataset alone, with the retrying search
+            st = run_search_sync(it.ds, it.k, it.top_n, it.tc ? EPI_PATH_TC : EPI_PATH_POPC, 0, it.total, outs[i],
+                                 counts ? counts[i] : nullptr, &n_outs[i]);
+            if (st != EPI_OK) return fail(st, "dataset %d: %s", i, epi_last_error());
+            continue;
+        }
+        if (code != EPI_OK) return fail((epi_status)code, "dataset %d: device status %d", i, code);
+        const int n = *reinterpret_cast<int32_t *>(host + it.h_nout);
+        memcpy(outs[i], host + it.h_rec, (size_t)n * sizeof(epi_result));
+        if (counts && counts[i]) memcpy(counts[i], host + it.h_cnt, (size_t)n * 2 * it.cells * 4);
+        n_outs[i] = n;
+    }
+    return EPI_OK;
+}
+
 extern "C" {
 
 const char *epi_last_error(void) { return g_err.c_str(); }
@@ -417,6 +756,10 @@ static void free_ctx(epi_ctx *ctx)
     }
     for (auto &pr : ctx->prof_events) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
     if (ctx->waits_dev) cudaFree(ctx->waits_dev);
+    if (ctx->batch_exec) cudaGraphExecDestroy(ctx->batch_exec);
+    if (ctx->batch_dev) cudaFree(ctx->batch_dev);
+    if (ctx->batch_host) cudaFreeHost(ctx->batch_host);
+    if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     delete ctx;
 }
 
@@ -477,6 +820,7 @@ epi_status epi_dataset_create(epi_ctx *ctx, const uint8_t *geno, const uint8_t *
     } else {
         ds = new epi_dataset();
         ds->ctx = ctx;
+        ds->id = ctx->next_dataset_id++;
         ds->n = n; ds->m = m; ds->m1 = m1; ds->m0 = m - m1;
         ds->W1 = (int32_t)(((m1 + 127) / 128) * 4);
         ds->W0 = (int32_t)(((m - m1 + 127) / 128) * 4);

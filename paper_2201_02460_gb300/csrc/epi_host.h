@@ -39,6 +39,13 @@ int popc_max_active(int k, int R, size_t smem);
 cudaError_t launch_popc_search(const DevData &d, int k, int R, uint64_t rank_begin, uint64_t rank_end, int tile,
                                int pool, int slots, int cand_p2, uint32_t *global_thr, float *list_score,
                                uint64_t *list_rank, int32_t *list_count, int grid, size_t smem, cudaStream_t st);
+// batched: one launch over several datasets of order k (descriptors in device memory)
+size_t popc_ds_bytes();
+void popc_fill_ds(void *dst, const DevData &d, uint64_t rank_begin, uint64_t rank_end, int cta_begin, int cta_count,
+                  uint32_t *global_thr);
+cudaError_t launch_popc_batch(const void *ds_dev, const int32_t *cta_ds_dev, int k, int R, int max_wt, int tile,
+                              int pool, int slots, int cand_p2, float *list_score, uint64_t *list_rank,
+                              int32_t *list_count, int grid, size_t smem, cudaStream_t st);
 
 // epi_tc.cu
 size_t tc_b8_bytes(const DevData &d);
@@ -50,6 +57,15 @@ cudaError_t launch_tc_search(const DevData &d, int k, const unsigned char *b8, u
                              int32_t *status, int grid, uint64_t total, cudaStream_t st, int *cand_p2_out,
                              uint32_t *dump = nullptr, unsigned long long *waits = nullptr);
 constexpr int kTcWaitSlots = 8;
+// batched tensor-core launches: per-dataset descriptors and B-operand maps
+// (128-byte CUtensorMap, 64-byte aligned) live in device memory
+size_t tc_ds_bytes();
+cudaError_t launch_tc_item_cum(const DevData &d, int k, uint64_t *item_cum, cudaStream_t st);
+cudaError_t tc_fill_batch_entry(void *ds_host, void *tmap_host, const DevData &d, int k, const unsigned char *b8,
+                                uint64_t *item_cum, uint32_t *global_thr, uint64_t total, const void *tmap_dev,
+                                int cta_begin, int cta_count);
+cudaError_t launch_tc_batch(const void *ds_dev, const int32_t *cta_ds_dev, int k, int pool, float *list_score,
+                            uint64_t *list_rank, int32_t *list_count, int32_t *status, int grid, cudaStream_t st);
 
 // epi_select.cu
 cudaError_t launch_merge(const float *ls, const uint64_t *lr, const int32_t *lc, int nlists, int stride, int pool,

@@ -28,15 +28,25 @@ namespace epi {
 
 __host__ __device__ constexpr int ipow3(int k) { return k <= 0 ? 1 : 3 * ipow3(k - 1); }
 
-struct PopcParams {
+// One dataset of a launch.  A launch may cover several datasets of the same
+// order (batched search): CTAs [cta_begin, cta_begin + cta_count) of the grid
+// search this dataset's rank range, sized in proportion to its work.
+struct PopcDs {
     DevData d;
     uint64_t rank_begin, rank_end;  // lexicographic range searched
+    int32_t cta_begin, cta_count;
+    uint32_t *global_thr;           // float bits of max over its CTAs of their pool-th score
+};
+
+struct PopcParams {
+    PopcDs one;                     // the dataset when the launch has one
+    const PopcDs *many;             // else [n_ds] in device memory
+    const int32_t *cta_ds;          // and the dataset of each CTA
     int32_t tile;                   // combinations per sub-tile (T)
     int32_t pool;                   // list entries kept per CTA
     int32_t slots;                  // prefixes staged per sub-tile
-    int32_t slot_words;             // words per staged prefix (skewed by 4 words)
     int32_t cand_p2;                // shared candidate arrays (power of two)
-    uint32_t *global_thr;           // float bits of max over CTAs of their pool-th score
+    int32_t max_wt;                 // largest Wt of the launch (shared-memory layout)
     float *list_score;              // [grid][pool]
     uint64_t *list_rank;            // [grid][pool]
     int32_t *list_count;            // [grid]
@@ -151,11 +161,13 @@ template <int K, int R>
 __global__ void __launch_bounds__(128) popc_search_kernel(PopcParams P)
 {
     constexpr int PR = ipow3(K - 1);
-    const DevData &d = P.d;
+    const PopcDs &D = P.many ? P.many[P.cta_ds[blockIdx.x]] : P.one;
+    const DevData d = D.d;
+    const int slot_words = PR * d.Wt + 4;   // 16-byte skew: slots start on different banks
     extern __shared__ __align__(16) unsigned char smem[];
     // layout: prefix rows | totals | candidate scores | candidate ranks
     uint32_t *pre = reinterpret_cast<uint32_t *>(smem);
-    const size_t pre_words = (size_t)P.slots * P.slot_words;
+    const size_t pre_words = (size_t)P.slots * (PR * P.max_wt + 4);
     uint32_t *tot = pre + pre_words;
     uint64_t *rk = reinterpret_cast<uint64_t *>(smem + (((pre_words + (size_t)P.slots * PR * 2) * 4 + 15) & ~(size_t)15));
     float *sc = reinterpret_cast<float *>(rk + P.cand_p2);
@@ -164,9 +176,10 @@ __global__ void __launch_bounds__(128) popc_search_kernel(PopcParams P)
 
     const int km1 = K - 1;
     const MiConstF32 mc = make_mi_const(d.m, d.m1, d.m0);
-    const uint64_t span = P.rank_end - P.rank_begin;
-    const int64_t R_b = (int64_t)(P.rank_begin + (uint64_t)(((unsigned __int128)span * blockIdx.x) / gridDim.x));
-    const int64_t R_e = (int64_t)(P.rank_begin + (uint64_t)(((unsigned __int128)span * (blockIdx.x + 1)) / gridDim.x));
+    const uint64_t span = D.rank_end - D.rank_begin;
+    const uint64_t cb = blockIdx.x - (uint64_t)D.cta_begin, cn = (uint64_t)D.cta_count;
+    const int64_t R_b = (int64_t)(D.rank_begin + (uint64_t)(((unsigned __int128)span * cb) / cn));
+    const int64_t R_e = (int64_t)(D.rank_begin + (uint64_t)(((unsigned __int128)span * (cb + 1)) / cn));
 
     if (threadIdx.x == 0) {
         S.list_len = 0; S.nbuf = 0; S.thr = -1.0f; S.done = R_b >= R_e;
@@ -217,7 +230,7 @@ __global__ void __launch_bounds__(128) popc_search_kernel(PopcParams P)
                 S.cur_base = last.base;
             }
             // stricter of the CTA threshold and the best known global one
-            const float g = __uint_as_float(*(volatile uint32_t *)P.global_thr);
+            const float g = __uint_as_float(*(volatile uint32_t *)D.global_thr);
             if (S.list_len == P.pool || g > 0.0f) S.thr = fmaxf(S.thr, g);
         }
         __syncthreads();
@@ -256,14 +269,14 @@ __global__ void __launch_bounds__(128) popc_search_kernel(PopcParams P)
                     acc.x &= v.x; acc.y &= v.y; acc.z &= v.z; acc.w &= v.w;
                 }
             }
-            reinterpret_cast<uint4 *>(pre + (size_t)s * P.slot_words + (size_t)row * d.Wt)[w4] = acc;
+            reinterpret_cast<uint4 *>(pre + (size_t)s * slot_words + (size_t)row * d.Wt)[w4] = acc;
         }
         __syncthreads();
         // per-row totals of each subtable (the third genotype by subtraction)
         for (int idx = threadIdx.x; idx < ns * PR * 2; idx += blockDim.x) {
             const int half = idx & 1;
             const int sr = idx >> 1;
-            const uint32_t *row = pre + (size_t)(sr / PR) * P.slot_words + (size_t)(sr % PR) * d.Wt;
+            const uint32_t *row = pre + (size_t)(sr / PR) * slot_words + (size_t)(sr % PR) * d.Wt;
             uint32_t c = 0;
             const int wb = half ? d.W1 : 0, we = half ? d.Wt : d.W1;
             for (int w = wb; w < we; w++) c += __popc(row[w]);
@@ -279,7 +292,7 @@ __global__ void __launch_bounds__(128) popc_search_kernel(PopcParams P)
             int s = 0;
             while (s + 1 < ns && f >= slot[s + 1].base) s++;
             const int32_t j = slot[s].s_last + 1 + (int32_t)(f - slot[s].base);
-            const float score = score_popc<K, R>(pre + (size_t)s * P.slot_words, tot + s * PR * 2,
+            const float score = score_popc<K, R>(pre + (size_t)s * slot_words, tot + s * PR * 2,
                                                  d.masks + (int64_t)j * 3 * d.Wt, d, mc);
             if (score >= thr) {
                 const int pos = list_len + atomicAdd(&S.nbuf, 1);
@@ -293,7 +306,7 @@ __global__ void __launch_bounds__(128) popc_search_kernel(PopcParams P)
             S.done = F_end >= R_e;
         }
         __syncthreads();
-        if (S.nbuf > P.tile || (S.done && S.nbuf > 0)) flush_list(S, sc, rk, P.pool, P.cand_p2, P.global_thr);
+        if (S.nbuf > P.tile || (S.done && S.nbuf > 0)) flush_list(S, sc, rk, P.pool, P.cand_p2, D.global_thr);
     }
     __syncthreads();
     const int L = S.list_len;
@@ -368,23 +381,8 @@ int popc_max_active(int k, int R, size_t smem)
     }
 }
 
-cudaError_t launch_popc_search(const DevData &d, int k, int R, uint64_t rank_begin, uint64_t rank_end, int tile,
-                               int pool, int slots, int cand_p2, uint32_t *global_thr, float *list_score,
-                               uint64_t *list_rank, int32_t *list_count, int grid, size_t smem, cudaStream_t st)
+static cudaError_t launch_dispatch(const PopcParams &p, int k, int R, int grid, size_t smem, cudaStream_t st)
 {
-    PopcParams p;
-    p.d = d;
-    p.rank_begin = rank_begin;
-    p.rank_end = rank_end;
-    p.tile = tile;
-    p.pool = pool;
-    p.slots = slots;
-    p.slot_words = popc_slot_words(k, d.Wt);
-    p.cand_p2 = cand_p2;
-    p.global_thr = global_thr;
-    p.list_score = list_score;
-    p.list_rank = list_rank;
-    p.list_count = list_count;
     switch (k * 100 + R) {
     case 101: return launch_kr<1, 1>(p, grid, smem, st);
     case 203: return launch_kr<2, 3>(p, grid, smem, st);
@@ -395,6 +393,63 @@ cudaError_t launch_popc_search(const DevData &d, int k, int R, uint64_t rank_beg
     case 527: return launch_kr<5, 27>(p, grid, smem, st);
     default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_popc_search(const DevData &d, int k, int R, uint64_t rank_begin, uint64_t rank_end, int tile,
+                               int pool, int slots, int cand_p2, uint32_t *global_thr, float *list_score,
+                               uint64_t *list_rank, int32_t *list_count, int grid, size_t smem, cudaStream_t st)
+{
+    PopcParams p;
+    p.one.d = d;
+    p.one.rank_begin = rank_begin;
+    p.one.rank_end = rank_end;
+    p.one.cta_begin = 0;
+    p.one.cta_count = grid;
+    p.one.global_thr = global_thr;
+    p.many = nullptr;
+    p.cta_ds = nullptr;
+    p.tile = tile;
+    p.pool = pool;
+    p.slots = slots;
+    p.cand_p2 = cand_p2;
+    p.max_wt = d.Wt;
+    p.list_score = list_score;
+    p.list_rank = list_rank;
+    p.list_count = list_count;
+    return launch_dispatch(p, k, R, grid, smem, st);
+}
+
+size_t popc_ds_bytes() { return sizeof(PopcDs); }
+
+void popc_fill_ds(void *dst, const DevData &d, uint64_t rank_begin, uint64_t rank_end, int cta_begin, int cta_count,
+                  uint32_t *global_thr)
+{
+    PopcDs *o = static_cast<PopcDs *>(dst);
+    o->d = d;
+    o->rank_begin = rank_begin;
+    o->rank_end = rank_end;
+    o->cta_begin = cta_begin;
+    o->cta_count = cta_count;
+    o->global_thr = global_thr;
+}
+
+cudaError_t launch_popc_batch(const void *ds_dev, const int32_t *cta_ds_dev, int k, int R, int max_wt, int tile,
+                              int pool, int slots, int cand_p2, float *list_score, uint64_t *list_rank,
+                              int32_t *list_count, int grid, size_t smem, cudaStream_t st)
+{
+    PopcParams p;
+    p.one = PopcDs();
+    p.many = static_cast<const PopcDs *>(ds_dev);
+    p.cta_ds = cta_ds_dev;
+    p.tile = tile;
+    p.pool = pool;
+    p.slots = slots;
+    p.cand_p2 = cand_p2;
+    p.max_wt = max_wt;
+    p.list_score = list_score;
+    p.list_rank = list_rank;
+    p.list_count = list_count;
+    return launch_dispatch(p, k, R, grid, smem, st);
 }
 
 }  // namespace epi

@@ -42,6 +42,7 @@
 // ST_TIMEOUT and all roles leave their loops, drain their own asynchronous
 // work and free tensor memory.
 #include <cuda.h>
+#include <cstring>
 #include <cudaTypedefs.h>
 
 #include "epi_host.h"
@@ -73,19 +74,29 @@ struct Desc {
     int32_t snp[kMaxDescSnps];   // prefix p occupies snp[p*(k-1) .. p*(k-1)+k-2]
 };
 
-struct Params {
+// One dataset of a launch; a batched launch covers several datasets of the
+// same order, CTAs [cta_begin, cta_begin + cta_count) working on this one.
+struct DsParams {
     DevData d;
-    int k, PR, ppw, ppt;
     uint64_t n_prefix;         // C(n-1, k-1)
     uint64_t n_items;
     const uint64_t *item_cum;  // [n + 1] items of M tiles starting in panels < c
     int chunks, chunks_case;   // K stages in total / over the cases
-    int pool, cand_p2;
     float delta;               // screening margin (nats)
     float tconst;              // T(m) - T(m1) - T(m0), T(c) = c log2 c
     float ln2_over_m;
     uint64_t total;            // C(n, k)
     uint32_t *global_thr;
+    const CUtensorMap *tmap;   // B-operand map in global memory (batched launches)
+    int32_t cta_begin, cta_count;
+};
+
+struct Params {
+    DsParams one;              // the dataset when the launch has one
+    const DsParams *many;      // else [n_ds] in device memory
+    const int32_t *cta_ds;     // and the dataset of each CTA
+    int k, PR, ppw, ppt;
+    int pool, cand_p2;
     float *list_score;
     uint64_t *list_rank;
     int32_t *list_count;
@@ -381,10 +392,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const DevData &d = P.d;
+    const DsParams &DS = P.many ? P.many[P.cta_ds[blockIdx.x]] : P.one;
+    const DevData d = DS.d;
+    const CUtensorMap *tmap = DS.tmap ? DS.tmap : &tmap_b;
 
-    const uint64_t it_b = (uint64_t)(((unsigned __int128)P.n_items * blockIdx.x) / gridDim.x);
-    const uint64_t it_e = (uint64_t)(((unsigned __int128)P.n_items * (blockIdx.x + 1)) / gridDim.x);
+    const uint64_t cb = blockIdx.x - (uint64_t)DS.cta_begin, cn = (uint64_t)DS.cta_count;
+    const uint64_t it_b = (uint64_t)(((unsigned __int128)DS.n_items * cb) / cn);
+    const uint64_t it_e = (uint64_t)(((unsigned __int128)DS.n_items * (cb + 1)) / cn);
     const int64_t n_my = (int64_t)(it_e - it_b);
 
     if (tid == 0) {
@@ -428,11 +442,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
             int64_t lo = 0, hi = d.n - 1;
             while (lo < hi) {
                 const int64_t mid = (lo + hi + 1) >> 1;
-                if (P.item_cum[mid] <= w0) lo = mid;
+                if (DS.item_cum[mid] <= w0) lo = mid;
                 else hi = mid - 1;
             }
             const int32_t c0 = (int32_t)lo;
-            const uint64_t off = w0 - P.item_cum[c0];
+            const uint64_t off = w0 - DS.item_cum[c0];
             const int64_t nt0 = ntiles_of(d, c0);
             const uint64_t tfirst = (binom_at(d.binom, d.n, c0, km1) + kPPT - 1) / kPPT;
             const uint64_t t = tfirst + off / (uint64_t)nt0;
@@ -446,7 +460,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                 cmin = it.c;
 #pragma unroll
                 for (int p = 0; p < kPPT; p++) {
-                    if (it.q < P.n_prefix) {
+                    if (it.q < DS.n_prefix) {
 #pragma unroll
                         for (int s2 = 0; s2 < km1 - 1; s2++) tile_snp[p * km1 + s2] = it.a[s2];
                         tile_snp[p * km1 + km1 - 1] = it.c;
@@ -469,12 +483,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                 for (int q = 0; q < kPPT * km1; q++) D.snp[q] = tile_snp[q];
                 mbar_arrive(&desc_full[dq]);
                 const int y = 2 * D.j0;
-                for (int kc = 0; kc < P.chunks; kc++, g++) {
+                for (int kc = 0; kc < DS.chunks; kc++, g++) {
                     const int s = (int)(g % kStagesB);
                     const uint32_t us = (uint32_t)(g / kStagesB);
                     if (!wait_fast(&empty_b[s], (us & 1) ^ 1, &abort_flag, w_tma)) break;
                     mbar_arrive_tx(&full_b[s], kTxBytes);
-                    tma_load_2d(stages_b + s * kTileBytes, &tmap_b, kc * kKC, y, &full_b[s]);
+                    tma_load_2d(stages_b + s * kTileBytes, tmap, kc * kKC, y, &full_b[s]);
                 }
                 u++;
                 if (u == ntiles_of(d, cmin)) {
@@ -505,14 +519,14 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                 if (!wait_fast(&acc_empty[b], (ub & 1) ^ 1, &abort_flag, w_acc)) break;
                 tc_fence_after();
                 bool ok = true;
-                for (int kc = 0; kc < P.chunks; kc++, g++) {
+                for (int kc = 0; kc < DS.chunks; kc++, g++) {
                     const int sa = (int)(g % kStagesA), sb = (int)(g % kStagesB);
                     const uint32_t ua = (uint32_t)(g / kStagesA), ubb = (uint32_t)(g / kStagesB);
                     if (!wait_fast(&full_a[sa], ua & 1, &abort_flag, w_a)) { ok = false; break; }
                     if (!wait_fast(&full_b[sb], ubb & 1, &abort_flag, w_b)) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t dcol = tmem_base + (uint32_t)(b * 2 * kN) + (kc < P.chunks_case ? 0u : (uint32_t)kN);
-                    const bool first = (kc == 0) || (kc == P.chunks_case);
+                    const uint32_t dcol = tmem_base + (uint32_t)(b * 2 * kN) + (kc < DS.chunks_case ? 0u : (uint32_t)kN);
+                    const bool first = (kc == 0) || (kc == DS.chunks_case);
                     const uint64_t ad = sdesc(sa0 + sa * kTileBytes);
                     const uint64_t bd = sdesc(sb0 + sb * kTileBytes);
 #pragma unroll
@@ -577,7 +591,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
 #pragma unroll
             for (int u = 0; u < kPf; u++) {
                 ring[u] = make_uint2(0, 0);
-                if (active && u < P.chunks) {
+                if (active && u < DS.chunks) {
                     ring[u] = __ldg(rows[0] + 2 * u);
 #pragma unroll
                     for (int tt = 1; tt < km1; tt++) {
@@ -586,13 +600,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                     }
                 }
             }
-            for (int kb = 0; kb < P.chunks && ok; kb += kPf) {
+            for (int kb = 0; kb < DS.chunks && ok; kb += kPf) {
 #pragma unroll
                 for (int u = 0; u < kPf; u++) {
                     const int kc = kb + u;
-                    if (kc >= P.chunks) break;
+                    if (kc >= DS.chunks) break;
                     const uint2 cur = ring[u];
-                    if (active && kc + kPf < P.chunks) {
+                    if (active && kc + kPf < DS.chunks) {
                         ring[u] = __ldg(rows[0] + 2 * (kc + kPf));
 #pragma unroll
                         for (int tt = 1; tt < km1; tt++) {
@@ -605,7 +619,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                     if (!wait_fast(&empty_a[s], (us & 1) ^ 1, &abort_flag, w_prod)) { ok = false; break; }
                     if (active) {
                         const uint32_t c2 = __popc(cur.x) + __popc(cur.y);
-                        if (kc < P.chunks_case) t1 += c2;
+                        if (kc < DS.chunks_case) t1 += c2;
                         else t0 += c2;
                     }
                     unsigned char *arow = stages_a + s * kTileBytes + r * 128;
@@ -670,14 +684,14 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
             const float fT1 = u2f_exact(T1), fT0 = u2f_exact(T0);
             const int32_t j0 = D.j0 + 32 * jhalf;
             if (tid == 0) {
-                const float gthr = __uint_as_float(*(volatile uint32_t *)P.global_thr);
+                const float gthr = __uint_as_float(*(volatile uint32_t *)DS.global_thr);
                 if (ES.list_len == P.pool || gthr > 0.0f) ES.thr = fmaxf(ES.thr, gthr);
             }
             epi_bar();
 #pragma unroll 1
             for (int jc = 0; jc < 4; jc++) {
                 const float thr = ES.thr;
-                const float cut = thr - P.delta;
+                const float cut = thr - DS.delta;
                 const int list_len = ES.list_len;
                 uint32_t cs[16], cn[16];
                 if (ok) {
@@ -711,11 +725,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                         for (int tt = 0; tt < km1; tt++) rs += binom_at(d.binom, d.n, d.n - 1 - psnp[tt], K - tt);
                         rs += binom_at(d.binom, d.n, d.n - 1 - j, 1);
                         constexpr int cells = kPR * 3;
-                        uint32_t *o = P.dump + (P.total - 1 - rs) * 2 * cells;
+                        uint32_t *o = P.dump + (DS.total - 1 - rs) * 2 * cells;
                         o[pos * 3 + 0] = a0; o[pos * 3 + 1] = a1; o[pos * 3 + 2] = a2;
                         o[cells + pos * 3 + 0] = b0; o[cells + pos * 3 + 1] = b1; o[cells + pos * 3 + 2] = b2;
                     }
-                    const float approx = (v + P.tconst) * P.ln2_over_m;
+                    const float approx = (v + DS.tconst) * DS.ln2_over_m;
                     const bool cand = valid && pos == 0 && approx >= cut;
                     uint32_t seg_mask = __ballot_sync(0xffffffffu, cand);
                     while (seg_mask) {
@@ -736,13 +750,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                                 rk_sum += binom_at(d.binom, d.n, d.n - 1 - j, 1);
                                 const int slot = list_len + atomicAdd(&ES.nbuf, 1);
                                 sc[slot] = score;
-                                rk[slot] = P.total - 1 - rk_sum;
+                                rk[slot] = DS.total - 1 - rk_sum;
                             }
                         }
                     }
                 }
                 epi_bar();
-                if (ES.nbuf > 16 * kPPT) epi_flush(ES, sc, rk, P.pool, P.global_thr, tid);
+                if (ES.nbuf > 16 * kPPT) epi_flush(ES, sc, rk, P.pool, DS.global_thr, tid);
             }
             tc_fence_before();
             __syncwarp();
@@ -756,7 +770,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
             if (ES.stop) break;
         }
         epi_bar();
-        if (ES.nbuf > 0) epi_flush(ES, sc, rk, P.pool, P.global_thr, tid);
+        if (ES.nbuf > 0) epi_flush(ES, sc, rk, P.pool, DS.global_thr, tid);
         const int L = ES.list_len;
         for (int q = tid; q < L; q += kEpiThreads) {
             P.list_score[(size_t)blockIdx.x * P.pool + q] = sc[q];
@@ -888,68 +902,127 @@ size_t tc_smem_bytes(int cand_p2)
            tc::kDescDepth * sizeof(tc::Desc) + 64;
 }
 
-cudaError_t launch_tc_search(const DevData &d, int k, const unsigned char *b8, uint64_t *item_cum, int pool,
-                             uint32_t *global_thr, float *list_score, uint64_t *list_rank, int32_t *list_count,
-                             int32_t *status, int grid, uint64_t total, cudaStream_t st, int *cand_p2_out,
-                             uint32_t *dump, unsigned long long *waits)
+static int tc_ppt(int k) { return 4 * (32 / (k == 2 ? 3 : (k == 3 ? 9 : 27))); }
+
+static cudaError_t encode_map(CUtensorMap *map, const DevData &d, const unsigned char *b8)
 {
     cudaError_t e = get_encode();
     if (e != cudaSuccess) return e;
-    tc::Params P;
-    P.d = d;
+    const int64_t Kt = (int64_t)d.Wt * 32;
+    cuuint64_t gdim[2] = {(cuuint64_t)Kt, (cuuint64_t)(2 * d.n)};
+    cuuint64_t gstride[1] = {(cuuint64_t)Kt};
+    cuuint32_t box[2] = {(cuuint32_t)tc::kKC, 128u};
+    cuuint32_t estr[2] = {1u, 1u};
+    CUresult cr = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<unsigned char *>(b8), gdim, gstride, box,
+                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return cr == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// Per-dataset parameters (host side); the B-operand map goes to tmap_dev when
+// the launch is batched (nullptr: passed as a kernel parameter instead).
+static void fill_ds(tc::DsParams &D, const DevData &d, int k, uint64_t *item_cum, uint32_t *global_thr,
+                    uint64_t total, const CUtensorMap *tmap_dev, int cta_begin, int cta_count)
+{
+    D.d = d;
+    unsigned __int128 np = 1;
+    for (int t = 0; t < k - 1; t++) np = np * (unsigned __int128)(d.n - 1 - t) / (unsigned __int128)(t + 1);
+    D.n_prefix = (uint64_t)np;
+    D.n_items = tc_item_count(d.n, k);
+    D.item_cum = item_cum;
+    const int64_t Kt = (int64_t)d.Wt * 32;
+    D.chunks = (int)(Kt / tc::kKC);
+    D.chunks_case = (int)((int64_t)d.W1 * 32 / tc::kKC);
+    auto T = [](double c) { return c > 0 ? c * log2(c) : 0.0; };
+    D.tconst = (float)(T((double)d.m) - T((double)d.m1) - T((double)d.m0));
+    D.ln2_over_m = (float)(0.6931471805599453 / (double)d.m);
+    // screening margin: relative errors of the log2 approximation (2^-21)
+    // and of the float sums over (T(m) + T(m1) + T(m0)), doubled
+    const int64_t cells = (int64_t)(k == 2 ? 3 : (k == 3 ? 9 : 27)) * 3;
+    const double mag = T((double)d.m) + T((double)d.m1) + T((double)d.m0);
+    D.delta = (float)(2.0 * (4.0 * 4.76837158203125e-7 + (double)(2 * cells + 40) * 5.9604644775390625e-8) * mag *
+                      0.6931471805599453 / (double)d.m) + 1e-7f;
+    D.total = total;
+    D.global_thr = global_thr;
+    D.tmap = tmap_dev;
+    D.cta_begin = cta_begin;
+    D.cta_count = cta_count;
+}
+
+static void fill_launch(tc::Params &P, int k, int pool, float *list_score, uint64_t *list_rank, int32_t *list_count,
+                        int32_t *status, uint32_t *dump, unsigned long long *waits)
+{
     P.k = k;
     P.PR = k == 2 ? 3 : (k == 3 ? 9 : 27);
     P.ppw = 32 / P.PR;
     P.ppt = 4 * P.ppw;
-    // C(n-1, k-1) prefixes, computed with the same exact arithmetic as the host
-    unsigned __int128 np = 1;
-    for (int t = 0; t < k - 1; t++) np = np * (unsigned __int128)(d.n - 1 - t) / (unsigned __int128)(t + 1);
-    P.n_prefix = (uint64_t)np;
-    P.item_cum = item_cum;
-    tc::item_cum_kernel<<<1, 1024, 0, st>>>(d, k, P.ppt, item_cum);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    P.n_items = tc_item_count(d.n, k);
-    const int64_t Kt = (int64_t)d.Wt * 32;
-    P.chunks = (int)(Kt / tc::kKC);
-    P.chunks_case = (int)((int64_t)d.W1 * 32 / tc::kKC);
     P.pool = pool;
     P.cand_p2 = next_pow2(pool + 2 * 16 * P.ppt);
-    *cand_p2_out = P.cand_p2;
-    auto T = [](double c) { return c > 0 ? c * log2(c) : 0.0; };
-    const double tconst = T((double)d.m) - T((double)d.m1) - T((double)d.m0);
-    P.tconst = (float)tconst;
-    P.ln2_over_m = (float)(0.6931471805599453 / (double)d.m);
-    // screening margin: relative errors of the log2 approximation (2^-21)
-    // and of the float sums over (T(m) + T(m1) + T(m0)), doubled
-    const int64_t cells = (int64_t)P.PR * 3;
-    const double mag = T((double)d.m) + T((double)d.m1) + T((double)d.m0);
-    P.delta = (float)(2.0 * (4.0 * 4.76837158203125e-7 + (double)(2 * cells + 40) * 5.9604644775390625e-8) * mag *
-                      0.6931471805599453 / (double)d.m) + 1e-7f;
-    P.total = total;
-    P.global_thr = global_thr;
     P.list_score = list_score;
     P.list_rank = list_rank;
     P.list_count = list_count;
     P.status = status;
     P.dump = dump;
     P.waits = waits;
+}
 
-    CUtensorMap map;
-    cuuint64_t gdim[2] = {(cuuint64_t)Kt, (cuuint64_t)(2 * d.n)};
-    cuuint64_t gstride[1] = {(cuuint64_t)Kt};
-    cuuint32_t box[2] = {(cuuint32_t)tc::kKC, 128u};
-    cuuint32_t estr[2] = {1u, 1u};
-    CUresult cr = g_encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<unsigned char *>(b8), gdim, gstride, box,
-                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
+static cudaError_t launch_kernel(const CUtensorMap &map, const tc::Params &P, int k, int grid, cudaStream_t st)
+{
     const size_t smem = tc_smem_bytes(P.cand_p2);
     auto kern = k == 2 ? tc::tc_search_kernel<2> : (k == 3 ? tc::tc_search_kernel<3> : tc::tc_search_kernel<4>);
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, tc::kThreads, smem, st>>>(map, P);
     return cudaGetLastError();
+}
+
+cudaError_t launch_tc_item_cum(const DevData &d, int k, uint64_t *item_cum, cudaStream_t st)
+{
+    tc::item_cum_kernel<<<1, 1024, 0, st>>>(d, k, tc_ppt(k), item_cum);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_search(const DevData &d, int k, const unsigned char *b8, uint64_t *item_cum, int pool,
+                             uint32_t *global_thr, float *list_score, uint64_t *list_rank, int32_t *list_count,
+                             int32_t *status, int grid, uint64_t total, cudaStream_t st, int *cand_p2_out,
+                             uint32_t *dump, unsigned long long *waits)
+{
+    tc::Params P;
+    fill_ds(P.one, d, k, item_cum, global_thr, total, nullptr, 0, grid);
+    P.many = nullptr;
+    P.cta_ds = nullptr;
+    fill_launch(P, k, pool, list_score, list_rank, list_count, status, dump, waits);
+    *cand_p2_out = P.cand_p2;
+    cudaError_t e = launch_tc_item_cum(d, k, item_cum, st);
+    if (e != cudaSuccess) return e;
+    CUtensorMap map;
+    e = encode_map(&map, d, b8);
+    if (e != cudaSuccess) return e;
+    return launch_kernel(map, P, k, grid, st);
+}
+
+size_t tc_ds_bytes() { return sizeof(tc::DsParams); }
+
+cudaError_t tc_fill_batch_entry(void *ds_host, void *tmap_host, const DevData &d, int k, const unsigned char *b8,
+                                uint64_t *item_cum, uint32_t *global_thr, uint64_t total, const void *tmap_dev,
+                                int cta_begin, int cta_count)
+{
+    fill_ds(*static_cast<tc::DsParams *>(ds_host), d, k, item_cum, global_thr, total,
+            static_cast<const CUtensorMap *>(tmap_dev), cta_begin, cta_count);
+    return encode_map(static_cast<CUtensorMap *>(tmap_host), d, b8);
+}
+
+cudaError_t launch_tc_batch(const void *ds_dev, const int32_t *cta_ds_dev, int k, int pool, float *list_score,
+                            uint64_t *list_rank, int32_t *list_count, int32_t *status, int grid, cudaStream_t st)
+{
+    tc::Params P;
+    P.one = tc::DsParams();
+    P.many = static_cast<const tc::DsParams *>(ds_dev);
+    P.cta_ds = cta_ds_dev;
+    fill_launch(P, k, pool, list_score, list_rank, list_count, status, nullptr, nullptr);
+    CUtensorMap unused;
+    memset(&unused, 0, sizeof(unused));
+    return launch_kernel(unused, P, k, grid, st);
 }
 
 }  // namespace epi

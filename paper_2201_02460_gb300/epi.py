@@ -100,6 +100,8 @@ def load(path: str | None = None):
         lib.epi_score_tables.argtypes = [V, i32, P, i64, P, P]
         lib.epi_kernel_launches.restype = u64
         lib.epi_kernel_launches.argtypes = [V]
+        lib.epi_search_batched.restype = i32
+        lib.epi_search_batched.argtypes = [V, P, P, P, i32, i32, P, P, P]
         lib.epi_debug_counts.restype = i32
         lib.epi_debug_counts.argtypes = [V, i32, P]
         lib.epi_profile_begin.restype = i32
@@ -275,6 +277,27 @@ def search_async(ds: Dataset, order: int, top_n: int, out_dev, counts_dev, n_out
     cp = C.c_void_p(counts_dev.data_ptr()) if counts_dev is not None else None
     _check(lib.epi_search_async(ds.handle, order, top_n, PATHS[path], C.c_void_p(out_dev.data_ptr()), cp,
                                 C.c_void_p(n_out_dev.data_ptr()), C.c_void_p(status_dev.data_ptr())))
+
+
+def search_batched(ctx: Context, datasets, orders, top_ns, path: str = "auto",
+                   with_counts: bool = True) -> list:
+    """One batched search over several datasets (see epi_search_batched);
+    returns one SearchResult per dataset."""
+    lib = load()
+    n = len(datasets)
+    orders = [int(x) for x in orders]
+    top_ns = [int(x) for x in top_ns]
+    outs = [np.zeros(t, dtype=RESULT_DTYPE) for t in top_ns]
+    cnts = [np.zeros((t, 2, 3 ** k), dtype=np.uint32) for t, k in zip(top_ns, orders)] if with_counts else None
+    h = (C.c_void_p * n)(*[d.handle.value for d in datasets])
+    o_arr = (C.c_int * n)(*orders)
+    t_arr = (C.c_int * n)(*top_ns)
+    out_p = (C.c_void_p * n)(*[o.ctypes.data for o in outs])
+    cnt_p = (C.c_void_p * n)(*[c.ctypes.data for c in cnts]) if with_counts else None
+    n_out = (C.c_int * n)()
+    _check(lib.epi_search_batched(ctx.handle, h, o_arr, t_arr, n, PATHS[path], out_p, cnt_p, n_out))
+    return [SearchResult(outs[i][: n_out[i]], cnts[i][: n_out[i]] if with_counts else None, orders[i])
+            for i in range(n)]
 
 
 def debug_counts(ds: Dataset, order: int) -> np.ndarray:

@@ -288,3 +288,48 @@ def test_profile_trace_survives_scratch_growth(epi, ctx):
     ms, n = ctx.profile_end()
     assert n == 2 and ms > 0
     assert w["mma_loop"] > 0
+
+
+# ---------------------------------------------------------------------------
+# batched searches
+# ---------------------------------------------------------------------------
+
+def _batch_case(seed):
+    rng = np.random.default_rng(seed)
+    specs = []
+    for i in range(10):
+        k = int(rng.integers(1, 6))
+        n = int(rng.integers(k + 2, {1: 300, 2: 120, 3: 60, 4: 30, 5: 18}[k]))
+        m = int(rng.integers(40, 2500))
+        m1 = int(rng.integers(1, m)) if i % 4 else int(rng.integers(0, 2)) * m
+        specs.append((k, n, m, m1, int(rng.integers(1, 80))))
+    return specs
+
+
+@pytest.mark.parametrize("path", ["auto", "popc"])
+def test_batched_matches_single(epi, ctx, path):
+    specs = _batch_case(5)
+    data = [random_data(n, m, seed=100 + i, m1=m1) for i, (k, n, m, m1, t) in enumerate(specs)]
+    dss = [epi.Dataset(ctx, g, p) for g, p in data]
+    orders = [s[0] for s in specs]
+    tops = [s[4] for s in specs]
+    for rep in range(2):                       # capture, then replay
+        res = epi.search_batched(ctx, dss, orders, tops, path=path)
+        for ds, k, t, r in zip(dss, orders, tops, res):
+            one = epi.search(ds, k, t, path=path)
+            assert (r.records == one.records).all()
+            assert (r.counts == one.counts).all()
+
+
+def test_batched_against_oracle_and_new_graph(epi, ctx):
+    specs = [(3, 40, 900, 400, 30), (2, 90, 1300, 650, 25), (4, 20, 700, 300, 20), (3, 50, 2100, 1000, 40)]
+    data = [random_data(n, m, seed=7 + i, m1=m1) for i, (k, n, m, m1, t) in enumerate(specs)]
+    dss = [epi.Dataset(ctx, g, p) for g, p in data]
+    res = epi.search_batched(ctx, dss, [s[0] for s in specs], [s[4] for s in specs])
+    for (g, p), (k, n, m, m1, t), r in zip(data, specs, res):
+        oc, om, ot = O.search(g, p, k, t)
+        _check_result(r, g, p, oc, om)
+    # different top_n: a new graph
+    res2 = epi.search_batched(ctx, dss, [s[0] for s in specs], [5, 6, 7, 8])
+    for r, r_old in zip(res2, res):
+        assert (r.records == r_old.records[: len(r)]).all()
