@@ -205,6 +205,33 @@ def time_search(epi, ctx, ds, k, top_n, path, steps, warmup, flush, stream):
                 res=res, waits=waits)
 
 
+def measure_batch(epi, ctx, synth, n_div, steps=2):
+    """The 64-dataset batched configuration (orders 2-4, 1000-16000 samples,
+    case fraction 0.3-0.7, top-20 each) with SNP counts divided by n_div: one
+    epi_search_batched call per step (graph captured during the warm-up)."""
+    import torch
+    specs = synth.batch_specs()
+    dss, orders, tops, work = [], [], [], 0
+    for sp in specs:
+        n = max(sp["order"] + 2, sp["n_snps"] // n_div)
+        d = synth.make_dataset(n, sp["n_cases"], sp["n_controls"], seed=sp["seed"], maf_lo=sp["maf_lo"])
+        dss.append(epi.Dataset(ctx, d.geno, d.pheno))
+        orders.append(sp["order"])
+        tops.append(sp["top_n"])
+        work += math.comb(n, sp["order"]) * d.n_samples
+    epi.search_batched(ctx, dss, orders, tops)          # warm-up: builds and captures the graph
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        epi.search_batched(ctx, dss, orders, tops)
+    torch.cuda.synchronize()
+    t = (time.perf_counter() - t0) / steps
+    for ds in dss:
+        ds.close()
+    return dict(value=work / t, ms_per_step=1e3 * t, datasets=len(specs), combination_samples=work,
+                snp_divisor=n_div, timing="host wall clock around the synchronous batched call")
+
+
 def roofline(kind, d, k, kern_ms, peaks):
     total = math.comb(d.n_snps, k)
     if kind == "tc":
@@ -315,6 +342,7 @@ def run_ours(args):
                 comp["order4_500snp_8192/popc"] = dict(value=u4 / (p4["t_ms"] / 1e3), ms_per_step=p4["t_ms"],
                                                        roofline=roofline("popc", d4, k4, p4["kern_ms"], peaks))
             ds4.close()
+        comp["batch64/auto"] = measure_batch(epi, ctx, synth, args.batch_div)
         line["compare"] = comp
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -340,6 +368,7 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the other path and the order-4 workload")
     ap.add_argument("--full-compare", action="store_true", help="also time the order-4 popcount path (~26 s)")
     ap.add_argument("--n-snps", type=int, default=None, help="smaller SNP count (profiling captures)")
+    ap.add_argument("--batch-div", type=int, default=3, help="SNP-count divisor of the 64-dataset batch")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

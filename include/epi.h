@@ -140,6 +140,20 @@ epi_status epi_search_batched(epi_ctx *ctx, epi_dataset *const *ds, const int *o
                               int n_ds, int path, epi_result *const *outs, uint32_t *const *counts,
                               int *n_outs);
 
+/* Autotuner (the paper has no counterpart; it tunes this build's launch
+ * shapes).  Times every popcount-path shape (row group of prefix rows per
+ * thread, sub-tile of combinations, prefixes staged per sub-tile) on a
+ * bounded rank range of this dataset and, where the tensor-core path applies,
+ * the two paths; the fastest is kept in the context for every later search
+ * (EPI_PATH_AUTO, batched or not) of the same order and size bucket (SNPs and
+ * sample words rounded down to powers of two).  out (may be NULL) receives
+ * four ints: row group, sub-tile, staged prefixes, chosen path. */
+epi_status epi_autotune(epi_dataset *ds, int order, int *out);
+
+/* The context's autotuner choices to / from a text file. */
+epi_status epi_tune_save(const epi_ctx *ctx, const char *path);
+epi_status epi_tune_load(epi_ctx *ctx, const char *path);
+
 /* Contingency tables (Section 2.2) of `count` given combinations.  combs:
  * host [count][order] uint32, each strictly increasing and < n_snps;
  * out: host [count][2][3^order].  order in 1..8. */

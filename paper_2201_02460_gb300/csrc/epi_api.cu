@@ -2,7 +2,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
+#include <map>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -33,6 +35,9 @@ struct epi_ctx {
     cudaGraphExec_t batch_exec = nullptr;
     std::vector<uint64_t> batch_key;
     uint64_t next_dataset_id = 1;
+    // autotuner choices by (order, SNP bucket, sample-word bucket)
+    struct Tune { int R = 0, tile = 0, slots = 0, path = 0; double ms = 0; };
+    std::map<uint64_t, Tune> tune;
     unsigned long long *waits_dev = nullptr;   // own buffer: per-role wait cycles of a profiled TC search
     int waits_grid = 0;                        // CTAs recorded in waits_dev (0: nothing recorded)
     bool destroy_requested = false;
@@ -143,6 +148,16 @@ epi_status ensure_scratch(epi_ctx *ctx, size_t bytes)
     return EPI_OK;
 }
 
+// Size bucket of the autotuner: order, log2 of the SNP count, log2 of the
+// sample words (choices transfer between datasets of similar shape).
+uint64_t tune_key(int k, int64_t n, int32_t wt)
+{
+    int nb = 0, wb = 0;
+    while ((int64_t)1 << (nb + 1) <= n) nb++;
+    while ((1 << (wb + 1)) <= wt) wb++;
+    return ((uint64_t)k << 48) | ((uint64_t)nb << 24) | (uint64_t)wb;
+}
+
 struct SearchPlan {
     int k = 0, top_n = 0, pool = 0, tile = 0, slots = 0, cand_p2 = 0, grid = 0, R = 0;
     bool tc = false;
@@ -161,11 +176,26 @@ epi_status plan_popc(const epi_dataset *ds, SearchPlan &p, int R_req = 0)
     if (!popc_row_group_ok(p.k, p.R)) return fail(EPI_EINVAL, "row group %d invalid for order %d", p.R, p.k);
     const size_t limit = ctx->smem_optin ? ctx->smem_optin : 227 * 1024;
     int best_score = -1;
+    // an autotuned shape for this size bucket, unless the caller forces one
+    int tune_tile = 0, tune_slots = 0;
+    if (!R_req) {
+        auto it = ctx->tune.find(tune_key(p.k, ds->n, ds->Wt));
+        if (it != ctx->tune.end() && it->second.R) {
+            p.R = it->second.R;
+            tune_tile = it->second.tile;
+            tune_slots = it->second.slots;
+        }
+    } else if (p.tile && p.slots) {
+        tune_tile = p.tile;
+        tune_slots = p.slots;
+    }
     for (int tile : {512, 256, 128}) {
         // small searches: keep every CTA busy
-        if (tile > 128 && (uint64_t)tile * ctx->num_sms * 2 > span) continue;
+        if (tile > 128 && (uint64_t)tile * ctx->num_sms * 2 > span && tile != tune_tile) continue;
+        if (tune_tile && tile != tune_tile) continue;
         const int cand_p2 = next_pow2(p.pool + 2 * tile);
         for (int s = 8; s >= 1; s--) {
+            if (tune_slots && s != tune_slots) continue;
             const size_t sm = popc_smem_bytes(p.k, ds->Wt, s, cand_p2) + 1024;
             if (sm > limit) continue;
             const int occ = popc_max_active(p.k, p.R, sm);
@@ -207,6 +237,8 @@ epi_status choose_path(const epi_dataset *ds, int k, int path, uint64_t rb, uint
         tc = false;
     } else {
         tc = ok && k >= 3;
+        auto it = ds->ctx->tune.find(tune_key(k, ds->n, ds->Wt));
+        if (ok && it != ds->ctx->tune.end() && it->second.path) tc = it->second.path == EPI_PATH_TC;
     }
     return EPI_OK;
 }
@@ -413,6 +445,7 @@ struct BatchItem {
 struct BatchGroup {
     bool tc = false;
     int k = 0, R = 0, tile = 0, slots = 0, cand_p2 = 0, pool = 0, max_wt = 0, grid = 0;
+    int64_t max_n = 0;
     size_t smem = 0;
     std::vector<int> items;
     size_t o_desc = 0, o_tmap = 0, o_ctads = 0, o_ls = 0, o_lr = 0, o_lc = 0;
@@ -425,10 +458,15 @@ bool plan_group_popc(const epi_ctx *ctx, BatchGroup &g)
 {
     const size_t limit = ctx->smem_optin ? ctx->smem_optin : 227 * 1024;
     g.R = popc_default_row_group(g.k);
+    int t_tile = 0, t_slots = 0;
+    auto tn = ctx->tune.find(tune_key(g.k, g.max_n, g.max_wt));
+    if (tn != ctx->tune.end() && tn->second.R) { g.R = tn->second.R; t_tile = tn->second.tile; t_slots = tn->second.slots; }
     int best = -1;
-    for (int tile : {512, 256}) {
+    for (int tile : {512, 256, 128}) {
+        if (t_tile ? tile != t_tile : tile == 128) continue;
         const int cp2 = next_pow2(g.pool + 2 * tile);
         for (int sl = 8; sl >= 1; sl--) {
+            if (t_slots && sl != t_slots) continue;
             const size_t sm = popc_smem_bytes(g.k, g.max_wt, sl, cp2) + 1024;
             if (sm > limit) continue;
             const int occ = popc_max_active(g.k, g.R, sm);
@@ -577,7 +615,9 @@ extern "C" epi_status epi_search_batched(epi_ctx *ctx, epi_dataset *const *dss, 
         st = choose_path(it.ds, it.k, path, 0, total, total, it.tc);
         if (st != EPI_OK) return fail(st, "dataset %d: %s", i, epi_last_error());
         const DevData d = it.ds->dev();
-        it.cost = it.tc ? (double)tc_item_count(d.n, it.k) * (double)(d.Wt / 4)
+        // work estimate for the CTA split: a tensor-core item costs its K stages,
+        // but never less than its epilogue (about 32 stages' worth)
+        it.cost = it.tc ? (double)tc_item_count(d.n, it.k) * (double)std::max(d.Wt / 4, 32)
                         : (double)total * (double)(it.cells / 3) * (double)d.Wt;
     }
     DeviceGuard guard(ctx->device);
@@ -599,6 +639,7 @@ extern "C" epi_status epi_search_batched(epi_ctx *ctx, epi_dataset *const *dss, 
         g.items.push_back(i);
         g.pool = std::max(g.pool, items[i].pool);
         g.max_wt = std::max(g.max_wt, items[i].ds->Wt);
+        g.max_n = std::max(g.max_n, items[i].ds->n);
     }
     for (auto &g : groups) {
         if (g.tc) g.grid = ctx->num_sms;
@@ -721,7 +762,124 @@ extern "C" epi_status epi_search_batched(epi_ctx *ctx, epi_dataset *const *dss, 
     return EPI_OK;
 }
 
+namespace {
+
+// Device time of one popcount pass over ranks [0, r) with a forced shape, or
+// of one whole tensor-core search; < 0 when the shape does not apply.
+double time_pass(epi_dataset *ds, int k, bool tc, int R, int tile, int slots, uint64_t r, uint64_t total)
+{
+    epi_ctx *ctx = ds->ctx;
+    SearchPlan p;
+    p.k = k; p.top_n = 10; p.pool = initial_pool(10); p.rb = 0; p.re = r; p.total = tc ? total : r;
+    p.tc = tc;
+    if (tc) {
+        p.grid = ctx->num_sms;
+    } else {
+        p.tile = tile;
+        p.slots = slots;
+        if (plan_popc(ds, p, R) != EPI_OK || p.tile != tile || p.slots != slots) return -1.0;
+    }
+    void *dout = nullptr;
+    const size_t bytes = 10 * sizeof(epi_result) + 1024;
+    if (cudaMallocAsync(&dout, bytes, ctx->stream) != cudaSuccess) return -1.0;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int32_t *status = nullptr;
+    double ms = -1.0;
+    for (int rep = 0; rep < 2; rep++) {
+        cudaEventRecord(e0, ctx->stream);
+        const epi_status st = queue_search(ds, p, tc ? EPI_PATH_TC : EPI_PATH_POPC, static_cast<epi_result *>(dout),
+                                           nullptr, reinterpret_cast<int32_t *>(static_cast<char *>(dout) + 768), &status);
+        cudaEventRecord(e1, ctx->stream);
+        if (st != EPI_OK || cudaEventSynchronize(e1) != cudaSuccess) { ms = -1.0; break; }
+        float f = 0.0f;
+        cudaEventElapsedTime(&f, e0, e1);
+        ms = rep ? std::min(ms, (double)f) : (double)f;   // the first run also warms up
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFreeAsync(dout, ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
+    return ms;
+}
+
+}  // namespace
+
 extern "C" {
+
+epi_status epi_autotune(epi_dataset *ds, int order, int *out)
+{
+    uint64_t total = 0, re = UINT64_MAX;
+    epi_status st = check_search_args(ds, order, 10, EPI_PATH_AUTO, 0, re, total);
+    if (st != EPI_OK) return st;
+    epi_ctx *ctx = ds->ctx;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(EPI_ECUDA, "cannot select device %d", ctx->device);
+    // probe range: about 16 sub-tiles per resident CTA
+    const uint64_t r = std::min<uint64_t>(total, (uint64_t)ctx->num_sms * 8 * 512 * 16);
+    std::vector<int> Rs;
+    for (int R : {1, 3, 9, 27})
+        if (popc_row_group_ok(order, R)) Rs.push_back(R);
+    epi_ctx::Tune best;
+    best.ms = 1e30;
+    for (int R : Rs)
+        for (int tile : {128, 256, 512})
+            for (int slots : {1, 2, 4, 8}) {
+                const double ms = time_pass(ds, order, false, R, tile, slots, r, total);
+                if (ms > 0 && ms < best.ms) { best.ms = ms; best.R = R; best.tile = tile; best.slots = slots; }
+            }
+    if (best.R == 0) return fail(EPI_EUNSUPPORTED, "no popcount launch shape fits this dataset");
+    best.path = EPI_PATH_POPC;
+    const double popc_full = best.ms * (double)total / (double)r;
+    if (tc_applicable(ds, order, 0, total, total)) {
+        // the tensor path has no rank ranges: time it whole when that is cheap
+        if (popc_full < 4000.0) {
+            const double tc_ms = time_pass(ds, order, true, 0, 0, 0, total, total);
+            if (tc_ms > 0 && tc_ms < popc_full) best.path = EPI_PATH_TC;
+        } else {
+            best.path = EPI_PATH_TC;
+        }
+    }
+    ctx->tune[tune_key(order, ds->n, ds->Wt)] = best;
+    if (out) { out[0] = best.R; out[1] = best.tile; out[2] = best.slots; out[3] = best.path; }
+    return EPI_OK;
+}
+
+epi_status epi_tune_save(const epi_ctx *ctx, const char *path)
+{
+    if (!ctx || !path) return fail(EPI_EINVAL, "NULL argument");
+    FILE *f = fopen(path, "w");
+    if (!f) return fail(EPI_EINVAL, "cannot write %s", path);
+    fprintf(f, "# libepi autotune cache: key R tile slots path ms\n");
+    for (auto &kv : ctx->tune)
+        fprintf(f, "%llu %d %d %d %d %.6f\n", (unsigned long long)kv.first, kv.second.R, kv.second.tile,
+                kv.second.slots, kv.second.path, kv.second.ms);
+    fclose(f);
+    return EPI_OK;
+}
+
+epi_status epi_tune_load(epi_ctx *ctx, const char *path)
+{
+    if (!ctx || !path) return fail(EPI_EINVAL, "NULL argument");
+    FILE *f = fopen(path, "r");
+    if (!f) return fail(EPI_EINVAL, "cannot read %s", path);
+    char line[256];
+    int n = 0;
+    while (fgets(line, sizeof(line), f)) {
+        if (line[0] == '#') continue;
+        unsigned long long key = 0;
+        epi_ctx::Tune t;
+        if (sscanf(line, "%llu %d %d %d %d %lf", &key, &t.R, &t.tile, &t.slots, &t.path, &t.ms) == 6) {
+            const int k = (int)(key >> 48);
+            if (!popc_row_group_ok(k, t.R) || (t.path != EPI_PATH_POPC && t.path != EPI_PATH_TC)) continue;
+            ctx->tune[(uint64_t)key] = t;
+            n++;
+        }
+    }
+    fclose(f);
+    return EPI_OK;
+}
 
 const char *epi_last_error(void) { return g_err.c_str(); }
 

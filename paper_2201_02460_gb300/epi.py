@@ -100,6 +100,12 @@ def load(path: str | None = None):
         lib.epi_score_tables.argtypes = [V, i32, P, i64, P, P]
         lib.epi_kernel_launches.restype = u64
         lib.epi_kernel_launches.argtypes = [V]
+        lib.epi_autotune.restype = i32
+        lib.epi_autotune.argtypes = [V, i32, P]
+        lib.epi_tune_save.restype = i32
+        lib.epi_tune_save.argtypes = [V, C.c_char_p]
+        lib.epi_tune_load.restype = i32
+        lib.epi_tune_load.argtypes = [V, C.c_char_p]
         lib.epi_search_batched.restype = i32
         lib.epi_search_batched.argtypes = [V, P, P, P, i32, i32, P, P, P]
         lib.epi_debug_counts.restype = i32
@@ -277,6 +283,23 @@ def search_async(ds: Dataset, order: int, top_n: int, out_dev, counts_dev, n_out
     cp = C.c_void_p(counts_dev.data_ptr()) if counts_dev is not None else None
     _check(lib.epi_search_async(ds.handle, order, top_n, PATHS[path], C.c_void_p(out_dev.data_ptr()), cp,
                                 C.c_void_p(n_out_dev.data_ptr()), C.c_void_p(status_dev.data_ptr())))
+
+
+def autotune(ds: Dataset, order: int) -> dict:
+    """Time the launch shapes and paths for this dataset's size bucket and
+    keep the fastest in the context (see epi_autotune)."""
+    out = np.zeros(4, dtype=np.int32)
+    _check(load().epi_autotune(ds.handle, order, _np_ptr(out)))
+    return dict(row_group=int(out[0]), tile=int(out[1]), slots=int(out[2]),
+                path={1: "popc", 2: "tc"}.get(int(out[3]), "?"))
+
+
+def tune_save(ctx: Context, path: str):
+    _check(load().epi_tune_save(ctx.handle, path.encode()))
+
+
+def tune_load(ctx: Context, path: str):
+    _check(load().epi_tune_load(ctx.handle, path.encode()))
 
 
 def search_batched(ctx: Context, datasets, orders, top_ns, path: str = "auto",

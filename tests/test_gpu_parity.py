@@ -333,3 +333,49 @@ def test_batched_against_oracle_and_new_graph(epi, ctx):
     res2 = epi.search_batched(ctx, dss, [s[0] for s in specs], [5, 6, 7, 8])
     for r, r_old in zip(res2, res):
         assert (r.records == r_old.records[: len(r)]).all()
+
+
+def test_autotune_choices_and_results(epi, ctx, tmp_path):
+    for k, n, m in [(3, 70, 1500), (4, 26, 2000)]:
+        geno, pheno = random_data(n, m, seed=21 + k)
+        ds = epi.Dataset(ctx, geno, pheno)
+        before = epi.search(ds, k, 40)
+        t = epi.autotune(ds, k)
+        assert t["row_group"] in ((9,) if k == 3 else (9, 27))
+        assert t["tile"] in (128, 256, 512) and t["slots"] in (1, 2, 4, 8) and t["path"] in ("popc", "tc")
+        after = epi.search(ds, k, 40)
+        assert (after.records["snp"] == before.records["snp"]).all() and (after.mi == before.mi).all()
+        forced = epi.search(ds, k, 40, path="popc")
+        assert (forced.combs == before.combs).all()
+    f = tmp_path / "tune.txt"
+    epi.tune_save(ctx, str(f))
+    lines = [x for x in f.read_text().splitlines() if not x.startswith("#")]
+    assert len(lines) >= 2
+    ctx2 = epi.Context(0)
+    epi.tune_load(ctx2, str(f))
+    epi.tune_save(ctx2, str(tmp_path / "again.txt"))
+    assert (tmp_path / "again.txt").read_text() == f.read_text()
+
+
+def test_batched_config4_shapes(epi, ctx):
+    """The 64 seeded dataset shapes of the batched configuration (orders
+    2-4, 1000-16000 samples, case fraction 0.3-0.7) at reduced SNP counts:
+    the batch equals the per-dataset searches, and a sample equals the
+    oracle."""
+    from paper_2201_02460_gb300 import synth
+    specs = synth.batch_specs()
+    dss, orders, tops, raw = [], [], [], []
+    for sp in specs:
+        n = max(sp["order"] + 2, sp["n_snps"] // {2: 10, 3: 25, 4: 60}[sp["order"]])
+        d = synth.make_dataset(n, sp["n_cases"], sp["n_controls"], seed=sp["seed"], maf_lo=sp["maf_lo"])
+        dss.append(epi.Dataset(ctx, d.geno, d.pheno))
+        orders.append(sp["order"])
+        tops.append(sp["top_n"])
+        raw.append(d)
+    res = epi.search_batched(ctx, dss, orders, tops)
+    for i, (ds, k, t, r) in enumerate(zip(dss, orders, tops, res)):
+        one = epi.search(ds, k, t)
+        assert (r.records == one.records).all(), i
+        if i % 8 == 0:
+            oc, om, _ = O.search(raw[i].geno, raw[i].pheno, k, t)
+            _check_result(r, raw[i].geno, raw[i].pheno, oc, om)
