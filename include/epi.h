@@ -210,6 +210,139 @@ epi_status epi_search_static(const uint8_t *geno_dev, const uint8_t *pheno_dev, 
                              epi_result *out_dev, uint32_t *counts_dev, int32_t *n_out_dev,
                              int32_t *status_dev, void *cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Learned proposer for orders where the exhaustive search is out of reach.
+ * The paper has no counterpart (it searches exhaustively); these calls rank
+ * candidate 5-sets by a small network fed with lower-order scores, and the
+ * ranked candidates are then scored exactly with epi_tables and
+ * epi_score_tables.
+ * ------------------------------------------------------------------------ */
+
+/* Every combination's single-precision MI (Eq. 1-3), by lexicographic rank:
+ * out_dev is device memory of C(n_snps, order) floats.  Orders 1..5. */
+epi_status epi_score_all(epi_dataset *ds, int order, float *out_dev);
+
+/* Combinations of `count` lexicographic ranks (device [count] uint64, each
+ * below C(n_snps, order)) into device combs [count][order]. */
+epi_status epi_unrank(epi_dataset *ds, int order, const uint64_t *ranks, int64_t count, uint32_t *combs);
+
+/* The 25 proposer features of `count` 5-sets: ln(MI + 1e-7) of the 5 SNPs,
+ * the 10 pairs and the 10 triples of each set, each group sorted descending.
+ * s1/s2/s3: device score tables of orders 1, 2, 3 from epi_score_all;
+ * combs: device [count][5] strictly increasing SNP indices; X: device
+ * [count][25] floats.  Queued on the context's stream. */
+epi_status epi_features5(epi_dataset *ds, const float *s1, const float *s2, const float *s3, const uint32_t *combs,
+                         int64_t count, float *X);
+
+/* Candidate 5-sets made of one of n_triples triples (device [n_triples][3],
+ * strictly increasing) and any two other SNPs: candidate index
+ * t * C(n-3, 2) + r is triple t with the r-th pair (lexicographic) of the
+ * remaining SNPs; writes candidates [first, first + count) to combs (device
+ * [count][5], sorted).  With s3 (the order-3 table of epi_score_all) and keep
+ * (device [count] bytes) both given, keep[i] = 1 exactly when candidate i's
+ * triple is the best of the set's ten triples by (score desc, rank asc), so
+ * that a set holding several listed triples is kept once; both NULL skips
+ * this.  Queued on the context's stream. */
+epi_status epi_candidates5(epi_dataset *ds, const uint32_t *triples, int64_t n_triples, int64_t first,
+                           int64_t count, uint32_t *combs, const float *s3, uint8_t *keep);
+
+/* out[i] = table[lexicographic rank of combs[i]] for an order-`order` table
+ * of epi_score_all (device arrays; combs [count][order] strictly increasing). */
+epi_status epi_lookup(epi_dataset *ds, int order, const float *table, const uint32_t *combs, int64_t count,
+                      float *out);
+
+/* The k largest of `count` device floats (ties: smaller index first),
+ * skipping entries whose keep byte is 0 when keep (device [count]) is given:
+ * device outputs out_scores [k], out_index [k], n_out one int32.  k in
+ * 1..4096.  NaN scores are never selected. */
+epi_status epi_topk(epi_ctx *ctx, const float *scores, const uint8_t *keep, int64_t count, int k, float *out_scores,
+                    uint64_t *out_index, int32_t *n_out);
+
+/* The ranking without a network, for comparison: the sum of the ten
+ * three-way features of each row of X (device [count][25]) into device out. */
+epi_status epi_heuristic5(epi_ctx *ctx, const float *X_dev, int64_t count, float *out_dev);
+
+/* A multilayer perceptron n_in -> hidden -> hidden -> 1 with ReLU, BF16
+ * weights and activations, FP32 accumulation and FP32 master weights for the
+ * optimiser; parameters in the order W1 [hidden][n_in], b1, W2
+ * [hidden][hidden], b2, W3 [hidden], b3.  He-uniform initialisation from
+ * `seed`.  Work runs on the context's stream. */
+typedef struct epi_mlp epi_mlp;
+epi_status epi_mlp_create(epi_ctx *ctx, int n_in, int hidden, uint64_t seed, epi_mlp **out);
+void epi_mlp_destroy(epi_mlp *net);
+int64_t epi_mlp_num_params(const epi_mlp *net);
+int epi_mlp_num_inputs(const epi_mlp *net);
+/* FP32 master parameters to / from host memory (epi_mlp_num_params floats);
+ * setting them also resets the optimiser's step count. */
+epi_status epi_mlp_get_params(const epi_mlp *net, float *host);
+epi_status epi_mlp_set_params(epi_mlp *net, const float *host);
+/* Input normalisation applied before the first layer: feature f enters as
+ * (x_f - shift[f]) * scale[f] (host arrays of n_in floats; defaults 0 and 1).
+ * Saved with the network by the bindings; not changed by training steps. */
+epi_status epi_mlp_set_input_norm(epi_mlp *net, const float *shift_host, const float *scale_host);
+epi_status epi_mlp_get_input_norm(const epi_mlp *net, float *shift_host, float *scale_host);
+/* Predictions for `rows` device inputs X [rows][n_in] into device y [rows]
+ * (any number of rows: processed in slices of bounded activation memory). */
+epi_status epi_mlp_forward(epi_mlp *net, const float *X_dev, int64_t rows, float *y_dev);
+/* Gradients of the mean squared error against device targets t [rows] into
+ * host grad [num_params] (may be NULL); host loss (may be NULL). */
+epi_status epi_mlp_gradients(epi_mlp *net, const float *X_dev, const float *t_dev, int64_t rows, float *grad_host,
+                             float *loss_host);
+/* One AdamW step (beta 0.9 / 0.999, eps 1e-8, decoupled weight decay wd) on
+ * the mean squared error of the batch; host loss before the step (may be NULL). */
+epi_status epi_mlp_train_step(epi_mlp *net, const float *X_dev, const float *t_dev, int64_t rows, float lr,
+                              float wd, float *loss_host);
+
+/* Order-5 proposal search.  The exhaustive order-1..3 scores of the dataset
+ * are computed (popcount path); the top_triples best triples by order-3 MI
+ * (ties by rank) are each joined with every pair of other SNPs; every distinct
+ * 5-set of that space (a set holding several of the triples is taken once) is
+ * ranked by `net` from its 25 features (epi_features5), or, with net NULL, by
+ * the sum of its ten three-way log-scores (epi_heuristic5); the best `budget`
+ * are counted and scored exactly (Section 2.2 tables, Eq. 1-3 in FP64), and
+ * the best top_n by exact MI (ties by lexicographic rank) are written to host
+ * out [top_n] (order 5) with their tables in host counts [top_n][2][243]
+ * (counts may be NULL).  chunk = candidates ranked per pass (0: 4Mi).  The
+ * paper has no counterpart: it searches exhaustively; this call is an
+ * approximation whose result is exact only for the sets it proposes. */
+typedef struct epi_proposer_opts {
+    int top_triples;   /* 1..4096 */
+    int budget;        /* proposals re-scored exactly, 1..4096 */
+    int top_n;         /* 1..budget */
+    int64_t chunk;
+} epi_proposer_opts;
+typedef struct epi_proposer_stats {
+    uint64_t candidates;   /* top_triples * C(n_snps - 3, 2) */
+    uint64_t kept;         /* distinct sets among them (ranked) */
+    uint64_t proposals;    /* sets re-scored exactly */
+    double ms_lower, ms_rank, ms_rescore;   /* wall time of the three stages */
+} epi_proposer_stats;
+epi_status epi_proposer_search(epi_dataset *ds, epi_mlp *net, const epi_proposer_opts *opts, epi_result *out,
+                               uint32_t *counts, int32_t *n_out, epi_proposer_stats *stats);
+
+/* Fits `net` (25 inputs) to rank order-5 sets: on each dataset (C(n_snps, 5)
+ * at most 2^32: the labels come from the exhaustive order-5 scores) the
+ * space of epi_proposer_search with the given top_triples is built, each
+ * distinct set labelled by its exact MI (see `target`); inputs are
+ * standardised (the normalisation is stored in the network), and `epochs` passes of
+ * mini-batch AdamW (cosine decay from lr to lr / 20, weight decay wd) are
+ * run; tail_fraction of each batch is drawn from the 4096 best-labelled sets
+ * of each dataset, the rest uniformly, from a counter-based generator seeded
+ * by `seed`.  Host epoch_loss [epochs] (may be NULL) receives the mean
+ * sampled batch loss of each epoch.  The paper has no counterpart. */
+typedef struct epi_train_opts {
+    int top_triples;
+    int epochs;
+    int batch;           /* 1..2^20 */
+    float lr, wd;
+    float tail_fraction; /* 0..1 */
+    uint64_t seed;
+    int target;          /* 0: standardised ln(MI + 1e-7); 1: 1 for the 4096
+                            best-labelled sets of each dataset, else 0 */
+} epi_train_opts;
+epi_status epi_proposer_train(epi_mlp *net, epi_dataset *const *datasets, int n_ds, const epi_train_opts *opts,
+                              float *epoch_loss);
+
 /* Timing of the dominant counting kernel.  After epi_profile_begin, every
  * launch of a search's counting kernel is bracketed by CUDA events on the
  * context's stream; epi_profile_end waits for those events and returns their

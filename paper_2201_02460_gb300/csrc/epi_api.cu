@@ -161,6 +161,7 @@ uint64_t tune_key(int k, int64_t n, int32_t wt)
 struct SearchPlan {
     int k = 0, top_n = 0, pool = 0, tile = 0, slots = 0, cand_p2 = 0, grid = 0, R = 0;
     bool tc = false;
+    float *all_scores = nullptr;   // optional: every combination's score (popcount path)
     size_t smem = 0;
     uint64_t rb = 0, re = 0, total = 0;
 };
@@ -326,7 +327,7 @@ epi_status queue_search(epi_dataset *ds, const SearchPlan &p, int path, epi_resu
         ctx->launches += 1;   // item table
     } else {
         CK(launch_popc_search(d, p.k, p.R, p.rb, p.re, p.tile, p.pool, p.slots, p.cand_p2, thr, ls, lr, lc, p.grid,
-                              p.smem, ctx->stream));
+                              p.smem, ctx->stream, p.all_scores));
     }
     if (ev1) CK(cudaEventRecord(ev1, ctx->stream));
     CK(launch_merge(ls, lr, lc, p.grid, p.pool, p.pool, cs, cr, cn, ctx->stream));
@@ -882,6 +883,117 @@ epi_status epi_tune_load(epi_ctx *ctx, const char *path)
 }
 
 const char *epi_last_error(void) { return g_err.c_str(); }
+
+epi_status epi_score_all(epi_dataset *ds, int order, float *out_dev)
+{
+    uint64_t total = 0, re = UINT64_MAX;
+    epi_status st = check_search_args(ds, order, 1, EPI_PATH_POPC, 0, re, total);
+    if (st != EPI_OK) return st;
+    epi_ctx *ctx = ds->ctx;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(EPI_ECUDA, "cannot select device %d", ctx->device);
+    if (!out_dev || !is_device_ptr(out_dev, ctx->device))
+        return fail(EPI_EINVAL, "epi_score_all: out must be device memory of device %d", ctx->device);
+    SearchPlan p;
+    p.k = order; p.top_n = 1; p.pool = initial_pool(1); p.rb = 0; p.re = total; p.total = total;
+    st = plan_popc(ds, p);
+    if (st != EPI_OK) return st;
+    p.all_scores = out_dev;
+    void *dout = nullptr;
+    CK(cudaMallocAsync(&dout, 1024, ctx->stream));
+    int32_t *status = nullptr;
+    st = queue_search(ds, p, EPI_PATH_POPC, static_cast<epi_result *>(dout), nullptr,
+                      reinterpret_cast<int32_t *>(static_cast<char *>(dout) + 512), &status);
+    cudaFreeAsync(dout, ctx->stream);
+    if (st != EPI_OK) return st;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return EPI_OK;
+}
+
+epi_status epi_unrank(epi_dataset *ds, int order, const uint64_t *ranks, int64_t count, uint32_t *combs)
+{
+    if (!ds || !ranks || !combs || count < 0) return fail(EPI_EINVAL, "epi_unrank: bad argument");
+    if (order < 1 || order > EPI_MAX_ORDER || order > ds->n) return fail(EPI_EINVAL, "epi_unrank: bad order");
+    if (count == 0) return EPI_OK;
+    epi_ctx *ctx = ds->ctx;
+    DeviceGuard g(ctx->device);
+    CK(launch_unrank(ds->dev(), order, ranks, count, combs, ctx->stream));
+    ctx->launches += 1;
+    return EPI_OK;
+}
+
+epi_status epi_features5(epi_dataset *ds, const float *s1, const float *s2, const float *s3, const uint32_t *combs,
+                         int64_t count, float *X)
+{
+    if (!ds || !s1 || !s2 || !s3 || !combs || !X || count < 0) return fail(EPI_EINVAL, "epi_features5: bad argument");
+    if (ds->n < 5) return fail(EPI_EINVAL, "epi_features5: needs at least 5 SNPs");
+    if (count == 0) return EPI_OK;
+    epi_ctx *ctx = ds->ctx;
+    DeviceGuard g(ctx->device);
+    CK(launch_features5(ds->dev(), s1, s2, s3, combs, count, X, ctx->stream));
+    ctx->launches += 1;
+    return EPI_OK;
+}
+
+epi_status epi_candidates5(epi_dataset *ds, const uint32_t *triples, int64_t n_triples, int64_t first, int64_t count,
+                           uint32_t *combs, const float *s3, uint8_t *keep)
+{
+    if ((s3 == nullptr) != (keep == nullptr)) return fail(EPI_EINVAL, "epi_candidates5: give both s3 and keep, or neither");
+    if (!ds || !triples || !combs || first < 0 || count < 0) return fail(EPI_EINVAL, "epi_candidates5: bad argument");
+    const int64_t rest = ds->n - 3;
+    if (rest < 2) return fail(EPI_EINVAL, "epi_candidates5: needs at least 5 SNPs");
+    const int64_t per = rest * (rest - 1) / 2;
+    if (first + count > n_triples * per) return fail(EPI_EINVAL, "epi_candidates5: range beyond the candidate space");
+    if (count == 0) return EPI_OK;
+    epi_ctx *ctx = ds->ctx;
+    DeviceGuard g(ctx->device);
+    CK(launch_candidates5(ds->dev(), triples, first, count, combs, s3, keep, ctx->stream));
+    ctx->launches += 1;
+    return EPI_OK;
+}
+
+epi_status epi_lookup(epi_dataset *ds, int order, const float *table, const uint32_t *combs, int64_t count, float *out)
+{
+    if (!ds || !table || !combs || !out || count < 0) return fail(EPI_EINVAL, "epi_lookup: bad argument");
+    if (order < 1 || order > EPI_MAX_ORDER || order > ds->n) return fail(EPI_EINVAL, "epi_lookup: bad order");
+    if (count == 0) return EPI_OK;
+    epi_ctx *ctx = ds->ctx;
+    DeviceGuard g(ctx->device);
+    CK(launch_lookup(ds->dev(), order, table, combs, count, out, ctx->stream));
+    ctx->launches += 1;
+    return EPI_OK;
+}
+
+epi_status epi_topk(epi_ctx *ctx, const float *scores, const uint8_t *keep, int64_t count, int k, float *out_scores,
+                    uint64_t *out_index, int32_t *n_out)
+{
+    if (!ctx || !scores || !out_scores || !out_index || !n_out || count < 0) return fail(EPI_EINVAL, "epi_topk: bad argument");
+    if (k < 1 || k > 4096) return fail(EPI_EINVAL, "epi_topk: k outside 1..4096");
+    DeviceGuard g(ctx->device);
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((count + 65535) / 65536, (int64_t)ctx->num_sms * 2));
+    Arena a;
+    const size_t o_s = a.take<float>((size_t)blocks * k);
+    const size_t o_i = a.take<uint64_t>((size_t)blocks * k);
+    const size_t o_n = a.take<int32_t>((size_t)blocks);
+    epi_status st = ensure_scratch(ctx, a.off);
+    if (st != EPI_OK) return st;
+    char *base = static_cast<char *>(ctx->scratch);
+    CK(launch_topk(scores, keep, count, k, reinterpret_cast<float *>(base + o_s), reinterpret_cast<uint64_t *>(base + o_i),
+                   reinterpret_cast<int32_t *>(base + o_n), blocks, out_scores, out_index, n_out, ctx->stream));
+    ctx->launches += 2;
+    return EPI_OK;
+}
+
+}  // extern "C"
+
+cudaStream_t epi_ctx_stream(const epi_ctx *ctx) { return ctx->stream; }
+int epi_ctx_device(const epi_ctx *ctx) { return ctx->device; }
+int epi_ctx_num_sms(const epi_ctx *ctx) { return ctx->num_sms; }
+void epi_ctx_count_launches(epi_ctx *ctx, int n) { ctx->launches += (uint64_t)n; }
+epi_ctx *epi_dataset_ctx(const epi_dataset *ds) { return ds->ctx; }
+epi::DevData epi_dataset_dev(const epi_dataset *ds) { return ds->dev(); }
+
+extern "C" {
 
 epi_status epi_create(int device, void *cuda_stream, epi_ctx **out)
 {

@@ -38,7 +38,8 @@ size_t popc_smem_bytes(int k, int32_t Wt, int slots, int cand_p2);
 int popc_max_active(int k, int R, size_t smem);
 cudaError_t launch_popc_search(const DevData &d, int k, int R, uint64_t rank_begin, uint64_t rank_end, int tile,
                                int pool, int slots, int cand_p2, uint32_t *global_thr, float *list_score,
-                               uint64_t *list_rank, int32_t *list_count, int grid, size_t smem, cudaStream_t st);
+                               uint64_t *list_rank, int32_t *list_count, int grid, size_t smem, cudaStream_t st,
+                               float *all_scores = nullptr);
 // batched: one launch over several datasets of order k (descriptors in device memory)
 size_t popc_ds_bytes();
 void popc_fill_ds(void *dst, const DevData &d, uint64_t rank_begin, uint64_t rank_end, int cta_begin, int cta_count,
@@ -67,9 +68,22 @@ cudaError_t tc_fill_batch_entry(void *ds_host, void *tmap_host, const DevData &d
 cudaError_t launch_tc_batch(const void *ds_dev, const int32_t *cta_ds_dev, int k, int pool, float *list_score,
                             uint64_t *list_rank, int32_t *list_count, int32_t *status, int grid, cudaStream_t st);
 
+// epi_learn.cu (proposer)
+cudaError_t launch_features5(const DevData &d, const float *s1, const float *s2, const float *s3, const uint32_t *combs,
+                             int64_t count, float *X, cudaStream_t st);
+cudaError_t launch_candidates5(const DevData &d, const uint32_t *triples, int64_t first, int64_t count,
+                               uint32_t *combs, const float *s3, uint8_t *keep, cudaStream_t st);
+cudaError_t launch_candidates5_at(const DevData &d, const uint32_t *triples, const uint64_t *idx, int64_t count,
+                                  uint32_t *combs, cudaStream_t st);
+cudaError_t launch_lookup(const DevData &d, int k, const float *table, const uint32_t *combs, int64_t count,
+                          float *out, cudaStream_t st);
+cudaError_t launch_topk(const float *scores, const uint8_t *keep, int64_t count, int k, float *blk_s, uint64_t *blk_i,
+                        int32_t *blk_n, int blocks, float *out_s, uint64_t *out_i, int32_t *out_n, cudaStream_t st);
+
 // epi_select.cu
+// floor: below every score to merge (the search's scores are >= 0)
 cudaError_t launch_merge(const float *ls, const uint64_t *lr, const int32_t *lc, int nlists, int stride, int pool,
-                         float *out_s, uint64_t *out_r, int32_t *out_n, cudaStream_t st);
+                         float *out_s, uint64_t *out_r, int32_t *out_n, cudaStream_t st, float floor = -1.0f);
 cudaError_t launch_rescore(const DevData &d, int k, int pool, const uint64_t *cand_r, const int32_t *cand_n,
                            uint32_t *counts, double *mi64, int32_t *combs, cudaStream_t st);
 cudaError_t launch_finalize(const DevData &d, int k, int top_n, int pool, const float *cand_s, const uint64_t *cand_r,
@@ -78,8 +92,20 @@ cudaError_t launch_finalize(const DevData &d, int k, int top_n, int pool, const 
                             int32_t *n_out, int32_t *status, cudaStream_t st);
 cudaError_t launch_tables(const DevData &d, int k, const uint32_t *combs, int64_t count, uint32_t *out, int num_sms,
                           cudaStream_t st);
+cudaError_t launch_unrank(const DevData &d, int k, const uint64_t *ranks, int64_t count, uint32_t *combs,
+                          cudaStream_t st);
 cudaError_t launch_publish_status(const int32_t *bits, int32_t *code, cudaStream_t st);
 cudaError_t launch_score_tables(const DevData &d, int k, const uint32_t *tabs, int64_t count, float *f32, double *f64,
                                 int num_sms, cudaStream_t st);
 
 }  // namespace epi
+
+// context accessors for the other translation units (epi_api.cu)
+struct epi_ctx;
+struct epi_dataset;
+cudaStream_t epi_ctx_stream(const epi_ctx *ctx);
+int epi_ctx_device(const epi_ctx *ctx);
+int epi_ctx_num_sms(const epi_ctx *ctx);
+void epi_ctx_count_launches(epi_ctx *ctx, int n);
+epi_ctx *epi_dataset_ctx(const epi_dataset *ds);
+epi::DevData epi_dataset_dev(const epi_dataset *ds);

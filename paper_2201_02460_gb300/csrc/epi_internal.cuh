@@ -167,6 +167,22 @@ __device__ __forceinline__ float cell_terms_f32(uint32_t a, uint32_t b, const Mi
     return class_term_f32(a, fx, rx, c.fm1, c.inv_m1, c) + class_term_f32(b, fx, rx, c.fm0, c.inv_m0, c);
 }
 
+// Compensated running sum of non-negative terms (Neumaier's variant of
+// Kahan summation): the exact rounding error of each addition (Fast2Sum,
+// larger operand first) is carried in c, so a long sum of cell terms keeps
+// the per-term accuracy instead of growing with the number of cells.
+struct SumF32 {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x)
+    {
+        const float big = fmaxf(s, x), small = fminf(s, x);
+        const float t = big + small;
+        c += small - (t - big);
+        s = t;
+    }
+    __device__ __forceinline__ float value() const { return s + c; }
+};
+
 __device__ __forceinline__ double mi_term_f64(uint32_t n, uint32_t nx, int64_t my, int64_t m)
 {
     if (nx == 0 || my == 0) return 0.0;

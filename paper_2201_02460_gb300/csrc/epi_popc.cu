@@ -50,6 +50,7 @@ struct PopcParams {
     float *list_score;              // [grid][pool]
     uint64_t *list_rank;            // [grid][pool]
     int32_t *list_count;            // [grid]
+    float *all_scores;              // optional: every score, [rank - rank_begin] (single dataset)
 };
 
 struct SlotInfo {
@@ -116,7 +117,7 @@ __device__ __forceinline__ float score_popc(const uint32_t *__restrict__ pre, co
     constexpr int PR = ipow3(K - 1);
     constexpr int G = PR / R;
     static_assert(PR % R == 0, "row group must divide the prefix rows");
-    float acc = 0.0f;
+    SumF32 acc;
 #pragma unroll 1
     for (int grp = 0; grp < G; grp++) {
         const uint32_t *pg = pre + grp * R * d.Wt;
@@ -127,12 +128,12 @@ __device__ __forceinline__ float score_popc(const uint32_t *__restrict__ pre, co
         for (int r = 0; r < R; r++) {
             const uint32_t t1 = tot[(grp * R + r) * 2 + 0];
             const uint32_t t0 = tot[(grp * R + r) * 2 + 1];
-            acc += cell_terms_f32(a0[r], b0[r], mc);
-            acc += cell_terms_f32(a1[r], b1[r], mc);
-            acc += cell_terms_f32(t1 - a0[r] - a1[r], t0 - b0[r] - b1[r], mc);
+            acc.add(cell_terms_f32(a0[r], b0[r], mc));
+            acc.add(cell_terms_f32(a1[r], b1[r], mc));
+            acc.add(cell_terms_f32(t1 - a0[r] - a1[r], t0 - b0[r] - b1[r], mc));
         }
     }
-    return acc * mc.inv_m;
+    return __fdiv_rn(acc.value(), mc.fm);
 }
 
 // Sort the live list + buffer, keep the best `pool`, refresh the threshold.
@@ -294,6 +295,7 @@ __global__ void __launch_bounds__(128) popc_search_kernel(PopcParams P)
             const int32_t j = slot[s].s_last + 1 + (int32_t)(f - slot[s].base);
             const float score = score_popc<K, R>(pre + (size_t)s * slot_words, tot + s * PR * 2,
                                                  d.masks + (int64_t)j * 3 * d.Wt, d, mc);
+            if (P.all_scores) P.all_scores[f - (int64_t)D.rank_begin] = score;
             if (score >= thr) {
                 const int pos = list_len + atomicAdd(&S.nbuf, 1);
                 sc[pos] = score;
@@ -397,9 +399,11 @@ static cudaError_t launch_dispatch(const PopcParams &p, int k, int R, int grid, 
 
 cudaError_t launch_popc_search(const DevData &d, int k, int R, uint64_t rank_begin, uint64_t rank_end, int tile,
                                int pool, int slots, int cand_p2, uint32_t *global_thr, float *list_score,
-                               uint64_t *list_rank, int32_t *list_count, int grid, size_t smem, cudaStream_t st)
+                               uint64_t *list_rank, int32_t *list_count, int grid, size_t smem, cudaStream_t st,
+                               float *all_scores)
 {
     PopcParams p;
+    p.all_scores = all_scores;
     p.one.d = d;
     p.one.rank_begin = rank_begin;
     p.one.rank_end = rank_end;
@@ -438,6 +442,7 @@ cudaError_t launch_popc_batch(const void *ds_dev, const int32_t *cta_ds_dev, int
                               int32_t *list_count, int grid, size_t smem, cudaStream_t st)
 {
     PopcParams p;
+    p.all_scores = nullptr;
     p.one = PopcDs();
     p.many = static_cast<const PopcDs *>(ds_dev);
     p.cta_ds = cta_ds_dev;

@@ -22,13 +22,14 @@ struct MergeState {
 __global__ void __launch_bounds__(1024) merge_lists_kernel(const float *__restrict__ ls, const uint64_t *__restrict__ lr,
                                                            const int32_t *__restrict__ lc, int nlists, int stride,
                                                            int pool, int cand_p2, float *__restrict__ out_s,
-                                                           uint64_t *__restrict__ out_r, int32_t *__restrict__ out_n)
+                                                           uint64_t *__restrict__ out_r, int32_t *__restrict__ out_n,
+                                                           float floor)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t *rk = reinterpret_cast<uint64_t *>(smem);
     float *sc = reinterpret_cast<float *>(rk + cand_p2);
     __shared__ MergeState S;
-    if (threadIdx.x == 0) { S.list_len = 0; S.nbuf = 0; S.thr = -1.0f; }
+    if (threadIdx.x == 0) { S.list_len = 0; S.nbuf = 0; S.thr = floor; }
     __syncthreads();
     const int64_t total = (int64_t)nlists * stride;
     for (int64_t base = 0; base < total; base += blockDim.x) {
@@ -50,7 +51,7 @@ __global__ void __launch_bounds__(1024) merge_lists_kernel(const float *__restri
         if (S.nbuf > (int)blockDim.x || (last && S.nbuf > 0)) {
             const int live = S.list_len + S.nbuf;
             const int p2 = next_pow2(live < 2 ? 2 : live);
-            for (int i = live + threadIdx.x; i < p2; i += blockDim.x) { sc[i] = -1.0f; rk[i] = ~0ull; }
+            for (int i = live + threadIdx.x; i < p2; i += blockDim.x) { sc[i] = floor; rk[i] = ~0ull; }
             __syncthreads();
             block_sort_cands(sc, rk, p2);
             if (threadIdx.x == 0) {
@@ -109,9 +110,9 @@ __device__ inline double table_mi_f64(const DevData &d, const uint32_t *ct, int 
 __device__ inline float table_mi_f32(const DevData &d, const uint32_t *ct, int cells)
 {
     const MiConstF32 mc = make_mi_const(d.m, d.m1, d.m0);
-    float acc = 0.0f;
-    for (int x = 0; x < cells; x++) acc += cell_terms_f32(ct[x], ct[cells + x], mc);
-    return acc * mc.inv_m;
+    SumF32 acc;
+    for (int x = 0; x < cells; x++) acc.add(cell_terms_f32(ct[x], ct[cells + x], mc));
+    return __fdiv_rn(acc.value(), mc.fm);
 }
 
 __global__ void __launch_bounds__(256) rescore_kernel(DevData d, int k, const uint64_t *__restrict__ cand_rank,
@@ -254,17 +255,36 @@ cudaError_t launch_publish_status(const int32_t *bits, int32_t *code, cudaStream
     return cudaGetLastError();
 }
 
+__global__ void unrank_kernel(DevData d, int k, const uint64_t *__restrict__ ranks, int64_t count,
+                              uint32_t *__restrict__ combs)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t c[EPI_MAX_ORDER];
+        unrank_lex(d.binom, d.n, k, ranks[i], c);
+        for (int t = 0; t < k; t++) combs[i * k + t] = (uint32_t)c[t];
+    }
+}
+
+cudaError_t launch_unrank(const DevData &d, int k, const uint64_t *ranks, int64_t count, uint32_t *combs,
+                          cudaStream_t st)
+{
+    int64_t g = (count + 255) / 256;
+    if (g > 4096) g = 4096;
+    unrank_kernel<<<(unsigned)(g < 1 ? 1 : g), 256, 0, st>>>(d, k, ranks, count, combs);
+    return cudaGetLastError();
+}
+
 size_t merge_smem_bytes(int cand_p2) { return (size_t)cand_p2 * 12; }
 size_t finalize_smem_bytes(int pool) { return (size_t)next_pow2(pool < 2 ? 2 : pool) * 20; }
 
 cudaError_t launch_merge(const float *ls, const uint64_t *lr, const int32_t *lc, int nlists, int stride, int pool,
-                         float *out_s, uint64_t *out_r, int32_t *out_n, cudaStream_t st)
+                         float *out_s, uint64_t *out_r, int32_t *out_n, cudaStream_t st, float floor)
 {
     const int cand_p2 = next_pow2(pool + 2 * 1024);
     const size_t smem = merge_smem_bytes(cand_p2);
     cudaError_t e = cudaFuncSetAttribute(merge_lists_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    merge_lists_kernel<<<1, 1024, smem, st>>>(ls, lr, lc, nlists, stride, pool, cand_p2, out_s, out_r, out_n);
+    merge_lists_kernel<<<1, 1024, smem, st>>>(ls, lr, lc, nlists, stride, pool, cand_p2, out_s, out_r, out_n, floor);
     return cudaGetLastError();
 }
 

@@ -741,7 +741,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                                                   f2u_exact(fa2), f2u_exact(fb2), mc);
                         e = seg_sum<kPR>(e, pos);
                         if (l == leader) {
-                            const float score = e * mc.inv_m;
+                            const float score = __fdiv_rn(e, mc.fm);
                             if (score >= thr) {
                                 uint64_t rk_sum = 0;
 #pragma unroll

@@ -64,6 +64,20 @@ def exported_names() -> list[str]:
                                  text, flags=re.M)))
 
 
+class ProposerOpts(C.Structure):
+    _fields_ = [("top_triples", C.c_int), ("budget", C.c_int), ("top_n", C.c_int), ("chunk", C.c_int64)]
+
+
+class ProposerStats(C.Structure):
+    _fields_ = [("candidates", C.c_uint64), ("kept", C.c_uint64), ("proposals", C.c_uint64),
+                ("ms_lower", C.c_double), ("ms_rank", C.c_double), ("ms_rescore", C.c_double)]
+
+
+class TrainOpts(C.Structure):
+    _fields_ = [("top_triples", C.c_int), ("epochs", C.c_int), ("batch", C.c_int), ("lr", C.c_float),
+                ("wd", C.c_float), ("tail_fraction", C.c_float), ("seed", C.c_uint64), ("target", C.c_int)]
+
+
 def load(path: str | None = None):
     """Load libepi (raises if it was not built)."""
     global _lib
@@ -100,6 +114,46 @@ def load(path: str | None = None):
         lib.epi_score_tables.argtypes = [V, i32, P, i64, P, P]
         lib.epi_kernel_launches.restype = u64
         lib.epi_kernel_launches.argtypes = [V]
+        lib.epi_score_all.restype = i32
+        lib.epi_score_all.argtypes = [V, i32, P]
+        lib.epi_unrank.restype = i32
+        lib.epi_unrank.argtypes = [V, i32, P, i64, P]
+        lib.epi_features5.restype = i32
+        lib.epi_features5.argtypes = [V, P, P, P, P, i64, P]
+        lib.epi_candidates5.restype = i32
+        lib.epi_candidates5.argtypes = [V, P, i64, i64, i64, P, P, P]
+        lib.epi_lookup.restype = i32
+        lib.epi_lookup.argtypes = [V, i32, P, P, i64, P]
+        lib.epi_topk.restype = i32
+        lib.epi_topk.argtypes = [V, P, P, i64, i32, P, P, P]
+        lib.epi_heuristic5.restype = i32
+        lib.epi_heuristic5.argtypes = [V, P, i64, P]
+        lib.epi_mlp_create.restype = i32
+        lib.epi_mlp_create.argtypes = [V, i32, i32, u64, C.POINTER(V)]
+        lib.epi_mlp_destroy.restype = None
+        lib.epi_mlp_destroy.argtypes = [V]
+        lib.epi_mlp_num_params.restype = i64
+        lib.epi_mlp_num_params.argtypes = [V]
+        lib.epi_mlp_get_params.restype = i32
+        lib.epi_mlp_get_params.argtypes = [V, P]
+        lib.epi_mlp_set_params.restype = i32
+        lib.epi_mlp_set_params.argtypes = [V, P]
+        lib.epi_mlp_forward.restype = i32
+        lib.epi_mlp_forward.argtypes = [V, P, i64, P]
+        lib.epi_mlp_gradients.restype = i32
+        lib.epi_mlp_gradients.argtypes = [V, P, P, i64, P, P]
+        lib.epi_mlp_train_step.restype = i32
+        lib.epi_mlp_train_step.argtypes = [V, P, P, i64, C.c_float, C.c_float, P]
+        lib.epi_mlp_num_inputs.restype = i32
+        lib.epi_mlp_num_inputs.argtypes = [V]
+        lib.epi_mlp_set_input_norm.restype = i32
+        lib.epi_mlp_set_input_norm.argtypes = [V, P, P]
+        lib.epi_mlp_get_input_norm.restype = i32
+        lib.epi_mlp_get_input_norm.argtypes = [V, P, P]
+        lib.epi_proposer_search.restype = i32
+        lib.epi_proposer_search.argtypes = [V, V, C.POINTER(ProposerOpts), P, P, P, C.POINTER(ProposerStats)]
+        lib.epi_proposer_train.restype = i32
+        lib.epi_proposer_train.argtypes = [V, P, i32, C.POINTER(TrainOpts), P]
         lib.epi_autotune.restype = i32
         lib.epi_autotune.argtypes = [V, i32, P]
         lib.epi_tune_save.restype = i32
@@ -353,3 +407,202 @@ def score_tables(ds: Dataset, order: int, tabs) -> tuple[np.ndarray, np.ndarray]
     f64 = np.zeros(count, dtype=np.float64)
     _check(lib.epi_score_tables(ds.handle, order, _np_ptr(tabs), count, _np_ptr(f32), _np_ptr(f64)))
     return f32, f64
+
+
+# ---------------------------------------------------------------------------
+# learned proposer (device buffers are torch CUDA tensors)
+# ---------------------------------------------------------------------------
+
+def _dptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+def score_all(ds: Dataset, order: int):
+    """Every combination's FP32 MI by lexicographic rank (torch float32 on
+    the dataset's device)."""
+    import math
+    import torch
+    out = torch.empty(math.comb(ds.n_snps, order), dtype=torch.float32, device=f"cuda:{ds.ctx.device}")
+    _check(load().epi_score_all(ds.handle, order, _dptr(out)))
+    return out
+
+
+def unrank(ds: Dataset, order: int, ranks):
+    """Device combinations (int32 [count, order]) of device int64 ranks."""
+    import torch
+    ranks = ranks.contiguous()
+    out = torch.empty((ranks.numel(), order), dtype=torch.int32, device=ranks.device)
+    _check(load().epi_unrank(ds.handle, order, _dptr(ranks), ranks.numel(), _dptr(out)))
+    return out
+
+
+def features5(ds: Dataset, s1, s2, s3, combs):
+    """25 features of device 5-sets combs (int32 [count, 5])."""
+    import torch
+    combs = combs.contiguous()
+    X = torch.empty((combs.shape[0], 25), dtype=torch.float32, device=combs.device)
+    _check(load().epi_features5(ds.handle, _dptr(s1), _dptr(s2), _dptr(s3), _dptr(combs), combs.shape[0], _dptr(X)))
+    return X
+
+
+def candidates5(ds: Dataset, triples, first: int, count: int, s3=None):
+    """Candidates [first, first + count) of the triples-plus-pair space
+    (int32 [count, 5] on the device); with the order-3 table s3, also the
+    keep mask (uint8 [count]) that marks each set once."""
+    import torch
+    triples = triples.contiguous()
+    out = torch.empty((count, 5), dtype=torch.int32, device=triples.device)
+    keep = None if s3 is None else torch.empty(count, dtype=torch.uint8, device=triples.device)
+    _check(load().epi_candidates5(ds.handle, _dptr(triples), triples.shape[0], first, count, _dptr(out),
+                                  None if s3 is None else _dptr(s3), None if keep is None else _dptr(keep)))
+    return out if s3 is None else (out, keep)
+
+
+def lookup(ds: Dataset, order: int, table, combs):
+    """table[rank(combs[i])] for device combinations (float32 [count])."""
+    import torch
+    combs = combs.contiguous()
+    out = torch.empty(combs.shape[0], dtype=torch.float32, device=combs.device)
+    _check(load().epi_lookup(ds.handle, order, _dptr(table), _dptr(combs), combs.shape[0], _dptr(out)))
+    return out
+
+
+def topk(ctx: Context, scores, k: int, keep=None):
+    """(values, indices) of the k largest device floats, ties by index,
+    entries with keep == 0 skipped."""
+    import torch
+    k = min(k, scores.numel())
+    vals = torch.empty(k, dtype=torch.float32, device=scores.device)
+    idx = torch.empty(k, dtype=torch.int64, device=scores.device)
+    n = torch.zeros(1, dtype=torch.int32, device=scores.device)
+    _check(load().epi_topk(ctx.handle, _dptr(scores), None if keep is None else _dptr(keep), scores.numel(), k,
+                           _dptr(vals), _dptr(idx), _dptr(n)))
+    m = int(n.item())
+    return vals[:m], idx[:m]
+
+
+def heuristic5(ctx: Context, X):
+    """Network-free ranking score of feature rows (sum of the three-way
+    log-scores)."""
+    import torch
+    X = X.contiguous()
+    out = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+    _check(load().epi_heuristic5(ctx.handle, _dptr(X), X.shape[0], _dptr(out)))
+    return out
+
+
+class MLP:
+    """The proposer network (see epi_mlp_create)."""
+
+    def __init__(self, ctx: Context, n_in: int = 25, hidden: int = 256, seed: int = 1):
+        self.ctx = ctx
+        self.n_in, self.hidden = n_in, hidden
+        h = C.c_void_p()
+        _check(load().epi_mlp_create(ctx.handle, n_in, hidden, seed, C.byref(h)))
+        self._h = h
+        self.n_params = int(load().epi_mlp_num_params(h))
+
+    def params(self) -> np.ndarray:
+        out = np.zeros(self.n_params, dtype=np.float32)
+        _check(load().epi_mlp_get_params(self._h, _np_ptr(out)))
+        return out
+
+    def set_params(self, theta):
+        theta = np.ascontiguousarray(theta, dtype=np.float32)
+        assert theta.size == self.n_params
+        _check(load().epi_mlp_set_params(self._h, _np_ptr(theta)))
+
+    def forward(self, X):
+        import torch
+        X = X.contiguous()
+        y = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+        _check(load().epi_mlp_forward(self._h, _dptr(X), X.shape[0], _dptr(y)))
+        return y
+
+    def gradients(self, X, t):
+        g = np.zeros(self.n_params, dtype=np.float32)
+        loss = C.c_float(0.0)
+        _check(load().epi_mlp_gradients(self._h, _dptr(X.contiguous()), _dptr(t.contiguous()), X.shape[0],
+                                         _np_ptr(g), C.byref(loss)))
+        return g, loss.value
+
+    def train_step(self, X, t, lr: float, wd: float) -> float:
+        loss = C.c_float(0.0)
+        _check(load().epi_mlp_train_step(self._h, _dptr(X.contiguous()), _dptr(t.contiguous()), X.shape[0],
+                                          lr, wd, C.byref(loss)))
+        return loss.value
+
+    def input_norm(self) -> tuple[np.ndarray, np.ndarray]:
+        shift = np.zeros(self.n_in, dtype=np.float32)
+        scale = np.zeros(self.n_in, dtype=np.float32)
+        _check(load().epi_mlp_get_input_norm(self._h, _np_ptr(shift), _np_ptr(scale)))
+        return shift, scale
+
+    def set_input_norm(self, shift, scale):
+        shift = np.ascontiguousarray(shift, dtype=np.float32)
+        scale = np.ascontiguousarray(scale, dtype=np.float32)
+        assert shift.size == self.n_in and scale.size == self.n_in
+        _check(load().epi_mlp_set_input_norm(self._h, _np_ptr(shift), _np_ptr(scale)))
+
+    def save(self, path: str):
+        """Flat little-endian file: int32 n_in, hidden; float32 parameters
+        (epi_mlp_create's order), input shift [n_in], input scale [n_in]."""
+        shift, scale = self.input_norm()
+        with open(path, "wb") as f:
+            np.array([self.n_in, self.hidden], dtype="<i4").tofile(f)
+            self.params().astype("<f4").tofile(f)
+            shift.astype("<f4").tofile(f)
+            scale.astype("<f4").tofile(f)
+
+    def load_file(self, path: str):
+        with open(path, "rb") as f:
+            hdr = np.fromfile(f, dtype="<i4", count=2)
+            if tuple(hdr) != (self.n_in, self.hidden):
+                raise ValueError(f"network shape {tuple(hdr)} does not match {(self.n_in, self.hidden)}")
+            theta = np.fromfile(f, dtype="<f4", count=self.n_params)
+            norm = np.fromfile(f, dtype="<f4", count=2 * self.n_in)
+            if theta.size != self.n_params or norm.size != 2 * self.n_in:
+                raise ValueError("truncated network file")
+            self.set_params(theta)
+            self.set_input_norm(norm[:self.n_in], norm[self.n_in:])
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().epi_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def proposer_search(ds: Dataset, net: "MLP | None", top_triples: int, budget: int, top_n: int,
+                    chunk: int = 0, with_counts: bool = False) -> tuple[SearchResult, dict]:
+    """Order-5 proposals ranked by `net` (None: the network-free heuristic),
+    re-scored exactly (see epi_proposer_search)."""
+    out = np.zeros(top_n, dtype=RESULT_DTYPE)
+    counts = np.zeros((top_n, 2, 243), dtype=np.uint32) if with_counts else None
+    n_out = C.c_int(0)
+    opts = ProposerOpts(top_triples, budget, top_n, chunk)
+    stats = ProposerStats()
+    _check(load().epi_proposer_search(ds.handle, None if net is None else net._h, C.byref(opts), _np_ptr(out),
+                                      _np_ptr(counts) if with_counts else None, C.byref(n_out), C.byref(stats)))
+    n = n_out.value
+    st = {f: getattr(stats, f) for f, _ in ProposerStats._fields_}
+    return SearchResult(out[:n], counts[:n] if with_counts else None, 5), st
+
+
+TARGETS = {"log_mi": 0, "top_membership": 1}
+
+
+def proposer_train(net: "MLP", datasets, top_triples: int, epochs: int, batch: int, lr: float, wd: float = 0.0,
+                   tail_fraction: float = 0.5, seed: int = 1, target: str = "log_mi") -> np.ndarray:
+    """Fit `net` on exhaustive order-5 labels of `datasets` (see
+    epi_proposer_train); returns the mean sampled batch loss per epoch."""
+    arr = (C.c_void_p * len(datasets))(*[d.handle for d in datasets])
+    losses = np.zeros(epochs, dtype=np.float32)
+    opts = TrainOpts(top_triples, epochs, batch, lr, wd, tail_fraction, seed, TARGETS[target])
+    _check(load().epi_proposer_train(net._h, arr, len(datasets), C.byref(opts), _np_ptr(losses)))
+    return losses

@@ -1,0 +1,292 @@
+"""GPU parity of the learned order-5 proposer's kernels.
+
+Score tables against the oracle's MI; unranking, candidate enumeration,
+table lookup and top-k against plain enumerations; the network's forward
+pass, gradients and AdamW steps against the float64 reference network
+(oracle/mlp.py), with and without the library's BF16 storage rounding.
+"""
+from __future__ import annotations
+
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mlp as M
+from oracle import oracle as O
+from tests.helpers import F32_RTOL, random_data
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def epi():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2201_02460_gb300 import epi as E
+    E.load()
+    return E
+
+
+@pytest.fixture(scope="module")
+def ctx(epi):
+    return epi.Context(0)
+
+
+@pytest.fixture(scope="module")
+def small(epi, ctx):
+    # 23 SNPs x 700 samples: every table of orders 1..5 fits the oracle
+    geno, pheno = random_data(23, 700, seed=41)
+    ds = epi.Dataset(ctx, geno, pheno)
+    return geno, pheno, ds
+
+
+def _oracle_all(geno, pheno, k):
+    n, m = geno.shape
+    combs = np.array(list(itertools.combinations(range(n), k)), dtype=np.int32)
+    t = O.tables(geno, pheno, combs)
+    return combs, np.array([O.mi(x[0], x[1], m) for x in t])
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+def test_score_all_matches_oracle(epi, small, k):
+    geno, pheno, ds = small
+    s = epi.score_all(ds, k).cpu().numpy().astype(np.float64)
+    combs, want = _oracle_all(geno, pheno, k)
+    assert s.shape == want.shape
+    # lexicographic order: index r is the r-th combination
+    for r in (0, 1, len(combs) // 2, len(combs) - 1):
+        assert O.rank(geno.shape[0], k, combs[r]) == r
+    err = np.abs(s - want)
+    assert (err <= F32_RTOL * want + 1e-12).all(), err.max()
+
+
+def test_score_all_ragged_sizes(epi, ctx):
+    # samples not a multiple of any word or tile size; one class small
+    geno, pheno = random_data(17, 389, seed=5, m1=37)
+    ds = epi.Dataset(ctx, geno, pheno)
+    for k in (2, 3):
+        s = epi.score_all(ds, k).cpu().numpy().astype(np.float64)
+        _, want = _oracle_all(geno, pheno, k)
+        assert (np.abs(s - want) <= F32_RTOL * want + 1e-12).all()
+
+
+def test_unrank_matches_oracle(epi, ctx):
+    import torch
+    rng = np.random.default_rng(3)
+    geno, pheno = random_data(2000, 64, seed=9)
+    ds = epi.Dataset(ctx, geno, pheno)
+    for k in (1, 3, 5):
+        total = O.binom(2000, k)
+        ranks = np.unique(np.concatenate([[0, total - 1], rng.integers(0, total, 500, dtype=np.int64)]))
+        got = epi.unrank(ds, k, torch.from_numpy(ranks).cuda()).cpu().numpy()
+        want = np.array([O.unrank(2000, k, int(r)) for r in ranks])
+        assert (got == want).all()
+
+
+def _features_cpu(mi_by_order, n, comb):
+    f = []
+    for k in (1, 2, 3):
+        vals = [mi_by_order[k][O.rank(n, k, c)] for c in itertools.combinations(comb, k)]
+        vals = np.sort(np.log(np.maximum(np.array(vals), 0.0) + 1e-7))[::-1]
+        f.extend(vals)
+    return np.array(f)
+
+
+def test_features5_match_oracle_scores(epi, small):
+    import torch
+    geno, pheno, ds = small
+    n = geno.shape[0]
+    tabs = [epi.score_all(ds, k) for k in (1, 2, 3)]
+    mi = {k: _oracle_all(geno, pheno, k)[1] for k in (1, 2, 3)}
+    rng = np.random.default_rng(11)
+    combs = np.array([np.sort(rng.choice(n, 5, replace=False)) for _ in range(300)], dtype=np.int32)
+    X = epi.features5(ds, *tabs, torch.from_numpy(combs).cuda()).cpu().numpy().astype(np.float64)
+    want = np.stack([_features_cpu(mi, n, c) for c in combs])
+    assert X.shape == (300, 25)
+    np.testing.assert_allclose(X, want, rtol=0, atol=5e-6)
+    # each group is sorted descending
+    for lo, hi in ((0, 5), (5, 15), (15, 25)):
+        assert (np.diff(X[:, lo:hi], axis=1) <= 0).all()
+
+
+def _candidate_space(n, triples):
+    out = []
+    for t in triples:
+        rest = [s for s in range(n) if s not in t]
+        for u, v in itertools.combinations(rest, 2):
+            out.append(sorted(list(t) + [u, v]))
+    return np.array(out, dtype=np.int32)
+
+
+def test_candidates5_enumeration_and_keep(epi, small):
+    import torch
+    geno, pheno, ds = small
+    n = geno.shape[0]
+    s3 = epi.score_all(ds, 3)
+    s3h = s3.cpu().numpy()
+    triples = np.array([[0, 1, 2], [3, 9, 20], [1, 2, 7], [0, 2, 21], [5, 6, 22]], dtype=np.int32)
+    want = _candidate_space(n, triples)
+    tri_d = torch.from_numpy(triples).cuda()
+    got, keep = epi.candidates5(ds, tri_d, 0, len(want), s3=s3)
+    assert (got.cpu().numpy() == want).all()
+    # ragged sub-range
+    sub = epi.candidates5(ds, tri_d, 101, 333)
+    assert (sub.cpu().numpy() == want[101:434]).all()
+    # keep: the generating triple is the best of the set's ten triples
+    per = math.comb(n - 3, 2)
+    keep = keep.cpu().numpy()
+    for i in range(len(want)):
+        t = tuple(triples[i // per])
+        key = lambda c: (-s3h[O.rank(n, 3, c)], O.rank(n, 3, c))
+        best = min(itertools.combinations(want[i], 3), key=key)
+        assert keep[i] == (1 if tuple(best) == t else 0)
+    # every distinct set of the space is kept exactly once when its best
+    # triple is listed
+    kept = {tuple(c) for c, k in zip(want, keep) if k}
+    assert sum(keep) == len(kept)
+
+
+def test_lookup_is_table_at_rank(epi, small):
+    import torch
+    geno, pheno, ds = small
+    n = geno.shape[0]
+    s5 = epi.score_all(ds, 5)
+    rng = np.random.default_rng(2)
+    combs = np.array([np.sort(rng.choice(n, 5, replace=False)) for _ in range(257)], dtype=np.int32)
+    got = epi.lookup(ds, 5, s5, torch.from_numpy(combs).cuda()).cpu().numpy()
+    s5h = s5.cpu().numpy()
+    want = np.array([s5h[O.rank(n, 5, c)] for c in combs])
+    assert (got == want).all()
+
+
+@pytest.mark.parametrize("count,k", [(1, 1), (100, 4096), (1_000_003, 100), (2_500_000, 4096), (70_000, 1000)])
+def test_topk_matches_sort(epi, ctx, count, k):
+    import torch
+    rng = np.random.default_rng(count + k)
+    # few distinct values: many ties broken by index
+    v = rng.integers(0, 50, count).astype(np.float32) * np.float32(0.25)
+    keep = (rng.random(count) < 0.7).astype(np.uint8)
+    vals, idx = epi.topk(ctx, torch.from_numpy(v).cuda(), k, keep=torch.from_numpy(keep).cuda())
+    cand = np.nonzero(keep)[0]
+    order = cand[np.lexsort((cand, -v[cand]))][:k]
+    assert (idx.cpu().numpy() == order).all()
+    assert (vals.cpu().numpy() == v[order]).all()
+    vals, idx = epi.topk(ctx, torch.from_numpy(v).cuda(), k)
+    order = np.lexsort((np.arange(count), -v))[:k]
+    assert (idx.cpu().numpy() == order).all()
+
+
+def test_topk_skips_nan_keeps_neg_inf(epi, ctx):
+    import torch
+    v = np.array([np.nan, -np.inf, 1.0, np.nan, 0.5, -np.inf], dtype=np.float32)
+    vals, idx = epi.topk(ctx, torch.from_numpy(v).cuda(), 6)
+    assert list(idx.cpu().numpy()) == [2, 4, 1, 5]
+
+
+def _bf16(a):
+    import torch
+    return torch.from_numpy(np.asarray(a, np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def _net_inputs(rows, n_in, seed):
+    rng = np.random.default_rng(seed)
+    X = rng.uniform(-9.0, -1.0, (rows, n_in)).astype(np.float32)
+    t = rng.normal(-2.0, 0.5, rows).astype(np.float32)
+    return X, t
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+
+
+@pytest.mark.parametrize("rows,hidden", [(1, 64), (300, 64), (1000, 256)])
+def test_mlp_gradients_match_reference(epi, ctx, rows, hidden):
+    import torch
+    net = epi.MLP(ctx, 25, hidden, seed=7)
+    theta = net.params().astype(np.float64)
+    X, t = _net_inputs(rows, 25, rows)
+    Xd, td = torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda()
+    y = net.forward(Xd).cpu().numpy().astype(np.float64)
+    g, loss = net.gradients(Xd, td)
+    g = g.astype(np.float64)
+    # same storage rounding as the library: agreement up to FP32 accumulation
+    y_q, _ = M.forward(theta, X, 25, hidden, rnd=_bf16)
+    g_q = M.gradients(theta, X, t, 25, hidden, rnd=_bf16)
+    assert _rel(y, y_q) <= 1e-4
+    offs = np.cumsum([0, hidden * 25, hidden, hidden * hidden, hidden, hidden, 1])
+    for a, b in zip(offs[:-1], offs[1:]):
+        assert _rel(g[a:b], g_q[a:b]) <= 2e-3, (a, b, _rel(g[a:b], g_q[a:b]))
+    assert abs(loss - M.loss(theta, X, t, 25, hidden, rnd=_bf16)) <= 1e-4 * abs(loss) + 1e-7
+    # plain float64 network: every prediction within the BF16 rounding of the
+    # sum of absolute products feeding it (the output is a difference of much
+    # larger terms) ...
+    y_64, (_, _, _, _, H2, _, W3) = M.forward(theta, X, 25, hidden)
+    scale = np.abs(H2) @ np.abs(W3) + 1.0
+    assert (np.abs(y - y_64) <= 2.0 ** -6 * scale).all()
+    # ... and, over a batch, gradients at targets well away from the
+    # predictions within a few BF16 roundings
+    if rows >= 300:
+        t2 = (y_64 + scale).astype(np.float32)
+        g2, _ = net.gradients(Xd, torch.from_numpy(t2).cuda())
+        g_64 = M.gradients(theta, X, t2, 25, hidden)
+        assert _rel(g2.astype(np.float64), g_64) <= 3e-2
+    net.close()
+
+
+def test_mlp_adamw_steps_match_reference(epi, ctx):
+    import torch
+    h = 64
+    net = epi.MLP(ctx, 25, h, seed=3)
+    theta = net.params().astype(np.float64)
+    m = np.zeros_like(theta)
+    v = np.zeros_like(theta)
+    X, t = _net_inputs(513, 25, 1)
+    Xd, td = torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda()
+    lr, wd = 3e-3, 1e-2
+    for step in (1, 2, 3):
+        g, _ = net.gradients(Xd, td)          # the gradient the step will use
+        net.train_step(Xd, td, lr, wd)
+        theta, m, v = M.adamw_step(theta, g.astype(np.float64), m, v, step, lr, wd)
+        got = net.params().astype(np.float64)
+        np.testing.assert_allclose(got, theta, rtol=2e-6, atol=2e-8)
+        theta = got
+    net.close()
+
+
+def test_mlp_training_reduces_loss(epi, ctx):
+    import torch
+    rng = np.random.default_rng(0)
+    X = rng.uniform(-4, 0, (4096, 25)).astype(np.float32)
+    t = (X[:, 15:25].mean(axis=1) * 0.5 + np.sin(X[:, 0])).astype(np.float32)
+    Xd, td = torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda()
+    net = epi.MLP(ctx, 25, 128, seed=1)
+    first = net.train_step(Xd, td, 1e-3, 0.0)
+    for _ in range(300):
+        last = net.train_step(Xd, td, 1e-3, 0.0)
+    assert last < 0.05 * first
+
+
+def test_mlp_save_load_roundtrip(epi, ctx, tmp_path):
+    import torch
+    a = epi.MLP(ctx, 25, 32, seed=5)
+    b = epi.MLP(ctx, 25, 32, seed=6)
+    p = str(tmp_path / "net.bin")
+    a.save(p)
+    b.load_file(p)
+    assert (a.params() == b.params()).all()
+    X, _ = _net_inputs(77, 25, 9)
+    Xd = torch.from_numpy(X).cuda()
+    assert torch.equal(a.forward(Xd), b.forward(Xd))
+    c = epi.MLP(ctx, 25, 64, seed=5)
+    with pytest.raises(ValueError):
+        c.load_file(p)
+
+
+def test_heuristic5_is_sum_of_triple_features(epi, ctx):
+    import torch
+    X, _ = _net_inputs(1001, 25, 4)
+    got = epi.heuristic5(ctx, torch.from_numpy(X).cuda()).cpu().numpy()
+    np.testing.assert_allclose(got, X[:, 15:25].astype(np.float64).sum(axis=1), rtol=1e-6)

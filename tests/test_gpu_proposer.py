@@ -1,0 +1,136 @@
+"""GPU checks of the order-5 proposer pipeline (epi_proposer_search / _train).
+
+With every triple listed and a budget covering every 5-set, the proposer must
+return the exhaustive order-5 top-N of the oracle.  With smaller budgets its
+proposals must be the best-ranked distinct candidates (checked against the
+same ranking built from the single-step calls) and every returned score
+exact.  Training must fit, reduce its loss and store the input
+standardisation it used.
+"""
+from __future__ import annotations
+
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from tests.helpers import F64_ATOL, check_topn, random_data
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def epi():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2201_02460_gb300 import epi as E
+    E.load()
+    return E
+
+
+@pytest.fixture(scope="module")
+def ctx(epi):
+    return epi.Context(0)
+
+
+@pytest.mark.parametrize("use_net", [False, True])
+def test_all_triples_reproduce_exhaustive_top(epi, ctx, use_net):
+    geno, pheno = random_data(12, 600, seed=17)
+    ds = epi.Dataset(ctx, geno, pheno)
+    net = epi.MLP(ctx, 25, 32, seed=2) if use_net else None
+    r, st = epi.proposer_search(ds, net, top_triples=220, budget=4096, top_n=20, chunk=1000, with_counts=True)
+    assert st["candidates"] == 220 * math.comb(9, 2)
+    assert st["kept"] == math.comb(12, 5) == st["proposals"]
+    oc, om, _ = O.search(geno, pheno, 5, 20)
+    check_topn(r.combs, r.mi, oc, om)
+    assert (O.tables(geno, pheno, r.combs.astype(np.int32)) == r.counts).all()
+    for c, rk in zip(r.combs, r.rank):
+        assert O.rank(12, 5, c) == int(rk)
+
+
+def _direct_proposals(epi, ctx, ds, n, T, R, scorer):
+    """Best R distinct candidates (score desc, index asc), built from the
+    single-step calls over the whole candidate space at once."""
+    import torch
+    S = [epi.score_all(ds, k) for k in (1, 2, 3)]
+    _, ti = epi.topk(ctx, S[2], T)
+    tri = epi.unrank(ds, 3, ti)
+    total = T * math.comb(n - 3, 2)
+    combs, keep = epi.candidates5(ds, tri, 0, total, s3=S[2])
+    y = scorer(epi.features5(ds, *S, combs)).cpu().numpy()
+    k = keep.cpu().numpy().astype(bool)
+    idx = np.nonzero(k)[0]
+    idx = idx[np.lexsort((idx, -y[idx]))][:R]
+    return combs.cpu().numpy()[idx], int(k.sum())
+
+
+@pytest.mark.parametrize("use_net", [False, True])
+def test_proposals_are_best_ranked_and_exact(epi, ctx, use_net):
+    n, T, R, top_n = 40, 50, 300, 60
+    geno, pheno = random_data(n, 800, seed=23)
+    ds = epi.Dataset(ctx, geno, pheno)
+    net = epi.MLP(ctx, 25, 64, seed=4) if use_net else None
+    scorer = (lambda X: net.forward(X)) if use_net else (lambda X: epi.heuristic5(ctx, X))
+    # small chunks: many merges of partial lists
+    r, st = epi.proposer_search(ds, net, T, R, top_n, chunk=4097, with_counts=True)
+    want, kept = _direct_proposals(epi, ctx, ds, n, T, R, scorer)
+    assert st["kept"] == kept and st["proposals"] == min(R, kept)
+    # exact scores of the proposals (oracle), best top_n
+    t = O.tables(geno, pheno, want.astype(np.int32))
+    mi = np.array([O.mi(x[0], x[1], 800) for x in t])
+    ranks = np.array([O.rank(n, 5, c) for c in want])
+    order = np.lexsort((ranks, -mi))[:top_n]
+    assert len(r) == top_n
+    check_topn(r.combs, r.mi, want[order], mi[order])
+    assert (r.counts == O.tables(geno, pheno, r.combs.astype(np.int32))).all()
+    assert (np.diff(r.mi) <= 0).all()
+
+
+def test_train_fits_and_stores_standardisation(epi, ctx):
+    import torch
+    sets = [random_data(24, 500, seed=s) for s in (1, 2, 3)]
+    dss = [epi.Dataset(ctx, g, p) for g, p in sets]
+    net = epi.MLP(ctx, 25, 64, seed=9)
+    theta0 = net.params()
+    losses = epi.proposer_train(net, dss, top_triples=100, epochs=4, batch=512, lr=2e-3, wd=1e-4,
+                                tail_fraction=0.25, seed=3)
+    assert np.isfinite(losses).all()
+    assert losses[-1] < losses[0]
+    assert not np.array_equal(theta0, net.params())
+    # stored input standardisation: mean and 1/sd of every feature over the
+    # training rows
+    rows = []
+    for ds in dss:
+        S = [epi.score_all(ds, k) for k in (1, 2, 3)]
+        _, ti = epi.topk(ctx, S[2], 100)
+        tri = epi.unrank(ds, 3, ti)
+        combs = epi.candidates5(ds, tri, 0, 100 * math.comb(21, 2))
+        rows.append(epi.features5(ds, *S, combs).cpu().numpy().astype(np.float64))
+    X = np.concatenate(rows)
+    shift, scale = net.input_norm()
+    np.testing.assert_allclose(shift, X.mean(axis=0), rtol=1e-5, atol=1e-5)
+    np.testing.assert_allclose(scale, 1.0 / X.std(axis=0), rtol=1e-4)
+
+
+def test_invalid_arguments(epi, ctx):
+    geno, pheno = random_data(12, 300, seed=1)
+    ds = epi.Dataset(ctx, geno, pheno)
+    for kw in (dict(top_triples=0, budget=10, top_n=5), dict(top_triples=5, budget=5000, top_n=5),
+               dict(top_triples=5, budget=10, top_n=11)):
+        with pytest.raises(epi.EpiError):
+            epi.proposer_search(ds, None, **kw)
+    g4, p4 = random_data(4, 300, seed=1)
+    with pytest.raises(epi.EpiError):
+        epi.proposer_search(epi.Dataset(ctx, g4, p4), None, 2, 10, 5)
+    with pytest.raises(epi.EpiError):
+        epi.proposer_search(ds, epi.MLP(ctx, 24, 8), 5, 10, 5)
+    with pytest.raises(epi.EpiError):
+        epi.proposer_train(epi.MLP(ctx, 24, 8), [ds], 5, 1, 16, 1e-3)
+    # exhaustive labels would not fit: refused before any work
+    gb, pb = random_data(300, 64, seed=1)
+    with pytest.raises(epi.EpiError) as e:
+        epi.proposer_train(epi.MLP(ctx, 25, 8), [epi.Dataset(ctx, gb, pb)], 5, 1, 16, 1e-3)
+    assert e.value.status == 4      # EPI_EUNSUPPORTED
