@@ -232,6 +232,40 @@ def measure_batch(epi, ctx, synth, n_div, steps=2):
                 snp_divisor=n_div, timing="host wall clock around the synchronous batched call")
 
 
+def measure_proposer(epi, ctx, ds, peaks, top_triples=256, budget=4096):
+    """Order-5 proposal search on the given dataset: candidates ranked per
+    second by the network (fused tensor-core inference; weights as
+    initialised, so this measures throughput, not recall) and by the
+    network-free heuristic, each followed by the exact re-score."""
+    import torch
+    net = epi.MLP(ctx, 25, 256, seed=1)
+    out = {}
+    for name, scorer in (("network", net), ("heuristic", None)):
+        epi.proposer_search(ds, scorer, top_triples, budget, 100)      # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r, st = epi.proposer_search(ds, scorer, top_triples, budget, 100)
+        t = time.perf_counter() - t0
+        out[name] = dict(seconds=t, candidates=int(st["candidates"]), kept=int(st["kept"]),
+                         ranked_per_s=st["candidates"] / (st["ms_rank"] / 1e3), ms_lower=st["ms_lower"],
+                         ms_rank=st["ms_rank"], ms_rescore=st["ms_rescore"], best_mi=float(r.mi[0]))
+    # the network alone on resident rows: fused BF16 tensor-core inference
+    X = torch.randn(1 << 24, 25, device="cuda") - 4.0
+    net.forward(X)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(3):
+        net.forward(X)
+    torch.cuda.synchronize()
+    t = (time.perf_counter() - t0) / 3
+    flops = X.shape[0] * 2.0 * (25 * 256 + 256 * 256 + 256)
+    out["mlp_inference"] = dict(rows_per_s=X.shape[0] / t, tflops=flops / t / 1e12,
+                                frac_of_bf16_peak=flops / t / 1e12 / peaks["bf16"],
+                                note="2*(25*256+256*256+256) flop per row; K of layer 1 padded to 64 on the device")
+    net.close()
+    return out
+
+
 def roofline(kind, d, k, kern_ms, peaks):
     total = math.comb(d.n_snps, k)
     if kind == "tc":
@@ -343,6 +377,8 @@ def run_ours(args):
                                                        roofline=roofline("popc", d4, k4, p4["kern_ms"], peaks))
             ds4.close()
         comp["batch64/auto"] = measure_batch(epi, ctx, synth, args.batch_div)
+        if d.n_snps >= 5:
+            comp[f"proposer_order5/{args.workload}"] = measure_proposer(epi, ctx, ds, peaks)
         line["compare"] = comp
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

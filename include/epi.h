@@ -271,6 +271,9 @@ typedef struct epi_mlp epi_mlp;
 epi_status epi_mlp_create(epi_ctx *ctx, int n_in, int hidden, uint64_t seed, epi_mlp **out);
 void epi_mlp_destroy(epi_mlp *net);
 int64_t epi_mlp_num_params(const epi_mlp *net);
+/* Inference kernel choice: 0 automatic (tensor cores where they apply),
+ * 1 CUDA-core layers, 2 tensor cores (EPI_EUNSUPPORTED for other shapes). */
+epi_status epi_mlp_set_forward_path(epi_mlp *net, int path);
 int epi_mlp_num_inputs(const epi_mlp *net);
 /* FP32 master parameters to / from host memory (epi_mlp_num_params floats);
  * setting them also resets the optimiser's step count. */
@@ -281,8 +284,12 @@ epi_status epi_mlp_set_params(epi_mlp *net, const float *host);
  * Saved with the network by the bindings; not changed by training steps. */
 epi_status epi_mlp_set_input_norm(epi_mlp *net, const float *shift_host, const float *scale_host);
 epi_status epi_mlp_get_input_norm(const epi_mlp *net, float *shift_host, float *scale_host);
-/* Predictions for `rows` device inputs X [rows][n_in] into device y [rows]
- * (any number of rows: processed in slices of bounded activation memory). */
+/* Predictions for `rows` device inputs X [rows][n_in] into device y [rows].
+ * With hidden = 256 and n_in <= 64 one fused tensor-core kernel runs the
+ * three layers (BF16 operands, FP32 accumulation, activations rounded to
+ * BF16 between layers, as in training) and the call waits for it (status
+ * EPI_ETIMEOUT if a bounded wait gave up); other shapes run the CUDA-core
+ * layers in slices of bounded activation memory, queued on the stream. */
 epi_status epi_mlp_forward(epi_mlp *net, const float *X_dev, int64_t rows, float *y_dev);
 /* Gradients of the mean squared error against device targets t [rows] into
  * host grad [num_params] (may be NULL); host loss (may be NULL). */
@@ -354,7 +361,8 @@ epi_status epi_profile_end(epi_ctx *ctx, double *kernel_ms, int64_t *launches);
  * (the paper has no counterpart): out[8] receives, averaged over CTAs, the
  * SM cycles the MMA issuer waited for generated prefix tiles [0], for TMA
  * tiles [1] and for a free accumulator [2], the A producers waited for a free
- * stage [3], the epilogue waited for a finished accumulator [5], the TMA
+ * stage [3] and for a free accumulator [4], the epilogue waited for a
+ * finished accumulator and its row totals [5], the TMA
  * producer waited for a free stage [6], and the MMA issuer's whole loop [7].
  * Zeros when no such search ran.  The value must be read before the context's
  * next search (the scratch memory is reused). */

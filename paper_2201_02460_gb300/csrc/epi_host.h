@@ -75,6 +75,12 @@ cudaError_t launch_candidates5(const DevData &d, const uint32_t *triples, int64_
                                uint32_t *combs, const float *s3, uint8_t *keep, cudaStream_t st);
 cudaError_t launch_candidates5_at(const DevData &d, const uint32_t *triples, const uint64_t *idx, int64_t count,
                                   uint32_t *combs, cudaStream_t st);
+// epi_mlp_tc.cu
+size_t mlp_tc_smem_bytes();
+bool mlp_tc_applies(int n_in, int hidden);
+cudaError_t launch_mlp_forward_tc(const float *X, int64_t rows, int n_in, const float *norm, const void *W1,
+                                  const float *b1, const void *W2, const float *b2, const void *W3, const float *b3,
+                                  float *y, int32_t *status, int num_sms, cudaStream_t st);
 cudaError_t launch_lookup(const DevData &d, int k, const float *table, const uint32_t *combs, int64_t count,
                           float *out, cudaStream_t st);
 cudaError_t launch_topk(const float *scores, const uint8_t *keep, int64_t count, int k, float *blk_s, uint64_t *blk_i,

@@ -415,6 +415,9 @@ struct epi_mlp {
     float *g = nullptr, *m1 = nullptr, *m2 = nullptr;
     __nv_bfloat16 *wb = nullptr;   // BF16 working copy
     float *norm = nullptr;         // input shift [n_in] then scale [n_in]
+    int32_t *status = nullptr;     // tensor-core inference status word
+    int forward_path = 0;          // 0 auto, 1 CUDA cores, 2 tensor cores
+    int num_sms = 0;
     int64_t step = 0;
     // activation buffers for a batch (grown on demand)
     int64_t cap = 0;
@@ -557,6 +560,7 @@ epi_status epi_mlp_create(epi_ctx *ctx, int n_in, int hidden, uint64_t seed, epi
     net->hidden = hidden;
     net->stream = epi_ctx_stream(ctx);
     net->device = epi_ctx_device(ctx);
+    net->num_sms = epi_ctx_num_sms(ctx);
     cudaSetDevice(net->device);
     const Offs o = offsets(n_in, hidden);
     net->n_params = o.total;
@@ -564,7 +568,8 @@ epi_status epi_mlp_create(epi_ctx *ctx, int n_in, int hidden, uint64_t seed, epi
     if (cudaMalloc((void **)&net->w, fb) != cudaSuccess || cudaMalloc((void **)&net->g, fb) != cudaSuccess ||
         cudaMalloc((void **)&net->m1, fb) != cudaSuccess || cudaMalloc((void **)&net->m2, fb) != cudaSuccess ||
         cudaMalloc((void **)&net->wb, (size_t)o.total * 2) != cudaSuccess ||
-        cudaMalloc((void **)&net->norm, (size_t)n_in * 8) != cudaSuccess) {
+        cudaMalloc((void **)&net->norm, (size_t)n_in * 8) != cudaSuccess ||
+        cudaMalloc((void **)&net->status, 4) != cudaSuccess) {
         epi_mlp_destroy(net);
         return lfail(EPI_ENOMEM, "epi_mlp_create: allocation failed");
     }
@@ -602,7 +607,7 @@ void epi_mlp_destroy(epi_mlp *net)
 {
     if (!net) return;
     cudaStreamSynchronize(net->stream);
-    cudaFree(net->w); cudaFree(net->g); cudaFree(net->m1); cudaFree(net->m2); cudaFree(net->wb); cudaFree(net->norm);
+    cudaFree(net->w); cudaFree(net->g); cudaFree(net->m1); cudaFree(net->m2); cudaFree(net->wb); cudaFree(net->norm); cudaFree(net->status);
     if (net->act) cudaFree(net->act);
     delete net;
 }
@@ -647,9 +652,31 @@ epi_status epi_mlp_get_input_norm(const epi_mlp *net, float *shift_host, float *
     return EPI_OK;
 }
 
+epi_status epi_mlp_set_forward_path(epi_mlp *net, int path)
+{
+    if (!net || path < 0 || path > 2) return lfail(EPI_EINVAL, "epi_mlp_set_forward_path: bad argument");
+    if (path == 2 && !mlp_tc_applies(net->n_in, net->hidden))
+        return lfail(EPI_EUNSUPPORTED, "tensor-core inference needs hidden = 256 and n_in <= 64");
+    net->forward_path = path;
+    return EPI_OK;
+}
+
 epi_status epi_mlp_forward(epi_mlp *net, const float *X_dev, int64_t rows, float *y_dev)
 {
     if (!net || !X_dev || !y_dev || rows < 1) return lfail(EPI_EINVAL, "epi_mlp_forward: bad argument");
+    if (net->forward_path != 1 && mlp_tc_applies(net->n_in, net->hidden)) {
+        const int in = net->n_in, h = net->hidden;
+        const Offs o = offsets(in, h);
+        LCK(cudaMemsetAsync(net->status, 0, 4, net->stream));
+        LCK(launch_mlp_forward_tc(X_dev, rows, in, net->norm, net->wb + o.W1, net->w + o.b1, net->wb + o.W2,
+                                  net->w + o.b2, net->wb + o.W3, net->w + o.b3, y_dev, net->status, net->num_sms,
+                                  net->stream));
+        int32_t st = 0;
+        LCK(cudaMemcpyAsync(&st, net->status, 4, cudaMemcpyDeviceToHost, net->stream));
+        LCK(cudaStreamSynchronize(net->stream));
+        if (st) return lfail(EPI_ETIMEOUT, "epi_mlp_forward: a tensor-core wait gave up");
+        return EPI_OK;
+    }
     // slices of at most 128K rows bound the activation memory
     constexpr int64_t kSlice = (int64_t)1 << 17;
     Acts a;

@@ -1,0 +1,289 @@
+// Fused tensor-core inference of the proposer network (tcgen05, sm_103a).
+//
+// y = W3 . relu(W2 . relu(W1 . x' + b1) + b2) + b3 for 128 rows per step,
+// x' = (x - shift) * scale, with BF16 operands and FP32 accumulation in
+// tensor memory, and the hidden activations rounded to BF16 between layers
+// (the same storage points as the training kernels).  One persistent CTA per
+// SM keeps both weight matrices in shared memory for the whole launch:
+//   W2   [256 out][256 in]  BF16, K-major, 4 K blocks of 64     128 KiB
+//   W1   [256 out][64 in]   BF16, inputs zero-padded to 64       32 KiB
+//   H1   [128 rows][256]    BF16, 4 K blocks (also holds x' and
+//        the row partials of the last layer)                     64 KiB
+// all in the 128-byte swizzle (8-row atoms of 1024 bytes).  Per step:
+//   1. the 256 threads stage x' (BF16) into H1's first K block;
+//   2. one thread issues layer 1 (M128 N256 K64: 4 MMAs of K16) into tensor
+//      memory columns [0, 256) and commits to an mbarrier;
+//   3. warp w reads lane quadrant w % 4, columns half w / 4, adds b1, ReLU,
+//      rounds to BF16 and writes H1;
+//   4. one thread issues layer 2 (M128 N256 K256: 16 MMAs) into columns
+//      [256, 512);
+//   5. the same warps add b2, ReLU, round to BF16 and dot with W3; the two
+//      column halves of a row meet in shared memory and b3 is added.
+// Every mbarrier wait is bounded (about 2 s); a wait that gives up sets the
+// status word and the CTA drains its MMAs and frees tensor memory.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "epi_host.h"
+#include "epi_internal.cuh"
+#include "epi_tcgen05.cuh"
+
+namespace epi {
+namespace mlptc {
+
+constexpr int kRows = 128;
+constexpr int kHidden = 256;
+constexpr int kKin = 64;                       // padded inputs
+constexpr int kThreads = 256;
+constexpr uint32_t kW2Bytes = 4 * kHidden * 128;
+constexpr uint32_t kW1Bytes = kHidden * 128;
+constexpr uint32_t kH1Bytes = 4 * kRows * 128;
+constexpr uint32_t kKBlockH = kRows * 128;     // one K block of H1
+constexpr uint32_t kKBlockW = kHidden * 128;   // one K block of W2
+constexpr unsigned long long kTimeoutNs = 2000000000ull;
+
+// kind::f16 with BF16 A and B, FP32 D, K-major operands, M = 128, N = 256
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kHidden >> 3) << 17) |
+                            ((uint32_t)(kRows >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            d_tmem),
+        "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate));
+}
+
+// byte offset of 16-byte chunk c (0..7) of row r inside a swizzled K block
+__device__ __forceinline__ uint32_t sw(int r, int c) { return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4)); }
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b)
+{
+    const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+__device__ __forceinline__ float bf16_round(float v) { return __bfloat162float(__float2bfloat16(v)); }
+
+// bounded wait; every thread calls it, the caller syncs and tests the flag
+__device__ __forceinline__ void wait_phase(uint64_t *bar, uint32_t parity, volatile int *abort_flag)
+{
+    if (mbar_try(bar, parity)) return;
+    const uint64_t t0 = now_ns();
+    while (!mbar_try(bar, parity)) {
+        if (*abort_flag) return;
+        if (now_ns() - t0 > kTimeoutNs) {
+            *abort_flag = 1;
+            return;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    mlp_forward_kernel(const float *__restrict__ X, int64_t rows, int n_in, const float *__restrict__ norm,
+                       const __nv_bfloat16 *__restrict__ W1, const float *__restrict__ b1,
+                       const __nv_bfloat16 *__restrict__ W2, const float *__restrict__ b2,
+                       const __nv_bfloat16 *__restrict__ W3, const float *__restrict__ b3, float *__restrict__ y,
+                       int32_t *__restrict__ status)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
+    unsigned char *w2s = smem;
+    unsigned char *w1s = w2s + kW2Bytes;
+    unsigned char *h1s = w1s + kW1Bytes;
+    // [2][128] row partials of the last layer; they live in H1's last K
+    // block, which layer 2 has finished reading when they are written
+    float *part = reinterpret_cast<float *>(h1s + 3 * kKBlockH);
+    __shared__ __align__(8) uint64_t mma_bar, drain_bar;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ volatile int abort_flag;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quad = warp & 3, half = warp >> 2;
+    const int64_t n_tiles = (rows + kRows - 1) / kRows;
+
+    if (tid == 0) {
+        mbar_init(&mma_bar, 1);
+        mbar_init(&drain_bar, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // weights into the swizzled layouts
+    for (int idx = tid; idx < kHidden * 32; idx += kThreads) {
+        const int n = idx >> 5, c32 = idx & 31;
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(W2 + (size_t)n * kHidden) + c32);
+        *reinterpret_cast<uint4 *>(w2s + (c32 >> 3) * kKBlockW + sw(n, c32 & 7)) = v;
+    }
+    const unsigned short *w1u = reinterpret_cast<const unsigned short *>(W1);
+    for (int idx = tid; idx < kHidden * 8; idx += kThreads) {
+        const int n = idx >> 3, c = idx & 7;
+        uint32_t w[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int e0 = 8 * c + 2 * q, e1 = e0 + 1;
+            const uint32_t lo = e0 < n_in ? w1u[(size_t)n * n_in + e0] : 0u;
+            const uint32_t hi = e1 < n_in ? w1u[(size_t)n * n_in + e1] : 0u;
+            w[q] = lo | (hi << 16);
+        }
+        *reinterpret_cast<uint4 *>(w1s + sw(n, c)) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = tmem_base_sh;
+    const uint32_t lane_addr = tmem_base + ((uint32_t)(quad * 32) << 16);
+    const int r = quad * 32 + lane;            // this thread's tile row in the epilogues
+    uint32_t phase = 0;
+    bool issued = false;
+
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        // ---- 1. stage x' (two threads per row, four 16-byte chunks each) --
+        {
+            const int sr = tid >> 1, sh = tid & 1;
+            const int64_t row = tile * kRows + sr;
+            const bool valid = row < rows;
+#pragma unroll
+            for (int cc = 0; cc < 4; cc++) {
+                const int c = 4 * sh + cc;
+                uint32_t w[4];
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const int e0 = 8 * c + 2 * q, e1 = e0 + 1;
+                    const float a = (valid && e0 < n_in) ? (X[row * n_in + e0] - norm[e0]) * norm[n_in + e0] : 0.0f;
+                    const float b = (valid && e1 < n_in) ? (X[row * n_in + e1] - norm[e1]) * norm[n_in + e1] : 0.0f;
+                    w[q] = pack_bf16(a, b);
+                }
+                *reinterpret_cast<uint4 *>(h1s + sw(sr, c)) = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+        fence_proxy_async();
+        tc_fence_before();
+        __syncthreads();
+        // ---- 2. layer 1 -----------------------------------------------------
+        if (tid == 0) {
+            tc_fence_after();
+            const uint64_t ad = sdesc(smem_u32(h1s)), bd = sdesc(smem_u32(w1s));
+#pragma unroll
+            for (int kk = 0; kk < kKin / 16; kk++) mma_bf16(tmem_base, ad + 2 * kk, bd + 2 * kk, kk ? 1u : 0u);
+            mma_commit(&mma_bar);
+            issued = true;
+        }
+        wait_phase(&mma_bar, phase, &abort_flag);
+        phase ^= 1;
+        __syncthreads();
+        if (abort_flag) break;
+        tc_fence_after();
+        // ---- 3. bias, ReLU, BF16 into H1 ---------------------------------------
+#pragma unroll 1
+        for (int q = 0; q < 4; q++) {
+            const int col0 = 128 * half + 32 * q;
+            uint32_t v[32];
+            TMEM_LD32(lane_addr + (uint32_t)col0, v);
+            tmem_wait_ld();
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                uint32_t w[4];
+#pragma unroll
+                for (int p = 0; p < 4; p++) {
+                    const int i = 8 * c + 2 * p;
+                    const float a = fmaxf(__uint_as_float(v[i]) + __ldg(b1 + col0 + i), 0.0f);
+                    const float b = fmaxf(__uint_as_float(v[i + 1]) + __ldg(b1 + col0 + i + 1), 0.0f);
+                    w[p] = pack_bf16(a, b);
+                }
+                const int col = col0 + 8 * c;
+                *reinterpret_cast<uint4 *>(h1s + (col >> 6) * kKBlockH + sw(r, (col & 63) >> 3)) =
+                    make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+        fence_proxy_async();
+        tc_fence_before();
+        __syncthreads();
+        // ---- 4. layer 2 -----------------------------------------------------
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t h0 = smem_u32(h1s), w0 = smem_u32(w2s);
+#pragma unroll
+            for (int kb = 0; kb < 4; kb++) {
+                const uint64_t ad = sdesc(h0 + kb * kKBlockH), bd = sdesc(w0 + kb * kKBlockW);
+#pragma unroll
+                for (int kk = 0; kk < 4; kk++)
+                    mma_bf16(tmem_base + kHidden, ad + 2 * kk, bd + 2 * kk, (kb | kk) ? 1u : 0u);
+            }
+            mma_commit(&mma_bar);
+        }
+        wait_phase(&mma_bar, phase, &abort_flag);
+        phase ^= 1;
+        __syncthreads();
+        if (abort_flag) break;
+        tc_fence_after();
+        // ---- 5. bias, ReLU, BF16, dot with W3 ------------------------------------
+        float acc = 0.0f;
+#pragma unroll 1
+        for (int q = 0; q < 4; q++) {
+            const int col0 = 128 * half + 32 * q;
+            uint32_t v[32];
+            TMEM_LD32(lane_addr + (uint32_t)(kHidden + col0), v);
+            tmem_wait_ld();
+#pragma unroll
+            for (int i = 0; i < 32; i++) {
+                const float h2 = bf16_round(fmaxf(__uint_as_float(v[i]) + __ldg(b2 + col0 + i), 0.0f));
+                acc = fmaf(h2, __bfloat162float(W3[col0 + i]), acc);
+            }
+        }
+        part[half * kRows + r] = acc;
+        tc_fence_before();
+        __syncthreads();
+        if (tid < kRows) {
+            const int64_t row = tile * kRows + tid;
+            if (row < rows) y[row] = part[tid] + part[kRows + tid] + __ldg(b3);
+        }
+    }
+    __syncthreads();
+    if (tid == 0 && issued && abort_flag) {
+        // drain whatever MMA is still in flight before tensor memory is freed
+        mma_commit(&drain_bar);
+        const uint64_t t0 = now_ns();
+        while (!mbar_try(&drain_bar, 0) && now_ns() - t0 < kTimeoutNs) {}
+        atomicOr(status, ST_TIMEOUT);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(512) : "memory");
+    }
+}
+
+}  // namespace mlptc
+
+size_t mlp_tc_smem_bytes()
+{
+    return 1024 + mlptc::kW2Bytes + mlptc::kW1Bytes + mlptc::kH1Bytes;
+}
+
+bool mlp_tc_applies(int n_in, int hidden) { return hidden == mlptc::kHidden && n_in >= 1 && n_in <= mlptc::kKin; }
+
+cudaError_t launch_mlp_forward_tc(const float *X, int64_t rows, int n_in, const float *norm, const void *W1,
+                                  const float *b1, const void *W2, const float *b2, const void *W3, const float *b3,
+                                  float *y, int32_t *status, int num_sms, cudaStream_t st)
+{
+    if (rows <= 0) return cudaSuccess;
+    const size_t smem = mlp_tc_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(mlptc::mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t tiles = (rows + mlptc::kRows - 1) / mlptc::kRows;
+    const int grid = (int)(tiles < num_sms ? tiles : num_sms);
+    mlptc::mlp_forward_kernel<<<grid, mlptc::kThreads, smem, st>>>(
+        X, rows, n_in, norm, static_cast<const __nv_bfloat16 *>(W1), b1, static_cast<const __nv_bfloat16 *>(W2), b2,
+        static_cast<const __nv_bfloat16 *>(W3), b3, y, status);
+    return cudaGetLastError();
+}
+
+}  // namespace epi

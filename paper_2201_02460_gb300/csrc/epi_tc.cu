@@ -47,6 +47,16 @@
 
 #include "epi_host.h"
 #include "epi_internal.cuh"
+#include "epi_tcgen05.cuh"
+
+// A producers' load distance in K stages and the stage-release group size
+// (tuning parameters)
+#ifndef EPI_TC_PREFETCH
+#define EPI_TC_PREFETCH 4
+#endif
+#ifndef EPI_TC_RELEASE
+#define EPI_TC_RELEASE 3
+#endif
 
 namespace epi {
 
@@ -57,6 +67,11 @@ constexpr int kN = 2 * kJ;             // accumulator columns per class
 constexpr int kKC = 128;               // individuals (bytes) per K stage
 constexpr int kStagesA = 6;            // generated prefix-row stages
 constexpr int kStagesB = 6;            // TMA stages of single-SNP rows
+// Stages are released to the producers in groups: a tcgen05.commit lets the
+// following MMAs start only after the earlier ones finish (about one MMA
+// latency of idle tensor pipe), so the issuer commits once per group of
+// kRelease stages instead of once per stage.
+constexpr int kRelease = EPI_TC_RELEASE;
 constexpr int kDescDepth = 4;
 constexpr int kEpiWarps = 8;           // two per TMEM lane quadrant
 constexpr int kProdWarps = 8;          // two threads per tile row
@@ -106,42 +121,6 @@ struct Params {
 };
 
 // ------------------------------------------------------------------ PTX --
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint64_t now_ns()
-{
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_tx(uint64_t *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
 // Bounded wait for the phase of parity `parity`; false when it gave up (the
 // CTA-wide abort flag is then set).
 __device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag)
@@ -158,20 +137,17 @@ __device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile 
     }
 }
 
-// Hot-path wait: one inline try_wait; the bounded out-of-line wait (and the
-// cycle accounting of the trace) only when the phase is not complete yet.
+// Hot-path wait: one inline non-blocking test; the bounded out-of-line wait
+// (and the cycle accounting of the trace) only when the phase is not
+// complete yet, so the trace counts every cycle spent waiting.
 __device__ __forceinline__ bool wait_fast(uint64_t *bar, uint32_t parity, volatile int *abort_flag, long long &acc)
 {
-    if (mbar_try(bar, parity)) return true;
+    if (mbar_test(bar, parity)) return true;
     const long long t0 = clock64();
     const bool ok = mbar_wait(bar, parity, abort_flag);
     acc += clock64() - t0;
     return ok;
 }
-
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar)
 {
@@ -180,18 +156,6 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
         "[%4];" ::"r"(smem_u32(dst)),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
         : "memory");
-}
-
-// K-major operand in the 128-byte swizzle: 8-row atoms of 1024 bytes stacked
-// along M/N (stride 1024), descriptor version 1, layout SWIZZLE_128B.
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr)
-{
-    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
-    d |= (uint64_t)1 << 16;
-    d |= (uint64_t)(1024 >> 4) << 32;
-    d |= (uint64_t)1 << 46;
-    d |= (uint64_t)2 << 61;
-    return d;
 }
 
 // kind::f8f6f4, E4M3 x E4M3 -> F32, K-major A and B, M = 128, N = 128
@@ -205,23 +169,32 @@ __device__ __forceinline__ void mma_f8(uint32_t d_tmem, uint64_t a, uint64_t b, 
         "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate));
 }
 
-__device__ __forceinline__ void mma_commit(uint64_t *bar)
+// The same MMA executed by a whole warp in step; only the elected lane
+// (`leader` nonzero) issues it.
+__device__ __forceinline__ void mma_f8_warp(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate,
+                                            uint32_t leader)
 {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
+    asm volatile(
+        "{\n .reg .pred p, e;\n setp.ne.b32 p, %4, 0;\n setp.ne.b32 e, %5, 0;\n"
+        " @e tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate), "r"(leader));
 }
 
-#define TMEM_LD32(taddr, r)                                                                                        \
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"  \
-                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"                        \
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), \
-                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),       \
-                   "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),     \
-                   "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),     \
-                   "=r"(r[29]), "=r"(r[30]), "=r"(r[31])                                                           \
-                 : "r"(taddr))
+__device__ __forceinline__ void mma_commit_warp(uint64_t *bar, uint32_t leader)
+{
+    asm volatile(
+        "{\n .reg .pred e;\n setp.ne.b32 e, %1, 0;\n"
+        " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}\n" ::"r"(smem_u32(bar)),
+        "r"(leader)
+        : "memory");
+}
 
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ uint32_t elect_one()
+{
+    uint32_t pred;
+    asm volatile("{\n .reg .pred p;\n elect.sync _|p, 0xffffffff;\n selp.u32 %0, 1, 0, p;\n}\n" : "=r"(pred));
+    return pred;
+}
 
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory"); }
 
@@ -383,7 +356,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
     uint32_t *tot = reinterpret_cast<uint32_t *>(rk + P.cand_p2);   // [2][128][2 halves][2 classes]
     Desc *desc = reinterpret_cast<Desc *>(tot + 2 * 128 * 4);
 
-    __shared__ __align__(8) uint64_t full_a[kStagesA], empty_a[kStagesA], full_b[kStagesB], empty_b[kStagesB];
+    // one "stage free" barrier per stage for both operands (the A and B rings
+    // advance together), released by one MMA commit
+    static_assert(kStagesA == kStagesB, "the A and B rings share their release barriers");
+    static_assert(kStagesA % kRelease == 0, "release groups tile the ring");
+    // full_ab[s]: the A producers' warps and the TMA thread (with its bytes)
+    // have filled stage s of both operands
+    __shared__ __align__(8) uint64_t full_ab[kStagesA], empty_ab[kStagesA / kRelease];
     __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], tot_full[2];
     __shared__ __align__(8) uint64_t desc_full[kDescDepth], desc_empty[kDescDepth], drain_bar;
     __shared__ uint32_t tmem_base_sh;
@@ -403,12 +382,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
 
     if (tid == 0) {
         for (int s = 0; s < kStagesA; s++) {
-            mbar_init(&full_a[s], kProdWarps);
-            mbar_init(&empty_a[s], 1);
-        }
-        for (int s = 0; s < kStagesB; s++) {
-            mbar_init(&full_b[s], 1);
-            mbar_init(&empty_b[s], 1);
+            mbar_init(&full_ab[s], kProdWarps + 1);
+            if (s % kRelease == 0) mbar_init(&empty_ab[s / kRelease], 1);
         }
         for (int b = 0; b < 2; b++) {
             mbar_init(&acc_full[b], 1);
@@ -486,9 +461,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                 for (int kc = 0; kc < DS.chunks; kc++, g++) {
                     const int s = (int)(g % kStagesB);
                     const uint32_t us = (uint32_t)(g / kStagesB);
-                    if (!wait_fast(&empty_b[s], (us & 1) ^ 1, &abort_flag, w_tma)) break;
-                    mbar_arrive_tx(&full_b[s], kTxBytes);
-                    tma_load_2d(stages_b + s * kTileBytes, tmap, kc * kKC, y, &full_b[s]);
+                    if (!wait_fast(&empty_ab[s / kRelease], (us & 1) ^ 1, &abort_flag, w_tma)) break;
+                    mbar_arrive_tx(&full_ab[s], kTxBytes);
+                    tma_load_2d(stages_b + s * kTileBytes, tmap, kc * kKC, y, &full_ab[s]);
                 }
                 u++;
                 if (u == ntiles_of(d, cmin)) {
@@ -502,15 +477,24 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                     const uint64_t last = ((g - 1 - s) / kStagesB) * kStagesB + s;
                     const uint32_t us = (uint32_t)(last / kStagesB);
                     const uint64_t t0 = now_ns();
-                    while (!mbar_try(&full_b[s], us & 1) && now_ns() - t0 < kTimeoutNs) {}
+                    while (!mbar_try(&full_ab[s], us & 1) && now_ns() - t0 < kTimeoutNs) {}
                 }
             }
         }
     } else if (warp == kWarpMma) {
         // ------------------------------------------------------------- MMA
-        if (lane == 0 && n_my > 0) {
-            uint64_t g = 0;
-            const uint32_t sa0 = smem_u32(stages_a), sb0 = smem_u32(stages_b);
+        if (n_my > 0) {
+            // a lean issue loop run by the whole warp in step (warp-uniform
+            // values stay on the uniform datapath); one elected lane issues
+            // the MMAs and commits.  The tensor pipe is fed only as fast as
+            // this instruction stream runs, so stage descriptors are formed
+            // by one add and the ring position and phase are carried.
+            const uint32_t leader = elect_one();
+            const uint64_t ad0 = sdesc(smem_u32(stages_a)), bd0 = sdesc(smem_u32(stages_b));
+            constexpr uint32_t kStageDesc = kTileBytes >> 4;   // stage stride in descriptor address units
+            int s = 0;
+            uint32_t ph = 0;
+            const int chunks = DS.chunks, chunks_case = DS.chunks_case;
             long long w_a = 0, w_b = 0, w_acc = 0;
             const long long t_start = clock64();
             for (int64_t i = 0; i < n_my && !abort_flag; i++) {
@@ -518,34 +502,32 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                 const uint32_t ub = (uint32_t)(i >> 1);
                 if (!wait_fast(&acc_empty[b], (ub & 1) ^ 1, &abort_flag, w_acc)) break;
                 tc_fence_after();
+                const uint32_t d_case = tmem_base + (uint32_t)(b * 2 * kN), d_ctrl = d_case + (uint32_t)kN;
                 bool ok = true;
-                for (int kc = 0; kc < DS.chunks; kc++, g++) {
-                    const int sa = (int)(g % kStagesA), sb = (int)(g % kStagesB);
-                    const uint32_t ua = (uint32_t)(g / kStagesA), ubb = (uint32_t)(g / kStagesB);
-                    if (!wait_fast(&full_a[sa], ua & 1, &abort_flag, w_a)) { ok = false; break; }
-                    if (!wait_fast(&full_b[sb], ubb & 1, &abort_flag, w_b)) { ok = false; break; }
+                for (int kc = 0; kc < chunks; kc++) {
+                    if (!wait_fast(&full_ab[s], ph, &abort_flag, w_a)) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t dcol = tmem_base + (uint32_t)(b * 2 * kN) + (kc < DS.chunks_case ? 0u : (uint32_t)kN);
-                    const bool first = (kc == 0) || (kc == DS.chunks_case);
-                    const uint64_t ad = sdesc(sa0 + sa * kTileBytes);
-                    const uint64_t bd = sdesc(sb0 + sb * kTileBytes);
+                    const uint32_t dcol = kc < chunks_case ? d_case : d_ctrl;
+                    const uint32_t acc0 = (kc == 0 || kc == chunks_case) ? 0u : 1u;
+                    const uint64_t ad = ad0 + (uint64_t)(s * kStageDesc), bd = bd0 + (uint64_t)(s * kStageDesc);
+                    mma_f8_warp(dcol, ad, bd, acc0, leader);
 #pragma unroll
-                    for (int kk = 0; kk < kKC / 32; kk++)
-                        mma_f8(dcol, ad + 2 * kk, bd + 2 * kk, (first && kk == 0) ? 0u : 1u);
-                    mma_commit(&empty_a[sa]);
-                    mma_commit(&empty_b[sb]);
+                    for (int kk = 1; kk < kKC / 32; kk++) mma_f8_warp(dcol, ad + 2 * kk, bd + 2 * kk, 1u, leader);
+                    if (s % kRelease == kRelease - 1) mma_commit_warp(&empty_ab[s / kRelease], leader);
+                    if (++s == kStagesA) { s = 0; ph ^= 1; }
                 }
                 if (!ok) break;
-                mma_commit(&acc_full[b]);
+                mma_commit_warp(&acc_full[b], leader);
             }
-            if (P.waits) {
+            if (P.waits && leader) {
                 unsigned long long *wp = P.waits + blockIdx.x * kWaitSlots;
                 wp[0] = (unsigned long long)w_a;
                 wp[1] = (unsigned long long)w_b;
                 wp[2] = (unsigned long long)w_acc;
                 wp[7] = (unsigned long long)(clock64() - t_start);
             }
-            mma_commit(&drain_bar);
+            __syncwarp();
+            mma_commit_warp(&drain_bar, leader);
             const uint64_t t0 = now_ns();
             while (!mbar_try(&drain_bar, 0) && now_ns() - t0 < kTimeoutNs) {}
         }
@@ -557,7 +539,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
         const int l = r & 31, w = r >> 5;
         const int pwarp = (tid >> 5) - kEpiWarps;
         uint64_t g = 0;
-        long long w_prod = 0;
+        long long w_prod = 0, w_prod_acc = 0;
         for (int64_t i = 0; i < n_my; i++) {
             if (abort_flag) break;
             const int dq = (int)(i % kDescDepth);
@@ -586,7 +568,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
             bool ok = true;
             // two-word slices of this row, loaded kPf stages ahead (a register
             // ring indexed statically: the stage loop is unrolled by kPf)
-            constexpr int kPf = 4;
+            constexpr int kPf = EPI_TC_PREFETCH;
             uint2 ring[kPf];
 #pragma unroll
             for (int u = 0; u < kPf; u++) {
@@ -616,7 +598,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                     }
                     const int s = (int)(g % kStagesA);
                     const uint32_t us = (uint32_t)(g / kStagesA);
-                    if (!wait_fast(&empty_a[s], (us & 1) ^ 1, &abort_flag, w_prod)) { ok = false; break; }
+                    if (!wait_fast(&empty_ab[s / kRelease], (us & 1) ^ 1, &abort_flag, w_prod)) { ok = false; break; }
                     if (active) {
                         const uint32_t c2 = __popc(cur.x) + __popc(cur.y);
                         if (kc < DS.chunks_case) t1 += c2;
@@ -636,20 +618,23 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                     }
                     fence_proxy_async();
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(&full_a[s]);
+                    if (lane == 0) mbar_arrive(&full_ab[s]);
                     g++;
                 }
             }
             if (!ok) break;
             const int b = (int)(i & 1);
             const uint32_t ub = (uint32_t)(i >> 1);
-            if (!mbar_wait(&acc_empty[b], (ub & 1) ^ 1, &abort_flag)) break;
+            if (!wait_fast(&acc_empty[b], (ub & 1) ^ 1, &abort_flag, w_prod_acc)) break;
             tot[((b * 128 + r) * 2 + half) * 2 + 0] = t1;
             tot[((b * 128 + r) * 2 + half) * 2 + 1] = t0;
             __syncwarp();
             if (lane == 0) mbar_arrive(&tot_full[b]);
         }
-        if (P.waits && t == 0) P.waits[blockIdx.x * kWaitSlots + 3] = (unsigned long long)w_prod;
+        if (P.waits && t == 0) {
+            P.waits[blockIdx.x * kWaitSlots + 3] = (unsigned long long)w_prod;
+            P.waits[blockIdx.x * kWaitSlots + 4] = (unsigned long long)w_prod_acc;
+        }
         (void)pwarp;
     } else {
         // -------------------------------------------------------- epilogue
@@ -669,7 +654,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
             const uint32_t ub = (uint32_t)(i >> 1);
             bool ok = mbar_wait(&desc_full[dq], ud & 1, &abort_flag);
             ok = ok && wait_fast(&acc_full[b], ub & 1, &abort_flag, w_epi);
-            ok = ok && mbar_wait(&tot_full[b], ub & 1, &abort_flag);
+            ok = ok && wait_fast(&tot_full[b], ub & 1, &abort_flag, w_epi);
             ok = __all_sync(0xffffffffu, ok);
             tc_fence_after();
             const Desc &D = desc[dq];

@@ -144,6 +144,8 @@ def load(path: str | None = None):
         lib.epi_mlp_gradients.argtypes = [V, P, P, i64, P, P]
         lib.epi_mlp_train_step.restype = i32
         lib.epi_mlp_train_step.argtypes = [V, P, P, i64, C.c_float, C.c_float, P]
+        lib.epi_mlp_set_forward_path.restype = i32
+        lib.epi_mlp_set_forward_path.argtypes = [V, i32]
         lib.epi_mlp_num_inputs.restype = i32
         lib.epi_mlp_num_inputs.argtypes = [V]
         lib.epi_mlp_set_input_norm.restype = i32
@@ -230,7 +232,7 @@ class Context:
         """Per-role wait cycles of the last profiled tensor-core search."""
         out = np.zeros(8, dtype=np.float64)
         _check(load().epi_profile_waits(self._h, _np_ptr(out)))
-        names = ["mma_wait_a", "mma_wait_b", "mma_wait_acc", "prod_wait_stage", "unused4", "epi_wait_acc",
+        names = ["mma_wait_a", "mma_wait_b", "mma_wait_acc", "prod_wait_stage", "prod_wait_acc", "epi_wait_acc",
                  "tma_wait_stage", "mma_loop"]
         return {k: float(v) for k, v in zip(names, out)}
 
@@ -531,6 +533,10 @@ class MLP:
         _check(load().epi_mlp_train_step(self._h, _dptr(X.contiguous()), _dptr(t.contiguous()), X.shape[0],
                                           lr, wd, C.byref(loss)))
         return loss.value
+
+    def set_forward_path(self, path: str):
+        """'auto', 'cuda_cores' or 'tensor_cores' for forward()."""
+        _check(load().epi_mlp_set_forward_path(self._h, {"auto": 0, "cuda_cores": 1, "tensor_cores": 2}[path]))
 
     def input_norm(self) -> tuple[np.ndarray, np.ndarray]:
         shift = np.zeros(self.n_in, dtype=np.float32)
