@@ -314,8 +314,14 @@ epi_status epi_mlp_train_step(epi_mlp *net, const float *X_dev, const float *t_d
  * approximation whose result is exact only for the sets it proposes. */
 typedef struct epi_proposer_opts {
     int top_triples;   /* 1..4096 */
-    int budget;        /* proposals re-scored exactly, 1..4096 */
-    int top_n;         /* 1..budget */
+    int budget;        /* proposals re-scored exactly, 1..2^30; above 4096 every
+                          ranked score is kept in device memory (5 bytes per
+                          candidate, EPI_ENOMEM if that does not fit), the
+                          budget is met by a threshold on the ranking score
+                          (candidates tied at it are all proposed), every
+                          proposal is scored exactly in FP32 and the 4096 best
+                          of those again in FP64 */
+    int top_n;         /* 1..min(budget, 4096) */
     int64_t chunk;
 } epi_proposer_opts;
 typedef struct epi_proposer_stats {
@@ -323,6 +329,9 @@ typedef struct epi_proposer_stats {
     uint64_t kept;         /* distinct sets among them (ranked) */
     uint64_t proposals;    /* sets re-scored exactly */
     double ms_lower, ms_rank, ms_rescore;   /* wall time of the three stages */
+    int32_t exact_in_proposals;   /* 1: out is the exact top_n of the proposals
+                                     (always for budgets up to 4096; above, when
+                                     the FP32 pool margin proves it) */
 } epi_proposer_stats;
 epi_status epi_proposer_search(epi_dataset *ds, epi_mlp *net, const epi_proposer_opts *opts, epi_result *out,
                                uint32_t *counts, int32_t *n_out, epi_proposer_stats *stats);

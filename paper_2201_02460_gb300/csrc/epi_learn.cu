@@ -189,6 +189,77 @@ __global__ void candidates5_at_kernel(DevData d, const uint32_t *__restrict__ tr
     }
 }
 
+// C(x, 2) and C(x, 3) by arithmetic (x < 2^21, so no overflow)
+__device__ __forceinline__ uint64_t c2(int64_t x) { return x < 2 ? 0ull : (uint64_t)(x * (x - 1) / 2); }
+__device__ __forceinline__ uint64_t c3(int64_t x) { return x < 3 ? 0ull : (uint64_t)(x * (x - 1) * (x - 2) / 6); }
+
+// Candidates [first, first + count) in one pass: the set, whether its
+// generating triple is its best (keep), its 25 features, and optionally its
+// order-5 label ln(s5[rank] + 1e-7) (training); the set itself is written
+// only when combs is given.
+__global__ void __launch_bounds__(256) cand_features5_kernel(DevData d, const uint32_t *__restrict__ triples,
+                                                             int64_t first, int64_t count, const float *__restrict__ s1,
+                                                             const float *__restrict__ s2, const float *__restrict__ s3,
+                                                             const float *__restrict__ s5, float *__restrict__ X,
+                                                             uint8_t *__restrict__ keep, float *__restrict__ label,
+                                                             uint32_t *__restrict__ combs)
+{
+    const int64_t n = d.n;
+    const uint64_t n2 = c2(n), n3 = c3(n);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t v[5], g3[3];
+        candidate_at(d, triples, (uint64_t)(first + i), v, g3);
+        if (combs) {
+#pragma unroll
+            for (int p = 0; p < 5; p++) combs[i * 5 + p] = (uint32_t)v[p];
+        }
+        // the ten triples: ranks and scores; the generating triple's rank
+        const uint64_t gr = n3 - 1 - (c3(n - 1 - g3[0]) + c2(n - 1 - g3[1]) + (uint64_t)(n - 1 - g3[2]));
+        float f3[10];
+        float gs = 0.0f;
+        uint64_t r3[10];
+        int q = 0;
+#pragma unroll
+        for (int a = 0; a < 5; a++)
+#pragma unroll
+            for (int b = a + 1; b < 5; b++)
+#pragma unroll
+                for (int e = b + 1; e < 5; e++) {
+                    r3[q] = n3 - 1 - (c3(n - 1 - v[a]) + c2(n - 1 - v[b]) + (uint64_t)(n - 1 - v[e]));
+                    f3[q] = s3[r3[q]];
+                    if (r3[q] == gr) gs = f3[q];
+                    q++;
+                }
+        bool best = true;
+#pragma unroll
+        for (int t = 0; t < 10; t++)
+            if (f3[t] > gs || (f3[t] == gs && r3[t] < gr)) best = false;
+        keep[i] = best ? 1 : 0;
+        float f2[10], f1[5];
+        q = 0;
+#pragma unroll
+        for (int a = 0; a < 5; a++)
+#pragma unroll
+            for (int b = a + 1; b < 5; b++) f2[q++] = s2[n2 - 1 - (c2(n - 1 - v[a]) + (uint64_t)(n - 1 - v[b]))];
+#pragma unroll
+        for (int t = 0; t < 5; t++) f1[t] = s1[v[t]];
+        if (label) {
+            int32_t c5[5] = {v[0], v[1], v[2], v[3], v[4]};
+            label[i] = logf(fmaxf(s5[lex_rank(d.binom, n, 5, c5)], 0.0f) + 1e-7f);
+        }
+        sort_desc(f1);
+        sort_desc(f2);
+        sort_desc(f3);
+        float *x = X + i * 25;
+#pragma unroll
+        for (int t = 0; t < 5; t++) x[t] = logf(fmaxf(f1[t], 0.0f) + 1e-7f);
+#pragma unroll
+        for (int t = 0; t < 10; t++) x[5 + t] = logf(fmaxf(f2[t], 0.0f) + 1e-7f);
+#pragma unroll
+        for (int t = 0; t < 10; t++) x[15 + t] = logf(fmaxf(f3[t], 0.0f) + 1e-7f);
+    }
+}
+
 // out[i] = table[lex rank of combs[i]] for an order-k score table
 __global__ void lookup_kernel(DevData d, int k, const float *__restrict__ table, const uint32_t *__restrict__ combs,
                               int64_t count, float *__restrict__ out)
@@ -758,6 +829,15 @@ cudaError_t launch_candidates5_at(const DevData &d, const uint32_t *triples, con
                                   uint32_t *combs, cudaStream_t st)
 {
     learn::candidates5_at_kernel<<<blocks_for(count), 256, 0, st>>>(d, triples, idx, count, combs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cand_features5(const DevData &d, const uint32_t *triples, int64_t first, int64_t count,
+                                  const float *s1, const float *s2, const float *s3, const float *s5, float *X,
+                                  uint8_t *keep, float *label, uint32_t *combs, cudaStream_t st)
+{
+    learn::cand_features5_kernel<<<blocks_for(count), 256, 0, st>>>(d, triples, first, count, s1, s2, s3, s5, X, keep,
+                                                                    label, combs);
     return cudaGetLastError();
 }
 

@@ -45,13 +45,6 @@ __global__ void count_kernel(const uint8_t *__restrict__ keep, int64_t count, un
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
 }
 
-// t[i] = ln(max(s, 0) + 1e-7): the training label of an order-5 score
-__global__ void log_label_kernel(float *t, int64_t count)
-{
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
-        t[i] = logf(fmaxf(t[i], 0.0f) + 1e-7f);
-}
-
 // mean and standard deviation of column f of X [rows][cols] (one block per
 // column, FP64 sums in a fixed order)
 __global__ void __launch_bounds__(256) moments_kernel(const float *__restrict__ X, int64_t rows, int cols,
@@ -111,6 +104,52 @@ __global__ void gather_batch_kernel(const float *__restrict__ X, const float *__
 }
 
 int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8192)); }
+
+// order-preserving unsigned key of a float (NaN below every number)
+__device__ __forceinline__ uint32_t fkey(float v)
+{
+    if (v != v) return 0u;
+    const uint32_t b = __float_as_uint(v);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+// histogram of key bits [shift, shift + log2 bins) over kept entries whose
+// key agrees with `prefix` above bit `pshift` (pshift = 32: no condition)
+__global__ void __launch_bounds__(256) key_hist_kernel(const float *__restrict__ v, const uint8_t *__restrict__ keep,
+                                                       uint64_t count, int shift, int bins, int pshift,
+                                                       uint32_t prefix, unsigned long long *__restrict__ hist)
+{
+    __shared__ uint32_t h[4096];
+    for (int i = threadIdx.x; i < bins; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (uint64_t)gridDim.x * blockDim.x) {
+        if (!keep[i]) continue;
+        const uint32_t k = fkey(v[i]);
+        if (pshift < 32 && (k >> pshift) != prefix) continue;
+        atomicAdd(&h[(k >> shift) & (uint32_t)(bins - 1)], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < bins; i += blockDim.x)
+        if (h[i]) atomicAdd(&hist[i], (unsigned long long)h[i]);
+}
+
+// indices of kept entries with key >= thr (appended in any order)
+__global__ void select_kernel(const float *__restrict__ v, const uint8_t *__restrict__ keep, uint64_t count, uint32_t thr,
+                              uint64_t *__restrict__ out, unsigned long long *__restrict__ n_out, uint64_t cap)
+{
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (uint64_t)gridDim.x * blockDim.x) {
+        if (keep[i] && fkey(v[i]) >= thr) {
+            const unsigned long long at = atomicAdd(n_out, 1ull);
+            if (at < cap) out[at] = i;
+        }
+    }
+}
+
+__global__ void gather_u64_kernel(const uint64_t *__restrict__ src, const uint64_t *__restrict__ pos,
+                                  const int32_t *__restrict__ n, uint64_t *__restrict__ dst)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < *n; i += gridDim.x * blockDim.x) dst[i] = src[pos[i]];
+}
 
 // device allocations released on the stream when the scope ends
 struct Pool {
@@ -200,6 +239,117 @@ epi_status best_triples(epi_dataset *ds, Pool &pool, const float *s3, int T, uin
     return EPI_OK;
 }
 
+// Budgets above 4096: every ranked score stays in device memory (5 bytes per
+// candidate); the budget's threshold is found by a three-pass radix select on
+// the scores' order-preserving keys (12 + 12 + 8 bits), every kept candidate at
+// or above it is proposed (ties at the threshold included), every proposal is
+// counted and scored exactly in FP32 in slices, and the 4096 best by exact
+// FP32 score form the pool that the caller re-scores in FP64.
+epi_status large_budget(epi_dataset *ds, epi_mlp *net, const DevData &d, const Lower &L, const uint32_t *triples,
+                        uint64_t total, uint64_t R, int64_t chunk, Pool &pool, uint64_t **pool_idx, int32_t *n_pool,
+                        unsigned long long *kept_out, uint64_t *selected_out, float *pool_floor, int &launches)
+{
+    epi_ctx *ctx = epi_dataset_ctx(ds);
+    cudaStream_t st = epi_ctx_stream(ctx);
+    size_t free_b = 0, total_b = 0;
+    PCK(cudaMemGetInfo(&free_b, &total_b));
+    const size_t need = (size_t)total * 5 + (size_t)chunk * 100 + ((size_t)1 << 30);
+    if (need > free_b) return pfail(EPI_ENOMEM, "epi_proposer_search: the candidate space's scores do not fit in device memory");
+    float *score;
+    uint8_t *keep;
+    float *X;
+    unsigned long long *kept_dev, *hist, *nsel;
+    PCK(pool.get(&score, total));
+    PCK(pool.get(&keep, total));
+    PCK(pool.get(&X, (size_t)chunk * 25));
+    PCK(pool.get(&kept_dev, 1));
+    PCK(pool.get(&hist, 4096));
+    PCK(pool.get(&nsel, 1));
+    PCK(cudaMemsetAsync(kept_dev, 0, 8, st));
+    for (uint64_t first = 0; first < total; first += (uint64_t)chunk) {
+        const int64_t cnt = (int64_t)std::min<uint64_t>((uint64_t)chunk, total - first);
+        PCK(launch_cand_features5(d, triples, (int64_t)first, cnt, L.s[1], L.s[2], L.s[3], nullptr, X, keep + first,
+                                  nullptr, nullptr, st));
+        if (net) PST(epi_mlp_forward(net, X, cnt, score + first));
+        else PST(epi_heuristic5(ctx, X, cnt, score + first));
+        count_kernel<<<grid_for(cnt), 256, 0, st>>>(keep + first, cnt, kept_dev);
+        launches += 3;
+    }
+    PCK(cudaMemcpyAsync(kept_out, kept_dev, 8, cudaMemcpyDeviceToHost, st));
+    // radix select of the R-th best key among the kept candidates
+    const int hgrid = 4 * epi_ctx_num_sms(ctx);
+    uint32_t prefix = 0;
+    uint64_t above = 0;           // kept keys above the current prefix's range
+    uint64_t at_thr = 0;          // kept keys equal to the final threshold
+    const int shifts[3] = {20, 8, 0}, widths[3] = {12, 12, 8};
+    std::vector<unsigned long long> h(4096);
+    for (int pass = 0; pass < 3; pass++) {
+        const int bins = 1 << widths[pass];
+        const int pshift = pass == 0 ? 32 : shifts[pass - 1];
+        PCK(cudaMemsetAsync(hist, 0, (size_t)bins * 8, st));
+        key_hist_kernel<<<hgrid, 256, 0, st>>>(score, keep, total, shifts[pass], bins, pshift, prefix, hist);
+        launches += 1;
+        PCK(cudaMemcpyAsync(h.data(), hist, (size_t)bins * 8, cudaMemcpyDeviceToHost, st));
+        PCK(cudaStreamSynchronize(st));
+        int b = bins - 1;
+        while (b > 0 && above + h[b] < R) above += h[b--];
+        prefix = (prefix << widths[pass]) | (uint32_t)b;
+        at_thr = h[b];
+    }
+    const uint32_t thr = prefix;
+    const uint64_t cap = above + at_thr;
+    uint64_t *sel;
+    PCK(pool.get(&sel, std::max<uint64_t>(cap, 1)));
+    PCK(cudaMemsetAsync(nsel, 0, 8, st));
+    select_kernel<<<hgrid, 256, 0, st>>>(score, keep, total, thr, sel, nsel, cap);
+    launches += 1;
+    unsigned long long n_sel = 0;
+    PCK(cudaMemcpyAsync(&n_sel, nsel, 8, cudaMemcpyDeviceToHost, st));
+    PCK(cudaStreamSynchronize(st));
+    n_sel = std::min<unsigned long long>(n_sel, cap);
+    *selected_out = n_sel;
+    pool.release(score);
+    pool.release(X);
+    if (n_sel == 0) {
+        *n_pool = 0;
+        return EPI_OK;
+    }
+    // exact FP32 scores of every proposal, in slices
+    constexpr int64_t kSlice = (int64_t)1 << 20;
+    float *exact;
+    uint32_t *pc, *tabs;
+    PCK(pool.get(&exact, n_sel));
+    PCK(pool.get(&pc, (size_t)std::min<int64_t>((int64_t)n_sel, kSlice) * 5));
+    PCK(pool.get(&tabs, (size_t)std::min<int64_t>((int64_t)n_sel, kSlice) * 2 * 243));
+    for (int64_t off = 0; off < (int64_t)n_sel; off += kSlice) {
+        const int64_t c = std::min<int64_t>(kSlice, (int64_t)n_sel - off);
+        PCK(launch_candidates5_at(d, triples, sel + off, c, pc, st));
+        PCK(launch_tables(d, 5, pc, c, tabs, epi_ctx_num_sms(ctx), st));
+        PCK(launch_score_tables(d, 5, tabs, c, exact + off, nullptr, epi_ctx_num_sms(ctx), st));
+        launches += 3;
+    }
+    // the pool: the 4096 best proposals by exact FP32 score
+    const int kp = (int)std::min<unsigned long long>(4096ull, n_sel);
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)n_sel + 65535) / 65536, 2 * epi_ctx_num_sms(ctx)));
+    float *bs, *vs;
+    uint64_t *bi, *pos;
+    int32_t *bn, *nn;
+    PCK(pool.get(&bs, (size_t)blocks * kp));
+    PCK(pool.get(&bi, (size_t)blocks * kp));
+    PCK(pool.get(&bn, blocks));
+    PCK(pool.get(&vs, kp));
+    PCK(pool.get(&pos, kp));
+    PCK(pool.get(&nn, 1));
+    PCK(launch_topk(exact, nullptr, (int64_t)n_sel, kp, bs, bi, bn, blocks, vs, pos, nn, st));
+    PCK(pool.get(pool_idx, kp));
+    gather_u64_kernel<<<(kp + 255) / 256, 256, 0, st>>>(sel, pos, nn, *pool_idx);
+    launches += 3;
+    PCK(cudaMemcpyAsync(n_pool, nn, 4, cudaMemcpyDeviceToHost, st));
+    PCK(cudaMemcpyAsync(pool_floor, vs + kp - 1, 4, cudaMemcpyDeviceToHost, st));
+    PCK(cudaStreamSynchronize(st));
+    return EPI_OK;
+}
+
 }  // namespace prop
 }  // namespace epi
 
@@ -217,8 +367,8 @@ epi_status epi_proposer_search(epi_dataset *ds, epi_mlp *net, const epi_proposer
     const int R = opts->budget, top_n = opts->top_n;
     if (opts->top_triples < 1 || opts->top_triples > 4096)
         return pfail(EPI_EINVAL, "epi_proposer_search: top_triples outside 1..4096");
-    if (R < 1 || R > 4096) return pfail(EPI_EINVAL, "epi_proposer_search: budget outside 1..4096");
-    if (top_n < 1 || top_n > R) return pfail(EPI_EINVAL, "epi_proposer_search: top_n outside 1..budget");
+    if (R < 1 || R > (1 << 30)) return pfail(EPI_EINVAL, "epi_proposer_search: budget outside 1..2^30");
+    if (top_n < 1 || top_n > std::min(R, 4096)) return pfail(EPI_EINVAL, "epi_proposer_search: top_n outside 1..min(budget, 4096)");
     const DevData d = epi_dataset_dev(ds);
     if (d.n < 5) return pfail(EPI_EINVAL, "epi_proposer_search: needs at least 5 SNPs");
     epi_ctx *ctx = epi_dataset_ctx(ds);
@@ -240,17 +390,26 @@ epi_status epi_proposer_search(epi_dataset *ds, epi_mlp *net, const epi_proposer
     const uint64_t per = host_binom(d.n - 3, 2);
     const uint64_t total = (uint64_t)T * per;
     const int64_t chunk = (int64_t)std::min<uint64_t>(total, opts->chunk > 0 ? (uint64_t)opts->chunk : (uint64_t)1 << 22);
-    uint32_t *combs;
+    int launches = 0;
+    // the proposals: candidate indices (device) of the sets re-scored below
+    int32_t n_prop = 0;
+    unsigned long long kept = 0;
+    uint64_t *lr = nullptr;
+    uint64_t selected = 0;
+    float pool_floor = -INFINITY;     // exact FP32 score of the weakest pooled proposal (large budgets)
+    if (R > 4096) {
+        PST(large_budget(ds, net, d, L, triples, total, (uint64_t)R, chunk, pool, &lr, &n_prop, &kept, &selected,
+                         &pool_floor, launches));
+    } else {
     uint8_t *keep;
     float *X, *y;
-    PCK(pool.get(&combs, (size_t)chunk * 5));
     PCK(pool.get(&keep, chunk));
     PCK(pool.get(&X, (size_t)chunk * 25));
     PCK(pool.get(&y, chunk));
     // running best: list 0 = best so far, list 1 = this chunk's best
     const int topk_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((chunk + 65535) / 65536, 2 * epi_ctx_num_sms(ctx)));
     float *ls, *bs, *ms;
-    uint64_t *lr, *bi, *mr;
+    uint64_t *bi, *mr;
     int32_t *lc, *bn, *mn;
     unsigned long long *kept_dev;
     PCK(pool.get(&ls, (size_t)2 * R));
@@ -265,11 +424,10 @@ epi_status epi_proposer_search(epi_dataset *ds, epi_mlp *net, const epi_proposer
     PCK(pool.get(&kept_dev, 1));
     PCK(cudaMemsetAsync(lc, 0, 8, st));
     PCK(cudaMemsetAsync(kept_dev, 0, 8, st));
-    int launches = 0;
     for (uint64_t first = 0; first < total; first += (uint64_t)chunk) {
         const int64_t cnt = (int64_t)std::min<uint64_t>((uint64_t)chunk, total - first);
-        PCK(launch_candidates5(d, triples, (int64_t)first, cnt, combs, L.s[3], keep, st));
-        PCK(launch_features5(d, L.s[1], L.s[2], L.s[3], combs, cnt, X, st));
+        PCK(launch_cand_features5(d, triples, (int64_t)first, cnt, L.s[1], L.s[2], L.s[3], nullptr, X, keep, nullptr,
+                                  nullptr, st));
         if (net) PST(epi_mlp_forward(net, X, cnt, y));
         else PST(epi_heuristic5(ctx, X, cnt, y));
         count_kernel<<<grid_for(cnt), 256, 0, st>>>(keep, cnt, kept_dev);
@@ -281,11 +439,11 @@ epi_status epi_proposer_search(epi_dataset *ds, epi_mlp *net, const epi_proposer
         PCK(cudaMemcpyAsync(lc, mn, 4, cudaMemcpyDeviceToDevice, st));
         launches += 7;
     }
-    int32_t n_prop = 0;
-    unsigned long long kept = 0;
     PCK(cudaMemcpyAsync(&n_prop, lc, 4, cudaMemcpyDeviceToHost, st));
     PCK(cudaMemcpyAsync(&kept, kept_dev, 8, cudaMemcpyDeviceToHost, st));
     PCK(cudaStreamSynchronize(st));
+    selected = (uint64_t)n_prop;
+    }
     const double t2 = now_ms();
 
     // exact re-score of the proposals
@@ -347,7 +505,14 @@ epi_status epi_proposer_search(epi_dataset *ds, epi_mlp *net, const epi_proposer
     if (stats) {
         stats->candidates = total;
         stats->kept = kept;
-        stats->proposals = (uint64_t)n_prop;
+        stats->proposals = selected;
+        // exact among the proposals: every proposal outside the pool scored at
+        // most pool_floor in FP32, so at most pool_floor (1 + eps) exactly
+        stats->exact_in_proposals =
+            (selected <= (uint64_t)n_prop ||
+             (n_res == top_n && h64[order[n_res - 1]] > (double)pool_floor * (1.0 + f32_rel_bound(5))))
+                ? 1
+                : 0;
         stats->ms_lower = t1 - t0;
         stats->ms_rank = t2 - t1;
         stats->ms_rescore = t3 - t2;
@@ -407,16 +572,12 @@ epi_status epi_proposer_train(epi_mlp *net, epi_dataset *const *datasets, int n_
         int T = 0;
         PST(best_triples(ds, lp, L.s[3], Ts[i], &triples, &T));
         const int64_t cnt = base[i + 1] - base[i];
-        uint32_t *combs;
-        PCK(lp.get(&combs, (size_t)std::min<int64_t>(cnt, (int64_t)1 << 24) * 5));
         for (int64_t f = 0; f < cnt; f += (int64_t)1 << 24) {
             const int64_t c = std::min<int64_t>(cnt - f, (int64_t)1 << 24);
             const int64_t at = base[i] + f;
-            PCK(launch_candidates5(d, triples, f, c, combs, L.s[3], keep + at, st));
-            PCK(launch_features5(d, L.s[1], L.s[2], L.s[3], combs, c, X + at * n_in, st));
-            PCK(launch_lookup(d, 5, L.s[5], combs, c, t + at, st));
-            log_label_kernel<<<grid_for(c), 256, 0, st>>>(t + at, c);
-            launches += 4;
+            PCK(launch_cand_features5(d, triples, f, c, L.s[1], L.s[2], L.s[3], L.s[5], X + at * n_in, keep + at,
+                                      t + at, nullptr, st));
+            launches += 1;
         }
         // this dataset's best-labelled kept rows
         const int kt = (int)std::min<int64_t>(kTail, cnt);

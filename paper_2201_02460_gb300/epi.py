@@ -70,7 +70,8 @@ class ProposerOpts(C.Structure):
 
 class ProposerStats(C.Structure):
     _fields_ = [("candidates", C.c_uint64), ("kept", C.c_uint64), ("proposals", C.c_uint64),
-                ("ms_lower", C.c_double), ("ms_rank", C.c_double), ("ms_rescore", C.c_double)]
+                ("ms_lower", C.c_double), ("ms_rank", C.c_double), ("ms_rescore", C.c_double),
+                ("exact_in_proposals", C.c_int32)]
 
 
 class TrainOpts(C.Structure):

@@ -118,8 +118,8 @@ def test_train_fits_and_stores_standardisation(epi, ctx):
 def test_invalid_arguments(epi, ctx):
     geno, pheno = random_data(12, 300, seed=1)
     ds = epi.Dataset(ctx, geno, pheno)
-    for kw in (dict(top_triples=0, budget=10, top_n=5), dict(top_triples=5, budget=5000, top_n=5),
-               dict(top_triples=5, budget=10, top_n=11)):
+    for kw in (dict(top_triples=0, budget=10, top_n=5), dict(top_triples=5, budget=0, top_n=1),
+               dict(top_triples=5, budget=10, top_n=11), dict(top_triples=5, budget=10000, top_n=4097)):
         with pytest.raises(epi.EpiError):
             epi.proposer_search(ds, None, **kw)
     g4, p4 = random_data(4, 300, seed=1)
@@ -171,3 +171,41 @@ def test_trained_network_ranks_better_than_heuristic(epi, ctx):
         r_net = _spearman(net.forward(X)[k].cpu().numpy(), truth)
         r_heur = _spearman(epi.heuristic5(ctx, X)[k].cpu().numpy(), truth)
         assert r_net >= 0.45 and r_net >= r_heur + 0.1, (es, r_net, r_heur)
+
+
+def test_large_budget_covering_every_set_is_exhaustive(epi, ctx):
+    # budget above 4096 (threshold path) and above the number of distinct sets
+    geno, pheno = random_data(14, 500, seed=29)
+    ds = epi.Dataset(ctx, geno, pheno)
+    r, st = epi.proposer_search(ds, None, top_triples=math.comb(14, 3), budget=100000, top_n=20, chunk=3001)
+    assert st["kept"] == math.comb(14, 5) == st["proposals"]
+    oc, om, _ = O.search(geno, pheno, 5, 20)
+    check_topn(r.combs, r.mi, oc, om)
+
+
+@pytest.mark.parametrize("use_net", [False, True])
+def test_large_budget_proposals_follow_the_ranking(epi, ctx, use_net):
+    n, T, R, top_n = 40, 128, 20000, 100
+    geno, pheno = random_data(n, 900, seed=31)
+    ds = epi.Dataset(ctx, geno, pheno)
+    net = epi.MLP(ctx, 25, 64, seed=5) if use_net else None
+    scorer = (lambda X: net.forward(X)) if use_net else (lambda X: epi.heuristic5(ctx, X))
+    r, st = epi.proposer_search(ds, net, T, R, top_n, chunk=10007)
+    # the same ranking from the single-step calls: every kept candidate whose
+    # score reaches the budget's threshold (ties at it included)
+    S = [epi.score_all(ds, k) for k in (1, 2, 3)]
+    _, ti = epi.topk(ctx, S[2], T)
+    tri = epi.unrank(ds, 3, ti)
+    combs, keep = epi.candidates5(ds, tri, 0, T * math.comb(n - 3, 2), s3=S[2])
+    y = scorer(epi.features5(ds, *S, combs)).cpu().numpy()
+    k = keep.cpu().numpy().astype(bool)
+    ys = np.sort(y[k])[::-1]
+    thr = ys[R - 1]
+    sel = combs.cpu().numpy()[k & (y >= thr)]
+    assert st["proposals"] == len(sel) >= R
+    t = O.tables(geno, pheno, sel.astype(np.int32))
+    mi = np.array([O.mi(x[0], x[1], 900) for x in t])
+    ranks = np.array([O.rank(n, 5, c) for c in sel])
+    order = np.lexsort((ranks, -mi))[:top_n]
+    assert st["exact_in_proposals"] == 1
+    check_topn(r.combs, r.mi, sel[order], mi[order])
