@@ -35,7 +35,8 @@
 //               tile's last SNPs
 //   warps 8-15  A producers: prefix rows = AND of the prefix SNPs' bit rows,
 //               expanded to E4M3 bytes in the 128-byte-swizzled K-major
-//               layout; two threads per row, next K stage prefetched
+//               layout; one thread per row and alternate K stages per
+//               half of the producers, own stages prefetched
 //   warp 16     TMA producer of B tiles, and writer of the item descriptors
 //   warp 17     TMEM allocator and MMA issuer (one elected thread)
 // Every mbarrier wait is bounded (about 2 s); a wait that gives up sets
@@ -52,7 +53,7 @@
 // A producers' load distance in K stages and the stage-release group size
 // (tuning parameters)
 #ifndef EPI_TC_PREFETCH
-#define EPI_TC_PREFETCH 4
+#define EPI_TC_PREFETCH 2
 #endif
 #ifndef EPI_TC_RELEASE
 #define EPI_TC_RELEASE 3
@@ -360,8 +361,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
     // advance together), released by one MMA commit
     static_assert(kStagesA == kStagesB, "the A and B rings share their release barriers");
     static_assert(kStagesA % kRelease == 0, "release groups tile the ring");
-    // full_ab[s]: the A producers' warps and the TMA thread (with its bytes)
-    // have filled stage s of both operands
+    static_assert(kStagesA % 2 == 0, "the producer halves take the ring slots of one parity each");
+    // full_ab[s]: the A producer warps of the slot's parity and the TMA
+    // thread (with its bytes) have filled stage s of both operands
     __shared__ __align__(8) uint64_t full_ab[kStagesA], empty_ab[kStagesA / kRelease];
     __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], tot_full[2];
     __shared__ __align__(8) uint64_t desc_full[kDescDepth], desc_empty[kDescDepth], drain_bar;
@@ -382,7 +384,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
 
     if (tid == 0) {
         for (int s = 0; s < kStagesA; s++) {
-            mbar_init(&full_ab[s], kProdWarps + 1);
+            mbar_init(&full_ab[s], kProdWarps / 2 + 1);   // one half of the producers + the TMA thread
             if (s % kRelease == 0) mbar_init(&empty_ab[s / kRelease], 1);
         }
         for (int b = 0; b < 2; b++) {
@@ -533,12 +535,15 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
         }
     } else if (warp >= kEpiWarps) {
         // ---------------------------------------------------- A producers
+        // Thread t owns tile row r = t % 128 in the ring slots of parity
+        // t / 128 (the two halves of the producers take alternate stages), and
+        // writes all 128 individuals of the row's stage: four mask words,
+        // each expanded to 32 bytes.
         const int t = tid - kEpiThreads;     // 0 .. 255
-        const int r = t >> 1;                // tile row
-        const int half = t & 1;              // words 2 half, 2 half + 1 of a stage
+        const int r = t & 127;
+        const int grp = t >> 7;
         const int l = r & 31, w = r >> 5;
-        const int pwarp = (tid >> 5) - kEpiWarps;
-        uint64_t g = 0;
+        uint64_t g = 0;                      // stages of the CTA so far (both halves)
         long long w_prod = 0, w_prod_acc = 0;
         for (int64_t i = 0; i < n_my; i++) {
             if (abort_flag) break;
@@ -546,7 +551,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
             const uint32_t ud = (uint32_t)(i / kDescDepth);
             if (!mbar_wait(&desc_full[dq], ud & 1, &abort_flag)) break;
             const Desc &D = desc[dq];
-            const uint2 *rows[km1];
+            const uint4 *rows[km1];
             bool active = false;
             if (l < kPPW * kPR) {
                 const int p = w * kPPW + l / kPR;
@@ -558,7 +563,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                         const int gg = rem / div;
                         rem -= gg * div;
                         div = div > 1 ? div / 3 : 1;
-                        rows[tt] = reinterpret_cast<const uint2 *>(d.masks + ((int64_t)D.snp[p * km1 + tt] * 3 + gg) * d.Wt) + half;
+                        rows[tt] = reinterpret_cast<const uint4 *>(d.masks + ((int64_t)D.snp[p * km1 + tt] * 3 + gg) * d.Wt);
                     }
                 }
             }
@@ -566,68 +571,67 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
             if (lane == 0) mbar_arrive(&desc_empty[dq]);
             uint32_t t1 = 0, t0 = 0;
             bool ok = true;
-            // two-word slices of this row, loaded kPf stages ahead (a register
-            // ring indexed statically: the stage loop is unrolled by kPf)
+            const int chunks = DS.chunks, chunks_case = DS.chunks_case;
+            const int kc0 = (int)(((uint64_t)grp + 2 - (g & 1)) & 1);   // this half's first stage of the item
+            const int mine = (chunks - kc0 + 1) / 2;
+            // this row's words of the next kPf own stages (a register ring
+            // indexed statically: the loop is unrolled by kPf)
             constexpr int kPf = EPI_TC_PREFETCH;
-            uint2 ring[kPf];
+            uint4 ring[kPf];
+            auto fetch = [&](int kc) {
+                uint4 a = __ldg(rows[0] + kc);
 #pragma unroll
-            for (int u = 0; u < kPf; u++) {
-                ring[u] = make_uint2(0, 0);
-                if (active && u < DS.chunks) {
-                    ring[u] = __ldg(rows[0] + 2 * u);
-#pragma unroll
-                    for (int tt = 1; tt < km1; tt++) {
-                        const uint2 v = __ldg(rows[tt] + 2 * u);
-                        ring[u].x &= v.x; ring[u].y &= v.y;
-                    }
+                for (int tt = 1; tt < km1; tt++) {
+                    const uint4 v = __ldg(rows[tt] + kc);
+                    a.x &= v.x; a.y &= v.y; a.z &= v.z; a.w &= v.w;
                 }
-            }
-            for (int kb = 0; kb < DS.chunks && ok; kb += kPf) {
+                return a;
+            };
+#pragma unroll
+            for (int u = 0; u < kPf; u++)
+                ring[u] = (active && u < mine) ? fetch(kc0 + 2 * u) : make_uint4(0, 0, 0, 0);
+            uint64_t gs = g + (uint64_t)kc0;                   // global stage of own stage m
+            int s = (int)(gs % kStagesA);
+            uint32_t ph = (uint32_t)((gs / kStagesA) & 1);
+            for (int mb = 0; mb < mine && ok; mb += kPf) {
 #pragma unroll
                 for (int u = 0; u < kPf; u++) {
-                    const int kc = kb + u;
-                    if (kc >= DS.chunks) break;
-                    const uint2 cur = ring[u];
-                    if (active && kc + kPf < DS.chunks) {
-                        ring[u] = __ldg(rows[0] + 2 * (kc + kPf));
-#pragma unroll
-                        for (int tt = 1; tt < km1; tt++) {
-                            const uint2 v = __ldg(rows[tt] + 2 * (kc + kPf));
-                            ring[u].x &= v.x; ring[u].y &= v.y;
-                        }
-                    }
-                    const int s = (int)(g % kStagesA);
-                    const uint32_t us = (uint32_t)(g / kStagesA);
-                    if (!wait_fast(&empty_ab[s / kRelease], (us & 1) ^ 1, &abort_flag, w_prod)) { ok = false; break; }
-                    if (active) {
-                        const uint32_t c2 = __popc(cur.x) + __popc(cur.y);
-                        if (kc < DS.chunks_case) t1 += c2;
-                        else t0 += c2;
-                    }
+                    const int m = mb + u;
+                    if (m >= mine) break;
+                    const int kc = kc0 + 2 * m;
+                    const uint4 cur = ring[u];
+                    if (active && m + kPf < mine) ring[u] = fetch(kc + 2 * kPf);
+                    if (!wait_fast(&empty_ab[s / kRelease], ph ^ 1, &abort_flag, w_prod)) { ok = false; break; }
+                    const uint32_t c4 = __popc(cur.x) + __popc(cur.y) + __popc(cur.z) + __popc(cur.w);
+                    if (kc < chunks_case) t1 += c4;
+                    else t0 += c4;
                     unsigned char *arow = stages_a + s * kTileBytes + r * 128;
+                    const uint32_t wv4[4] = {cur.x, cur.y, cur.z, cur.w};
 #pragma unroll
-                    for (int q = 0; q < 2; q++) {
+                    for (int q = 0; q < 4; q++) {
                         // output word i = bit i of every byte of the mask word
-                        const uint32_t wv = q ? cur.y : cur.x;
+                        const uint32_t wv = wv4[q];
                         const uint32_t s4 = wv << 4, r4 = wv >> 4;
                         const uint4 lo = make_uint4(s4 & 0x10101010u, s4 & 0x20202020u, s4 & 0x40404040u, wv & 0x08080808u);
                         const uint4 hi = make_uint4(wv & 0x10101010u, wv & 0x20202020u, wv & 0x40404040u, r4 & 0x08080808u);
-                        const int cc = 4 * half + 2 * q;
-                        *reinterpret_cast<uint4 *>(arow + ((cc ^ (r & 7)) << 4)) = lo;
-                        *reinterpret_cast<uint4 *>(arow + (((cc + 1) ^ (r & 7)) << 4)) = hi;
+                        *reinterpret_cast<uint4 *>(arow + (((2 * q) ^ (r & 7)) << 4)) = lo;
+                        *reinterpret_cast<uint4 *>(arow + (((2 * q + 1) ^ (r & 7)) << 4)) = hi;
                     }
                     fence_proxy_async();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&full_ab[s]);
-                    g++;
+                    // next own stage: two global stages on
+                    s += 2;
+                    if (s >= kStagesA) { s -= kStagesA; ph ^= 1; }
                 }
             }
             if (!ok) break;
+            g += (uint64_t)chunks;
             const int b = (int)(i & 1);
             const uint32_t ub = (uint32_t)(i >> 1);
             if (!wait_fast(&acc_empty[b], (ub & 1) ^ 1, &abort_flag, w_prod_acc)) break;
-            tot[((b * 128 + r) * 2 + half) * 2 + 0] = t1;
-            tot[((b * 128 + r) * 2 + half) * 2 + 1] = t0;
+            tot[((b * 128 + r) * 2 + grp) * 2 + 0] = t1;
+            tot[((b * 128 + r) * 2 + grp) * 2 + 1] = t0;
             __syncwarp();
             if (lane == 0) mbar_arrive(&tot_full[b]);
         }
@@ -635,7 +639,6 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
             P.waits[blockIdx.x * kWaitSlots + 3] = (unsigned long long)w_prod;
             P.waits[blockIdx.x * kWaitSlots + 4] = (unsigned long long)w_prod_acc;
         }
-        (void)pwarp;
     } else {
         // -------------------------------------------------------- epilogue
         const int quad = warp & 3;           // TMEM lane quadrant
