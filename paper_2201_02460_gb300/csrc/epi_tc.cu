@@ -259,10 +259,10 @@ __device__ __forceinline__ int64_t ntiles_of(const DevData &d, int32_t c) { retu
 
 // -------------------------------------------------------------- epilogue --
 // accumulator = count * 2^-5 (exact): the count as a float, and as an integer
-__device__ __forceinline__ float acc2f(uint32_t bits) { return __uint_as_float(bits) * 32.0f; }
 __device__ __forceinline__ uint32_t f2u_exact(float v) { return __float_as_uint(v + 8388608.0f) & 0x7FFFFFu; }
 
-__device__ __forceinline__ float tlog(float c) { return c * __log2f(fmaxf(c, 1.0f)); }
+// t(x) = x log2 x of an accumulator value x = count / 32 (0 for x = 0)
+__device__ __forceinline__ float tlog32(float x) { return x * __log2f(fmaxf(x, 0.03125f)); }
 
 template <int PR>
 __device__ __forceinline__ float seg_sum(float v, int pos)
@@ -347,6 +347,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
     constexpr int km1 = K - 1;
     constexpr int kWarpTma = kEpiWarps + kProdWarps;
     constexpr int kWarpMma = kWarpTma + 1;
+    // candidate-buffer checks (a barrier and maybe a sort) every kJcPerCheck
+    // groups of 8 last SNPs; the buffer holds two intervals' worth
+    constexpr int kJcPerCheck = K == 2 ? 1 : 2;
 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
@@ -649,6 +652,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
         const int pl = l / kPR;
         const bool lane_real = l < kPPW * kPR;
         const MiConstF32 mc = make_mi_const(d.m, d.m1, d.m0);
+        const float vscale = 32.0f * DS.ln2_over_m, voff = DS.tconst * DS.ln2_over_m;
         long long w_epi = 0;
         for (int64_t i = 0; i < n_my; i++) {
             const int dq = (int)(i % kDescDepth);
@@ -669,18 +673,18 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
             for (int tt = 0; tt < km1; tt++) psnp[tt] = prow ? D.snp[p * km1 + tt] : 0;
             const uint32_t T1 = tot[((b * 128 + r) * 2 + 0) * 2 + 0] + tot[((b * 128 + r) * 2 + 1) * 2 + 0];
             const uint32_t T0 = tot[((b * 128 + r) * 2 + 0) * 2 + 1] + tot[((b * 128 + r) * 2 + 1) * 2 + 1];
-            const float fT1 = u2f_exact(T1), fT0 = u2f_exact(T0);
+            // row totals in accumulator units (count / 32, exact)
+            const float fT1 = u2f_exact(T1) * 0.03125f, fT0 = u2f_exact(T0) * 0.03125f;
             const int32_t j0 = D.j0 + 32 * jhalf;
             if (tid == 0) {
                 const float gthr = __uint_as_float(*(volatile uint32_t *)DS.global_thr);
                 if (ES.list_len == P.pool || gthr > 0.0f) ES.thr = fmaxf(ES.thr, gthr);
             }
             epi_bar();
+            float thr = ES.thr, cut = thr - DS.delta;
+            int list_len = ES.list_len;
 #pragma unroll 1
             for (int jc = 0; jc < 4; jc++) {
-                const float thr = ES.thr;
-                const float cut = thr - DS.delta;
-                const int list_len = ES.list_len;
                 uint32_t cs[16], cn[16];
                 if (ok) {
                     const uint32_t ta = tmem_base + ((uint32_t)(quad * 32) << 16) +
@@ -692,22 +696,29 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
 #pragma unroll
                     for (int q = 0; q < 16; q++) { cs[q] = 0; cn[q] = 0; }
                 }
+                if (jc == 3) {
+                    // every accumulator value is in registers: hand the
+                    // buffer back to the MMA issuer before the last scoring
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&acc_empty[b]);
+                }
 #pragma unroll
                 for (int jj = 0; jj < 8; jj++) {
                     const int32_t j = j0 + 8 * jc + jj;
-                    // counts as exact floats (all below 2^23)
-                    const float fa0 = acc2f(cs[2 * jj]), fa1 = acc2f(cs[2 * jj + 1]);
-                    const float fb0 = acc2f(cn[2 * jj]), fb1 = acc2f(cn[2 * jj + 1]);
+                    // accumulator values x = count / 32 (exact); with
+                    // t(x) = x log2 x, T(32 x) = 32 t(x) + 160 x and the
+                    // linear parts cancel within a cell, so the screen sums
+                    // t over the raw values and scales once
+                    const float fa0 = __uint_as_float(cs[2 * jj]), fa1 = __uint_as_float(cs[2 * jj + 1]);
+                    const float fb0 = __uint_as_float(cn[2 * jj]), fb1 = __uint_as_float(cn[2 * jj + 1]);
                     const float fa2 = fT1 - fa0 - fa1, fb2 = fT0 - fb0 - fb1;
-                    float v = 0.0f;
-                    if (prow)
-                        v = (tlog(fa0) + tlog(fb0) - tlog(fa0 + fb0)) + (tlog(fa1) + tlog(fb1) - tlog(fa1 + fb1)) +
-                            (tlog(fa2) + tlog(fb2) - tlog(fa2 + fb2));
-                    v = seg_sum<kPR>(v, pos);
                     const bool valid = prow && j < d.n && j > cpre;
                     if (P.dump && valid) {
-                        const uint32_t a0 = f2u_exact(fa0), a1 = f2u_exact(fa1), a2 = f2u_exact(fa2);
-                        const uint32_t b0 = f2u_exact(fb0), b1 = f2u_exact(fb1), b2 = f2u_exact(fb2);
+                        const uint32_t a0 = f2u_exact(32.0f * fa0), a1 = f2u_exact(32.0f * fa1),
+                                       a2 = f2u_exact(32.0f * fa2);
+                        const uint32_t b0 = f2u_exact(32.0f * fb0), b1 = f2u_exact(32.0f * fb1),
+                                       b2 = f2u_exact(32.0f * fb2);
                         uint64_t rs = 0;
 #pragma unroll
                         for (int tt = 0; tt < km1; tt++) rs += binom_at(d.binom, d.n, d.n - 1 - psnp[tt], K - tt);
@@ -717,7 +728,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                         o[pos * 3 + 0] = a0; o[pos * 3 + 1] = a1; o[pos * 3 + 2] = a2;
                         o[cells + pos * 3 + 0] = b0; o[cells + pos * 3 + 1] = b1; o[cells + pos * 3 + 2] = b2;
                     }
-                    const float approx = (v + DS.tconst) * DS.ln2_over_m;
+                    float v = 0.0f;
+                    if (prow)
+                        v = (tlog32(fa0) + tlog32(fb0) - tlog32(fa0 + fb0)) +
+                            (tlog32(fa1) + tlog32(fb1) - tlog32(fa1 + fb1)) +
+                            (tlog32(fa2) + tlog32(fb2) - tlog32(fa2 + fb2));
+                    v = seg_sum<kPR>(v, pos);
+                    const float approx = fmaf(v, vscale, voff);
                     const bool cand = valid && pos == 0 && approx >= cut;
                     uint32_t seg_mask = __ballot_sync(0xffffffffu, cand);
                     while (seg_mask) {
@@ -725,8 +742,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                         seg_mask &= seg_mask - 1;
                         float e = 0.0f;
                         if (l / kPR == leader / kPR && lane_real)
-                            e = row_terms_precise(f2u_exact(fa0), f2u_exact(fb0), f2u_exact(fa1), f2u_exact(fb1),
-                                                  f2u_exact(fa2), f2u_exact(fb2), mc);
+                            e = row_terms_precise(f2u_exact(32.0f * fa0), f2u_exact(32.0f * fb0),
+                                                  f2u_exact(32.0f * fa1), f2u_exact(32.0f * fb1),
+                                                  f2u_exact(32.0f * fa2), f2u_exact(32.0f * fb2), mc);
                         e = seg_sum<kPR>(e, pos);
                         if (l == leader) {
                             const float score = __fdiv_rn(e, mc.fm);
@@ -743,15 +761,16 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                         }
                     }
                 }
-                epi_bar();
-                if (ES.nbuf > 16 * kPPT) epi_flush(ES, sc, rk, P.pool, DS.global_thr, tid);
+                if (jc % kJcPerCheck == kJcPerCheck - 1) {
+                    epi_bar();
+                    if (ES.nbuf > kJcPerCheck * 16 * kPPT) epi_flush(ES, sc, rk, P.pool, DS.global_thr, tid);
+                    thr = ES.thr;
+                    cut = thr - DS.delta;
+                    list_len = ES.list_len;
+                }
             }
-            tc_fence_before();
             __syncwarp();
-            if (lane == 0) {
-                mbar_arrive(&acc_empty[b]);
-                mbar_arrive(&desc_empty[dq]);
-            }
+            if (lane == 0) mbar_arrive(&desc_empty[dq]);
             epi_bar();
             if (tid == 0) ES.stop = abort_flag;
             epi_bar();
@@ -927,7 +946,10 @@ static void fill_ds(tc::DsParams &D, const DevData &d, int k, uint64_t *item_cum
     // screening margin: relative errors of the log2 approximation (2^-21)
     // and of the float sums over (T(m) + T(m1) + T(m0)), doubled
     const int64_t cells = (int64_t)(k == 2 ? 3 : (k == 3 ? 9 : 27)) * 3;
-    const double mag = T((double)d.m) + T((double)d.m1) + T((double)d.m0);
+    // bound on the summed magnitudes of the screen's terms: with t(x) =
+    // T(32 x) / 32 - 5 x over accumulator values x = count / 32, 32 sum |t|
+    // <= sum T(c) + 5 sum c <= T(m) + T(m1) + T(m0) + 10 m
+    const double mag = T((double)d.m) + T((double)d.m1) + T((double)d.m0) + 10.0 * (double)d.m;
     D.delta = (float)(2.0 * (4.0 * 4.76837158203125e-7 + (double)(2 * cells + 40) * 5.9604644775390625e-8) * mag *
                       0.6931471805599453 / (double)d.m) + 1e-7f;
     D.total = total;
@@ -945,7 +967,7 @@ static void fill_launch(tc::Params &P, int k, int pool, float *list_score, uint6
     P.ppw = 32 / P.PR;
     P.ppt = 4 * P.ppw;
     P.pool = pool;
-    P.cand_p2 = next_pow2(pool + 2 * 16 * P.ppt);
+    P.cand_p2 = next_pow2(pool + 2 * (k == 2 ? 1 : 2) * 16 * P.ppt);   // two check intervals (kJcPerCheck)
     P.list_score = list_score;
     P.list_rank = list_rank;
     P.list_count = list_count;
