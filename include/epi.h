@@ -301,7 +301,9 @@ epi_status epi_mlp_train_step(epi_mlp *net, const float *X_dev, const float *t_d
                               float wd, float *loss_host);
 
 /* Order-5 proposal search.  The exhaustive order-1..3 scores of the dataset
- * are computed (popcount path); the top_triples best triples by order-3 MI
+ * are computed (popcount path) on the first proposer call and kept with the
+ * dataset until it is destroyed (4 (n + C(n,2) + C(n,3)) bytes of device
+ * memory); the top_triples best triples by order-3 MI
  * (ties by rank) are each joined with every pair of other SNPs; every distinct
  * 5-set of that space (a set holding several of the triples is taken once) is
  * ranked by `net` from its 25 features (epi_features5), or, with net NULL, by
@@ -314,13 +316,13 @@ epi_status epi_mlp_train_step(epi_mlp *net, const float *X_dev, const float *t_d
  * approximation whose result is exact only for the sets it proposes. */
 typedef struct epi_proposer_opts {
     int top_triples;   /* 1..4096 */
-    int budget;        /* proposals re-scored exactly, 1..2^30; above 4096 every
-                          ranked score is kept in device memory (5 bytes per
-                          candidate, EPI_ENOMEM if that does not fit), the
-                          budget is met by a threshold on the ranking score
-                          (candidates tied at it are all proposed), every
-                          proposal is scored exactly in FP32 and the 4096 best
-                          of those again in FP64 */
+    int budget;        /* proposals re-scored exactly, 1..2^30: the budget's
+                          best distinct candidates by (ranking score desc,
+                          candidate index asc), selected by radix select over
+                          every ranked score (kept in device memory, 5 bytes
+                          per candidate; EPI_ENOMEM if that does not fit);
+                          every proposal is scored exactly in FP32 and the
+                          4096 best of those again in FP64 */
     int top_n;         /* 1..min(budget, 4096) */
     int64_t chunk;
 } epi_proposer_opts;

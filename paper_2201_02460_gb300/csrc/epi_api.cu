@@ -51,6 +51,7 @@ struct epi_dataset {
     uint32_t *masks = nullptr;
     uint64_t *binom = nullptr;
     unsigned char *b8 = nullptr;   // tensor-core operand, built on first use
+    float *lower[4] = {};          // exhaustive order-1..3 scores for the proposer, built on first use
     DevData dev() const
     {
         DevData d;
@@ -970,17 +971,10 @@ epi_status epi_topk(epi_ctx *ctx, const float *scores, const uint8_t *keep, int6
     if (!ctx || !scores || !out_scores || !out_index || !n_out || count < 0) return fail(EPI_EINVAL, "epi_topk: bad argument");
     if (k < 1 || k > 4096) return fail(EPI_EINVAL, "epi_topk: k outside 1..4096");
     DeviceGuard g(ctx->device);
-    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((count + 65535) / 65536, (int64_t)ctx->num_sms * 2));
-    Arena a;
-    const size_t o_s = a.take<float>((size_t)blocks * k);
-    const size_t o_i = a.take<uint64_t>((size_t)blocks * k);
-    const size_t o_n = a.take<int32_t>((size_t)blocks);
-    epi_status st = ensure_scratch(ctx, a.off);
+    epi_status st = ensure_scratch(ctx, topk_scratch_bytes(k));
     if (st != EPI_OK) return st;
-    char *base = static_cast<char *>(ctx->scratch);
-    CK(launch_topk(scores, keep, count, k, reinterpret_cast<float *>(base + o_s), reinterpret_cast<uint64_t *>(base + o_i),
-                   reinterpret_cast<int32_t *>(base + o_n), blocks, out_scores, out_index, n_out, ctx->stream));
-    ctx->launches += 2;
+    CK(launch_topk(scores, keep, count, k, ctx->scratch, true, out_scores, out_index, n_out, ctx->num_sms, ctx->stream));
+    ctx->launches += 14;
     return EPI_OK;
 }
 
@@ -992,6 +986,26 @@ int epi_ctx_num_sms(const epi_ctx *ctx) { return ctx->num_sms; }
 void epi_ctx_count_launches(epi_ctx *ctx, int n) { ctx->launches += (uint64_t)n; }
 epi_ctx *epi_dataset_ctx(const epi_dataset *ds) { return ds->ctx; }
 epi::DevData epi_dataset_dev(const epi_dataset *ds) { return ds->dev(); }
+
+// The dataset's exhaustive single-precision scores of order k (1..3), computed
+// on first use and kept until the dataset is destroyed.
+epi_status epi_dataset_lower_scores(epi_dataset *ds, int k, const float **out)
+{
+    if (k < 1 || k > 3) return fail(EPI_EINVAL, "lower scores: order %d outside 1..3", k);
+    if (!ds->lower[k]) {
+        DeviceGuard g(ds->ctx->device);
+        float *t = nullptr;
+        CK(cudaMalloc(&t, (size_t)host_binom(ds->n, k) * sizeof(float)));
+        const epi_status st = epi_score_all(ds, k, t);
+        if (st != EPI_OK) {
+            cudaFree(t);
+            return st;
+        }
+        ds->lower[k] = t;
+    }
+    *out = ds->lower[k];
+    return EPI_OK;
+}
 
 extern "C" {
 
@@ -1132,6 +1146,8 @@ void epi_dataset_destroy(epi_dataset *ds)
         cudaFree(ds->masks);
         cudaFree(ds->binom);
         if (ds->b8) cudaFree(ds->b8);
+        for (float *t : ds->lower)
+            if (t) cudaFree(t);
     }
     delete ds;
     ctx->live_datasets--;

@@ -86,8 +86,12 @@ cudaError_t launch_cand_features5(const DevData &d, const uint32_t *triples, int
                                   uint8_t *keep, float *label, uint32_t *combs, cudaStream_t st);
 cudaError_t launch_lookup(const DevData &d, int k, const float *table, const uint32_t *combs, int64_t count,
                           float *out, cudaStream_t st);
-cudaError_t launch_topk(const float *scores, const uint8_t *keep, int64_t count, int k, float *blk_s, uint64_t *blk_i,
-                        int32_t *blk_n, int blocks, float *out_s, uint64_t *out_i, int32_t *out_n, cudaStream_t st);
+// epi_topk.cu: the k best of count scores (score desc, index asc; keep may
+// be NULL), by radix select; sorted (k <= 4096) or as an unordered set;
+// scratch of topk_scratch_bytes(k) device bytes
+size_t topk_scratch_bytes(int64_t k);
+cudaError_t launch_topk(const float *scores, const uint8_t *keep, int64_t count, int64_t k, void *scratch, bool sorted,
+                        float *out_s, uint64_t *out_i, int32_t *out_n, int num_sms, cudaStream_t st);
 
 // epi_select.cu
 // floor: below every score to merge (the search's scores are >= 0)
@@ -118,3 +122,4 @@ int epi_ctx_num_sms(const epi_ctx *ctx);
 void epi_ctx_count_launches(epi_ctx *ctx, int n);
 epi_ctx *epi_dataset_ctx(const epi_dataset *ds);
 epi::DevData epi_dataset_dev(const epi_dataset *ds);
+epi_status epi_dataset_lower_scores(epi_dataset *ds, int k, const float **out);

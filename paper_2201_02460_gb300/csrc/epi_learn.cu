@@ -39,6 +39,10 @@ __device__ __forceinline__ uint64_t lex_rank(const uint64_t *tab, int64_t n, int
     return binom_at(tab, n, n, k) - 1 - s;
 }
 
+// feature value of a score: ln(max(s, 0) + 1e-7) by the hardware log2
+// approximation (about 2^-21 relative; the features only rank candidates)
+__device__ __forceinline__ float feat_log(float s) { return __logf(fmaxf(s, 0.0f) + 1e-7f); }
+
 template <int L>
 __device__ __forceinline__ void sort_desc(float (&v)[L])
 {
@@ -89,11 +93,11 @@ __global__ void features5_kernel(DevData d, const float *__restrict__ s1, const 
         sort_desc(f3);
         float *x = X + i * 25;
 #pragma unroll
-        for (int t = 0; t < 5; t++) x[t] = logf(fmaxf(f1[t], 0.0f) + 1e-7f);
+        for (int t = 0; t < 5; t++) x[t] = feat_log(f1[t]);
 #pragma unroll
-        for (int t = 0; t < 10; t++) x[5 + t] = logf(fmaxf(f2[t], 0.0f) + 1e-7f);
+        for (int t = 0; t < 10; t++) x[5 + t] = feat_log(f2[t]);
 #pragma unroll
-        for (int t = 0; t < 10; t++) x[15 + t] = logf(fmaxf(f3[t], 0.0f) + 1e-7f);
+        for (int t = 0; t < 10; t++) x[15 + t] = feat_log(f3[t]);
     }
 }
 
@@ -189,10 +193,6 @@ __global__ void candidates5_at_kernel(DevData d, const uint32_t *__restrict__ tr
     }
 }
 
-// C(x, 2) and C(x, 3) by arithmetic (x < 2^21, so no overflow)
-__device__ __forceinline__ uint64_t c2(int64_t x) { return x < 2 ? 0ull : (uint64_t)(x * (x - 1) / 2); }
-__device__ __forceinline__ uint64_t c3(int64_t x) { return x < 3 ? 0ull : (uint64_t)(x * (x - 1) * (x - 2) / 6); }
-
 // Candidates [first, first + count) in one pass: the set, whether its
 // generating triple is its best (keep), its 25 features, and optionally its
 // order-5 label ln(s5[rank] + 1e-7) (training); the set itself is written
@@ -205,7 +205,10 @@ __global__ void __launch_bounds__(256) cand_features5_kernel(DevData d, const ui
                                                              uint32_t *__restrict__ combs)
 {
     const int64_t n = d.n;
-    const uint64_t n2 = c2(n), n3 = c3(n);
+    // binomials C(x, 2), C(x, 3) from the dataset's table (L1-resident rows)
+    const uint64_t *__restrict__ b2 = d.binom + 2 * (n + 1);
+    const uint64_t *__restrict__ b3 = d.binom + 3 * (n + 1);
+    const uint64_t n2 = b2[n], n3 = b3[n];
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
         int32_t v[5], g3[3];
         candidate_at(d, triples, (uint64_t)(first + i), v, g3);
@@ -214,7 +217,7 @@ __global__ void __launch_bounds__(256) cand_features5_kernel(DevData d, const ui
             for (int p = 0; p < 5; p++) combs[i * 5 + p] = (uint32_t)v[p];
         }
         // the ten triples: ranks and scores; the generating triple's rank
-        const uint64_t gr = n3 - 1 - (c3(n - 1 - g3[0]) + c2(n - 1 - g3[1]) + (uint64_t)(n - 1 - g3[2]));
+        const uint64_t gr = n3 - 1 - (b3[n - 1 - g3[0]] + b2[n - 1 - g3[1]] + (uint64_t)(n - 1 - g3[2]));
         float f3[10];
         float gs = 0.0f;
         uint64_t r3[10];
@@ -225,7 +228,7 @@ __global__ void __launch_bounds__(256) cand_features5_kernel(DevData d, const ui
             for (int b = a + 1; b < 5; b++)
 #pragma unroll
                 for (int e = b + 1; e < 5; e++) {
-                    r3[q] = n3 - 1 - (c3(n - 1 - v[a]) + c2(n - 1 - v[b]) + (uint64_t)(n - 1 - v[e]));
+                    r3[q] = n3 - 1 - (b3[n - 1 - v[a]] + b2[n - 1 - v[b]] + (uint64_t)(n - 1 - v[e]));
                     f3[q] = s3[r3[q]];
                     if (r3[q] == gr) gs = f3[q];
                     q++;
@@ -240,7 +243,7 @@ __global__ void __launch_bounds__(256) cand_features5_kernel(DevData d, const ui
 #pragma unroll
         for (int a = 0; a < 5; a++)
 #pragma unroll
-            for (int b = a + 1; b < 5; b++) f2[q++] = s2[n2 - 1 - (c2(n - 1 - v[a]) + (uint64_t)(n - 1 - v[b]))];
+            for (int b = a + 1; b < 5; b++) f2[q++] = s2[n2 - 1 - (b2[n - 1 - v[a]] + (uint64_t)(n - 1 - v[b]))];
 #pragma unroll
         for (int t = 0; t < 5; t++) f1[t] = s1[v[t]];
         if (label) {
@@ -252,11 +255,11 @@ __global__ void __launch_bounds__(256) cand_features5_kernel(DevData d, const ui
         sort_desc(f3);
         float *x = X + i * 25;
 #pragma unroll
-        for (int t = 0; t < 5; t++) x[t] = logf(fmaxf(f1[t], 0.0f) + 1e-7f);
+        for (int t = 0; t < 5; t++) x[t] = feat_log(f1[t]);
 #pragma unroll
-        for (int t = 0; t < 10; t++) x[5 + t] = logf(fmaxf(f2[t], 0.0f) + 1e-7f);
+        for (int t = 0; t < 10; t++) x[5 + t] = feat_log(f2[t]);
 #pragma unroll
-        for (int t = 0; t < 10; t++) x[15 + t] = logf(fmaxf(f3[t], 0.0f) + 1e-7f);
+        for (int t = 0; t < 10; t++) x[15 + t] = feat_log(f3[t]);
     }
 }
 
@@ -411,62 +414,6 @@ __global__ void heuristic5_kernel(const float *__restrict__ X, int64_t count, fl
         for (int t = 15; t < 25; t++) s += X[i * 25 + t];
         out[i] = s;
     }
-}
-
-// ---------------------------------------------------------------- top-k
-struct TopState {
-    int32_t list_len, nbuf;
-    float thr;
-};
-
-// Each block keeps the best `k` of its slice of (score, index) by
-// (score desc, index asc) and writes them to out[block][k].
-__global__ void __launch_bounds__(512) topk_blocks_kernel(const float *__restrict__ scores,
-                                                          const uint8_t *__restrict__ keep, int64_t count, int k,
-                                                          int cand_p2, float *__restrict__ out_s,
-                                                          uint64_t *__restrict__ out_i, int32_t *__restrict__ out_n)
-{
-    extern __shared__ __align__(16) unsigned char sm[];
-    uint64_t *rk = reinterpret_cast<uint64_t *>(sm);
-    float *sc = reinterpret_cast<float *>(rk + cand_p2);
-    __shared__ TopState S;
-    if (threadIdx.x == 0) { S.list_len = 0; S.nbuf = 0; S.thr = -INFINITY; }
-    __syncthreads();
-    const int64_t per = (count + gridDim.x - 1) / gridDim.x;
-    const int64_t b = (int64_t)blockIdx.x * per, e = min(count, b + per);
-    for (int64_t base = b; base < e; base += blockDim.x) {
-        const int64_t i = base + threadIdx.x;
-        const int list_len = S.list_len;
-        if (i < e) {
-            const float v = scores[i];
-            if (v >= S.thr && (!keep || keep[i])) {
-                const int pos = list_len + atomicAdd(&S.nbuf, 1);
-                sc[pos] = v;
-                rk[pos] = (uint64_t)i;
-            }
-        }
-        __syncthreads();
-        const bool last = base + blockDim.x >= e;
-        if (S.nbuf > (int)blockDim.x || (last && S.nbuf > 0)) {
-            const int live = S.list_len + S.nbuf;
-            const int p2 = next_pow2(live < 2 ? 2 : live);
-            for (int q = live + threadIdx.x; q < p2; q += blockDim.x) { sc[q] = -INFINITY; rk[q] = ~0ull; }
-            __syncthreads();
-            block_sort_cands(sc, rk, p2);
-            if (threadIdx.x == 0) {
-                S.list_len = live < k ? live : k;
-                S.nbuf = 0;
-                if (S.list_len == k) S.thr = sc[k - 1];
-            }
-        }
-        __syncthreads();
-    }
-    const int L = S.list_len;
-    for (int q = threadIdx.x; q < L; q += blockDim.x) {
-        out_s[(int64_t)blockIdx.x * k + q] = sc[q];
-        out_i[(int64_t)blockIdx.x * k + q] = rk[q];
-    }
-    if (threadIdx.x == 0) out_n[blockIdx.x] = L;
 }
 
 }  // namespace learn
@@ -848,17 +795,5 @@ cudaError_t launch_lookup(const DevData &d, int k, const float *table, const uin
     return cudaGetLastError();
 }
 
-cudaError_t launch_topk(const float *scores, const uint8_t *keep, int64_t count, int k, float *blk_s, uint64_t *blk_i,
-                        int32_t *blk_n, int blocks, float *out_s, uint64_t *out_i, int32_t *out_n, cudaStream_t st)
-{
-    const int cand_p2 = next_pow2(k + 2 * 512);
-    const size_t smem = (size_t)cand_p2 * 12;
-    cudaError_t e = cudaFuncSetAttribute(learn::topk_blocks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    learn::topk_blocks_kernel<<<blocks, 512, smem, st>>>(scores, keep, count, k, cand_p2, blk_s, blk_i, blk_n);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    return launch_merge(blk_s, blk_i, blk_n, blocks, k, k, out_s, out_i, out_n, st, -INFINITY);
-}
 
 }  // namespace epi

@@ -31,11 +31,6 @@ void set_last_error(const char *msg);
 
 namespace prop {
 
-__global__ void add_offset_kernel(uint64_t *idx, const int32_t *n, uint64_t first)
-{
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < *n; i += gridDim.x * blockDim.x) idx[i] += first;
-}
-
 __global__ void count_kernel(const uint8_t *__restrict__ keep, int64_t count, unsigned long long *out)
 {
     unsigned long long c = 0;
@@ -105,46 +100,6 @@ __global__ void gather_batch_kernel(const float *__restrict__ X, const float *__
 
 int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8192)); }
 
-// order-preserving unsigned key of a float (NaN below every number)
-__device__ __forceinline__ uint32_t fkey(float v)
-{
-    if (v != v) return 0u;
-    const uint32_t b = __float_as_uint(v);
-    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
-}
-
-// histogram of key bits [shift, shift + log2 bins) over kept entries whose
-// key agrees with `prefix` above bit `pshift` (pshift = 32: no condition)
-__global__ void __launch_bounds__(256) key_hist_kernel(const float *__restrict__ v, const uint8_t *__restrict__ keep,
-                                                       uint64_t count, int shift, int bins, int pshift,
-                                                       uint32_t prefix, unsigned long long *__restrict__ hist)
-{
-    __shared__ uint32_t h[4096];
-    for (int i = threadIdx.x; i < bins; i += blockDim.x) h[i] = 0;
-    __syncthreads();
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (uint64_t)gridDim.x * blockDim.x) {
-        if (!keep[i]) continue;
-        const uint32_t k = fkey(v[i]);
-        if (pshift < 32 && (k >> pshift) != prefix) continue;
-        atomicAdd(&h[(k >> shift) & (uint32_t)(bins - 1)], 1u);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < bins; i += blockDim.x)
-        if (h[i]) atomicAdd(&hist[i], (unsigned long long)h[i]);
-}
-
-// indices of kept entries with key >= thr (appended in any order)
-__global__ void select_kernel(const float *__restrict__ v, const uint8_t *__restrict__ keep, uint64_t count, uint32_t thr,
-                              uint64_t *__restrict__ out, unsigned long long *__restrict__ n_out, uint64_t cap)
-{
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (uint64_t)gridDim.x * blockDim.x) {
-        if (keep[i] && fkey(v[i]) >= thr) {
-            const unsigned long long at = atomicAdd(n_out, 1ull);
-            if (at < cap) out[at] = i;
-        }
-    }
-}
-
 __global__ void gather_u64_kernel(const uint64_t *__restrict__ src, const uint64_t *__restrict__ pos,
                                   const int32_t *__restrict__ n, uint64_t *__restrict__ dst)
 {
@@ -202,18 +157,21 @@ double now_ms()
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
-// Exhaustive single-precision scores of orders 1, 2, 3 (and 5 when wanted).
+// Exhaustive single-precision scores of orders 1, 2, 3 (kept with the
+// dataset) and, when wanted, 5 (owned by the pool).
 struct Lower {
-    float *s[6] = {};
+    const float *s[6] = {};
 };
 
 epi_status lower_tables(epi_dataset *ds, Pool &pool, Lower &L, bool with5)
 {
     const DevData d = epi_dataset_dev(ds);
-    for (int k : {1, 2, 3, 5}) {
-        if (k == 5 && !with5) continue;
-        PCK(pool.get(&L.s[k], host_binom(d.n, k)));
-        PST(epi_score_all(ds, k, L.s[k]));
+    for (int k : {1, 2, 3}) PST(epi_dataset_lower_scores(ds, k, &L.s[k]));
+    if (with5) {
+        float *s5;
+        PCK(pool.get(&s5, host_binom(d.n, 5)));
+        PST(epi_score_all(ds, 5, s5));
+        L.s[5] = s5;
     }
     return EPI_OK;
 }
@@ -239,32 +197,34 @@ epi_status best_triples(epi_dataset *ds, Pool &pool, const float *s3, int T, uin
     return EPI_OK;
 }
 
-// Budgets above 4096: every ranked score stays in device memory (5 bytes per
-// candidate); the budget's threshold is found by a three-pass radix select on
-// the scores' order-preserving keys (12 + 12 + 8 bits), every kept candidate at
-// or above it is proposed (ties at the threshold included), every proposal is
-// counted and scored exactly in FP32 in slices, and the 4096 best by exact
-// FP32 score form the pool that the caller re-scores in FP64.
-epi_status large_budget(epi_dataset *ds, epi_mlp *net, const DevData &d, const Lower &L, const uint32_t *triples,
-                        uint64_t total, uint64_t R, int64_t chunk, Pool &pool, uint64_t **pool_idx, int32_t *n_pool,
-                        unsigned long long *kept_out, uint64_t *selected_out, float *pool_floor, int &launches)
+// Ranking and proposal selection: every ranked score stays in device memory
+// (5 bytes per candidate), the budget's R best distinct candidates (ranking
+// score desc, candidate index asc) are selected by radix select, every
+// proposal is counted and scored exactly in FP32 in slices, and the 4096 best
+// by exact FP32 score form the pool that the caller re-scores in FP64.
+epi_status rank_and_select(epi_dataset *ds, epi_mlp *net, const DevData &d, const Lower &L, const uint32_t *triples,
+                           uint64_t total, uint64_t R, int64_t chunk, Pool &pool, uint64_t **pool_idx, int32_t *n_pool,
+                           unsigned long long *kept_out, uint64_t *selected_out, float *pool_floor, int &launches)
 {
     epi_ctx *ctx = epi_dataset_ctx(ds);
     cudaStream_t st = epi_ctx_stream(ctx);
     size_t free_b = 0, total_b = 0;
     PCK(cudaMemGetInfo(&free_b, &total_b));
-    const size_t need = (size_t)total * 5 + (size_t)chunk * 100 + ((size_t)1 << 30);
+    const size_t need = (size_t)total * 5 + (size_t)chunk * 100 + (size_t)R * 12 + ((size_t)1 << 30);
     if (need > free_b) return pfail(EPI_ENOMEM, "epi_proposer_search: the candidate space's scores do not fit in device memory");
-    float *score;
+    float *score, *X;
     uint8_t *keep;
-    float *X;
-    unsigned long long *kept_dev, *hist, *nsel;
+    unsigned long long *kept_dev;
+    int32_t *nsel;
+    uint64_t *sel;
+    void *scratch;
     PCK(pool.get(&score, total));
     PCK(pool.get(&keep, total));
     PCK(pool.get(&X, (size_t)chunk * 25));
     PCK(pool.get(&kept_dev, 1));
-    PCK(pool.get(&hist, 4096));
     PCK(pool.get(&nsel, 1));
+    PCK(pool.get(&sel, R));
+    PCK(pool.get(reinterpret_cast<unsigned char **>(&scratch), topk_scratch_bytes(4096)));
     PCK(cudaMemsetAsync(kept_dev, 0, 8, st));
     for (uint64_t first = 0; first < total; first += (uint64_t)chunk) {
         const int64_t cnt = (int64_t)std::min<uint64_t>((uint64_t)chunk, total - first);
@@ -275,42 +235,19 @@ epi_status large_budget(epi_dataset *ds, epi_mlp *net, const DevData &d, const L
         count_kernel<<<grid_for(cnt), 256, 0, st>>>(keep + first, cnt, kept_dev);
         launches += 3;
     }
+    // the proposals: the R best kept candidates (an unordered set)
+    PCK(launch_topk(score, keep, (int64_t)total, (int64_t)R, scratch, false, nullptr, sel, nsel, epi_ctx_num_sms(ctx),
+                    st));
+    launches += 12;
+    int32_t n_sel = 0;
     PCK(cudaMemcpyAsync(kept_out, kept_dev, 8, cudaMemcpyDeviceToHost, st));
-    // radix select of the R-th best key among the kept candidates
-    const int hgrid = 4 * epi_ctx_num_sms(ctx);
-    uint32_t prefix = 0;
-    uint64_t above = 0;           // kept keys above the current prefix's range
-    uint64_t at_thr = 0;          // kept keys equal to the final threshold
-    const int shifts[3] = {20, 8, 0}, widths[3] = {12, 12, 8};
-    std::vector<unsigned long long> h(4096);
-    for (int pass = 0; pass < 3; pass++) {
-        const int bins = 1 << widths[pass];
-        const int pshift = pass == 0 ? 32 : shifts[pass - 1];
-        PCK(cudaMemsetAsync(hist, 0, (size_t)bins * 8, st));
-        key_hist_kernel<<<hgrid, 256, 0, st>>>(score, keep, total, shifts[pass], bins, pshift, prefix, hist);
-        launches += 1;
-        PCK(cudaMemcpyAsync(h.data(), hist, (size_t)bins * 8, cudaMemcpyDeviceToHost, st));
-        PCK(cudaStreamSynchronize(st));
-        int b = bins - 1;
-        while (b > 0 && above + h[b] < R) above += h[b--];
-        prefix = (prefix << widths[pass]) | (uint32_t)b;
-        at_thr = h[b];
-    }
-    const uint32_t thr = prefix;
-    const uint64_t cap = above + at_thr;
-    uint64_t *sel;
-    PCK(pool.get(&sel, std::max<uint64_t>(cap, 1)));
-    PCK(cudaMemsetAsync(nsel, 0, 8, st));
-    select_kernel<<<hgrid, 256, 0, st>>>(score, keep, total, thr, sel, nsel, cap);
-    launches += 1;
-    unsigned long long n_sel = 0;
-    PCK(cudaMemcpyAsync(&n_sel, nsel, 8, cudaMemcpyDeviceToHost, st));
+    PCK(cudaMemcpyAsync(&n_sel, nsel, 4, cudaMemcpyDeviceToHost, st));
     PCK(cudaStreamSynchronize(st));
-    n_sel = std::min<unsigned long long>(n_sel, cap);
-    *selected_out = n_sel;
+    *selected_out = (uint64_t)n_sel;
     pool.release(score);
     pool.release(X);
-    if (n_sel == 0) {
+    pool.release(keep);
+    if (n_sel <= 0) {
         *n_pool = 0;
         return EPI_OK;
     }
@@ -319,8 +256,8 @@ epi_status large_budget(epi_dataset *ds, epi_mlp *net, const DevData &d, const L
     float *exact;
     uint32_t *pc, *tabs;
     PCK(pool.get(&exact, n_sel));
-    PCK(pool.get(&pc, (size_t)std::min<int64_t>((int64_t)n_sel, kSlice) * 5));
-    PCK(pool.get(&tabs, (size_t)std::min<int64_t>((int64_t)n_sel, kSlice) * 2 * 243));
+    PCK(pool.get(&pc, (size_t)std::min<int64_t>(n_sel, kSlice) * 5));
+    PCK(pool.get(&tabs, (size_t)std::min<int64_t>(n_sel, kSlice) * 2 * 243));
     for (int64_t off = 0; off < (int64_t)n_sel; off += kSlice) {
         const int64_t c = std::min<int64_t>(kSlice, (int64_t)n_sel - off);
         PCK(launch_candidates5_at(d, triples, sel + off, c, pc, st));
@@ -329,21 +266,17 @@ epi_status large_budget(epi_dataset *ds, epi_mlp *net, const DevData &d, const L
         launches += 3;
     }
     // the pool: the 4096 best proposals by exact FP32 score
-    const int kp = (int)std::min<unsigned long long>(4096ull, n_sel);
-    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)n_sel + 65535) / 65536, 2 * epi_ctx_num_sms(ctx)));
-    float *bs, *vs;
-    uint64_t *bi, *pos;
-    int32_t *bn, *nn;
-    PCK(pool.get(&bs, (size_t)blocks * kp));
-    PCK(pool.get(&bi, (size_t)blocks * kp));
-    PCK(pool.get(&bn, blocks));
+    const int kp = std::min(4096, n_sel);
+    float *vs;
+    uint64_t *pos;
+    int32_t *nn;
     PCK(pool.get(&vs, kp));
     PCK(pool.get(&pos, kp));
     PCK(pool.get(&nn, 1));
-    PCK(launch_topk(exact, nullptr, (int64_t)n_sel, kp, bs, bi, bn, blocks, vs, pos, nn, st));
+    PCK(launch_topk(exact, nullptr, (int64_t)n_sel, kp, scratch, true, vs, pos, nn, epi_ctx_num_sms(ctx), st));
     PCK(pool.get(pool_idx, kp));
     gather_u64_kernel<<<(kp + 255) / 256, 256, 0, st>>>(sel, pos, nn, *pool_idx);
-    launches += 3;
+    launches += 15;
     PCK(cudaMemcpyAsync(n_pool, nn, 4, cudaMemcpyDeviceToHost, st));
     PCK(cudaMemcpyAsync(pool_floor, vs + kp - 1, 4, cudaMemcpyDeviceToHost, st));
     PCK(cudaStreamSynchronize(st));
@@ -396,54 +329,9 @@ epi_status epi_proposer_search(epi_dataset *ds, epi_mlp *net, const epi_proposer
     unsigned long long kept = 0;
     uint64_t *lr = nullptr;
     uint64_t selected = 0;
-    float pool_floor = -INFINITY;     // exact FP32 score of the weakest pooled proposal (large budgets)
-    if (R > 4096) {
-        PST(large_budget(ds, net, d, L, triples, total, (uint64_t)R, chunk, pool, &lr, &n_prop, &kept, &selected,
-                         &pool_floor, launches));
-    } else {
-    uint8_t *keep;
-    float *X, *y;
-    PCK(pool.get(&keep, chunk));
-    PCK(pool.get(&X, (size_t)chunk * 25));
-    PCK(pool.get(&y, chunk));
-    // running best: list 0 = best so far, list 1 = this chunk's best
-    const int topk_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((chunk + 65535) / 65536, 2 * epi_ctx_num_sms(ctx)));
-    float *ls, *bs, *ms;
-    uint64_t *bi, *mr;
-    int32_t *lc, *bn, *mn;
-    unsigned long long *kept_dev;
-    PCK(pool.get(&ls, (size_t)2 * R));
-    PCK(pool.get(&lr, (size_t)2 * R));
-    PCK(pool.get(&lc, 2));
-    PCK(pool.get(&bs, (size_t)topk_blocks * R));
-    PCK(pool.get(&bi, (size_t)topk_blocks * R));
-    PCK(pool.get(&bn, topk_blocks));
-    PCK(pool.get(&ms, R));
-    PCK(pool.get(&mr, R));
-    PCK(pool.get(&mn, 1));
-    PCK(pool.get(&kept_dev, 1));
-    PCK(cudaMemsetAsync(lc, 0, 8, st));
-    PCK(cudaMemsetAsync(kept_dev, 0, 8, st));
-    for (uint64_t first = 0; first < total; first += (uint64_t)chunk) {
-        const int64_t cnt = (int64_t)std::min<uint64_t>((uint64_t)chunk, total - first);
-        PCK(launch_cand_features5(d, triples, (int64_t)first, cnt, L.s[1], L.s[2], L.s[3], nullptr, X, keep, nullptr,
-                                  nullptr, st));
-        if (net) PST(epi_mlp_forward(net, X, cnt, y));
-        else PST(epi_heuristic5(ctx, X, cnt, y));
-        count_kernel<<<grid_for(cnt), 256, 0, st>>>(keep, cnt, kept_dev);
-        PCK(launch_topk(y, keep, cnt, R, bs, bi, bn, topk_blocks, ls + R, lr + R, lc + 1, st));
-        add_offset_kernel<<<(R + 255) / 256, 256, 0, st>>>(lr + R, lc + 1, first);
-        PCK(launch_merge(ls, lr, lc, 2, R, R, ms, mr, mn, st, -INFINITY));
-        PCK(cudaMemcpyAsync(ls, ms, (size_t)R * 4, cudaMemcpyDeviceToDevice, st));
-        PCK(cudaMemcpyAsync(lr, mr, (size_t)R * 8, cudaMemcpyDeviceToDevice, st));
-        PCK(cudaMemcpyAsync(lc, mn, 4, cudaMemcpyDeviceToDevice, st));
-        launches += 7;
-    }
-    PCK(cudaMemcpyAsync(&n_prop, lc, 4, cudaMemcpyDeviceToHost, st));
-    PCK(cudaMemcpyAsync(&kept, kept_dev, 8, cudaMemcpyDeviceToHost, st));
-    PCK(cudaStreamSynchronize(st));
-    selected = (uint64_t)n_prop;
-    }
+    float pool_floor = -INFINITY;     // exact FP32 score of the weakest pooled proposal
+    PST(rank_and_select(ds, net, d, L, triples, total, (uint64_t)R, chunk, pool, &lr, &n_prop, &kept, &selected,
+                        &pool_floor, launches));
     const double t2 = now_ms();
 
     // exact re-score of the proposals
@@ -581,17 +469,13 @@ epi_status epi_proposer_train(epi_mlp *net, epi_dataset *const *datasets, int n_
         }
         // this dataset's best-labelled kept rows
         const int kt = (int)std::min<int64_t>(kTail, cnt);
-        float *vs, *bs;
-        uint64_t *bi;
-        int32_t *bn, *nn;
-        const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((cnt + 65535) / 65536, 2 * epi_ctx_num_sms(ctx)));
-        PCK(lp.get(&vs, kt));
-        PCK(lp.get(&bs, (size_t)blocks * kt));
-        PCK(lp.get(&bi, (size_t)blocks * kt));
-        PCK(lp.get(&bn, blocks));
+        int32_t *nn;
+        unsigned char *scratch;
         PCK(lp.get(&nn, 1));
-        PCK(launch_topk(t + base[i], keep + base[i], cnt, kt, bs, bi, bn, blocks, vs, tail + (size_t)i * kTail, nn, st));
-        launches += 2;
+        PCK(lp.get(&scratch, topk_scratch_bytes(kt)));
+        PCK(launch_topk(t + base[i], keep + base[i], cnt, kt, scratch, false, nullptr, tail + (size_t)i * kTail, nn,
+                        epi_ctx_num_sms(ctx), st));
+        launches += 12;
         int32_t got = 0;
         std::vector<uint64_t> ti(kt);
         PCK(cudaMemcpyAsync(&got, nn, 4, cudaMemcpyDeviceToHost, st));

@@ -106,7 +106,9 @@ def test_features5_match_oracle_scores(epi, small):
     X = epi.features5(ds, *tabs, torch.from_numpy(combs).cuda()).cpu().numpy().astype(np.float64)
     want = np.stack([_features_cpu(mi, n, c) for c in combs])
     assert X.shape == (300, 25)
-    np.testing.assert_allclose(X, want, rtol=0, atol=5e-6)
+    # the kernels take logs with the hardware approximation (|error| about
+    # 2^-21 relative to the log's magnitude, < 2e-5 here)
+    np.testing.assert_allclose(X, want, rtol=0, atol=2e-5)
     # each group is sorted descending
     for lo, hi in ((0, 5), (5, 15), (15, 25)):
         assert (np.diff(X[:, lo:hi], axis=1) <= 0).all()

@@ -191,18 +191,11 @@ def test_large_budget_proposals_follow_the_ranking(epi, ctx, use_net):
     net = epi.MLP(ctx, 25, 64, seed=5) if use_net else None
     scorer = (lambda X: net.forward(X)) if use_net else (lambda X: epi.heuristic5(ctx, X))
     r, st = epi.proposer_search(ds, net, T, R, top_n, chunk=10007)
-    # the same ranking from the single-step calls: every kept candidate whose
-    # score reaches the budget's threshold (ties at it included)
-    S = [epi.score_all(ds, k) for k in (1, 2, 3)]
-    _, ti = epi.topk(ctx, S[2], T)
-    tri = epi.unrank(ds, 3, ti)
-    combs, keep = epi.candidates5(ds, tri, 0, T * math.comb(n - 3, 2), s3=S[2])
-    y = scorer(epi.features5(ds, *S, combs)).cpu().numpy()
-    k = keep.cpu().numpy().astype(bool)
-    ys = np.sort(y[k])[::-1]
-    thr = ys[R - 1]
-    sel = combs.cpu().numpy()[k & (y >= thr)]
-    assert st["proposals"] == len(sel) >= R
+    # the same ranking from the single-step calls: the R best kept
+    # candidates by (score desc, candidate index asc)
+    want, kept = _direct_proposals(epi, ctx, ds, n, T, R, scorer)
+    sel = want
+    assert st["proposals"] == R == len(sel) and st["kept"] == kept
     t = O.tables(geno, pheno, sel.astype(np.int32))
     mi = np.array([O.mi(x[0], x[1], 900) for x in t])
     ranks = np.array([O.rank(n, 5, c) for c in sel])
