@@ -10,7 +10,8 @@
 //   H1   [128 rows][256]    BF16, 4 K blocks (also holds x' and
 //        the row partials of the last layer)                     64 KiB
 // all in the 128-byte swizzle (8-row atoms of 1024 bytes).  Per step:
-//   1. the 256 threads stage x' (BF16) into H1's first K block;
+//   1. the 256 threads copy the tile's input rows (coalesced) into H1's
+//      second K block and stage x' (BF16) into its first;
 //   2. one thread issues layer 1 (M128 N256 K64: 4 MMAs of K16) into tensor
 //      memory columns [0, 256) and commits to an mbarrier;
 //   3. warp w reads lane quadrant w % 4, columns half w / 4, adds b1, ReLU,
@@ -143,11 +144,26 @@ __global__ void __launch_bounds__(kThreads, 1)
     bool issued = false;
 
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        // ---- 1. stage x' (two threads per row, four 16-byte chunks each) --
+        // ---- 1. stage x': the tile's rows (contiguous floats) are copied with
+        // coalesced 16-byte loads into H1's second K block, then each thread
+        // normalises two 16-byte chunks of its row into the first (BF16)
         {
+            const int64_t r0 = tile * kRows;
+            const int64_t nrows = rows - r0 < kRows ? rows - r0 : kRows;
+            const int64_t nfl = nrows * n_in;                 // floats of the tile
+            float *xs = reinterpret_cast<float *>(h1s + kKBlockH);
+            const float *src = X + r0 * n_in;
+            if ((((uintptr_t)src) & 15) == 0) {
+                const int64_t n4 = nfl >> 2;
+                for (int64_t q = tid; q < n4; q += kThreads)
+                    reinterpret_cast<float4 *>(xs)[q] = __ldg(reinterpret_cast<const float4 *>(src) + q);
+                for (int64_t q = (n4 << 2) + tid; q < nfl; q += kThreads) xs[q] = __ldg(src + q);
+            } else {
+                for (int64_t q = tid; q < nfl; q += kThreads) xs[q] = __ldg(src + q);
+            }
+            __syncthreads();
             const int sr = tid >> 1, sh = tid & 1;
-            const int64_t row = tile * kRows + sr;
-            const bool valid = row < rows;
+            const bool valid = sr < nrows;
 #pragma unroll
             for (int cc = 0; cc < 4; cc++) {
                 const int c = 4 * sh + cc;
@@ -155,8 +171,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                 for (int q = 0; q < 4; q++) {
                     const int e0 = 8 * c + 2 * q, e1 = e0 + 1;
-                    const float a = (valid && e0 < n_in) ? (X[row * n_in + e0] - norm[e0]) * norm[n_in + e0] : 0.0f;
-                    const float b = (valid && e1 < n_in) ? (X[row * n_in + e1] - norm[e1]) * norm[n_in + e1] : 0.0f;
+                    const float a = (valid && e0 < n_in) ? (xs[sr * n_in + e0] - norm[e0]) * norm[n_in + e0] : 0.0f;
+                    const float b = (valid && e1 < n_in) ? (xs[sr * n_in + e1] - norm[e1]) * norm[n_in + e1] : 0.0f;
                     w[q] = pack_bf16(a, b);
                 }
                 *reinterpret_cast<uint4 *>(h1s + sw(sr, c)) = make_uint4(w[0], w[1], w[2], w[3]);
@@ -188,12 +204,15 @@ __global__ void __launch_bounds__(kThreads, 1)
             tmem_wait_ld();
 #pragma unroll
             for (int c = 0; c < 4; c++) {
+                const float4 ba = __ldg(reinterpret_cast<const float4 *>(b1 + col0 + 8 * c));
+                const float4 bb = __ldg(reinterpret_cast<const float4 *>(b1 + col0 + 8 * c + 4));
+                const float bias[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
                 uint32_t w[4];
 #pragma unroll
                 for (int p = 0; p < 4; p++) {
                     const int i = 8 * c + 2 * p;
-                    const float a = fmaxf(__uint_as_float(v[i]) + __ldg(b1 + col0 + i), 0.0f);
-                    const float b = fmaxf(__uint_as_float(v[i + 1]) + __ldg(b1 + col0 + i + 1), 0.0f);
+                    const float a = fmaxf(__uint_as_float(v[i]) + bias[2 * p], 0.0f);
+                    const float b = fmaxf(__uint_as_float(v[i + 1]) + bias[2 * p + 1], 0.0f);
                     w[p] = pack_bf16(a, b);
                 }
                 const int col = col0 + 8 * c;
@@ -231,9 +250,21 @@ __global__ void __launch_bounds__(kThreads, 1)
             TMEM_LD32(lane_addr + (uint32_t)(kHidden + col0), v);
             tmem_wait_ld();
 #pragma unroll
-            for (int i = 0; i < 32; i++) {
-                const float h2 = bf16_round(fmaxf(__uint_as_float(v[i]) + __ldg(b2 + col0 + i), 0.0f));
-                acc = fmaf(h2, __bfloat162float(W3[col0 + i]), acc);
+            for (int c = 0; c < 4; c++) {
+                const float4 ba = __ldg(reinterpret_cast<const float4 *>(b2 + col0 + 8 * c));
+                const float4 bb = __ldg(reinterpret_cast<const float4 *>(b2 + col0 + 8 * c + 4));
+                const float bias[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
+                const uint4 w3 = __ldg(reinterpret_cast<const uint4 *>(W3 + col0 + 8 * c));
+                const __nv_bfloat162 *wp = reinterpret_cast<const __nv_bfloat162 *>(&w3);
+#pragma unroll
+                for (int p = 0; p < 4; p++) {
+                    const float2 wf = __bfloat1622float2(wp[p]);
+                    const int i = 8 * c + 2 * p;
+                    const float h0 = bf16_round(fmaxf(__uint_as_float(v[i]) + bias[2 * p], 0.0f));
+                    const float h1 = bf16_round(fmaxf(__uint_as_float(v[i + 1]) + bias[2 * p + 1], 0.0f));
+                    acc = fmaf(h0, wf.x, acc);
+                    acc = fmaf(h1, wf.y, acc);
+                }
             }
         }
         part[half * kRows + r] = acc;
