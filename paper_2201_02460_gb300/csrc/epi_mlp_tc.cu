@@ -7,21 +7,25 @@
 // SM keeps both weight matrices in shared memory for the whole launch:
 //   W2   [256 out][256 in]  BF16, K-major, 4 K blocks of 64     128 KiB
 //   W1   [256 out][64 in]   BF16, inputs zero-padded to 64       32 KiB
-//   H1   [128 rows][256]    BF16, 4 K blocks (also holds x' and
-//        the row partials of the last layer)                     64 KiB
-// all in the 128-byte swizzle (8-row atoms of 1024 bytes).  Per step:
-//   1. the 256 threads copy the tile's input rows (coalesced) into H1's
-//      second K block and stage x' (BF16) into its first;
-//   2. one thread issues layer 1 (M128 N256 K64: 4 MMAs of K16) into tensor
-//      memory columns [0, 256) and commits to an mbarrier;
-//   3. warp w reads lane quadrant w % 4, columns half w / 4, adds b1, ReLU,
-//      rounds to BF16 and writes H1;
-//   4. one thread issues layer 2 (M128 N256 K256: 16 MMAs) into columns
-//      [256, 512);
-//   5. the same warps add b2, ReLU, round to BF16 and dot with W3; the two
-//      column halves of a row meet in shared memory and b3 is added.
-// Every mbarrier wait is bounded (about 2 s); a wait that gives up sets the
-// status word and the CTA drains its MMAs and frees tensor memory.
+//   H1   [128 rows][256]    BF16, 4 K blocks (also the staging
+//        area of the input rows and of x')                      64 KiB
+// all in the 128-byte swizzle (8-row atoms of 1024 bytes).  Tensor memory:
+// layer 1 in columns [0, 256), layer 2 in [256, 512).  Warp roles, pipelined
+// across the CTA's 128-row tiles:
+//   group A (warps 0-7): copy the tile's input rows (coalesced) into H1's
+//      second K block, stage x' (BF16) into its first; after layer 1, read
+//      lane quadrant w % 4, column half w / 4, add b1, ReLU, round to BF16
+//      and write H1;
+//   warp 16, one lane: layer 1 (M128 N256 K64: 4 MMAs of K16) once x' is
+//      staged, layer 2 (M128 N256 K256: 16 MMAs) once H1 is written and the
+//      previous tile's layer-2 columns are read;
+//   group B (warps 8-15): after layer 2, add b2, ReLU, round to BF16, dot
+//      with W3; the two column halves of a row meet in shared memory and b3
+//      is added.
+// Group B's output of tile t overlaps group A's staging and layer-1 epilogue
+// of tile t + 1.  Every mbarrier wait is bounded (about 2 s); a wait that
+// gives up sets the status word, every role leaves its loop, the MMAs are
+// drained and tensor memory is freed.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -35,7 +39,10 @@ namespace mlptc {
 constexpr int kRows = 128;
 constexpr int kHidden = 256;
 constexpr int kKin = 64;                       // padded inputs
-constexpr int kThreads = 256;
+constexpr int kGroupWarps = 8;                 // per epilogue group
+constexpr int kGroupThreads = 32 * kGroupWarps;
+constexpr int kWarpMma = 2 * kGroupWarps;      // warp 16
+constexpr int kThreads = 32 * (2 * kGroupWarps + 1);
 constexpr uint32_t kW2Bytes = 4 * kHidden * 128;
 constexpr uint32_t kW1Bytes = kHidden * 128;
 constexpr uint32_t kH1Bytes = 4 * kRows * 128;
@@ -80,6 +87,36 @@ __device__ __forceinline__ void wait_phase(uint64_t *bar, uint32_t parity, volat
     }
 }
 
+
+__device__ __forceinline__ void named_bar(int id, int count)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// Every thread of a named-barrier group waits, then the group meets in a
+// barrier that ORs the threads' abort flags, so that all of its threads leave
+// their loop at the same point when any wait gave up (a group barrier never
+// waits for threads that left).
+__device__ __forceinline__ bool group_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag, int group)
+{
+    wait_phase(bar, parity, abort_flag);
+    const int mine = *abort_flag ? 1 : 0;
+    int any;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.s32 p, %1, 0;\n bar.red.or.pred q, %2, %3, p;\n selp.s32 %0, 1, 0, q;\n}\n"
+        : "=r"(any)
+        : "r"(mine), "r"(group), "r"(kGroupThreads)
+        : "memory");
+    return !any;
+}
+
+// the single MMA thread
+__device__ __forceinline__ bool wait_ok(uint64_t *bar, uint32_t parity, volatile int *abort_flag)
+{
+    wait_phase(bar, parity, abort_flag);
+    return !*abort_flag;
+}
+
 __global__ void __launch_bounds__(kThreads, 1)
     mlp_forward_kernel(const float *__restrict__ X, int64_t rows, int n_in, const float *__restrict__ norm,
                        const __nv_bfloat16 *__restrict__ W1, const float *__restrict__ b1,
@@ -87,35 +124,37 @@ __global__ void __launch_bounds__(kThreads, 1)
                        const __nv_bfloat16 *__restrict__ W3, const float *__restrict__ b3, float *__restrict__ y,
                        int32_t *__restrict__ status)
 {
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
     unsigned char *w2s = smem;
     unsigned char *w1s = w2s + kW2Bytes;
     unsigned char *h1s = w1s + kW1Bytes;
-    // [2][128] row partials of the last layer; they live in H1's last K
-    // block, which layer 2 has finished reading when they are written
-    float *part = reinterpret_cast<float *>(h1s + 3 * kKBlockH);
-    __shared__ __align__(8) uint64_t mma_bar, drain_bar;
+    __shared__ float part[2][kRows];           // row partials of the last layer
+    __shared__ __align__(8) uint64_t x_full, m1_done, h1_full, m2_done, e2_free, drain_bar;
     __shared__ uint32_t tmem_base_sh;
     __shared__ volatile int abort_flag;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int quad = warp & 3, half = warp >> 2;
     const int64_t n_tiles = (rows + kRows - 1) / kRows;
+    const int64_t my_tiles = (int64_t)blockIdx.x < n_tiles ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
     if (tid == 0) {
-        mbar_init(&mma_bar, 1);
+        mbar_init(&x_full, kGroupWarps);
+        mbar_init(&m1_done, 1);
+        mbar_init(&h1_full, kGroupWarps);
+        mbar_init(&m2_done, 1);
+        mbar_init(&e2_free, kGroupWarps);
         mbar_init(&drain_bar, 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) {
+    if (warp == kWarpMma) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
                      "r"(512)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    // weights into the swizzled layouts
+    // weights into the swizzled layouts (all threads)
     for (int idx = tid; idx < kHidden * 32; idx += kThreads) {
         const int n = idx >> 5, c32 = idx & 31;
         const uint4 v = __ldg(reinterpret_cast<const uint4 *>(W2 + (size_t)n * kHidden) + c32);
@@ -134,158 +173,174 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         *reinterpret_cast<uint4 *>(w1s + sw(n, c)) = make_uint4(w[0], w[1], w[2], w[3]);
     }
+    fence_proxy_async();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = tmem_base_sh;
-    const uint32_t lane_addr = tmem_base + ((uint32_t)(quad * 32) << 16);
-    const int r = quad * 32 + lane;            // this thread's tile row in the epilogues
-    uint32_t phase = 0;
-    bool issued = false;
 
-    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        // ---- 1. stage x': the tile's rows (contiguous floats) are copied with
-        // coalesced 16-byte loads into H1's second K block, then each thread
-        // normalises two 16-byte chunks of its row into the first (BF16)
-        {
-            const int64_t r0 = tile * kRows;
-            const int64_t nrows = rows - r0 < kRows ? rows - r0 : kRows;
-            const int64_t nfl = nrows * n_in;                 // floats of the tile
-            float *xs = reinterpret_cast<float *>(h1s + kKBlockH);
-            const float *src = X + r0 * n_in;
-            if ((((uintptr_t)src) & 15) == 0) {
-                const int64_t n4 = nfl >> 2;
-                for (int64_t q = tid; q < n4; q += kThreads)
-                    reinterpret_cast<float4 *>(xs)[q] = __ldg(reinterpret_cast<const float4 *>(src) + q);
-                for (int64_t q = (n4 << 2) + tid; q < nfl; q += kThreads) xs[q] = __ldg(src + q);
-            } else {
-                for (int64_t q = tid; q < nfl; q += kThreads) xs[q] = __ldg(src + q);
-            }
-            __syncthreads();
-            const int sr = tid >> 1, sh = tid & 1;
-            const bool valid = sr < nrows;
-#pragma unroll
-            for (int cc = 0; cc < 4; cc++) {
-                const int c = 4 * sh + cc;
-                uint32_t w[4];
-#pragma unroll
-                for (int q = 0; q < 4; q++) {
-                    const int e0 = 8 * c + 2 * q, e1 = e0 + 1;
-                    const float a = (valid && e0 < n_in) ? (xs[sr * n_in + e0] - norm[e0]) * norm[n_in + e0] : 0.0f;
-                    const float b = (valid && e1 < n_in) ? (xs[sr * n_in + e1] - norm[e1]) * norm[n_in + e1] : 0.0f;
-                    w[q] = pack_bf16(a, b);
+    if (warp < kGroupWarps) {
+        // ------------------------------------- group A: stage x', layer-1 epilogue
+        const int quad = warp & 3, half = warp >> 2;
+        const int r = quad * 32 + lane;
+        const uint32_t lane_addr = tmem_base + ((uint32_t)(quad * 32) << 16);
+        for (int64_t i = 0; i < my_tiles; i++) {
+            const int64_t tile = blockIdx.x + i * (int64_t)gridDim.x;
+            // H1 (and the staging area) is free once the previous layer 2 is done
+            if (i > 0 && !group_wait(&m2_done, (uint32_t)((i - 1) & 1), &abort_flag, 1)) break;
+            {
+                const int64_t r0 = tile * kRows;
+                const int64_t nrows = rows - r0 < kRows ? rows - r0 : kRows;
+                const int64_t nfl = nrows * n_in;
+                float *xs = reinterpret_cast<float *>(h1s + kKBlockH);
+                const float *src = X + r0 * n_in;
+                if ((((uintptr_t)src) & 15) == 0) {
+                    const int64_t n4 = nfl >> 2;
+                    for (int64_t q = tid; q < n4; q += kGroupThreads)
+                        reinterpret_cast<float4 *>(xs)[q] = __ldg(reinterpret_cast<const float4 *>(src) + q);
+                    for (int64_t q = (n4 << 2) + tid; q < nfl; q += kGroupThreads) xs[q] = __ldg(src + q);
+                } else {
+                    for (int64_t q = tid; q < nfl; q += kGroupThreads) xs[q] = __ldg(src + q);
                 }
-                *reinterpret_cast<uint4 *>(h1s + sw(sr, c)) = make_uint4(w[0], w[1], w[2], w[3]);
-            }
-        }
-        fence_proxy_async();
-        tc_fence_before();
-        __syncthreads();
-        // ---- 2. layer 1 -----------------------------------------------------
-        if (tid == 0) {
-            tc_fence_after();
-            const uint64_t ad = sdesc(smem_u32(h1s)), bd = sdesc(smem_u32(w1s));
+                named_bar(1, kGroupThreads);
+                const int sr = tid >> 1, sh = tid & 1;
+                const bool valid = sr < nrows;
 #pragma unroll
-            for (int kk = 0; kk < kKin / 16; kk++) mma_bf16(tmem_base, ad + 2 * kk, bd + 2 * kk, kk ? 1u : 0u);
-            mma_commit(&mma_bar);
-            issued = true;
-        }
-        wait_phase(&mma_bar, phase, &abort_flag);
-        phase ^= 1;
-        __syncthreads();
-        if (abort_flag) break;
-        tc_fence_after();
-        // ---- 3. bias, ReLU, BF16 into H1 ---------------------------------------
+                for (int cc = 0; cc < 4; cc++) {
+                    const int c = 4 * sh + cc;
+                    uint32_t w[4];
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        const int e0 = 8 * c + 2 * q, e1 = e0 + 1;
+                        const float a = (valid && e0 < n_in) ? (xs[sr * n_in + e0] - norm[e0]) * norm[n_in + e0] : 0.0f;
+                        const float b = (valid && e1 < n_in) ? (xs[sr * n_in + e1] - norm[e1]) * norm[n_in + e1] : 0.0f;
+                        w[q] = pack_bf16(a, b);
+                    }
+                    *reinterpret_cast<uint4 *>(h1s + sw(sr, c)) = make_uint4(w[0], w[1], w[2], w[3]);
+                }
+            }
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&x_full);
+            // (the group meets here: every warp has also finished reading the
+            // staging rows that the layer-1 epilogue overwrites)
+            if (!group_wait(&m1_done, (uint32_t)(i & 1), &abort_flag, 1)) break;
+            tc_fence_after();
 #pragma unroll 1
-        for (int q = 0; q < 4; q++) {
-            const int col0 = 128 * half + 32 * q;
-            uint32_t v[32];
-            TMEM_LD32(lane_addr + (uint32_t)col0, v);
-            tmem_wait_ld();
+            for (int q = 0; q < 4; q++) {
+                const int col0 = 128 * half + 32 * q;
+                uint32_t v[32];
+                TMEM_LD32(lane_addr + (uint32_t)col0, v);
+                tmem_wait_ld();
 #pragma unroll
-            for (int c = 0; c < 4; c++) {
-                const float4 ba = __ldg(reinterpret_cast<const float4 *>(b1 + col0 + 8 * c));
-                const float4 bb = __ldg(reinterpret_cast<const float4 *>(b1 + col0 + 8 * c + 4));
-                const float bias[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
-                uint32_t w[4];
+                for (int c = 0; c < 4; c++) {
+                    const float4 ba = __ldg(reinterpret_cast<const float4 *>(b1 + col0 + 8 * c));
+                    const float4 bb = __ldg(reinterpret_cast<const float4 *>(b1 + col0 + 8 * c + 4));
+                    const float bias[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
+                    uint32_t w[4];
 #pragma unroll
-                for (int p = 0; p < 4; p++) {
-                    const int i = 8 * c + 2 * p;
-                    const float a = fmaxf(__uint_as_float(v[i]) + bias[2 * p], 0.0f);
-                    const float b = fmaxf(__uint_as_float(v[i + 1]) + bias[2 * p + 1], 0.0f);
-                    w[p] = pack_bf16(a, b);
+                    for (int p = 0; p < 4; p++) {
+                        const int ii = 8 * c + 2 * p;
+                        const float a = fmaxf(__uint_as_float(v[ii]) + bias[2 * p], 0.0f);
+                        const float b = fmaxf(__uint_as_float(v[ii + 1]) + bias[2 * p + 1], 0.0f);
+                        w[p] = pack_bf16(a, b);
+                    }
+                    const int col = col0 + 8 * c;
+                    *reinterpret_cast<uint4 *>(h1s + (col >> 6) * kKBlockH + sw(r, (col & 63) >> 3)) =
+                        make_uint4(w[0], w[1], w[2], w[3]);
                 }
-                const int col = col0 + 8 * c;
-                *reinterpret_cast<uint4 *>(h1s + (col >> 6) * kKBlockH + sw(r, (col & 63) >> 3)) =
-                    make_uint4(w[0], w[1], w[2], w[3]);
             }
+            fence_proxy_async();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&h1_full);
         }
-        fence_proxy_async();
-        tc_fence_before();
-        __syncthreads();
-        // ---- 4. layer 2 -----------------------------------------------------
-        if (tid == 0) {
+    } else if (warp < 2 * kGroupWarps) {
+        // ------------------------------------- group B: layer-2 epilogue and output
+        const int gw = warp - kGroupWarps;
+        const int quad = gw & 3, half = gw >> 2;
+        const int r = quad * 32 + lane;
+        const int gt = tid - kGroupThreads;
+        const uint32_t lane_addr = tmem_base + ((uint32_t)(quad * 32) << 16);
+        for (int64_t i = 0; i < my_tiles; i++) {
+            const int64_t tile = blockIdx.x + i * (int64_t)gridDim.x;
+            if (!group_wait(&m2_done, (uint32_t)(i & 1), &abort_flag, 2)) break;
             tc_fence_after();
+            float acc = 0.0f;
+#pragma unroll 1
+            for (int q = 0; q < 4; q++) {
+                const int col0 = 128 * half + 32 * q;
+                uint32_t v[32];
+                TMEM_LD32(lane_addr + (uint32_t)(kHidden + col0), v);
+                tmem_wait_ld();
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+                    const float4 ba = __ldg(reinterpret_cast<const float4 *>(b2 + col0 + 8 * c));
+                    const float4 bb = __ldg(reinterpret_cast<const float4 *>(b2 + col0 + 8 * c + 4));
+                    const float bias[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
+                    const uint4 w3 = __ldg(reinterpret_cast<const uint4 *>(W3 + col0 + 8 * c));
+                    const __nv_bfloat162 *wp = reinterpret_cast<const __nv_bfloat162 *>(&w3);
+#pragma unroll
+                    for (int p = 0; p < 4; p++) {
+                        const float2 wf = __bfloat1622float2(wp[p]);
+                        const int ii = 8 * c + 2 * p;
+                        const float h0 = bf16_round(fmaxf(__uint_as_float(v[ii]) + bias[2 * p], 0.0f));
+                        const float h1 = bf16_round(fmaxf(__uint_as_float(v[ii + 1]) + bias[2 * p + 1], 0.0f));
+                        acc = fmaf(h0, wf.x, acc);
+                        acc = fmaf(h1, wf.y, acc);
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&e2_free);
+            part[half][r] = acc;
+            named_bar(2, kGroupThreads);
+            if (gt < kRows) {
+                const int64_t row = tile * kRows + gt;
+                if (row < rows) y[row] = part[0][gt] + part[1][gt] + __ldg(b3);
+            }
+            named_bar(2, kGroupThreads);
+        }
+    } else if (warp == kWarpMma) {
+        // ------------------------------------- MMA issuer (one elected lane)
+        if (lane == 0) {
+            const uint64_t ad1 = sdesc(smem_u32(h1s)), bd1 = sdesc(smem_u32(w1s));
             const uint32_t h0 = smem_u32(h1s), w0 = smem_u32(w2s);
+            bool issued = false;
+            for (int64_t i = 0; i < my_tiles; i++) {
+                const uint32_t par = (uint32_t)(i & 1);
+                if (!wait_ok(&x_full, par, &abort_flag)) break;
+                tc_fence_after();
 #pragma unroll
-            for (int kb = 0; kb < 4; kb++) {
-                const uint64_t ad = sdesc(h0 + kb * kKBlockH), bd = sdesc(w0 + kb * kKBlockW);
+                for (int kk = 0; kk < kKin / 16; kk++) mma_bf16(tmem_base, ad1 + 2 * kk, bd1 + 2 * kk, kk ? 1u : 0u);
+                mma_commit(&m1_done);
+                issued = true;
+                if (!wait_ok(&h1_full, par, &abort_flag)) break;
+                if (i > 0 && !wait_ok(&e2_free, (uint32_t)((i - 1) & 1), &abort_flag)) break;
+                tc_fence_after();
 #pragma unroll
-                for (int kk = 0; kk < 4; kk++)
-                    mma_bf16(tmem_base + kHidden, ad + 2 * kk, bd + 2 * kk, (kb | kk) ? 1u : 0u);
-            }
-            mma_commit(&mma_bar);
-        }
-        wait_phase(&mma_bar, phase, &abort_flag);
-        phase ^= 1;
-        __syncthreads();
-        if (abort_flag) break;
-        tc_fence_after();
-        // ---- 5. bias, ReLU, BF16, dot with W3 ------------------------------------
-        float acc = 0.0f;
-#pragma unroll 1
-        for (int q = 0; q < 4; q++) {
-            const int col0 = 128 * half + 32 * q;
-            uint32_t v[32];
-            TMEM_LD32(lane_addr + (uint32_t)(kHidden + col0), v);
-            tmem_wait_ld();
+                for (int kb = 0; kb < 4; kb++) {
+                    const uint64_t ad = sdesc(h0 + kb * kKBlockH), bd = sdesc(w0 + kb * kKBlockW);
 #pragma unroll
-            for (int c = 0; c < 4; c++) {
-                const float4 ba = __ldg(reinterpret_cast<const float4 *>(b2 + col0 + 8 * c));
-                const float4 bb = __ldg(reinterpret_cast<const float4 *>(b2 + col0 + 8 * c + 4));
-                const float bias[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
-                const uint4 w3 = __ldg(reinterpret_cast<const uint4 *>(W3 + col0 + 8 * c));
-                const __nv_bfloat162 *wp = reinterpret_cast<const __nv_bfloat162 *>(&w3);
-#pragma unroll
-                for (int p = 0; p < 4; p++) {
-                    const float2 wf = __bfloat1622float2(wp[p]);
-                    const int i = 8 * c + 2 * p;
-                    const float h0 = bf16_round(fmaxf(__uint_as_float(v[i]) + bias[2 * p], 0.0f));
-                    const float h1 = bf16_round(fmaxf(__uint_as_float(v[i + 1]) + bias[2 * p + 1], 0.0f));
-                    acc = fmaf(h0, wf.x, acc);
-                    acc = fmaf(h1, wf.y, acc);
+                    for (int kk = 0; kk < 4; kk++)
+                        mma_bf16(tmem_base + kHidden, ad + 2 * kk, bd + 2 * kk, (kb | kk) ? 1u : 0u);
                 }
+                mma_commit(&m2_done);
             }
+            if (issued) {
+                // every MMA finished before tensor memory is freed
+                mma_commit(&drain_bar);
+                const uint64_t t0 = now_ns();
+                while (!mbar_try(&drain_bar, 0) && now_ns() - t0 < kTimeoutNs) {}
+            }
+            if (abort_flag) atomicOr(status, ST_TIMEOUT);
         }
-        part[half * kRows + r] = acc;
-        tc_fence_before();
-        __syncthreads();
-        if (tid < kRows) {
-            const int64_t row = tile * kRows + tid;
-            if (row < rows) y[row] = part[tid] + part[kRows + tid] + __ldg(b3);
-        }
-    }
-    __syncthreads();
-    if (tid == 0 && issued && abort_flag) {
-        // drain whatever MMA is still in flight before tensor memory is freed
-        mma_commit(&drain_bar);
-        const uint64_t t0 = now_ns();
-        while (!mbar_try(&drain_bar, 0) && now_ns() - t0 < kTimeoutNs) {}
-        atomicOr(status, ST_TIMEOUT);
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) {
+    if (warp == kWarpMma) {
+        __syncwarp();
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(512) : "memory");
     }
