@@ -57,7 +57,9 @@ typedef enum {
 typedef enum {
     EPI_PATH_AUTO = 0,     /* fastest exact path for the order and sizes */
     EPI_PATH_POPC = 1,     /* bitwise AND + POPC on the integer pipe */
-    EPI_PATH_TC = 2        /* exact 0/1 GEMM on tcgen05 tensor cores */
+    EPI_PATH_TC = 2        /* exact 0/1 GEMM on tcgen05 tensor cores: orders
+                              2..5 with cases and controls present, whole
+                              combination range only (EPI_EUNSUPPORTED else) */
 } epi_path;
 
 #define EPI_MAX_ORDER 8    /* highest order the API accepts (Table 2 goes to 8) */
@@ -338,15 +340,17 @@ typedef struct epi_proposer_stats {
 epi_status epi_proposer_search(epi_dataset *ds, epi_mlp *net, const epi_proposer_opts *opts, epi_result *out,
                                uint32_t *counts, int32_t *n_out, epi_proposer_stats *stats);
 
-/* Fits `net` (25 inputs) to rank order-5 sets: on each dataset (C(n_snps, 5)
- * at most 2^32: the labels come from the exhaustive order-5 scores) the
- * space of epi_proposer_search with the given top_triples is built, each
- * distinct set labelled by its exact MI (see `target`); inputs are
- * standardised (the normalisation is stored in the network), and `epochs` passes of
+/* Fits `net` (25 inputs) to rank order-5 sets: on each dataset the space of
+ * epi_proposer_search with the given top_triples is built and every row (a
+ * candidate 5-set) is labelled by its exact MI (its table counted, Section
+ * 2.2, and scored, Eq. 1-3; see `target`), a set holding several of the
+ * triples counted once for sampling; inputs are standardised (the
+ * normalisation is stored in the network), and `epochs` passes of
  * mini-batch AdamW (cosine decay from lr to lr / 20, weight decay wd) are
  * run; tail_fraction of each batch is drawn from the 4096 best-labelled sets
  * of each dataset, the rest uniformly, from a counter-based generator seeded
- * by `seed`.  Host epoch_loss [epochs] (may be NULL) receives the mean
+ * by `seed`.  The rows stay in device memory (113 bytes each; EPI_ENOMEM if
+ * they do not fit).  Host epoch_loss [epochs] (may be NULL) receives the mean
  * sampled batch loss of each epoch.  The paper has no counterpart. */
 typedef struct epi_train_opts {
     int top_triples;

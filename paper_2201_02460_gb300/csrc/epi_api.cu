@@ -220,11 +220,11 @@ epi_status plan_popc(const epi_dataset *ds, SearchPlan &p, int R_req = 0)
     return EPI_OK;
 }
 
-// Tensor-core path conditions: orders 2..4, both classes present, the whole
+// Tensor-core path conditions: orders 2..5, both classes present, the whole
 // combination range (the tensor tiles follow panel order, not rank order).
 bool tc_applicable(const epi_dataset *ds, int k, uint64_t rb, uint64_t re, uint64_t total)
 {
-    return k >= 2 && k <= 4 && ds->m1 > 0 && ds->m0 > 0 && rb == 0 && re == total && ds->n >= k + 1;
+    return k >= 2 && k <= 5 && ds->m1 > 0 && ds->m0 > 0 && rb == 0 && re == total && ds->n >= k + 1;
 }
 
 epi_status choose_path(const epi_dataset *ds, int k, int path, uint64_t rb, uint64_t re, uint64_t total, bool &tc)
@@ -233,7 +233,7 @@ epi_status choose_path(const epi_dataset *ds, int k, int path, uint64_t rb, uint
     if (path == EPI_PATH_TC) {
         if (!ok)
             return fail(EPI_EUNSUPPORTED,
-                        "tensor-core path needs order 2..4, cases and controls, and the whole combination range");
+                        "tensor-core path needs order 2..5, cases and controls, and the whole combination range");
         tc = true;
     } else if (path == EPI_PATH_POPC) {
         tc = false;

@@ -82,8 +82,8 @@ cudaError_t launch_mlp_forward_tc(const float *X, int64_t rows, int n_in, const 
                                   const float *b1, const void *W2, const float *b2, const void *W3, const float *b3,
                                   float *y, int32_t *status, int num_sms, cudaStream_t st);
 cudaError_t launch_cand_features5(const DevData &d, const uint32_t *triples, int64_t first, int64_t count,
-                                  const float *s1, const float *s2, const float *s3, const float *s5, float *X,
-                                  uint8_t *keep, float *label, uint32_t *combs, cudaStream_t st);
+                                  const float *s1, const float *s2, const float *s3, float *X, uint8_t *keep,
+                                  uint32_t *combs, cudaStream_t st);
 cudaError_t launch_lookup(const DevData &d, int k, const float *table, const uint32_t *combs, int64_t count,
                           float *out, cudaStream_t st);
 // epi_topk.cu: the k best of count scores (score desc, index asc; keep may

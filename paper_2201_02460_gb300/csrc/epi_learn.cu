@@ -194,14 +194,12 @@ __global__ void candidates5_at_kernel(DevData d, const uint32_t *__restrict__ tr
 }
 
 // Candidates [first, first + count) in one pass: the set, whether its
-// generating triple is its best (keep), its 25 features, and optionally its
-// order-5 label ln(s5[rank] + 1e-7) (training); the set itself is written
-// only when combs is given.
+// generating triple is its best (keep) and its 25 features; the set itself is
+// written only when combs is given.
 __global__ void __launch_bounds__(256) cand_features5_kernel(DevData d, const uint32_t *__restrict__ triples,
                                                              int64_t first, int64_t count, const float *__restrict__ s1,
                                                              const float *__restrict__ s2, const float *__restrict__ s3,
-                                                             const float *__restrict__ s5, float *__restrict__ X,
-                                                             uint8_t *__restrict__ keep, float *__restrict__ label,
+                                                             float *__restrict__ X, uint8_t *__restrict__ keep,
                                                              uint32_t *__restrict__ combs)
 {
     const int64_t n = d.n;
@@ -246,10 +244,6 @@ __global__ void __launch_bounds__(256) cand_features5_kernel(DevData d, const ui
             for (int b = a + 1; b < 5; b++) f2[q++] = s2[n2 - 1 - (b2[n - 1 - v[a]] + (uint64_t)(n - 1 - v[b]))];
 #pragma unroll
         for (int t = 0; t < 5; t++) f1[t] = s1[v[t]];
-        if (label) {
-            int32_t c5[5] = {v[0], v[1], v[2], v[3], v[4]};
-            label[i] = logf(fmaxf(s5[lex_rank(d.binom, n, 5, c5)], 0.0f) + 1e-7f);
-        }
         sort_desc(f1);
         sort_desc(f2);
         sort_desc(f3);
@@ -780,11 +774,11 @@ cudaError_t launch_candidates5_at(const DevData &d, const uint32_t *triples, con
 }
 
 cudaError_t launch_cand_features5(const DevData &d, const uint32_t *triples, int64_t first, int64_t count,
-                                  const float *s1, const float *s2, const float *s3, const float *s5, float *X,
-                                  uint8_t *keep, float *label, uint32_t *combs, cudaStream_t st)
+                                  const float *s1, const float *s2, const float *s3, float *X, uint8_t *keep,
+                                  uint32_t *combs, cudaStream_t st)
 {
-    learn::cand_features5_kernel<<<blocks_for(count), 256, 0, st>>>(d, triples, first, count, s1, s2, s3, s5, X, keep,
-                                                                    label, combs);
+    learn::cand_features5_kernel<<<blocks_for(count), 256, 0, st>>>(d, triples, first, count, s1, s2, s3, X, keep,
+                                                                    combs);
     return cudaGetLastError();
 }
 

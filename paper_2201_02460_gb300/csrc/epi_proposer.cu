@@ -6,9 +6,9 @@
 // the network-free heuristic), the best R are recounted and scored exactly
 // (tables and FP64 MI of Eq. 1-3), and the best top_n of those are returned.
 //
-// Training: on datasets small enough for the exhaustive order-5 search, the
-// same expansions are labelled with their exact order-5 MI (from the
-// exhaustive scores) and the network is fitted to ln(MI + 1e-7), standardised,
+// Training: the same expansions of training datasets are labelled with their
+// exact order-5 MI (every row's table counted and scored, Section 2.2 and
+// Eq. 1-3) and the network is fitted to ln(MI + 1e-7), standardised,
 // by AdamW on mini-batches drawn on the device; part of every batch comes from
 // each dataset's best-labelled rows, where the ranking matters.
 //
@@ -38,6 +38,13 @@ __global__ void count_kernel(const uint8_t *__restrict__ keep, int64_t count, un
         c += keep[i];
     for (int off = 16; off; off >>= 1) c += __shfl_down_sync(0xffffffffu, c, off);
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+// t[i] = ln(max(s, 0) + 1e-7): the training label of an exact order-5 score
+__global__ void log_label_kernel(float *t, int64_t count)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        t[i] = logf(fmaxf(t[i], 0.0f) + 1e-7f);
 }
 
 // mean and standard deviation of column f of X [rows][cols] (one block per
@@ -158,21 +165,14 @@ double now_ms()
 }
 
 // Exhaustive single-precision scores of orders 1, 2, 3 (kept with the
-// dataset) and, when wanted, 5 (owned by the pool).
+// dataset).
 struct Lower {
-    const float *s[6] = {};
+    const float *s[4] = {};
 };
 
-epi_status lower_tables(epi_dataset *ds, Pool &pool, Lower &L, bool with5)
+epi_status lower_tables(epi_dataset *ds, Lower &L)
 {
-    const DevData d = epi_dataset_dev(ds);
     for (int k : {1, 2, 3}) PST(epi_dataset_lower_scores(ds, k, &L.s[k]));
-    if (with5) {
-        float *s5;
-        PCK(pool.get(&s5, host_binom(d.n, 5)));
-        PST(epi_score_all(ds, 5, s5));
-        L.s[5] = s5;
-    }
     return EPI_OK;
 }
 
@@ -228,8 +228,8 @@ epi_status rank_and_select(epi_dataset *ds, epi_mlp *net, const DevData &d, cons
     PCK(cudaMemsetAsync(kept_dev, 0, 8, st));
     for (uint64_t first = 0; first < total; first += (uint64_t)chunk) {
         const int64_t cnt = (int64_t)std::min<uint64_t>((uint64_t)chunk, total - first);
-        PCK(launch_cand_features5(d, triples, (int64_t)first, cnt, L.s[1], L.s[2], L.s[3], nullptr, X, keep + first,
-                                  nullptr, nullptr, st));
+        PCK(launch_cand_features5(d, triples, (int64_t)first, cnt, L.s[1], L.s[2], L.s[3], X, keep + first, nullptr,
+                                  st));
         if (net) PST(epi_mlp_forward(net, X, cnt, score + first));
         else PST(epi_heuristic5(ctx, X, cnt, score + first));
         count_kernel<<<grid_for(cnt), 256, 0, st>>>(keep + first, cnt, kept_dev);
@@ -313,7 +313,7 @@ epi_status epi_proposer_search(epi_dataset *ds, epi_mlp *net, const epi_proposer
 
     // exhaustive lower orders and the expanded triples
     Lower L;
-    PST(lower_tables(ds, pool, L, false));
+    PST(lower_tables(ds, L));
     uint32_t *triples;
     int T = 0;
     PST(best_triples(ds, pool, L.s[3], opts->top_triples, &triples, &T));
@@ -426,8 +426,6 @@ epi_status epi_proposer_train(epi_mlp *net, epi_dataset *const *datasets, int n_
             return pfail(EPI_EINVAL, "epi_proposer_train: datasets must share one context");
         const DevData d = epi_dataset_dev(datasets[i]);
         if (d.n < 5) return pfail(EPI_EINVAL, "epi_proposer_train: every dataset needs at least 5 SNPs");
-        if (host_binom(d.n, 5) > ((uint64_t)1 << 32))
-            return pfail(EPI_EUNSUPPORTED, "epi_proposer_train: C(n_snps, 5) above 2^32 (exhaustive labels too large)");
     }
     Pool pool(st);
     // rows of every dataset: features, labels, keep mask
@@ -440,6 +438,12 @@ epi_status epi_proposer_train(epi_mlp *net, epi_dataset *const *datasets, int n_
         base[i + 1] = base[i] + (int64_t)T * (int64_t)host_binom(d.n - 3, 2);
     }
     const int64_t rows = base[n_ds];
+    {
+        size_t free_b = 0, total_b = 0;
+        PCK(cudaMemGetInfo(&free_b, &total_b));
+        if ((size_t)rows * ((size_t)n_in * 4 + 13) + ((size_t)4 << 30) > free_b)
+            return pfail(EPI_ENOMEM, "epi_proposer_train: the training rows do not fit in device memory");
+    }
     float *X, *t;
     uint8_t *keep;
     PCK(pool.get(&X, (size_t)rows * n_in));
@@ -455,17 +459,24 @@ epi_status epi_proposer_train(epi_mlp *net, epi_dataset *const *datasets, int n_
         const DevData d = epi_dataset_dev(ds);
         Pool lp(st);
         Lower L;
-        PST(lower_tables(ds, lp, L, true));
+        PST(lower_tables(ds, L));
         uint32_t *triples;
         int T = 0;
         PST(best_triples(ds, lp, L.s[3], Ts[i], &triples, &T));
         const int64_t cnt = base[i + 1] - base[i];
-        for (int64_t f = 0; f < cnt; f += (int64_t)1 << 24) {
-            const int64_t c = std::min<int64_t>(cnt - f, (int64_t)1 << 24);
+        // labels: every row's 5-way table counted and scored exactly
+        constexpr int64_t kSlice = (int64_t)1 << 20;
+        uint32_t *combs, *tabs;
+        PCK(lp.get(&combs, (size_t)std::min<int64_t>(cnt, kSlice) * 5));
+        PCK(lp.get(&tabs, (size_t)std::min<int64_t>(cnt, kSlice) * 2 * 243));
+        for (int64_t f = 0; f < cnt; f += kSlice) {
+            const int64_t c = std::min<int64_t>(cnt - f, kSlice);
             const int64_t at = base[i] + f;
-            PCK(launch_cand_features5(d, triples, f, c, L.s[1], L.s[2], L.s[3], L.s[5], X + at * n_in, keep + at,
-                                      t + at, nullptr, st));
-            launches += 1;
+            PCK(launch_cand_features5(d, triples, f, c, L.s[1], L.s[2], L.s[3], X + at * n_in, keep + at, combs, st));
+            PCK(launch_tables(d, 5, combs, c, tabs, epi_ctx_num_sms(ctx), st));
+            PCK(launch_score_tables(d, 5, tabs, c, t + at, nullptr, epi_ctx_num_sms(ctx), st));
+            log_label_kernel<<<grid_for(c), 256, 0, st>>>(t + at, c);
+            launches += 4;
         }
         // this dataset's best-labelled kept rows
         const int kt = (int)std::min<int64_t>(kTail, cnt);

@@ -264,6 +264,13 @@ __device__ __forceinline__ uint32_t f2u_exact(float v) { return __float_as_uint(
 // t(x) = x log2 x of an accumulator value x = count / 32 (0 for x = 0)
 __device__ __forceinline__ float tlog32(float x) { return x * __log2f(fmaxf(x, 0.03125f)); }
 
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
 template <int PR>
 __device__ __forceinline__ float seg_sum(float v, int pos)
 {
@@ -341,9 +348,12 @@ template <int K>
 __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_constant__ CUtensorMap tmap_b,
                                                                 const Params P)
 {
-    constexpr int kPR = K == 2 ? 3 : (K == 3 ? 9 : 27);
-    constexpr int kPPW = 32 / kPR;
-    constexpr int kPPT = 4 * kPPW;
+    constexpr int kPR = K == 2 ? 3 : (K == 3 ? 9 : (K == 4 ? 27 : 81));
+    // order 5: one prefix per tile, its 81 rows over lane quadrants 0-2 (the
+    // epilogue sums a combination across warps through shared memory)
+    constexpr bool kWide = kPR > 32;
+    constexpr int kPPW = kWide ? 0 : 32 / kPR;
+    constexpr int kPPT = kWide ? 1 : 4 * kPPW;
     constexpr int km1 = K - 1;
     constexpr int kWarpTma = kEpiWarps + kProdWarps;
     constexpr int kWarpMma = kWarpTma + 1;
@@ -373,6 +383,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
     __shared__ uint32_t tmem_base_sh;
     __shared__ volatile int abort_flag;
     __shared__ EpiState ES;
+    // order 5: per-warp partial sums [jhalf][quadrant][last SNP of the chunk]
+    __shared__ float wred[2][4][8], wpre[2][4][8];
+    __shared__ int wflag[2][8];
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -556,11 +569,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
             const Desc &D = desc[dq];
             const uint4 *rows[km1];
             bool active = false;
-            if (l < kPPW * kPR) {
-                const int p = w * kPPW + l / kPR;
+            if (kWide ? r < kPR : l < kPPW * kPR) {
+                const int p = kWide ? 0 : w * kPPW + l / kPR;
                 if (p < D.nvalid) {
                     active = true;
-                    int rem = l % kPR, div = kPR / 3;
+                    int rem = kWide ? r : l % kPR, div = kPR / 3;
 #pragma unroll
                     for (int tt = 0; tt < km1; tt++) {
                         const int gg = rem / div;
@@ -648,9 +661,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
         const int jhalf = warp >> 2;         // which 32 last SNPs of the tile
         const int r = quad * 32 + lane;      // tile row = TMEM lane
         const int l = lane;
-        const int pos = l % kPR;
-        const int pl = l / kPR;
-        const bool lane_real = l < kPPW * kPR;
+        const int pos = kWide ? r : l % kPR;          // row of the prefix's table
+        const int pl = kWide ? 0 : l / kPR;
+        const bool lane_real = kWide ? r < kPR : l < kPPW * kPR;
         const MiConstF32 mc = make_mi_const(d.m, d.m1, d.m0);
         const float vscale = 32.0f * DS.ln2_over_m, voff = DS.tconst * DS.ln2_over_m;
         long long w_epi = 0;
@@ -703,6 +716,90 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&acc_empty[b]);
                 }
+                if constexpr (kWide) {
+                    // screen sums of the chunk's 8 last SNPs: each warp sums
+                    // its rows, the quadrant-0 warp of the half adds the three
+                    float vs[8];
+#pragma unroll
+                    for (int jj = 0; jj < 8; jj++) {
+                        const int32_t j = j0 + 8 * jc + jj;
+                        const float fa0 = __uint_as_float(cs[2 * jj]), fa1 = __uint_as_float(cs[2 * jj + 1]);
+                        const float fb0 = __uint_as_float(cn[2 * jj]), fb1 = __uint_as_float(cn[2 * jj + 1]);
+                        const float fa2 = fT1 - fa0 - fa1, fb2 = fT0 - fb0 - fb1;
+                        const bool valid = prow && j < d.n && j > cpre;
+                        if (P.dump && valid) {
+                            uint64_t rs = 0;
+#pragma unroll
+                            for (int tt = 0; tt < km1; tt++) rs += binom_at(d.binom, d.n, d.n - 1 - psnp[tt], K - tt);
+                            rs += binom_at(d.binom, d.n, d.n - 1 - j, 1);
+                            constexpr int cells = kPR * 3;
+                            uint32_t *o = P.dump + (DS.total - 1 - rs) * 2 * cells;
+                            o[pos * 3 + 0] = f2u_exact(32.0f * fa0); o[pos * 3 + 1] = f2u_exact(32.0f * fa1);
+                            o[pos * 3 + 2] = f2u_exact(32.0f * fa2);
+                            o[cells + pos * 3 + 0] = f2u_exact(32.0f * fb0);
+                            o[cells + pos * 3 + 1] = f2u_exact(32.0f * fb1);
+                            o[cells + pos * 3 + 2] = f2u_exact(32.0f * fb2);
+                        }
+                        float v = 0.0f;
+                        if (prow)
+                            v = (tlog32(fa0) + tlog32(fb0) - tlog32(fa0 + fb0)) +
+                                (tlog32(fa1) + tlog32(fb1) - tlog32(fa1 + fb1)) +
+                                (tlog32(fa2) + tlog32(fb2) - tlog32(fa2 + fb2));
+                        vs[jj] = warp_sum(v);
+                    }
+                    if (lane == 0) {
+#pragma unroll
+                        for (int jj = 0; jj < 8; jj++) wred[jhalf][quad][jj] = vs[jj];
+                    }
+                    epi_bar();
+                    if (quad == 0 && lane < 8) {
+                        const float tv = wred[jhalf][0][lane] + wred[jhalf][1][lane] + wred[jhalf][2][lane] +
+                                         wred[jhalf][3][lane];
+                        const int32_t j = j0 + 8 * jc + lane;
+                        const bool valid = prow && j < d.n && j > cpre;
+                        wflag[jhalf][lane] = (valid && fmaf(tv, vscale, voff) >= cut) ? 1 : 0;
+                    }
+                    epi_bar();
+                    int anyf = 0;
+#pragma unroll
+                    for (int q = 0; q < 16; q++) anyf |= wflag[q >> 3][q & 7];
+                    if (anyf) {
+                        // precise single-precision scores of the flagged sets
+#pragma unroll 1
+                        for (int jj = 0; jj < 8; jj++) {
+                            if (!wflag[jhalf][jj]) continue;
+                            float e = 0.0f;
+                            if (prow) {
+                                const float fa0 = __uint_as_float(cs[2 * jj]), fa1 = __uint_as_float(cs[2 * jj + 1]);
+                                const float fb0 = __uint_as_float(cn[2 * jj]), fb1 = __uint_as_float(cn[2 * jj + 1]);
+                                e = row_terms_precise(f2u_exact(32.0f * fa0), f2u_exact(32.0f * fb0),
+                                                      f2u_exact(32.0f * fa1), f2u_exact(32.0f * fb1),
+                                                      f2u_exact(32.0f * (fT1 - fa0 - fa1)),
+                                                      f2u_exact(32.0f * (fT0 - fb0 - fb1)), mc);
+                            }
+                            e = warp_sum(e);
+                            if (lane == 0) wpre[jhalf][quad][jj] = e;
+                        }
+                        epi_bar();
+                        if (quad == 0 && lane < 8 && wflag[jhalf][lane]) {
+                            const float e = wpre[jhalf][0][lane] + wpre[jhalf][1][lane] + wpre[jhalf][2][lane] +
+                                            wpre[jhalf][3][lane];
+                            const float score = __fdiv_rn(e, mc.fm);
+                            if (score >= thr) {
+                                const int32_t j = j0 + 8 * jc + lane;
+                                uint64_t rk_sum = 0;
+#pragma unroll
+                                for (int tt = 0; tt < km1; tt++)
+                                    rk_sum += binom_at(d.binom, d.n, d.n - 1 - psnp[tt], K - tt);
+                                rk_sum += binom_at(d.binom, d.n, d.n - 1 - j, 1);
+                                const int slot = list_len + atomicAdd(&ES.nbuf, 1);
+                                sc[slot] = score;
+                                rk[slot] = DS.total - 1 - rk_sum;
+                            }
+                        }
+                        epi_bar();
+                    }
+                } else {
 #pragma unroll
                 for (int jj = 0; jj < 8; jj++) {
                     const int32_t j = j0 + 8 * jc + jj;
@@ -760,6 +857,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                             }
                         }
                     }
+                }
                 }
                 if (jc % kJcPerCheck == kJcPerCheck - 1) {
                     epi_bar();
@@ -884,10 +982,12 @@ cudaError_t launch_build_b8(const DevData &d, unsigned char *b8, int num_sms, cu
 
 // Work items of an order-k search (same formula as item_cum_kernel): the
 // host needs the count to split items over the CTAs.
+static int tc_pr(int k) { return k == 2 ? 3 : (k == 3 ? 9 : (k == 4 ? 27 : 81)); }
+static int tc_ppt(int k) { return tc_pr(k) > 32 ? 1 : 4 * (32 / tc_pr(k)); }
+
 uint64_t tc_item_count(int64_t n, int k)
 {
-    const int PR = k == 2 ? 3 : (k == 3 ? 9 : 27);
-    const uint64_t ppt = 4 * (32 / PR);
+    const uint64_t ppt = (uint64_t)tc_ppt(k);
     uint64_t total = 0;
     for (int64_t c = k - 2; c <= n - 2; c++) {
         const uint64_t t0 = (host_binom(c, k - 1) + ppt - 1) / ppt;
@@ -909,7 +1009,6 @@ size_t tc_smem_bytes(int cand_p2)
            tc::kDescDepth * sizeof(tc::Desc) + 64;
 }
 
-static int tc_ppt(int k) { return 4 * (32 / (k == 2 ? 3 : (k == 3 ? 9 : 27))); }
 
 static cudaError_t encode_map(CUtensorMap *map, const DevData &d, const unsigned char *b8)
 {
@@ -945,7 +1044,7 @@ static void fill_ds(tc::DsParams &D, const DevData &d, int k, uint64_t *item_cum
     D.ln2_over_m = (float)(0.6931471805599453 / (double)d.m);
     // screening margin: relative errors of the log2 approximation (2^-21)
     // and of the float sums over (T(m) + T(m1) + T(m0)), doubled
-    const int64_t cells = (int64_t)(k == 2 ? 3 : (k == 3 ? 9 : 27)) * 3;
+    const int64_t cells = (int64_t)tc_pr(k) * 3;
     // bound on the summed magnitudes of the screen's terms: with t(x) =
     // T(32 x) / 32 - 5 x over accumulator values x = count / 32, 32 sum |t|
     // <= sum T(c) + 5 sum c <= T(m) + T(m1) + T(m0) + 10 m
@@ -963,9 +1062,9 @@ static void fill_launch(tc::Params &P, int k, int pool, float *list_score, uint6
                         int32_t *status, uint32_t *dump, unsigned long long *waits)
 {
     P.k = k;
-    P.PR = k == 2 ? 3 : (k == 3 ? 9 : 27);
-    P.ppw = 32 / P.PR;
-    P.ppt = 4 * P.ppw;
+    P.PR = tc_pr(k);
+    P.ppw = P.PR > 32 ? 0 : 32 / P.PR;
+    P.ppt = tc_ppt(k);
     P.pool = pool;
     P.cand_p2 = next_pow2(pool + 2 * (k == 2 ? 1 : 2) * 16 * P.ppt);   // two check intervals (kJcPerCheck)
     P.list_score = list_score;
@@ -979,7 +1078,10 @@ static void fill_launch(tc::Params &P, int k, int pool, float *list_score, uint6
 static cudaError_t launch_kernel(const CUtensorMap &map, const tc::Params &P, int k, int grid, cudaStream_t st)
 {
     const size_t smem = tc_smem_bytes(P.cand_p2);
-    auto kern = k == 2 ? tc::tc_search_kernel<2> : (k == 3 ? tc::tc_search_kernel<3> : tc::tc_search_kernel<4>);
+    auto kern = k == 2   ? tc::tc_search_kernel<2>
+                : k == 3 ? tc::tc_search_kernel<3>
+                : k == 4 ? tc::tc_search_kernel<4>
+                         : tc::tc_search_kernel<5>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, tc::kThreads, smem, st>>>(map, P);

@@ -213,7 +213,7 @@ def test_score_tables_fp32_accuracy(epi, ctx):
 # ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("k,n,m", [(2, 50, 300), (3, 24, 700), (3, 40, 129), (4, 14, 1000), (4, 12, 257),
-                                   (3, 70, 2000), (2, 150, 64)])
+                                   (3, 70, 2000), (2, 150, 64), (5, 12, 700), (5, 16, 129), (5, 30, 1000)])
 def test_tc_counts_bit_exact(epi, ctx, k, n, m):
     """Every combination's table from the tensor-core kernel equals the
     popcount table kernel's and the oracle's, bit for bit."""
@@ -228,7 +228,8 @@ def test_tc_counts_bit_exact(epi, ctx, k, n, m):
 
 
 @pytest.mark.parametrize("k,n,m,top_n", [(2, 60, 257, 25), (3, 30, 700, 50), (3, 90, 1500, 100),
-                                         (4, 22, 1100, 40), (4, 30, 513, 64)])
+                                         (4, 22, 1100, 40), (4, 30, 513, 64), (5, 18, 900, 40),
+                                         (5, 26, 400, 100)])
 def test_tc_search_small(epi, ctx, k, n, m, top_n):
     geno, pheno = random_data(n, m, seed=11 * k + n)
     ds, r, oc, om, _ = _search_both(epi, ctx, geno, pheno, k, top_n, path="tc")
@@ -241,6 +242,19 @@ def test_tc_matches_popc(epi, ctx):
     ds = epi.Dataset(ctx, geno, pheno)
     a = epi.search(ds, 3, 200, path="popc")
     b = epi.search(ds, 3, 200, path="tc")
+    assert (a.combs == b.combs).all()
+    assert (a.mi == b.mi).all()
+    assert (a.counts == b.counts).all()
+    np.testing.assert_allclose(a.mi_f32, b.mi_f32, rtol=2e-6)
+
+
+def test_tc_matches_popc_order5(epi, ctx):
+    # order 5: one prefix per tile, a combination summed across three warps
+    geno, pheno = random_data(90, 2000, seed=78)
+    geno[40] = geno[3]
+    ds = epi.Dataset(ctx, geno, pheno)
+    a = epi.search(ds, 5, 150, path="popc")
+    b = epi.search(ds, 5, 150, path="tc")
     assert (a.combs == b.combs).all()
     assert (a.mi == b.mi).all()
     assert (a.counts == b.counts).all()
