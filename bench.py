@@ -379,6 +379,9 @@ def run_ours(args):
         comp["batch64/auto"] = measure_batch(epi, ctx, synth, args.batch_div)
         if d.n_snps >= 5:
             comp[f"proposer_order5/{args.workload}"] = measure_proposer(epi, ctx, ds, peaks)
+        if args.proposer_eval:
+            from paper_2201_02460_gb300 import proposer_eval
+            comp["proposer_order5/recall_200snp_2000"] = proposer_eval.evaluate(ctx)
         line["compare"] = comp
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -405,6 +408,8 @@ def main():
     ap.add_argument("--full-compare", action="store_true", help="also time the order-4 popcount path (~26 s)")
     ap.add_argument("--n-snps", type=int, default=None, help="smaller SNP count (profiling captures)")
     ap.add_argument("--batch-div", type=int, default=3, help="SNP-count divisor of the 64-dataset batch")
+    ap.add_argument("--proposer-eval", action="store_true",
+                    help="also train the order-5 proposer and measure its recall (several minutes)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -1,0 +1,82 @@
+"""Training and recall evaluation of the learned order-5 proposer.
+
+Trains the 25-256-256-1 network (epi_proposer_train) on synthetic
+200-SNP x 2000-sample datasets shaped like the training configuration
+(Hardy-Weinberg genotypes, MAF ~ U[0.05, 0.5], balanced classes, every other
+dataset with a planted 5-SNP parity), then measures on held-out datasets of
+the same shape the recall of the exhaustive order-5 top-100 (the tensor-core
+search) among the proposer's top-100, for the network and for the
+network-free heuristic, at several re-score budgets.
+
+    python -m paper_2201_02460_gb300.proposer_eval [--train 8] [--epochs 4] [--top-triples 1024]
+
+prints one JSON line.  Every step runs in the library's kernels.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+from . import epi, synth
+
+
+def make(ctx, seed: int, plant: bool, n_snps: int = 200, n_samples: int = 2000):
+    d = synth.make_dataset(n_snps, n_samples // 2, n_samples - n_samples // 2, seed=seed,
+                           plant_q=5 if plant else 0, plant_e=0.25 if plant else 0.0)
+    return epi.Dataset(ctx, d.geno, d.pheno)
+
+
+def evaluate(ctx=None, n_train: int = 8, epochs: int = 4, top_triples: int = 1024, n_eval: int = 3,
+             budgets=(4096, 10 ** 6, 10 ** 7), eval_triples=(1024, 4096), seed: int = 7) -> dict:
+    ctx = ctx or epi.Context(0)
+    t0 = time.perf_counter()
+    train = [make(ctx, synth.BASE_SEED + 200 + i, i % 2 == 0) for i in range(n_train)]
+    evals = [make(ctx, synth.BASE_SEED + 103 + i, i % 2 == 0) for i in range(n_eval)]
+    truth = []
+    t_truth = time.perf_counter()
+    for ds in evals:
+        r = epi.search(ds, 5, 100, path="tc")
+        truth.append({tuple(int(x) for x in c) for c in r.combs})
+    t_truth = time.perf_counter() - t_truth
+    net = epi.MLP(ctx, 25, 256, seed=1)
+    t_train = time.perf_counter()
+    losses = epi.proposer_train(net, train, top_triples, epochs, 8192, 1e-3, 1e-4, 0.5, seed)
+    t_train = time.perf_counter() - t_train
+    rows = []
+    for T in eval_triples:
+        for R in budgets:
+            for name, scorer in (("heuristic", None), ("network", net)):
+                rec, secs = [], []
+                for ds, tr in zip(evals, truth):
+                    t1 = time.perf_counter()
+                    r, st = epi.proposer_search(ds, scorer, T, R, 100)
+                    secs.append(time.perf_counter() - t1)
+                    rec.append(len({tuple(int(x) for x in c) for c in r.combs} & tr) / 100.0)
+                rows.append(dict(ranking=name, top_triples=T, budget=R, recall_at_100=rec,
+                                 mean_recall=sum(rec) / len(rec), seconds_per_search=sum(secs) / len(secs)))
+    net.close()
+    for ds in train + evals:
+        ds.close()
+    return dict(metric="top-N recall at k=5 (recall@100 of the exhaustive order-5 top-100)",
+                datasets=dict(train=n_train, eval=n_eval, n_snps=200, n_samples=2000,
+                              data="synthetic HWE, MAF U[0.05,0.5], every other dataset with a planted 5-SNP parity"),
+                training=dict(top_triples=top_triples, epochs=epochs, batch=8192, lr=1e-3, wd=1e-4,
+                              tail_fraction=0.5, losses=[float(x) for x in losses], seconds=t_train),
+                exhaustive_seconds_per_dataset=t_truth / n_eval, results=rows,
+                seconds=time.perf_counter() - t0)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--train", type=int, default=8)
+    ap.add_argument("--epochs", type=int, default=4)
+    ap.add_argument("--top-triples", type=int, default=1024)
+    ap.add_argument("--eval", type=int, default=3)
+    args = ap.parse_args()
+    print(json.dumps(evaluate(n_train=args.train, epochs=args.epochs, top_triples=args.top_triples,
+                              n_eval=args.eval)), flush=True)
+
+
+if __name__ == "__main__":
+    main()
