@@ -228,13 +228,15 @@ epi_status epi_score_all(epi_dataset *ds, int order, float *out_dev);
  * below C(n_snps, order)) into device combs [count][order]. */
 epi_status epi_unrank(epi_dataset *ds, int order, const uint64_t *ranks, int64_t count, uint32_t *combs);
 
-/* The 25 proposer features of `count` 5-sets: ln(MI + 1e-7) of the 5 SNPs,
- * the 10 pairs and the 10 triples of each set, each group sorted descending.
- * s1/s2/s3: device score tables of orders 1, 2, 3 from epi_score_all;
- * combs: device [count][5] strictly increasing SNP indices; X: device
- * [count][25] floats.  Queued on the context's stream. */
-epi_status epi_features5(epi_dataset *ds, const float *s1, const float *s2, const float *s3, const uint32_t *combs,
-                         int64_t count, float *X);
+/* The proposer features of `count` 5-sets: ln(MI + 1e-7) of the 5 SNPs,
+ * the 10 pairs and the 10 triples of each set (25 features), and, when s4 is
+ * given, of its 5 four-SNP subsets (30 features); each group sorted
+ * descending.  s1/s2/s3/s4: device score tables of orders 1..4 from
+ * epi_score_all (s4 may be NULL); combs: device [count][5] strictly
+ * increasing SNP indices; X: device [count][25 or 30] floats.  Queued on the
+ * context's stream. */
+epi_status epi_features5(epi_dataset *ds, const float *s1, const float *s2, const float *s3, const float *s4,
+                         const uint32_t *combs, int64_t count, float *X);
 
 /* Candidate 5-sets made of one of n_triples triples (device [n_triples][3],
  * strictly increasing) and any two other SNPs: candidate index
@@ -260,9 +262,10 @@ epi_status epi_lookup(epi_dataset *ds, int order, const float *table, const uint
 epi_status epi_topk(epi_ctx *ctx, const float *scores, const uint8_t *keep, int64_t count, int k, float *out_scores,
                     uint64_t *out_index, int32_t *n_out);
 
-/* The ranking without a network, for comparison: the sum of the ten
- * three-way features of each row of X (device [count][25]) into device out. */
-epi_status epi_heuristic5(epi_ctx *ctx, const float *X_dev, int64_t count, float *out_dev);
+/* The ranking without a network, for comparison: for rows of n_feat = 25
+ * features (device X [count][25]) the sum of the ten three-way features, for
+ * n_feat = 30 the sum of the five four-way features; into device out. */
+epi_status epi_heuristic5(epi_ctx *ctx, const float *X_dev, int64_t count, int n_feat, float *out_dev);
 
 /* A multilayer perceptron n_in -> hidden -> hidden -> 1 with ReLU, BF16
  * weights and activations, FP32 accumulation and FP32 master weights for the
@@ -303,13 +306,15 @@ epi_status epi_mlp_train_step(epi_mlp *net, const float *X_dev, const float *t_d
                               float wd, float *loss_host);
 
 /* Order-5 proposal search.  The exhaustive order-1..3 scores of the dataset
- * are computed (popcount path) on the first proposer call and kept with the
- * dataset until it is destroyed (4 (n + C(n,2) + C(n,3)) bytes of device
- * memory); the top_triples best triples by order-3 MI
- * (ties by rank) are each joined with every pair of other SNPs; every distinct
- * 5-set of that space (a set holding several of the triples is taken once) is
- * ranked by `net` from its 25 features (epi_features5), or, with net NULL, by
- * the sum of its ten three-way log-scores (epi_heuristic5); the best `budget`
+ * (and order 4 with quad_features) are computed (popcount path) on the first
+ * proposer call that needs them and kept with the dataset until it is
+ * destroyed (4 (n + C(n,2) + C(n,3) [+ C(n,4)]) bytes of device memory;
+ * EPI_ENOMEM if the order-4 table would take more than half of the free
+ * memory); the top_triples best triples by order-3 MI (ties by rank), listed
+ * in rank order, are each joined with every pair of other SNPs; every
+ * distinct 5-set of that space (a set holding several of the triples is taken
+ * once) is ranked by `net` from its 25 or 30 features (epi_features5), or,
+ * with net NULL, by epi_heuristic5 of those features; the best `budget`
  * are counted and scored exactly (Section 2.2 tables, Eq. 1-3 in FP64), and
  * the best top_n by exact MI (ties by lexicographic rank) are written to host
  * out [top_n] (order 5) with their tables in host counts [top_n][2][243]
@@ -317,7 +322,7 @@ epi_status epi_mlp_train_step(epi_mlp *net, const float *X_dev, const float *t_d
  * paper has no counterpart: it searches exhaustively; this call is an
  * approximation whose result is exact only for the sets it proposes. */
 typedef struct epi_proposer_opts {
-    int top_triples;   /* 1..4096 */
+    int top_triples;   /* 1..2^24 (capped at C(n_snps, 3)) */
     int budget;        /* proposals re-scored exactly, 1..2^30: the budget's
                           best distinct candidates by (ranking score desc,
                           candidate index asc), selected by radix select over
@@ -327,6 +332,9 @@ typedef struct epi_proposer_opts {
                           4096 best of those again in FP64 */
     int top_n;         /* 1..min(budget, 4096) */
     int64_t chunk;
+    int quad_features; /* 0: the 25 features of orders 1-3; 1: the 30
+                          features with the four-way scores (a network must
+                          then take 30 inputs) */
 } epi_proposer_opts;
 typedef struct epi_proposer_stats {
     uint64_t candidates;   /* top_triples * C(n_snps - 3, 2) */
@@ -340,7 +348,8 @@ typedef struct epi_proposer_stats {
 epi_status epi_proposer_search(epi_dataset *ds, epi_mlp *net, const epi_proposer_opts *opts, epi_result *out,
                                uint32_t *counts, int32_t *n_out, epi_proposer_stats *stats);
 
-/* Fits `net` (25 inputs) to rank order-5 sets: on each dataset the space of
+/* Fits `net` (25 inputs, or 30 for the features with four-way scores) to
+ * rank order-5 sets: on each dataset the space of
  * epi_proposer_search with the given top_triples is built and every row (a
  * candidate 5-set) is labelled by its exact MI (its table counted, Section
  * 2.2, and scored, Eq. 1-3; see `target`), a set holding several of the
@@ -349,7 +358,7 @@ epi_status epi_proposer_search(epi_dataset *ds, epi_mlp *net, const epi_proposer
  * mini-batch AdamW (cosine decay from lr to lr / 20, weight decay wd) are
  * run; tail_fraction of each batch is drawn from the 4096 best-labelled sets
  * of each dataset, the rest uniformly, from a counter-based generator seeded
- * by `seed`.  The rows stay in device memory (113 bytes each; EPI_ENOMEM if
+ * by `seed`.  The rows stay in device memory (4 n_in + 13 bytes each; EPI_ENOMEM if
  * they do not fit).  Host epoch_loss [epochs] (may be NULL) receives the mean
  * sampled batch loss of each epoch.  The paper has no counterpart. */
 typedef struct epi_train_opts {

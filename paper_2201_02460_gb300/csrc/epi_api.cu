@@ -51,7 +51,7 @@ struct epi_dataset {
     uint32_t *masks = nullptr;
     uint64_t *binom = nullptr;
     unsigned char *b8 = nullptr;   // tensor-core operand, built on first use
-    float *lower[4] = {};          // exhaustive order-1..3 scores for the proposer, built on first use
+    float *lower[5] = {};          // exhaustive order-1..4 scores for the proposer, built on first use
     DevData dev() const
     {
         DevData d;
@@ -923,15 +923,15 @@ epi_status epi_unrank(epi_dataset *ds, int order, const uint64_t *ranks, int64_t
     return EPI_OK;
 }
 
-epi_status epi_features5(epi_dataset *ds, const float *s1, const float *s2, const float *s3, const uint32_t *combs,
-                         int64_t count, float *X)
+epi_status epi_features5(epi_dataset *ds, const float *s1, const float *s2, const float *s3, const float *s4,
+                         const uint32_t *combs, int64_t count, float *X)
 {
     if (!ds || !s1 || !s2 || !s3 || !combs || !X || count < 0) return fail(EPI_EINVAL, "epi_features5: bad argument");
     if (ds->n < 5) return fail(EPI_EINVAL, "epi_features5: needs at least 5 SNPs");
     if (count == 0) return EPI_OK;
     epi_ctx *ctx = ds->ctx;
     DeviceGuard g(ctx->device);
-    CK(launch_features5(ds->dev(), s1, s2, s3, combs, count, X, ctx->stream));
+    CK(launch_features5(ds->dev(), s1, s2, s3, s4, combs, count, X, ctx->stream));
     ctx->launches += 1;
     return EPI_OK;
 }
@@ -987,11 +987,11 @@ void epi_ctx_count_launches(epi_ctx *ctx, int n) { ctx->launches += (uint64_t)n;
 epi_ctx *epi_dataset_ctx(const epi_dataset *ds) { return ds->ctx; }
 epi::DevData epi_dataset_dev(const epi_dataset *ds) { return ds->dev(); }
 
-// The dataset's exhaustive single-precision scores of order k (1..3), computed
+// The dataset's exhaustive single-precision scores of order k (1..4), computed
 // on first use and kept until the dataset is destroyed.
 epi_status epi_dataset_lower_scores(epi_dataset *ds, int k, const float **out)
 {
-    if (k < 1 || k > 3) return fail(EPI_EINVAL, "lower scores: order %d outside 1..3", k);
+    if (k < 1 || k > 4 || k > ds->n) return fail(EPI_EINVAL, "lower scores: order %d outside 1..min(4, n)", k);
     if (!ds->lower[k]) {
         DeviceGuard g(ds->ctx->device);
         float *t = nullptr;

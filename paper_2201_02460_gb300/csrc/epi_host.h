@@ -69,8 +69,8 @@ cudaError_t launch_tc_batch(const void *ds_dev, const int32_t *cta_ds_dev, int k
                             uint64_t *list_rank, int32_t *list_count, int32_t *status, int grid, cudaStream_t st);
 
 // epi_learn.cu (proposer)
-cudaError_t launch_features5(const DevData &d, const float *s1, const float *s2, const float *s3, const uint32_t *combs,
-                             int64_t count, float *X, cudaStream_t st);
+cudaError_t launch_features5(const DevData &d, const float *s1, const float *s2, const float *s3, const float *s4,
+                             const uint32_t *combs, int64_t count, float *X, cudaStream_t st);
 cudaError_t launch_candidates5(const DevData &d, const uint32_t *triples, int64_t first, int64_t count,
                                uint32_t *combs, const float *s3, uint8_t *keep, cudaStream_t st);
 cudaError_t launch_candidates5_at(const DevData &d, const uint32_t *triples, const uint64_t *idx, int64_t count,
@@ -82,8 +82,8 @@ cudaError_t launch_mlp_forward_tc(const float *X, int64_t rows, int n_in, const 
                                   const float *b1, const void *W2, const float *b2, const void *W3, const float *b3,
                                   float *y, int32_t *status, int num_sms, cudaStream_t st);
 cudaError_t launch_cand_features5(const DevData &d, const uint32_t *triples, int64_t first, int64_t count,
-                                  const float *s1, const float *s2, const float *s3, float *X, uint8_t *keep,
-                                  uint32_t *combs, cudaStream_t st);
+                                  const float *s1, const float *s2, const float *s3, const float *s4, float *X,
+                                  uint8_t *keep, uint32_t *combs, cudaStream_t st);
 cudaError_t launch_lookup(const DevData &d, int k, const float *table, const uint32_t *combs, int64_t count,
                           float *out, cudaStream_t st);
 // epi_topk.cu: the k best of count scores (score desc, index asc; keep may

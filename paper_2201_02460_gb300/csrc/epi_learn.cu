@@ -3,17 +3,17 @@
 // An exhaustive order-5 search is out of reach for large SNP counts (C(2000,5)
 // = 2.65e14).  The proposer ranks candidate 5-sets with a small MLP fed by the
 // lower-order scores of the candidate's SNPs (5 per-SNP, 10 pair and 10
-// three-way MI values, each group sorted so the features do not depend on SNP
-// order); the best-ranked candidates are then recounted and scored exactly by
-// the search's own kernels.  The network is trained on exhaustive order-5 scores
-// of smaller instances.  Everything here runs in these kernels:
-//   * features5_kernel: gathers and sorts the 25 lower-order scores;
+// three-way MI values, and optionally the 5 four-way values, each group sorted
+// so the features do not depend on SNP order); the best-ranked candidates are
+// then recounted and scored exactly by the search's own kernels.  The network
+// is trained on exhaustive order-5 scores of smaller instances.  Everything
+// here runs in these kernels:
+//   * features5_kernel: gathers and sorts the 25 (or 30) lower-order scores;
 //   * gemm_kernel: C = A x B with FP32 accumulation over BF16 or FP32
 //     operands in shared-memory tiles (every layer, forward and backward);
 //   * bias/ReLU/convert, MSE-loss, column-sum and AdamW kernels;
-//   * candidates5_kernel: the 5-sets made of a given triple plus any two
-//     other SNPs;
-//   * topk kernels: per-block candidate lists merged into the best k.
+//   * candidates5_kernel / cand_features5_kernel: the 5-sets made of a given
+//     triple plus any two other SNPs, with their features.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -58,11 +58,13 @@ __device__ __forceinline__ void sort_desc(float (&v)[L])
 }
 
 // 25 features of each 5-set: ln(MI + 1e-7) of its SNPs, pairs and triples,
-// each group sorted descending.
+// each group sorted descending; with the order-4 table s4, 30 features (the
+// five four-way subsets' values appended, sorted descending).
 __global__ void features5_kernel(DevData d, const float *__restrict__ s1, const float *__restrict__ s2,
-                                 const float *__restrict__ s3, const uint32_t *__restrict__ combs, int64_t count,
-                                 float *__restrict__ X)
+                                 const float *__restrict__ s3, const float *__restrict__ s4,
+                                 const uint32_t *__restrict__ combs, int64_t count, float *__restrict__ X)
 {
+    const int cols = s4 ? 30 : 25;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
         int32_t c[5];
 #pragma unroll
@@ -91,13 +93,28 @@ __global__ void features5_kernel(DevData d, const float *__restrict__ s1, const 
         sort_desc(f1);
         sort_desc(f2);
         sort_desc(f3);
-        float *x = X + i * 25;
+        float *x = X + i * cols;
 #pragma unroll
         for (int t = 0; t < 5; t++) x[t] = feat_log(f1[t]);
 #pragma unroll
         for (int t = 0; t < 10; t++) x[5 + t] = feat_log(f2[t]);
 #pragma unroll
         for (int t = 0; t < 10; t++) x[15 + t] = feat_log(f3[t]);
+        if (s4) {
+            float f4[5];
+#pragma unroll
+            for (int j = 0; j < 5; j++) {
+                int32_t p[4];
+                int m = 0;
+#pragma unroll
+                for (int t = 0; t < 5; t++)
+                    if (t != j) p[m++] = c[t];
+                f4[j] = s4[lex_rank(d.binom, d.n, 4, p)];
+            }
+            sort_desc(f4);
+#pragma unroll
+            for (int t = 0; t < 5; t++) x[25 + t] = feat_log(f4[t]);
+        }
     }
 }
 
@@ -194,18 +211,20 @@ __global__ void candidates5_at_kernel(DevData d, const uint32_t *__restrict__ tr
 }
 
 // Candidates [first, first + count) in one pass: the set, whether its
-// generating triple is its best (keep) and its 25 features; the set itself is
-// written only when combs is given.
+// generating triple is its best (keep) and its 25 features (30 with the
+// order-4 table s4); the set itself is written only when combs is given.
 __global__ void __launch_bounds__(256) cand_features5_kernel(DevData d, const uint32_t *__restrict__ triples,
                                                              int64_t first, int64_t count, const float *__restrict__ s1,
                                                              const float *__restrict__ s2, const float *__restrict__ s3,
-                                                             float *__restrict__ X, uint8_t *__restrict__ keep,
-                                                             uint32_t *__restrict__ combs)
+                                                             const float *__restrict__ s4, float *__restrict__ X,
+                                                             uint8_t *__restrict__ keep, uint32_t *__restrict__ combs)
 {
     const int64_t n = d.n;
-    // binomials C(x, 2), C(x, 3) from the dataset's table (L1-resident rows)
+    const int cols = s4 ? 30 : 25;
+    // binomials C(x, 2), C(x, 3), C(x, 4) from the dataset's table (L1-resident rows)
     const uint64_t *__restrict__ b2 = d.binom + 2 * (n + 1);
     const uint64_t *__restrict__ b3 = d.binom + 3 * (n + 1);
+    const uint64_t *__restrict__ b4 = d.binom + 4 * (n + 1);
     const uint64_t n2 = b2[n], n3 = b3[n];
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
         int32_t v[5], g3[3];
@@ -247,13 +266,32 @@ __global__ void __launch_bounds__(256) cand_features5_kernel(DevData d, const ui
         sort_desc(f1);
         sort_desc(f2);
         sort_desc(f3);
-        float *x = X + i * 25;
+        float *x = X + i * cols;
 #pragma unroll
         for (int t = 0; t < 5; t++) x[t] = feat_log(f1[t]);
 #pragma unroll
         for (int t = 0; t < 10; t++) x[5 + t] = feat_log(f2[t]);
 #pragma unroll
         for (int t = 0; t < 10; t++) x[15 + t] = feat_log(f3[t]);
+        if (s4) {
+            // the five four-way subsets (v sorted ascending): drop v[j]
+            const uint64_t n4 = b4[n];
+            float f4[5];
+#pragma unroll
+            for (int j = 0; j < 5; j++) {
+                int32_t p[4];
+                int m = 0;
+#pragma unroll
+                for (int t = 0; t < 5; t++)
+                    if (t != j) p[m++] = v[t];
+                const uint64_t r4 = n4 - 1 - (b4[n - 1 - p[0]] + b3[n - 1 - p[1]] + b2[n - 1 - p[2]] +
+                                              (uint64_t)(n - 1 - p[3]));
+                f4[j] = s4[r4];
+            }
+            sort_desc(f4);
+#pragma unroll
+            for (int t = 0; t < 5; t++) x[25 + t] = feat_log(f4[t]);
+        }
     }
 }
 
@@ -399,13 +437,14 @@ __global__ void adamw_kernel(float *__restrict__ w, const float *__restrict__ g,
     }
 }
 
-// The ranking without the network: the sum of the ten three-way log-scores.
-__global__ void heuristic5_kernel(const float *__restrict__ X, int64_t count, float *__restrict__ out)
+// The ranking without the network: the sum of the ten three-way log-scores
+// of 25-column rows, or of the five four-way log-scores of 30-column rows.
+__global__ void heuristic5_kernel(const float *__restrict__ X, int64_t count, int cols, float *__restrict__ out)
 {
+    const int lo = cols == 30 ? 25 : 15;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
         float s = 0.0f;
-#pragma unroll
-        for (int t = 15; t < 25; t++) s += X[i * 25 + t];
+        for (int t = lo; t < cols; t++) s += X[i * cols + t];
         out[i] = s;
     }
 }
@@ -737,12 +776,13 @@ epi_status epi_mlp_train_step(epi_mlp *net, const float *X_dev, const float *t_d
     return EPI_OK;
 }
 
-epi_status epi_heuristic5(epi_ctx *ctx, const float *X_dev, int64_t count, float *out_dev)
+epi_status epi_heuristic5(epi_ctx *ctx, const float *X_dev, int64_t count, int n_feat, float *out_dev)
 {
     if (!ctx || !X_dev || !out_dev || count < 0) return lfail(EPI_EINVAL, "epi_heuristic5: bad argument");
+    if (n_feat != 25 && n_feat != 30) return lfail(EPI_EINVAL, "epi_heuristic5: n_feat must be 25 or 30");
     if (count == 0) return EPI_OK;
     cudaSetDevice(epi_ctx_device(ctx));
-    learn::heuristic5_kernel<<<blocks_for(count), 256, 0, epi_ctx_stream(ctx)>>>(X_dev, count, out_dev);
+    learn::heuristic5_kernel<<<blocks_for(count), 256, 0, epi_ctx_stream(ctx)>>>(X_dev, count, n_feat, out_dev);
     LCK(cudaGetLastError());
     return EPI_OK;
 }
@@ -752,10 +792,10 @@ epi_status epi_heuristic5(epi_ctx *ctx, const float *X_dev, int64_t count, float
 // dataset-side kernels of the proposer
 namespace epi {
 
-cudaError_t launch_features5(const DevData &d, const float *s1, const float *s2, const float *s3, const uint32_t *combs,
-                             int64_t count, float *X, cudaStream_t st)
+cudaError_t launch_features5(const DevData &d, const float *s1, const float *s2, const float *s3, const float *s4,
+                             const uint32_t *combs, int64_t count, float *X, cudaStream_t st)
 {
-    learn::features5_kernel<<<blocks_for(count), 256, 0, st>>>(d, s1, s2, s3, combs, count, X);
+    learn::features5_kernel<<<blocks_for(count), 256, 0, st>>>(d, s1, s2, s3, s4, combs, count, X);
     return cudaGetLastError();
 }
 
@@ -774,11 +814,11 @@ cudaError_t launch_candidates5_at(const DevData &d, const uint32_t *triples, con
 }
 
 cudaError_t launch_cand_features5(const DevData &d, const uint32_t *triples, int64_t first, int64_t count,
-                                  const float *s1, const float *s2, const float *s3, float *X, uint8_t *keep,
-                                  uint32_t *combs, cudaStream_t st)
+                                  const float *s1, const float *s2, const float *s3, const float *s4, float *X,
+                                  uint8_t *keep, uint32_t *combs, cudaStream_t st)
 {
-    learn::cand_features5_kernel<<<blocks_for(count), 256, 0, st>>>(d, triples, first, count, s1, s2, s3, X, keep,
-                                                                    combs);
+    learn::cand_features5_kernel<<<blocks_for(count), 256, 0, st>>>(d, triples, first, count, s1, s2, s3, s4, X,
+                                                                    keep, combs);
     return cudaGetLastError();
 }
 

@@ -1,8 +1,8 @@
 // Learned order-5 proposer: the pipelines around the network.
 //
-// Search: the exhaustive order-1..3 scores (the popcount path) give the
-// features; the best T triples by exact order-3 score are expanded by every
-// pair of other SNPs; each distinct expansion is ranked by the network (or by
+// Search: the exhaustive order-1..3 scores (the popcount path; with the
+// 30-feature set also order 4) give the features; the best T triples by
+// order-3 score are expanded by every pair of other SNPs; each distinct expansion is ranked by the network (or by
 // the network-free heuristic), the best R are recounted and scored exactly
 // (tables and FP64 MI of Eq. 1-3), and the best top_n of those are returned.
 //
@@ -146,6 +146,8 @@ epi_status pfail(epi_status s, const char *msg)
     return s;
 }
 
+constexpr int kMaxTriples = 1 << 24;
+
 #define PCK(call)                                                                             \
     do {                                                                                      \
         cudaError_t e_ = (call);                                                              \
@@ -164,37 +166,141 @@ double now_ms()
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
-// Exhaustive single-precision scores of orders 1, 2, 3 (kept with the
-// dataset).
+// Exhaustive single-precision scores of orders 1, 2, 3 and, for the
+// 30-feature set, 4 (kept with the dataset).
 struct Lower {
-    const float *s[4] = {};
+    const float *s[5] = {};
 };
 
-epi_status lower_tables(epi_dataset *ds, Lower &L)
+epi_status lower_tables(epi_dataset *ds, Lower &L, bool quad)
 {
     for (int k : {1, 2, 3}) PST(epi_dataset_lower_scores(ds, k, &L.s[k]));
+    if (quad) {
+        const DevData d = epi_dataset_dev(ds);
+        size_t free_b = 0, total_b = 0;
+        PCK(cudaMemGetInfo(&free_b, &total_b));
+        if ((double)host_binom(d.n, 4) * 4.0 > 0.5 * (double)free_b)
+            return pfail(EPI_ENOMEM, "proposer: the exhaustive order-4 table of the 30-feature set does not fit in "
+                                     "device memory (use the 25-feature set)");
+        PST(epi_dataset_lower_scores(ds, 4, &L.s[4]));
+    }
     return EPI_OK;
 }
 
-// The best T triples by order-3 score (score desc, rank asc) as [T][3].
+// ordered compaction of the marked positions of flags[0, count): per-block
+// counts, an exclusive scan, then each block writes its marked positions in
+// index order
+constexpr int kCompactBlocks = 1024;
+
+__device__ __forceinline__ void compact_range(uint64_t count, uint64_t &b, uint64_t &e)
+{
+    const uint64_t per = (count + kCompactBlocks - 1) / kCompactBlocks;
+    b = (uint64_t)blockIdx.x * per;
+    e = b + per < count ? b + per : count;
+    if (b > count) b = count;
+}
+
+__global__ void __launch_bounds__(256) flag_count_kernel(const uint8_t *__restrict__ flags, uint64_t count,
+                                                         unsigned long long *__restrict__ cnt)
+{
+    __shared__ unsigned long long c;
+    if (threadIdx.x == 0) c = 0;
+    __syncthreads();
+    uint64_t b, e;
+    compact_range(count, b, e);
+    unsigned long long mine = 0;
+    for (uint64_t i = b + threadIdx.x; i < e; i += blockDim.x) mine += flags[i];
+    atomicAdd(&c, mine);
+    __syncthreads();
+    if (threadIdx.x == 0) cnt[blockIdx.x] = c;
+}
+
+__global__ void __launch_bounds__(kCompactBlocks) flag_scan_kernel(unsigned long long *__restrict__ cnt)
+{
+    __shared__ unsigned long long s[kCompactBlocks];
+    const int t = threadIdx.x;
+    const unsigned long long own = cnt[t];
+    s[t] = own;
+    __syncthreads();
+    for (int o = 1; o < kCompactBlocks; o <<= 1) {
+        const unsigned long long add = t >= o ? s[t - o] : 0ull;
+        __syncthreads();
+        s[t] += add;
+        __syncthreads();
+    }
+    cnt[t] = s[t] - own;   // exclusive
+}
+
+__global__ void __launch_bounds__(256) flag_write_kernel(const uint8_t *__restrict__ flags, uint64_t count,
+                                                         const unsigned long long *__restrict__ off,
+                                                         uint64_t *__restrict__ out)
+{
+    __shared__ uint32_t wsum[8];
+    uint64_t b, e;
+    compact_range(count, b, e);
+    uint64_t base = off[blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint64_t i0 = b; i0 < e; i0 += blockDim.x) {
+        const uint64_t i = i0 + threadIdx.x;
+        const bool f = i < e && flags[i] != 0;
+        const uint32_t m = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) wsum[warp] = __popc(m);
+        __syncthreads();
+        uint64_t before = base;
+        for (int w = 0; w < warp; w++) before += wsum[w];
+        before += __popc(m & ((1u << lane) - 1u));
+        if (f) out[before] = i;
+        uint32_t total = 0;
+        for (int w = 0; w < 8; w++) total += wsum[w];
+        __syncthreads();
+        base += total;
+    }
+}
+
+__global__ void flag_set_kernel(uint8_t *__restrict__ flags, const uint64_t *__restrict__ idx, int64_t count)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        flags[idx[i]] = 1;
+}
+
+// The best T triples by (order-3 score desc, rank asc), listed as [T][3] in
+// rank order: radix select of the T best, then their ranks marked and
+// compacted in index order (deterministic for any T).
 epi_status best_triples(epi_dataset *ds, Pool &pool, const float *s3, int T, uint32_t **triples, int *T_out)
 {
     epi_ctx *ctx = epi_dataset_ctx(ds);
+    cudaStream_t st = epi_ctx_stream(ctx);
     const DevData d = epi_dataset_dev(ds);
     const int64_t total3 = (int64_t)host_binom(d.n, 3);
     T = (int)std::min<int64_t>(T, total3);
-    float *vs;
-    uint64_t *rk;
+    uint64_t *sel, *rk;
     int32_t *nn;
-    PCK(pool.get(&vs, T));
+    uint8_t *flags;
+    unsigned long long *cnt;
+    unsigned char *scratch;
+    PCK(pool.get(&sel, T));
     PCK(pool.get(&rk, T));
     PCK(pool.get(&nn, 1));
-    PST(epi_topk(ctx, s3, nullptr, total3, T, vs, rk, nn));
-    PCK(pool.get(triples, (size_t)T * 3));
-    PCK(launch_unrank(d, 3, rk, T, *triples, epi_ctx_stream(ctx)));
-    epi_ctx_count_launches(ctx, 1);
+    PCK(pool.get(&flags, total3));
+    PCK(pool.get(&cnt, kCompactBlocks));
+    PCK(pool.get(&scratch, topk_scratch_bytes(T)));
+    PCK(launch_topk(s3, nullptr, total3, T, scratch, false, nullptr, sel, nn, epi_ctx_num_sms(ctx), st));
+    PCK(cudaMemsetAsync(flags, 0, (size_t)total3, st));
+    flag_set_kernel<<<grid_for(T), 256, 0, st>>>(flags, sel, T);
+    flag_count_kernel<<<kCompactBlocks, 256, 0, st>>>(flags, (uint64_t)total3, cnt);
+    flag_scan_kernel<<<1, kCompactBlocks, 0, st>>>(cnt);
+    flag_write_kernel<<<kCompactBlocks, 256, 0, st>>>(flags, (uint64_t)total3, cnt, rk);
+    PCK(cudaGetLastError());
+    int32_t got = 0;
+    PCK(cudaMemcpyAsync(&got, nn, 4, cudaMemcpyDeviceToHost, st));
+    PCK(cudaStreamSynchronize(st));
+    T = std::min(T, std::max(got, 0));   // fewer only if scores are NaN
+    PCK(pool.get(triples, (size_t)std::max(T, 1) * 3));
+    if (T > 0) PCK(launch_unrank(d, 3, rk, T, *triples, st));
+    epi_ctx_count_launches(ctx, 12 + 5);
+    pool.release(flags);
     *T_out = T;
-    return EPI_OK;
+    return T > 0 ? EPI_OK : pfail(EPI_EINVAL, "proposer: no finite order-3 scores");
 }
 
 // Ranking and proposal selection: every ranked score stays in device memory
@@ -202,15 +308,16 @@ epi_status best_triples(epi_dataset *ds, Pool &pool, const float *s3, int T, uin
 // score desc, candidate index asc) are selected by radix select, every
 // proposal is counted and scored exactly in FP32 in slices, and the 4096 best
 // by exact FP32 score form the pool that the caller re-scores in FP64.
-epi_status rank_and_select(epi_dataset *ds, epi_mlp *net, const DevData &d, const Lower &L, const uint32_t *triples,
-                           uint64_t total, uint64_t R, int64_t chunk, Pool &pool, uint64_t **pool_idx, int32_t *n_pool,
-                           unsigned long long *kept_out, uint64_t *selected_out, float *pool_floor, int &launches)
+epi_status rank_and_select(epi_dataset *ds, epi_mlp *net, const DevData &d, const Lower &L, int n_feat,
+                           const uint32_t *triples, uint64_t total, uint64_t R, int64_t chunk, Pool &pool,
+                           uint64_t **pool_idx, int32_t *n_pool, unsigned long long *kept_out, uint64_t *selected_out,
+                           float *pool_floor, int &launches)
 {
     epi_ctx *ctx = epi_dataset_ctx(ds);
     cudaStream_t st = epi_ctx_stream(ctx);
     size_t free_b = 0, total_b = 0;
     PCK(cudaMemGetInfo(&free_b, &total_b));
-    const size_t need = (size_t)total * 5 + (size_t)chunk * 100 + (size_t)R * 12 + ((size_t)1 << 30);
+    const size_t need = (size_t)total * 5 + (size_t)chunk * n_feat * 4 + (size_t)R * 12 + ((size_t)1 << 30);
     if (need > free_b) return pfail(EPI_ENOMEM, "epi_proposer_search: the candidate space's scores do not fit in device memory");
     float *score, *X;
     uint8_t *keep;
@@ -220,7 +327,7 @@ epi_status rank_and_select(epi_dataset *ds, epi_mlp *net, const DevData &d, cons
     void *scratch;
     PCK(pool.get(&score, total));
     PCK(pool.get(&keep, total));
-    PCK(pool.get(&X, (size_t)chunk * 25));
+    PCK(pool.get(&X, (size_t)chunk * n_feat));
     PCK(pool.get(&kept_dev, 1));
     PCK(pool.get(&nsel, 1));
     PCK(pool.get(&sel, R));
@@ -228,10 +335,10 @@ epi_status rank_and_select(epi_dataset *ds, epi_mlp *net, const DevData &d, cons
     PCK(cudaMemsetAsync(kept_dev, 0, 8, st));
     for (uint64_t first = 0; first < total; first += (uint64_t)chunk) {
         const int64_t cnt = (int64_t)std::min<uint64_t>((uint64_t)chunk, total - first);
-        PCK(launch_cand_features5(d, triples, (int64_t)first, cnt, L.s[1], L.s[2], L.s[3], X, keep + first, nullptr,
-                                  st));
+        PCK(launch_cand_features5(d, triples, (int64_t)first, cnt, L.s[1], L.s[2], L.s[3], L.s[4], X, keep + first,
+                                  nullptr, st));
         if (net) PST(epi_mlp_forward(net, X, cnt, score + first));
-        else PST(epi_heuristic5(ctx, X, cnt, score + first));
+        else PST(epi_heuristic5(ctx, X, cnt, n_feat, score + first));
         count_kernel<<<grid_for(cnt), 256, 0, st>>>(keep + first, cnt, kept_dev);
         launches += 3;
     }
@@ -295,11 +402,14 @@ epi_status epi_proposer_search(epi_dataset *ds, epi_mlp *net, const epi_proposer
                                uint32_t *counts, int32_t *n_out, epi_proposer_stats *stats)
 {
     if (!ds || !opts || !out || !n_out) return pfail(EPI_EINVAL, "epi_proposer_search: NULL argument");
-    if (net && epi_mlp_num_inputs(net) != 25)
-        return pfail(EPI_EINVAL, "epi_proposer_search: the network must take the 25 proposer features");
+    const bool quad = opts->quad_features != 0;
+    const int n_feat = quad ? 30 : 25;
+    if (net && epi_mlp_num_inputs(net) != n_feat)
+        return pfail(EPI_EINVAL, quad ? "epi_proposer_search: the network must take the 30 proposer features"
+                                      : "epi_proposer_search: the network must take the 25 proposer features");
     const int R = opts->budget, top_n = opts->top_n;
-    if (opts->top_triples < 1 || opts->top_triples > 4096)
-        return pfail(EPI_EINVAL, "epi_proposer_search: top_triples outside 1..4096");
+    if (opts->top_triples < 1 || opts->top_triples > kMaxTriples)
+        return pfail(EPI_EINVAL, "epi_proposer_search: top_triples outside 1..2^24");
     if (R < 1 || R > (1 << 30)) return pfail(EPI_EINVAL, "epi_proposer_search: budget outside 1..2^30");
     if (top_n < 1 || top_n > std::min(R, 4096)) return pfail(EPI_EINVAL, "epi_proposer_search: top_n outside 1..min(budget, 4096)");
     const DevData d = epi_dataset_dev(ds);
@@ -313,7 +423,7 @@ epi_status epi_proposer_search(epi_dataset *ds, epi_mlp *net, const epi_proposer
 
     // exhaustive lower orders and the expanded triples
     Lower L;
-    PST(lower_tables(ds, L));
+    PST(lower_tables(ds, L, quad));
     uint32_t *triples;
     int T = 0;
     PST(best_triples(ds, pool, L.s[3], opts->top_triples, &triples, &T));
@@ -330,8 +440,8 @@ epi_status epi_proposer_search(epi_dataset *ds, epi_mlp *net, const epi_proposer
     uint64_t *lr = nullptr;
     uint64_t selected = 0;
     float pool_floor = -INFINITY;     // exact FP32 score of the weakest pooled proposal
-    PST(rank_and_select(ds, net, d, L, triples, total, (uint64_t)R, chunk, pool, &lr, &n_prop, &kept, &selected,
-                        &pool_floor, launches));
+    PST(rank_and_select(ds, net, d, L, n_feat, triples, total, (uint64_t)R, chunk, pool, &lr, &n_prop, &kept,
+                        &selected, &pool_floor, launches));
     const double t2 = now_ms();
 
     // exact re-score of the proposals
@@ -412,12 +522,14 @@ epi_status epi_proposer_train(epi_mlp *net, epi_dataset *const *datasets, int n_
                               float *epoch_loss)
 {
     if (!net || !datasets || n_ds < 1 || !o) return pfail(EPI_EINVAL, "epi_proposer_train: bad argument");
-    if (o->top_triples < 1 || o->top_triples > 4096 || o->epochs < 1 || o->batch < 1 || o->batch > (1 << 20) ||
+    if (o->top_triples < 1 || o->top_triples > kMaxTriples || o->epochs < 1 || o->batch < 1 || o->batch > (1 << 20) ||
         !(o->tail_fraction >= 0.0f && o->tail_fraction <= 1.0f) || !(o->lr > 0.0f) || o->target < 0 ||
         o->target > 1)
         return pfail(EPI_EINVAL, "epi_proposer_train: options out of range");
     const int64_t n_in = epi_mlp_num_inputs(net);
-    if (n_in != 25) return pfail(EPI_EINVAL, "epi_proposer_train: the network must take the 25 proposer features");
+    if (n_in != 25 && n_in != 30)
+        return pfail(EPI_EINVAL, "epi_proposer_train: the network must take the 25 or 30 proposer features");
+    const bool quad = n_in == 30;
     epi_ctx *ctx = epi_dataset_ctx(datasets[0]);
     cudaStream_t st = epi_ctx_stream(ctx);
     PCK(cudaSetDevice(epi_ctx_device(ctx)));
@@ -459,7 +571,7 @@ epi_status epi_proposer_train(epi_mlp *net, epi_dataset *const *datasets, int n_
         const DevData d = epi_dataset_dev(ds);
         Pool lp(st);
         Lower L;
-        PST(lower_tables(ds, L));
+        PST(lower_tables(ds, L, quad));
         uint32_t *triples;
         int T = 0;
         PST(best_triples(ds, lp, L.s[3], Ts[i], &triples, &T));
@@ -472,7 +584,8 @@ epi_status epi_proposer_train(epi_mlp *net, epi_dataset *const *datasets, int n_
         for (int64_t f = 0; f < cnt; f += kSlice) {
             const int64_t c = std::min<int64_t>(cnt - f, kSlice);
             const int64_t at = base[i] + f;
-            PCK(launch_cand_features5(d, triples, f, c, L.s[1], L.s[2], L.s[3], X + at * n_in, keep + at, combs, st));
+            PCK(launch_cand_features5(d, triples, f, c, L.s[1], L.s[2], L.s[3], L.s[4], X + at * n_in, keep + at, combs,
+                                      st));
             PCK(launch_tables(d, 5, combs, c, tabs, epi_ctx_num_sms(ctx), st));
             PCK(launch_score_tables(d, 5, tabs, c, t + at, nullptr, epi_ctx_num_sms(ctx), st));
             log_label_kernel<<<grid_for(c), 256, 0, st>>>(t + at, c);

@@ -65,7 +65,8 @@ def exported_names() -> list[str]:
 
 
 class ProposerOpts(C.Structure):
-    _fields_ = [("top_triples", C.c_int), ("budget", C.c_int), ("top_n", C.c_int), ("chunk", C.c_int64)]
+    _fields_ = [("top_triples", C.c_int), ("budget", C.c_int), ("top_n", C.c_int), ("chunk", C.c_int64),
+                ("quad_features", C.c_int)]
 
 
 class ProposerStats(C.Structure):
@@ -120,7 +121,7 @@ def load(path: str | None = None):
         lib.epi_unrank.restype = i32
         lib.epi_unrank.argtypes = [V, i32, P, i64, P]
         lib.epi_features5.restype = i32
-        lib.epi_features5.argtypes = [V, P, P, P, P, i64, P]
+        lib.epi_features5.argtypes = [V, P, P, P, P, P, i64, P]
         lib.epi_candidates5.restype = i32
         lib.epi_candidates5.argtypes = [V, P, i64, i64, i64, P, P, P]
         lib.epi_lookup.restype = i32
@@ -128,7 +129,7 @@ def load(path: str | None = None):
         lib.epi_topk.restype = i32
         lib.epi_topk.argtypes = [V, P, P, i64, i32, P, P, P]
         lib.epi_heuristic5.restype = i32
-        lib.epi_heuristic5.argtypes = [V, P, i64, P]
+        lib.epi_heuristic5.argtypes = [V, P, i64, C.c_int, P]
         lib.epi_mlp_create.restype = i32
         lib.epi_mlp_create.argtypes = [V, i32, i32, u64, C.POINTER(V)]
         lib.epi_mlp_destroy.restype = None
@@ -439,12 +440,14 @@ def unrank(ds: Dataset, order: int, ranks):
     return out
 
 
-def features5(ds: Dataset, s1, s2, s3, combs):
-    """25 features of device 5-sets combs (int32 [count, 5])."""
+def features5(ds: Dataset, s1, s2, s3, combs, s4=None):
+    """25 features of device 5-sets combs (int32 [count, 5]); 30 with the
+    order-4 table s4."""
     import torch
     combs = combs.contiguous()
-    X = torch.empty((combs.shape[0], 25), dtype=torch.float32, device=combs.device)
-    _check(load().epi_features5(ds.handle, _dptr(s1), _dptr(s2), _dptr(s3), _dptr(combs), combs.shape[0], _dptr(X)))
+    X = torch.empty((combs.shape[0], 25 if s4 is None else 30), dtype=torch.float32, device=combs.device)
+    _check(load().epi_features5(ds.handle, _dptr(s1), _dptr(s2), _dptr(s3), None if s4 is None else _dptr(s4),
+                                _dptr(combs), combs.shape[0], _dptr(X)))
     return X
 
 
@@ -486,11 +489,11 @@ def topk(ctx: Context, scores, k: int, keep=None):
 
 def heuristic5(ctx: Context, X):
     """Network-free ranking score of feature rows (sum of the three-way
-    log-scores)."""
+    log-scores of 25-column rows, of the four-way ones of 30-column rows)."""
     import torch
     X = X.contiguous()
     out = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
-    _check(load().epi_heuristic5(ctx.handle, _dptr(X), X.shape[0], _dptr(out)))
+    _check(load().epi_heuristic5(ctx.handle, _dptr(X), X.shape[0], X.shape[1], _dptr(out)))
     return out
 
 
@@ -586,13 +589,17 @@ class MLP:
 
 
 def proposer_search(ds: Dataset, net: "MLP | None", top_triples: int, budget: int, top_n: int,
-                    chunk: int = 0, with_counts: bool = False) -> tuple[SearchResult, dict]:
+                    chunk: int = 0, with_counts: bool = False,
+                    quad_features: bool | None = None) -> tuple[SearchResult, dict]:
     """Order-5 proposals ranked by `net` (None: the network-free heuristic),
-    re-scored exactly (see epi_proposer_search)."""
+    re-scored exactly (see epi_proposer_search).  quad_features (default: the
+    network takes 30 inputs) selects the 30 features with four-way scores."""
+    if quad_features is None:
+        quad_features = net is not None and net.n_in == 30
     out = np.zeros(top_n, dtype=RESULT_DTYPE)
     counts = np.zeros((top_n, 2, 243), dtype=np.uint32) if with_counts else None
     n_out = C.c_int(0)
-    opts = ProposerOpts(top_triples, budget, top_n, chunk)
+    opts = ProposerOpts(top_triples, budget, top_n, chunk, 1 if quad_features else 0)
     stats = ProposerStats()
     _check(load().epi_proposer_search(ds.handle, None if net is None else net._h, C.byref(opts), _np_ptr(out),
                                       _np_ptr(counts) if with_counts else None, C.byref(n_out), C.byref(stats)))

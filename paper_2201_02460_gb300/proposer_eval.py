@@ -1,14 +1,16 @@
 """Training and recall evaluation of the learned order-5 proposer.
 
-Trains the 25-256-256-1 network (epi_proposer_train) on synthetic
-200-SNP x 2000-sample datasets shaped like the training configuration
-(Hardy-Weinberg genotypes, MAF ~ U[0.05, 0.5], balanced classes, every other
-dataset with a planted 5-SNP parity), then measures on held-out datasets of
-the same shape the recall of the exhaustive order-5 top-100 (the tensor-core
-search) among the proposer's top-100, for the network and for the
-network-free heuristic, at several re-score budgets.
+Trains the proposer networks (epi_proposer_train) on synthetic 200-SNP x
+2000-sample datasets shaped like the training configuration (Hardy-Weinberg
+genotypes, MAF ~ U[0.05, 0.5], balanced classes, every other dataset with a
+planted 5-SNP parity): the 25-256-256-1 network on the order-1..3 features
+and the 30-256-256-1 network that also sees the five four-way scores.  Then
+measures on held-out datasets of the same shape the recall of the exhaustive
+order-5 top-100 (the tensor-core search) among the proposer's top-100, for
+each network and for the network-free heuristic of the same features, by
+expanded triples T and re-score budget R.
 
-    python -m paper_2201_02460_gb300.proposer_eval [--train 8] [--epochs 4] [--top-triples 1024]
+    python -m paper_2201_02460_gb300.proposer_eval [--train 8] [--epochs 4] [--epochs30 2]
 
 prints one JSON line.  Every step runs in the library's kernels.
 """
@@ -27,8 +29,8 @@ def make(ctx, seed: int, plant: bool, n_snps: int = 200, n_samples: int = 2000):
     return epi.Dataset(ctx, d.geno, d.pheno)
 
 
-def evaluate(ctx=None, n_train: int = 8, epochs: int = 4, top_triples: int = 1024, n_eval: int = 3,
-             budgets=(4096, 10 ** 6, 10 ** 7), eval_triples=(1024, 4096), seed: int = 7) -> dict:
+def evaluate(ctx=None, n_train: int = 8, epochs: int = 4, epochs30: int = 2, train_triples: int = 1024,
+             n_eval: int = 3, budgets=(10 ** 6, 10 ** 7), eval_triples=(4096, 65536), seed: int = 7) -> dict:
     ctx = ctx or epi.Context(0)
     t0 = time.perf_counter()
     train = [make(ctx, synth.BASE_SEED + 200 + i, i % 2 == 0) for i in range(n_train)]
@@ -39,30 +41,36 @@ def evaluate(ctx=None, n_train: int = 8, epochs: int = 4, top_triples: int = 102
         r = epi.search(ds, 5, 100, path="tc")
         truth.append({tuple(int(x) for x in c) for c in r.combs})
     t_truth = time.perf_counter() - t_truth
-    net = epi.MLP(ctx, 25, 256, seed=1)
-    t_train = time.perf_counter()
-    losses = epi.proposer_train(net, train, top_triples, epochs, 8192, 1e-3, 1e-4, 0.5, seed)
-    t_train = time.perf_counter() - t_train
+    nets, training = {}, {}
+    for n_in, ep in ((25, epochs), (30, epochs30)):
+        net = epi.MLP(ctx, n_in, 256, seed=1)
+        t1 = time.perf_counter()
+        losses = epi.proposer_train(net, train, train_triples, ep, 8192, 1e-3, 1e-4, 0.5, seed)
+        training[n_in] = dict(epochs=ep, losses=[float(x) for x in losses], seconds=time.perf_counter() - t1)
+        nets[n_in] = net
     rows = []
-    for T in eval_triples:
-        for R in budgets:
-            for name, scorer in (("heuristic", None), ("network", net)):
-                rec, secs = [], []
-                for ds, tr in zip(evals, truth):
-                    t1 = time.perf_counter()
-                    r, st = epi.proposer_search(ds, scorer, T, R, 100)
-                    secs.append(time.perf_counter() - t1)
-                    rec.append(len({tuple(int(x) for x in c) for c in r.combs} & tr) / 100.0)
-                rows.append(dict(ranking=name, top_triples=T, budget=R, recall_at_100=rec,
-                                 mean_recall=sum(rec) / len(rec), seconds_per_search=sum(secs) / len(secs)))
-    net.close()
+    for n_in, net in nets.items():
+        for T in eval_triples:
+            for R in budgets:
+                for name, scorer in (("heuristic", None), ("network", net)):
+                    rec, secs = [], []
+                    for ds, tr in zip(evals, truth):
+                        t1 = time.perf_counter()
+                        r, st = epi.proposer_search(ds, scorer, T, R, 100, quad_features=n_in == 30)
+                        secs.append(time.perf_counter() - t1)
+                        rec.append(len({tuple(int(x) for x in c) for c in r.combs} & tr) / 100.0)
+                    rows.append(dict(features=n_in, ranking=name, top_triples=T, budget=R, recall_at_100=rec,
+                                     mean_recall=sum(rec) / len(rec),
+                                     seconds_per_search=sum(secs[1:]) / max(len(secs) - 1, 1)))
+    for net in nets.values():
+        net.close()
     for ds in train + evals:
         ds.close()
     return dict(metric="top-N recall at k=5 (recall@100 of the exhaustive order-5 top-100)",
                 datasets=dict(train=n_train, eval=n_eval, n_snps=200, n_samples=2000,
                               data="synthetic HWE, MAF U[0.05,0.5], every other dataset with a planted 5-SNP parity"),
-                training=dict(top_triples=top_triples, epochs=epochs, batch=8192, lr=1e-3, wd=1e-4,
-                              tail_fraction=0.5, losses=[float(x) for x in losses], seconds=t_train),
+                training=dict(top_triples=train_triples, batch=8192, lr=1e-3, wd=1e-4, tail_fraction=0.5,
+                              by_features={str(k): v for k, v in training.items()}),
                 exhaustive_seconds_per_dataset=t_truth / n_eval, results=rows,
                 seconds=time.perf_counter() - t0)
 
@@ -70,12 +78,13 @@ def evaluate(ctx=None, n_train: int = 8, epochs: int = 4, top_triples: int = 102
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--train", type=int, default=8)
-    ap.add_argument("--epochs", type=int, default=4)
-    ap.add_argument("--top-triples", type=int, default=1024)
+    ap.add_argument("--epochs", type=int, default=4, help="epochs of the 25-feature network")
+    ap.add_argument("--epochs30", type=int, default=2, help="epochs of the 30-feature network")
+    ap.add_argument("--train-triples", type=int, default=1024)
     ap.add_argument("--eval", type=int, default=3)
     args = ap.parse_args()
-    print(json.dumps(evaluate(n_train=args.train, epochs=args.epochs, top_triples=args.top_triples,
-                              n_eval=args.eval)), flush=True)
+    print(json.dumps(evaluate(n_train=args.train, epochs=args.epochs, epochs30=args.epochs30,
+                              train_triples=args.train_triples, n_eval=args.eval)), flush=True)
 
 
 if __name__ == "__main__":

@@ -86,31 +86,34 @@ def test_unrank_matches_oracle(epi, ctx):
         assert (got == want).all()
 
 
-def _features_cpu(mi_by_order, n, comb):
+def _features_cpu(mi_by_order, n, comb, orders=(1, 2, 3)):
     f = []
-    for k in (1, 2, 3):
+    for k in orders:
         vals = [mi_by_order[k][O.rank(n, k, c)] for c in itertools.combinations(comb, k)]
         vals = np.sort(np.log(np.maximum(np.array(vals), 0.0) + 1e-7))[::-1]
         f.extend(vals)
     return np.array(f)
 
 
-def test_features5_match_oracle_scores(epi, small):
+@pytest.mark.parametrize("quad", [False, True])
+def test_features5_match_oracle_scores(epi, small, quad):
     import torch
     geno, pheno, ds = small
     n = geno.shape[0]
-    tabs = [epi.score_all(ds, k) for k in (1, 2, 3)]
-    mi = {k: _oracle_all(geno, pheno, k)[1] for k in (1, 2, 3)}
+    orders = (1, 2, 3, 4) if quad else (1, 2, 3)
+    tabs = [epi.score_all(ds, k) for k in orders]
+    mi = {k: _oracle_all(geno, pheno, k)[1] for k in orders}
     rng = np.random.default_rng(11)
     combs = np.array([np.sort(rng.choice(n, 5, replace=False)) for _ in range(300)], dtype=np.int32)
-    X = epi.features5(ds, *tabs, torch.from_numpy(combs).cuda()).cpu().numpy().astype(np.float64)
-    want = np.stack([_features_cpu(mi, n, c) for c in combs])
-    assert X.shape == (300, 25)
+    cd = torch.from_numpy(combs).cuda()
+    X = epi.features5(ds, *tabs[:3], cd, s4=tabs[3] if quad else None).cpu().numpy().astype(np.float64)
+    want = np.stack([_features_cpu(mi, n, c, orders) for c in combs])
+    assert X.shape == (300, 30 if quad else 25)
     # the kernels take logs with the hardware approximation (|error| about
     # 2^-21 relative to the log's magnitude, < 2e-5 here)
     np.testing.assert_allclose(X, want, rtol=0, atol=2e-5)
     # each group is sorted descending
-    for lo, hi in ((0, 5), (5, 15), (15, 25)):
+    for lo, hi in ((0, 5), (5, 15), (15, 25)) + (((25, 30),) if quad else ()):
         assert (np.diff(X[:, lo:hi], axis=1) <= 0).all()
 
 
@@ -287,11 +290,13 @@ def test_mlp_save_load_roundtrip(epi, ctx, tmp_path):
         c.load_file(p)
 
 
-def test_heuristic5_is_sum_of_triple_features(epi, ctx):
+@pytest.mark.parametrize("cols", [25, 30])
+def test_heuristic5_is_sum_of_top_order_features(epi, ctx, cols):
     import torch
-    X, _ = _net_inputs(1001, 25, 4)
+    X, _ = _net_inputs(1001, cols, 4)
     got = epi.heuristic5(ctx, torch.from_numpy(X).cuda()).cpu().numpy()
-    np.testing.assert_allclose(got, X[:, 15:25].astype(np.float64).sum(axis=1), rtol=1e-6)
+    lo = 15 if cols == 25 else 25
+    np.testing.assert_allclose(got, X[:, lo:cols].astype(np.float64).sum(axis=1), rtol=1e-6)
 
 
 @pytest.mark.parametrize("rows", [1, 127, 128, 129, 1000, 70001])
