@@ -379,9 +379,11 @@ def run_ours(args):
         comp["batch64/auto"] = measure_batch(epi, ctx, synth, args.batch_div)
         if d.n_snps >= 5:
             comp[f"proposer_order5/{args.workload}"] = measure_proposer(epi, ctx, ds, peaks)
+        from paper_2201_02460_gb300 import proposer_eval
         if args.proposer_eval:
-            from paper_2201_02460_gb300 import proposer_eval
             comp["proposer_order5/recall_200snp_2000"] = proposer_eval.evaluate(ctx)
+        else:
+            comp["proposer_order5/recall_200snp_2000_quick"] = proposer_eval.quick(ctx)
         line["compare"] = comp
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

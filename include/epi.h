@@ -250,6 +250,14 @@ epi_status epi_features5(epi_dataset *ds, const float *s1, const float *s2, cons
 epi_status epi_candidates5(epi_dataset *ds, const uint32_t *triples, int64_t n_triples, int64_t first,
                            int64_t count, uint32_t *combs, const float *s3, uint8_t *keep);
 
+/* Exact single-precision MI (Eq. 1-3 of the Section 2.2 table) of `count`
+ * order-5 sets: combs device [count][5] (strictly increasing SNP indices
+ * below n_snps), out device [count] floats.  The tables are counted in
+ * registers and not stored (one warp per set); the value agrees with the
+ * FP32 score of epi_score_tables within the same error bound (the cell terms
+ * are summed in another order).  Queued on the context's stream. */
+epi_status epi_score5(epi_dataset *ds, const uint32_t *combs, int64_t count, float *out);
+
 /* out[i] = table[lexicographic rank of combs[i]] for an order-`order` table
  * of epi_score_all (device arrays; combs [count][order] strictly increasing). */
 epi_status epi_lookup(epi_dataset *ds, int order, const float *table, const uint32_t *combs, int64_t count,

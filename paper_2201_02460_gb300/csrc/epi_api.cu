@@ -953,6 +953,20 @@ epi_status epi_candidates5(epi_dataset *ds, const uint32_t *triples, int64_t n_t
     return EPI_OK;
 }
 
+epi_status epi_score5(epi_dataset *ds, const uint32_t *combs, int64_t count, float *out)
+{
+    if (!ds || !combs || !out || count < 0) return fail(EPI_EINVAL, "epi_score5: bad argument");
+    if (ds->n < 5) return fail(EPI_EINVAL, "epi_score5: needs at least 5 SNPs");
+    if (count == 0) return EPI_OK;
+    epi_ctx *ctx = ds->ctx;
+    DeviceGuard g(ctx->device);
+    if (!is_device_ptr(combs, ctx->device) || !is_device_ptr(out, ctx->device))
+        return fail(EPI_EINVAL, "epi_score5: combs and out must be device memory of device %d", ctx->device);
+    CK(launch_score5_f32(ds->dev(), combs, count, out, ctx->num_sms, ctx->stream));
+    ctx->launches += 1;
+    return EPI_OK;
+}
+
 epi_status epi_lookup(epi_dataset *ds, int order, const float *table, const uint32_t *combs, int64_t count, float *out)
 {
     if (!ds || !table || !combs || !out || count < 0) return fail(EPI_EINVAL, "epi_lookup: bad argument");

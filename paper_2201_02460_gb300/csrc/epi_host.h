@@ -110,6 +110,10 @@ cudaError_t launch_unrank(const DevData &d, int k, const uint64_t *ranks, int64_
 cudaError_t launch_publish_status(const int32_t *bits, int32_t *code, cudaStream_t st);
 cudaError_t launch_score_tables(const DevData &d, int k, const uint32_t *tabs, int64_t count, float *f32, double *f64,
                                 int num_sms, cudaStream_t st);
+// exact FP32 MI of order-5 sets [count][5] (tables counted in registers, not
+// stored)
+cudaError_t launch_score5_f32(const DevData &d, const uint32_t *combs, int64_t count, float *out, int num_sms,
+                              cudaStream_t st);
 
 }  // namespace epi
 

@@ -358,19 +358,17 @@ epi_status rank_and_select(epi_dataset *ds, epi_mlp *net, const DevData &d, cons
         *n_pool = 0;
         return EPI_OK;
     }
-    // exact FP32 scores of every proposal, in slices
-    constexpr int64_t kSlice = (int64_t)1 << 20;
+    // exact FP32 scores of every proposal (tables counted in registers), in slices
+    constexpr int64_t kSlice = (int64_t)1 << 22;
     float *exact;
-    uint32_t *pc, *tabs;
+    uint32_t *pc;
     PCK(pool.get(&exact, n_sel));
     PCK(pool.get(&pc, (size_t)std::min<int64_t>(n_sel, kSlice) * 5));
-    PCK(pool.get(&tabs, (size_t)std::min<int64_t>(n_sel, kSlice) * 2 * 243));
     for (int64_t off = 0; off < (int64_t)n_sel; off += kSlice) {
         const int64_t c = std::min<int64_t>(kSlice, (int64_t)n_sel - off);
         PCK(launch_candidates5_at(d, triples, sel + off, c, pc, st));
-        PCK(launch_tables(d, 5, pc, c, tabs, epi_ctx_num_sms(ctx), st));
-        PCK(launch_score_tables(d, 5, tabs, c, exact + off, nullptr, epi_ctx_num_sms(ctx), st));
-        launches += 3;
+        PCK(launch_score5_f32(d, pc, c, exact + off, epi_ctx_num_sms(ctx), st));
+        launches += 2;
     }
     // the pool: the 4096 best proposals by exact FP32 score
     const int kp = std::min(4096, n_sel);
@@ -576,20 +574,18 @@ epi_status epi_proposer_train(epi_mlp *net, epi_dataset *const *datasets, int n_
         int T = 0;
         PST(best_triples(ds, lp, L.s[3], Ts[i], &triples, &T));
         const int64_t cnt = base[i + 1] - base[i];
-        // labels: every row's 5-way table counted and scored exactly
-        constexpr int64_t kSlice = (int64_t)1 << 20;
-        uint32_t *combs, *tabs;
+        // labels: every row's 5-way table counted and scored exactly (FP32)
+        constexpr int64_t kSlice = (int64_t)1 << 22;
+        uint32_t *combs;
         PCK(lp.get(&combs, (size_t)std::min<int64_t>(cnt, kSlice) * 5));
-        PCK(lp.get(&tabs, (size_t)std::min<int64_t>(cnt, kSlice) * 2 * 243));
         for (int64_t f = 0; f < cnt; f += kSlice) {
             const int64_t c = std::min<int64_t>(cnt - f, kSlice);
             const int64_t at = base[i] + f;
             PCK(launch_cand_features5(d, triples, f, c, L.s[1], L.s[2], L.s[3], L.s[4], X + at * n_in, keep + at, combs,
                                       st));
-            PCK(launch_tables(d, 5, combs, c, tabs, epi_ctx_num_sms(ctx), st));
-            PCK(launch_score_tables(d, 5, tabs, c, t + at, nullptr, epi_ctx_num_sms(ctx), st));
+            PCK(launch_score5_f32(d, combs, c, t + at, epi_ctx_num_sms(ctx), st));
             log_label_kernel<<<grid_for(c), 256, 0, st>>>(t + at, c);
-            launches += 4;
+            launches += 3;
         }
         // this dataset's best-labelled kept rows
         const int kt = (int)std::min<int64_t>(kTail, cnt);

@@ -327,4 +327,88 @@ cudaError_t launch_score_tables(const DevData &d, int k, const uint32_t *tabs, i
     return cudaGetLastError();
 }
 
+// Exact single-precision MI of order-5 sets without materialising their
+// tables (Section 2.2 counts, Eq. 1-3 in the cancellation-free form): one
+// warp per set.  The set's 15 genotype rows are staged in shared memory in
+// chunks of kS5Ch words (rows padded to an odd stride, so lanes reading the
+// three genotype rows of one SNP hit distinct banks); lane l owns the
+// four-SNP prefixes p = l, l + 32, l + 64 (p < 81; the lanes past 81 repeat
+// prefix 0 and discard it) and, per word, counts popc(prefix & last-SNP
+// genotype g) into case or control counters (the class of a word is uniform
+// across the warp).  Cell x = 3 p + g; each lane sums the terms of its cells,
+// the warp sums the lanes.  The summation order differs from the serial
+// table sum, inside the same FP32 error bound.
+constexpr int kS5Warps = 8, kS5Ch = 64, kS5Pad = kS5Ch + 1;
+
+__global__ void __launch_bounds__(kS5Warps * 32) score5_f32_kernel(DevData d, const uint32_t *__restrict__ combs,
+                                                                  int64_t count, float *__restrict__ out)
+{
+    __shared__ uint32_t rows[kS5Warps][15][kS5Pad];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t(*R)[kS5Pad] = rows[warp];
+    const MiConstF32 mc = make_mi_const(d.m, d.m1, d.m0);
+    const int Wt = d.Wt, W1 = d.W1;
+    // the lane's prefixes: row index t * 3 + g_t of the four prefix SNPs
+    int off[3][4];
+    bool valid[3];
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        const int p0 = lane + 32 * j;
+        valid[j] = p0 < 81;
+        const int p = valid[j] ? p0 : 0;
+        off[j][0] = p / 27;
+        off[j][1] = 3 + (p / 9) % 3;
+        off[j][2] = 6 + (p / 3) % 3;
+        off[j][3] = 9 + p % 3;
+    }
+    for (int64_t s = (int64_t)blockIdx.x * kS5Warps + warp; s < count; s += (int64_t)gridDim.x * kS5Warps) {
+        const uint32_t *src[5];
+#pragma unroll
+        for (int t = 0; t < 5; t++) src[t] = d.masks + (int64_t)combs[s * 5 + t] * 3 * Wt;
+        uint32_t cc[3][3] = {}, ck[3][3] = {};
+        for (int c0 = 0; c0 < Wt; c0 += kS5Ch) {
+            const int cw = min(kS5Ch, Wt - c0);
+            __syncwarp();
+#pragma unroll
+            for (int r = 0; r < 15; r++)
+                for (int w = lane; w < cw; w += 32) R[r][w] = src[r / 3][(r % 3) * Wt + c0 + w];
+            __syncwarp();
+            const int split = min(max(W1 - c0, 0), cw);   // words [0, split) are cases
+            auto word = [&](int w, uint32_t (&acc)[3][3]) {
+                const uint32_t l0 = R[12][w], l1 = R[13][w], l2 = R[14][w];
+#pragma unroll
+                for (int j = 0; j < 3; j++) {
+                    const uint32_t pw = R[off[j][0]][w] & R[off[j][1]][w] & R[off[j][2]][w] & R[off[j][3]][w];
+                    acc[j][0] += __popc(pw & l0);
+                    acc[j][1] += __popc(pw & l1);
+                    acc[j][2] += __popc(pw & l2);
+                }
+            };
+            for (int w = 0; w < split; w++) word(w, cc);
+            for (int w = split; w < cw; w++) word(w, ck);
+        }
+        SumF32 acc;
+#pragma unroll
+        for (int j = 0; j < 3; j++)
+            if (valid[j]) {
+#pragma unroll
+                for (int g = 0; g < 3; g++) acc.add(cell_terms_f32(cc[j][g], ck[j][g], mc));
+            }
+        float v = acc.value();
+#pragma unroll
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) out[s] = __fdiv_rn(v, mc.fm);
+    }
+}
+
+cudaError_t launch_score5_f32(const DevData &d, const uint32_t *combs, int64_t count, float *out, int num_sms,
+                              cudaStream_t st)
+{
+    if (count <= 0) return cudaSuccess;
+    int64_t g = (count + kS5Warps - 1) / kS5Warps;
+    if (g > (int64_t)num_sms * 6) g = (int64_t)num_sms * 6;
+    score5_f32_kernel<<<(unsigned)g, kS5Warps * 32, 0, st>>>(d, combs, count, out);
+    return cudaGetLastError();
+}
+
 }  // namespace epi

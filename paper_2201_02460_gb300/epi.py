@@ -128,6 +128,8 @@ def load(path: str | None = None):
         lib.epi_lookup.argtypes = [V, i32, P, P, i64, P]
         lib.epi_topk.restype = i32
         lib.epi_topk.argtypes = [V, P, P, i64, i32, P, P, P]
+        lib.epi_score5.restype = i32
+        lib.epi_score5.argtypes = [V, P, i64, P]
         lib.epi_heuristic5.restype = i32
         lib.epi_heuristic5.argtypes = [V, P, i64, C.c_int, P]
         lib.epi_mlp_create.restype = i32
@@ -462,6 +464,16 @@ def candidates5(ds: Dataset, triples, first: int, count: int, s3=None):
     _check(load().epi_candidates5(ds.handle, _dptr(triples), triples.shape[0], first, count, _dptr(out),
                                   None if s3 is None else _dptr(s3), None if keep is None else _dptr(keep)))
     return out if s3 is None else (out, keep)
+
+
+def score5(ds: Dataset, combs):
+    """Exact FP32 MI of device order-5 sets (int32 [count, 5]), tables
+    counted in registers (float32 [count] on the device)."""
+    import torch
+    combs = combs.contiguous()
+    out = torch.empty(combs.shape[0], dtype=torch.float32, device=combs.device)
+    _check(load().epi_score5(ds.handle, _dptr(combs), combs.shape[0], _dptr(out)))
+    return out
 
 
 def lookup(ds: Dataset, order: int, table, combs):

@@ -75,6 +75,40 @@ def evaluate(ctx=None, n_train: int = 8, epochs: int = 4, epochs30: int = 2, tra
                 seconds=time.perf_counter() - t0)
 
 
+def quick(ctx=None, seed_eval: int = synth.BASE_SEED + 104, top_triples: int = 65536,
+          budgets=(10 ** 6, 10 ** 7)) -> dict:
+    """A short recall measurement for the benchmark: one held-out 200 x 2000
+    dataset, its exhaustive order-5 top-100 (tensor path), and the 30-feature
+    proposals of the heuristic and of a network trained briefly (two
+    datasets, T = 256, one epoch) at each budget."""
+    ctx = ctx or epi.Context(0)
+    ds = make(ctx, seed_eval, False)
+    t0 = time.perf_counter()
+    truth = {tuple(int(x) for x in c) for c in epi.search(ds, 5, 100, path="tc").combs}
+    t_ex = time.perf_counter() - t0
+    train = [make(ctx, synth.BASE_SEED + 200 + i, i % 2 == 0) for i in range(2)]
+    net = epi.MLP(ctx, 30, 256, seed=1)
+    t1 = time.perf_counter()
+    epi.proposer_train(net, train, 256, 1, 8192, 1e-3, 1e-4, 0.5, 7)
+    t_train = time.perf_counter() - t1
+    out = dict(metric="top-N recall at k=5 (recall@100 of the exhaustive order-5 top-100)", n_snps=200,
+               n_samples=2000, features=30, top_triples=top_triples, exhaustive_seconds=t_ex,
+               train_seconds=t_train, results=[])
+    epi.proposer_search(ds, None, top_triples, 4096, 100, quad_features=True)   # order-4 table, warm-up
+    for R in budgets:
+        for name, scorer in (("heuristic", None), ("network", net)):
+            t2 = time.perf_counter()
+            r, st = epi.proposer_search(ds, scorer, top_triples, R, 100, quad_features=True)
+            secs = time.perf_counter() - t2
+            rec = len({tuple(int(x) for x in c) for c in r.combs} & truth) / 100.0
+            out["results"].append(dict(ranking=name, budget=R, recall_at_100=rec, seconds=secs,
+                                       exact_in_proposals=int(st["exact_in_proposals"])))
+    net.close()
+    for d in train + [ds]:
+        d.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--train", type=int, default=8)
