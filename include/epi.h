@@ -298,7 +298,7 @@ epi_status epi_mlp_set_params(epi_mlp *net, const float *host);
 epi_status epi_mlp_set_input_norm(epi_mlp *net, const float *shift_host, const float *scale_host);
 epi_status epi_mlp_get_input_norm(const epi_mlp *net, float *shift_host, float *scale_host);
 /* Predictions for `rows` device inputs X [rows][n_in] into device y [rows].
- * With hidden = 256 and n_in <= 64 one fused tensor-core kernel runs the
+ * With hidden = 256 and n_in <= 32 one fused tensor-core kernel runs the
  * three layers (BF16 operands, FP32 accumulation, activations rounded to
  * BF16 between layers, as in training) and the call waits for it (status
  * EPI_ETIMEOUT if a bounded wait gave up); other shapes run the CUDA-core

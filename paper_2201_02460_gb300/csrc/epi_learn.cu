@@ -707,7 +707,7 @@ epi_status epi_mlp_set_forward_path(epi_mlp *net, int path)
 {
     if (!net || path < 0 || path > 2) return lfail(EPI_EINVAL, "epi_mlp_set_forward_path: bad argument");
     if (path == 2 && !mlp_tc_applies(net->n_in, net->hidden))
-        return lfail(EPI_EUNSUPPORTED, "tensor-core inference needs hidden = 256 and n_in <= 64");
+        return lfail(EPI_EUNSUPPORTED, "tensor-core inference needs hidden = 256 and n_in <= 32");
     net->forward_path = path;
     return EPI_OK;
 }

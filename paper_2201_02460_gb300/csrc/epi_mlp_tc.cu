@@ -6,26 +6,30 @@
 // (the same storage points as the training kernels).  One persistent CTA per
 // SM keeps both weight matrices in shared memory for the whole launch:
 //   W2   [256 out][256 in]  BF16, K-major, 4 K blocks of 64     128 KiB
-//   W1   [256 out][64 in]   BF16, inputs zero-padded to 64       32 KiB
-//   H1   [128 rows][256]    BF16, 4 K blocks (also the staging
-//        area of the input rows and of x')                      64 KiB
-// all in the 128-byte swizzle (8-row atoms of 1024 bytes).  Tensor memory:
-// layer 1 in columns [0, 256), layer 2 in [256, 512).  Warp roles, pipelined
-// across the CTA's 128-row tiles:
-//   group A (warps 0-7): copy the tile's input rows (coalesced) into H1's
-//      second K block, stage x' (BF16) into its first; after layer 1, read
+//   H1   [128 rows][256]    BF16, 4 K blocks                     64 KiB
+//   W1   [256 out][32 in]   BF16, inputs zero-padded to 32       16 KiB
+//   X'   2 x [128 rows][32] BF16 (double-buffered input tiles)   16 KiB
+// W2 and H1 in the 128-byte swizzle (8-row atoms of 1024 bytes), W1 and X'
+// in the 64-byte swizzle (8-row atoms of 512 bytes).  Tensor memory: layer 1
+// in columns [0, 256), layer 2 in [256, 512).  Warp roles, pipelined across
+// the CTA's 128-row tiles:
+//   group A (warps 0-7): load the next tile's input rows straight into
+//      registers (thread: one row, 16 inputs), normalise, round to BF16 and
+//      write X' while layer 2 of the current tile runs; after layer 1, read
 //      lane quadrant w % 4, column half w / 4, add b1, ReLU, round to BF16
 //      and write H1;
-//   warp 16, one lane: layer 1 (M128 N256 K64: 4 MMAs of K16) once x' is
-//      staged, layer 2 (M128 N256 K256: 16 MMAs) once H1 is written and the
-//      previous tile's layer-2 columns are read;
+//   warp 16, one lane: layer 1 (M128 N256 K32: 2 MMAs of K16) once X' is
+//      staged (queued behind the previous layer 2), layer 2 (M128 N256 K256:
+//      16 MMAs) once H1 is written and the previous tile's layer-2 columns
+//      are read;
 //   group B (warps 8-15): after layer 2, add b2, ReLU, round to BF16, dot
 //      with W3; the two column halves of a row meet in shared memory and b3
 //      is added.
-// Group B's output of tile t overlaps group A's staging and layer-1 epilogue
-// of tile t + 1.  Every mbarrier wait is bounded (about 2 s); a wait that
-// gives up sets the status word, every role leaves its loop, the MMAs are
-// drained and tensor memory is freed.
+// Group B's output of tile t overlaps group A's layer-1 epilogue of tile
+// t + 1, and the staging of tile t + 1 overlaps layer 2 of tile t.  Every
+// mbarrier wait is bounded (about 2 s); a wait that gives up sets the status
+// word, every role leaves its loop, the MMAs are drained and tensor memory is
+// freed.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -38,14 +42,15 @@ namespace mlptc {
 
 constexpr int kRows = 128;
 constexpr int kHidden = 256;
-constexpr int kKin = 64;                       // padded inputs
+constexpr int kKin = 32;                       // padded inputs
 constexpr int kGroupWarps = 8;                 // per epilogue group
 constexpr int kGroupThreads = 32 * kGroupWarps;
 constexpr int kWarpMma = 2 * kGroupWarps;      // warp 16
 constexpr int kThreads = 32 * (2 * kGroupWarps + 1);
 constexpr uint32_t kW2Bytes = 4 * kHidden * 128;
-constexpr uint32_t kW1Bytes = kHidden * 128;
+constexpr uint32_t kW1Bytes = kHidden * 64;
 constexpr uint32_t kH1Bytes = 4 * kRows * 128;
+constexpr uint32_t kXBytes = kRows * 64;        // one input tile
 constexpr uint32_t kKBlockH = kRows * 128;     // one K block of H1
 constexpr uint32_t kKBlockW = kHidden * 128;   // one K block of W2
 constexpr unsigned long long kTimeoutNs = 2000000000ull;
@@ -62,8 +67,25 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
         "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate));
 }
 
-// byte offset of 16-byte chunk c (0..7) of row r inside a swizzled K block
+// byte offset of 16-byte chunk c (0..7) of row r inside a K block in the
+// 128-byte swizzle
 __device__ __forceinline__ uint32_t sw(int r, int c) { return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4)); }
+
+// the same in the 64-byte swizzle (rows of 64 bytes, chunk c in 0..3; the
+// chunk index is XORed with bits 7-8 of the row's byte offset)
+__device__ __forceinline__ uint32_t sw64(int r, int c) { return (uint32_t)(r * 64 + ((c ^ ((r >> 1) & 3)) << 4)); }
+
+// K-major operand in the 64-byte swizzle: 8-row atoms of 512 bytes stacked
+// along M/N (stride 512), descriptor version 1, layout SWIZZLE_64B
+__device__ __forceinline__ uint64_t sdesc64(uint32_t saddr)
+{
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(512 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)4 << 61;
+    return d;
+}
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
 {
@@ -127,9 +149,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
     unsigned char *w2s = smem;
-    unsigned char *w1s = w2s + kW2Bytes;
-    unsigned char *h1s = w1s + kW1Bytes;
+    unsigned char *h1s = w2s + kW2Bytes;
+    unsigned char *w1s = h1s + kH1Bytes;
+    unsigned char *xs = w1s + kW1Bytes;        // two input tiles
     __shared__ float part[2][kRows];           // row partials of the last layer
+    __shared__ float nrm[2][kKin];             // input shift and scale (0 past n_in)
     __shared__ __align__(8) uint64_t x_full, m1_done, h1_full, m2_done, e2_free, drain_bar;
     __shared__ uint32_t tmem_base_sh;
     __shared__ volatile int abort_flag;
@@ -161,8 +185,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         *reinterpret_cast<uint4 *>(w2s + (c32 >> 3) * kKBlockW + sw(n, c32 & 7)) = v;
     }
     const unsigned short *w1u = reinterpret_cast<const unsigned short *>(W1);
-    for (int idx = tid; idx < kHidden * 8; idx += kThreads) {
-        const int n = idx >> 3, c = idx & 7;
+    for (int idx = tid; idx < kHidden * 4; idx += kThreads) {
+        const int n = idx >> 2, c = idx & 3;
         uint32_t w[4];
 #pragma unroll
         for (int q = 0; q < 4; q++) {
@@ -171,7 +195,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t hi = e1 < n_in ? w1u[(size_t)n * n_in + e1] : 0u;
             w[q] = lo | (hi << 16);
         }
-        *reinterpret_cast<uint4 *>(w1s + sw(n, c)) = make_uint4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<uint4 *>(w1s + sw64(n, c)) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    for (int e = tid; e < kKin; e += kThreads) {
+        nrm[0][e] = e < n_in ? norm[e] : 0.0f;
+        nrm[1][e] = e < n_in ? norm[n_in + e] : 0.0f;
     }
     fence_proxy_async();
     tc_fence_before();
@@ -180,51 +208,43 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tmem_base = tmem_base_sh;
 
     if (warp < kGroupWarps) {
-        // ------------------------------------- group A: stage x', layer-1 epilogue
+        // ------------------------------------- group A: stage X', layer-1 epilogue
         const int quad = warp & 3, half = warp >> 2;
         const int r = quad * 32 + lane;
         const uint32_t lane_addr = tmem_base + ((uint32_t)(quad * 32) << 16);
-        for (int64_t i = 0; i < my_tiles; i++) {
-            const int64_t tile = blockIdx.x + i * (int64_t)gridDim.x;
-            // H1 (and the staging area) is free once the previous layer 2 is done
-            if (i > 0 && !group_wait(&m2_done, (uint32_t)((i - 1) & 1), &abort_flag, 1)) break;
-            {
-                const int64_t r0 = tile * kRows;
-                const int64_t nrows = rows - r0 < kRows ? rows - r0 : kRows;
-                const int64_t nfl = nrows * n_in;
-                float *xs = reinterpret_cast<float *>(h1s + kKBlockH);
-                const float *src = X + r0 * n_in;
-                if ((((uintptr_t)src) & 15) == 0) {
-                    const int64_t n4 = nfl >> 2;
-                    for (int64_t q = tid; q < n4; q += kGroupThreads)
-                        reinterpret_cast<float4 *>(xs)[q] = __ldg(reinterpret_cast<const float4 *>(src) + q);
-                    for (int64_t q = (n4 << 2) + tid; q < nfl; q += kGroupThreads) xs[q] = __ldg(src + q);
-                } else {
-                    for (int64_t q = tid; q < nfl; q += kGroupThreads) xs[q] = __ldg(src + q);
-                }
-                named_bar(1, kGroupThreads);
-                const int sr = tid >> 1, sh = tid & 1;
-                const bool valid = sr < nrows;
+        // staging: thread tid takes row tid / 2, inputs [16 (tid % 2), +16)
+        const int sr = tid >> 1, sh = tid & 1;
+        auto stage = [&](int64_t tile, int buf) {
+            const int64_t row = tile * kRows + sr;
+            const bool valid = row < rows;
+            const float *src = X + row * n_in;
+            float v[16];
 #pragma unroll
-                for (int cc = 0; cc < 4; cc++) {
-                    const int c = 4 * sh + cc;
-                    uint32_t w[4];
+            for (int j = 0; j < 16; j++) {
+                const int e = 16 * sh + j;
+                v[j] = (valid && e < n_in) ? __ldg(src + e) : 0.0f;
+            }
 #pragma unroll
-                    for (int q = 0; q < 4; q++) {
-                        const int e0 = 8 * c + 2 * q, e1 = e0 + 1;
-                        const float a = (valid && e0 < n_in) ? (xs[sr * n_in + e0] - norm[e0]) * norm[n_in + e0] : 0.0f;
-                        const float b = (valid && e1 < n_in) ? (xs[sr * n_in + e1] - norm[e1]) * norm[n_in + e1] : 0.0f;
-                        w[q] = pack_bf16(a, b);
-                    }
-                    *reinterpret_cast<uint4 *>(h1s + sw(sr, c)) = make_uint4(w[0], w[1], w[2], w[3]);
+            for (int cc = 0; cc < 2; cc++) {
+                uint32_t w[4];
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const int j = 8 * cc + 2 * q, e = 16 * sh + j;
+                    w[q] = pack_bf16((v[j] - nrm[0][e]) * nrm[1][e], (v[j + 1] - nrm[0][e + 1]) * nrm[1][e + 1]);
                 }
+                *reinterpret_cast<uint4 *>(xs + buf * kXBytes + sw64(sr, 2 * sh + cc)) =
+                    make_uint4(w[0], w[1], w[2], w[3]);
             }
             fence_proxy_async();
             __syncwarp();
             if (lane == 0) mbar_arrive(&x_full);
-            // (the group meets here: every warp has also finished reading the
-            // staging rows that the layer-1 epilogue overwrites)
+        };
+        if (my_tiles > 0) stage(blockIdx.x, 0);
+        for (int64_t i = 0; i < my_tiles; i++) {
+            const int64_t tile = blockIdx.x + i * (int64_t)gridDim.x;
+            // layer 1 done, and H1 free once the previous layer 2 is done
             if (!group_wait(&m1_done, (uint32_t)(i & 1), &abort_flag, 1)) break;
+            if (i > 0 && !group_wait(&m2_done, (uint32_t)((i - 1) & 1), &abort_flag, 1)) break;
             tc_fence_after();
 #pragma unroll 1
             for (int q = 0; q < 4; q++) {
@@ -254,6 +274,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&h1_full);
+            // the next tile's inputs while layer 2 runs (its layer 1 then
+            // follows in the tensor pipe; layer-1 columns were read above)
+            if (i + 1 < my_tiles) stage(tile + gridDim.x, (int)((i + 1) & 1));
         }
     } else if (warp < 2 * kGroupWarps) {
         // ------------------------------------- group B: layer-2 epilogue and output
@@ -305,13 +328,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp == kWarpMma) {
         // ------------------------------------- MMA issuer (one elected lane)
         if (lane == 0) {
-            const uint64_t ad1 = sdesc(smem_u32(h1s)), bd1 = sdesc(smem_u32(w1s));
-            const uint32_t h0 = smem_u32(h1s), w0 = smem_u32(w2s);
+            const uint64_t bd1 = sdesc64(smem_u32(w1s));
+            const uint32_t h0 = smem_u32(h1s), w0 = smem_u32(w2s), x0 = smem_u32(xs);
             bool issued = false;
             for (int64_t i = 0; i < my_tiles; i++) {
                 const uint32_t par = (uint32_t)(i & 1);
                 if (!wait_ok(&x_full, par, &abort_flag)) break;
                 tc_fence_after();
+                const uint64_t ad1 = sdesc64(x0 + (uint32_t)(i & 1) * kXBytes);
 #pragma unroll
                 for (int kk = 0; kk < kKin / 16; kk++) mma_bf16(tmem_base, ad1 + 2 * kk, bd1 + 2 * kk, kk ? 1u : 0u);
                 mma_commit(&m1_done);
@@ -350,7 +374,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 size_t mlp_tc_smem_bytes()
 {
-    return 1024 + mlptc::kW2Bytes + mlptc::kW1Bytes + mlptc::kH1Bytes;
+    return 1024 + mlptc::kW2Bytes + mlptc::kH1Bytes + mlptc::kW1Bytes + 2 * mlptc::kXBytes;
 }
 
 bool mlp_tc_applies(int n_in, int hidden) { return hidden == mlptc::kHidden && n_in >= 1 && n_in <= mlptc::kKin; }

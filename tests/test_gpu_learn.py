@@ -320,26 +320,27 @@ def test_heuristic5_is_sum_of_top_order_features(epi, ctx, cols):
     np.testing.assert_allclose(got, X[:, lo:cols].astype(np.float64).sum(axis=1), rtol=1e-6)
 
 
-@pytest.mark.parametrize("rows", [1, 127, 128, 129, 1000, 70001])
-def test_mlp_tensor_core_forward_matches_reference(epi, ctx, rows):
+@pytest.mark.parametrize("rows,n_in", [(1, 25), (127, 25), (128, 25), (129, 25), (1000, 25), (70001, 25),
+                                      (70001, 30), (3001, 32), (385, 1), (1000, 16), (1000, 17)])
+def test_mlp_tensor_core_forward_matches_reference(epi, ctx, rows, n_in):
     import torch
-    net = epi.MLP(ctx, 25, 256, seed=rows)
-    rng = np.random.default_rng(rows)
-    shift = rng.uniform(-6, -3, 25).astype(np.float32)
-    scale = rng.uniform(0.5, 2.0, 25).astype(np.float32)
+    net = epi.MLP(ctx, n_in, 256, seed=rows)
+    rng = np.random.default_rng(rows + n_in)
+    shift = rng.uniform(-6, -3, n_in).astype(np.float32)
+    scale = rng.uniform(0.5, 2.0, n_in).astype(np.float32)
     net.set_input_norm(shift, scale)
     theta = net.params().astype(np.float64)
-    theta[25 * 256:25 * 256 + 256] = rng.normal(0, 0.1, 256)          # nonzero b1
+    theta[n_in * 256:n_in * 256 + 256] = rng.normal(0, 0.1, 256)      # nonzero b1
     net.set_params(theta.astype(np.float32))
     theta = net.params().astype(np.float64)
-    X, _ = _net_inputs(rows, 25, rows + 1)
+    X, _ = _net_inputs(rows, n_in, rows + 1)
     Xd = torch.from_numpy(X).cuda()
     net.set_forward_path("tensor_cores")
     y_tc = net.forward(Xd).cpu().numpy().astype(np.float64)
     net.set_forward_path("cuda_cores")
     y_cc = net.forward(Xd).cpu().numpy().astype(np.float64)
     Xn = (X - shift) * scale                                            # float32, as the kernels form it
-    y_q, (_, _, _, _, H2, _, W3) = M.forward(theta, Xn, 25, 256, rnd=_bf16)
+    y_q, (_, _, _, _, H2, _, W3) = M.forward(theta, Xn, n_in, 256, rnd=_bf16)
     bound = 2.0 ** -7 * (np.abs(H2) @ np.abs(W3) + 1.0)
     # both paths round the hidden layers to BF16 at the reference's points;
     # a different FP32 accumulation order may move a rounded activation by
@@ -354,4 +355,4 @@ def test_mlp_tensor_core_path_needs_its_shape(epi, ctx):
     with pytest.raises(epi.EpiError):
         epi.MLP(ctx, 25, 64).set_forward_path("tensor_cores")
     with pytest.raises(epi.EpiError):
-        epi.MLP(ctx, 65, 256).set_forward_path("tensor_cores")
+        epi.MLP(ctx, 33, 256).set_forward_path("tensor_cores")
