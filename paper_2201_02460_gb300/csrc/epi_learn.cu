@@ -127,17 +127,17 @@ __device__ __forceinline__ void candidate_at(const DevData &d, const uint32_t *_
 {
     const int64_t rest = d.n - 3;
     const uint64_t per = (uint64_t)(rest * (rest - 1) / 2);
-    const uint64_t t = g / per;
+    const uint64_t t = (g >> 32) == 0 && (per >> 32) == 0 ? (uint64_t)((uint32_t)g / (uint32_t)per) : g / per;
     const int64_t r = (int64_t)(g - t * per);
     const int32_t a = (int32_t)triples[t * 3], b = (int32_t)triples[t * 3 + 1], c = (int32_t)triples[t * 3 + 2];
     g3[0] = a; g3[1] = b; g3[2] = c;
     // pair (x, y) of [0, rest) with lexicographic rank r: pairs whose first
     // element is below x number S(x) = x (2 rest - x - 1) / 2; x is the
-    // largest value with S(x) <= r (closed form, then corrected by integer
-    // comparisons)
+    // largest value with S(x) <= r (closed form in single precision, then
+    // corrected by integer comparisons)
     auto S = [&](int64_t x) { return x * (2 * rest - x - 1) / 2; };
-    const double B = (double)(2 * rest - 1);
-    int64_t x = (int64_t)((B - sqrt(fmax(B * B - 8.0 * (double)r, 0.0))) * 0.5);
+    const float B = (float)(2 * rest - 1);
+    int64_t x = (int64_t)((B - sqrtf(fmaxf(B * B - 8.0f * (float)r, 0.0f))) * 0.5f);
     if (x < 0) x = 0;
     if (x > rest - 2) x = rest - 2;
     while (x > 0 && S(x) > r) x--;
@@ -213,7 +213,9 @@ __global__ void candidates5_at_kernel(DevData d, const uint32_t *__restrict__ tr
 // Candidates [first, first + count) in one pass: the set, whether its
 // generating triple is its best (keep) and its 25 features (30 with the
 // order-4 table s4); the set itself is written only when combs is given.
-__global__ void __launch_bounds__(256) cand_features5_kernel(DevData d, const uint32_t *__restrict__ triples,
+constexpr int kFeatThreads = 256;
+
+__global__ void __launch_bounds__(kFeatThreads) cand_features5_kernel(DevData d, const uint32_t *__restrict__ triples,
                                                              int64_t first, int64_t count, const float *__restrict__ s1,
                                                              const float *__restrict__ s2, const float *__restrict__ s3,
                                                              const float *__restrict__ s4, float *__restrict__ X,
@@ -221,12 +223,20 @@ __global__ void __launch_bounds__(256) cand_features5_kernel(DevData d, const ui
 {
     const int64_t n = d.n;
     const int cols = s4 ? 30 : 25;
+    const int stride = cols | 1;          // odd row stride in shared memory: no bank conflicts
+    // a block's rows are staged here and written out coalesced (each thread
+    // owning a 100- or 120-byte row would scatter every store over 32 rows)
+    __shared__ float rows_s[kFeatThreads * 31];
     // binomials C(x, 2), C(x, 3), C(x, 4) from the dataset's table (L1-resident rows)
     const uint64_t *__restrict__ b2 = d.binom + 2 * (n + 1);
     const uint64_t *__restrict__ b3 = d.binom + 3 * (n + 1);
     const uint64_t *__restrict__ b4 = d.binom + 4 * (n + 1);
     const uint64_t n2 = b2[n], n3 = b3[n];
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t base = (int64_t)blockIdx.x * kFeatThreads; base < count; base += (int64_t)gridDim.x * kFeatThreads) {
+        const int64_t i = base + threadIdx.x;
+        const int nrows = count - base < kFeatThreads ? (int)(count - base) : kFeatThreads;
+        __syncthreads();                  // the previous rows are written out
+        if (i < count) {
         int32_t v[5], g3[3];
         candidate_at(d, triples, (uint64_t)(first + i), v, g3);
         if (combs) {
@@ -266,7 +276,7 @@ __global__ void __launch_bounds__(256) cand_features5_kernel(DevData d, const ui
         sort_desc(f1);
         sort_desc(f2);
         sort_desc(f3);
-        float *x = X + i * cols;
+        float *x = rows_s + threadIdx.x * stride;
 #pragma unroll
         for (int t = 0; t < 5; t++) x[t] = feat_log(f1[t]);
 #pragma unroll
@@ -291,6 +301,15 @@ __global__ void __launch_bounds__(256) cand_features5_kernel(DevData d, const ui
             sort_desc(f4);
 #pragma unroll
             for (int t = 0; t < 5; t++) x[25 + t] = feat_log(f4[t]);
+        }
+        }
+        __syncthreads();
+        // the block's rows are contiguous in X: coalesced word stores
+        float *dst = X + base * cols;
+        const int words = nrows * cols;
+        for (int w = threadIdx.x; w < words; w += kFeatThreads) {
+            const int row = w / cols, col = w - row * cols;
+            dst[w] = rows_s[row * stride + col];
         }
     }
 }
