@@ -78,9 +78,15 @@ cudaError_t launch_candidates5_at(const DevData &d, const uint32_t *triples, con
 // epi_mlp_tc.cu
 size_t mlp_tc_smem_bytes();
 bool mlp_tc_applies(int n_in, int hidden);
-cudaError_t launch_mlp_forward_tc(const float *X, int64_t rows, int n_in, const float *norm, const void *W1,
-                                  const float *b1, const void *W2, const float *b2, const void *W3, const float *b3,
-                                  float *y, int32_t *status, int num_sms, cudaStream_t st);
+cudaError_t launch_mlp_forward_tc(const float *X, int64_t rows, const uint32_t *idx, const int32_t *rows_dev, int n_in,
+                                  const float *norm, const void *W1, const float *b1, const void *W2, const float *b2,
+                                  const void *W3, const float *b3, float *y, int32_t *status, int num_sms,
+                                  cudaStream_t st);
+// Tensor-core predictions for the listed rows only: row j < *n_dev (at most
+// max_rows) is X[idx[j]], its prediction goes to y[idx[j]]; waits for the
+// kernel.  EPI_EUNSUPPORTED where the fused kernel does not apply.
+epi_status mlp_forward_rows(epi_mlp *net, const float *X, int64_t max_rows, const uint32_t *idx, const int32_t *n_dev,
+                            float *y);
 cudaError_t launch_cand_features5(const DevData &d, const uint32_t *triples, int64_t first, int64_t count,
                                   const float *s1, const float *s2, const float *s3, const float *s4, float *X,
                                   uint8_t *keep, uint32_t *combs, cudaStream_t st);

@@ -738,9 +738,9 @@ epi_status epi_mlp_forward(epi_mlp *net, const float *X_dev, int64_t rows, float
         const int in = net->n_in, h = net->hidden;
         const Offs o = offsets(in, h);
         LCK(cudaMemsetAsync(net->status, 0, 4, net->stream));
-        LCK(launch_mlp_forward_tc(X_dev, rows, in, net->norm, net->wb + o.W1, net->w + o.b1, net->wb + o.W2,
-                                  net->w + o.b2, net->wb + o.W3, net->w + o.b3, y_dev, net->status, net->num_sms,
-                                  net->stream));
+        LCK(launch_mlp_forward_tc(X_dev, rows, nullptr, nullptr, in, net->norm, net->wb + o.W1, net->w + o.b1,
+                                  net->wb + o.W2, net->w + o.b2, net->wb + o.W3, net->w + o.b3, y_dev, net->status,
+                                  net->num_sms, net->stream));
         int32_t st = 0;
         LCK(cudaMemcpyAsync(&st, net->status, 4, cudaMemcpyDeviceToHost, net->stream));
         LCK(cudaStreamSynchronize(net->stream));
@@ -810,6 +810,23 @@ epi_status epi_heuristic5(epi_ctx *ctx, const float *X_dev, int64_t count, int n
 
 // dataset-side kernels of the proposer
 namespace epi {
+
+epi_status mlp_forward_rows(epi_mlp *net, const float *X, int64_t max_rows, const uint32_t *idx, const int32_t *n_dev,
+                            float *y)
+{
+    if (!(net->forward_path != 1 && mlp_tc_applies(net->n_in, net->hidden))) return EPI_EUNSUPPORTED;
+    if (max_rows < 1) return EPI_OK;
+    const Offs o = offsets(net->n_in, net->hidden);
+    LCK(cudaMemsetAsync(net->status, 0, 4, net->stream));
+    LCK(launch_mlp_forward_tc(X, max_rows, idx, n_dev, net->n_in, net->norm, net->wb + o.W1, net->w + o.b1,
+                              net->wb + o.W2, net->w + o.b2, net->wb + o.W3, net->w + o.b3, y, net->status,
+                              net->num_sms, net->stream));
+    int32_t st = 0;
+    LCK(cudaMemcpyAsync(&st, net->status, 4, cudaMemcpyDeviceToHost, net->stream));
+    LCK(cudaStreamSynchronize(net->stream));
+    if (st) return lfail(EPI_ETIMEOUT, "network inference: a tensor-core wait gave up");
+    return EPI_OK;
+}
 
 cudaError_t launch_features5(const DevData &d, const float *s1, const float *s2, const float *s3, const float *s4,
                              const uint32_t *combs, int64_t count, float *X, cudaStream_t st)

@@ -140,7 +140,8 @@ __device__ __forceinline__ bool wait_ok(uint64_t *bar, uint32_t parity, volatile
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
-    mlp_forward_kernel(const float *__restrict__ X, int64_t rows, int n_in, const float *__restrict__ norm,
+    mlp_forward_kernel(const float *__restrict__ X, int64_t rows, const uint32_t *__restrict__ idx,
+                       const int32_t *__restrict__ rows_dev, int n_in, const float *__restrict__ norm,
                        const __nv_bfloat16 *__restrict__ W1, const float *__restrict__ b1,
                        const __nv_bfloat16 *__restrict__ W2, const float *__restrict__ b2,
                        const __nv_bfloat16 *__restrict__ W3, const float *__restrict__ b3, float *__restrict__ y,
@@ -159,6 +160,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ volatile int abort_flag;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // with rows_dev, the row count is read on the device (at most `rows`);
+    // with idx, row j of the launch is input row idx[j] and its prediction
+    // goes to y[idx[j]]
+    if (rows_dev) {
+        const int64_t rd = *rows_dev;
+        rows = rd < rows ? (rd > 0 ? rd : 0) : rows;
+    }
     const int64_t n_tiles = (rows + kRows - 1) / kRows;
     const int64_t my_tiles = (int64_t)blockIdx.x < n_tiles ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
@@ -217,7 +225,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         auto stage = [&](int64_t tile, int buf) {
             const int64_t row = tile * kRows + sr;
             const bool valid = row < rows;
-            const float *src = X + row * n_in;
+            const float *src = X + (idx && valid ? (int64_t)idx[row] : row) * n_in;
             float v[16];
 #pragma unroll
             for (int j = 0; j < 16; j++) {
@@ -321,7 +329,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             named_bar(2, kGroupThreads);
             if (gt < kRows) {
                 const int64_t row = tile * kRows + gt;
-                if (row < rows) y[row] = part[0][gt] + part[1][gt] + __ldg(b3);
+                if (row < rows) y[idx ? (int64_t)idx[row] : row] = part[0][gt] + part[1][gt] + __ldg(b3);
             }
             named_bar(2, kGroupThreads);
         }
@@ -379,9 +387,10 @@ size_t mlp_tc_smem_bytes()
 
 bool mlp_tc_applies(int n_in, int hidden) { return hidden == mlptc::kHidden && n_in >= 1 && n_in <= mlptc::kKin; }
 
-cudaError_t launch_mlp_forward_tc(const float *X, int64_t rows, int n_in, const float *norm, const void *W1,
-                                  const float *b1, const void *W2, const float *b2, const void *W3, const float *b3,
-                                  float *y, int32_t *status, int num_sms, cudaStream_t st)
+cudaError_t launch_mlp_forward_tc(const float *X, int64_t rows, const uint32_t *idx, const int32_t *rows_dev, int n_in,
+                                  const float *norm, const void *W1, const float *b1, const void *W2, const float *b2,
+                                  const void *W3, const float *b3, float *y, int32_t *status, int num_sms,
+                                  cudaStream_t st)
 {
     if (rows <= 0) return cudaSuccess;
     const size_t smem = mlp_tc_smem_bytes();
@@ -391,7 +400,7 @@ cudaError_t launch_mlp_forward_tc(const float *X, int64_t rows, int n_in, const 
     const int64_t tiles = (rows + mlptc::kRows - 1) / mlptc::kRows;
     const int grid = (int)(tiles < num_sms ? tiles : num_sms);
     mlptc::mlp_forward_kernel<<<grid, mlptc::kThreads, smem, st>>>(
-        X, rows, n_in, norm, static_cast<const __nv_bfloat16 *>(W1), b1, static_cast<const __nv_bfloat16 *>(W2), b2,
+        X, rows, idx, rows_dev, n_in, norm, static_cast<const __nv_bfloat16 *>(W1), b1, static_cast<const __nv_bfloat16 *>(W2), b2,
         static_cast<const __nv_bfloat16 *>(W3), b3, y, status);
     return cudaGetLastError();
 }

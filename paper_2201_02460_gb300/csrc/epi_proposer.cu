@@ -215,7 +215,8 @@ __global__ void __launch_bounds__(256) flag_count_kernel(const uint8_t *__restri
     if (threadIdx.x == 0) cnt[blockIdx.x] = c;
 }
 
-__global__ void __launch_bounds__(kCompactBlocks) flag_scan_kernel(unsigned long long *__restrict__ cnt)
+__global__ void __launch_bounds__(kCompactBlocks) flag_scan_kernel(unsigned long long *__restrict__ cnt,
+                                                                   int32_t *__restrict__ total)
 {
     __shared__ unsigned long long s[kCompactBlocks];
     const int t = threadIdx.x;
@@ -229,11 +230,13 @@ __global__ void __launch_bounds__(kCompactBlocks) flag_scan_kernel(unsigned long
         __syncthreads();
     }
     cnt[t] = s[t] - own;   // exclusive
+    if (total && t == kCompactBlocks - 1) *total = (int32_t)s[t];
 }
 
+template <typename T>
 __global__ void __launch_bounds__(256) flag_write_kernel(const uint8_t *__restrict__ flags, uint64_t count,
                                                          const unsigned long long *__restrict__ off,
-                                                         uint64_t *__restrict__ out)
+                                                         T *__restrict__ out)
 {
     __shared__ uint32_t wsum[8];
     uint64_t b, e;
@@ -249,7 +252,7 @@ __global__ void __launch_bounds__(256) flag_write_kernel(const uint8_t *__restri
         uint64_t before = base;
         for (int w = 0; w < warp; w++) before += wsum[w];
         before += __popc(m & ((1u << lane) - 1u));
-        if (f) out[before] = i;
+        if (f) out[before] = (T)i;
         uint32_t total = 0;
         for (int w = 0; w < 8; w++) total += wsum[w];
         __syncthreads();
@@ -288,8 +291,8 @@ epi_status best_triples(epi_dataset *ds, Pool &pool, const float *s3, int T, uin
     PCK(cudaMemsetAsync(flags, 0, (size_t)total3, st));
     flag_set_kernel<<<grid_for(T), 256, 0, st>>>(flags, sel, T);
     flag_count_kernel<<<kCompactBlocks, 256, 0, st>>>(flags, (uint64_t)total3, cnt);
-    flag_scan_kernel<<<1, kCompactBlocks, 0, st>>>(cnt);
-    flag_write_kernel<<<kCompactBlocks, 256, 0, st>>>(flags, (uint64_t)total3, cnt, rk);
+    flag_scan_kernel<<<1, kCompactBlocks, 0, st>>>(cnt, nullptr);
+    flag_write_kernel<uint64_t><<<kCompactBlocks, 256, 0, st>>>(flags, (uint64_t)total3, cnt, rk);
     PCK(cudaGetLastError());
     int32_t got = 0;
     PCK(cudaMemcpyAsync(&got, nn, 4, cudaMemcpyDeviceToHost, st));
@@ -317,17 +320,21 @@ epi_status rank_and_select(epi_dataset *ds, epi_mlp *net, const DevData &d, cons
     cudaStream_t st = epi_ctx_stream(ctx);
     size_t free_b = 0, total_b = 0;
     PCK(cudaMemGetInfo(&free_b, &total_b));
-    const size_t need = (size_t)total * 5 + (size_t)chunk * n_feat * 4 + (size_t)R * 12 + ((size_t)1 << 30);
+    const size_t need = (size_t)total * 5 + (size_t)chunk * (n_feat * 4 + 4) + (size_t)R * 12 + ((size_t)1 << 30);
     if (need > free_b) return pfail(EPI_ENOMEM, "epi_proposer_search: the candidate space's scores do not fit in device memory");
     float *score, *X;
     uint8_t *keep;
-    unsigned long long *kept_dev;
-    int32_t *nsel;
+    unsigned long long *kept_dev, *ccnt;
+    int32_t *nsel, *nkept;
+    uint32_t *kidx;
     uint64_t *sel;
     void *scratch;
     PCK(pool.get(&score, total));
     PCK(pool.get(&keep, total));
     PCK(pool.get(&X, (size_t)chunk * n_feat));
+    PCK(pool.get(&kidx, chunk));
+    PCK(pool.get(&ccnt, kCompactBlocks));
+    PCK(pool.get(&nkept, 1));
     PCK(pool.get(&kept_dev, 1));
     PCK(pool.get(&nsel, 1));
     PCK(pool.get(&sel, R));
@@ -337,8 +344,21 @@ epi_status rank_and_select(epi_dataset *ds, epi_mlp *net, const DevData &d, cons
         const int64_t cnt = (int64_t)std::min<uint64_t>((uint64_t)chunk, total - first);
         PCK(launch_cand_features5(d, triples, (int64_t)first, cnt, L.s[1], L.s[2], L.s[3], L.s[4], X, keep + first,
                                   nullptr, st));
-        if (net) PST(epi_mlp_forward(net, X, cnt, score + first));
-        else PST(epi_heuristic5(ctx, X, cnt, n_feat, score + first));
+        if (net) {
+            // the network only for the kept rows (a set is ranked once):
+            // their chunk positions in order, then gathered and scattered by
+            // the fused kernel; where it does not apply, every row
+            flag_count_kernel<<<kCompactBlocks, 256, 0, st>>>(keep + first, (uint64_t)cnt, ccnt);
+            flag_scan_kernel<<<1, kCompactBlocks, 0, st>>>(ccnt, nkept);
+            flag_write_kernel<uint32_t><<<kCompactBlocks, 256, 0, st>>>(keep + first, (uint64_t)cnt, ccnt, kidx);
+            PCK(cudaGetLastError());
+            launches += 3;
+            const epi_status fs = mlp_forward_rows(net, X, cnt, kidx, nkept, score + first);
+            if (fs == EPI_EUNSUPPORTED) PST(epi_mlp_forward(net, X, cnt, score + first));
+            else PST(fs);
+        } else {
+            PST(epi_heuristic5(ctx, X, cnt, n_feat, score + first));
+        }
         count_kernel<<<grid_for(cnt), 256, 0, st>>>(keep + first, cnt, kept_dev);
         launches += 3;
     }

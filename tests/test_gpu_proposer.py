@@ -76,12 +76,15 @@ def _direct_proposals(epi, ctx, ds, n, T, R, scorer, quad=False):
     return combs.cpu().numpy()[idx], int(k.sum())
 
 
-@pytest.mark.parametrize("use_net,quad", [(False, False), (True, False), (False, True), (True, True)])
-def test_proposals_are_best_ranked_and_exact(epi, ctx, use_net, quad):
+@pytest.mark.parametrize("use_net,quad,hidden", [(False, False, 0), (True, False, 64), (False, True, 0),
+                                                (True, True, 64), (True, False, 256), (True, True, 256)])
+def test_proposals_are_best_ranked_and_exact(epi, ctx, use_net, quad, hidden):
+    # hidden 256: the fused tensor-core network, run on the kept rows only
+    # (gathered and scattered); hidden 64: the CUDA-core layers on every row
     n, T, R, top_n = 40, 50, 300, 60
     geno, pheno = random_data(n, 800, seed=23)
     ds = epi.Dataset(ctx, geno, pheno)
-    net = epi.MLP(ctx, 30 if quad else 25, 64, seed=4) if use_net else None
+    net = epi.MLP(ctx, 30 if quad else 25, hidden, seed=4) if use_net else None
     scorer = (lambda X: net.forward(X)) if use_net else (lambda X: epi.heuristic5(ctx, X))
     # small chunks: many passes
     r, st = epi.proposer_search(ds, net, T, R, top_n, chunk=4097, with_counts=True, quad_features=quad)
@@ -198,12 +201,12 @@ def test_large_budget_covering_every_set_is_exhaustive(epi, ctx):
     check_topn(r.combs, r.mi, oc, om)
 
 
-@pytest.mark.parametrize("use_net", [False, True])
-def test_large_budget_proposals_follow_the_ranking(epi, ctx, use_net):
+@pytest.mark.parametrize("use_net,hidden", [(False, 0), (True, 64), (True, 256)])
+def test_large_budget_proposals_follow_the_ranking(epi, ctx, use_net, hidden):
     n, T, R, top_n = 40, 128, 20000, 100
     geno, pheno = random_data(n, 900, seed=31)
     ds = epi.Dataset(ctx, geno, pheno)
-    net = epi.MLP(ctx, 25, 64, seed=5) if use_net else None
+    net = epi.MLP(ctx, 25, hidden, seed=5) if use_net else None
     scorer = (lambda X: net.forward(X)) if use_net else (lambda X: epi.heuristic5(ctx, X))
     r, st = epi.proposer_search(ds, net, T, R, top_n, chunk=10007)
     # the same ranking from the single-step calls: the R best kept
