@@ -261,7 +261,7 @@ def measure_proposer(epi, ctx, ds, peaks, top_triples=256, budget=4096):
     flops = X.shape[0] * 2.0 * (25 * 256 + 256 * 256 + 256)
     out["mlp_inference"] = dict(rows_per_s=X.shape[0] / t, tflops=flops / t / 1e12,
                                 frac_of_bf16_peak=flops / t / 1e12 / peaks["bf16"],
-                                note="2*(25*256+256*256+256) flop per row; K of layer 1 padded to 64 on the device")
+                                note="2*(25*256+256*256+256) flop per row; K of layer 1 padded to 32 on the device")
     net.close()
     return out
 
