@@ -216,7 +216,8 @@ __global__ void __launch_bounds__(256) flag_count_kernel(const uint8_t *__restri
 }
 
 __global__ void __launch_bounds__(kCompactBlocks) flag_scan_kernel(unsigned long long *__restrict__ cnt,
-                                                                   int32_t *__restrict__ total)
+                                                                   int32_t *__restrict__ total,
+                                                                   unsigned long long *__restrict__ running)
 {
     __shared__ unsigned long long s[kCompactBlocks];
     const int t = threadIdx.x;
@@ -230,7 +231,10 @@ __global__ void __launch_bounds__(kCompactBlocks) flag_scan_kernel(unsigned long
         __syncthreads();
     }
     cnt[t] = s[t] - own;   // exclusive
-    if (total && t == kCompactBlocks - 1) *total = (int32_t)s[t];
+    if (t == kCompactBlocks - 1) {
+        if (total) *total = (int32_t)s[t];
+        if (running) *running += s[t];     // one thread: a running count over calls
+    }
 }
 
 template <typename T>
@@ -291,7 +295,7 @@ epi_status best_triples(epi_dataset *ds, Pool &pool, const float *s3, int T, uin
     PCK(cudaMemsetAsync(flags, 0, (size_t)total3, st));
     flag_set_kernel<<<grid_for(T), 256, 0, st>>>(flags, sel, T);
     flag_count_kernel<<<kCompactBlocks, 256, 0, st>>>(flags, (uint64_t)total3, cnt);
-    flag_scan_kernel<<<1, kCompactBlocks, 0, st>>>(cnt, nullptr);
+    flag_scan_kernel<<<1, kCompactBlocks, 0, st>>>(cnt, nullptr, nullptr);
     flag_write_kernel<uint64_t><<<kCompactBlocks, 256, 0, st>>>(flags, (uint64_t)total3, cnt, rk);
     PCK(cudaGetLastError());
     int32_t got = 0;
@@ -349,7 +353,7 @@ epi_status rank_and_select(epi_dataset *ds, epi_mlp *net, const DevData &d, cons
             // their chunk positions in order, then gathered and scattered by
             // the fused kernel; where it does not apply, every row
             flag_count_kernel<<<kCompactBlocks, 256, 0, st>>>(keep + first, (uint64_t)cnt, ccnt);
-            flag_scan_kernel<<<1, kCompactBlocks, 0, st>>>(ccnt, nkept);
+            flag_scan_kernel<<<1, kCompactBlocks, 0, st>>>(ccnt, nkept, kept_dev);
             flag_write_kernel<uint32_t><<<kCompactBlocks, 256, 0, st>>>(keep + first, (uint64_t)cnt, ccnt, kidx);
             PCK(cudaGetLastError());
             launches += 3;
@@ -358,9 +362,10 @@ epi_status rank_and_select(epi_dataset *ds, epi_mlp *net, const DevData &d, cons
             else PST(fs);
         } else {
             PST(epi_heuristic5(ctx, X, cnt, n_feat, score + first));
+            count_kernel<<<grid_for(cnt), 256, 0, st>>>(keep + first, cnt, kept_dev);
+            launches += 1;
         }
-        count_kernel<<<grid_for(cnt), 256, 0, st>>>(keep + first, cnt, kept_dev);
-        launches += 3;
+        launches += 2;
     }
     // the proposals: the R best kept candidates (an unordered set)
     PCK(launch_topk(score, keep, (int64_t)total, (int64_t)R, scratch, false, nullptr, sel, nsel, epi_ctx_num_sms(ctx),
