@@ -383,7 +383,17 @@ def run_ours(args):
         if args.proposer_eval:
             comp["proposer_order5/recall_200snp_2000"] = proposer_eval.evaluate(ctx)
         else:
-            comp["proposer_order5/recall_200snp_2000_quick"] = proposer_eval.quick(ctx)
+            q = proposer_eval.quick(ctx)
+            comp["proposer_order5/recall_200snp_2000_quick"] = q
+            # the metric's second part: recall@100 of the exhaustive order-5
+            # top-100 among the proposer's top-100 (30 features, network)
+            best = [r for r in q["results"] if r["ranking"] == "network"]
+            line["recall_k5"] = dict(value=best[-1]["recall_at_100"], budget=best[-1]["budget"],
+                                     by_budget={str(r["budget"]): r["recall_at_100"] for r in best},
+                                     heuristic={str(r["budget"]): r["recall_at_100"] for r in q["results"]
+                                                if r["ranking"] == "heuristic"},
+                                     workload="200 SNPs x 2000 samples, held-out synthetic dataset, "
+                                              "T = 65536 expanded triples")
         line["compare"] = comp
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
