@@ -162,6 +162,7 @@ uint64_t tune_key(int k, int64_t n, int32_t wt)
 struct SearchPlan {
     int k = 0, top_n = 0, pool = 0, tile = 0, slots = 0, cand_p2 = 0, grid = 0, R = 0;
     bool tc = false;
+    bool global_prefix = false;    // popcount path: prefix tables in a global buffer (orders 7-8)
     float *all_scores = nullptr;   // optional: every combination's score (popcount path)
     size_t smem = 0;
     uint64_t rb = 0, re = 0, total = 0;
@@ -207,6 +208,25 @@ epi_status plan_popc(const epi_dataset *ds, SearchPlan &p, int R_req = 0)
                 best_score = score;
                 p.tile = tile; p.cand_p2 = cand_p2; p.slots = s; p.smem = sm; p.grid = occ;
             }
+        }
+    }
+    p.global_prefix = false;
+    if (best_score < 0 && popc_global_prefix_ok(p.k, p.R)) {
+        // one prefix table exceeds shared memory: it is materialised in a
+        // per-CTA global buffer; at most two CTAs per SM, so that the CTAs'
+        // tables stay resident in L2 and the threads of a CTA, which walk
+        // the same rows, share them through L1
+        for (int tile : {256, 128}) {
+            if (tune_tile && tile != tune_tile) continue;
+            const int cand_p2 = next_pow2(p.pool + 2 * tile);
+            const size_t sm = popc_smem_bytes(p.k, ds->Wt, 1, cand_p2, true) + 1024;
+            if (sm > limit) continue;
+            const int occ = popc_max_active(p.k, p.R, sm, true);
+            if (occ <= 0) continue;
+            p.tile = tile; p.cand_p2 = cand_p2; p.slots = 1; p.smem = sm; p.grid = std::min(occ, 2);
+            p.global_prefix = true;
+            best_score = 0;
+            break;
         }
     }
     if (best_score < 0)
@@ -284,6 +304,8 @@ epi_status queue_search(epi_dataset *ds, const SearchPlan &p, int path, epi_resu
     const size_t o_mi = a.take<double>((size_t)p.pool);
     const size_t o_cb = a.take<int32_t>((size_t)p.pool * p.k);
     const size_t o_ic = a.take<uint64_t>((size_t)ds->n + 1);
+    const size_t o_pre =
+        p.global_prefix ? a.take<uint32_t>((size_t)p.grid * p.slots * popc_slot_words(p.k, ds->Wt)) : 0;
     epi_status st = ensure_scratch(ctx, a.off);
     if (st != EPI_OK) return st;
     char *base = static_cast<char *>(ctx->scratch);
@@ -328,7 +350,8 @@ epi_status queue_search(epi_dataset *ds, const SearchPlan &p, int path, epi_resu
         ctx->launches += 1;   // item table
     } else {
         CK(launch_popc_search(d, p.k, p.R, p.rb, p.re, p.tile, p.pool, p.slots, p.cand_p2, thr, ls, lr, lc, p.grid,
-                              p.smem, ctx->stream, p.all_scores));
+                              p.smem, ctx->stream, p.all_scores,
+                              p.global_prefix ? reinterpret_cast<uint32_t *>(base + o_pre) : nullptr));
     }
     if (ev1) CK(cudaEventRecord(ev1, ctx->stream));
     CK(launch_merge(ls, lr, lc, p.grid, p.pool, p.pool, cs, cr, cn, ctx->stream));

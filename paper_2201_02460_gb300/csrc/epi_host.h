@@ -32,14 +32,17 @@ void launch_binom(int64_t n, uint64_t *tab, int num_sms, cudaStream_t st);
 
 // epi_popc.cu
 bool popc_row_group_ok(int k, int R);
+bool popc_global_prefix_ok(int k, int R);
 int popc_default_row_group(int k);
 int popc_slot_words(int k, int32_t Wt);
-size_t popc_smem_bytes(int k, int32_t Wt, int slots, int cand_p2);
-int popc_max_active(int k, int R, size_t smem);
+// shared memory of one CTA; with global_prefix the prefix tables live in a
+// global buffer of grid x slots x popc_slot_words words instead
+size_t popc_smem_bytes(int k, int32_t Wt, int slots, int cand_p2, bool global_prefix = false);
+int popc_max_active(int k, int R, size_t smem, bool global_prefix = false);
 cudaError_t launch_popc_search(const DevData &d, int k, int R, uint64_t rank_begin, uint64_t rank_end, int tile,
                                int pool, int slots, int cand_p2, uint32_t *global_thr, float *list_score,
                                uint64_t *list_rank, int32_t *list_count, int grid, size_t smem, cudaStream_t st,
-                               float *all_scores = nullptr);
+                               float *all_scores = nullptr, uint32_t *pre_global = nullptr);
 // batched: one launch over several datasets of order k (descriptors in device memory)
 size_t popc_ds_bytes();
 void popc_fill_ds(void *dst, const DevData &d, uint64_t rank_begin, uint64_t rank_end, int cta_begin, int cta_count,

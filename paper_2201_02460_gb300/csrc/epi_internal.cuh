@@ -18,7 +18,8 @@
 
 namespace epi {
 
-constexpr int kMaxOrderGpu = 5;          // orders with specialised kernels
+constexpr int kMaxOrderGpu = 8;          // orders of the popcount search kernels
+constexpr int kMaxOrderTc = 5;           // orders of the tensor-core search
 constexpr int kMaxPoolLists = 8192;      // entries of one candidate list
 constexpr uint64_t kBinomSaturated = ~0ull;
 

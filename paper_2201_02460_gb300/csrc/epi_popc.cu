@@ -20,13 +20,24 @@
 //     the work);
 //   * the counts never leave registers: MI is evaluated in the same thread
 //     and compared against the CTA's current threshold; survivors go to a
-//     shared-memory buffer that is merged into the CTA's sorted list.
+//     shared-memory buffer that is merged into the CTA's sorted list;
+//   * orders 6-8: the same kernel; where one prefix table (3^(k-1) rows) does
+//     not fit in shared memory (order 8, or order 7 with many samples) it is
+//     materialised in a per-CTA global buffer instead (the paper's stored
+//     `combine` table, Section 2.1), read through L1/L2 by the CTA's threads,
+//     which walk the same prefix rows together.
 #include "epi_internal.cuh"
 #include "epi_host.h"
 
 namespace epi {
 
 __host__ __device__ constexpr int ipow3(int k) { return k <= 0 ? 1 : 3 * ipow3(k - 1); }
+
+// Words between consecutive rows of a staged prefix table.  Orders 6-8 read
+// the table with one lane per row (a warp per combination), so the stride is
+// made an odd number of 16-byte units: the 32 lanes' uint4 loads of one word
+// position then spread over all banks.
+__host__ __device__ inline int popc_row_stride(int k, int32_t Wt) { return k >= 6 && (Wt & 4) == 0 ? Wt + 4 : Wt; }
 
 // One dataset of a launch.  A launch may cover several datasets of the same
 // order (batched search): CTAs [cta_begin, cta_begin + cta_count) of the grid
@@ -51,6 +62,8 @@ struct PopcParams {
     uint64_t *list_rank;            // [grid][pool]
     int32_t *list_count;            // [grid]
     float *all_scores;              // optional: every score, [rank - rank_begin] (single dataset)
+    uint32_t *pre_global;           // global prefix tables: [grid][pre_cta_words] (global-prefix kernels)
+    int64_t pre_cta_words;
 };
 
 struct SlotInfo {
@@ -158,18 +171,78 @@ __device__ inline void flush_list(SubtileState &S, float *sc, uint64_t *rk, int 
     __syncthreads();
 }
 
-template <int K, int R>
+// Exact FP32 MI of one combination by one warp (orders 6-8): lane l takes
+// the prefix rows l, l + 32, ... four at a time, counts them against the last
+// SNP's genotype-0/1 rows (the same words for every lane: broadcast loads),
+// derives genotype 2 from the row totals, sums its cell terms, and the warp
+// adds the lanes' sums.
+template <int K>
+__device__ __forceinline__ float score_popc_warp(const uint32_t *__restrict__ pre, int rstride,
+                                                 const uint32_t *__restrict__ tot, const uint32_t *__restrict__ mj,
+                                                 const DevData &d, const MiConstF32 &mc, int lane)
+{
+    constexpr int PR = ipow3(K - 1);
+    SumF32 acc;
+#pragma unroll 1
+    for (int r0 = lane; r0 < PR; r0 += 4 * 32) {
+        const uint32_t *rp[4];
+#pragma unroll
+        for (int i = 0; i < 4; i++) rp[i] = pre + (size_t)min(r0 + 32 * i, PR - 1) * rstride;
+        uint32_t a0[4] = {0, 0, 0, 0}, a1[4] = {0, 0, 0, 0}, b0[4] = {0, 0, 0, 0}, b1[4] = {0, 0, 0, 0};
+#pragma unroll 2
+        for (int w = 0; w < d.W1; w += 4) {
+            const uint4 x = __ldg(reinterpret_cast<const uint4 *>(mj + w));
+            const uint4 y = __ldg(reinterpret_cast<const uint4 *>(mj + d.Wt + w));
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                const uint4 p = *reinterpret_cast<const uint4 *>(rp[i] + w);
+                a0[i] += popc4(p, x);
+                a1[i] += popc4(p, y);
+            }
+        }
+#pragma unroll 2
+        for (int w = d.W1; w < d.Wt; w += 4) {
+            const uint4 x = __ldg(reinterpret_cast<const uint4 *>(mj + w));
+            const uint4 y = __ldg(reinterpret_cast<const uint4 *>(mj + d.Wt + w));
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                const uint4 p = *reinterpret_cast<const uint4 *>(rp[i] + w);
+                b0[i] += popc4(p, x);
+                b1[i] += popc4(p, y);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const int r = r0 + 32 * i;
+            if (r < PR) {
+                const uint32_t t1 = tot[r * 2 + 0], t0 = tot[r * 2 + 1];
+                acc.add(cell_terms_f32(a0[i], b0[i], mc));
+                acc.add(cell_terms_f32(a1[i], b1[i], mc));
+                acc.add(cell_terms_f32(t1 - a0[i] - a1[i], t0 - b0[i] - b1[i], mc));
+            }
+        }
+    }
+    float v = acc.value();
+#pragma unroll
+    for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return __fdiv_rn(v, mc.fm);
+}
+
+template <int K, int R, bool GP>
 __global__ void __launch_bounds__(128) popc_search_kernel(PopcParams P)
 {
     constexpr int PR = ipow3(K - 1);
+    constexpr bool kWarpPerComb = K >= 6;
     const PopcDs &D = P.many ? P.many[P.cta_ds[blockIdx.x]] : P.one;
     const DevData d = D.d;
-    const int slot_words = PR * d.Wt + 4;   // 16-byte skew: slots start on different banks
+    const int rstride = popc_row_stride(K, d.Wt);
+    const int slot_words = PR * rstride + 4;   // 16-byte skew: slots start on different banks
     extern __shared__ __align__(16) unsigned char smem[];
-    // layout: prefix rows | totals | candidate scores | candidate ranks
-    uint32_t *pre = reinterpret_cast<uint32_t *>(smem);
-    const size_t pre_words = (size_t)P.slots * (PR * P.max_wt + 4);
-    uint32_t *tot = pre + pre_words;
+    // layout: prefix rows (unless global) | totals | candidate scores | candidate ranks
+    const size_t pre_words = GP ? 0 : (size_t)P.slots * (PR * popc_row_stride(K, P.max_wt) + 4);
+    uint32_t *pre = GP ? P.pre_global + (size_t)blockIdx.x * (size_t)P.pre_cta_words
+                       : reinterpret_cast<uint32_t *>(smem);
+    uint32_t *tot = reinterpret_cast<uint32_t *>(smem) + pre_words;
     uint64_t *rk = reinterpret_cast<uint64_t *>(smem + (((pre_words + (size_t)P.slots * PR * 2) * 4 + 15) & ~(size_t)15));
     float *sc = reinterpret_cast<float *>(rk + P.cand_p2);
     __shared__ SlotInfo slot[8];
@@ -270,14 +343,14 @@ __global__ void __launch_bounds__(128) popc_search_kernel(PopcParams P)
                     acc.x &= v.x; acc.y &= v.y; acc.z &= v.z; acc.w &= v.w;
                 }
             }
-            reinterpret_cast<uint4 *>(pre + (size_t)s * slot_words + (size_t)row * d.Wt)[w4] = acc;
+            reinterpret_cast<uint4 *>(pre + (size_t)s * slot_words + (size_t)row * rstride)[w4] = acc;
         }
         __syncthreads();
         // per-row totals of each subtable (the third genotype by subtraction)
         for (int idx = threadIdx.x; idx < ns * PR * 2; idx += blockDim.x) {
             const int half = idx & 1;
             const int sr = idx >> 1;
-            const uint32_t *row = pre + (size_t)(sr / PR) * slot_words + (size_t)(sr % PR) * d.Wt;
+            const uint32_t *row = pre + (size_t)(sr / PR) * slot_words + (size_t)(sr % PR) * rstride;
             uint32_t c = 0;
             const int wb = half ? d.W1 : 0, we = half ? d.Wt : d.W1;
             for (int w = wb; w < we; w++) c += __popc(row[w]);
@@ -289,6 +362,25 @@ __global__ void __launch_bounds__(128) popc_search_kernel(PopcParams P)
         const int64_t F = S.F, F_end = S.F_end;
         const int list_len = S.list_len;
         const float thr = S.thr;
+        if constexpr (kWarpPerComb) {
+            // one warp per combination
+            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+            for (int64_t f = F + warp; f < F_end; f += blockDim.x >> 5) {
+                int s = 0;
+                while (s + 1 < ns && f >= slot[s + 1].base) s++;
+                const int32_t j = slot[s].s_last + 1 + (int32_t)(f - slot[s].base);
+                const float score = score_popc_warp<K>(pre + (size_t)s * slot_words, rstride, tot + s * PR * 2,
+                                                       d.masks + (int64_t)j * 3 * d.Wt, d, mc, lane);
+                if (lane == 0) {
+                    if (P.all_scores) P.all_scores[f - (int64_t)D.rank_begin] = score;
+                    if (score >= thr) {
+                        const int pos = list_len + atomicAdd(&S.nbuf, 1);
+                        sc[pos] = score;
+                        rk[pos] = (uint64_t)f;
+                    }
+                }
+            }
+        } else
         for (int64_t f = F + threadIdx.x; f < F_end; f += blockDim.x) {
             int s = 0;
             while (s + 1 < ns && f >= slot[s + 1].base) s++;
@@ -319,20 +411,20 @@ __global__ void __launch_bounds__(128) popc_search_kernel(PopcParams P)
     if (threadIdx.x == 0) P.list_count[blockIdx.x] = L;
 }
 
-template <int K, int R>
+template <int K, int R, bool GP>
 static cudaError_t launch_kr(const PopcParams &p, int grid, size_t smem, cudaStream_t st)
 {
-    auto kern = popc_search_kernel<K, R>;
+    auto kern = popc_search_kernel<K, R, GP>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, 128, smem, st>>>(p);
     return cudaGetLastError();
 }
 
-template <int K, int R>
+template <int K, int R, bool GP>
 static int occupancy_kr(size_t smem)
 {
-    auto kern = popc_search_kernel<K, R>;
+    auto kern = popc_search_kernel<K, R, GP>;
     int n = 0;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, 128, smem) != cudaSuccess) return 0;
@@ -348,9 +440,15 @@ bool popc_row_group_ok(int k, int R)
     case 3: return R == 9;
     case 4: return R == 9 || R == 27;
     case 5: return R == 9 || R == 27;
+    case 6: return R == 9;
+    case 7: return R == 9;
+    case 8: return R == 9;
     default: return false;
     }
 }
+
+// orders whose prefix tables may also live in global memory
+bool popc_global_prefix_ok(int k, int R) { return (k == 7 || k == 8) && R == 9; }
 
 int popc_default_row_group(int k)
 {
@@ -359,40 +457,61 @@ int popc_default_row_group(int k)
 
 int popc_slot_words(int k, int32_t Wt)
 {
-    return ipow3(k - 1) * Wt + 4;   // 16-byte skew: slots start on different banks
+    return ipow3(k - 1) * popc_row_stride(k, Wt) + 4;   // 16-byte skew: slots start on different banks
 }
 
-size_t popc_smem_bytes(int k, int32_t Wt, int slots, int cand_p2)
+size_t popc_smem_bytes(int k, int32_t Wt, int slots, int cand_p2, bool global_prefix)
 {
     const size_t PR = (size_t)ipow3(k - 1);
-    size_t b = (((size_t)slots * popc_slot_words(k, Wt) + (size_t)slots * PR * 2) * 4 + 15) & ~(size_t)15;
+    const size_t pre = global_prefix ? 0 : (size_t)slots * popc_slot_words(k, Wt);
+    size_t b = ((pre + (size_t)slots * PR * 2) * 4 + 15) & ~(size_t)15;
     return b + (size_t)cand_p2 * 12;
 }
 
-int popc_max_active(int k, int R, size_t smem)
+int popc_max_active(int k, int R, size_t smem, bool global_prefix)
 {
+    if (global_prefix) {
+        switch (k * 100 + R) {
+        case 709: return occupancy_kr<7, 9, true>(smem);
+        case 809: return occupancy_kr<8, 9, true>(smem);
+        default: return 0;
+        }
+    }
     switch (k * 100 + R) {
-    case 101: return occupancy_kr<1, 1>(smem);
-    case 203: return occupancy_kr<2, 3>(smem);
-    case 309: return occupancy_kr<3, 9>(smem);
-    case 409: return occupancy_kr<4, 9>(smem);
-    case 427: return occupancy_kr<4, 27>(smem);
-    case 509: return occupancy_kr<5, 9>(smem);
-    case 527: return occupancy_kr<5, 27>(smem);
+    case 101: return occupancy_kr<1, 1, false>(smem);
+    case 203: return occupancy_kr<2, 3, false>(smem);
+    case 309: return occupancy_kr<3, 9, false>(smem);
+    case 409: return occupancy_kr<4, 9, false>(smem);
+    case 427: return occupancy_kr<4, 27, false>(smem);
+    case 509: return occupancy_kr<5, 9, false>(smem);
+    case 527: return occupancy_kr<5, 27, false>(smem);
+    case 609: return occupancy_kr<6, 9, false>(smem);
+    case 709: return occupancy_kr<7, 9, false>(smem);
+    case 809: return occupancy_kr<8, 9, false>(smem);
     default: return 0;
     }
 }
 
 static cudaError_t launch_dispatch(const PopcParams &p, int k, int R, int grid, size_t smem, cudaStream_t st)
 {
+    if (p.pre_global) {
+        switch (k * 100 + R) {
+        case 709: return launch_kr<7, 9, true>(p, grid, smem, st);
+        case 809: return launch_kr<8, 9, true>(p, grid, smem, st);
+        default: return cudaErrorInvalidValue;
+        }
+    }
     switch (k * 100 + R) {
-    case 101: return launch_kr<1, 1>(p, grid, smem, st);
-    case 203: return launch_kr<2, 3>(p, grid, smem, st);
-    case 309: return launch_kr<3, 9>(p, grid, smem, st);
-    case 409: return launch_kr<4, 9>(p, grid, smem, st);
-    case 427: return launch_kr<4, 27>(p, grid, smem, st);
-    case 509: return launch_kr<5, 9>(p, grid, smem, st);
-    case 527: return launch_kr<5, 27>(p, grid, smem, st);
+    case 101: return launch_kr<1, 1, false>(p, grid, smem, st);
+    case 203: return launch_kr<2, 3, false>(p, grid, smem, st);
+    case 309: return launch_kr<3, 9, false>(p, grid, smem, st);
+    case 409: return launch_kr<4, 9, false>(p, grid, smem, st);
+    case 427: return launch_kr<4, 27, false>(p, grid, smem, st);
+    case 509: return launch_kr<5, 9, false>(p, grid, smem, st);
+    case 527: return launch_kr<5, 27, false>(p, grid, smem, st);
+    case 609: return launch_kr<6, 9, false>(p, grid, smem, st);
+    case 709: return launch_kr<7, 9, false>(p, grid, smem, st);
+    case 809: return launch_kr<8, 9, false>(p, grid, smem, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -400,10 +519,12 @@ static cudaError_t launch_dispatch(const PopcParams &p, int k, int R, int grid, 
 cudaError_t launch_popc_search(const DevData &d, int k, int R, uint64_t rank_begin, uint64_t rank_end, int tile,
                                int pool, int slots, int cand_p2, uint32_t *global_thr, float *list_score,
                                uint64_t *list_rank, int32_t *list_count, int grid, size_t smem, cudaStream_t st,
-                               float *all_scores)
+                               float *all_scores, uint32_t *pre_global)
 {
     PopcParams p;
     p.all_scores = all_scores;
+    p.pre_global = pre_global;
+    p.pre_cta_words = (int64_t)slots * popc_slot_words(k, d.Wt);
     p.one.d = d;
     p.one.rank_begin = rank_begin;
     p.one.rank_end = rank_end;
@@ -443,6 +564,8 @@ cudaError_t launch_popc_batch(const void *ds_dev, const int32_t *cta_ds_dev, int
 {
     PopcParams p;
     p.all_scores = nullptr;
+    p.pre_global = nullptr;
+    p.pre_cta_words = 0;
     p.one = PopcDs();
     p.many = static_cast<const PopcDs *>(ds_dev);
     p.cta_ds = cta_ds_dev;

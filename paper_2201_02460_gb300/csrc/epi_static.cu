@@ -96,7 +96,7 @@ extern "C" epi_status epi_search_static(const uint8_t *geno_dev, const uint8_t *
     if (n_snps < 1 || n_samples < 1 || n_samples > (1 << 23) - 1 || n_snps > (1 << 24))
         return bad(EPI_EINVAL, "epi_search_static: need 1 <= n_snps <= 2^24 and 1 <= n_samples < 2^23");
     if (n_cases < 0 || n_cases > n_samples) return bad(EPI_EINVAL, "epi_search_static: n_cases outside 0..n_samples");
-    if (order < 1 || order > kMaxOrderGpu || order > n_snps)
+    if (order < 1 || order > kMaxOrderTc || order > n_snps)
         return bad(EPI_EINVAL, "epi_search_static: order must lie in 1..min(5, n_snps)");
     if (top_n < 1 || top_n > 1024) return bad(EPI_EINVAL, "epi_search_static: top_n outside 1..1024");
     const uint64_t total = host_binom(n_snps, order);

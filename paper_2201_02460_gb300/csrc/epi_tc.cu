@@ -204,7 +204,7 @@ __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"
 // panel order: panel c holds the C(c, k-2) subsets ending in c, ordered
 // colexicographically by their first k-2 SNPs; panel c starts at C(c, k-1).
 struct PrefixIter {
-    int32_t a[kMaxOrderGpu];   // first k-2 SNPs (ascending)
+    int32_t a[kMaxOrderTc];    // first k-2 SNPs (ascending)
     int32_t c;                 // last prefix SNP (panel)
     uint64_t q;                // index in panel order
 };

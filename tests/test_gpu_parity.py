@@ -86,6 +86,31 @@ def test_search_small(epi, ctx, k, n, m, top_n):
     _check_result(r, geno, pheno, oc, om)
 
 
+# Orders 6-8 (popcount path; the tensor path stops at 5).  Sizes chosen so
+# that both placements of the prefix tables run: shared memory (order 7 at 700
+# samples: 729 rows x 24 words; order 8 at 200: 2187 x 8) and the per-CTA
+# global buffer (order 7 at 3000: 729 x 96 words; order 8 at 1000: 2187 x 32).
+@pytest.mark.parametrize("k,n,m,m1,top_n", [
+    (6, 14, 300, None, 40), (6, 12, 129, 40, 20), (7, 13, 700, None, 30), (7, 11, 3000, 1500, 20),
+    (8, 12, 200, None, 25), (8, 11, 1000, 500, 15),
+])
+def test_search_high_orders(epi, ctx, k, n, m, m1, top_n):
+    geno, pheno = random_data(n, m, seed=13 * k + n, m1=m1)
+    ds, r, oc, om, _ = _search_both(epi, ctx, geno, pheno, k, top_n)
+    _check_result(r, geno, pheno, oc, om)
+
+
+@pytest.mark.parametrize("k,m,m1", [(7, 3000, 1500), (8, 200, None)])
+def test_search_range_high_orders(epi, ctx, k, m, m1):
+    n = 14 if k == 7 else 13
+    geno, pheno = random_data(n, m, seed=31 + k, m1=m1)
+    total = O.binom(n, k)
+    for r0, r1 in [(0, 1), (17, 1000), (total - 100, total + 10)]:
+        ds, r, oc, om, _ = _search_both(epi, ctx, geno, pheno, k, 20, rank_range=(r0, r1))
+        _check_result(r, geno, pheno, oc, om)
+        assert all(r0 <= int(x) < r1 for x in r.rank)
+
+
 def test_search_with_exact_ties(epi, ctx):
     geno, pheno = random_data(24, 301, seed=99)
     geno[10] = geno[3]
@@ -180,7 +205,7 @@ def test_invalid_inputs(epi, ctx):
             epi.search(ds, k, n)
         assert e.value.status == epi.EPI_EINVAL
     with pytest.raises(epi.EpiError) as e:
-        epi.search(ds, 6, 5)
+        epi.search(ds, 6, 5, path="tc")
     assert e.value.status == epi.EPI_EUNSUPPORTED
     with pytest.raises(epi.EpiError):
         epi.tables(ds, np.array([[3, 3]], dtype=np.uint32))
