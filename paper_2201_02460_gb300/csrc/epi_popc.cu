@@ -312,6 +312,44 @@ __global__ void __launch_bounds__(128) popc_search_kernel(PopcParams P)
         // ---- stage prefix tables: row x' = sum_t g_t 3^(k-2-t) -------------
         const int ns = S.nslots;
         const int W4 = d.Wt >> 2;
+        if constexpr (K >= 6) {
+            // blocks of 9 rows that share the genotypes of the first k-3
+            // prefix SNPs: their AND is formed once, then the last two SNPs'
+            // rows (k + 3 loads per 9 rows instead of 9 (k - 1))
+            constexpr int PB = PR / 9;
+            for (int idx = threadIdx.x; idx < ns * PB * W4; idx += blockDim.x) {
+                const int w4 = idx % W4;
+                const int blk = (idx / W4) % PB;
+                const int s = idx / (W4 * PB);
+                uint4 base = make_uint4(~0u, ~0u, ~0u, ~0u);
+                int rem = blk;
+                int div = PB / 3;
+#pragma unroll
+                for (int t = 0; t < km1 - 2; t++) {
+                    const int g = rem / div;
+                    rem -= g * div;
+                    div = div > 1 ? div / 3 : 1;
+                    const uint4 v = __ldg(reinterpret_cast<const uint4 *>(
+                        d.masks + ((int64_t)slot[s].snp[t] * 3 + g) * d.Wt) + w4);
+                    base.x &= v.x; base.y &= v.y; base.z &= v.z; base.w &= v.w;
+                }
+                const uint4 *ma = reinterpret_cast<const uint4 *>(d.masks + (int64_t)slot[s].snp[km1 - 2] * 3 * d.Wt);
+                const uint4 *mb = reinterpret_cast<const uint4 *>(d.masks + (int64_t)slot[s].snp[km1 - 1] * 3 * d.Wt);
+                uint4 lb[3];
+#pragma unroll
+                for (int h = 0; h < 3; h++) lb[h] = __ldg(mb + h * W4 + w4);
+                uint32_t *ps = pre + (size_t)s * slot_words + (size_t)blk * 9 * rstride;
+#pragma unroll
+                for (int g = 0; g < 3; g++) {
+                    const uint4 a = __ldg(ma + g * W4 + w4);
+                    const uint4 b1 = make_uint4(base.x & a.x, base.y & a.y, base.z & a.z, base.w & a.w);
+#pragma unroll
+                    for (int h = 0; h < 3; h++)
+                        reinterpret_cast<uint4 *>(ps + (size_t)(g * 3 + h) * rstride)[w4] =
+                            make_uint4(b1.x & lb[h].x, b1.y & lb[h].y, b1.z & lb[h].z, b1.w & lb[h].w);
+                }
+            }
+        } else
         for (int idx = threadIdx.x; idx < ns * PR * W4; idx += blockDim.x) {
             const int w4 = idx % W4;
             const int row = (idx / W4) % PR;
