@@ -376,6 +376,16 @@ def run_ours(args):
                 comp["order4_500snp_8192/popc"] = dict(value=u4 / (p4["t_ms"] / 1e3), ms_per_step=p4["t_ms"],
                                                        roofline=roofline("popc", d4, k4, p4["kern_ms"], peaks))
             ds4.close()
+        if args.workload != "order8_23snp_2048":
+            # the order-8 row of Table 2 (popcount path, global prefix tables)
+            d8, k8, n8 = synth.make_workload("order8_23snp_2048")
+            ds8 = epi.Dataset(ctx, d8.geno, d8.pheno)
+            u8 = math.comb(d8.n_snps, k8) * d8.n_samples
+            m8 = time_search(epi, ctx, ds8, k8, n8, "popc", 2, 1, flush, stream)
+            comp["order8_23snp_2048/popc"] = dict(value=u8 / (m8["t_ms"] / 2 / 1e3), ms_per_step=m8["t_ms"] / 2,
+                                                  cells_per_s=math.comb(d8.n_snps, k8) * 3 ** k8 / (m8["t_ms"] / 2 / 1e3),
+                                                  roofline=roofline("popc", d8, k8, m8["kern_ms"], peaks))
+            ds8.close()
         comp["batch64/auto"] = measure_batch(epi, ctx, synth, args.batch_div)
         if d.n_snps >= 5:
             comp[f"proposer_order5/{args.workload}"] = measure_proposer(epi, ctx, ds, peaks)

@@ -192,6 +192,9 @@ WORKLOADS = {
     # order-4 search, 500 SNPs x 8192 samples, no plant
     "order4_500snp_8192": dict(n_snps=500, n_cases=4096, n_controls=4096, maf_lo=0.1,
                                plant_q=0, plant_e=0.0, order=4, top_n=100, seed=BASE_SEED + 3),
+    # order-8 search, 23 SNPs x 2048 samples (the order-8 row of Table 2), no plant
+    "order8_23snp_2048": dict(n_snps=23, n_cases=1024, n_controls=1024, maf_lo=0.05,
+                              plant_q=0, plant_e=0.0, order=8, top_n=100, seed=BASE_SEED + 8),
 }
 
 

@@ -111,6 +111,18 @@ def test_search_range_high_orders(epi, ctx, k, m, m1):
         assert all(r0 <= int(x) < r1 for x in r.rank)
 
 
+def test_workload_order8_table2_ranges(epi, ctx):
+    """The order-8 row of Table 2 (23 SNPs x 2048 samples) at full size, on
+    rank ranges the oracle covers quickly: the first, a middle and the last
+    3000 combinations."""
+    from paper_2201_02460_gb300 import synth
+    d, k, top_n = synth.make_workload("order8_23snp_2048")
+    total = O.binom(d.n_snps, k)
+    for r0 in (0, total // 2, total - 3000):
+        ds, r, oc, om, _ = _search_both(epi, ctx, d.geno, d.pheno, k, 25, rank_range=(r0, r0 + 3000))
+        _check_result(r, d.geno, d.pheno, oc, om)
+
+
 def test_search_with_exact_ties(epi, ctx):
     geno, pheno = random_data(24, 301, seed=99)
     geno[10] = geno[3]
