@@ -220,6 +220,20 @@ epi_status epi_search_static(const uint8_t *geno_dev, const uint8_t *pheno_dev, 
  * epi_score_tables.
  * ------------------------------------------------------------------------ */
 
+/* Thresholded output (the "significant association" branch of Fig. 1, in
+ * place of a top-N): every combination of `order` (1..8) whose double-
+ * precision MI (Eq. 1-3) is at least `threshold`, sorted by (MI desc, rank
+ * asc).  Every combination is scored in single precision by the popcount
+ * path (Section 2.2 counts, in passes of `chunk` ranks, 0 = 2^28, each pass
+ * holding 4 bytes per rank of device memory); those at or above
+ * threshold (1 - 2 b), b the FP32 bound of the exact top-N, are recounted and
+ * scored in double precision, which decides.  *n_found receives how many
+ * qualify; the best min(n_found, capacity) are written to host out [capacity]
+ * and, if counts is not NULL, their tables to host counts
+ * [capacity][2][3^order].  Synchronous on the context's stream. */
+epi_status epi_search_threshold(epi_dataset *ds, int order, double threshold, int64_t chunk, epi_result *out,
+                                int64_t capacity, uint32_t *counts, int64_t *n_found);
+
 /* Every combination's single-precision MI (Eq. 1-3), by lexicographic rank:
  * out_dev is device memory of C(n_snps, order) floats.  Orders 1..5. */
 epi_status epi_score_all(epi_dataset *ds, int order, float *out_dev);

@@ -908,6 +908,144 @@ epi_status epi_tune_load(epi_ctx *ctx, const char *path)
 
 const char *epi_last_error(void) { return g_err.c_str(); }
 
+epi_status epi_search_threshold(epi_dataset *ds, int order, double threshold, int64_t chunk, epi_result *out,
+                                int64_t capacity, uint32_t *counts, int64_t *n_found)
+{
+    uint64_t total = 0, re = UINT64_MAX;
+    epi_status st = check_search_args(ds, order, 1, EPI_PATH_POPC, 0, re, total);
+    if (st != EPI_OK) return st;
+    if (!n_found || capacity < 0 || (capacity > 0 && !out) || !std::isfinite(threshold) || chunk < 0)
+        return fail(EPI_EINVAL, "epi_search_threshold: bad argument");
+    *n_found = 0;
+    epi_ctx *ctx = ds->ctx;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(EPI_ECUDA, "cannot select device %d", ctx->device);
+    cudaStream_t sm = ctx->stream;
+    const DevData d = ds->dev();
+    const int cells = pow3i(order);
+    // FP32 screen: a combination with MI >= threshold scores at least
+    // threshold (1 - bound) in single precision (the bound covers the
+    // roundings of the 2 * 3^k terms); the FP64 value decides
+    const float thr32 = threshold > 0.0 ? (float)(threshold * (1.0 - 2.0 * f32_rel_bound(order))) : -INFINITY;
+    const uint64_t ch = chunk > 0 ? std::min<uint64_t>((uint64_t)chunk, total) : std::min<uint64_t>(total, 1ull << 28);
+    const int64_t slice = std::max<int64_t>(1, std::min<int64_t>(1 << 20, ((int64_t)256 << 20) / (8 * cells)));
+    float *scores = nullptr;
+    unsigned long long *n_dev = nullptr;
+    uint64_t *cand = nullptr;
+    uint32_t *combs = nullptr, *tabs = nullptr;
+    float *f32 = nullptr;
+    double *f64 = nullptr;
+    void *dout = nullptr;
+    uint64_t cand_cap = std::min<uint64_t>(ch, 1ull << 20);
+    struct Found {
+        uint64_t rank;
+        double mi;
+        float mi32;
+        std::vector<uint32_t> snp, tab;
+    };
+    std::vector<Found> found;
+    auto cleanup = [&]() {
+        for (void *q : {(void *)scores, (void *)n_dev, (void *)cand, (void *)combs, (void *)tabs, (void *)f32,
+                        (void *)f64, dout})
+            if (q) cudaFreeAsync(q, sm);
+        cudaStreamSynchronize(sm);
+    };
+#define TCK(call)                                                                    \
+    do {                                                                             \
+        cudaError_t e_ = (call);                                                     \
+        if (e_ != cudaSuccess) {                                                     \
+            cleanup();                                                               \
+            return fail(e_ == cudaErrorMemoryAllocation ? EPI_ENOMEM : EPI_ECUDA,    \
+                        "epi_search_threshold: %s", cudaGetErrorString(e_));         \
+        }                                                                            \
+    } while (0)
+    TCK(cudaMallocAsync((void **)&scores, (size_t)ch * 4, sm));
+    TCK(cudaMallocAsync((void **)&n_dev, 8, sm));
+    TCK(cudaMallocAsync((void **)&cand, (size_t)cand_cap * 8, sm));
+    TCK(cudaMallocAsync((void **)&combs, (size_t)slice * order * 4, sm));
+    TCK(cudaMallocAsync((void **)&tabs, (size_t)slice * 2 * cells * 4, sm));
+    TCK(cudaMallocAsync((void **)&f32, (size_t)slice * 4, sm));
+    TCK(cudaMallocAsync((void **)&f64, (size_t)slice * 8, sm));
+    TCK(cudaMallocAsync(&dout, 1024, sm));
+    std::vector<uint32_t> hc, ht;
+    std::vector<double> h64;
+    std::vector<float> h32;
+    std::vector<uint64_t> hr;
+    for (uint64_t rb = 0; rb < total; rb += ch) {
+        // every score of ranks [rb, rb + ch): the popcount path
+        SearchPlan p;
+        p.k = order; p.top_n = 1; p.pool = initial_pool(1); p.rb = rb; p.re = std::min(total, rb + ch); p.total = total;
+        st = plan_popc(ds, p);
+        if (st != EPI_OK) { cleanup(); return st; }
+        p.all_scores = scores;
+        int32_t *status = nullptr;
+        st = queue_search(ds, p, EPI_PATH_POPC, static_cast<epi_result *>(dout), nullptr,
+                          reinterpret_cast<int32_t *>(static_cast<char *>(dout) + 512), &status);
+        if (st != EPI_OK) { cleanup(); return st; }
+        const int64_t cnt = (int64_t)(p.re - p.rb);
+        // the candidates of the FP32 screen
+        unsigned long long nc = 0;
+        for (;;) {
+            TCK(cudaMemsetAsync(n_dev, 0, 8, sm));
+            TCK(launch_select_ge(scores, cnt, thr32, rb, cand, cand_cap, n_dev, ctx->num_sms, sm));
+            TCK(cudaMemcpyAsync(&nc, n_dev, 8, cudaMemcpyDeviceToHost, sm));
+            TCK(cudaStreamSynchronize(sm));
+            ctx->launches += 2;
+            if (nc <= cand_cap) break;
+            cudaFreeAsync(cand, sm);
+            cand = nullptr;
+            cand_cap = nc;
+            TCK(cudaMallocAsync((void **)&cand, (size_t)cand_cap * 8, sm));
+        }
+        // exact FP64 scores of the candidates, in slices
+        for (int64_t off = 0; off < (int64_t)nc; off += slice) {
+            const int64_t c = std::min<int64_t>(slice, (int64_t)nc - off);
+            TCK(launch_unrank(d, order, cand + off, c, combs, sm));
+            TCK(launch_tables(d, order, combs, c, tabs, ctx->num_sms, sm));
+            TCK(launch_score_tables(d, order, tabs, c, f32, f64, ctx->num_sms, sm));
+            ctx->launches += 3;
+            hr.resize(c); hc.resize((size_t)c * order); h64.resize(c); h32.resize(c);
+            TCK(cudaMemcpyAsync(hr.data(), cand + off, (size_t)c * 8, cudaMemcpyDeviceToHost, sm));
+            TCK(cudaMemcpyAsync(hc.data(), combs, (size_t)c * order * 4, cudaMemcpyDeviceToHost, sm));
+            TCK(cudaMemcpyAsync(h64.data(), f64, (size_t)c * 8, cudaMemcpyDeviceToHost, sm));
+            TCK(cudaMemcpyAsync(h32.data(), f32, (size_t)c * 4, cudaMemcpyDeviceToHost, sm));
+            if (counts) {
+                ht.resize((size_t)c * 2 * cells);
+                TCK(cudaMemcpyAsync(ht.data(), tabs, ht.size() * 4, cudaMemcpyDeviceToHost, sm));
+            }
+            TCK(cudaStreamSynchronize(sm));
+            for (int64_t i = 0; i < c; i++) {
+                if (!(h64[i] >= threshold)) continue;
+                Found f;
+                f.rank = hr[i];
+                f.mi = h64[i];
+                f.mi32 = h32[i];
+                f.snp.assign(hc.begin() + i * order, hc.begin() + (i + 1) * order);
+                if (counts) f.tab.assign(ht.begin() + i * 2 * cells, ht.begin() + (i + 1) * 2 * cells);
+                found.push_back(std::move(f));
+            }
+        }
+    }
+#undef TCK
+    cleanup();
+    std::sort(found.begin(), found.end(),
+              [](const Found &a, const Found &b) { return a.mi > b.mi || (a.mi == b.mi && a.rank < b.rank); });
+    *n_found = (int64_t)found.size();
+    const int64_t n_out = std::min<int64_t>(capacity, (int64_t)found.size());
+    for (int64_t q = 0; q < n_out; q++) {
+        epi_result r;
+        std::memset(&r, 0, sizeof(r));
+        for (int t = 0; t < order; t++) r.snp[t] = found[q].snp[t];
+        r.mi = found[q].mi;
+        r.mi_f32 = found[q].mi32;
+        r.order = order;
+        r.rank = found[q].rank;
+        out[q] = r;
+        if (counts) std::memcpy(counts + (size_t)q * 2 * cells, found[q].tab.data(), (size_t)2 * cells * 4);
+    }
+    return EPI_OK;
+}
+
 epi_status epi_score_all(epi_dataset *ds, int order, float *out_dev)
 {
     uint64_t total = 0, re = UINT64_MAX;

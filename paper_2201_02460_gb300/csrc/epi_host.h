@@ -114,6 +114,9 @@ cudaError_t launch_finalize(const DevData &d, int k, int top_n, int pool, const 
                             int32_t *n_out, int32_t *status, cudaStream_t st);
 cudaError_t launch_tables(const DevData &d, int k, const uint32_t *combs, int64_t count, uint32_t *out, int num_sms,
                           cudaStream_t st);
+// ranks of the scores >= thr (unordered; at most cap written, *n counts all)
+cudaError_t launch_select_ge(const float *scores, int64_t count, float thr, uint64_t rank_base, uint64_t *out,
+                             uint64_t cap, unsigned long long *n, int num_sms, cudaStream_t st);
 cudaError_t launch_unrank(const DevData &d, int k, const uint64_t *ranks, int64_t count, uint32_t *combs,
                           cudaStream_t st);
 cudaError_t launch_publish_status(const int32_t *bits, int32_t *code, cudaStream_t st);

@@ -411,4 +411,28 @@ cudaError_t launch_score5_f32(const DevData &d, const uint32_t *combs, int64_t c
     return cudaGetLastError();
 }
 
+// Ranks rank_base + i of the scores at or above thr (any order), appended
+// while they fit in `cap`; *n counts all of them.
+__global__ void select_ge_kernel(const float *__restrict__ scores, int64_t count, float thr, uint64_t rank_base,
+                                 uint64_t *__restrict__ out, uint64_t cap, unsigned long long *__restrict__ n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        const float v = scores[i];
+        if (v >= thr) {
+            const unsigned long long at = atomicAdd(n, 1ull);
+            if (at < cap) out[at] = rank_base + (uint64_t)i;
+        }
+    }
+}
+
+cudaError_t launch_select_ge(const float *scores, int64_t count, float thr, uint64_t rank_base, uint64_t *out,
+                             uint64_t cap, unsigned long long *n, int num_sms, cudaStream_t st)
+{
+    if (count <= 0) return cudaSuccess;
+    int64_t g = (count + 255) / 256;
+    if (g > (int64_t)num_sms * 8) g = (int64_t)num_sms * 8;
+    select_ge_kernel<<<(unsigned)g, 256, 0, st>>>(scores, count, thr, rank_base, out, cap, n);
+    return cudaGetLastError();
+}
+
 }  // namespace epi

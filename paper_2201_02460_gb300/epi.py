@@ -128,6 +128,8 @@ def load(path: str | None = None):
         lib.epi_lookup.argtypes = [V, i32, P, P, i64, P]
         lib.epi_topk.restype = i32
         lib.epi_topk.argtypes = [V, P, P, i64, i32, P, P, P]
+        lib.epi_search_threshold.restype = i32
+        lib.epi_search_threshold.argtypes = [V, C.c_int, C.c_double, i64, P, i64, P, C.POINTER(C.c_int64)]
         lib.epi_score5.restype = i32
         lib.epi_score5.argtypes = [V, P, i64, P]
         lib.epi_heuristic5.restype = i32
@@ -421,6 +423,19 @@ def score_tables(ds: Dataset, order: int, tabs) -> tuple[np.ndarray, np.ndarray]
 
 def _dptr(t):
     return C.c_void_p(t.data_ptr())
+
+
+def search_threshold(ds: Dataset, order: int, threshold: float, capacity: int, chunk: int = 0,
+                     with_counts: bool = True) -> tuple[SearchResult, int]:
+    """Every combination with MI >= threshold, best first (at most
+    `capacity` returned), and how many qualify (epi_search_threshold)."""
+    out = np.zeros(max(capacity, 1), dtype=RESULT_DTYPE)
+    counts = np.zeros((max(capacity, 1), 2, 3 ** order), dtype=np.uint32) if with_counts else None
+    n = C.c_int64(0)
+    _check(load().epi_search_threshold(ds.handle, order, float(threshold), chunk, _np_ptr(out), capacity,
+                                       _np_ptr(counts) if with_counts else None, C.byref(n)))
+    m = min(capacity, n.value)
+    return SearchResult(out[:m], counts[:m] if with_counts else None, order), n.value
 
 
 def score_all(ds: Dataset, order: int):

@@ -123,6 +123,32 @@ def test_workload_order8_table2_ranges(epi, ctx):
         _check_result(r, d.geno, d.pheno, oc, om)
 
 
+@pytest.mark.parametrize("k,n,m,chunk", [(2, 40, 300, 0), (3, 16, 257, 100), (5, 12, 400, 0), (7, 11, 300, 77)])
+def test_search_threshold_matches_oracle(epi, ctx, k, n, m, chunk):
+    """Thresholded output: every combination with MI >= threshold, best
+    first, with its table; a capacity below the count keeps the best; a
+    threshold of 0 takes every combination and one above the maximum none.
+    Small chunks make several scoring passes."""
+    geno, pheno = random_data(n, m, seed=5 * k + n)
+    ds = epi.Dataset(ctx, geno, pheno)
+    total = O.binom(n, k)
+    oc, om, _ = O.search(geno, pheno, k, total)
+    # a threshold between two distinct values, about 40 combinations in
+    i = next(i for i in range(min(40, total - 1), total) if om[i - 1] - om[i] > 1e-9 * max(om[i], 1e-12))
+    thr = 0.5 * (om[i - 1] + om[i])
+    r, nf = epi.search_threshold(ds, k, thr, capacity=total, chunk=chunk)
+    assert nf == i and len(r) == i
+    check_topn(r.combs, r.mi, oc[:i], om[:i])
+    assert (r.counts == O.tables(geno, pheno, r.combs.astype(np.int32))).all()
+    r2, nf2 = epi.search_threshold(ds, k, thr, capacity=5, chunk=chunk)
+    assert nf2 == i and len(r2) == 5
+    check_topn(r2.combs, r2.mi, oc[:5], om[:5])
+    _, nf3 = epi.search_threshold(ds, k, 0.0, capacity=0, chunk=chunk, with_counts=False)
+    assert nf3 == total
+    _, nf4 = epi.search_threshold(ds, k, om[0] * 1.001 + 1e-9, capacity=10, chunk=chunk)
+    assert nf4 == 0
+
+
 def test_search_with_exact_ties(epi, ctx):
     geno, pheno = random_data(24, 301, seed=99)
     geno[10] = geno[3]
