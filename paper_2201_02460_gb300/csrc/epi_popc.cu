@@ -21,11 +21,11 @@
 //   * the counts never leave registers: MI is evaluated in the same thread
 //     and compared against the CTA's current threshold; survivors go to a
 //     shared-memory buffer that is merged into the CTA's sorted list;
-//   * orders 6-8: the same kernel; where one prefix table (3^(k-1) rows) does
-//     not fit in shared memory (order 8, or order 7 with many samples) it is
-//     materialised in a per-CTA global buffer instead (the paper's stored
-//     `combine` table, Section 2.1), read through L1/L2 by the CTA's threads,
-//     which walk the same prefix rows together.
+//   * orders 6-8: the same kernel with one warp per combination; at orders
+//     7-8 the prefix table (729 or 2187 rows) is materialised in a per-CTA
+//     global buffer (the paper's stored `combine` table, Section 2.1), read
+//     through L1/L2 by the CTA's threads, which walk the same prefix rows
+//     (batched launches keep it in shared memory where it fits).
 #include "epi_internal.cuh"
 #include "epi_host.h"
 

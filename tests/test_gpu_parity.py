@@ -86,10 +86,10 @@ def test_search_small(epi, ctx, k, n, m, top_n):
     _check_result(r, geno, pheno, oc, om)
 
 
-# Orders 6-8 (popcount path; the tensor path stops at 5).  Sizes chosen so
-# that both placements of the prefix tables run: shared memory (order 7 at 700
-# samples: 729 rows x 24 words; order 8 at 200: 2187 x 8) and the per-CTA
-# global buffer (order 7 at 3000: 729 x 96 words; order 8 at 1000: 2187 x 32).
+# Orders 6-8 (popcount path; the tensor path stops at 5).  Single searches
+# keep the order-6 prefix tables in shared memory and the order-7/8 tables in
+# per-CTA global buffers; batched launches keep order-7/8 tables in shared
+# memory where they fit (test_batched_high_orders).
 @pytest.mark.parametrize("k,n,m,m1,top_n", [
     (6, 14, 300, None, 40), (6, 12, 129, 40, 20), (7, 13, 700, None, 30), (7, 11, 3000, 1500, 20),
     (8, 12, 200, None, 25), (8, 11, 1000, 500, 15),
@@ -147,6 +147,21 @@ def test_search_threshold_matches_oracle(epi, ctx, k, n, m, chunk):
     assert nf3 == total
     _, nf4 = epi.search_threshold(ds, k, om[0] * 1.001 + 1e-9, capacity=10, chunk=chunk)
     assert nf4 == 0
+
+
+def test_batched_high_orders(epi, ctx):
+    """Orders 6-8 in one batched launch per order (prefix tables in shared
+    memory: 729 rows x 12 words at order 7, 2187 x 8 at order 8) match the
+    single searches (global tables at orders 7-8) and the oracle."""
+    sets = [random_data(n, m, seed=70 + i) for i, (n, m) in enumerate([(12, 300), (11, 350), (11, 200), (12, 180)])]
+    orders, tops = [6, 7, 8, 7], [15, 12, 10, 9]
+    dss = [epi.Dataset(ctx, g, p) for g, p in sets]
+    res = epi.search_batched(ctx, dss, orders, tops, path="popc")
+    for (g, p), ds, k, t, r in zip(sets, dss, orders, tops, res):
+        single = epi.search(ds, k, t, path="popc")
+        oc, om, _ = O.search(g, p, k, t)
+        _check_result(r, g, p, oc, om)
+        assert (r.combs == single.combs).all() and np.array_equal(r.mi, single.mi)
 
 
 def test_search_with_exact_ties(epi, ctx):
