@@ -107,7 +107,8 @@ epi_status epi_dataset_info(const epi_dataset *ds, int64_t *n_snps, int64_t *n_s
 /* Exhaustive search of every k-subset (Algorithm 1), keeping the best top_n
  * (Section 2.4).  out: host array of top_n records; counts (optional, may be
  * NULL): host array [top_n][2][3^k]; *n_out receives min(top_n, C(n,k)).
- * Orders 1..5 run on the GPU (EPI_EUNSUPPORTED above); top_n in [1, 1024]. */
+ * Orders 1..8 run on the GPU (the tensor-core path covers orders 2..5, the
+ * popcount path 1..8); top_n in [1, 1024]. */
 epi_status epi_search(epi_dataset *ds, int order, int top_n, int path, epi_result *out,
                       uint32_t *counts, int *n_out);
 
@@ -134,7 +135,9 @@ epi_status epi_search_async(epi_dataset *ds, int order, int top_n, int path,
  * batch (counting launches, per-dataset merge, re-score and selection, and
  * the copies back) is captured once into a CUDA graph that later calls with
  * the same datasets, orders and top_n replay.  ds[i] must belong to ctx;
- * orders[i] in 1..5, top_ns[i] in 1..1024; outs[i] host arrays of top_ns[i]
+ * orders[i] in 1..8 (at orders 6..8 one prefix table of the largest dataset
+ * must fit in shared memory, else EPI_EUNSUPPORTED), top_ns[i] in 1..1024;
+ * outs[i] host arrays of top_ns[i]
  * records; counts NULL or counts[i] NULL or a host array [top_ns[i]][2][3^k];
  * n_outs[i] receives the record count.  Same results as epi_search on each
  * dataset.  Destroying a dataset invalidates the cached graph. */
@@ -235,7 +238,7 @@ epi_status epi_search_threshold(epi_dataset *ds, int order, double threshold, in
                                 int64_t capacity, uint32_t *counts, int64_t *n_found);
 
 /* Every combination's single-precision MI (Eq. 1-3), by lexicographic rank:
- * out_dev is device memory of C(n_snps, order) floats.  Orders 1..5. */
+ * out_dev is device memory of C(n_snps, order) floats.  Orders 1..8. */
 epi_status epi_score_all(epi_dataset *ds, int order, float *out_dev);
 
 /* Combinations of `count` lexicographic ranks (device [count] uint64, each
