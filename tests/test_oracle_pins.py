@@ -177,7 +177,7 @@ def _rand(n, m, seed, m1=None):
 
 
 @pytest.mark.parametrize("m", [1, 7, 31, 32, 33, 63, 64, 65, 70, 129])
-@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6, 7, 8])
 def test_tables_match_brute_force(oracle_lib, k, m):
     n = 9
     geno, pheno = _rand(n, m, seed=1000 * k + m)
@@ -314,7 +314,7 @@ def _all_sorted(geno, pheno, k):
     return rows
 
 
-@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6, 7, 8])
 @pytest.mark.parametrize("threads", [1, 3])
 def test_search_matches_full_sort(oracle_lib, k, threads):
     n, m = 10, 67
