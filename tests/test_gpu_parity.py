@@ -164,6 +164,20 @@ def test_batched_high_orders(epi, ctx):
         assert (r.combs == single.combs).all() and np.array_equal(r.mi, single.mi)
 
 
+def test_sharded_ranges_merge_to_the_full_search(epi, ctx):
+    """The sharding hook on the GPU: range searches of a three-way rank
+    split, merged by (MI desc, rank asc), give the whole search's top-N."""
+    from paper_2201_02460_gb300 import shard
+    geno, pheno = random_data(60, 700, seed=21)
+    ds = epi.Dataset(ctx, geno, pheno)
+    k, t = 3, 40
+    total = O.binom(60, k)
+    parts = [epi.search(ds, k, t, path="popc", rank_range=(b, e)).records for b, e in shard.rank_ranges(total, 3)]
+    got = shard.merge_topn(parts, t)
+    full = epi.search(ds, k, t, path="popc")
+    assert (got["rank"] == full.records["rank"]).all() and (got["mi"] == full.records["mi"]).all()
+
+
 def test_search_with_exact_ties(epi, ctx):
     geno, pheno = random_data(24, 301, seed=99)
     geno[10] = geno[3]
