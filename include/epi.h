@@ -48,7 +48,7 @@ typedef enum {
     EPI_EINVAL = 1,        /* bad argument (value, size, pointer, order) */
     EPI_ENOMEM = 2,        /* device or host allocation failed */
     EPI_ECUDA = 3,         /* a CUDA runtime call failed */
-    EPI_EUNSUPPORTED = 4,  /* valid request this build cannot run */
+    EPI_EUNSUPPORTED = 4,  /* valid request the library cannot run */
     EPI_ETIMEOUT = 5,      /* a bounded device wait gave up */
     EPI_EOVERFLOW = 6      /* exact top-N not guaranteed even after retries */
 } epi_status;
@@ -145,7 +145,7 @@ epi_status epi_search_batched(epi_ctx *ctx, epi_dataset *const *ds, const int *o
                               int n_ds, int path, epi_result *const *outs, uint32_t *const *counts,
                               int *n_outs);
 
-/* Autotuner (the paper has no counterpart; it tunes this build's launch
+/* Autotuner (the paper has no counterpart; it tunes the library's launch
  * shapes).  Times every popcount-path shape (row group of prefix rows per
  * thread, sub-tile of combinations, prefixes staged per sub-tile) on a
  * bounded rank range of this dataset and, where the tensor-core path applies,

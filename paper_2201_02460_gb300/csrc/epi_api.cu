@@ -1208,7 +1208,7 @@ epi_status epi_create(int device, void *cuda_stream, epi_ctx **out)
     if (!g.ok) return fail(EPI_ECUDA, "cannot select device %d", device);
     cudaDeviceProp prop;
     CK(cudaGetDeviceProperties(&prop, device));
-    if (prop.major < 10) return fail(EPI_EUNSUPPORTED, "device %d is sm_%d%d; this build targets sm_103a", device,
+    if (prop.major < 10) return fail(EPI_EUNSUPPORTED, "device %d is sm_%d%d; the library targets sm_103a", device,
                                      prop.major, prop.minor);
     epi_ctx *c = new epi_ctx();
     c->device = device;
