@@ -46,3 +46,31 @@ def test_product_has_no_oracle_import():
     for p in pkg.rglob("*.py"):
         text = p.read_text()
         assert "import oracle" not in text and "from oracle" not in text, p
+
+
+def _header_param_counts():
+    """Parameter count of every function prototype in include/epi.h."""
+    import pathlib
+    import re
+    text = (pathlib.Path(__file__).resolve().parents[1] / "include" / "epi.h").read_text()
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    out = {}
+    for m in re.finditer(r"\b(epi_[a-z0-9_]+)\s*\(([^;{}]*?)\)\s*;", text):
+        args = m.group(2).strip()
+        out[m.group(1)] = 0 if args in ("", "void") else args.count(",") + 1
+    return out
+
+
+def test_binding_argument_counts_match_the_header(lib):
+    """Every function the binding declares argument types for takes as many
+    arguments as its prototype in the header."""
+    counts = _header_param_counts()
+    assert len(counts) >= 40
+    checked = 0
+    for name, n in counts.items():
+        fn = getattr(lib, name)
+        if fn.argtypes is not None:
+            assert len(fn.argtypes) == n, (name, len(fn.argtypes), n)
+            checked += 1
+    assert checked >= 30
