@@ -205,8 +205,15 @@ epi_status epi_debug_counts(epi_dataset *ds, int order, uint32_t *out);
  * queued (the genotype tables take about n_snps * 3 * 2 * ceil(n_samples/128)
  * * 16 bytes).
  *
+ * With invalid genotype or phenotype values or a wrong n_cases, *n_out_dev
+ * is 0 and no genotype is read outside geno_dev.
+ *
  * The first call on each device resolves the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * (cudaGetSymbolAddress) and the device's SM count and shared-memory limit,
+ * and keeps them for every later call; make that first call before any stream
+ * capture.  The address belongs to the runtime's primary context of the
+ * device: calls made under another context of the same device, or after a
+ * cudaDeviceReset in the same process, are not supported.
  * Every call uses the same array and leaves its contents behind; calls whose
  * work overlaps on the GPU (other streams, other host threads) race on it and
  * must be serialised by the caller. */

@@ -47,16 +47,21 @@ __global__ void __launch_bounds__(1024) scan_pheno_kernel(const uint8_t *__restr
 // One warp per (SNP, 32-individual word of a subtable): lane b loads the
 // genotype of individual 32 w + b and three ballots give the three rows.
 // Pad bits (past the subtable's size) stay 0.  Genotypes above 2 set
-// ST_BAD_GENO.
+// ST_BAD_GENO.  With m1_check given (the case count the scan kernel found on
+// the device), a class size m1 that differs from it means the index maps hold
+// fewer written entries than m1 / m0 claim: then no index is read and every
+// row is written as zeros (the caller reports the mismatch).
 __global__ void pack_masks_kernel(const uint8_t *__restrict__ geno, int64_t n, int64_t m,
                                   const int32_t *__restrict__ case_idx, const int32_t *__restrict__ ctrl_idx,
                                   int64_t m1, int32_t W1, int32_t Wt, uint32_t *__restrict__ masks,
-                                  int32_t *__restrict__ status)
+                                  int32_t *__restrict__ status, const int64_t *__restrict__ m1_check)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int64_t total = n * Wt;
-    const int64_t m0 = m - m1;
+    const bool counts_ok = m1_check == nullptr || *m1_check == m1;
+    const int64_t m0 = counts_ok ? m - m1 : 0;
+    if (!counts_ok) m1 = 0;
     for (int64_t wi = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); wi < total; wi += warps) {
         const int64_t s = wi / Wt;
         const int32_t w = (int32_t)(wi - s * Wt);
@@ -109,14 +114,15 @@ void launch_scan_pheno(const uint8_t *pheno, int64_t m, int32_t *case_idx, int32
 
 void launch_pack_masks(const uint8_t *geno, int64_t n, int64_t m, const int32_t *case_idx, const int32_t *ctrl_idx,
                        int64_t m1, int32_t W1, int32_t Wt, uint32_t *masks, int32_t *status, int num_sms,
-                       cudaStream_t st)
+                       cudaStream_t st, const int64_t *m1_check)
 {
     const int64_t warps = n * (int64_t)Wt;
     int64_t blocks = (warps + 7) / 8;
     const int64_t cap = (int64_t)num_sms * 16;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    pack_masks_kernel<<<(unsigned)blocks, 256, 0, st>>>(geno, n, m, case_idx, ctrl_idx, m1, W1, Wt, masks, status);
+    pack_masks_kernel<<<(unsigned)blocks, 256, 0, st>>>(geno, n, m, case_idx, ctrl_idx, m1, W1, Wt, masks, status,
+                                                       m1_check);
 }
 
 void launch_binom(int64_t n, uint64_t *tab, int num_sms, cudaStream_t st)

@@ -25,9 +25,11 @@ inline uint64_t host_binom(int64_t n, int64_t k)
 // epi_data.cu
 void launch_scan_pheno(const uint8_t *pheno, int64_t m, int32_t *case_idx, int32_t *ctrl_idx, int64_t *m1,
                        int32_t *status, cudaStream_t st);
+// m1_check (device, may be NULL): the case count found by scan_pheno; where it
+// differs from m1 the index maps are not read and the rows are zeros
 void launch_pack_masks(const uint8_t *geno, int64_t n, int64_t m, const int32_t *case_idx, const int32_t *ctrl_idx,
                        int64_t m1, int32_t W1, int32_t Wt, uint32_t *masks, int32_t *status, int num_sms,
-                       cudaStream_t st);
+                       cudaStream_t st, const int64_t *m1_check = nullptr);
 void launch_binom(int64_t n, uint64_t *tab, int num_sms, cudaStream_t st);
 
 // epi_popc.cu

@@ -30,27 +30,47 @@ constexpr size_t kStaticScratchBytes = (size_t)64 << 20;   // 64 MiB
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
 constexpr int kMaxDevices = 64;
-std::mutex g_addr_mu;
-unsigned char *g_addr[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device; resolved on the
-// first call per device and kept.
-cudaError_t scratch_address(int device, unsigned char **out)
+// What one device needs per call, resolved on the first call on that device
+// (in the runtime's primary context of the device) and kept: the scratch
+// array's device address and the two device attributes the launch plan uses.
+struct DeviceSetup {
+    unsigned char *scratch = nullptr;
+    int num_sms = 0;
+    int smem_optin = 0;
+};
+std::mutex g_setup_mu;
+DeviceSetup g_setup[kMaxDevices];
+
+cudaError_t device_setup(int device, DeviceSetup *out)
 {
-    std::lock_guard<std::mutex> lk(g_addr_mu);
-    if (!g_addr[device]) {
+    std::lock_guard<std::mutex> lk(g_setup_mu);
+    DeviceSetup &S = g_setup[device];
+    if (!S.scratch) {
+        int sms = 0, optin = 0;
+        cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
         void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e == cudaSuccess) e = cudaGetSymbolAddress(&p, g_static_scratch);
         if (e != cudaSuccess) return e;
-        g_addr[device] = static_cast<unsigned char *>(p);
+        S.num_sms = sms;
+        S.smem_optin = optin;
+        S.scratch = static_cast<unsigned char *>(p);
     }
-    *out = g_addr[device];
+    *out = S;
     return cudaSuccess;
 }
 
 __global__ void check_cases_kernel(const int64_t *m1_dev, int64_t m1_given, int32_t *status)
 {
     if (*m1_dev != m1_given) atomicOr(status, ST_BAD_PHENO);
+}
+
+// Invalid inputs leave no result: the record count is zeroed so that a caller
+// reading n_out before status_dev sees an empty result.
+__global__ void clear_on_bad_input_kernel(const int32_t *status, int32_t *n_out)
+{
+    if (*status & (ST_BAD_GENO | ST_BAD_PHENO)) *n_out = 0;
 }
 
 struct Carve {
@@ -108,11 +128,11 @@ extern "C" epi_status epi_search_static(const uint8_t *geno_dev, const uint8_t *
     if (!is_dev(geno_dev, device) || !is_dev(pheno_dev, device) || !is_dev(out_dev, device) ||
         !is_dev(n_out_dev, device) || !is_dev(status_dev, device) || (counts_dev && !is_dev(counts_dev, device)))
         return bad(EPI_EINVAL, "epi_search_static: inputs and outputs must be device memory of the current device");
-    cudaDeviceProp prop;
-    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess)
-        return bad(EPI_ECUDA, "epi_search_static: cannot read device properties");
-    const int num_sms = prop.multiProcessorCount;
-    const size_t smem_limit = prop.sharedMemPerBlockOptin;
+    DeviceSetup setup;
+    if (device_setup(device, &setup) != cudaSuccess)
+        return bad(EPI_ECUDA, "epi_search_static: cannot read the device attributes or the scratch array's address");
+    const int num_sms = setup.num_sms;
+    const size_t smem_limit = (size_t)setup.smem_optin;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
 
     // layout of the dataset (Section 2.1) and of the search
@@ -169,9 +189,8 @@ extern "C" epi_status epi_search_static(const uint8_t *geno_dev, const uint8_t *
         return bad(EPI_EINVAL, "epi_search_static: dataset too large for the 64 MiB static scratch "
                                "(needs about n_snps * 3 * 2 * ceil(n_samples/128) * 16 bytes of genotype tables)");
 
-    unsigned char *base = nullptr;
-    cudaError_t e = scratch_address(device, &base);
-    if (e != cudaSuccess) return bad(EPI_ECUDA, "epi_search_static: cudaGetSymbolAddress of the scratch array failed");
+    unsigned char *base = setup.scratch;
+    cudaError_t e;
     int32_t *case_idx = reinterpret_cast<int32_t *>(base + o_case);
     int32_t *ctrl_idx = reinterpret_cast<int32_t *>(base + o_ctrl);
     int64_t *dm1 = reinterpret_cast<int64_t *>(base + o_m1);
@@ -199,7 +218,12 @@ extern "C" epi_status epi_search_static(const uint8_t *geno_dev, const uint8_t *
     if (e != cudaSuccess) return bad(EPI_ECUDA, "epi_search_static: cudaMemsetAsync failed");
     launch_scan_pheno(pheno_dev, n_samples, case_idx, ctrl_idx, dm1, status, st);
     check_cases_kernel<<<1, 1, 0, st>>>(dm1, n_cases, status);
-    launch_pack_masks(geno_dev, n_snps, n_samples, case_idx, ctrl_idx, n_cases, d.W1, d.Wt, masks, status, num_sms, st);
+    // the index maps hold exactly *dm1 cases and n_samples - *dm1 controls
+    // written by this call; the pack kernel reads them only when that matches
+    // n_cases (otherwise the search runs on all-zero rows and is reported as
+    // EPI_EINVAL with no records)
+    launch_pack_masks(geno_dev, n_snps, n_samples, case_idx, ctrl_idx, n_cases, d.W1, d.Wt, masks, status, num_sms, st,
+                      dm1);
     launch_binom(n_snps, binom, num_sms, st);
     e = cudaGetLastError();
     if (e == cudaSuccess)
@@ -209,6 +233,10 @@ extern "C" epi_status epi_search_static(const uint8_t *geno_dev, const uint8_t *
     if (e == cudaSuccess)
         e = launch_finalize(d, k, top_n, pool, cs, cr, cn, mi, cb, ct, thr, total, out_dev, counts_dev, n_out_dev,
                             status, st);
+    if (e == cudaSuccess) {
+        clear_on_bad_input_kernel<<<1, 1, 0, st>>>(status, n_out_dev);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess) e = launch_publish_status(status, status_dev, st);
     if (e != cudaSuccess) return bad(EPI_ECUDA, cudaGetErrorString(e));
     return EPI_OK;

@@ -64,19 +64,34 @@ def test_static_search_matches_search_on_consecutive_calls(env):
 
 def test_static_search_reports_bad_inputs_and_refuses_large_datasets(env):
     torch, epi, fn = env
+    # a larger dataset first, so that the shared array holds index entries
+    # beyond what the small dataset below writes
+    big_geno, big_pheno = random_data(40, 1500, seed=5)
+    status, recs, _ = _run_static(torch, epi, fn, big_geno, big_pheno, 2, 10)
+    assert status == 0 and len(recs) == 10
     geno, pheno = random_data(30, 200, seed=4)
-    # n_cases that does not match the phenotype comes back as EPI_EINVAL
+    # n_cases that does not match the phenotype comes back as EPI_EINVAL with
+    # no records (one more or one fewer than the true count; the genotype
+    # reads stay inside this call's inputs either way)
     g = torch.from_numpy(geno).cuda()
     p = torch.from_numpy(pheno).cuda()
-    out = torch.zeros(10 * 56, dtype=torch.uint8, device="cuda")
+    out = torch.zeros(10 * epi.RESULT_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
     n_out = torch.zeros(1, dtype=torch.int32, device="cuda")
     st = torch.zeros(1, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream().cuda_stream
-    rc = fn(g.data_ptr(), p.data_ptr(), 30, 200, int(pheno.sum()) + 1, 2, 10, out.data_ptr(), None,
-            n_out.data_ptr(), st.data_ptr(), stream)
-    assert rc == 0
-    torch.cuda.synchronize()
-    assert int(st.item()) == epi.EPI_EINVAL
+    for wrong in (int(pheno.sum()) + 1, int(pheno.sum()) - 1):
+        n_out.fill_(7)
+        rc = fn(g.data_ptr(), p.data_ptr(), 30, 200, wrong, 2, 10, out.data_ptr(), None,
+                n_out.data_ptr(), st.data_ptr(), stream)
+        assert rc == 0
+        torch.cuda.synchronize()
+        assert int(st.item()) == epi.EPI_EINVAL
+        assert int(n_out.item()) == 0
+    # the array is usable again right after the rejected calls
+    want = epi.search(epi.Dataset(epi.Context(0), geno, pheno), 2, 10, path="popc")
+    status, recs, _ = _run_static(torch, epi, fn, geno, pheno, 2, 10)
+    assert status == 0
+    assert (recs["snp"][:, :2].astype(np.int64) == want.combs).all()
     # genotype tables larger than the fixed array: refused before any work
     big = torch.empty((12000, 16000), dtype=torch.uint8, device="cuda")
     bp = torch.zeros(16000, dtype=torch.uint8, device="cuda")
