@@ -58,8 +58,8 @@ typedef enum {
     EPI_PATH_AUTO = 0,     /* fastest exact path for the order and sizes */
     EPI_PATH_POPC = 1,     /* bitwise AND + POPC on the integer pipe */
     EPI_PATH_TC = 2        /* exact 0/1 GEMM on tcgen05 tensor cores: orders
-                              2..5 with cases and controls present, whole
-                              combination range only (EPI_EUNSUPPORTED else) */
+                              2..5 with cases and controls present
+                              (EPI_EUNSUPPORTED else) */
 } epi_path;
 
 #define EPI_MAX_ORDER 8    /* highest order the API accepts (Table 2 goes to 8) */
@@ -114,7 +114,11 @@ epi_status epi_search(epi_dataset *ds, int order, int top_n, int path, epi_resul
 
 /* The same restricted to combinations of lexicographic rank in
  * [rank_begin, rank_end) (rank_end clipped to C(n,k)): the resumable and
- * shardable form of the search. */
+ * shardable form of the search.  Both counting paths take ranges; the
+ * tensor-core path counts every combination whose first SNP lies between
+ * those of ranks rank_begin and rank_end - 1 and keeps only the range's, so
+ * EPI_PATH_AUTO takes it for a range only when that adds at most the range's
+ * own size of work. */
 epi_status epi_search_range(epi_dataset *ds, int order, int top_n, int path,
                             uint64_t rank_begin, uint64_t rank_end, epi_result *out,
                             uint32_t *counts, int *n_out);
@@ -406,7 +410,17 @@ typedef struct epi_train_opts {
 epi_status epi_proposer_train(epi_mlp *net, epi_dataset *const *datasets, int n_ds, const epi_train_opts *opts,
                               float *epoch_loss);
 
-/* Timing of the dominant counting kernel.  After epi_profile_begin, every
+/* Rate of the tensor pipe for the one MMA the tensor-core counting path
+ * issues (tcgen05.mma kind::f8f6f4, M128 N128 K32, E4M3 operands in shared
+ * memory, FP32 accumulation): one CTA per SM issues `stages` (32..2^32)
+ * groups of four such MMAs back to back from one thread, with no other work.
+ * The paper has no counterpart; this is the roofline's denominator.
+ * out[4]: dense rate in TFLOP/s (2 flop per multiply-add, over the launch's
+ * event time), multiply-adds per SM clock (over each CTA's own cycle count,
+ * averaged), the launch's milliseconds, and the implied SM clock in MHz. */
+epi_status epi_tc_rate(epi_ctx *ctx, int64_t stages, double *out);
+
+/* Timing of the dominant counting kernel./* Timing of the dominant counting kernel.  After epi_profile_begin, every
  * launch of a search's counting kernel is bracketed by CUDA events on the
  * context's stream; epi_profile_end waits for those events and returns their
  * summed duration in milliseconds and the number of bracketed launches. */

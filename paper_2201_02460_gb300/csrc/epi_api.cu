@@ -242,11 +242,12 @@ epi_status plan_popc(const epi_dataset *ds, SearchPlan &p, int R_req = 0)
     return EPI_OK;
 }
 
-// Tensor-core path conditions: orders 2..5, both classes present, the whole
-// combination range (the tensor tiles follow panel order, not rank order).
+// Tensor-core path conditions: orders 2..5, both classes present.  A rank
+// range is searched over whole first-SNP blocks and clipped in the epilogue.
 bool tc_applicable(const epi_dataset *ds, int k, uint64_t rb, uint64_t re, uint64_t total)
 {
-    return k >= 2 && k <= 5 && ds->m1 > 0 && ds->m0 > 0 && rb == 0 && re == total && ds->n >= k + 1;
+    (void)rb; (void)re; (void)total;
+    return k >= 2 && k <= 5 && ds->m1 > 0 && ds->m0 > 0 && ds->n >= k + 1;
 }
 
 epi_status choose_path(const epi_dataset *ds, int k, int path, uint64_t rb, uint64_t re, uint64_t total, bool &tc)
@@ -260,7 +261,10 @@ epi_status choose_path(const epi_dataset *ds, int k, int path, uint64_t rb, uint
     } else if (path == EPI_PATH_POPC) {
         tc = false;
     } else {
-        tc = ok && k >= 3;
+        // automatic choice: the tensor path counts whole first-SNP blocks, so
+        // it is taken for a rank range only when that adds at most as much
+        // work again as the range itself
+        tc = ok && k >= 3 && (re - rb == total || tc_range_work(ds->n, k, rb, re) <= 2 * (re - rb));
         auto it = ds->ctx->tune.find(tune_key(k, ds->n, ds->Wt));
         if (ok && it != ds->ctx->tune.end() && it->second.path) tc = it->second.path == EPI_PATH_TC;
     }
@@ -305,7 +309,7 @@ epi_status queue_search(epi_dataset *ds, const SearchPlan &p, int path, epi_resu
     const size_t o_ct = a.take<uint32_t>((size_t)p.pool * 2 * cells);
     const size_t o_mi = a.take<double>((size_t)p.pool);
     const size_t o_cb = a.take<int32_t>((size_t)p.pool * p.k);
-    const size_t o_ic = a.take<uint64_t>((size_t)ds->n + 1);
+    const size_t o_ic = a.take<uint64_t>(2 * ((size_t)ds->n + 1));
     const size_t o_pre =
         p.global_prefix ? a.take<uint32_t>((size_t)p.grid * p.slots * popc_slot_words(p.k, ds->Wt)) : 0;
     epi_status st = ensure_scratch(ctx, a.off);
@@ -347,8 +351,8 @@ epi_status queue_search(epi_dataset *ds, const SearchPlan &p, int path, epi_resu
             waits = ctx->waits_dev;
             ctx->waits_grid = p.grid;
         }
-        CK(launch_tc_search(d, p.k, ds->b8, ic, p.pool, thr, ls, lr, lc, status, p.grid, p.total, ctx->stream,
-                            &cand_p2, dump, waits));
+        CK(launch_tc_search(d, p.k, ds->b8, ic, p.pool, thr, ls, lr, lc, status, p.grid, p.total, p.rb, p.re,
+                            ctx->stream, &cand_p2, dump, waits));
         ctx->launches += 1;   // item table
     } else {
         CK(launch_popc_search(d, p.k, p.R, p.rb, p.re, p.tile, p.pool, p.slots, p.cand_p2, thr, ls, lr, lc, p.grid,
@@ -571,7 +575,9 @@ epi_status record_batch(epi_ctx *ctx, std::vector<BatchItem> &items, std::vector
     CK(cudaMemsetAsync(dev, 0, items.size() * 256, st));
     for (auto &g : groups) {
         if (g.tc)
-            for (int i : g.items) CK(launch_tc_item_cum(items[i].ds->dev(), g.k, reinterpret_cast<uint64_t *>(dev + items[i].o_ic), st));
+            for (int i : g.items)
+                CK(launch_tc_item_cum(items[i].ds->dev(), g.k, 0, items[i].total,
+                                      reinterpret_cast<uint64_t *>(dev + items[i].o_ic), st));
         float *ls = reinterpret_cast<float *>(dev + g.o_ls);
         uint64_t *lr = reinterpret_cast<uint64_t *>(dev + g.o_lr);
         int32_t *lc = reinterpret_cast<int32_t *>(dev + g.o_lc);
@@ -698,7 +704,7 @@ extern "C" epi_status epi_search_batched(epi_ctx *ctx, epi_dataset *const *dss, 
         it.o_ct = a.take<uint32_t>((size_t)it.pool * 2 * it.cells);
         it.o_mi = a.take<double>((size_t)it.pool);
         it.o_cb = a.take<int32_t>((size_t)it.pool * it.k);
-        it.o_ic = a.take<uint64_t>((size_t)it.ds->n + 1);
+        it.o_ic = a.take<uint64_t>(2 * ((size_t)it.ds->n + 1));
         it.o_rec = a.take<epi_result>((size_t)it.top_n);
         it.o_cnt = a.take<uint32_t>((size_t)it.top_n * 2 * it.cells);
     }
@@ -797,7 +803,7 @@ double time_pass(epi_dataset *ds, int k, bool tc, int R, int tile, int slots, ui
 {
     epi_ctx *ctx = ds->ctx;
     SearchPlan p;
-    p.k = k; p.top_n = 10; p.pool = initial_pool(10); p.rb = 0; p.re = r; p.total = tc ? total : r;
+    p.k = k; p.top_n = 10; p.pool = initial_pool(10); p.rb = 0; p.re = tc ? total : r; p.total = tc ? total : r;
     p.tc = tc;
     if (tc) {
         p.grid = ctx->num_sms;
@@ -1493,6 +1499,51 @@ epi_status epi_debug_counts(epi_dataset *ds, int order, uint32_t *out)
     cudaFreeAsync(buf, ctx->stream);
     cudaStreamSynchronize(ctx->stream);
     return st;
+}
+
+epi_status epi_tc_rate(epi_ctx *ctx, int64_t stages, double *out)
+{
+    if (!ctx || !out) return fail(EPI_EINVAL, "NULL argument");
+    if (stages < 32 || stages > ((int64_t)1 << 32)) return fail(EPI_EINVAL, "stages outside 32..2^32");
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(EPI_ECUDA, "cannot select device %d", ctx->device);
+    const int grid = ctx->num_sms;
+    void *buf = nullptr;
+    CK(cudaMallocAsync(&buf, (size_t)grid * 8 + 256, ctx->stream));
+    unsigned long long *cycles = static_cast<unsigned long long *>(buf);
+    int32_t *status = reinterpret_cast<int32_t *>(static_cast<char *>(buf) + (size_t)grid * 8);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    std::vector<unsigned long long> cyc((size_t)grid);
+    int32_t hs = 0;
+    float ms = 0.0f;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, 4, ctx->stream);
+    // a short warm-up launch, then the timed one
+    if (e == cudaSuccess) e = launch_mma_rate(32, cycles, status, grid, ctx->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
+    if (e == cudaSuccess) e = launch_mma_rate(stages, cycles, status, grid, ctx->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cyc.data(), cycles, (size_t)grid * 8, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, status, 4, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFreeAsync(buf, ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return fail(EPI_ECUDA, "%s", cudaGetErrorString(e));
+    if (hs & ST_TIMEOUT) return fail(EPI_ETIMEOUT, "device wait expired");
+    ctx->launches += 2;
+    const double macs_per_sm = (double)stages * 4.0 * 128.0 * 128.0 * 32.0;
+    double mean_cyc = 0.0;
+    for (unsigned long long c : cyc) mean_cyc += (double)c;
+    mean_cyc /= (double)grid;
+    out[0] = 2.0 * macs_per_sm * grid / ((double)ms * 1e-3) / 1e12;
+    out[1] = macs_per_sm / mean_cyc;
+    out[2] = (double)ms;
+    out[3] = mean_cyc / ((double)ms * 1e3);
+    return EPI_OK;
 }
 
 epi_status epi_profile_begin(epi_ctx *ctx)

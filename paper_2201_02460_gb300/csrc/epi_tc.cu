@@ -25,7 +25,13 @@
 // the epilogue reduces a prefix with warp shuffles); N = 128 columns = 64 last
 // SNPs x genotypes {0, 1}; K = 128 individuals per stage.
 // Prefixes are taken in "panel order" (by their last SNP c ascending) so the
-// last SNPs of a tile, j > c, form one contiguous range.
+// last SNPs of a tile, j > c, form one contiguous range.  A lexicographic rank
+// range [r0, r1) of combinations covers the first SNPs s1 in [a, b] (those of
+// ranks r0 and r1 - 1); within a panel the prefixes are listed
+// lexicographically, so the ones with s1 in [a, b] are contiguous, and the
+// epilogue keeps, per prefix, only the last SNPs whose combination's rank lies
+// in [r0, r1) (consecutive ranks share their prefix and differ in the last
+// SNP, so that is one interval of j).
 //
 // Warp roles (576 threads, one CTA per SM, persistent, a contiguous range of
 // work items per CTA; an item = one M tile x one N tile x the whole K range):
@@ -94,9 +100,12 @@ struct Desc {
 // same order, CTAs [cta_begin, cta_begin + cta_count) working on this one.
 struct DsParams {
     DevData d;
-    uint64_t n_prefix;         // C(n-1, k-1)
+    uint64_t n_prefix;         // prefixes searched (first SNP in [s1_lo, s1_hi])
     uint64_t n_items;
     const uint64_t *item_cum;  // [n + 1] items of M tiles starting in panels < c
+    const uint64_t *pcum;      // [n + 1] prefixes searched in panels < c
+    uint64_t rank_begin, rank_end;   // lexicographic ranks searched
+    int32_t s1_lo, s1_hi;      // first SNPs of ranks rank_begin and rank_end - 1
     int chunks, chunks_case;   // K stages in total / over the cases
     float delta;               // screening margin (nats)
     float tconst;              // T(m) - T(m1) - T(m0), T(c) = c log2 c
@@ -201,58 +210,80 @@ __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"
 
 // ------------------------------------------------------------ enumeration --
 // Prefixes of order k are the (k-1)-subsets whose last SNP c is <= n-2, in
-// panel order: panel c holds the C(c, k-2) subsets ending in c, ordered
-// colexicographically by their first k-2 SNPs; panel c starts at C(c, k-1).
+// panel order: panel c holds the subsets ending in c whose first SNP lies in
+// [s1_lo, s1_hi], their first k-2 SNPs in lexicographic order.  pcum[c]
+// counts the prefixes of panels < c; q is a prefix's index in this order.
 struct PrefixIter {
     int32_t a[kMaxOrderTc];    // first k-2 SNPs (ascending)
     int32_t c;                 // last prefix SNP (panel)
     uint64_t q;                // index in panel order
 };
 
-__device__ inline void prefix_unrank(const DevData &d, int k, uint64_t q, PrefixIter &it)
+// Subsets of [0, c) of size m with first element >= x: C(c - x, m) (0 when
+// c - x < m); for m = 0 the single empty subset, which has no first element
+// and counts for every x.
+__device__ __forceinline__ uint64_t subsets_from(const DevData &d, int64_t c, int64_t x, int m)
 {
-    // panel: largest c with C(c, k-1) <= q
-    int64_t lo = k - 2, hi = d.n - 2;
+    if (m == 0) return 1;
+    return c - x >= m ? binom_at(d.binom, d.n, c - x, m) : 0;
+}
+
+// Lexicographic unranking of r among the m-subsets of [0, c) (m <= 3).
+__device__ inline void lex_unrank_below(const DevData &d, int64_t c, int m, uint64_t r, int32_t *out)
+{
+    int64_t start = 0;
+    for (int i = 0; i < m; i++) {
+        const int rem = m - i;
+        const uint64_t all = binom_at(d.binom, d.n, c - start, rem);
+        // largest x in [start, c - rem] with fewer than r + 1 subsets whose
+        // element i is below x
+        int64_t lo = start, hi = c - rem;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (all - binom_at(d.binom, d.n, c - mid, rem) <= r) lo = mid;
+            else hi = mid - 1;
+        }
+        r -= all - binom_at(d.binom, d.n, c - lo, rem);
+        out[i] = (int32_t)lo;
+        start = lo + 1;
+    }
+}
+
+__device__ inline void prefix_unrank(const DsParams &P, int k, uint64_t q, PrefixIter &it)
+{
+    const DevData &d = P.d;
+    // panel: largest c with pcum[c] <= q (a non-empty panel)
+    int64_t lo = 0, hi = d.n - 2;
     while (lo < hi) {
         const int64_t mid = (lo + hi + 1) >> 1;
-        if (binom_at(d.binom, d.n, mid, k - 1) <= q) lo = mid;
+        if (P.pcum[mid] <= q) lo = mid;
         else hi = mid - 1;
     }
     it.c = (int32_t)lo;
     it.q = q;
-    uint64_t r = q - binom_at(d.binom, d.n, lo, k - 1);
-    // colexicographic unranking of the first k-2 SNPs within [0, c)
-    int64_t top = lo - 1;
-    for (int i = k - 3; i >= 0; i--) {
-        int64_t l2 = i, h2 = top;
-        while (l2 < h2) {
-            const int64_t mid = (l2 + h2 + 1) >> 1;
-            if (binom_at(d.binom, d.n, mid, i + 1) <= r) l2 = mid;
-            else h2 = mid - 1;
-        }
-        it.a[i] = (int32_t)l2;
-        r -= binom_at(d.binom, d.n, l2, i + 1);
-        top = l2 - 1;
-    }
+    const int m2 = k - 2;
+    // index within the panel: the subsets whose first SNP is below s1_lo come first
+    const uint64_t skip = subsets_from(d, lo, 0, m2) - subsets_from(d, lo, P.s1_lo, m2);
+    lex_unrank_below(d, lo, m2, (m2 ? skip : 0) + (q - P.pcum[lo]), it.a);
 }
 
-__device__ inline void prefix_next(int k, PrefixIter &it)
+__device__ inline void prefix_next(const DsParams &P, int k, PrefixIter &it)
 {
     it.q++;
     const int m2 = k - 2;
-    int i = 0;
-    while (i < m2) {
-        const int32_t lim = (i + 1 < m2) ? it.a[i + 1] : it.c;
-        if (it.a[i] + 1 < lim) break;
-        i++;
-    }
-    if (i < m2) {
+    // lexicographic successor within the panel: the last position that can
+    // still grow; the first SNP must stay <= s1_hi
+    int i = m2 - 1;
+    while (i >= 0 && it.a[i] >= it.c - m2 + i) i--;
+    if (i > 0 || (i == 0 && it.a[0] + 1 <= P.s1_hi)) {
         it.a[i]++;
-        for (int t = 0; t < i; t++) it.a[t] = t;
+        for (int t = i + 1; t < m2; t++) it.a[t] = it.a[t - 1] + 1;
         return;
     }
+    // next panel (every panel after a non-empty one is non-empty): its first
+    // prefix starts at s1_lo
     it.c++;
-    for (int t = 0; t < m2; t++) it.a[t] = t;
+    for (int t = 0; t < m2; t++) it.a[t] = P.s1_lo + t;
 }
 
 __device__ __forceinline__ int64_t ntiles_of(const DevData &d, int32_t c) { return (d.n - 1 - c + kJ - 1) / kJ; }
@@ -441,11 +472,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
             const int32_t c0 = (int32_t)lo;
             const uint64_t off = w0 - DS.item_cum[c0];
             const int64_t nt0 = ntiles_of(d, c0);
-            const uint64_t tfirst = (binom_at(d.binom, d.n, c0, km1) + kPPT - 1) / kPPT;
+            const uint64_t tfirst = (DS.pcum[c0] + kPPT - 1) / kPPT;
             const uint64_t t = tfirst + off / (uint64_t)nt0;
             int64_t u = (int64_t)(off % (uint64_t)nt0);
             PrefixIter it;
-            prefix_unrank(d, K, t * (uint64_t)kPPT, it);
+            prefix_unrank(DS, K, t * (uint64_t)kPPT, it);
             int32_t tile_snp[kPPT * km1];
             int32_t nvalid = 0, cmin = it.c;
             auto fill_tile = [&]() {
@@ -458,7 +489,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                         for (int s2 = 0; s2 < km1 - 1; s2++) tile_snp[p * km1 + s2] = it.a[s2];
                         tile_snp[p * km1 + km1 - 1] = it.c;
                         nvalid++;
-                        prefix_next(K, it);
+                        prefix_next(DS, K, it);
                     }
                 }
             };
@@ -684,6 +715,20 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
             int32_t psnp[km1];
 #pragma unroll
             for (int tt = 0; tt < km1; tt++) psnp[tt] = prow ? D.snp[p * km1 + tt] : 0;
+            // last SNPs of this prefix inside the searched rank range: the
+            // combination (prefix, j) has rank base + j
+            int32_t jlo = cpre + 1, jhi = (int32_t)d.n;
+            if (prow) {
+                uint64_t sp = 0;
+#pragma unroll
+                for (int tt = 0; tt < km1; tt++) sp += binom_at(d.binom, d.n, d.n - 1 - psnp[tt], K - tt);
+                const int64_t base = (int64_t)DS.total - (int64_t)sp - d.n;
+                int64_t lo64 = (int64_t)DS.rank_begin - base, hi64 = (int64_t)DS.rank_end - base;
+                lo64 = lo64 < (int64_t)jlo ? (int64_t)jlo : (lo64 > d.n ? d.n : lo64);
+                hi64 = hi64 > d.n ? d.n : (hi64 < lo64 ? lo64 : hi64);
+                jlo = (int32_t)lo64;
+                jhi = (int32_t)hi64;
+            }
             const uint32_t T1 = tot[((b * 128 + r) * 2 + 0) * 2 + 0] + tot[((b * 128 + r) * 2 + 1) * 2 + 0];
             const uint32_t T0 = tot[((b * 128 + r) * 2 + 0) * 2 + 1] + tot[((b * 128 + r) * 2 + 1) * 2 + 1];
             // row totals in accumulator units (count / 32, exact)
@@ -726,7 +771,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                         const float fa0 = __uint_as_float(cs[2 * jj]), fa1 = __uint_as_float(cs[2 * jj + 1]);
                         const float fb0 = __uint_as_float(cn[2 * jj]), fb1 = __uint_as_float(cn[2 * jj + 1]);
                         const float fa2 = fT1 - fa0 - fa1, fb2 = fT0 - fb0 - fb1;
-                        const bool valid = prow && j < d.n && j > cpre;
+                        const bool valid = prow && j >= jlo && j < jhi;
                         if (P.dump && valid) {
                             uint64_t rs = 0;
 #pragma unroll
@@ -756,7 +801,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                         const float tv = wred[jhalf][0][lane] + wred[jhalf][1][lane] + wred[jhalf][2][lane] +
                                          wred[jhalf][3][lane];
                         const int32_t j = j0 + 8 * jc + lane;
-                        const bool valid = prow && j < d.n && j > cpre;
+                        const bool valid = prow && j >= jlo && j < jhi;
                         wflag[jhalf][lane] = (valid && fmaf(tv, vscale, voff) >= cut) ? 1 : 0;
                     }
                     epi_bar();
@@ -810,7 +855,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                     const float fa0 = __uint_as_float(cs[2 * jj]), fa1 = __uint_as_float(cs[2 * jj + 1]);
                     const float fb0 = __uint_as_float(cn[2 * jj]), fb1 = __uint_as_float(cn[2 * jj + 1]);
                     const float fa2 = fT1 - fa0 - fa1, fb2 = fT0 - fb0 - fb1;
-                    const bool valid = prow && j < d.n && j > cpre;
+                    const bool valid = prow && j >= jlo && j < jhi;
                     if (P.dump && valid) {
                         const uint32_t a0 = f2u_exact(32.0f * fa0), a1 = f2u_exact(32.0f * fa1),
                                        a2 = f2u_exact(32.0f * fa2);
@@ -895,22 +940,19 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
     if (tid == 0 && abort_flag) atomicOr(P.status, ST_TIMEOUT);
 }
 
-// Items per panel: the M tiles whose first prefix lies in panel c, times the
-// N tiles of that panel; exclusive prefix sum over c (one block).
-__global__ void __launch_bounds__(1024) item_cum_kernel(DevData d, int k, int ppt, uint64_t *cum)
+// Prefixes searched per panel (first SNP in [a, b]) and their exclusive
+// prefix sum over c into pcum; then items per panel (the M tiles whose first
+// prefix lies in panel c, times the N tiles of that panel) and their
+// exclusive prefix sum into cum.  One block.
+__device__ __forceinline__ uint64_t panel_prefixes(const DevData &d, int k, int64_t c, int64_t a, int64_t b)
 {
-    __shared__ uint64_t part[1024];
-    const int64_t n = d.n;
-    const int64_t per = (n + 1023) / 1024;
-    const int64_t b = (int64_t)threadIdx.x * per, e = min(n, b + per);
-    auto items = [&](int64_t c) -> uint64_t {
-        if (c < k - 2 || c > n - 2) return 0;
-        const uint64_t t0 = (binom_at(d.binom, n, c, k - 1) + ppt - 1) / ppt;
-        const uint64_t t1 = (binom_at(d.binom, n, c + 1, k - 1) + ppt - 1) / ppt;
-        return (t1 - t0) * (uint64_t)((n - 1 - c + kJ - 1) / kJ);
-    };
-    uint64_t s = 0;
-    for (int64_t c = b; c < e; c++) s += items(c);
+    if (c < k - 2 || c > d.n - 2) return 0;
+    if (k == 2) return (c >= a && c <= b) ? 1 : 0;
+    return subsets_from(d, c, a, k - 2) - subsets_from(d, c, b + 1, k - 2);
+}
+
+__device__ void block_exclusive_scan(uint64_t *part, uint64_t s, uint64_t &before, uint64_t &total)
+{
     part[threadIdx.x] = s;
     __syncthreads();
     for (int off = 1; off < 1024; off <<= 1) {
@@ -919,12 +961,41 @@ __global__ void __launch_bounds__(1024) item_cum_kernel(DevData d, int k, int pp
         part[threadIdx.x] += v;
         __syncthreads();
     }
-    uint64_t run = part[threadIdx.x] - s;
-    for (int64_t c = b; c < e; c++) {
+    before = part[threadIdx.x] - s;
+    total = part[1023];
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(1024) item_cum_kernel(DevData d, int k, int ppt, int32_t a, int32_t b,
+                                                        uint64_t *pcum, uint64_t *cum)
+{
+    __shared__ uint64_t part[1024];
+    const int64_t n = d.n;
+    const int64_t per = (n + 1023) / 1024;
+    const int64_t cb = (int64_t)threadIdx.x * per, ce = min(n, cb + per);
+    uint64_t s = 0, run = 0, all = 0;
+    for (int64_t c = cb; c < ce; c++) s += panel_prefixes(d, k, c, a, b);
+    block_exclusive_scan(part, s, run, all);
+    for (int64_t c = cb; c < ce; c++) {
+        pcum[c] = run;
+        run += panel_prefixes(d, k, c, a, b);
+    }
+    if (threadIdx.x == 1023) pcum[n] = all;
+    __syncthreads();
+    auto items = [&](int64_t c) -> uint64_t {
+        if (c < k - 2 || c > n - 2) return 0;
+        const uint64_t t0 = (pcum[c] + ppt - 1) / ppt;
+        const uint64_t t1 = (pcum[c + 1] + ppt - 1) / ppt;
+        return (t1 - t0) * (uint64_t)((n - 1 - c + kJ - 1) / kJ);
+    };
+    s = 0;
+    for (int64_t c = cb; c < ce; c++) s += items(c);
+    block_exclusive_scan(part, s, run, all);
+    for (int64_t c = cb; c < ce; c++) {
         cum[c] = run;
         run += items(c);
     }
-    if (threadIdx.x == 1023) cum[n] = part[1023];
+    if (threadIdx.x == 1023) cum[n] = all;
 }
 
 // B operand: row 2j+g (g = 0, 1) of SNP j, K byte 32 w + 4 i + b = individual
@@ -980,21 +1051,57 @@ cudaError_t launch_build_b8(const DevData &d, unsigned char *b8, int num_sms, cu
     return cudaGetLastError();
 }
 
-// Work items of an order-k search (same formula as item_cum_kernel): the
-// host needs the count to split items over the CTAs.
 static int tc_pr(int k) { return k == 2 ? 3 : (k == 3 ? 9 : (k == 4 ? 27 : 81)); }
 static int tc_ppt(int k) { return tc_pr(k) > 32 ? 1 : 4 * (32 / tc_pr(k)); }
 
-uint64_t tc_item_count(int64_t n, int k)
+// Work items of an order-k search over first SNPs [a, b] (same formulas as
+// item_cum_kernel): the host needs the count to split items over the CTAs.
+static uint64_t host_subsets_from(int64_t c, int64_t x, int m)
+{
+    if (m == 0) return 1;
+    return c - x >= m ? host_binom(c - x, m) : 0;
+}
+
+uint64_t tc_item_count(int64_t n, int k, int64_t a, int64_t b)
 {
     const uint64_t ppt = (uint64_t)tc_ppt(k);
-    uint64_t total = 0;
+    uint64_t total = 0, pc = 0;
     for (int64_t c = k - 2; c <= n - 2; c++) {
-        const uint64_t t0 = (host_binom(c, k - 1) + ppt - 1) / ppt;
-        const uint64_t t1 = (host_binom(c + 1, k - 1) + ppt - 1) / ppt;
+        uint64_t cnt;
+        if (k == 2) cnt = (c >= a && c <= b) ? 1 : 0;
+        else cnt = host_subsets_from(c, a, k - 2) - host_subsets_from(c, b + 1, k - 2);
+        const uint64_t t0 = (pc + ppt - 1) / ppt;
+        pc += cnt;
+        const uint64_t t1 = (pc + ppt - 1) / ppt;
         total += (t1 - t0) * (uint64_t)((n - 1 - c + tc::kJ - 1) / tc::kJ);
     }
     return total;
+}
+
+uint64_t tc_item_count(int64_t n, int k) { return tc_item_count(n, k, 0, n - k); }
+
+// First SNP of the combination of lexicographic rank r: the largest s with
+// C(n, k) - C(n - s, k) <= r (the combinations starting below s come first).
+int64_t tc_first_snp(int64_t n, int k, uint64_t r)
+{
+    const uint64_t total = host_binom(n, k);
+    int64_t lo = 0, hi = n - k;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (total - host_binom(n - mid, k) <= r) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Combinations the tensor path counts for the rank range [rb, re): every
+// combination whose first SNP lies in [first SNP of rb, first SNP of re - 1].
+uint64_t tc_range_work(int64_t n, int k, uint64_t rb, uint64_t re)
+{
+    if (re <= rb) return 0;
+    const int64_t a = tc_first_snp(n, k, rb), b = tc_first_snp(n, k, re - 1);
+    // combinations whose first SNP is >= a, minus those whose first SNP is > b
+    return host_binom(n - a, k) - host_binom(n - b - 1, k);
 }
 
 int tc_prefixes_per_warp(int k)
@@ -1028,14 +1135,24 @@ static cudaError_t encode_map(CUtensorMap *map, const DevData &d, const unsigned
 // Per-dataset parameters (host side); the B-operand map goes to tmap_dev when
 // the launch is batched (nullptr: passed as a kernel parameter instead).
 static void fill_ds(tc::DsParams &D, const DevData &d, int k, uint64_t *item_cum, uint32_t *global_thr,
-                    uint64_t total, const CUtensorMap *tmap_dev, int cta_begin, int cta_count)
+                    uint64_t total, uint64_t rb, uint64_t re, const CUtensorMap *tmap_dev, int cta_begin,
+                    int cta_count)
 {
     D.d = d;
-    unsigned __int128 np = 1;
-    for (int t = 0; t < k - 1; t++) np = np * (unsigned __int128)(d.n - 1 - t) / (unsigned __int128)(t + 1);
-    D.n_prefix = (uint64_t)np;
-    D.n_items = tc_item_count(d.n, k);
+    D.rank_begin = rb;
+    D.rank_end = re;
+    D.s1_lo = (int32_t)tc_first_snp(d.n, k, rb);
+    D.s1_hi = (int32_t)tc_first_snp(d.n, k, re - 1);
+    // prefixes whose first SNP lies in [s1_lo, s1_hi]
+    uint64_t np = 0;
+    for (int64_t c = k - 2; c <= d.n - 2; c++) {
+        if (k == 2) np += (c >= D.s1_lo && c <= D.s1_hi) ? 1 : 0;
+        else np += host_subsets_from(c, D.s1_lo, k - 2) - host_subsets_from(c, D.s1_hi + 1, k - 2);
+    }
+    D.n_prefix = np;
+    D.n_items = tc_item_count(d.n, k, D.s1_lo, D.s1_hi);
     D.item_cum = item_cum;
+    D.pcum = item_cum + d.n + 1;
     const int64_t Kt = (int64_t)d.Wt * 32;
     D.chunks = (int)(Kt / tc::kKC);
     D.chunks_case = (int)((int64_t)d.W1 * 32 / tc::kKC);
@@ -1088,24 +1205,26 @@ static cudaError_t launch_kernel(const CUtensorMap &map, const tc::Params &P, in
     return cudaGetLastError();
 }
 
-cudaError_t launch_tc_item_cum(const DevData &d, int k, uint64_t *item_cum, cudaStream_t st)
+cudaError_t launch_tc_item_cum(const DevData &d, int k, uint64_t rb, uint64_t re, uint64_t *item_cum,
+                               cudaStream_t st)
 {
-    tc::item_cum_kernel<<<1, 1024, 0, st>>>(d, k, tc_ppt(k), item_cum);
+    const int32_t a = (int32_t)tc_first_snp(d.n, k, rb), b = (int32_t)tc_first_snp(d.n, k, re - 1);
+    tc::item_cum_kernel<<<1, 1024, 0, st>>>(d, k, tc_ppt(k), a, b, item_cum + d.n + 1, item_cum);
     return cudaGetLastError();
 }
 
 cudaError_t launch_tc_search(const DevData &d, int k, const unsigned char *b8, uint64_t *item_cum, int pool,
                              uint32_t *global_thr, float *list_score, uint64_t *list_rank, int32_t *list_count,
-                             int32_t *status, int grid, uint64_t total, cudaStream_t st, int *cand_p2_out,
-                             uint32_t *dump, unsigned long long *waits)
+                             int32_t *status, int grid, uint64_t total, uint64_t rb, uint64_t re, cudaStream_t st,
+                             int *cand_p2_out, uint32_t *dump, unsigned long long *waits)
 {
     tc::Params P;
-    fill_ds(P.one, d, k, item_cum, global_thr, total, nullptr, 0, grid);
+    fill_ds(P.one, d, k, item_cum, global_thr, total, rb, re, nullptr, 0, grid);
     P.many = nullptr;
     P.cta_ds = nullptr;
     fill_launch(P, k, pool, list_score, list_rank, list_count, status, dump, waits);
     *cand_p2_out = P.cand_p2;
-    cudaError_t e = launch_tc_item_cum(d, k, item_cum, st);
+    cudaError_t e = launch_tc_item_cum(d, k, rb, re, item_cum, st);
     if (e != cudaSuccess) return e;
     CUtensorMap map;
     e = encode_map(&map, d, b8);
@@ -1119,7 +1238,7 @@ cudaError_t tc_fill_batch_entry(void *ds_host, void *tmap_host, const DevData &d
                                 uint64_t *item_cum, uint32_t *global_thr, uint64_t total, const void *tmap_dev,
                                 int cta_begin, int cta_count)
 {
-    fill_ds(*static_cast<tc::DsParams *>(ds_host), d, k, item_cum, global_thr, total,
+    fill_ds(*static_cast<tc::DsParams *>(ds_host), d, k, item_cum, global_thr, total, 0, total,
             static_cast<const CUtensorMap *>(tmap_dev), cta_begin, cta_count);
     return encode_map(static_cast<CUtensorMap *>(tmap_host), d, b8);
 }

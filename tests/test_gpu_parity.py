@@ -164,18 +164,27 @@ def test_batched_high_orders(epi, ctx):
         assert (r.combs == single.combs).all() and np.array_equal(r.mi, single.mi)
 
 
-def test_sharded_ranges_merge_to_the_full_search(epi, ctx):
-    """The sharding hook on the GPU: range searches of a three-way rank
-    split, merged by (MI desc, rank asc), give the whole search's top-N."""
+@pytest.mark.parametrize("path,k,world", [("popc", 3, 3), ("tc", 3, 3), ("tc", 4, 5), ("tc", 2, 4)])
+def test_sharded_ranges_merge_to_the_full_search(epi, ctx, path, k, world):
+    """The sharding hook on the GPU: every range search of a rank split
+    against the oracle's search of the same range, and the ranges' records,
+    merged by (MI desc, rank asc), against the oracle's whole top-N."""
     from paper_2201_02460_gb300 import shard
-    geno, pheno = random_data(60, 700, seed=21)
+    n = {2: 200, 3: 60, 4: 30}[k]
+    geno, pheno = random_data(n, 700, seed=21 + k)
     ds = epi.Dataset(ctx, geno, pheno)
-    k, t = 3, 40
-    total = O.binom(60, k)
-    parts = [epi.search(ds, k, t, path="popc", rank_range=(b, e)).records for b, e in shard.rank_ranges(total, 3)]
+    t = 40
+    total = O.binom(n, k)
+    parts = []
+    for b, e in shard.rank_ranges(total, world):
+        r = epi.search(ds, k, t, path=path, rank_range=(b, e))
+        oc, om, _ = O.search(geno, pheno, k, t, rank_begin=b, rank_end=e)
+        _check_result(r, geno, pheno, oc, om)
+        assert all(b <= int(x) < e for x in r.rank)
+        parts.append(r.records)
     got = shard.merge_topn(parts, t)
-    full = epi.search(ds, k, t, path="popc")
-    assert (got["rank"] == full.records["rank"]).all() and (got["mi"] == full.records["mi"]).all()
+    oc, om, _ = O.search(geno, pheno, k, t)
+    check_topn(got["snp"][:, :k], got["mi"], oc, om)
 
 
 def test_search_with_exact_ties(epi, ctx):
@@ -194,13 +203,15 @@ def test_search_single_or_nearly_single_class(epi, ctx, m1):
     _check_result(r, geno, pheno, oc, om)
 
 
-@pytest.mark.parametrize("k", [2, 3, 4])
-def test_search_range(epi, ctx, k):
-    n = {2: 300, 3: 80, 4: 40}[k]
+@pytest.mark.parametrize("path", ["popc", "tc"])
+@pytest.mark.parametrize("k", [2, 3, 4, 5])
+def test_search_range(epi, ctx, k, path):
+    n = {2: 300, 3: 80, 4: 40, 5: 24}[k]
     geno, pheno = random_data(n, 513, seed=11 + k)
     total = O.binom(n, k)
-    for r0, r1 in [(0, 1), (17, 5000), (total // 3, total // 3 + 77777), (total - 999, total + 10)]:
-        ds, r, oc, om, _ = _search_both(epi, ctx, geno, pheno, k, 30, rank_range=(r0, r1))
+    for r0, r1 in [(0, 1), (17, 5000), (total // 3, total // 3 + 77777), (total - 999, total + 10),
+                   (total // 2, total // 2 + 1)]:
+        ds, r, oc, om, _ = _search_both(epi, ctx, geno, pheno, k, 30, path=path, rank_range=(r0, r1))
         _check_result(r, geno, pheno, oc, om)
         assert all(r0 <= int(x) < r1 for x in r.rank)
 
@@ -375,11 +386,15 @@ def test_tc_unsupported_cases(epi, ctx):
     assert e.value.status == epi.EPI_EUNSUPPORTED
     geno, pheno = random_data(20, 100, seed=1)
     ds = epi.Dataset(ctx, geno, pheno)
-    with pytest.raises(epi.EpiError):
-        epi.search(ds, 3, 10, path="tc", rank_range=(0, 100))
-    # auto falls back to the popcount path for a range
+    with pytest.raises(epi.EpiError) as e:
+        epi.search(ds, 6, 10, path="tc")
+    assert e.value.status == epi.EPI_EUNSUPPORTED
+    # a short range: auto takes the popcount path, the tensor path still
+    # answers when asked for
     r = epi.search(ds, 3, 10, path="auto", rank_range=(0, 100))
     assert len(r) == 10
+    t = epi.search(ds, 3, 10, path="tc", rank_range=(0, 100))
+    assert (t.combs == r.combs).all()
 
 
 def test_profile_trace_survives_scratch_growth(epi, ctx):
