@@ -262,6 +262,86 @@ def test_mlp_gradients_match_reference(epi, ctx, rows, hidden):
     net.close()
 
 
+def _grad_magnitudes(theta, X, t, n_in, h, rnd):
+    """Per gradient element: S, the sum of the absolute values of its terms
+    (the same chain rule with every factor replaced by its absolute value);
+    L, its largest single term; and A, the part of S that passes through ReLU
+    masks whose pre-activation lies within float32 rounding of zero (where the
+    library's float32 sum and the float64 reference may disagree about the
+    sign)."""
+    W1, b1, W2, b2, W3, b3 = M.unpack(np.asarray(theta, np.float64), n_in, h)
+    W1q, W2q, W3q = rnd(W1), rnd(W2), rnd(W3)
+    Xq = np.abs(rnd(np.asarray(X, np.float64)))
+    Z1 = rnd(np.asarray(X, np.float64)) @ W1q.T + b1
+    S_z1 = Xq @ np.abs(W1q.T) + np.abs(b1)
+    H1 = rnd(np.maximum(Z1, 0.0))
+    Z2 = H1 @ W2q.T + b2
+    S_z2 = H1 @ np.abs(W2q.T) + np.abs(b2)
+    H2 = rnd(np.maximum(Z2, 0.0))
+    y = H2 @ W3q + b3[0]
+    B = X.shape[0]
+    dy = np.abs(2.0 * (y - np.asarray(t, np.float64)) / B)
+    amb1 = np.abs(Z1) <= 1e-5 * S_z1
+    amb2 = np.abs(Z2) <= 1e-5 * S_z2
+    on1, on2 = (Z1 > 0) | amb1, (Z2 > 0) | amb2
+    D2 = np.outer(dy, np.abs(W3q)) * on2            # |dZ2| (ambiguous entries counted)
+    D2a = np.outer(dy, np.abs(W3q)) * amb2
+    D1 = (D2 @ np.abs(W2q)) * on1
+    D1a = (D2a @ np.abs(W2q)) * on1 + (D2 @ np.abs(W2q)) * amb1
+
+    def outer_max(P, Q):                            # max over rows b of P[b, i] Q[b, j]
+        out = np.zeros((P.shape[1], Q.shape[1]))
+        for b0 in range(0, P.shape[0], 64):
+            blk = P[b0:b0 + 64, :, None] * Q[b0:b0 + 64, None, :]
+            out = np.maximum(out, blk.max(axis=0))
+        return out
+
+    S = np.concatenate([(D1.T @ Xq).ravel(), D1.sum(0), (D2.T @ H1).ravel(), D2.sum(0), H2.T @ dy, [dy.sum()]])
+    L = np.concatenate([outer_max(D1, Xq).ravel(), D1.max(0), outer_max(D2, H1).ravel(), D2.max(0),
+                        (H2 * dy[:, None]).max(0), [dy.max()]])
+    A = np.concatenate([(D1a.T @ Xq).ravel(), D1a.sum(0), (D2a.T @ H1).ravel(), D2a.sum(0),
+                        np.zeros(h), [0.0]])
+    return S, L, A
+
+
+@pytest.mark.parametrize("rows,hidden", [(1, 64), (300, 64), (1000, 256)])
+def test_mlp_gradients_elementwise(epi, ctx, rows, hidden):
+    """Every gradient element against the float64 reference with the
+    library's BF16 storage points.  Both compute the same chain rule on the
+    same rounded operands; they differ by float32 accumulation (at most about
+    K 2^-24 S_i for K summed terms), by a stored BF16 activation that rounds to
+    the neighbouring value when its float32 and float64 pre-images straddle a
+    rounding boundary (one term off by at most 2^-7 of itself), and by ReLU
+    masks at pre-activations within rounding of zero.  Hence, per element i
+    with S_i the sum of the absolute values of its terms, L_i the largest
+    term and A_i the part through such masks:
+        |g_i - g_ref,i| <= 2^-6 L_i + 2^-12 S_i + A_i.
+    A wrong element (a dropped term, a wrong sign, a missing bias row) moves
+    g_i by a whole term or by g_i itself, beyond that bound except under
+    extreme cancellation; the median relative error must also stay at
+    float32 level."""
+    import torch
+    net = epi.MLP(ctx, 25, hidden, seed=11)
+    theta = net.params().astype(np.float64)
+    X, _ = _net_inputs(rows, 25, rows + 5)
+    # targets away from the predictions, so that dy = 2 (y - t) / B has no
+    # cancellation of its own
+    y_q, (_, _, _, _, H2, _, W3) = M.forward(theta, X, 25, hidden, rnd=_bf16)
+    scale = np.abs(H2) @ np.abs(W3) + 1.0
+    t = (y_q + 4.0 * scale * np.where(np.arange(rows) % 2 == 0, 1.0, -1.0)).astype(np.float32)
+    g, _ = net.gradients(torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda())
+    g = g.astype(np.float64)
+    g_q = M.gradients(theta, X, t, 25, hidden, rnd=_bf16)
+    S, L, A = _grad_magnitudes(theta, X, t, 25, hidden, _bf16)
+    err = np.abs(g - g_q)
+    bound = 2.0 ** -6 * L + 2.0 ** -12 * S + A + 1e-30
+    worst = int(np.argmax(err / bound))
+    assert (err <= bound).all(), (worst, g[worst], g_q[worst], S[worst], L[worst], A[worst])
+    nz = np.abs(g_q) > 1e-3 * S
+    assert np.median(err[nz] / np.abs(g_q[nz])) <= 1e-4
+    net.close()
+
+
 def test_mlp_adamw_steps_match_reference(epi, ctx):
     import torch
     h = 64
