@@ -232,6 +232,97 @@ def measure_batch(epi, ctx, synth, n_div, steps=2):
                 snp_divisor=n_div, timing="host wall clock around the synchronous batched call")
 
 
+def measure_count_variants(epi, ctx, synth, flush, stream):
+    """The GPU counterpart of the paper's popcount comparison (Table 1): every
+    order-3 table of the first 500 SNPs of the 2000 x 4000 workload counted
+    with the POPC instruction, a byte lookup table in shared memory, and the
+    binary tensor-core MMA (AND + POPC), each run twice (the second timed);
+    paper work 3^k (W1 + W0) 32-bit word operations per combination, against
+    the POPC pipe's rate.  The FP8 tensor-core search of the same dataset is
+    timed beside them (it also scores and selects)."""
+    import torch
+    d, k, top_n = synth.make_workload("order3_2000snp_4000", n_snps=500)
+    ds = epi.Dataset(ctx, d.geno, d.pheno)
+    W = 4 * (-(-d.n_cases // 128) + -(-(d.n_samples - d.n_cases) // 128))
+    ops = math.comb(d.n_snps, k) * 3 ** k * W
+    peak = N_SMS * POPC_PER_SM_CLK * SM_MAX_MHZ * 1e6
+    out = {}
+    sums = set()
+    for v in ("popc", "lut", "mma_b1"):
+        epi.count_variant(ds, k, v)
+        r = epi.count_variant(ds, k, v)
+        sums.add(r["checksum"])
+        out[v] = dict(ms=r["ms"], word_ops_per_s=ops / (r["ms"] / 1e3), frac_of_popc_peak=ops / (r["ms"] / 1e3) / peak)
+    m = time_search(epi, ctx, ds, k, top_n, "tc", 2, 1, flush, stream)
+    out["tc_fp8_search"] = dict(ms=m["t_ms"] / 2, word_ops_per_s=ops / (m["t_ms"] / 2 / 1e3),
+                                note="whole search (count, score, top-N), paper work in the same units")
+    ds.close()
+    out["checksums_agree"] = len(sums) == 1
+    out["workload"] = f"order 3, {d.n_snps} SNPs x {d.n_samples} samples, every table"
+    return out
+
+
+def measure_batch_full(epi, ctx, synth, peaks, tc_rate, stream):
+    """The 64-dataset batched configuration at its configured sizes (SNPs
+    ~ U{100..1000}, samples ~ U{1000..16000}, case fraction ~ U[0.3, 0.7],
+    orders ~ U{2, 3, 4}, top-20 each): the autotuner first runs once per size
+    bucket, then one epi_search_batched call (its first: the graph is captured
+    and launched) is timed with CUDA events on the context's stream.  The
+    scheduler efficiency is the time every dataset would take alone at its
+    path's peak (paper work: 2*3^k*m flop per combination on the tensor path
+    against the measured MMA rate, 3^k*(W1+W0) word operations on the popcount
+    path against the POPC rate), summed, over the measured time."""
+    import torch
+    specs = synth.batch_specs()
+    dss, orders, tops, data = [], [], [], []
+    for sp in specs:
+        d = synth.make_dataset(sp["n_snps"], sp["n_cases"], sp["n_controls"], seed=sp["seed"], maf_lo=sp["maf_lo"])
+        dss.append(epi.Dataset(ctx, d.geno, d.pheno))
+        orders.append(sp["order"])
+        tops.append(sp["top_n"])
+        data.append(d)
+    # autotune one dataset per (order, log2 SNPs, log2 sample words) bucket
+    t0 = time.perf_counter()
+    chosen = {}
+    for ds, d, k in zip(dss, data, orders):
+        wt = 4 * (-(-d.n_cases // 128) + -(-(d.n_samples - d.n_cases) // 128))
+        key = (k, d.n_snps.bit_length() - 1, wt.bit_length() - 1)
+        if key not in chosen:
+            chosen[key] = epi.autotune(ds, k)
+    tune_s = time.perf_counter() - t0
+    tc_peak = 2.0 * tc_rate["mac_per_clk_sm"] * N_SMS * SM_MAX_MHZ * 1e6 if tc_rate else FP8_OVER_BF16 * peaks["bf16"] * 1e12
+    popc_peak = N_SMS * POPC_PER_SM_CLK * SM_MAX_MHZ * 1e6
+    work = 0
+    ideal_s = 0.0
+    for d, k in zip(data, orders):
+        wt = 4 * (-(-d.n_cases // 128) + -(-(d.n_samples - d.n_cases) // 128))
+        key = (k, d.n_snps.bit_length() - 1, wt.bit_length() - 1)
+        total = math.comb(d.n_snps, k)
+        work += total * d.n_samples
+        if chosen[key]["path"] == "tc":
+            ideal_s += 2.0 * total * 3 ** k * d.n_samples / tc_peak
+        else:
+            ideal_s += total * 3 ** k * wt / popc_peak
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    epi.search_batched(ctx, dss, orders, tops)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    for ds in dss:
+        ds.close()
+    paths = {}
+    for (k, _, _), c in chosen.items():
+        nm = f"order{k}/{c['path']}"
+        paths[nm] = paths.get(nm, 0) + 1
+    return dict(value=work / t, ms_per_step=1e3 * t, datasets=len(specs), combination_samples=work,
+                scheduler_efficiency=ideal_s / t, ideal_seconds=ideal_s, autotune_seconds=tune_s,
+                tuned_buckets=paths,
+                timing="CUDA events on the context's stream around the first batched call (graph capture and "
+                       "launch; capture is host work of milliseconds)")
+
+
 def measure_proposer(epi, ctx, ds, peaks, top_triples=256, budget=4096):
     """Order-5 proposal search on the given dataset: candidates ranked per
     second by the network (fused tensor-core inference; weights as
@@ -266,17 +357,46 @@ def measure_proposer(epi, ctx, ds, peaks, top_triples=256, budget=4096):
     return out
 
 
-def roofline(kind, d, k, kern_ms, peaks):
+def tc_executed_flops(d, k):
+    """Multiply-adds the tensor-core counting kernel issues for a whole search,
+    x 2: every work item is one M128 x N128 tile over the padded K of both
+    classes (128-individual stages), and the items are the M tiles of
+    ppt prefixes that start in panel c times the N tiles of 64 last SNPs
+    after c (the kernel's item table)."""
+    n = d.n_snps
+    ppt = 1 if 3 ** (k - 1) > 32 else 4 * (32 // 3 ** (k - 1))
+    items = 0
+    for c in range(k - 2, n - 1):
+        t0 = -(-math.comb(c, k - 1) // ppt)
+        t1 = -(-math.comb(c + 1, k - 1) // ppt)
+        items += (t1 - t0) * (-(-(n - 1 - c) // 64))
+    kt = 32 * 4 * (-(-d.n_cases // 128) + -(-(d.n_samples - d.n_cases) // 128))
+    return 2.0 * items * 128 * 128 * kt
+
+
+def roofline(kind, d, k, kern_ms, peaks, tc_rate=None):
     total = math.comb(d.n_snps, k)
     if kind == "tc":
-        # algorithmic work: 3^k cells x m individuals multiply-adds per combination
+        # algorithmic (paper) work: 3^k cells x m individuals multiply-adds
+        # per combination; executed: the MMAs the kernel issues (two genotype
+        # columns of the last SNP, padded rows and K)
         flops = 2.0 * total * (3 ** k) * d.n_samples
         achieved = flops / (kern_ms / 1e3) / 1e12
-        peak = FP8_OVER_BF16 * peaks["bf16_sustained"]
+        executed = tc_executed_flops(d, k) / (kern_ms / 1e3) / 1e12
+        fp8_conv = FP8_OVER_BF16 * peaks["bf16"]
+        if tc_rate:
+            # the measured rate of the kernel's own MMA, at the maximum SM clock
+            peak = 2.0 * tc_rate["mac_per_clk_sm"] * N_SMS * SM_MAX_MHZ * 1e6 / 1e12
+            note = (f"peak = measured FP8 M128 N128 K32 tcgen05.mma rate, {tc_rate['mac_per_clk_sm']:.0f} "
+                    f"MAC/clk/SM x 152 SMs x 2070 MHz (probe ran at {tc_rate['sm_mhz']:.0f} MHz: "
+                    f"{tc_rate['tflops']:.0f} TFLOP/s); work 2*3^k*m flop per combination")
+        else:
+            peak = fp8_conv
+            note = f"FP8 (E4M3) dense = 2 x {peaks['source']} burst BF16; work 2*3^k*m flop per combination"
         return dict(bound="tensor", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
                     traffic=None, kernel="tc_search_kernel", kernel_ms=kern_ms,
-                    note=f"FP8 (E4M3) dense = 2 x {peaks['source']} sustained BF16 "
-                         f"{peaks['bf16_sustained']} TFLOP/s; work 2*3^k*m flop per combination")
+                    executed_tflops=executed, executed_frac=executed / peak,
+                    frac_vs_2x_bf16=achieved / fp8_conv, note=note)
     W = ((d.n_cases + 127) // 128 + (d.n_samples - d.n_cases + 127) // 128) * 4
     ops = total * (3 ** k) * W
     achieved = ops / (kern_ms / 1e3) / 1e12
@@ -327,6 +447,8 @@ def run_ours(args):
         t_ms = float(tt.item())
     value = world * units * args.steps / (t_ms / 1e3)
     res = main_m["res"]
+    # the roofline's denominator: the tensor pipe's rate for the counting MMA
+    tc_rate = ctx.tc_rate() if kind == "tc" or not args.no_compare else None
 
     # end to end through the C-ABI: host genotypes in, host records out
     e2e_times = []
@@ -349,7 +471,7 @@ def run_ours(args):
                 e2e=dict(value=units / e2e_t, unit=UNIT, h2d_bytes_per_step=int(d.geno.nbytes + d.pheno.nbytes),
                          d2h_bytes_per_step=int(top_n * epi.RESULT_DTYPE.itemsize + top_n * 2 * 3 ** k * 4),
                          seconds=e2e_t),
-                roofline=roofline(kind, d, k, main_m["kern_ms"], peaks),
+                roofline=roofline(kind, d, k, main_m["kern_ms"], peaks, tc_rate),
                 gpu_launches=int(main_m["launches"]), clocks=clocks,
                 top1=dict(snps=[int(x) for x in res.combs[0]], mi=float(res.mi[0]), planted=list(d.planted)))
     if kind == "tc" and main_m["waits"].get("mma_loop"):
@@ -363,19 +485,32 @@ def run_ours(args):
         if other:
             m2 = time_search(epi, ctx, ds, k, top_n, other, 2, 1, flush, stream)
             comp[f"{args.workload}/{other}"] = dict(value=units / (m2["t_ms"] / 2 / 1e3), ms_per_step=m2["t_ms"] / 2,
-                                                     roofline=roofline(other, d, k, m2["kern_ms"], peaks))
+                                                     roofline=roofline(other, d, k, m2["kern_ms"], peaks, tc_rate))
         if args.workload != "order4_500snp_8192":
             d4, k4, n4 = synth.make_workload("order4_500snp_8192")
             ds4 = epi.Dataset(ctx, d4.geno, d4.pheno)
             u4 = math.comb(d4.n_snps, k4) * d4.n_samples
             m4 = time_search(epi, ctx, ds4, k4, n4, "tc", 2, 1, flush, stream)
             comp["order4_500snp_8192/tc"] = dict(value=u4 / (m4["t_ms"] / 2 / 1e3), ms_per_step=m4["t_ms"] / 2,
-                                                 roofline=roofline("tc", d4, k4, m4["kern_ms"], peaks))
-            if args.full_compare:
+                                                 roofline=roofline("tc", d4, k4, m4["kern_ms"], peaks, tc_rate))
+            if not args.quick:
+                # one step (about 28 s): the popcount path on the same workload
                 p4 = time_search(epi, ctx, ds4, k4, n4, "popc", 1, 0, flush, stream)
                 comp["order4_500snp_8192/popc"] = dict(value=u4 / (p4["t_ms"] / 1e3), ms_per_step=p4["t_ms"],
                                                        roofline=roofline("popc", d4, k4, p4["kern_ms"], peaks))
             ds4.close()
+        if args.workload != "order2_200snp_1600":
+            # the order-2 workload (200 SNPs x 1600 samples): launch-bound,
+            # reported without a roofline
+            d2, k2, n2 = synth.make_workload("order2_200snp_1600")
+            ds2w = epi.Dataset(ctx, d2.geno, d2.pheno)
+            u2 = math.comb(d2.n_snps, k2) * d2.n_samples
+            m2w = time_search(epi, ctx, ds2w, k2, n2, "auto", 20, 3, flush, stream)
+            r2 = m2w["res"]
+            comp["order2_200snp_1600/auto"] = dict(value=u2 / (m2w["t_ms"] / 20 / 1e3), ms_per_step=m2w["t_ms"] / 20,
+                                                   kernel_ms=m2w["kern_ms"],
+                                                   top1=[int(x) for x in r2.combs[0]], planted=list(d2.planted))
+            ds2w.close()
         # thresholded output (every combination above an MI threshold; here
         # the 100th best of the top-N search): all scores on the popcount path
         torch.cuda.synchronize()
@@ -395,7 +530,10 @@ def run_ours(args):
                                                   cells_per_s=math.comb(d8.n_snps, k8) * 3 ** k8 / (m8["t_ms"] / 2 / 1e3),
                                                   roofline=roofline("popc", d8, k8, m8["kern_ms"], peaks))
             ds8.close()
+        comp["count_variants/order3_500snp_4000"] = measure_count_variants(epi, ctx, synth, flush, stream)
         comp["batch64/auto"] = measure_batch(epi, ctx, synth, args.batch_div)
+        if not args.quick:
+            comp["batch64_full/auto"] = measure_batch_full(epi, ctx, synth, peaks, tc_rate, stream)
         if d.n_snps >= 5:
             comp[f"proposer_order5/{args.workload}"] = measure_proposer(epi, ctx, ds, peaks)
         from paper_2201_02460_gb300 import proposer_eval
@@ -436,7 +574,8 @@ def main():
     ap.add_argument("--path", default="auto", choices=["popc", "tc", "auto"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the other path and the order-4 workload")
-    ap.add_argument("--full-compare", action="store_true", help="also time the order-4 popcount path (~26 s)")
+    ap.add_argument("--quick", action="store_true",
+                    help="skip the order-4 popcount leg (~28 s) and the full 64-dataset batch (~2 min)")
     ap.add_argument("--n-snps", type=int, default=None, help="smaller SNP count (profiling captures)")
     ap.add_argument("--batch-div", type=int, default=3, help="SNP-count divisor of the 64-dataset batch")
     ap.add_argument("--proposer-eval", action="store_true",

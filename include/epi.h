@@ -410,6 +410,38 @@ typedef struct epi_train_opts {
 epi_status epi_proposer_train(epi_mlp *net, epi_dataset *const *datasets, int n_ds, const epi_train_opts *opts,
                               float *epoch_loss);
 
+/* Every contingency table of order 2..4 (Section 2.2), its last level
+ * counted with one of three instructions, for comparing them (the paper
+ * compares popcount implementations the same way, Section 3.1, Table 1):
+ * variant 0 the POPC instruction, 1 a 256-entry byte lookup table in shared
+ * memory, 2 the binary tensor-core MMA (mma.sync m16n8k256, AND + POPC).
+ * Each prefix's genotype table is built once in shared memory and genotype 2
+ * of the last SNP comes by subtraction, as in the search.  *checksum
+ * receives sum over all tables and cells of count * (1 + cell + 3^k class),
+ * the same for every variant; tables (may be NULL) receives every table,
+ * host [C(n,k)][2][3^k] in lexicographic rank order (at most 2 GiB); *ms
+ * (may be NULL) the kernel's event time. */
+epi_status epi_count_variant(epi_dataset *ds, int order, int variant, uint32_t *tables, uint64_t *checksum,
+                             double *ms);
+
+/* Test controls of a context (the paper has no counterpart; they exist so
+ * that the failure paths can be exercised without faulting a GPU).
+ *
+ * epi_set_wait_limit: every pipeline wait of the tensor-core counting kernel
+ * (a role waiting for another role's stage, accumulator or descriptor) gives
+ * up after limit_ns nanoseconds instead of the default 2 s (0 restores the
+ * default).  A wait that gives up makes every role leave its loop, wait (with
+ * the default limit) for its own copies and MMAs in flight, free tensor
+ * memory and return; the search then fails with EPI_ETIMEOUT and the context
+ * stays usable.
+ *
+ * epi_inject_alloc_failure: the device allocation of this context's calls
+ * that comes after `after` further successful ones fails as if the device
+ * were out of memory (the call returns EPI_ENOMEM and releases what it had
+ * taken); it fires once.  A negative value cancels it. */
+epi_status epi_set_wait_limit(epi_ctx *ctx, uint64_t limit_ns);
+epi_status epi_inject_alloc_failure(epi_ctx *ctx, int64_t after);
+
 /* Rate of the tensor pipe for the one MMA the tensor-core counting path
  * issues (tcgen05.mma kind::f8f6f4, M128 N128 K32, E4M3 operands in shared
  * memory, FP32 accumulation): one CTA per SM issues `stages` (32..2^32)

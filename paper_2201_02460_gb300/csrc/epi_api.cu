@@ -41,6 +41,9 @@ struct epi_ctx {
     unsigned long long *waits_dev = nullptr;   // own buffer: per-role wait cycles of a profiled TC search
     int waits_grid = 0;                        // CTAs recorded in waits_dev (0: nothing recorded)
     bool destroy_requested = false;
+    // test controls (epi_set_wait_limit, epi_inject_alloc_failure)
+    unsigned long long wait_limit_ns = 0;   // tensor-core pipeline waits; 0 = the kernels' default
+    int64_t fail_alloc_in = -1;             // device allocations until one fails; -1 = none
 };
 
 struct epi_dataset {
@@ -113,6 +116,31 @@ bool is_device_ptr(const void *p, int device)
     return a.type == cudaMemoryTypeDevice && a.device == device;
 }
 
+// Every device allocation of a context's calls goes through these, so that a
+// test can make the n-th one fail as an exhausted device would.
+bool injected_alloc_failure(epi_ctx *ctx)
+{
+    if (ctx->fail_alloc_in < 0) return false;
+    if (ctx->fail_alloc_in == 0) {
+        ctx->fail_alloc_in = -1;
+        return true;
+    }
+    ctx->fail_alloc_in--;
+    return false;
+}
+
+cudaError_t ctx_malloc(epi_ctx *ctx, void **p, size_t bytes)
+{
+    if (injected_alloc_failure(ctx)) return cudaErrorMemoryAllocation;
+    return cudaMalloc(p, bytes);
+}
+
+cudaError_t ctx_malloc_async(epi_ctx *ctx, void **p, size_t bytes, cudaStream_t st)
+{
+    if (injected_alloc_failure(ctx)) return cudaErrorMemoryAllocation;
+    return cudaMallocAsync(p, bytes, st);
+}
+
 int pow3i(int k)
 {
     int r = 1;
@@ -144,7 +172,7 @@ epi_status ensure_scratch(epi_ctx *ctx, size_t bytes)
     }
     size_t want = std::max(bytes, (size_t)1 << 20);
     want = (want + ((1u << 20) - 1)) & ~(size_t)((1u << 20) - 1);
-    CK(cudaMalloc(&ctx->scratch, want));
+    CK(ctx_malloc(ctx, &ctx->scratch, want));
     ctx->scratch_bytes = want;
     return EPI_OK;
 }
@@ -275,7 +303,7 @@ epi_status ensure_b8(epi_dataset *ds)
 {
     if (ds->b8) return EPI_OK;
     epi_ctx *ctx = ds->ctx;
-    CK(cudaMalloc((void **)&ds->b8, tc_b8_bytes(ds->dev())));
+    CK(ctx_malloc(ctx, (void **)&ds->b8, tc_b8_bytes(ds->dev())));
     CK(launch_build_b8(ds->dev(), ds->b8, ctx->num_sms, ctx->stream));
     ctx->launches += 1;
     return EPI_OK;
@@ -312,6 +340,12 @@ epi_status queue_search(epi_dataset *ds, const SearchPlan &p, int path, epi_resu
     const size_t o_ic = a.take<uint64_t>(2 * ((size_t)ds->n + 1));
     const size_t o_pre =
         p.global_prefix ? a.take<uint32_t>((size_t)p.grid * p.slots * popc_slot_words(p.k, ds->Wt)) : 0;
+    // tensor path: candidate buffers in global memory when they do not fit
+    // beside the operand rings in shared memory (large pools)
+    const int tc_cp2 = p.tc ? tc_cand_p2(p.k, p.pool) : 0;
+    const bool tc_cg = p.tc && tc_smem_bytes(tc_cp2, p.k, false) > ctx->smem_optin;
+    const size_t o_tcs = tc_cg ? a.take<float>((size_t)p.grid * tc_cp2) : 0;
+    const size_t o_tcr = tc_cg ? a.take<uint64_t>((size_t)p.grid * tc_cp2) : 0;
     epi_status st = ensure_scratch(ctx, a.off);
     if (st != EPI_OK) return st;
     char *base = static_cast<char *>(ctx->scratch);
@@ -352,7 +386,9 @@ epi_status queue_search(epi_dataset *ds, const SearchPlan &p, int path, epi_resu
             ctx->waits_grid = p.grid;
         }
         CK(launch_tc_search(d, p.k, ds->b8, ic, p.pool, thr, ls, lr, lc, status, p.grid, p.total, p.rb, p.re,
-                            ctx->stream, &cand_p2, dump, waits));
+                            ctx->stream, &cand_p2, tc_cg ? reinterpret_cast<float *>(base + o_tcs) : nullptr,
+                            tc_cg ? reinterpret_cast<uint64_t *>(base + o_tcr) : nullptr, dump, waits,
+                            ctx->wait_limit_ns));
         ctx->launches += 1;   // item table
     } else {
         CK(launch_popc_search(d, p.k, p.R, p.rb, p.re, p.tile, p.pool, p.slots, p.cand_p2, thr, ls, lr, lc, p.grid,
@@ -418,7 +454,7 @@ epi_status run_search_sync(epi_dataset *ds, int order, int top_n, int path, uint
         const size_t rec_b = ((size_t)top_n * sizeof(epi_result) + 255) & ~(size_t)255;
         const size_t cnt_b = ((size_t)top_n * 2 * cells * 4 + 255) & ~(size_t)255;
         void *dout = nullptr;
-        CK(cudaMallocAsync(&dout, rec_b + cnt_b + 256, ctx->stream));
+        CK(ctx_malloc_async(ctx, &dout, rec_b + cnt_b + 256, ctx->stream));
         epi_result *out_dev = static_cast<epi_result *>(dout);
         uint32_t *cnt_dev = reinterpret_cast<uint32_t *>(static_cast<char *>(dout) + rec_b);
         int32_t *nout_dev = reinterpret_cast<int32_t *>(static_cast<char *>(dout) + rec_b + cnt_b);
@@ -480,6 +516,7 @@ struct BatchGroup {
     size_t smem = 0;
     std::vector<int> items;
     size_t o_desc = 0, o_tmap = 0, o_ctads = 0, o_ls = 0, o_lr = 0, o_lc = 0;
+    size_t o_tcs = 0, o_tcr = 0;   // tensor path: global candidate buffers (0: in shared memory)
 };
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) & ~(a - 1); }
@@ -551,7 +588,7 @@ epi_status ensure_batch_buffers(epi_ctx *ctx, size_t dev_bytes, size_t host_byte
         if (ctx->batch_dev) cudaFree(ctx->batch_dev);
         ctx->batch_dev = nullptr;
         ctx->batch_dev_bytes = 0;
-        CK(cudaMalloc(&ctx->batch_dev, dev_bytes));
+        CK(ctx_malloc(ctx, &ctx->batch_dev, dev_bytes));
         ctx->batch_dev_bytes = dev_bytes;
     }
     if (ctx->batch_host_bytes < host_bytes) {
@@ -585,7 +622,9 @@ epi_status record_batch(epi_ctx *ctx, std::vector<BatchItem> &items, std::vector
         // every CTA of a TC group reports a timeout through its dataset's status
         if (g.tc)
             CK(launch_tc_batch(dev + g.o_desc, ctads, g.k, g.pool, ls, lr, lc,
-                               reinterpret_cast<int32_t *>(dev + items[g.items[0]].o_status), g.grid, st));
+                               reinterpret_cast<int32_t *>(dev + items[g.items[0]].o_status), g.grid, st,
+                               g.o_tcs ? reinterpret_cast<float *>(dev + g.o_tcs) : nullptr,
+                               g.o_tcs ? reinterpret_cast<uint64_t *>(dev + g.o_tcr) : nullptr));
         else
             CK(launch_popc_batch(dev + g.o_desc, ctads, g.k, g.R, g.max_wt, g.tile, g.pool, g.slots, g.cand_p2, ls, lr,
                                  lc, g.grid, g.smem, st));
@@ -696,6 +735,10 @@ extern "C" epi_status epi_search_batched(epi_ctx *ctx, epi_dataset *const *dss, 
         g.o_ls = a.take<float>((size_t)g.grid * g.pool);
         g.o_lr = a.take<uint64_t>((size_t)g.grid * g.pool);
         g.o_lc = a.take<int32_t>((size_t)g.grid);
+        if (g.tc && tc_smem_bytes(tc_cand_p2(g.k, g.pool), g.k, false) > ctx->smem_optin) {
+            g.o_tcs = a.take<float>((size_t)g.grid * tc_cand_p2(g.k, g.pool));
+            g.o_tcr = a.take<uint64_t>((size_t)g.grid * tc_cand_p2(g.k, g.pool));
+        }
     }
     for (auto &it : items) {
         it.o_cs = a.take<float>((size_t)it.pool);
@@ -934,7 +977,7 @@ epi_status epi_search_threshold(epi_dataset *ds, int order, double threshold, in
     // FP32 screen: a combination with MI >= threshold scores at least
     // threshold (1 - bound) in single precision (the bound covers the
     // roundings of the 2 * 3^k terms); the FP64 value decides
-    const float thr32 = threshold > 0.0 ? (float)(threshold * (1.0 - 2.0 * f32_rel_bound(order))) : -INFINITY;
+    const float thr32 = threshold > 0.0 ? (float)(threshold * (1.0 - 2.0 * f32_rel_bound(order, ds->m))) : -INFINITY;
     const uint64_t ch = chunk > 0 ? std::min<uint64_t>((uint64_t)chunk, total) : std::min<uint64_t>(total, 1ull << 28);
     const int64_t slice = std::max<int64_t>(1, std::min<int64_t>(1 << 20, ((int64_t)256 << 20) / (8 * cells)));
     float *scores = nullptr;
@@ -1269,7 +1312,7 @@ epi_status epi_dataset_create(epi_ctx *ctx, const uint8_t *geno, const uint8_t *
         dgeno = const_cast<uint8_t *>(geno);
         dpheno = const_cast<uint8_t *>(pheno);
     } else {
-        CK(cudaMallocAsync((void **)&tmp, (size_t)(n * m + m), st));
+        CK(ctx_malloc_async(ctx, (void **)&tmp, (size_t)(n * m + m), st));
         dgeno = tmp;
         dpheno = tmp + n * m;
         CK(cudaMemcpyAsync(dgeno, geno, (size_t)(n * m), cudaMemcpyHostToDevice, st));
@@ -1277,7 +1320,15 @@ epi_status epi_dataset_create(epi_ctx *ctx, const uint8_t *geno, const uint8_t *
     }
     void *work = nullptr;
     const size_t work_bytes = (size_t)m * 8 + 64;
-    CK(cudaMallocAsync(&work, work_bytes, st));
+    {
+        const cudaError_t ew = ctx_malloc_async(ctx, &work, work_bytes, st);
+        if (ew != cudaSuccess) {
+            if (tmp) cudaFreeAsync(tmp, st);
+            cudaStreamSynchronize(st);
+            return fail(ew == cudaErrorMemoryAllocation ? EPI_ENOMEM : EPI_ECUDA, "dataset work buffer: %s",
+                        cudaGetErrorString(ew));
+        }
+    }
     int32_t *case_idx = static_cast<int32_t *>(work);
     int32_t *ctrl_idx = case_idx + m;
     // 2 m int32 entries end on an 8-byte boundary
@@ -1303,8 +1354,8 @@ epi_status epi_dataset_create(epi_ctx *ctx, const uint8_t *geno, const uint8_t *
         ds->W1 = (int32_t)(((m1 + 127) / 128) * 4);
         ds->W0 = (int32_t)(((m - m1 + 127) / 128) * 4);
         ds->Wt = ds->W1 + ds->W0;
-        cudaError_t e1 = cudaMalloc((void **)&ds->masks, (size_t)n * 3 * ds->Wt * 4);
-        cudaError_t e2 = cudaMalloc((void **)&ds->binom, (size_t)9 * (n + 1) * 8);
+        cudaError_t e1 = ctx_malloc(ctx, (void **)&ds->masks, (size_t)n * 3 * ds->Wt * 4);
+        cudaError_t e2 = ctx_malloc(ctx, (void **)&ds->binom, (size_t)9 * (n + 1) * 8);
         if (e1 != cudaSuccess || e2 != cudaSuccess) {
             ret = fail(EPI_ENOMEM, "dataset allocation failed");
         } else {
@@ -1499,6 +1550,66 @@ epi_status epi_debug_counts(epi_dataset *ds, int order, uint32_t *out)
     cudaFreeAsync(buf, ctx->stream);
     cudaStreamSynchronize(ctx->stream);
     return st;
+}
+
+epi_status epi_count_variant(epi_dataset *ds, int order, int variant, uint32_t *tables, uint64_t *checksum,
+                             double *ms)
+{
+    if (!ds || !checksum) return fail(EPI_EINVAL, "NULL argument");
+    if (order < 2 || order > 4) return fail(EPI_EINVAL, "order %d outside 2..4", order);
+    if (variant < 0 || variant > 2) return fail(EPI_EINVAL, "variant %d outside 0..2", variant);
+    if (order > ds->n) return fail(EPI_EINVAL, "order %d exceeds the %lld SNPs", order, (long long)ds->n);
+    epi_ctx *ctx = ds->ctx;
+    const uint64_t total = host_binom(ds->n, order);
+    const size_t cells = (size_t)pow3i(order);
+    const size_t bytes = tables ? (size_t)total * 2 * cells * 4 : 0;
+    if (tables && bytes > ((size_t)1 << 31)) return fail(EPI_EINVAL, "table dump limited to 2 GiB");
+    if (count_variant_smem_bytes(order, ds->Wt) > ctx->smem_optin)
+        return fail(EPI_EUNSUPPORTED, "one prefix table does not fit in shared memory");
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(EPI_ECUDA, "cannot select device %d", ctx->device);
+    void *buf = nullptr;
+    CK(ctx_malloc_async(ctx, &buf, bytes + 256, ctx->stream));
+    unsigned long long *sum = static_cast<unsigned long long *>(buf);
+    uint32_t *dtab = tables ? reinterpret_cast<uint32_t *>(static_cast<char *>(buf) + 256) : nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float t = 0.0f;
+    unsigned long long hsum = 0;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sum, 0, 8, ctx->stream);
+    if (e == cudaSuccess && dtab) e = cudaMemsetAsync(dtab, 0xff, bytes, ctx->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
+    if (e == cudaSuccess)
+        e = launch_count_variant(ds->dev(), order, variant, total, dtab, sum, ctx->num_sms * 8, ctx->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hsum, sum, 8, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess && dtab) e = cudaMemcpyAsync(tables, dtab, bytes, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFreeAsync(buf, ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return fail(EPI_ECUDA, "%s", cudaGetErrorString(e));
+    ctx->launches += 1;
+    *checksum = hsum;
+    if (ms) *ms = (double)t;
+    return EPI_OK;
+}
+
+epi_status epi_set_wait_limit(epi_ctx *ctx, uint64_t limit_ns)
+{
+    if (!ctx) return fail(EPI_EINVAL, "context is NULL");
+    ctx->wait_limit_ns = limit_ns;
+    return EPI_OK;
+}
+
+epi_status epi_inject_alloc_failure(epi_ctx *ctx, int64_t after)
+{
+    if (!ctx) return fail(EPI_EINVAL, "context is NULL");
+    ctx->fail_alloc_in = after < 0 ? -1 : after;
+    return EPI_OK;
 }
 
 epi_status epi_tc_rate(epi_ctx *ctx, int64_t stages, double *out)

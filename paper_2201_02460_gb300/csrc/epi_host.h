@@ -63,12 +63,17 @@ uint64_t tc_item_count(int64_t n, int k, int64_t a, int64_t b);
 int64_t tc_first_snp(int64_t n, int k, uint64_t r);
 // combinations the tensor path counts to search the rank range [rb, re)
 uint64_t tc_range_work(int64_t n, int k, uint64_t rb, uint64_t re);
-size_t tc_smem_bytes(int cand_p2);
-// item_cum: device [2][n + 1] (item and prefix tables); ranks [rb, re)
+// entries of a CTA's candidate buffer for a pool; shared memory of one CTA
+// with that buffer in shared memory or (cand_global) in a global buffer
+int tc_cand_p2(int k, int pool);
+size_t tc_smem_bytes(int cand_p2, int k, bool cand_global);
+// item_cum: device [2][n + 1] (item and prefix tables); ranks [rb, re);
+// cand_g / rank_g: NULL, or [grid][tc_cand_p2] global candidate buffers
 cudaError_t launch_tc_search(const DevData &d, int k, const unsigned char *b8, uint64_t *item_cum, int pool,
                              uint32_t *global_thr, float *list_score, uint64_t *list_rank, int32_t *list_count,
                              int32_t *status, int grid, uint64_t total, uint64_t rb, uint64_t re, cudaStream_t st,
-                             int *cand_p2_out, uint32_t *dump = nullptr, unsigned long long *waits = nullptr);
+                             int *cand_p2_out, float *cand_g, uint64_t *rank_g, uint32_t *dump = nullptr,
+                             unsigned long long *waits = nullptr, unsigned long long wait_ns = 0);
 constexpr int kTcWaitSlots = 8;
 // batched tensor-core launches: per-dataset descriptors and B-operand maps
 // (128-byte CUtensorMap, 64-byte aligned) live in device memory
@@ -79,12 +84,19 @@ cudaError_t tc_fill_batch_entry(void *ds_host, void *tmap_host, const DevData &d
                                 uint64_t *item_cum, uint32_t *global_thr, uint64_t total, const void *tmap_dev,
                                 int cta_begin, int cta_count);
 cudaError_t launch_tc_batch(const void *ds_dev, const int32_t *cta_ds_dev, int k, int pool, float *list_score,
-                            uint64_t *list_rank, int32_t *list_count, int32_t *status, int grid, cudaStream_t st);
+                            uint64_t *list_rank, int32_t *list_count, int32_t *status, int grid, cudaStream_t st,
+                            float *cand_g, uint64_t *rank_g);
 
 // epi_peak.cu: tensor-pipe rate of the counting MMA (one CTA per SM,
 // `stages` groups of four M128 N128 K32 FP8 MMAs; per-CTA cycles)
 size_t mma_rate_smem_bytes();
 cudaError_t launch_mma_rate(int64_t stages, unsigned long long *cycles, int32_t *status, int grid, cudaStream_t st);
+
+// epi_variants.cu: every table of order k (2..4) counted with the POPC
+// instruction (variant 0), a byte lookup table (1) or binary MMA (2)
+size_t count_variant_smem_bytes(int k, int32_t Wt);
+cudaError_t launch_count_variant(const DevData &d, int k, int variant, uint64_t total, uint32_t *tables,
+                                 unsigned long long *checksum, int grid, cudaStream_t st);
 
 // epi_learn.cu (proposer)
 cudaError_t launch_features5(const DevData &d, const float *s1, const float *s2, const float *s3, const float *s4,

@@ -194,14 +194,33 @@ __device__ __forceinline__ double mi_term_f64(uint32_t n, uint32_t nx, int64_t m
     return e * phi_f64((double)num / (double)den);
 }
 
-// Relative bound on |MI_f32 - MI| used to size the exact-top-N margin: each
-// term carries a few roundings, the sum of L = 2 * 3^k non-negative terms at
-// most L more; a factor 2 of headroom.
-__host__ __device__ inline double f32_rel_bound(int k)
+// Relative bound on |MI_f32 - MI| / MI of the single-precision score of an
+// order-k table over m individuals (u = 2^-24), the margin of the exact
+// top-N proof.  Per term e phi(v) of the sum:
+//   * e = (n_x m_y) / m: 3 roundings;
+//   * v = n / e - 1: 6 roundings (numerator formed as fma(n, m, -p) - err
+//     and its two roundings, the reciprocals 1 / n_x and 1 / m_y, two
+//     products), amplified by the condition number v phi'(v) / phi(v) =
+//     v ln(1+v) / phi(v), which is 2 near v = 0, tends to 1 for large v and
+//     grows like ln(e / n) <= ln m as v -> -1 (n >= 1; n = 0 is exact);
+//   * phi(v): at most 9 roundings' worth (series branch: the reciprocal,
+//     Horner steps whose terms shrink by y^2 <= 1/4, the final fma; log1p
+//     branch: log1pf's ulp and two roundings times the cancellation
+//     (1+v) ln(1+v) / phi(v) <= 2.6 at v >= 2);
+//   * the product e phi: 1.
+// So one term carries at most (3 + 6 (2 + ln m) + 9 + 1) u = (25 + 6 ln m) u.
+// The L = 2 3^k non-negative terms are summed either compensated (error
+// 2u + 2 L^2 u^2 of the sum) or as a tree of depth <= 12 (tensor-core rows,
+// warp lanes): 12u; the division by m is correctly rounded: 1u.  Total
+// (38 + 6 ln m) u + 2 L^2 u^2, doubled for the estimates above.
+__host__ __device__ inline double f32_rel_bound(int k, int64_t m)
 {
+    const double u = 5.9604644775390625e-8;
     int64_t cells = 1;
     for (int t = 0; t < k; t++) cells *= 3;
-    return 2.0 * (double)(2 * cells + 32) * 5.9604644775390625e-8;
+    const double L = 2.0 * (double)cells;
+    const double lnm = log((double)(m > 2 ? m : 2));
+    return 2.0 * ((38.0 + 6.0 * lnm) * u + 2.0 * L * L * u * u);
 }
 
 // ---------------------------------------------------------------------------

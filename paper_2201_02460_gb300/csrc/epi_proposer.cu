@@ -531,7 +531,7 @@ epi_status epi_proposer_search(epi_dataset *ds, epi_mlp *net, const epi_proposer
         // most pool_floor in FP32, so at most pool_floor (1 + eps) exactly
         stats->exact_in_proposals =
             (selected <= (uint64_t)n_prop ||
-             (n_res == top_n && h64[order[n_res - 1]] > (double)pool_floor * (1.0 + f32_rel_bound(5))))
+             (n_res == top_n && h64[order[n_res - 1]] > (double)pool_floor * (1.0 + f32_rel_bound(5, d.m))))
                 ? 1
                 : 0;
         stats->ms_lower = t1 - t0;

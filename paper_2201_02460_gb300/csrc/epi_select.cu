@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(1024) finalize_kernel(DevData d, int k, int to
         float tau = __uint_as_float(*global_thr);
         if (L == pool && (uint64_t)L < total) tau = fmaxf(tau, cand_s[L - 1]);
         if (tau > 0.0f && N > 0 && (uint64_t)L < total) {
-            const double eps = f32_rel_bound(k);
+            const double eps = f32_rel_bound(k, d.m);
             const double sigma = key[N - 1];
             if (!((double)tau / (1.0 - eps) < sigma * (1.0 - 1e-12))) atomicOr(status, ST_POOL_OVERFLOW);
         }

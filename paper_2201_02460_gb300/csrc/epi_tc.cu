@@ -106,6 +106,7 @@ struct DsParams {
     const uint64_t *pcum;      // [n + 1] prefixes searched in panels < c
     uint64_t rank_begin, rank_end;   // lexicographic ranks searched
     int32_t s1_lo, s1_hi;      // first SNPs of ranks rank_begin and rank_end - 1
+    int32_t clip;              // 0: the whole combination range
     int chunks, chunks_case;   // K stages in total / over the cases
     float delta;               // screening margin (nats)
     float tconst;              // T(m) - T(m1) - T(m0), T(c) = c log2 c
@@ -122,25 +123,38 @@ struct Params {
     const int32_t *cta_ds;     // and the dataset of each CTA
     int k, PR, ppw, ppt;
     int pool, cand_p2;
+    // the CTA's candidate buffer [cand_p2] in global memory (per CTA, at
+    // blockIdx.x * cand_p2) where it does not fit in shared memory; NULL:
+    // shared memory
+    float *cand_score_g;
+    uint64_t *cand_rank_g;
     float *list_score;
     uint64_t *list_rank;
     int32_t *list_count;
     int32_t *status;
+    unsigned long long wait_ns;   // limit of the pipeline waits (0: kTimeoutNs)
     uint32_t *dump;            // optional: every table, [rank][2][3^k] (validation)
     unsigned long long *waits; // optional: [grid][8] cycles spent waiting, per role (tracing)
 };
 
 // ------------------------------------------------------------------ PTX --
+// Limit of the pipeline waits of this CTA (set at start from Params.wait_ns,
+// the default kTimeoutNs when 0).  The drain waits at exit always use
+// kTimeoutNs, so that no asynchronous copy or MMA is outstanding when the CTA
+// leaves.
+__shared__ unsigned long long g_wait_limit_ns;
+
 // Bounded wait for the phase of parity `parity`; false when it gave up (the
 // CTA-wide abort flag is then set).
 __device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag)
 {
     if (mbar_try(bar, parity)) return true;
     const uint64_t t0 = now_ns();
+    const unsigned long long limit = g_wait_limit_ns;
     for (;;) {
         if (mbar_try(bar, parity)) return true;
         if (*abort_flag) return false;
-        if (now_ns() - t0 > kTimeoutNs) {
+        if (now_ns() - t0 > limit) {
             *abort_flag = 1;
             return false;
         }
@@ -391,15 +405,32 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
     // candidate-buffer checks (a barrier and maybe a sort) every kJcPerCheck
     // groups of 8 last SNPs; the buffer holds two intervals' worth
     constexpr int kJcPerCheck = K == 2 ? 1 : 2;
+    // orders 3-4: prefix sums through the shared transpose buffer
+    constexpr bool kTranspose = K == 3 || K == 4;
+    constexpr int kPairs = kWide ? 0 : kPPW * 8;              // (prefix, last SNP) pairs per warp and chunk
+    constexpr int kPairIters = (kPairs + 31) / 32;
 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
     unsigned char *stages_a = smem;
     unsigned char *stages_b = smem + kStagesA * kTileBytes;
-    float *sc = reinterpret_cast<float *>(stages_b + kStagesB * kTileBytes);
-    uint64_t *rk = reinterpret_cast<uint64_t *>(sc + P.cand_p2);
-    uint32_t *tot = reinterpret_cast<uint32_t *>(rk + P.cand_p2);   // [2][128][2 halves][2 classes]
+    float *sc;
+    uint64_t *rk;
+    uint32_t *tot;                                                   // [2][128][2 halves][2 classes]
+    if (P.cand_score_g) {
+        sc = P.cand_score_g + (size_t)blockIdx.x * P.cand_p2;
+        rk = P.cand_rank_g + (size_t)blockIdx.x * P.cand_p2;
+        tot = reinterpret_cast<uint32_t *>(stages_b + kStagesB * kTileBytes);
+    } else {
+        sc = reinterpret_cast<float *>(stages_b + kStagesB * kTileBytes);
+        rk = reinterpret_cast<uint64_t *>(sc + P.cand_p2);
+        tot = reinterpret_cast<uint32_t *>(rk + P.cand_p2);
+    }
     Desc *desc = reinterpret_cast<Desc *>(tot + 2 * 128 * 4);
+    // orders 3-4: per epilogue warp, the row terms of 8 last SNPs [lane][8]
+    // (transposed so that one lane sums one prefix's rows for one last SNP)
+    unsigned char *after_desc = reinterpret_cast<unsigned char *>(desc + kDescDepth);
+    float *wsum = reinterpret_cast<float *>(after_desc + ((16 - (smem_u32(after_desc) & 15)) & 15));
 
     // one "stage free" barrier per stage for both operands (the A and B rings
     // advance together), released by one MMA commit
@@ -445,6 +476,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
         }
         mbar_init(&drain_bar, 1);
         abort_flag = 0;
+        g_wait_limit_ns = P.wait_ns ? P.wait_ns : kTimeoutNs;
         ES.list_len = 0; ES.nbuf = 0; ES.stop = 0; ES.thr = -1.0f;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -716,9 +748,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
 #pragma unroll
             for (int tt = 0; tt < km1; tt++) psnp[tt] = prow ? D.snp[p * km1 + tt] : 0;
             // last SNPs of this prefix inside the searched rank range: the
-            // combination (prefix, j) has rank base + j
+            // combination (prefix, j) has rank base + j.  Only prefixes whose
+            // first SNP is the range's first or last can be cut.
             int32_t jlo = cpre + 1, jhi = (int32_t)d.n;
-            if (prow) {
+            if (prow && DS.clip && (psnp[0] == DS.s1_lo || psnp[0] == DS.s1_hi)) {
                 uint64_t sp = 0;
 #pragma unroll
                 for (int tt = 0; tt < km1; tt++) sp += binom_at(d.binom, d.n, d.n - 1 - psnp[tt], K - tt);
@@ -728,6 +761,38 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                 hi64 = hi64 > d.n ? d.n : (hi64 < lo64 ? lo64 : hi64);
                 jlo = (int32_t)lo64;
                 jhi = (int32_t)hi64;
+            }
+            // the same interval for the prefixes whose (prefix, last SNP)
+            // pairs this lane sums (orders 3-4): pair lane + 32 i is prefix
+            // (lane + 32 i) / 8 of the warp and last SNP (lane + 32 i) % 8 of
+            // each chunk
+            int32_t plo[kPairIters > 0 ? kPairIters : 1], phi[kPairIters > 0 ? kPairIters : 1];
+            if constexpr (kTranspose) {
+#pragma unroll
+                for (int q = 0; q < kPairIters; q++) {
+                    const int pp = (lane + 32 * q) >> 3;
+                    const int pt = quad * kPPW + pp;
+                    plo[q] = 1;
+                    phi[q] = 0;                      // empty: no valid last SNP
+                    if (ok && pp < kPPW && pt < D.nvalid) {
+                        int32_t qs[km1];
+#pragma unroll
+                        for (int tt = 0; tt < km1; tt++) qs[tt] = D.snp[pt * km1 + tt];
+                        plo[q] = qs[km1 - 1] + 1;
+                        phi[q] = (int32_t)d.n;
+                        if (DS.clip && (qs[0] == DS.s1_lo || qs[0] == DS.s1_hi)) {
+                            uint64_t sp = 0;
+#pragma unroll
+                            for (int tt = 0; tt < km1; tt++) sp += binom_at(d.binom, d.n, d.n - 1 - qs[tt], K - tt);
+                            const int64_t base = (int64_t)DS.total - (int64_t)sp - d.n;
+                            int64_t lo64 = (int64_t)DS.rank_begin - base, hi64 = (int64_t)DS.rank_end - base;
+                            lo64 = lo64 < (int64_t)plo[q] ? (int64_t)plo[q] : (lo64 > d.n ? d.n : lo64);
+                            hi64 = hi64 > d.n ? d.n : (hi64 < lo64 ? lo64 : hi64);
+                            plo[q] = (int32_t)lo64;
+                            phi[q] = (int32_t)hi64;
+                        }
+                    }
+                }
             }
             const uint32_t T1 = tot[((b * 128 + r) * 2 + 0) * 2 + 0] + tot[((b * 128 + r) * 2 + 1) * 2 + 0];
             const uint32_t T0 = tot[((b * 128 + r) * 2 + 0) * 2 + 1] + tot[((b * 128 + r) * 2 + 1) * 2 + 1];
@@ -844,6 +909,99 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                         }
                         epi_bar();
                     }
+                } else if constexpr (kTranspose) {
+                    // row terms of the chunk's 8 last SNPs, straight-line
+                    float vrow[8];
+#pragma unroll
+                    for (int jj = 0; jj < 8; jj++) {
+                        const int32_t j = j0 + 8 * jc + jj;
+                        // accumulator values x = count / 32 (exact); with
+                        // t(x) = x log2 x, T(32 x) = 32 t(x) + 160 x and the
+                        // linear parts cancel within a cell, so the screen
+                        // sums t over the raw values and scales once
+                        const float fa0 = __uint_as_float(cs[2 * jj]), fa1 = __uint_as_float(cs[2 * jj + 1]);
+                        const float fb0 = __uint_as_float(cn[2 * jj]), fb1 = __uint_as_float(cn[2 * jj + 1]);
+                        const float fa2 = fT1 - fa0 - fa1, fb2 = fT0 - fb0 - fb1;
+                        if (P.dump && prow && j >= jlo && j < jhi) {
+                            uint64_t rs = 0;
+#pragma unroll
+                            for (int tt = 0; tt < km1; tt++) rs += binom_at(d.binom, d.n, d.n - 1 - psnp[tt], K - tt);
+                            rs += binom_at(d.binom, d.n, d.n - 1 - j, 1);
+                            constexpr int cells = kPR * 3;
+                            uint32_t *o = P.dump + (DS.total - 1 - rs) * 2 * cells;
+                            o[pos * 3 + 0] = f2u_exact(32.0f * fa0); o[pos * 3 + 1] = f2u_exact(32.0f * fa1);
+                            o[pos * 3 + 2] = f2u_exact(32.0f * fa2);
+                            o[cells + pos * 3 + 0] = f2u_exact(32.0f * fb0);
+                            o[cells + pos * 3 + 1] = f2u_exact(32.0f * fb1);
+                            o[cells + pos * 3 + 2] = f2u_exact(32.0f * fb2);
+                        }
+                        vrow[jj] = prow ? (tlog32(fa0) + tlog32(fb0) - tlog32(fa0 + fb0)) +
+                                              (tlog32(fa1) + tlog32(fb1) - tlog32(fa1 + fb1)) +
+                                              (tlog32(fa2) + tlog32(fb2) - tlog32(fa2 + fb2))
+                                        : 0.0f;
+                    }
+                    // transpose: lane l's 8 values at [l][0..7]; the lane of
+                    // pair (prefix pp, last SNP jj) reads rows pp*kPR .. of
+                    // column jj (banks 8 (pp kPR + r) + jj: distinct over the
+                    // warp's pairs)
+                    float *wb = wsum + warp * 256;
+                    reinterpret_cast<float4 *>(wb + lane * 8)[0] = make_float4(vrow[0], vrow[1], vrow[2], vrow[3]);
+                    reinterpret_cast<float4 *>(wb + lane * 8)[1] = make_float4(vrow[4], vrow[5], vrow[6], vrow[7]);
+                    __syncwarp();
+                    uint32_t cmask[kPairIters];
+#pragma unroll
+                    for (int q = 0; q < kPairIters; q++) {
+                        const int pair = lane + 32 * q;
+                        bool cand = false;
+                        if (pair < kPairs) {
+                            const int pp = pair >> 3, jj = pair & 7;
+                            float v = 0.0f;
+#pragma unroll
+                            for (int rr = 0; rr < kPR; rr++) v += wb[(pp * kPR + rr) * 8 + jj];
+                            const int32_t j = j0 + 8 * jc + jj;
+                            cand = j >= plo[q] && j < phi[q] && fmaf(v, vscale, voff) >= cut;
+                        }
+                        cmask[q] = __ballot_sync(0xffffffffu, cand);
+                    }
+                    __syncwarp();
+                    // precise single-precision scores of the flagged pairs
+                    // (rare): the prefix's row lanes score their rows of that
+                    // column, the prefix's first row lane adds them up
+#pragma unroll
+                    for (int q = 0; q < kPairIters; q++) {
+                        while (cmask[q]) {
+                            const int pair = __ffs(cmask[q]) - 1 + 32 * q;
+                            cmask[q] &= cmask[q] - 1;
+                            const int pp = pair >> 3, jsel = pair & 7;
+                            uint32_t a0 = 0, a1 = 0, b0 = 0, b1 = 0;
+#pragma unroll
+                            for (int jj = 0; jj < 8; jj++)
+                                if (jj == jsel) { a0 = cs[2 * jj]; a1 = cs[2 * jj + 1]; b0 = cn[2 * jj]; b1 = cn[2 * jj + 1]; }
+                            const float fa0 = __uint_as_float(a0), fa1 = __uint_as_float(a1);
+                            const float fb0 = __uint_as_float(b0), fb1 = __uint_as_float(b1);
+                            float e = 0.0f;
+                            if (lane_real && pl == pp)
+                                e = row_terms_precise(f2u_exact(32.0f * fa0), f2u_exact(32.0f * fb0),
+                                                      f2u_exact(32.0f * fa1), f2u_exact(32.0f * fb1),
+                                                      f2u_exact(32.0f * (fT1 - fa0 - fa1)),
+                                                      f2u_exact(32.0f * (fT0 - fb0 - fb1)), mc);
+                            e = seg_sum<kPR>(e, pos);
+                            if (lane_real && pl == pp && pos == 0) {
+                                const float score = __fdiv_rn(e, mc.fm);
+                                if (score >= thr) {
+                                    const int32_t j = j0 + 8 * jc + jsel;
+                                    uint64_t rk_sum = 0;
+#pragma unroll
+                                    for (int tt = 0; tt < km1; tt++)
+                                        rk_sum += binom_at(d.binom, d.n, d.n - 1 - psnp[tt], K - tt);
+                                    rk_sum += binom_at(d.binom, d.n, d.n - 1 - j, 1);
+                                    const int slot = list_len + atomicAdd(&ES.nbuf, 1);
+                                    sc[slot] = score;
+                                    rk[slot] = DS.total - 1 - rk_sum;
+                                }
+                            }
+                        }
+                    }
                 } else {
 #pragma unroll
                 for (int jj = 0; jj < 8; jj++) {
@@ -906,7 +1064,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                 }
                 if (jc % kJcPerCheck == kJcPerCheck - 1) {
                     epi_bar();
-                    if (ES.nbuf > kJcPerCheck * 16 * kPPT) epi_flush(ES, sc, rk, P.pool, DS.global_thr, tid);
+                    // the next check interval adds at most kJcPerCheck * 16
+                    // candidates per prefix of the tile: sort and trim first
+                    // if the buffer could not hold them
+                    if (ES.list_len + ES.nbuf + kJcPerCheck * 16 * kPPT > P.cand_p2)
+                        epi_flush(ES, sc, rk, P.pool, DS.global_thr, tid);
                     thr = ES.thr;
                     cut = thr - DS.delta;
                     list_len = ES.list_len;
@@ -1110,10 +1272,19 @@ int tc_prefixes_per_warp(int k)
     return PR <= 32 ? 32 / PR : 0;
 }
 
-size_t tc_smem_bytes(int cand_p2)
+// Candidate buffer entries: the pool plus one check interval (2 chunks of 8
+// last SNPs, both halves, every prefix of the tile; order 2 checks every
+// chunk), rounded up to a power of two for the bitonic sort.
+int tc_cand_p2(int k, int pool)
 {
-    return 1024 + (size_t)(tc::kStagesA + tc::kStagesB) * tc::kTileBytes + (size_t)cand_p2 * 12 + 2 * 128 * 4 * 4 +
-           tc::kDescDepth * sizeof(tc::Desc) + 64;
+    return next_pow2(pool + (k == 2 ? 1 : 2) * 16 * tc_ppt(k));
+}
+
+size_t tc_smem_bytes(int cand_p2, int k, bool cand_global)
+{
+    const size_t transpose = (k == 3 || k == 4) ? (size_t)tc::kEpiWarps * 256 * 4 + 16 : 0;
+    return 1024 + (size_t)(tc::kStagesA + tc::kStagesB) * tc::kTileBytes + (cand_global ? 0 : (size_t)cand_p2 * 12) +
+           2 * 128 * 4 * 4 + tc::kDescDepth * sizeof(tc::Desc) + 64 + transpose;
 }
 
 
@@ -1143,6 +1314,7 @@ static void fill_ds(tc::DsParams &D, const DevData &d, int k, uint64_t *item_cum
     D.rank_end = re;
     D.s1_lo = (int32_t)tc_first_snp(d.n, k, rb);
     D.s1_hi = (int32_t)tc_first_snp(d.n, k, re - 1);
+    D.clip = !(rb == 0 && re == total);
     // prefixes whose first SNP lies in [s1_lo, s1_hi]
     uint64_t np = 0;
     for (int64_t c = k - 2; c <= d.n - 2; c++) {
@@ -1176,14 +1348,18 @@ static void fill_ds(tc::DsParams &D, const DevData &d, int k, uint64_t *item_cum
 }
 
 static void fill_launch(tc::Params &P, int k, int pool, float *list_score, uint64_t *list_rank, int32_t *list_count,
-                        int32_t *status, uint32_t *dump, unsigned long long *waits)
+                        int32_t *status, uint32_t *dump, unsigned long long *waits, float *cand_g,
+                        uint64_t *rank_g)
 {
     P.k = k;
     P.PR = tc_pr(k);
     P.ppw = P.PR > 32 ? 0 : 32 / P.PR;
     P.ppt = tc_ppt(k);
     P.pool = pool;
-    P.cand_p2 = next_pow2(pool + 2 * (k == 2 ? 1 : 2) * 16 * P.ppt);   // two check intervals (kJcPerCheck)
+    P.cand_p2 = tc_cand_p2(k, pool);
+    P.cand_score_g = cand_g;
+    P.cand_rank_g = rank_g;
+    P.wait_ns = 0;
     P.list_score = list_score;
     P.list_rank = list_rank;
     P.list_count = list_count;
@@ -1194,7 +1370,7 @@ static void fill_launch(tc::Params &P, int k, int pool, float *list_score, uint6
 
 static cudaError_t launch_kernel(const CUtensorMap &map, const tc::Params &P, int k, int grid, cudaStream_t st)
 {
-    const size_t smem = tc_smem_bytes(P.cand_p2);
+    const size_t smem = tc_smem_bytes(P.cand_p2, k, P.cand_score_g != nullptr);
     auto kern = k == 2   ? tc::tc_search_kernel<2>
                 : k == 3 ? tc::tc_search_kernel<3>
                 : k == 4 ? tc::tc_search_kernel<4>
@@ -1216,13 +1392,15 @@ cudaError_t launch_tc_item_cum(const DevData &d, int k, uint64_t rb, uint64_t re
 cudaError_t launch_tc_search(const DevData &d, int k, const unsigned char *b8, uint64_t *item_cum, int pool,
                              uint32_t *global_thr, float *list_score, uint64_t *list_rank, int32_t *list_count,
                              int32_t *status, int grid, uint64_t total, uint64_t rb, uint64_t re, cudaStream_t st,
-                             int *cand_p2_out, uint32_t *dump, unsigned long long *waits)
+                             int *cand_p2_out, float *cand_g, uint64_t *rank_g, uint32_t *dump,
+                             unsigned long long *waits, unsigned long long wait_ns)
 {
     tc::Params P;
     fill_ds(P.one, d, k, item_cum, global_thr, total, rb, re, nullptr, 0, grid);
     P.many = nullptr;
     P.cta_ds = nullptr;
-    fill_launch(P, k, pool, list_score, list_rank, list_count, status, dump, waits);
+    fill_launch(P, k, pool, list_score, list_rank, list_count, status, dump, waits, cand_g, rank_g);
+    P.wait_ns = wait_ns;
     *cand_p2_out = P.cand_p2;
     cudaError_t e = launch_tc_item_cum(d, k, rb, re, item_cum, st);
     if (e != cudaSuccess) return e;
@@ -1244,13 +1422,14 @@ cudaError_t tc_fill_batch_entry(void *ds_host, void *tmap_host, const DevData &d
 }
 
 cudaError_t launch_tc_batch(const void *ds_dev, const int32_t *cta_ds_dev, int k, int pool, float *list_score,
-                            uint64_t *list_rank, int32_t *list_count, int32_t *status, int grid, cudaStream_t st)
+                            uint64_t *list_rank, int32_t *list_count, int32_t *status, int grid, cudaStream_t st,
+                            float *cand_g, uint64_t *rank_g)
 {
     tc::Params P;
     P.one = tc::DsParams();
     P.many = static_cast<const tc::DsParams *>(ds_dev);
     P.cta_ds = cta_ds_dev;
-    fill_launch(P, k, pool, list_score, list_rank, list_count, status, nullptr, nullptr);
+    fill_launch(P, k, pool, list_score, list_rank, list_count, status, nullptr, nullptr, cand_g, rank_g);
     CUtensorMap unused;
     memset(&unused, 0, sizeof(unused));
     return launch_kernel(unused, P, k, grid, st);

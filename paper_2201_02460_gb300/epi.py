@@ -178,6 +178,14 @@ def load(path: str | None = None):
         lib.epi_profile_end.argtypes = [V, P, P]
         lib.epi_profile_waits.restype = i32
         lib.epi_profile_waits.argtypes = [V, P]
+        lib.epi_tc_rate.restype = i32
+        lib.epi_tc_rate.argtypes = [V, i64, P]
+        lib.epi_count_variant.restype = i32
+        lib.epi_count_variant.argtypes = [V, i32, i32, P, P, P]
+        lib.epi_set_wait_limit.restype = i32
+        lib.epi_set_wait_limit.argtypes = [V, u64]
+        lib.epi_inject_alloc_failure.restype = i32
+        lib.epi_inject_alloc_failure.argtypes = [V, i64]
         if path is None:
             _lib = lib
         return lib
@@ -241,6 +249,22 @@ class Context:
         names = ["mma_wait_a", "mma_wait_b", "mma_wait_acc", "prod_wait_stage", "prod_wait_acc", "epi_wait_acc",
                  "tma_wait_stage", "mma_loop"]
         return {k: float(v) for k, v in zip(names, out)}
+
+    def set_wait_limit(self, ns: int):
+        """Limit of the tensor-core kernel's pipeline waits (0: default)."""
+        _check(load().epi_set_wait_limit(self._h, int(ns)))
+
+    def inject_alloc_failure(self, after: int):
+        """Make the device allocation after `after` further ones fail once
+        (negative: cancel)."""
+        _check(load().epi_inject_alloc_failure(self._h, int(after)))
+
+    def tc_rate(self, stages: int = 1 << 19) -> dict:
+        """Rate of the tensor pipe for the counting path's MMA (FP8 M128 N128
+        K32), measured with one CTA per SM issuing it back to back."""
+        out = np.zeros(4, dtype=np.float64)
+        _check(load().epi_tc_rate(self._h, int(stages), _np_ptr(out)))
+        return dict(tflops=float(out[0]), mac_per_clk_sm=float(out[1]), ms=float(out[2]), sm_mhz=float(out[3]))
 
     def close(self):
         if getattr(self, "_h", None):
@@ -394,6 +418,23 @@ def debug_counts(ds: Dataset, order: int) -> np.ndarray:
     out = np.zeros((total, 2, 3 ** order), dtype=np.uint32)
     _check(lib.epi_debug_counts(ds.handle, order, _np_ptr(out)))
     return out
+
+
+COUNT_VARIANTS = {"popc": 0, "lut": 1, "mma_b1": 2}
+
+
+def count_variant(ds: Dataset, order: int, variant: str, with_tables: bool = False) -> dict:
+    """Every order-`order` table counted with one last-level instruction
+    (epi_count_variant): checksum, kernel milliseconds and, optionally, the
+    tables [C(n,k), 2, 3^k] in rank order."""
+    import math
+    lib = load()
+    tabs = np.zeros((math.comb(ds.n_snps, order), 2, 3 ** order), dtype=np.uint32) if with_tables else None
+    cs = C.c_uint64(0)
+    ms = C.c_double(0.0)
+    _check(lib.epi_count_variant(ds.handle, order, COUNT_VARIANTS[variant],
+                                 _np_ptr(tabs) if tabs is not None else None, C.byref(cs), C.byref(ms)))
+    return dict(checksum=int(cs.value), ms=float(ms.value), tables=tabs)
 
 
 def tables(ds: Dataset, combs) -> np.ndarray:

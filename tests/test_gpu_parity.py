@@ -500,3 +500,36 @@ def test_batched_config4_shapes(epi, ctx):
         if i % 8 == 0:
             oc, om, _ = O.search(raw[i].geno, raw[i].pheno, k, t)
             _check_result(r, raw[i].geno, raw[i].pheno, oc, om)
+
+
+def test_tc_rate_probe(epi, ctx):
+    """The tensor-pipe rate probe returns a consistent measurement: the rate
+    from event time and the per-SM cycle count agree with the SM clock it
+    reports, and the count per clock lies below the nominal dense FP8 bound
+    (4.5 PFLOP/s at about 1.9 GHz over 152 SMs: under 8 Ki multiply-adds per
+    SM clock, with 20 % headroom for clock reporting)."""
+    r = ctx.tc_rate(1 << 14)
+    assert r["ms"] > 0 and r["tflops"] > 0
+    assert 0 < r["mac_per_clk_sm"] <= 1.2 * 8192
+    implied = r["tflops"] * 1e12 / (2 * r["mac_per_clk_sm"] * 152) / 1e6
+    assert 0.8 * r["sm_mhz"] <= implied <= 1.25 * r["sm_mhz"]
+
+
+@pytest.mark.parametrize("k,n,m,m1", [(2, 40, 300, 140), (3, 20, 777, 400), (4, 13, 1000, 313), (3, 18, 4100, 2049),
+                                      (2, 30, 65, 1)])
+def test_count_variants_bit_exact(epi, ctx, k, n, m, m1):
+    """The three last-level counting instructions (POPC, byte lookup table,
+    binary MMA AND+POPC) give every table of the oracle, and the same
+    checksum."""
+    geno, pheno = random_data(n, m, seed=500 + 7 * k + m, m1=m1)
+    ds = epi.Dataset(ctx, geno, pheno)
+    combs = np.array(brute.all_combinations(n, k), dtype=np.int32)
+    want = O.tables(geno, pheno, combs)
+    cells = 3 ** k
+    weights = 1 + np.arange(cells, dtype=np.uint64)[None, None, :] + np.array([0, cells], dtype=np.uint64)[None, :, None]
+    want_sum = int((want.astype(np.uint64) * weights).sum())
+    for v in ("popc", "lut", "mma_b1"):
+        r = epi.count_variant(ds, k, v, with_tables=True)
+        bad = np.nonzero((r["tables"] != want).any(axis=(1, 2)))[0]
+        assert len(bad) == 0, (v, len(bad), bad[:5])
+        assert r["checksum"] == want_sum % (1 << 64), v
