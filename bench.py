@@ -232,6 +232,33 @@ def measure_batch(epi, ctx, synth, n_div, steps=2):
                 snp_divisor=n_div, timing="host wall clock around the synchronous batched call")
 
 
+def measure_training(epi, ctx, peaks, rows=8192, steps=50, n_in=25, hidden=256):
+    """Training throughput of the proposer network: AdamW steps on one
+    resident batch (forward, backward, optimiser), the three hidden x hidden
+    products on the tensor cores.  Work per row: 2 flop per multiply-add of
+    the forward (n_in h + h^2 + h) and backward (n_in h + 2 h^2 + 3 h)
+    products."""
+    import torch
+    net = epi.MLP(ctx, n_in, hidden, seed=2)
+    X = (torch.rand(rows, n_in, device="cuda") * -8.0).contiguous()
+    t = torch.randn(rows, device="cuda")
+    for _ in range(3):
+        net.train_step(X, t, 1e-4, 0.0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        net.train_step(X, t, 1e-4, 0.0)
+    e1.record()
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3 / steps
+    flops = 2.0 * rows * (2 * n_in * hidden + 3 * hidden * hidden + 4 * hidden)
+    net.close()
+    return dict(rows_per_step=rows, ms_per_step=sec * 1e3, rows_per_s=rows / sec, tflops=flops / sec / 1e12,
+                frac_of_bf16_peak=flops / sec / 1e12 / peaks["bf16"],
+                note="whole AdamW step on a resident batch, CUDA events; 2*(2*in*h + 3*h^2 + 4*h) flop per row")
+
+
 def measure_count_variants(epi, ctx, synth, flush, stream):
     """The GPU counterpart of the paper's popcount comparison (Table 1): every
     order-3 table of the first 500 SNPs of the 2000 x 4000 workload counted
@@ -323,23 +350,12 @@ def measure_batch_full(epi, ctx, synth, peaks, tc_rate, stream):
                        "launch; capture is host work of milliseconds)")
 
 
-def measure_proposer(epi, ctx, ds, peaks, top_triples=256, budget=4096):
-    """Order-5 proposal search on the given dataset: candidates ranked per
-    second by the network (fused tensor-core inference; weights as
-    initialised, so this measures throughput, not recall) and by the
-    network-free heuristic, each followed by the exact re-score."""
+def measure_mlp_inference(epi, ctx, peaks):
+    """Throughput of the proposer network's fused BF16 tensor-core inference
+    on 2^24 resident rows of 25 features."""
     import torch
     net = epi.MLP(ctx, 25, 256, seed=1)
     out = {}
-    for name, scorer in (("network", net), ("heuristic", None)):
-        epi.proposer_search(ds, scorer, top_triples, budget, 100)      # warm-up
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        r, st = epi.proposer_search(ds, scorer, top_triples, budget, 100)
-        t = time.perf_counter() - t0
-        out[name] = dict(seconds=t, candidates=int(st["candidates"]), kept=int(st["kept"]),
-                         ranked_per_s=st["candidates"] / (st["ms_rank"] / 1e3), ms_lower=st["ms_lower"],
-                         ms_rank=st["ms_rank"], ms_rescore=st["ms_rescore"], best_mi=float(r.mi[0]))
     # the network alone on resident rows: fused BF16 tensor-core inference
     X = torch.randn(1 << 24, 25, device="cuda") - 4.0
     net.forward(X)
@@ -534,9 +550,14 @@ def run_ours(args):
         comp["batch64/auto"] = measure_batch(epi, ctx, synth, args.batch_div)
         if not args.quick:
             comp["batch64_full/auto"] = measure_batch_full(epi, ctx, synth, peaks, tc_rate, stream)
-        if d.n_snps >= 5:
-            comp[f"proposer_order5/{args.workload}"] = measure_proposer(epi, ctx, ds, peaks)
         from paper_2201_02460_gb300 import proposer_eval
+        comp["proposer_order5/mlp_inference"] = measure_mlp_inference(epi, ctx, peaks)["mlp_inference"]
+        comp["proposer_order5/mlp_training"] = measure_training(epi, ctx, peaks)
+        if not args.quick:
+            # 2000 SNPs x 4000 samples with a planted 5-SNP parity: a trained
+            # network against the heuristic, recall of the candidate space's
+            # exact top-100
+            comp["proposer_order5/eval_2000snp_4000"] = proposer_eval.evaluate_large(ctx)
         if args.proposer_eval:
             comp["proposer_order5/recall_200snp_2000"] = proposer_eval.evaluate(ctx)
         else:

@@ -46,18 +46,23 @@ def loss(theta, X, t, n_in, h, rnd=None):
     return float(np.mean((y - np.asarray(t, np.float64)) ** 2))
 
 
-def gradients(theta, X, t, n_in, h, rnd=None):
+def gradients(theta, X, t, n_in, h, rnd=None, rnd_dz=None):
     """Analytic gradient of the mean squared error (chain rule by hand);
-    with rnd, the gradient the same formula gives on the rounded operands."""
+    with rnd, the gradient the same formula gives on the rounded operands;
+    with rnd_dz, the layer-2 pre-activation gradient is also stored in that
+    format where it enters the two layer-2 products (the weight gradient of
+    W2 and the gradient passed back to layer 1), as a tensor-core product
+    takes it; its bias gradient sums the unrounded values."""
     y, (X, Z1, H1, Z2, H2, W2, W3) = forward(theta, X, n_in, h, rnd)
     B = X.shape[0]
     dy = 2.0 * (y - np.asarray(t, np.float64)) / B
     gW3 = H2.T @ dy
     gb3 = np.array([dy.sum()])
     dZ2 = np.outer(dy, W3) * (Z2 > 0)
-    gW2 = dZ2.T @ H1
+    dZ2p = rnd_dz(dZ2) if rnd_dz is not None else dZ2
+    gW2 = dZ2p.T @ H1
     gb2 = dZ2.sum(axis=0)
-    dZ1 = (dZ2 @ W2) * (Z1 > 0)
+    dZ1 = (dZ2p @ W2) * (Z1 > 0)
     gW1 = dZ1.T @ X
     gb1 = dZ1.sum(axis=0)
     return np.concatenate([gW1.ravel(), gb1, gW2.ravel(), gb2, gW3, gb3])

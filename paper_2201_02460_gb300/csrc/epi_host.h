@@ -98,6 +98,13 @@ size_t count_variant_smem_bytes(int k, int32_t Wt);
 cudaError_t launch_count_variant(const DevData &d, int k, int variant, uint64_t total, uint32_t *tables,
                                  unsigned long long *checksum, int grid, cudaStream_t st);
 
+// epi_gemm_tc.cu: C = A . B^T on tcgen05 (BF16 K-major operands, FP32 C),
+// K split over CTAs into `partial` (gemm_tc_partial_floats floats, or NULL)
+size_t gemm_tc_smem_bytes(int nt);
+size_t gemm_tc_partial_floats(int M, int N, int K, int num_sms);
+cudaError_t launch_gemm_tc(const void *A, int64_t lda, const void *B, int64_t ldb, float *C, int64_t ldc, int M, int N,
+                           int K, float *partial, int32_t *status, int num_sms, cudaStream_t st);
+
 // epi_learn.cu (proposer)
 cudaError_t launch_features5(const DevData &d, const float *s1, const float *s2, const float *s3, const float *s4,
                              const uint32_t *combs, int64_t count, float *X, cudaStream_t st);

@@ -437,6 +437,88 @@ __global__ void colsum_kernel(const float *__restrict__ dZ, int64_t rows, int N,
     if (threadIdx.x == 0) db[n] = part[0];
 }
 
+// Reductions over the batch, sliced: part[s][i][j] = sum over the rows b of
+// slice s of U[b][i] V[b][j] for j < nj, and part[s][i][nj] = sum of U[b][i]
+// (the bias gradient); one thread per i, the slice's V rows staged in shared
+// memory.  Slices of kSliceRows rows keep every CTA busy whatever the batch.
+constexpr int kSliceRows = 64;
+constexpr int kMaxNj = 32;
+
+template <typename TU, typename TV>
+__global__ void __launch_bounds__(256) batch_outer_kernel(const TU *__restrict__ U, int64_t ldu,
+                                                          const TV *__restrict__ V, int64_t ldv, int64_t B, int ni,
+                                                          int nj, float *__restrict__ part)
+{
+    __shared__ float vs[kSliceRows][kMaxNj];
+    const int64_t b0 = (int64_t)blockIdx.x * kSliceRows;
+    const int rows = (int)min((int64_t)kSliceRows, B - b0);
+    for (int e = threadIdx.x; e < rows * nj; e += blockDim.x) {
+        const int r = e / nj, j = e - r * nj;
+        vs[r][j] = (float)V[(b0 + r) * ldv + j];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < ni; i += blockDim.x) {
+        float acc[kMaxNj];
+#pragma unroll
+        for (int j = 0; j < kMaxNj; j++) acc[j] = 0.0f;
+        float bias = 0.0f;
+        for (int r = 0; r < rows; r++) {
+            const float u = (float)U[(b0 + r) * ldu + i];
+            bias += u;
+#pragma unroll
+            for (int j = 0; j < kMaxNj; j++)
+                if (j < nj) acc[j] = fmaf(u, vs[r][j], acc[j]);
+        }
+        float *o = part + ((size_t)blockIdx.x * ni + i) * (nj + 1);
+        for (int j = 0; j < nj; j++) o[j] = acc[j];
+        o[nj] = bias;
+    }
+}
+
+// G[i][j] = sum over the slices (in slice order) of part[s][i][j], and the
+// bias sums into gb[i] (either output may be NULL)
+__global__ void sum_outer_kernel(const float *__restrict__ part, int slices, int ni, int nj, float *__restrict__ G,
+                                 float *__restrict__ gb)
+{
+    const int per = nj + 1;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ni * per; e += gridDim.x * blockDim.x) {
+        float sum = 0.0f;
+        for (int q = 0; q < slices; q++) sum += part[(size_t)q * ni * per + e];
+        const int i = e / per, j = e - i * per;
+        if (j < nj) { if (G) G[i * nj + j] = sum; }
+        else if (gb) gb[i] = sum;
+    }
+}
+
+// Tiled transpose into BF16: out[c][r] = in[r][c] for r < R, c < C (rows of
+// `in` ld_in apart, of `out` ld_out apart); optionally also the same values
+// in BF16 without transposing (out_same[r][c], stride C).
+template <typename T>
+__global__ void transpose_bf16_kernel(const T *__restrict__ in, int64_t R, int C, int64_t ld_in,
+                                      __nv_bfloat16 *__restrict__ out, int64_t ld_out,
+                                      __nv_bfloat16 *__restrict__ out_same)
+{
+    __shared__ __nv_bfloat16 tile[32][33];
+    const int64_t r0 = (int64_t)blockIdx.x * 32;
+    const int c0 = blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int64_t r = r0 + i;
+        const int c = c0 + threadIdx.x;
+        __nv_bfloat16 v = __float2bfloat16(0.0f);
+        if (r < R && c < C) {
+            v = __float2bfloat16((float)in[r * ld_in + c]);
+            if (out_same) out_same[r * C + c] = v;
+        }
+        tile[i][threadIdx.x] = v;
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int c = c0 + i;
+        const int64_t r = r0 + threadIdx.x;
+        if (c < C && r < R) out[(int64_t)c * ld_out + r] = tile[threadIdx.x][i];
+    }
+}
+
 // AdamW on the FP32 master weights; BF16 working copies refreshed
 __global__ void adamw_kernel(float *__restrict__ w, const float *__restrict__ g, float *__restrict__ m1,
                              float *__restrict__ m2, __nv_bfloat16 *__restrict__ wb, int64_t count, float lr, float b1,
@@ -546,13 +628,32 @@ struct Acts {
     float *Y;            // [B]
     float *dY;           // [B]
     float *loss;         // [1]
+    // tensor-core products of the training step (hidden a multiple of 8)
+    int64_t Bp;          // B rounded up to a multiple of 8 (row stride of the transposes)
+    __nv_bfloat16 *H1t;  // [h][Bp]  H1 transposed
+    __nv_bfloat16 *dZb;  // [B][h]   dZ2 in BF16
+    __nv_bfloat16 *dZt;  // [h][Bp]  dZ2 in BF16, transposed
+    __nv_bfloat16 *W2t;  // [h][h]   W2 transposed (BF16 working copy)
+    float *part;         // split-K partial tiles of dW2
+    float *opart;        // [slices][h][n_in + 1] partial sums of the batch reductions
 };
+
+// The three hidden x hidden products of a training step run on the tensor
+// cores (epi_gemm_tc.cu) when the hidden width allows 16-byte rows.
+bool train_tc(const epi_mlp *net);
 
 epi_status ensure_acts(epi_mlp *net, int64_t B, Acts &a)
 {
     const int in = net->n_in, h = net->hidden;
     auto bytes = [&](int64_t rows) {
-        return (size_t)rows * in * 2 + (size_t)rows * h * 4 * 2 + (size_t)rows * h * 2 * 2 + (size_t)rows * 8 + 1024 + 6 * 256;
+        const int64_t rp = (rows + 7) / 8 * 8;
+        size_t b = (size_t)rows * in * 2 + (size_t)rows * h * 4 * 2 + (size_t)rows * h * 2 * 2 + (size_t)rows * 8 + 1024 +
+                   6 * 256;
+        if (train_tc(net))
+            b += (size_t)h * rp * 2 * 2 + (size_t)rows * h * 2 + (size_t)h * h * 2 +
+                 gemm_tc_partial_floats(h, h, (int)std::min<int64_t>(rows, INT32_MAX), net->num_sms) * 4 + 5 * 256;
+        b += (size_t)((rows + learn::kSliceRows - 1) / learn::kSliceRows) * h * (std::max(in, 1) + 1) * 4 + 256;
+        return b;
     };
     if (net->cap < B) {
         if (net->act) cudaFree(net->act);
@@ -571,10 +672,35 @@ epi_status ensure_acts(epi_mlp *net, int64_t B, Acts &a)
     a.Y = reinterpret_cast<float *>(take((size_t)B * 4));
     a.dY = reinterpret_cast<float *>(take((size_t)B * 4));
     a.loss = reinterpret_cast<float *>(take(4));
+    a.Bp = (B + 7) / 8 * 8;
+    a.H1t = a.dZb = a.dZt = a.W2t = nullptr;
+    a.part = nullptr;
+    if (train_tc(net)) {
+        a.H1t = reinterpret_cast<__nv_bfloat16 *>(take((size_t)h * a.Bp * 2));
+        a.dZt = reinterpret_cast<__nv_bfloat16 *>(take((size_t)h * a.Bp * 2));
+        a.dZb = reinterpret_cast<__nv_bfloat16 *>(take((size_t)B * h * 2));
+        a.W2t = reinterpret_cast<__nv_bfloat16 *>(take((size_t)h * h * 2));
+        a.part = reinterpret_cast<float *>(take(gemm_tc_partial_floats(h, h, (int)B, net->num_sms) * 4));
+    }
+    a.opart = reinterpret_cast<float *>(
+        take((size_t)((B + learn::kSliceRows - 1) / learn::kSliceRows) * h * (std::max(in, 1) + 1) * 4));
     return EPI_OK;
 }
 
-epi_status forward(epi_mlp *net, const float *X, int64_t B, Acts &a, float *y_out)
+bool train_tc(const epi_mlp *net) { return net->hidden % 8 == 0; }
+
+template <typename T>
+cudaError_t transpose_bf16(const T *in, int64_t R, int C, int64_t ld_in, __nv_bfloat16 *out, int64_t ld_out,
+                           __nv_bfloat16 *out_same, cudaStream_t st)
+{
+    dim3 grid((unsigned)((R + 31) / 32), (unsigned)((C + 31) / 32));
+    learn::transpose_bf16_kernel<T><<<grid, dim3(32, 8), 0, st>>>(in, R, C, ld_in, out, ld_out, out_same);
+    return cudaGetLastError();
+}
+
+// tc: the layer-2 product on the tensor cores (training); otherwise every
+// layer on the CUDA cores
+epi_status forward(epi_mlp *net, const float *X, int64_t B, Acts &a, float *y_out, bool tc = false)
 {
     const int in = net->n_in, h = net->hidden;
     const Offs o = offsets(in, h);
@@ -583,7 +709,10 @@ epi_status forward(epi_mlp *net, const float *X, int64_t B, Acts &a, float *y_ou
     // layer 1: Z1 = X W1^T, H1 = relu(Z1 + b1)
     LCK(gemm(st, (int)B, h, in, a.X, in, 1, net->wb + o.W1, 1, in, a.Z1, h, 1, 0));
     learn::bias_act_kernel<<<blocks_for(B * h), 256, 0, st>>>(a.Z1, net->w + o.b1, B, h, 1, a.H1, nullptr);
-    LCK(gemm(st, (int)B, h, h, a.H1, h, 1, net->wb + o.W2, 1, h, a.Z2, h, 1, 0));
+    if (tc && train_tc(net))
+        LCK(launch_gemm_tc(a.H1, h, net->wb + o.W2, h, a.Z2, h, (int)B, h, h, nullptr, net->status, net->num_sms, st));
+    else
+        LCK(gemm(st, (int)B, h, h, a.H1, h, 1, net->wb + o.W2, 1, h, a.Z2, h, 1, 0));
     learn::bias_act_kernel<<<blocks_for(B * h), 256, 0, st>>>(a.Z2, net->w + o.b2, B, h, 1, a.H2, nullptr);
     LCK(gemm(st, (int)B, 1, h, a.H2, h, 1, net->wb + o.W3, 1, h, y_out, 1, 1, 0));
     learn::bias_act_kernel<<<blocks_for(B), 256, 0, st>>>(y_out, net->w + o.b3, B, 1, 0, nullptr, y_out);
@@ -599,20 +728,46 @@ epi_status backward(epi_mlp *net, const float *t, int64_t B, Acts &a)
     LCK(cudaMemsetAsync(a.loss, 0, 4, st));
     learn::mse_kernel<<<blocks_for(B), 256, 0, st>>>(a.Y, t, B, a.dY, a.loss);
     // layer 3: dW3 = dY^T H2, db3 = sum dY, dH2 = dY W3
-    LCK(gemm(st, 1, h, (int)B, a.dY, 1, 1, a.H2, h, 1, net->g + o.W3, h, 1, 0));
+    const int slices = (int)((B + learn::kSliceRows - 1) / learn::kSliceRows);
+    auto sum_outer = [&](int ni, int nj, float *G, float *gb) {
+        const int total = ni * (nj + 1);
+        learn::sum_outer_kernel<<<(total + 255) / 256, 256, 0, st>>>(a.opart, slices, ni, nj, G, gb);
+        return cudaGetLastError();
+    };
+    learn::batch_outer_kernel<<<slices, 256, 0, st>>>(a.H2, h, a.dY, 1, B, h, 1, a.opart);
+    LCK(sum_outer(h, 1, net->g + o.W3, nullptr));
     learn::colsum_kernel<<<1, 256, 0, st>>>(a.dY, B, 1, net->g + o.b3);
     float *dZ2 = a.Z2;   // reuse
     LCK(gemm(st, (int)B, h, 1, a.dY, 1, 1, net->wb + o.W3, 1, 1, dZ2, h, 1, 0));
     learn::relu_grad_kernel<<<blocks_for(B * h), 256, 0, st>>>(dZ2, a.H2, B * h);
-    // layer 2: dW2 = dZ2^T H1, db2, dH1 = dZ2 W2
-    LCK(gemm(st, h, h, (int)B, dZ2, 1, h, a.H1, h, 1, net->g + o.W2, h, 1, 0));
-    learn::colsum_kernel<<<h, 256, 0, st>>>(dZ2, B, h, net->g + o.b2);
     float *dZ1 = a.Z1;
-    LCK(gemm(st, (int)B, h, h, dZ2, h, 1, net->wb + o.W2, h, 1, dZ1, h, 1, 0));
+    if (train_tc(net)) {
+        // layer 2 on the tensor cores: dZ2 in BF16 (row-major and
+        // transposed), H1 and W2 transposed, so both products are K-major
+        LCK(transpose_bf16(a.H1, B, h, h, a.H1t, a.Bp, nullptr, st));
+        LCK(transpose_bf16(dZ2, B, h, h, a.dZt, a.Bp, a.dZb, st));
+        LCK(transpose_bf16(net->wb + o.W2, h, h, h, a.W2t, h, nullptr, st));
+        // dW2 = dZ2^T H1 (K = the batch, split over CTAs), db2, dH1 = dZ2 W2
+        LCK(launch_gemm_tc(a.dZt, a.Bp, a.H1t, a.Bp, net->g + o.W2, h, h, h, (int)B, a.part, net->status, net->num_sms,
+                           st));
+        learn::batch_outer_kernel<<<slices, 256, 0, st>>>(dZ2, h, a.X, in, B, h, 0, a.opart);
+        LCK(sum_outer(h, 0, nullptr, net->g + o.b2));
+        LCK(launch_gemm_tc(a.dZb, h, a.W2t, h, dZ1, h, (int)B, h, h, nullptr, net->status, net->num_sms, st));
+    } else {
+        // layer 2: dW2 = dZ2^T H1, db2, dH1 = dZ2 W2
+        LCK(gemm(st, h, h, (int)B, dZ2, 1, h, a.H1, h, 1, net->g + o.W2, h, 1, 0));
+        learn::colsum_kernel<<<h, 256, 0, st>>>(dZ2, B, h, net->g + o.b2);
+        LCK(gemm(st, (int)B, h, h, dZ2, h, 1, net->wb + o.W2, h, 1, dZ1, h, 1, 0));
+    }
     learn::relu_grad_kernel<<<blocks_for(B * h), 256, 0, st>>>(dZ1, a.H1, B * h);
-    // layer 1: dW1 = dZ1^T X, db1
-    LCK(gemm(st, h, in, (int)B, dZ1, 1, h, a.X, in, 1, net->g + o.W1, in, 1, 0));
-    learn::colsum_kernel<<<h, 256, 0, st>>>(dZ1, B, h, net->g + o.b1);
+    // layer 1: dW1 = dZ1^T X, db1 (sliced over the batch for up to 32 inputs)
+    if (in <= learn::kMaxNj) {
+        learn::batch_outer_kernel<<<slices, 256, 0, st>>>(dZ1, h, a.X, in, B, h, in, a.opart);
+        LCK(sum_outer(h, in, net->g + o.W1, net->g + o.b1));
+    } else {
+        LCK(gemm(st, h, in, (int)B, dZ1, 1, h, a.X, in, 1, net->g + o.W1, in, 1, 0));
+        learn::colsum_kernel<<<h, 256, 0, st>>>(dZ1, B, h, net->g + o.b1);
+    }
     return EPI_OK;
 }
 
@@ -764,12 +919,16 @@ epi_status epi_mlp_gradients(epi_mlp *net, const float *X_dev, const float *t_de
     if (!net || !X_dev || !t_dev || rows < 1) return lfail(EPI_EINVAL, "epi_mlp_gradients: bad argument");
     Acts a;
     epi_status s = ensure_acts(net, rows, a);
-    if (s == EPI_OK) s = forward(net, X_dev, rows, a, a.Y);
+    if (s == EPI_OK) LCK(cudaMemsetAsync(net->status, 0, 4, net->stream));
+    if (s == EPI_OK) s = forward(net, X_dev, rows, a, a.Y, true);
     if (s == EPI_OK) s = backward(net, t_dev, rows, a);
     if (s != EPI_OK) return s;
+    int32_t hs = 0;
     if (grad_host) LCK(cudaMemcpyAsync(grad_host, net->g, (size_t)net->n_params * 4, cudaMemcpyDeviceToHost, net->stream));
     if (loss_host) LCK(cudaMemcpyAsync(loss_host, a.loss, 4, cudaMemcpyDeviceToHost, net->stream));
+    LCK(cudaMemcpyAsync(&hs, net->status, 4, cudaMemcpyDeviceToHost, net->stream));
     LCK(cudaStreamSynchronize(net->stream));
+    if (hs) return lfail(EPI_ETIMEOUT, "epi_mlp_gradients: a tensor-core wait gave up");
     return EPI_OK;
 }
 
@@ -779,7 +938,8 @@ epi_status epi_mlp_train_step(epi_mlp *net, const float *X_dev, const float *t_d
     if (!net || !X_dev || !t_dev || rows < 1) return lfail(EPI_EINVAL, "epi_mlp_train_step: bad argument");
     Acts a;
     epi_status s = ensure_acts(net, rows, a);
-    if (s == EPI_OK) s = forward(net, X_dev, rows, a, a.Y);
+    if (s == EPI_OK) LCK(cudaMemsetAsync(net->status, 0, 4, net->stream));
+    if (s == EPI_OK) s = forward(net, X_dev, rows, a, a.Y, true);
     if (s == EPI_OK) s = backward(net, t_dev, rows, a);
     if (s != EPI_OK) return s;
     net->step++;
@@ -789,8 +949,12 @@ epi_status epi_mlp_train_step(epi_mlp *net, const float *X_dev, const float *t_d
                                                                           net->n_params, lr, b1, b2, 1e-8f, wd, c1, c2);
     LCK(cudaGetLastError());
     if (loss_host) {
+        // the status word is only ever set by a tensor-core wait that gave up
+        int32_t hs = 0;
         LCK(cudaMemcpyAsync(loss_host, a.loss, 4, cudaMemcpyDeviceToHost, net->stream));
+        LCK(cudaMemcpyAsync(&hs, net->status, 4, cudaMemcpyDeviceToHost, net->stream));
         LCK(cudaStreamSynchronize(net->stream));
+        if (hs) return lfail(EPI_ETIMEOUT, "epi_mlp_train_step: a tensor-core wait gave up");
     }
     return EPI_OK;
 }

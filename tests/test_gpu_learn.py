@@ -240,7 +240,7 @@ def test_mlp_gradients_match_reference(epi, ctx, rows, hidden):
     g = g.astype(np.float64)
     # same storage rounding as the library: agreement up to FP32 accumulation
     y_q, _ = M.forward(theta, X, 25, hidden, rnd=_bf16)
-    g_q = M.gradients(theta, X, t, 25, hidden, rnd=_bf16)
+    g_q = M.gradients(theta, X, t, 25, hidden, rnd=_bf16, rnd_dz=_bf16)
     assert _rel(y, y_q) <= 1e-4
     offs = np.cumsum([0, hidden * 25, hidden, hidden * hidden, hidden, hidden, 1])
     for a, b in zip(offs[:-1], offs[1:]):
@@ -331,7 +331,7 @@ def test_mlp_gradients_elementwise(epi, ctx, rows, hidden):
     t = (y_q + 4.0 * scale * np.where(np.arange(rows) % 2 == 0, 1.0, -1.0)).astype(np.float32)
     g, _ = net.gradients(torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda())
     g = g.astype(np.float64)
-    g_q = M.gradients(theta, X, t, 25, hidden, rnd=_bf16)
+    g_q = M.gradients(theta, X, t, 25, hidden, rnd=_bf16, rnd_dz=_bf16)
     S, L, A = _grad_magnitudes(theta, X, t, 25, hidden, _bf16)
     err = np.abs(g - g_q)
     bound = 2.0 ** -6 * L + 2.0 ** -12 * S + A + 1e-30

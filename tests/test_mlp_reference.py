@@ -61,3 +61,24 @@ def test_adamw_second_step_closed_form():
     np.testing.assert_allclose(th2, want, rtol=1e-12, atol=1e-15)
     np.testing.assert_allclose(m, -0.01 * g, rtol=1e-12)
     np.testing.assert_allclose(v, 0.001999 * g * g, rtol=1e-12)
+
+
+def test_rounded_layer2_gradient_only_changes_the_two_products():
+    # rnd_dz stores the layer-2 pre-activation gradient in a coarser format
+    # only where it enters the W2 gradient and the gradient passed to layer 1:
+    # every other block (W3, b3, b2) is unchanged, and with an identity
+    # rounding nothing changes
+    rng = np.random.default_rng(3)
+    n_in, h, B = 5, 8, 11
+    P = h * n_in + h + h * h + h + h + 1
+    theta = rng.normal(0, 0.5, P)
+    X = rng.normal(0, 1, (B, n_in))
+    t = rng.normal(0, 1, B)
+    g = mlp.gradients(theta, X, t, n_in, h)
+    assert np.array_equal(g, mlp.gradients(theta, X, t, n_in, h, rnd_dz=lambda a: a))
+    coarse = mlp.gradients(theta, X, t, n_in, h, rnd_dz=lambda a: np.round(a * 8) / 8)
+    o_w2 = h * n_in + h
+    o_b2 = o_w2 + h * h
+    assert np.array_equal(g[o_b2:], coarse[o_b2:])
+    assert not np.array_equal(g[o_w2:o_b2], coarse[o_w2:o_b2])
+    assert not np.array_equal(g[:h * n_in], coarse[:h * n_in])
