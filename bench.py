@@ -553,6 +553,7 @@ def run_ours(args):
         from paper_2201_02460_gb300 import proposer_eval
         comp["proposer_order5/mlp_inference"] = measure_mlp_inference(epi, ctx, peaks)["mlp_inference"]
         comp["proposer_order5/mlp_training"] = measure_training(epi, ctx, peaks)
+        comp["proposer_order5/mlp_training_65536"] = measure_training(epi, ctx, peaks, rows=65536, steps=20)
         if not args.quick:
             # 2000 SNPs x 4000 samples with a planted 5-SNP parity: a trained
             # network against the heuristic, recall of the candidate space's

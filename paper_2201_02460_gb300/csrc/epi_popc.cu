@@ -33,11 +33,12 @@ namespace epi {
 
 __host__ __device__ constexpr int ipow3(int k) { return k <= 0 ? 1 : 3 * ipow3(k - 1); }
 
-// Words between consecutive rows of a staged prefix table.  Orders 6-8 read
-// the table with one lane per row (a warp per combination), so the stride is
-// made an odd number of 16-byte units: the 32 lanes' uint4 loads of one word
-// position then spread over all banks.
-__host__ __device__ inline int popc_row_stride(int k, int32_t Wt) { return k >= 6 && (Wt & 4) == 0 ? Wt + 4 : Wt; }
+// Words between consecutive rows of a staged prefix table (orders 1-5).
+// Orders 6-8 read the table with one lane per row (a warp per combination)
+// and store it transposed by 16-byte words instead: uint4 u of row r at
+// [u][r], so the 32 lanes' loads of one word position are 512 contiguous
+// bytes (coalesced from global memory, conflict-free in shared memory).
+__host__ __device__ inline int popc_row_stride(int k, int32_t Wt) { (void)k; return Wt; }
 
 // One dataset of a launch.  A launch may cover several datasets of the same
 // order (batched search): CTAs [cta_begin, cta_begin + cta_count) of the grid
@@ -177,25 +178,28 @@ __device__ inline void flush_list(SubtileState &S, float *sc, uint64_t *rk, int 
 // derives genotype 2 from the row totals, sums its cell terms, and the warp
 // adds the lanes' sums.
 template <int K>
-__device__ __forceinline__ float score_popc_warp(const uint32_t *__restrict__ pre, int rstride,
+__device__ __forceinline__ float score_popc_warp(const uint32_t *__restrict__ pre,
                                                  const uint32_t *__restrict__ tot, const uint32_t *__restrict__ mj,
                                                  const DevData &d, const MiConstF32 &mc, int lane)
 {
     constexpr int PR = ipow3(K - 1);
     SumF32 acc;
+    // the table is transposed by uint4: word group u of row r at uint4 u PR + r
+    const uint4 *T = reinterpret_cast<const uint4 *>(pre);
 #pragma unroll 1
     for (int r0 = lane; r0 < PR; r0 += 4 * 32) {
-        const uint32_t *rp[4];
+        const uint4 *rp[4];
 #pragma unroll
-        for (int i = 0; i < 4; i++) rp[i] = pre + (size_t)min(r0 + 32 * i, PR - 1) * rstride;
+        for (int i = 0; i < 4; i++) rp[i] = T + min(r0 + 32 * i, PR - 1);
         uint32_t a0[4] = {0, 0, 0, 0}, a1[4] = {0, 0, 0, 0}, b0[4] = {0, 0, 0, 0}, b1[4] = {0, 0, 0, 0};
 #pragma unroll 2
         for (int w = 0; w < d.W1; w += 4) {
             const uint4 x = __ldg(reinterpret_cast<const uint4 *>(mj + w));
             const uint4 y = __ldg(reinterpret_cast<const uint4 *>(mj + d.Wt + w));
+            const size_t off = (size_t)(w >> 2) * PR;
 #pragma unroll
             for (int i = 0; i < 4; i++) {
-                const uint4 p = *reinterpret_cast<const uint4 *>(rp[i] + w);
+                const uint4 p = rp[i][off];
                 a0[i] += popc4(p, x);
                 a1[i] += popc4(p, y);
             }
@@ -204,9 +208,10 @@ __device__ __forceinline__ float score_popc_warp(const uint32_t *__restrict__ pr
         for (int w = d.W1; w < d.Wt; w += 4) {
             const uint4 x = __ldg(reinterpret_cast<const uint4 *>(mj + w));
             const uint4 y = __ldg(reinterpret_cast<const uint4 *>(mj + d.Wt + w));
+            const size_t off = (size_t)(w >> 2) * PR;
 #pragma unroll
             for (int i = 0; i < 4; i++) {
-                const uint4 p = *reinterpret_cast<const uint4 *>(rp[i] + w);
+                const uint4 p = rp[i][off];
                 b0[i] += popc4(p, x);
                 b1[i] += popc4(p, y);
             }
@@ -317,9 +322,11 @@ __global__ void __launch_bounds__(128) popc_search_kernel(PopcParams P)
             // prefix SNPs: their AND is formed once, then the last two SNPs'
             // rows (k + 3 loads per 9 rows instead of 9 (k - 1))
             constexpr int PB = PR / 9;
+            // block index fastest: consecutive threads write consecutive rows
+            // of one word group of the transposed table
             for (int idx = threadIdx.x; idx < ns * PB * W4; idx += blockDim.x) {
-                const int w4 = idx % W4;
-                const int blk = (idx / W4) % PB;
+                const int blk = idx % PB;
+                const int w4 = (idx / PB) % W4;
                 const int s = idx / (W4 * PB);
                 uint4 base = make_uint4(~0u, ~0u, ~0u, ~0u);
                 int rem = blk;
@@ -338,15 +345,14 @@ __global__ void __launch_bounds__(128) popc_search_kernel(PopcParams P)
                 uint4 lb[3];
 #pragma unroll
                 for (int h = 0; h < 3; h++) lb[h] = __ldg(mb + h * W4 + w4);
-                uint32_t *ps = pre + (size_t)s * slot_words + (size_t)blk * 9 * rstride;
+                uint4 *ps = reinterpret_cast<uint4 *>(pre + (size_t)s * slot_words) + (size_t)w4 * PR + blk * 9;
 #pragma unroll
                 for (int g = 0; g < 3; g++) {
                     const uint4 a = __ldg(ma + g * W4 + w4);
                     const uint4 b1 = make_uint4(base.x & a.x, base.y & a.y, base.z & a.z, base.w & a.w);
 #pragma unroll
                     for (int h = 0; h < 3; h++)
-                        reinterpret_cast<uint4 *>(ps + (size_t)(g * 3 + h) * rstride)[w4] =
-                            make_uint4(b1.x & lb[h].x, b1.y & lb[h].y, b1.z & lb[h].z, b1.w & lb[h].w);
+                        ps[g * 3 + h] = make_uint4(b1.x & lb[h].x, b1.y & lb[h].y, b1.z & lb[h].z, b1.w & lb[h].w);
                 }
             }
         } else
@@ -384,7 +390,24 @@ __global__ void __launch_bounds__(128) popc_search_kernel(PopcParams P)
             reinterpret_cast<uint4 *>(pre + (size_t)s * slot_words + (size_t)row * rstride)[w4] = acc;
         }
         __syncthreads();
-        // per-row totals of each subtable (the third genotype by subtraction)
+        // per-row totals of each subtable (the third genotype by subtraction);
+        // orders 6-8: one thread per (row, subtable) of the transposed table,
+        // consecutive threads on consecutive rows
+        if constexpr (K >= 6) {
+            for (int idx = threadIdx.x; idx < ns * PR * 2; idx += blockDim.x) {
+                const int row = idx % PR;
+                const int half = (idx / PR) & 1;
+                const int s = idx / (PR * 2);
+                const uint4 *T = reinterpret_cast<const uint4 *>(pre + (size_t)s * slot_words) + row;
+                const int ub = half ? d.W1 / 4 : 0, ue = half ? d.Wt / 4 : d.W1 / 4;
+                uint32_t c = 0;
+                for (int u = ub; u < ue; u++) {
+                    const uint4 v = T[(size_t)u * PR];
+                    c += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+                }
+                tot[((size_t)s * PR + row) * 2 + half] = c;
+            }
+        } else
         for (int idx = threadIdx.x; idx < ns * PR * 2; idx += blockDim.x) {
             const int half = idx & 1;
             const int sr = idx >> 1;
@@ -407,7 +430,7 @@ __global__ void __launch_bounds__(128) popc_search_kernel(PopcParams P)
                 int s = 0;
                 while (s + 1 < ns && f >= slot[s + 1].base) s++;
                 const int32_t j = slot[s].s_last + 1 + (int32_t)(f - slot[s].base);
-                const float score = score_popc_warp<K>(pre + (size_t)s * slot_words, rstride, tot + s * PR * 2,
+                const float score = score_popc_warp<K>(pre + (size_t)s * slot_words, tot + s * PR * 2,
                                                        d.masks + (int64_t)j * 3 * d.Wt, d, mc, lane);
                 if (lane == 0) {
                     if (P.all_scores) P.all_scores[f - (int64_t)D.rank_begin] = score;

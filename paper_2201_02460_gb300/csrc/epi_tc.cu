@@ -56,13 +56,10 @@
 #include "epi_internal.cuh"
 #include "epi_tcgen05.cuh"
 
-// A producers' load distance in K stages and the stage-release group size
-// (tuning parameters)
+// A producers' load distance in K stages (tuning parameter); the
+// stage-release group size is chosen per order (EPI_TC_RELEASE overrides it)
 #ifndef EPI_TC_PREFETCH
 #define EPI_TC_PREFETCH 2
-#endif
-#ifndef EPI_TC_RELEASE
-#define EPI_TC_RELEASE 3
 #endif
 
 namespace epi {
@@ -78,7 +75,17 @@ constexpr int kStagesB = 6;            // TMA stages of single-SNP rows
 // following MMAs start only after the earlier ones finish (about one MMA
 // latency of idle tensor pipe), so the issuer commits once per group of
 // kRelease stages instead of once per stage.
-constexpr int kRelease = EPI_TC_RELEASE;
+// measured best: groups of 2 stages at orders 2-3 (the epilogue bounds the
+// issuer), single stages at orders 4-5 (the A producers do)
+template <int K>
+constexpr int release_group()
+{
+#ifdef EPI_TC_RELEASE
+    return EPI_TC_RELEASE;
+#else
+    return K <= 3 ? 2 : 1;
+#endif
+}
 constexpr int kDescDepth = 4;
 constexpr int kEpiWarps = 8;           // two per TMEM lane quadrant
 constexpr int kProdWarps = 8;          // two threads per tile row
@@ -405,6 +412,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
     // candidate-buffer checks (a barrier and maybe a sort) every kJcPerCheck
     // groups of 8 last SNPs; the buffer holds two intervals' worth
     constexpr int kJcPerCheck = K == 2 ? 1 : 2;
+    constexpr int kRelease = release_group<K>();
     // orders 3-4: prefix sums through the shared transpose buffer
     constexpr bool kTranspose = K == 3 || K == 4;
     constexpr int kPairs = kWide ? 0 : kPPW * 8;              // (prefix, last SNP) pairs per warp and chunk
