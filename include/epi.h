@@ -452,7 +452,7 @@ epi_status epi_inject_alloc_failure(epi_ctx *ctx, int64_t after);
  * averaged), the launch's milliseconds, and the implied SM clock in MHz. */
 epi_status epi_tc_rate(epi_ctx *ctx, int64_t stages, double *out);
 
-/* Timing of the dominant counting kernel./* Timing of the dominant counting kernel.  After epi_profile_begin, every
+/* Timing of the dominant counting kernel.  After epi_profile_begin, every
  * launch of a search's counting kernel is bracketed by CUDA events on the
  * context's stream; epi_profile_end waits for those events and returns their
  * summed duration in milliseconds and the number of bracketed launches. */

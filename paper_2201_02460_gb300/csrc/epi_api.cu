@@ -196,6 +196,14 @@ struct SearchPlan {
     uint64_t rb = 0, re = 0, total = 0;
 };
 
+// Prefixes staged per sub-tile when the prefix tables live in global memory
+// (orders 7-8; tuning parameter: 1, 2 and 4 measured 170, 131 and 210 ms on
+// the order-8 Table-2 workload).
+#ifndef EPI_GP_SLOTS
+#define EPI_GP_SLOTS 2
+#endif
+constexpr int kGlobalPrefixSlots = EPI_GP_SLOTS;
+
 // Popcount-path launch shape: row group R (counters per thread), sub-tile T,
 // staged prefixes per sub-tile and CTAs per SM.  Residency first (the POPC
 // pipe needs many warps to hide its latency), then staged prefixes.
@@ -249,11 +257,11 @@ epi_status plan_popc(const epi_dataset *ds, SearchPlan &p, int R_req = 0)
         for (int tile : {256, 128}) {
             if (tune_tile && tile != tune_tile) continue;
             const int cand_p2 = next_pow2(p.pool + 2 * tile);
-            const size_t sm = popc_smem_bytes(p.k, ds->Wt, 1, cand_p2, true) + 1024;
+            const size_t sm = popc_smem_bytes(p.k, ds->Wt, kGlobalPrefixSlots, cand_p2, true) + 1024;
             if (sm > limit) continue;
             const int occ = popc_max_active(p.k, p.R, sm, true);
             if (occ <= 0) continue;
-            p.tile = tile; p.cand_p2 = cand_p2; p.slots = 1; p.smem = sm; p.grid = std::min(occ, 4);
+            p.tile = tile; p.cand_p2 = cand_p2; p.slots = kGlobalPrefixSlots; p.smem = sm; p.grid = std::min(occ, 4);
             p.global_prefix = true;
             best_score = 0;
             break;

@@ -110,7 +110,7 @@ def quick(ctx=None, seed_eval: int = synth.BASE_SEED + 104, top_triples: int = 6
 
 
 def evaluate_large(ctx=None, n_snps: int = 2000, n_samples: int = 4000, top_triples: int = 512,
-                   train_triples: int = 64, budgets=(10 ** 6, 10 ** 7, 10 ** 8),
+                   train_triples: int = 256, budgets=(10 ** 6, 10 ** 7, 10 ** 8),
                    seed: int = synth.BASE_SEED + 5) -> dict:
     """The proposer at 2000 SNPs x 4000 samples, where the exhaustive order-5
     search (C(2000, 5) = 2.65e14 sets) is out of reach.

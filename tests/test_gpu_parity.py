@@ -533,3 +533,13 @@ def test_count_variants_bit_exact(epi, ctx, k, n, m, m1):
         bad = np.nonzero((r["tables"] != want).any(axis=(1, 2)))[0]
         assert len(bad) == 0, (v, len(bad), bad[:5])
         assert r["checksum"] == want_sum % (1 << 64), v
+
+
+@pytest.mark.parametrize("k,n", [(3, 60), (4, 26)])
+def test_tc_large_top_n(epi, ctx, k, n):
+    """top_n = 1024: the candidate pool (1088) no longer fits beside the
+    operand rings, so the tensor kernel keeps its candidate lists in global
+    memory; the result is still the oracle's."""
+    geno, pheno = random_data(n, 900, seed=40 + k)
+    ds, r, oc, om, _ = _search_both(epi, ctx, geno, pheno, k, 1024, path="tc")
+    _check_result(r, geno, pheno, oc, om)
