@@ -316,6 +316,22 @@ __device__ __forceinline__ uint32_t f2u_exact(float v) { return __float_as_uint(
 // t(x) = x log2 x of an accumulator value x = count / 32 (0 for x = 0)
 __device__ __forceinline__ float tlog32(float x) { return x * __log2f(fmaxf(x, 0.03125f)); }
 
+// sum over the three cells of one tile row of t(a) + t(b) - t(a + b), as
+// one chain of fused multiply-adds (a, b: case and control accumulators)
+__device__ __forceinline__ float row_screen(float a0, float a1, float a2, float b0, float b1, float b2)
+{
+    const float s0 = a0 + b0, s1 = a1 + b1, s2 = a2 + b2;
+    float v = a0 * __log2f(fmaxf(a0, 0.03125f));
+    v = fmaf(b0, __log2f(fmaxf(b0, 0.03125f)), v);
+    v = fmaf(-s0, __log2f(fmaxf(s0, 0.03125f)), v);
+    v = fmaf(a1, __log2f(fmaxf(a1, 0.03125f)), v);
+    v = fmaf(b1, __log2f(fmaxf(b1, 0.03125f)), v);
+    v = fmaf(-s1, __log2f(fmaxf(s1, 0.03125f)), v);
+    v = fmaf(a2, __log2f(fmaxf(a2, 0.03125f)), v);
+    v = fmaf(b2, __log2f(fmaxf(b2, 0.03125f)), v);
+    return fmaf(-s2, __log2f(fmaxf(s2, 0.03125f)), v);
+}
+
 __device__ __forceinline__ float warp_sum(float v)
 {
 #pragma unroll
@@ -943,10 +959,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                             o[cells + pos * 3 + 1] = f2u_exact(32.0f * fb1);
                             o[cells + pos * 3 + 2] = f2u_exact(32.0f * fb2);
                         }
-                        vrow[jj] = prow ? (tlog32(fa0) + tlog32(fb0) - tlog32(fa0 + fb0)) +
-                                              (tlog32(fa1) + tlog32(fb1) - tlog32(fa1 + fb1)) +
-                                              (tlog32(fa2) + tlog32(fb2) - tlog32(fa2 + fb2))
-                                        : 0.0f;
+                        vrow[jj] = prow ? row_screen(fa0, fa1, fa2, fb0, fb1, fb2) : 0.0f;
                     }
                     // transpose: lane l's 8 values at [l][0..7]; the lane of
                     // pair (prefix pp, last SNP jj) reads rows pp*kPR .. of
