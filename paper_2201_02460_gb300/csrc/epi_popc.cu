@@ -472,6 +472,271 @@ __global__ void __launch_bounds__(128) popc_search_kernel(PopcParams P)
     if (threadIdx.x == 0) P.list_count[blockIdx.x] = L;
 }
 
+// ---------------------------------------------------------------------------
+// Orders 7-8 with the (k-2)-prefix table in shared memory.
+//
+// Combinations that share their first k-2 SNPs are consecutive in
+// lexicographic order, their last two SNPs (j1 < j2) running over the pairs
+// after the prefix.  The prefix's table (3^(k-2) = 243 or 729 rows, Section
+// 2.1) is built once in shared memory, transposed by 16-byte words, and each
+// warp counts one pair at a time, lanes over the rows: per row and class the
+// four joint counts n[g1][g2] (g1, g2 in {0, 1}: the prefix row AND both
+// last SNPs' genotype rows) and the four single counts of row & j1's
+// genotype-0/1 rows and row & j2's; the other five cells follow by
+// subtraction (n[g1][2] = row & j1:g1 minus n[g1][0] + n[g1][1], and so on,
+// n[2][2] from the row total).  No table leaves the SM, and every staged
+// table serves C(L, 2) combinations (L = SNPs after the prefix) instead of L.
+constexpr int kPairThreads = 256;
+constexpr int kPairChunk = 256;   // pairs counted between candidate-buffer checks
+
+__host__ __device__ inline size_t pair_table_bytes(int k, int32_t Wt)
+{
+    const size_t PR = (size_t)ipow3(k - 2);
+    return (size_t)(Wt / 4) * PR * 16 + PR * 2 * 4;
+}
+
+__host__ __device__ inline int pair_cand_p2(int pool) { return next_pow2(pool + 2 * kPairChunk); }
+
+__host__ __device__ inline size_t pair_smem_bytes(int k, int32_t Wt, int pool)
+{
+    return ((pair_table_bytes(k, Wt) + 15) & ~(size_t)15) + (size_t)pair_cand_p2(pool) * 12;
+}
+
+// next m-subset of [0, n) in lex order whose last element is at most n - 3
+// (two SNPs must follow); false after the last
+__device__ inline bool next_prefix_pairs(int32_t *p, int m, int64_t n)
+{
+    const int64_t u = n - 2;
+    int t = m - 1;
+    while (t >= 0 && p[t] == u - m + t) t--;
+    if (t < 0) return false;
+    p[t]++;
+    for (int v = t + 1; v < m; v++) p[v] = p[v - 1] + 1;
+    return true;
+}
+
+// the pair of lexicographic index i among the 2-subsets of [c + 1, n)
+__device__ __forceinline__ void pair_of_index(int64_t n, int32_t c, int64_t i, int32_t &j1, int32_t &j2)
+{
+    const int64_t L = n - 1 - c;
+    int64_t a = 0, before = 0;
+    while (before + (L - 1 - a) <= i) { before += L - 1 - a; a++; }
+    j1 = c + 1 + (int32_t)a;
+    j2 = j1 + 1 + (int32_t)(i - before);
+}
+
+// Single-precision MI of (prefix, j1, j2): lanes take prefix rows lane,
+// lane + 32, lane + 64, lane + 96 (then the next 128), counting per class the
+// joint counts n[g1][g2] (g1, g2 in {0, 1}) and the single counts of the row
+// with j1's and with j2's genotype-0/1 rows over the class's word groups.
+template <int PR>
+__device__ __forceinline__ float score_pair_warp(const uint4 *__restrict__ T, const uint32_t *__restrict__ tot,
+                                                 const uint32_t *__restrict__ mj1, const uint32_t *__restrict__ mj2,
+                                                 int W4, int W14, const MiConstF32 &mc, int lane)
+{
+    const uint4 *x0p = reinterpret_cast<const uint4 *>(mj1), *x1p = x0p + W4;
+    const uint4 *y0p = reinterpret_cast<const uint4 *>(mj2), *y1p = y0p + W4;
+    SumF32 acc;
+#pragma unroll 1
+    for (int r0 = lane; r0 < PR; r0 += 4 * 32) {
+        int rr[4];
+#pragma unroll
+        for (int i = 0; i < 4; i++) rr[i] = min(r0 + 32 * i, PR - 1);
+        // cnt[i][y][q]: q = n00, n01, n10, n11, j1 g0, j1 g1, j2 g0, j2 g1
+        uint32_t cnt[4][2][8];
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int y = 0; y < 2; y++)
+#pragma unroll
+                for (int q = 0; q < 8; q++) cnt[i][y][q] = 0;
+#pragma unroll
+        for (int y = 0; y < 2; y++) {
+            const int ub = y ? W14 : 0, ue = y ? W4 : W14;
+#pragma unroll 1
+            for (int u = ub; u < ue; u++) {
+                const uint4 x0 = __ldg(x0p + u), x1 = __ldg(x1p + u), y0 = __ldg(y0p + u), y1 = __ldg(y1p + u);
+                const uint4 j00 = make_uint4(x0.x & y0.x, x0.y & y0.y, x0.z & y0.z, x0.w & y0.w);
+                const uint4 j01 = make_uint4(x0.x & y1.x, x0.y & y1.y, x0.z & y1.z, x0.w & y1.w);
+                const uint4 j10 = make_uint4(x1.x & y0.x, x1.y & y0.y, x1.z & y0.z, x1.w & y0.w);
+                const uint4 j11 = make_uint4(x1.x & y1.x, x1.y & y1.y, x1.z & y1.z, x1.w & y1.w);
+                const size_t off = (size_t)u * PR;
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    const uint4 p = T[off + rr[i]];
+                    cnt[i][y][0] += popc4(p, j00);
+                    cnt[i][y][1] += popc4(p, j01);
+                    cnt[i][y][2] += popc4(p, j10);
+                    cnt[i][y][3] += popc4(p, j11);
+                    cnt[i][y][4] += popc4(p, x0);
+                    cnt[i][y][5] += popc4(p, x1);
+                    cnt[i][y][6] += popc4(p, y0);
+                    cnt[i][y][7] += popc4(p, y1);
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            if (r0 + 32 * i >= PR) continue;
+            uint32_t cell[2][9];
+#pragma unroll
+            for (int y = 0; y < 2; y++) {
+                const uint32_t *c = cnt[i][y];
+                const uint32_t t = tot[rr[i] * 2 + y];
+                cell[y][0] = c[0];                       // (g1, g2) = (0, 0)
+                cell[y][1] = c[1];                       // (0, 1)
+                cell[y][2] = c[4] - c[0] - c[1];         // (0, 2)
+                cell[y][3] = c[2];                       // (1, 0)
+                cell[y][4] = c[3];                       // (1, 1)
+                cell[y][5] = c[5] - c[2] - c[3];         // (1, 2)
+                cell[y][6] = c[6] - c[0] - c[2];         // (2, 0)
+                cell[y][7] = c[7] - c[1] - c[3];         // (2, 1)
+                cell[y][8] = t - c[4] - c[5] - cell[y][6] - cell[y][7];   // (2, 2)
+            }
+#pragma unroll
+            for (int q = 0; q < 9; q++) acc.add(cell_terms_f32(cell[0][q], cell[1][q], mc));
+        }
+    }
+    float v = acc.value();
+#pragma unroll
+    for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return __fdiv_rn(v, mc.fm);
+}
+
+template <int K>
+__global__ void __launch_bounds__(kPairThreads, 1) popc_pair_kernel(PopcParams P)
+{
+    constexpr int km2 = K - 2;
+    constexpr int PR = ipow3(K - 2);
+    constexpr int PB = PR / 9;
+    const PopcDs &D = P.one;
+    const DevData d = D.d;
+    const int W4 = d.Wt >> 2, W14 = d.W1 >> 2;
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint4 *T = reinterpret_cast<uint4 *>(smem);                          // [W4][PR]
+    uint32_t *tot = reinterpret_cast<uint32_t *>(T + (size_t)W4 * PR);   // [PR][2]
+    uint64_t *rk = reinterpret_cast<uint64_t *>(smem + ((pair_table_bytes(K, d.Wt) + 15) & ~(size_t)15));
+    const int cand_p2 = pair_cand_p2(P.pool);
+    float *sc = reinterpret_cast<float *>(rk + cand_p2);
+    __shared__ SubtileState S;
+    __shared__ int32_t pre[kMaxOrderGpu];
+    __shared__ int64_t pbase, i_lo, i_hi;
+
+    const MiConstF32 mc = make_mi_const(d.m, d.m1, d.m0);
+    const uint64_t span = D.rank_end - D.rank_begin;
+    const uint64_t cb = blockIdx.x - (uint64_t)D.cta_begin, cn = (uint64_t)D.cta_count;
+    const int64_t R_b = (int64_t)(D.rank_begin + (uint64_t)(((unsigned __int128)span * cb) / cn));
+    const int64_t R_e = (int64_t)(D.rank_begin + (uint64_t)(((unsigned __int128)span * (cb + 1)) / cn));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int kWarps = kPairThreads / 32;
+
+    if (threadIdx.x == 0) {
+        S.list_len = 0; S.nbuf = 0; S.thr = -1.0f; S.done = R_b >= R_e;
+        if (!S.done) {
+            int32_t c[kMaxOrderGpu];
+            unrank_lex(d.binom, d.n, K, (uint64_t)R_b, c);
+            for (int t = 0; t < km2; t++) pre[t] = c[t];
+            // rank of the prefix's first pair (c_last + 1, c_last + 2)
+            const int32_t cl = c[km2 - 1];
+            const int64_t L = d.n - 1 - cl;
+            const int64_t a = c[K - 2] - (cl + 1), b = c[K - 1] - (c[K - 2] + 1);
+            const int64_t idx = (a * (2 * L - a - 1)) / 2 + b;
+            pbase = R_b - idx;
+        }
+    }
+    __syncthreads();
+    while (!S.done) {
+        if (threadIdx.x == 0) {
+            const int64_t L = d.n - 1 - pre[km2 - 1];
+            const int64_t np = L * (L - 1) / 2;
+            i_lo = R_b > pbase ? R_b - pbase : 0;
+            i_hi = R_e - pbase < np ? R_e - pbase : np;
+            const float g = __uint_as_float(*(volatile uint32_t *)D.global_thr);
+            if (S.list_len == P.pool || g > 0.0f) S.thr = fmaxf(S.thr, g);
+        }
+        __syncthreads();
+        // ---- the prefix's table: blocks of 9 rows share the genotypes of
+        // the first k-4 SNPs, the last two prefix SNPs give the 9 rows
+        for (int idx = threadIdx.x; idx < PB * W4; idx += blockDim.x) {
+            const int blk = idx % PB;
+            const int w4 = idx / PB;
+            uint4 base = make_uint4(~0u, ~0u, ~0u, ~0u);
+            int rem = blk, div = PB / 3;
+#pragma unroll
+            for (int t = 0; t < km2 - 2; t++) {
+                const int g = rem / div;
+                rem -= g * div;
+                div = div > 1 ? div / 3 : 1;
+                const uint4 v = __ldg(reinterpret_cast<const uint4 *>(d.masks + ((int64_t)pre[t] * 3 + g) * d.Wt) + w4);
+                base.x &= v.x; base.y &= v.y; base.z &= v.z; base.w &= v.w;
+            }
+            const uint4 *ma = reinterpret_cast<const uint4 *>(d.masks + (int64_t)pre[km2 - 2] * 3 * d.Wt);
+            const uint4 *mb = reinterpret_cast<const uint4 *>(d.masks + (int64_t)pre[km2 - 1] * 3 * d.Wt);
+            uint4 lb[3];
+#pragma unroll
+            for (int h = 0; h < 3; h++) lb[h] = __ldg(mb + h * W4 + w4);
+            uint4 *ps = T + (size_t)w4 * PR + blk * 9;
+#pragma unroll
+            for (int g = 0; g < 3; g++) {
+                const uint4 a = __ldg(ma + g * W4 + w4);
+                const uint4 b1 = make_uint4(base.x & a.x, base.y & a.y, base.z & a.z, base.w & a.w);
+#pragma unroll
+                for (int h = 0; h < 3; h++)
+                    ps[g * 3 + h] = make_uint4(b1.x & lb[h].x, b1.y & lb[h].y, b1.z & lb[h].z, b1.w & lb[h].w);
+            }
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < PR * 2; idx += blockDim.x) {
+            const int row = idx % PR, half = idx / PR;
+            const int ub = half ? W14 : 0, ue = half ? W4 : W14;
+            uint32_t c = 0;
+            for (int u = ub; u < ue; u++) {
+                const uint4 v = T[(size_t)u * PR + row];
+                c += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+            }
+            tot[row * 2 + half] = c;
+        }
+        __syncthreads();
+        // ---- the pairs of this prefix in the CTA's range, in chunks
+        const int64_t lo = i_lo, hi = i_hi;
+        const int32_t cl = pre[km2 - 1];
+        const float thr0 = S.thr;
+        for (int64_t c0 = lo; c0 < hi; c0 += kPairChunk) {
+            const int64_t c1 = c0 + kPairChunk < hi ? c0 + kPairChunk : hi;
+            const int list_len = S.list_len;
+            const float thr = S.thr > thr0 ? S.thr : thr0;
+            for (int64_t i = c0 + warp; i < c1; i += kWarps) {
+                int32_t j1, j2;
+                pair_of_index(d.n, cl, i, j1, j2);
+                const float score = score_pair_warp<PR>(T, tot, d.masks + (int64_t)j1 * 3 * d.Wt,
+                                                        d.masks + (int64_t)j2 * 3 * d.Wt, W4, W14, mc, lane);
+                if (lane == 0 && score >= thr) {
+                    const int pos = list_len + atomicAdd(&S.nbuf, 1);
+                    sc[pos] = score;
+                    rk[pos] = (uint64_t)(pbase + i);
+                }
+            }
+            __syncthreads();
+            if (S.list_len + S.nbuf + kPairChunk > cand_p2) flush_list(S, sc, rk, P.pool, cand_p2, D.global_thr);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int64_t L = d.n - 1 - pre[km2 - 1];
+            pbase += L * (L - 1) / 2;
+            S.done = pbase >= R_e || !next_prefix_pairs(pre, km2, d.n);
+        }
+        __syncthreads();
+    }
+    if (S.nbuf > 0) flush_list(S, sc, rk, P.pool, cand_p2, D.global_thr);
+    __syncthreads();
+    const int Lc = S.list_len;
+    for (int i = threadIdx.x; i < Lc; i += blockDim.x) {
+        P.list_score[(size_t)blockIdx.x * P.pool + i] = sc[i];
+        P.list_rank[(size_t)blockIdx.x * P.pool + i] = rk[i];
+    }
+    if (threadIdx.x == 0) P.list_count[blockIdx.x] = Lc;
+}
+
 template <int K, int R, bool GP>
 static cudaError_t launch_kr(const PopcParams &p, int grid, size_t smem, cudaStream_t st)
 {
@@ -602,6 +867,22 @@ cudaError_t launch_popc_search(const DevData &d, int k, int R, uint64_t rank_beg
     p.list_score = list_score;
     p.list_rank = list_rank;
     p.list_count = list_count;
+    // orders 7-8 with the (k-2)-prefix table in shared memory where it fits
+    // (the searches that return every score keep the (k-1)-prefix kernel)
+    if ((k == 7 || k == 8) && !all_scores) {
+        int dev = 0, optin = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess) {
+            const size_t ps = pair_smem_bytes(k, d.Wt, pool);
+            if (ps <= (size_t)optin) {
+                auto kern = k == 7 ? popc_pair_kernel<7> : popc_pair_kernel<8>;
+                cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ps);
+                if (e != cudaSuccess) return e;
+                kern<<<grid, kPairThreads, ps, st>>>(p);
+                return cudaGetLastError();
+            }
+        }
+    }
     return launch_dispatch(p, k, R, grid, smem, st);
 }
 
