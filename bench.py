@@ -317,7 +317,8 @@ def measure_batch_full(epi, ctx, synth, peaks, tc_rate, stream):
         if key not in chosen:
             chosen[key] = epi.autotune(ds, k)
     tune_s = time.perf_counter() - t0
-    tc_peak = 2.0 * tc_rate["mac_per_clk_sm"] * N_SMS * SM_MAX_MHZ * 1e6 if tc_rate else FP8_OVER_BF16 * peaks["bf16"] * 1e12
+    tc_peak = (2.0 * tc_rate[0]["mac_per_clk_sm"] * N_SMS * SM_MAX_MHZ * 1e6 if tc_rate
+               else FP8_OVER_BF16 * peaks["bf16"] * 1e12)
     popc_peak = N_SMS * POPC_PER_SM_CLK * SM_MAX_MHZ * 1e6
     work = 0
     ideal_s = 0.0
@@ -373,21 +374,45 @@ def measure_mlp_inference(epi, ctx, peaks):
     return out
 
 
+def comb_shift(d, k):
+    """Class shift of the tensor path's combined-class variant, 0 where the
+    separate-class variant runs (the rule include/epi.h states for
+    EPI_TC_AUTO)."""
+    m1, m0 = d.n_cases, d.n_samples - d.n_cases
+    if k != 3:
+        return 0
+    p = 1
+    while p < 15 and (1 << p) <= m0:
+        p += 1
+    return p if p <= 14 and m1 * (1 << p) + m0 < (1 << 23) else 0
+
+
 def tc_executed_flops(d, k):
     """Multiply-adds the tensor-core counting kernel issues for a whole search,
-    x 2: every work item is one M128 x N128 tile over the padded K of both
-    classes (128-individual stages), and the items are the M tiles of
-    ppt prefixes that start in panel c times the N tiles of 64 last SNPs
-    after c (the kernel's item table)."""
+    x 2.  The items are the M tiles of ppt prefixes that start in panel c
+    times the N tiles after c (the kernel's item table), each over the padded
+    K of both classes (128-individual stages).  Separate classes: N tiles of
+    64 last SNPs, every MMA M128 x N128.  Combined classes: N tiles of 128
+    last SNPs, the MMA's N cut to the columns below 2 n (steps of 16)."""
     n = d.n_snps
     ppt = 1 if 3 ** (k - 1) > 32 else 4 * (32 // 3 ** (k - 1))
-    items = 0
+    comb = comb_shift(d, k) != 0
+    kj = 128 if comb else 64
+    cols = 0
     for c in range(k - 2, n - 1):
         t0 = -(-math.comb(c, k - 1) // ppt)
         t1 = -(-math.comb(c + 1, k - 1) // ppt)
-        items += (t1 - t0) * (-(-(n - 1 - c) // 64))
+        if t1 == t0:
+            continue
+        # the N tiles of an M tile whose first prefix lies in panel c
+        per_m = 0
+        for u in range(-(-(n - 1 - c) // kj)):
+            j0 = c + 1 + u * kj
+            live = 2 * (n - j0)
+            per_m += min(2 * kj, -(-live // 16) * 16) if comb else 2 * kj
+        cols += (t1 - t0) * per_m
     kt = 32 * 4 * (-(-d.n_cases // 128) + -(-(d.n_samples - d.n_cases) // 128))
-    return 2.0 * items * 128 * 128 * kt
+    return 2.0 * cols * 128 * kt
 
 
 def roofline(kind, d, k, kern_ms, peaks, tc_rate=None):
@@ -400,12 +425,16 @@ def roofline(kind, d, k, kern_ms, peaks, tc_rate=None):
         achieved = flops / (kern_ms / 1e3) / 1e12
         executed = tc_executed_flops(d, k) / (kern_ms / 1e3) / 1e12
         fp8_conv = FP8_OVER_BF16 * peaks["bf16"]
+        comb = comb_shift(d, k) != 0
         if tc_rate:
             # the measured rate of the kernel's own MMA, at the maximum SM clock
-            peak = 2.0 * tc_rate["mac_per_clk_sm"] * N_SMS * SM_MAX_MHZ * 1e6 / 1e12
-            note = (f"peak = measured FP8 M128 N128 K32 tcgen05.mma rate, {tc_rate['mac_per_clk_sm']:.0f} "
-                    f"MAC/clk/SM x 152 SMs x 2070 MHz (probe ran at {tc_rate['sm_mhz']:.0f} MHz: "
-                    f"{tc_rate['tflops']:.0f} TFLOP/s); work 2*3^k*m flop per combination")
+            r = tc_rate[1 if comb else 0]
+            shape = "E5M2 M128 N256 K32" if comb else "E4M3 M128 N128 K32"
+            peak = 2.0 * r["mac_per_clk_sm"] * N_SMS * SM_MAX_MHZ * 1e6 / 1e12
+            note = (f"peak = measured FP8 {shape} tcgen05.mma rate, {r['mac_per_clk_sm']:.0f} "
+                    f"MAC/clk/SM x 152 SMs x 2070 MHz (probe ran at {r['sm_mhz']:.0f} MHz: "
+                    f"{r['tflops']:.0f} TFLOP/s); work 2*3^k*m flop per combination; "
+                    f"{'combined' if comb else 'separate'}-class variant")
         else:
             peak = fp8_conv
             note = f"FP8 (E4M3) dense = 2 x {peaks['source']} burst BF16; work 2*3^k*m flop per combination"
@@ -464,7 +493,7 @@ def run_ours(args):
     value = world * units * args.steps / (t_ms / 1e3)
     res = main_m["res"]
     # the roofline's denominator: the tensor pipe's rate for the counting MMA
-    tc_rate = ctx.tc_rate() if kind == "tc" or not args.no_compare else None
+    tc_rate = {s: ctx.tc_rate(shape=s) for s in (0, 1)} if kind == "tc" or not args.no_compare else None
 
     # end to end through the C-ABI: host genotypes in, host records out
     e2e_times = []
@@ -480,7 +509,8 @@ def run_ours(args):
 
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=t_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
-                dtype="f8e4m3 0/1 operands, f32 accumulate" if kind == "tc" else "u32",
+                dtype=(("f8e5m2 0/1 operands (classes combined), f32 accumulate" if comb_shift(d, k)
+                        else "f8e4m3 0/1 operands, f32 accumulate") if kind == "tc" else "u32"),
                 data="synthetic",
                 config=dict(**workload_desc(args.workload, d, k, top_n), path=path, counting=kind,
                             l2="flushed between steps (256 MiB write)", parallelism="replicas"),

@@ -62,6 +62,15 @@ typedef enum {
                               (EPI_EUNSUPPORTED else) */
 } epi_path;
 
+/* Tensor-core counting variant (epi_set_tc_variant). */
+typedef enum {
+    EPI_TC_AUTO = 0,       /* order 3 with m1 * 2^p + m0 < 2^23 (2^p the
+                              least power of two above m0, p <= 14): both
+                              classes in one accumulator, 256-column tiles;
+                              else separate case and control accumulators */
+    EPI_TC_SEPARATE = 1    /* always separate case and control accumulators */
+} epi_tc_variant;
+
 #define EPI_MAX_ORDER 8    /* highest order the API accepts (Table 2 goes to 8) */
 
 typedef struct epi_ctx epi_ctx;
@@ -438,19 +447,27 @@ epi_status epi_count_variant(epi_dataset *ds, int order, int variant, uint32_t *
  * epi_inject_alloc_failure: the device allocation of this context's calls
  * that comes after `after` further successful ones fails as if the device
  * were out of memory (the call returns EPI_ENOMEM and releases what it had
- * taken); it fires once.  A negative value cancels it. */
+ * taken); it fires once.  A negative value cancels it.
+ *
+ * epi_set_tc_variant: which tensor-core counting variant this context's
+ * searches use (an epi_tc_variant; EPI_TC_AUTO is the default).  Both count
+ * exactly and give identical results; EPI_TC_SEPARATE exists so that either
+ * variant can be checked on any dataset.  EPI_EINVAL for other values. */
 epi_status epi_set_wait_limit(epi_ctx *ctx, uint64_t limit_ns);
 epi_status epi_inject_alloc_failure(epi_ctx *ctx, int64_t after);
+epi_status epi_set_tc_variant(epi_ctx *ctx, int variant);
 
-/* Rate of the tensor pipe for the one MMA the tensor-core counting path
- * issues (tcgen05.mma kind::f8f6f4, M128 N128 K32, E4M3 operands in shared
- * memory, FP32 accumulation): one CTA per SM issues `stages` (32..2^32)
+/* Rate of the tensor pipe for an MMA the tensor-core counting path issues
+ * (tcgen05.mma kind::f8f6f4, operands in shared memory, FP32 accumulation):
+ * shape 0 = M128 N128 K32 with E4M3 operands (separate-class variant),
+ * shape 1 = M128 N256 K32 with E5M2 operands (combined-class variant);
+ * EPI_EINVAL for other shapes.  One CTA per SM issues `stages` (32..2^32)
  * groups of four such MMAs back to back from one thread, with no other work.
  * The paper has no counterpart; this is the roofline's denominator.
  * out[4]: dense rate in TFLOP/s (2 flop per multiply-add, over the launch's
  * event time), multiply-adds per SM clock (over each CTA's own cycle count,
  * averaged), the launch's milliseconds, and the implied SM clock in MHz. */
-epi_status epi_tc_rate(epi_ctx *ctx, int64_t stages, double *out);
+epi_status epi_tc_rate(epi_ctx *ctx, int shape, int64_t stages, double *out);
 
 /* Timing of the dominant counting kernel.  After epi_profile_begin, every
  * launch of a search's counting kernel is bracketed by CUDA events on the

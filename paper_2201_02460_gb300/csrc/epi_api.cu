@@ -44,6 +44,7 @@ struct epi_ctx {
     // test controls (epi_set_wait_limit, epi_inject_alloc_failure)
     unsigned long long wait_limit_ns = 0;   // tensor-core pipeline waits; 0 = the kernels' default
     int64_t fail_alloc_in = -1;             // device allocations until one fails; -1 = none
+    bool tc_combined = true;                // epi_set_tc_variant: combined-class variant where it applies
 };
 
 struct epi_dataset {
@@ -53,7 +54,8 @@ struct epi_dataset {
     int32_t W1 = 0, W0 = 0, Wt = 0;
     uint32_t *masks = nullptr;
     uint64_t *binom = nullptr;
-    unsigned char *b8 = nullptr;   // tensor-core operand, built on first use
+    unsigned char *b8 = nullptr;   // tensor-core operand (separate classes, E4M3), built on first use
+    unsigned char *b8c = nullptr;  // the same for the combined-class variant (E5M2), built on first use
     float *lower[5] = {};          // exhaustive order-1..4 scores for the proposer, built on first use
     DevData dev() const
     {
@@ -190,6 +192,7 @@ uint64_t tune_key(int k, int64_t n, int32_t wt)
 struct SearchPlan {
     int k = 0, top_n = 0, pool = 0, tile = 0, slots = 0, cand_p2 = 0, grid = 0, R = 0;
     bool tc = false;
+    int comb_p = 0;                // tensor path: class shift of the combined-class variant, 0 = separate classes
     bool global_prefix = false;    // popcount path: prefix tables in a global buffer (orders 7-8)
     float *all_scores = nullptr;   // optional: every combination's score (popcount path)
     size_t smem = 0;
@@ -307,12 +310,14 @@ epi_status choose_path(const epi_dataset *ds, int k, int path, uint64_t rb, uint
     return EPI_OK;
 }
 
-epi_status ensure_b8(epi_dataset *ds)
+// The dataset's B operand for a class shift (0: separate-class variant).
+epi_status ensure_b8(epi_dataset *ds, int comb_p = 0)
 {
-    if (ds->b8) return EPI_OK;
+    unsigned char *&buf = comb_p ? ds->b8c : ds->b8;
+    if (buf) return EPI_OK;
     epi_ctx *ctx = ds->ctx;
-    CK(ctx_malloc(ctx, (void **)&ds->b8, tc_b8_bytes(ds->dev())));
-    CK(launch_build_b8(ds->dev(), ds->b8, ctx->num_sms, ctx->stream));
+    CK(ctx_malloc(ctx, (void **)&buf, tc_b8_bytes(ds->dev())));
+    CK(launch_build_b8(ds->dev(), buf, ctx->num_sms, ctx->stream, comb_p));
     ctx->launches += 1;
     return EPI_OK;
 }
@@ -323,6 +328,7 @@ epi_status make_plan(const epi_dataset *ds, SearchPlan &p, int path)
     if (st != EPI_OK) return st;
     if (!p.tc) return plan_popc(ds, p);
     p.grid = ds->ctx->num_sms;
+    p.comb_p = ds->ctx->tc_combined ? tc_comb_shift(ds->dev(), p.k) : 0;
     return EPI_OK;
 }
 
@@ -350,8 +356,8 @@ epi_status queue_search(epi_dataset *ds, const SearchPlan &p, int path, epi_resu
         p.global_prefix ? a.take<uint32_t>((size_t)p.grid * p.slots * popc_slot_words(p.k, ds->Wt)) : 0;
     // tensor path: candidate buffers in global memory when they do not fit
     // beside the operand rings in shared memory (large pools)
-    const int tc_cp2 = p.tc ? tc_cand_p2(p.k, p.pool) : 0;
-    const bool tc_cg = p.tc && tc_smem_bytes(tc_cp2, p.k, false) > ctx->smem_optin;
+    const int tc_cp2 = p.tc ? tc_cand_p2(p.k, p.pool, p.comb_p != 0) : 0;
+    const bool tc_cg = p.tc && tc_smem_bytes(tc_cp2, p.k, false, p.comb_p != 0) > ctx->smem_optin;
     const size_t o_tcs = tc_cg ? a.take<float>((size_t)p.grid * tc_cp2) : 0;
     const size_t o_tcr = tc_cg ? a.take<uint64_t>((size_t)p.grid * tc_cp2) : 0;
     epi_status st = ensure_scratch(ctx, a.off);
@@ -370,7 +376,7 @@ epi_status queue_search(epi_dataset *ds, const SearchPlan &p, int path, epi_resu
     int32_t *cb = reinterpret_cast<int32_t *>(base + o_cb);
     uint64_t *ic = reinterpret_cast<uint64_t *>(base + o_ic);
     if (p.tc) {
-        st = ensure_b8(ds);
+        st = ensure_b8(ds, p.comb_p);
         if (st != EPI_OK) return st;
     }
     // threshold word and status word live in the first 512 bytes
@@ -393,10 +399,11 @@ epi_status queue_search(epi_dataset *ds, const SearchPlan &p, int path, epi_resu
             waits = ctx->waits_dev;
             ctx->waits_grid = p.grid;
         }
-        CK(launch_tc_search(d, p.k, ds->b8, ic, p.pool, thr, ls, lr, lc, status, p.grid, p.total, p.rb, p.re,
-                            ctx->stream, &cand_p2, tc_cg ? reinterpret_cast<float *>(base + o_tcs) : nullptr,
+        CK(launch_tc_search(d, p.k, p.comb_p ? ds->b8c : ds->b8, ic, p.pool, thr, ls, lr, lc, status, p.grid,
+                            p.total, p.rb, p.re, ctx->stream, &cand_p2,
+                            tc_cg ? reinterpret_cast<float *>(base + o_tcs) : nullptr,
                             tc_cg ? reinterpret_cast<uint64_t *>(base + o_tcr) : nullptr, dump, waits,
-                            ctx->wait_limit_ns));
+                            ctx->wait_limit_ns, p.comb_p));
         ctx->launches += 1;   // item table
     } else {
         CK(launch_popc_search(d, p.k, p.R, p.rb, p.re, p.tile, p.pool, p.slots, p.cand_p2, thr, ls, lr, lc, p.grid,
@@ -1399,6 +1406,7 @@ void epi_dataset_destroy(epi_dataset *ds)
         cudaFree(ds->masks);
         cudaFree(ds->binom);
         if (ds->b8) cudaFree(ds->b8);
+        if (ds->b8c) cudaFree(ds->b8c);
         for (float *t : ds->lower)
             if (t) cudaFree(t);
     }
@@ -1620,9 +1628,18 @@ epi_status epi_inject_alloc_failure(epi_ctx *ctx, int64_t after)
     return EPI_OK;
 }
 
-epi_status epi_tc_rate(epi_ctx *ctx, int64_t stages, double *out)
+epi_status epi_set_tc_variant(epi_ctx *ctx, int variant)
+{
+    if (!ctx) return fail(EPI_EINVAL, "context is NULL");
+    if (variant != EPI_TC_AUTO && variant != EPI_TC_SEPARATE) return fail(EPI_EINVAL, "variant %d unknown", variant);
+    ctx->tc_combined = variant == EPI_TC_AUTO;
+    return EPI_OK;
+}
+
+epi_status epi_tc_rate(epi_ctx *ctx, int shape, int64_t stages, double *out)
 {
     if (!ctx || !out) return fail(EPI_EINVAL, "NULL argument");
+    if (shape != 0 && shape != 1) return fail(EPI_EINVAL, "shape %d unknown", shape);
     if (stages < 32 || stages > ((int64_t)1 << 32)) return fail(EPI_EINVAL, "stages outside 32..2^32");
     DeviceGuard g(ctx->device);
     if (!g.ok) return fail(EPI_ECUDA, "cannot select device %d", ctx->device);
@@ -1639,9 +1656,9 @@ epi_status epi_tc_rate(epi_ctx *ctx, int64_t stages, double *out)
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, 4, ctx->stream);
     // a short warm-up launch, then the timed one
-    if (e == cudaSuccess) e = launch_mma_rate(32, cycles, status, grid, ctx->stream);
+    if (e == cudaSuccess) e = launch_mma_rate(shape, 32, cycles, status, grid, ctx->stream);
     if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
-    if (e == cudaSuccess) e = launch_mma_rate(stages, cycles, status, grid, ctx->stream);
+    if (e == cudaSuccess) e = launch_mma_rate(shape, stages, cycles, status, grid, ctx->stream);
     if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(cyc.data(), cycles, (size_t)grid * 8, cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, status, 4, cudaMemcpyDeviceToHost, ctx->stream);
@@ -1654,7 +1671,7 @@ epi_status epi_tc_rate(epi_ctx *ctx, int64_t stages, double *out)
     if (e != cudaSuccess) return fail(EPI_ECUDA, "%s", cudaGetErrorString(e));
     if (hs & ST_TIMEOUT) return fail(EPI_ETIMEOUT, "device wait expired");
     ctx->launches += 2;
-    const double macs_per_sm = (double)stages * 4.0 * 128.0 * 128.0 * 32.0;
+    const double macs_per_sm = (double)stages * 4.0 * 128.0 * (shape ? 256.0 : 128.0) * 32.0;
     double mean_cyc = 0.0;
     for (unsigned long long c : cyc) mean_cyc += (double)c;
     mean_cyc /= (double)grid;

@@ -55,31 +55,39 @@ cudaError_t launch_popc_batch(const void *ds_dev, const int32_t *cta_ds_dev, int
 
 // epi_tc.cu
 size_t tc_b8_bytes(const DevData &d);
-cudaError_t launch_build_b8(const DevData &d, unsigned char *b8, int num_sms, cudaStream_t st);
-// work items of the whole search, or of the prefixes with first SNP in [a, b]
+// comb_p: 0 = E4M3 operand of the separate-class variant, else the E5M2
+// operand of the combined-class variant with class shift comb_p
+cudaError_t launch_build_b8(const DevData &d, unsigned char *b8, int num_sms, cudaStream_t st, int comb_p);
+// class shift of the combined-class variant for an order-k search, 0 where
+// the separate-class variant runs
+int tc_comb_shift(const DevData &d, int k);
+// work items of the whole search (separate-class tiles), or of the prefixes
+// with first SNP in [a, b] for N tiles of kj last SNPs
 uint64_t tc_item_count(int64_t n, int k);
-uint64_t tc_item_count(int64_t n, int k, int64_t a, int64_t b);
+uint64_t tc_item_count(int64_t n, int k, int64_t a, int64_t b, int kj);
 // first SNP of the combination of lexicographic rank r
 int64_t tc_first_snp(int64_t n, int k, uint64_t r);
 // combinations the tensor path counts to search the rank range [rb, re)
 uint64_t tc_range_work(int64_t n, int k, uint64_t rb, uint64_t re);
 // entries of a CTA's candidate buffer for a pool; shared memory of one CTA
 // with that buffer in shared memory or (cand_global) in a global buffer
-int tc_cand_p2(int k, int pool);
-size_t tc_smem_bytes(int cand_p2, int k, bool cand_global);
+int tc_cand_p2(int k, int pool, bool comb = false);
+size_t tc_smem_bytes(int cand_p2, int k, bool cand_global, bool comb = false);
 // item_cum: device [2][n + 1] (item and prefix tables); ranks [rb, re);
-// cand_g / rank_g: NULL, or [grid][tc_cand_p2] global candidate buffers
+// cand_g / rank_g: NULL, or [grid][tc_cand_p2] global candidate buffers;
+// comb_p: 0 = separate-class variant (b8 built with comb_p 0), else the
+// combined-class variant (b8 built with the same comb_p)
 cudaError_t launch_tc_search(const DevData &d, int k, const unsigned char *b8, uint64_t *item_cum, int pool,
                              uint32_t *global_thr, float *list_score, uint64_t *list_rank, int32_t *list_count,
                              int32_t *status, int grid, uint64_t total, uint64_t rb, uint64_t re, cudaStream_t st,
                              int *cand_p2_out, float *cand_g, uint64_t *rank_g, uint32_t *dump = nullptr,
-                             unsigned long long *waits = nullptr, unsigned long long wait_ns = 0);
+                             unsigned long long *waits = nullptr, unsigned long long wait_ns = 0, int comb_p = 0);
 constexpr int kTcWaitSlots = 8;
 // batched tensor-core launches: per-dataset descriptors and B-operand maps
 // (128-byte CUtensorMap, 64-byte aligned) live in device memory
 size_t tc_ds_bytes();
 cudaError_t launch_tc_item_cum(const DevData &d, int k, uint64_t rb, uint64_t re, uint64_t *item_cum,
-                               cudaStream_t st);
+                               cudaStream_t st, bool comb = false);
 cudaError_t tc_fill_batch_entry(void *ds_host, void *tmap_host, const DevData &d, int k, const unsigned char *b8,
                                 uint64_t *item_cum, uint32_t *global_thr, uint64_t total, const void *tmap_dev,
                                 int cta_begin, int cta_count);
@@ -89,8 +97,9 @@ cudaError_t launch_tc_batch(const void *ds_dev, const int32_t *cta_ds_dev, int k
 
 // epi_peak.cu: tensor-pipe rate of the counting MMA (one CTA per SM,
 // `stages` groups of four M128 N128 K32 FP8 MMAs; per-CTA cycles)
-size_t mma_rate_smem_bytes();
-cudaError_t launch_mma_rate(int64_t stages, unsigned long long *cycles, int32_t *status, int grid, cudaStream_t st);
+size_t mma_rate_smem_bytes(int shape);
+cudaError_t launch_mma_rate(int shape, int64_t stages, unsigned long long *cycles, int32_t *status, int grid,
+                            cudaStream_t st);
 
 // epi_variants.cu: every table of order k (2..4) counted with the POPC
 // instruction (variant 0), a byte lookup table (1) or binary MMA (2)

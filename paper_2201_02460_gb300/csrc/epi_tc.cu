@@ -66,34 +66,56 @@ namespace epi {
 
 namespace tc {
 
-constexpr int kJ = 64;                 // last SNPs per N tile
-constexpr int kN = 2 * kJ;             // accumulator columns per class
 constexpr int kKC = 128;               // individuals (bytes) per K stage
-constexpr int kStagesA = 6;            // generated prefix-row stages
-constexpr int kStagesB = 6;            // TMA stages of single-SNP rows
+
+// Tile shapes of the two variants.
+//   separate classes (C = false): N tile = 64 last SNPs (128 columns), E4M3
+//     operands, one accumulator per class (2 x 128 columns, double buffered),
+//     6 stages of A and B tiles;
+//   combined classes (C = true): N tile = 128 last SNPs (256 columns), E5M2
+//     operands whose case products are 2^p times the control products, so
+//     one accumulator holds ctrl + case * 2^p (exact while below 2^23);
+//     double buffered in 2 x 256 columns; 4 stages of A (128 rows) and B
+//     (256 rows) tiles.  The MMA of an N tile that ends the last SNPs is cut
+//     to the columns in use (a multiple of 16).
+template <bool C>
+struct Shape {
+    static constexpr int J = C ? 128 : 64;          // last SNPs per N tile
+    static constexpr int N = 2 * J;                 // tile columns
+    static constexpr int Stages = C ? 4 : 6;        // K stages in the rings
+    static constexpr int BBytes = N * kKC;          // one B stage
+    // warp roles: the combined variant's producers write each A row once
+    // per 512-cycle stage, so one group of 4 warps keeps up and 12 warps
+    // (3 per TMEM lane quadrant) run the epilogue; the separate variant has
+    // 2 producer groups taking alternate stages and 8 epilogue warps
+    static constexpr int EpiWarps = C ? 12 : 8;
+    static constexpr int ProdWarps = C ? 4 : 8;
+    static constexpr int EpiThreads = 32 * EpiWarps;
+    static constexpr int ProdGroups = ProdWarps / 4;  // one thread per tile row each
+    static constexpr int ColGroups = EpiWarps / 4;    // epilogue warps per lane quadrant
+};
 // Stages are released to the producers in groups: a tcgen05.commit lets the
 // following MMAs start only after the earlier ones finish (about one MMA
 // latency of idle tensor pipe), so the issuer commits once per group of
 // kRelease stages instead of once per stage.
 // measured best: groups of 2 stages at orders 2-3 (the epilogue bounds the
 // issuer), single stages at orders 4-5 (the A producers do)
-template <int K>
+template <int K, bool C>
 constexpr int release_group()
 {
 #ifdef EPI_TC_RELEASE
     return EPI_TC_RELEASE;
 #else
-    return K <= 3 ? 2 : 1;
+    return C ? 1 : (K <= 3 ? 2 : 1);
 #endif
 }
 constexpr int kDescDepth = 4;
-constexpr int kEpiWarps = 8;           // two per TMEM lane quadrant
-constexpr int kProdWarps = 8;          // two threads per tile row
-constexpr int kThreads = 32 * (kEpiWarps + kProdWarps + 2);
-constexpr int kEpiThreads = 32 * kEpiWarps;
-constexpr int kTileBytes = 128 * kKC;        // one A or B tile
+constexpr int kThreads = 32 * (16 + 2);   // 16 epilogue and producer warps, TMA, MMA
+static_assert(Shape<false>::EpiWarps + Shape<false>::ProdWarps == 16 &&
+                  Shape<true>::EpiWarps + Shape<true>::ProdWarps == 16,
+              "both variants launch 18 warps");
+constexpr int kTileBytes = 128 * kKC;        // one A tile (and a B tile of the separate-class variant)
 constexpr int kWaitSlots = 8;
-constexpr uint32_t kTxBytes = 128 * kKC;     // B tile bytes per stage
 constexpr int kMaxDescSnps = 40;
 constexpr unsigned long long kTimeoutNs = 2000000000ull;
 
@@ -114,6 +136,7 @@ struct DsParams {
     uint64_t rank_begin, rank_end;   // lexicographic ranks searched
     int32_t s1_lo, s1_hi;      // first SNPs of ranks rank_begin and rank_end - 1
     int32_t clip;              // 0: the whole combination range
+    int32_t comb_p;            // combined-class variant: control counts in the low comb_p bits
     int chunks, chunks_case;   // K stages in total / over the cases
     float delta;               // screening margin (nats)
     float tconst;              // T(m) - T(m1) - T(m0), T(c) = c log2 c
@@ -189,8 +212,13 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
-// kind::f8f6f4, E4M3 x E4M3 -> F32, K-major A and B, M = 128, N = 128
-constexpr uint32_t kIdesc = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(kN >> 3) << 17) | ((128u >> 4) << 24);
+// Instruction descriptor of kind::f8f6f4 with F32 accumulation, K-major A
+// and B, M = 128 and n columns; operand format 0 = E4M3, 1 = E5M2 (both).
+__host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt, uint32_t n)
+{
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24);
+}
+constexpr uint32_t kIdesc = make_idesc(0, 128);
 
 __device__ __forceinline__ void mma_f8(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate)
 {
@@ -203,12 +231,12 @@ __device__ __forceinline__ void mma_f8(uint32_t d_tmem, uint64_t a, uint64_t b, 
 // The same MMA executed by a whole warp in step; only the elected lane
 // (`leader` nonzero) issues it.
 __device__ __forceinline__ void mma_f8_warp(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate,
-                                            uint32_t leader)
+                                            uint32_t leader, uint32_t idesc = kIdesc)
 {
     asm volatile(
         "{\n .reg .pred p, e;\n setp.ne.b32 p, %4, 0;\n setp.ne.b32 e, %5, 0;\n"
         " @e tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate), "r"(leader));
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate), "r"(leader));
 }
 
 __device__ __forceinline__ void mma_commit_warp(uint64_t *bar, uint32_t leader)
@@ -227,7 +255,8 @@ __device__ __forceinline__ uint32_t elect_one()
     return pred;
 }
 
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory"); }
+template <int NT>
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory"); }
 
 // ------------------------------------------------------------ enumeration --
 // Prefixes of order k are the (k-1)-subsets whose last SNP c is <= n-2, in
@@ -307,11 +336,26 @@ __device__ inline void prefix_next(const DsParams &P, int k, PrefixIter &it)
     for (int t = 0; t < m2; t++) it.a[t] = P.s1_lo + t;
 }
 
-__device__ __forceinline__ int64_t ntiles_of(const DevData &d, int32_t c) { return (d.n - 1 - c + kJ - 1) / kJ; }
+template <int J>
+__device__ __forceinline__ int64_t ntiles_of(const DevData &d, int32_t c) { return (d.n - 1 - c + J - 1) / J; }
 
 // -------------------------------------------------------------- epilogue --
 // accumulator = count * 2^-5 (exact): the count as a float, and as an integer
 __device__ __forceinline__ uint32_t f2u_exact(float v) { return __float_as_uint(v + 8388608.0f) & 0x7FFFFFu; }
+
+// Combined-class accumulator x = 2^-12 (ctrl + case 2^p), an integer v
+// below 2^23 times 2^-12: fma(x, 2^12, 2^23) holds v in its 23 mantissa bits
+// (exact), and each class count c becomes the float c / 32 of the separate-
+// class variant by OR-ing its bits under the exponent of 2^23 and removing
+// 2^23 again, scaled by 1/32 in the same fused multiply-add.
+__device__ __forceinline__ void split_classes(uint32_t x, int p, uint32_t &case32, uint32_t &ctrl32)
+{
+    const uint32_t v = __float_as_uint(fmaf(__uint_as_float(x), 4096.0f, 8388608.0f));
+    const uint32_t lo = (v & ((1u << p) - 1u)) | 0x4B000000u;
+    const uint32_t hi = ((v & 0x7FFFFFu) >> p) | 0x4B000000u;
+    ctrl32 = __float_as_uint(fmaf(__uint_as_float(lo), 0.03125f, -262144.0f));
+    case32 = __float_as_uint(fmaf(__uint_as_float(hi), 0.03125f, -262144.0f));
+}
 
 // t(x) = x log2 x of an accumulator value x = count / 32 (0 for x = 0)
 __device__ __forceinline__ float tlog32(float x) { return x * __log2f(fmaxf(x, 0.03125f)); }
@@ -350,11 +394,12 @@ __device__ __forceinline__ float seg_sum(float v, int pos)
     return v;
 }
 
+template <int NT>
 __device__ inline void sort_cands_epi(float *sc, uint64_t *rk, int p2, int tid)
 {
     for (int kk = 2; kk <= p2; kk <<= 1) {
         for (int jj = kk >> 1; jj > 0; jj >>= 1) {
-            for (int i = tid; i < p2; i += kEpiThreads) {
+            for (int i = tid; i < p2; i += NT) {
                 const int ixj = i ^ jj;
                 if (ixj > i) {
                     const bool up = (i & kk) == 0;
@@ -366,7 +411,7 @@ __device__ inline void sort_cands_epi(float *sc, uint64_t *rk, int p2, int tid)
                     }
                 }
             }
-            epi_bar();
+            epi_bar<NT>();
         }
     }
 }
@@ -376,14 +421,15 @@ struct EpiState {
     float thr;
 };
 
+template <int NT>
 __device__ inline void epi_flush(EpiState &S, float *sc, uint64_t *rk, int pool, uint32_t *global_thr, int tid)
 {
-    epi_bar();
+    epi_bar<NT>();
     const int live = S.list_len + S.nbuf;
     const int p2 = next_pow2(live < 2 ? 2 : live);
-    for (int i = live + tid; i < p2; i += kEpiThreads) { sc[i] = -1.0f; rk[i] = ~0ull; }
-    epi_bar();
-    sort_cands_epi(sc, rk, p2, tid);
+    for (int i = live + tid; i < p2; i += NT) { sc[i] = -1.0f; rk[i] = ~0ull; }
+    epi_bar<NT>();
+    sort_cands_epi<NT>(sc, rk, p2, tid);
     if (tid == 0) {
         S.list_len = live < pool ? live : pool;
         S.nbuf = 0;
@@ -392,7 +438,7 @@ __device__ inline void epi_flush(EpiState &S, float *sc, uint64_t *rk, int pool,
             atomicMax(global_thr, __float_as_uint(S.thr));
         }
     }
-    epi_bar();
+    epi_bar<NT>();
 }
 
 // ---------------------------------------------------------------- kernel --
@@ -412,10 +458,21 @@ __device__ __noinline__ float row_terms_precise(uint32_t a0, uint32_t b0, uint32
                    "=r"(r[15])                                                                                   \
                  : "r"(taddr))
 
-template <int K>
+template <int K, bool C>
 __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_constant__ CUtensorMap tmap_b,
                                                                 const Params P)
 {
+    static_assert(!C || K == 3, "the combined-class variant serves order 3");
+    using S = Shape<C>;
+    constexpr int kStages = S::Stages;
+    constexpr int kJ = S::J;
+    constexpr int kBBytes = S::BBytes;
+    constexpr int kEpiWarps = S::EpiWarps, kProdWarps = S::ProdWarps, kEpiThreads = S::EpiThreads;
+    constexpr int kGroups = S::ProdGroups, kCG = S::ColGroups;
+    // epilogue: the kQC chunks of 8 last SNPs of a lane quadrant go round-
+    // robin to its kCG warps, kIters chunks each (the last may be empty)
+    constexpr int kQC = kJ / 8;
+    constexpr int kIters = (kQC + kCG - 1) / kCG;
     constexpr int kPR = K == 2 ? 3 : (K == 3 ? 9 : (K == 4 ? 27 : 81));
     // order 5: one prefix per tile, its 81 rows over lane quadrants 0-2 (the
     // epilogue sums a combination across warps through shared memory)
@@ -428,7 +485,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
     // candidate-buffer checks (a barrier and maybe a sort) every kJcPerCheck
     // groups of 8 last SNPs; the buffer holds two intervals' worth
     constexpr int kJcPerCheck = K == 2 ? 1 : 2;
-    constexpr int kRelease = release_group<K>();
+    static_assert(kIters % kJcPerCheck == 0, "every item ends on a candidate-buffer check");
+    constexpr int kRelease = release_group<K, C>();
     // orders 3-4: prefix sums through the shared transpose buffer
     constexpr bool kTranspose = K == 3 || K == 4;
     constexpr int kPairs = kWide ? 0 : kPPW * 8;              // (prefix, last SNP) pairs per warp and chunk
@@ -437,16 +495,16 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
     unsigned char *stages_a = smem;
-    unsigned char *stages_b = smem + kStagesA * kTileBytes;
+    unsigned char *stages_b = smem + kStages * kTileBytes;
     float *sc;
     uint64_t *rk;
     uint32_t *tot;                                                   // [2][128][2 halves][2 classes]
     if (P.cand_score_g) {
         sc = P.cand_score_g + (size_t)blockIdx.x * P.cand_p2;
         rk = P.cand_rank_g + (size_t)blockIdx.x * P.cand_p2;
-        tot = reinterpret_cast<uint32_t *>(stages_b + kStagesB * kTileBytes);
+        tot = reinterpret_cast<uint32_t *>(stages_b + kStages * kBBytes);
     } else {
-        sc = reinterpret_cast<float *>(stages_b + kStagesB * kTileBytes);
+        sc = reinterpret_cast<float *>(stages_b + kStages * kBBytes);
         rk = reinterpret_cast<uint64_t *>(sc + P.cand_p2);
         tot = reinterpret_cast<uint32_t *>(rk + P.cand_p2);
     }
@@ -458,15 +516,17 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
 
     // one "stage free" barrier per stage for both operands (the A and B rings
     // advance together), released by one MMA commit
-    static_assert(kStagesA == kStagesB, "the A and B rings share their release barriers");
-    static_assert(kStagesA % kRelease == 0, "release groups tile the ring");
-    static_assert(kStagesA % 2 == 0, "the producer halves take the ring slots of one parity each");
+    static_assert(kStages % kRelease == 0, "release groups tile the ring");
+    static_assert(kStages % 2 == 0, "the producer halves take the ring slots of one parity each");
     // full_ab[s]: the A producer warps of the slot's parity and the TMA
     // thread (with its bytes) have filled stage s of both operands
-    __shared__ __align__(8) uint64_t full_ab[kStagesA], empty_ab[kStagesA / kRelease];
+    __shared__ __align__(8) uint64_t full_ab[kStages], empty_ab[kStages / kRelease];
     __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], tot_full[2];
     __shared__ __align__(8) uint64_t desc_full[kDescDepth], desc_empty[kDescDepth], drain_bar;
     __shared__ uint32_t tmem_base_sh;
+    // combined variant: the MMA instruction descriptor of each item (its
+    // column count), written with the item's descriptor
+    __shared__ uint32_t item_idesc[kDescDepth];
     __shared__ volatile int abort_flag;
     __shared__ EpiState ES;
     // order 5: per-warp partial sums [jhalf][quadrant][last SNP of the chunk]
@@ -485,8 +545,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
     const int64_t n_my = (int64_t)(it_e - it_b);
 
     if (tid == 0) {
-        for (int s = 0; s < kStagesA; s++) {
-            mbar_init(&full_ab[s], kProdWarps / 2 + 1);   // one half of the producers + the TMA thread
+        for (int s = 0; s < kStages; s++) {
+            mbar_init(&full_ab[s], kProdWarps / kGroups + 1);   // one producer group + the TMA thread
             if (s % kRelease == 0) mbar_init(&empty_ab[s / kRelease], 1);
         }
         for (int b = 0; b < 2; b++) {
@@ -527,7 +587,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
             }
             const int32_t c0 = (int32_t)lo;
             const uint64_t off = w0 - DS.item_cum[c0];
-            const int64_t nt0 = ntiles_of(d, c0);
+            const int64_t nt0 = ntiles_of<kJ>(d, c0);
             const uint64_t tfirst = (DS.pcum[c0] + kPPT - 1) / kPPT;
             const uint64_t t = tfirst + off / (uint64_t)nt0;
             int64_t u = (int64_t)(off % (uint64_t)nt0);
@@ -561,26 +621,32 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                 D.nvalid = nvalid;
 #pragma unroll
                 for (int q = 0; q < kPPT * km1; q++) D.snp[q] = tile_snp[q];
+                if constexpr (C) {
+                    // columns in use: 2 per last SNP below n, in steps of 16
+                    const int32_t live = 2 * ((int32_t)d.n - D.j0);
+                    const uint32_t ncol = live >= S::N ? (uint32_t)S::N : (uint32_t)((live + 15) & ~15);
+                    item_idesc[dq] = make_idesc(1, ncol);
+                }
                 mbar_arrive(&desc_full[dq]);
                 const int y = 2 * D.j0;
                 for (int kc = 0; kc < DS.chunks; kc++, g++) {
-                    const int s = (int)(g % kStagesB);
-                    const uint32_t us = (uint32_t)(g / kStagesB);
+                    const int s = (int)(g % kStages);
+                    const uint32_t us = (uint32_t)(g / kStages);
                     if (!wait_fast(&empty_ab[s / kRelease], (us & 1) ^ 1, &abort_flag, w_tma)) break;
-                    mbar_arrive_tx(&full_ab[s], kTxBytes);
-                    tma_load_2d(stages_b + s * kTileBytes, tmap, kc * kKC, y, &full_ab[s]);
+                    mbar_arrive_tx(&full_ab[s], (uint32_t)kBBytes);
+                    tma_load_2d(stages_b + s * kBBytes, tmap, kc * kKC, y, &full_ab[s]);
                 }
                 u++;
-                if (u == ntiles_of(d, cmin)) {
+                if (u == ntiles_of<kJ>(d, cmin)) {
                     u = 0;
                     fill_tile();
                 }
             }
             if (P.waits) P.waits[blockIdx.x * kWaitSlots + 6] = (unsigned long long)w_tma;
-            for (int s = 0; s < kStagesB; s++) {
+            for (int s = 0; s < kStages; s++) {
                 if (g > (uint64_t)s) {
-                    const uint64_t last = ((g - 1 - s) / kStagesB) * kStagesB + s;
-                    const uint32_t us = (uint32_t)(last / kStagesB);
+                    const uint64_t last = ((g - 1 - s) / kStages) * kStages + s;
+                    const uint32_t us = (uint32_t)(last / kStages);
                     const uint64_t t0 = now_ns();
                     while (!mbar_try(&full_ab[s], us & 1) && now_ns() - t0 < kTimeoutNs) {}
                 }
@@ -596,7 +662,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
             // by one add and the ring position and phase are carried.
             const uint32_t leader = elect_one();
             const uint64_t ad0 = sdesc(smem_u32(stages_a)), bd0 = sdesc(smem_u32(stages_b));
-            constexpr uint32_t kStageDesc = kTileBytes >> 4;   // stage stride in descriptor address units
+            // stage strides in descriptor address units
+            constexpr uint32_t kStageDescA = kTileBytes >> 4, kStageDescB = kBBytes >> 4;
             int s = 0;
             uint32_t ph = 0;
             const int chunks = DS.chunks, chunks_case = DS.chunks_case;
@@ -607,19 +674,25 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                 const uint32_t ub = (uint32_t)(i >> 1);
                 if (!wait_fast(&acc_empty[b], (ub & 1) ^ 1, &abort_flag, w_acc)) break;
                 tc_fence_after();
-                const uint32_t d_case = tmem_base + (uint32_t)(b * 2 * kN), d_ctrl = d_case + (uint32_t)kN;
+                // separate classes: case and control accumulators of 128
+                // columns each; combined: one accumulator of 256 columns
+                const uint32_t d_case = tmem_base + (uint32_t)(b * 256), d_ctrl = d_case + (C ? 0u : 128u);
+                uint32_t idesc = kIdesc;
                 bool ok = true;
                 for (int kc = 0; kc < chunks; kc++) {
                     if (!wait_fast(&full_ab[s], ph, &abort_flag, w_a)) { ok = false; break; }
                     tc_fence_after();
+                    // the item's column count is in place once its first stage is full
+                    if (C && kc == 0) idesc = item_idesc[i % kDescDepth];
                     const uint32_t dcol = kc < chunks_case ? d_case : d_ctrl;
-                    const uint32_t acc0 = (kc == 0 || kc == chunks_case) ? 0u : 1u;
-                    const uint64_t ad = ad0 + (uint64_t)(s * kStageDesc), bd = bd0 + (uint64_t)(s * kStageDesc);
-                    mma_f8_warp(dcol, ad, bd, acc0, leader);
+                    const uint32_t acc0 = (kc == 0 || (!C && kc == chunks_case)) ? 0u : 1u;
+                    const uint64_t ad = ad0 + (uint64_t)(s * kStageDescA), bd = bd0 + (uint64_t)(s * kStageDescB);
+                    mma_f8_warp(dcol, ad, bd, acc0, leader, idesc);
 #pragma unroll
-                    for (int kk = 1; kk < kKC / 32; kk++) mma_f8_warp(dcol, ad + 2 * kk, bd + 2 * kk, 1u, leader);
+                    for (int kk = 1; kk < kKC / 32; kk++)
+                        mma_f8_warp(dcol, ad + 2 * kk, bd + 2 * kk, 1u, leader, idesc);
                     if (s % kRelease == kRelease - 1) mma_commit_warp(&empty_ab[s / kRelease], leader);
-                    if (++s == kStagesA) { s = 0; ph ^= 1; }
+                    if (++s == kStages) { s = 0; ph ^= 1; }
                 }
                 if (!ok) break;
                 mma_commit_warp(&acc_full[b], leader);
@@ -638,11 +711,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
         }
     } else if (warp >= kEpiWarps) {
         // ---------------------------------------------------- A producers
-        // Thread t owns tile row r = t % 128 in the ring slots of parity
-        // t / 128 (the two halves of the producers take alternate stages), and
-        // writes all 128 individuals of the row's stage: four mask words,
-        // each expanded to 32 bytes.
-        const int t = tid - kEpiThreads;     // 0 .. 255
+        // Thread t owns tile row r = t % 128 in the ring slots of group
+        // t / 128 (with two groups they take alternate stages), and writes
+        // all 128 individuals of the row's stage: four mask words, each
+        // expanded to 32 bytes.
+        const int t = tid - kEpiThreads;     // 0 .. 32 kProdWarps - 1
         const int r = t & 127;
         const int grp = t >> 7;
         const int l = r & 31, w = r >> 5;
@@ -675,8 +748,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
             uint32_t t1 = 0, t0 = 0;
             bool ok = true;
             const int chunks = DS.chunks, chunks_case = DS.chunks_case;
-            const int kc0 = (int)(((uint64_t)grp + 2 - (g & 1)) & 1);   // this half's first stage of the item
-            const int mine = (chunks - kc0 + 1) / 2;
+            // this group's first stage of the item and its number of stages
+            const int kc0 = (int)(((uint64_t)grp + kGroups - (g % kGroups)) % kGroups);
+            const int mine = (chunks - kc0 + kGroups - 1) / kGroups;
             // this row's words of the next kPf own stages (a register ring
             // indexed statically: the loop is unrolled by kPf)
             constexpr int kPf = EPI_TC_PREFETCH;
@@ -692,18 +766,18 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
             };
 #pragma unroll
             for (int u = 0; u < kPf; u++)
-                ring[u] = (active && u < mine) ? fetch(kc0 + 2 * u) : make_uint4(0, 0, 0, 0);
+                ring[u] = (active && u < mine) ? fetch(kc0 + kGroups * u) : make_uint4(0, 0, 0, 0);
             uint64_t gs = g + (uint64_t)kc0;                   // global stage of own stage m
-            int s = (int)(gs % kStagesA);
-            uint32_t ph = (uint32_t)((gs / kStagesA) & 1);
+            int s = (int)(gs % kStages);
+            uint32_t ph = (uint32_t)((gs / kStages) & 1);
             for (int mb = 0; mb < mine && ok; mb += kPf) {
 #pragma unroll
                 for (int u = 0; u < kPf; u++) {
                     const int m = mb + u;
                     if (m >= mine) break;
-                    const int kc = kc0 + 2 * m;
+                    const int kc = kc0 + kGroups * m;
                     const uint4 cur = ring[u];
-                    if (active && m + kPf < mine) ring[u] = fetch(kc + 2 * kPf);
+                    if (active && m + kPf < mine) ring[u] = fetch(kc + kGroups * kPf);
                     if (!wait_fast(&empty_ab[s / kRelease], ph ^ 1, &abort_flag, w_prod)) { ok = false; break; }
                     const uint32_t c4 = __popc(cur.x) + __popc(cur.y) + __popc(cur.z) + __popc(cur.w);
                     if (kc < chunks_case) t1 += c4;
@@ -723,9 +797,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                     fence_proxy_async();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&full_ab[s]);
-                    // next own stage: two global stages on
-                    s += 2;
-                    if (s >= kStagesA) { s -= kStagesA; ph ^= 1; }
+                    // next own stage: kGroups global stages on
+                    s += kGroups;
+                    if (s >= kStages) { s -= kStages; ph ^= 1; }
                 }
             }
             if (!ok) break;
@@ -745,7 +819,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
     } else {
         // -------------------------------------------------------- epilogue
         const int quad = warp & 3;           // TMEM lane quadrant
-        const int jhalf = warp >> 2;         // which 32 last SNPs of the tile
+        const int jhalf = warp >> 2;         // column group: chunks jhalf + kCG i of the quadrant
         const int r = quad * 32 + lane;      // tile row = TMEM lane
         const int l = lane;
         const int pos = kWide ? r : l % kPR;          // row of the prefix's table
@@ -818,32 +892,51 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                     }
                 }
             }
-            const uint32_t T1 = tot[((b * 128 + r) * 2 + 0) * 2 + 0] + tot[((b * 128 + r) * 2 + 1) * 2 + 0];
-            const uint32_t T0 = tot[((b * 128 + r) * 2 + 0) * 2 + 1] + tot[((b * 128 + r) * 2 + 1) * 2 + 1];
+            uint32_t T1 = 0, T0 = 0;
+#pragma unroll
+            for (int gq = 0; gq < kGroups; gq++) {
+                T1 += tot[((b * 128 + r) * 2 + gq) * 2 + 0];
+                T0 += tot[((b * 128 + r) * 2 + gq) * 2 + 1];
+            }
             // row totals in accumulator units (count / 32, exact)
             const float fT1 = u2f_exact(T1) * 0.03125f, fT0 = u2f_exact(T0) * 0.03125f;
-            const int32_t j0 = D.j0 + 32 * jhalf;
             if (tid == 0) {
                 const float gthr = __uint_as_float(*(volatile uint32_t *)DS.global_thr);
                 if (ES.list_len == P.pool || gthr > 0.0f) ES.thr = fmaxf(ES.thr, gthr);
             }
-            epi_bar();
+            epi_bar<kEpiThreads>();
             float thr = ES.thr, cut = thr - DS.delta;
             int list_len = ES.list_len;
 #pragma unroll 1
-            for (int jc = 0; jc < 4; jc++) {
+            for (int jc = 0; jc < kIters; jc++) {
                 uint32_t cs[16], cn[16];
-                if (ok) {
-                    const uint32_t ta = tmem_base + ((uint32_t)(quad * 32) << 16) +
-                                        (uint32_t)(b * 2 * kN + 64 * jhalf + 16 * jc);
-                    TMEM_LD16(ta, cs);
-                    TMEM_LD16(ta + kN, cn);
-                    tmem_wait_ld();
+                // this warp's chunk of the quadrant: last SNPs j0 .. j0 + 7
+                const int jcg = jhalf + kCG * jc;
+                const int32_t jb = D.j0 + 8 * jcg;   // the chunk's last SNPs are jb .. jb + 7
+                // a chunk past the quadrant's last one, or (orders 3-4) whose
+                // first last SNP is past the end (the last N tile of a panel),
+                // holds no combination, and its warp skips it (warp-uniform)
+                const bool live = ok && jcg < kQC && (!kTranspose || jb < (int32_t)d.n);
+                if (live) {
+                    // columns 2 (j - D.j0) + g of accumulator b; separate
+                    // classes: the control accumulator 128 columns on
+                    const uint32_t ta = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * 256 + 16 * jcg);
+                    if constexpr (C) {
+                        uint32_t cc[16];
+                        TMEM_LD16(ta, cc);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int q = 0; q < 16; q++) split_classes(cc[q], DS.comb_p, cs[q], cn[q]);
+                    } else {
+                        TMEM_LD16(ta, cs);
+                        TMEM_LD16(ta + 128, cn);
+                        tmem_wait_ld();
+                    }
                 } else {
 #pragma unroll
                     for (int q = 0; q < 16; q++) { cs[q] = 0; cn[q] = 0; }
                 }
-                if (jc == 3) {
+                if (jc == kIters - 1) {
                     // every accumulator value is in registers: hand the
                     // buffer back to the MMA issuer before the last scoring
                     tc_fence_before();
@@ -856,7 +949,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                     float vs[8];
 #pragma unroll
                     for (int jj = 0; jj < 8; jj++) {
-                        const int32_t j = j0 + 8 * jc + jj;
+                        const int32_t j = jb + jj;
                         const float fa0 = __uint_as_float(cs[2 * jj]), fa1 = __uint_as_float(cs[2 * jj + 1]);
                         const float fb0 = __uint_as_float(cn[2 * jj]), fb1 = __uint_as_float(cn[2 * jj + 1]);
                         const float fa2 = fT1 - fa0 - fa1, fb2 = fT0 - fb0 - fb1;
@@ -885,15 +978,15 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
 #pragma unroll
                         for (int jj = 0; jj < 8; jj++) wred[jhalf][quad][jj] = vs[jj];
                     }
-                    epi_bar();
+                    epi_bar<kEpiThreads>();
                     if (quad == 0 && lane < 8) {
                         const float tv = wred[jhalf][0][lane] + wred[jhalf][1][lane] + wred[jhalf][2][lane] +
                                          wred[jhalf][3][lane];
-                        const int32_t j = j0 + 8 * jc + lane;
+                        const int32_t j = jb + lane;
                         const bool valid = prow && j >= jlo && j < jhi;
                         wflag[jhalf][lane] = (valid && fmaf(tv, vscale, voff) >= cut) ? 1 : 0;
                     }
-                    epi_bar();
+                    epi_bar<kEpiThreads>();
                     int anyf = 0;
 #pragma unroll
                     for (int q = 0; q < 16; q++) anyf |= wflag[q >> 3][q & 7];
@@ -914,13 +1007,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                             e = warp_sum(e);
                             if (lane == 0) wpre[jhalf][quad][jj] = e;
                         }
-                        epi_bar();
+                        epi_bar<kEpiThreads>();
                         if (quad == 0 && lane < 8 && wflag[jhalf][lane]) {
                             const float e = wpre[jhalf][0][lane] + wpre[jhalf][1][lane] + wpre[jhalf][2][lane] +
                                             wpre[jhalf][3][lane];
                             const float score = __fdiv_rn(e, mc.fm);
                             if (score >= thr) {
-                                const int32_t j = j0 + 8 * jc + lane;
+                                const int32_t j = jb + lane;
                                 uint64_t rk_sum = 0;
 #pragma unroll
                                 for (int tt = 0; tt < km1; tt++)
@@ -931,14 +1024,15 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                                 rk[slot] = DS.total - 1 - rk_sum;
                             }
                         }
-                        epi_bar();
+                        epi_bar<kEpiThreads>();
                     }
                 } else if constexpr (kTranspose) {
+                  if (live) {
                     // row terms of the chunk's 8 last SNPs, straight-line
                     float vrow[8];
 #pragma unroll
                     for (int jj = 0; jj < 8; jj++) {
-                        const int32_t j = j0 + 8 * jc + jj;
+                        const int32_t j = jb + jj;
                         // accumulator values x = count / 32 (exact); with
                         // t(x) = x log2 x, T(32 x) = 32 t(x) + 160 x and the
                         // linear parts cancel within a cell, so the screen
@@ -979,7 +1073,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                             float v = 0.0f;
 #pragma unroll
                             for (int rr = 0; rr < kPR; rr++) v += wb[(pp * kPR + rr) * 8 + jj];
-                            const int32_t j = j0 + 8 * jc + jj;
+                            const int32_t j = jb + jj;
                             cand = j >= plo[q] && j < phi[q] && fmaf(v, vscale, voff) >= cut;
                         }
                         cmask[q] = __ballot_sync(0xffffffffu, cand);
@@ -1010,7 +1104,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                             if (lane_real && pl == pp && pos == 0) {
                                 const float score = __fdiv_rn(e, mc.fm);
                                 if (score >= thr) {
-                                    const int32_t j = j0 + 8 * jc + jsel;
+                                    const int32_t j = jb + jsel;
                                     uint64_t rk_sum = 0;
 #pragma unroll
                                     for (int tt = 0; tt < km1; tt++)
@@ -1023,10 +1117,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                             }
                         }
                     }
+                  }
                 } else {
 #pragma unroll
                 for (int jj = 0; jj < 8; jj++) {
-                    const int32_t j = j0 + 8 * jc + jj;
+                    const int32_t j = jb + jj;
                     // accumulator values x = count / 32 (exact); with
                     // t(x) = x log2 x, T(32 x) = 32 t(x) + 160 x and the
                     // linear parts cancel within a cell, so the screen sums
@@ -1084,12 +1179,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                 }
                 }
                 if (jc % kJcPerCheck == kJcPerCheck - 1) {
-                    epi_bar();
-                    // the next check interval adds at most kJcPerCheck * 16
-                    // candidates per prefix of the tile: sort and trim first
-                    // if the buffer could not hold them
-                    if (ES.list_len + ES.nbuf + kJcPerCheck * 16 * kPPT > P.cand_p2)
-                        epi_flush(ES, sc, rk, P.pool, DS.global_thr, tid);
+                    epi_bar<kEpiThreads>();
+                    // the next check interval adds at most kJcPerCheck chunks
+                    // of 8 last SNPs per column group and prefix of the tile:
+                    // sort and trim first if the buffer could not hold them
+                    if (ES.list_len + ES.nbuf + kJcPerCheck * 8 * kCG * kPPT > P.cand_p2)
+                        epi_flush<kEpiThreads>(ES, sc, rk, P.pool, DS.global_thr, tid);
                     thr = ES.thr;
                     cut = thr - DS.delta;
                     list_len = ES.list_len;
@@ -1097,13 +1192,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&desc_empty[dq]);
-            epi_bar();
+            epi_bar<kEpiThreads>();
             if (tid == 0) ES.stop = abort_flag;
-            epi_bar();
+            epi_bar<kEpiThreads>();
             if (ES.stop) break;
         }
-        epi_bar();
-        if (ES.nbuf > 0) epi_flush(ES, sc, rk, P.pool, DS.global_thr, tid);
+        epi_bar<kEpiThreads>();
+        if (ES.nbuf > 0) epi_flush<kEpiThreads>(ES, sc, rk, P.pool, DS.global_thr, tid);
         const int L = ES.list_len;
         for (int q = tid; q < L; q += kEpiThreads) {
             P.list_score[(size_t)blockIdx.x * P.pool + q] = sc[q];
@@ -1149,7 +1244,7 @@ __device__ void block_exclusive_scan(uint64_t *part, uint64_t s, uint64_t &befor
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(1024) item_cum_kernel(DevData d, int k, int ppt, int32_t a, int32_t b,
+__global__ void __launch_bounds__(1024) item_cum_kernel(DevData d, int k, int ppt, int kj, int32_t a, int32_t b,
                                                         uint64_t *pcum, uint64_t *cum)
 {
     __shared__ uint64_t part[1024];
@@ -1169,7 +1264,7 @@ __global__ void __launch_bounds__(1024) item_cum_kernel(DevData d, int k, int pp
         if (c < k - 2 || c > n - 2) return 0;
         const uint64_t t0 = (pcum[c] + ppt - 1) / ppt;
         const uint64_t t1 = (pcum[c + 1] + ppt - 1) / ppt;
-        return (t1 - t0) * (uint64_t)((n - 1 - c + kJ - 1) / kJ);
+        return (t1 - t0) * (uint64_t)((n - 1 - c + kj - 1) / kj);
     };
     s = 0;
     for (int64_t c = cb; c < ce; c++) s += items(c);
@@ -1183,10 +1278,16 @@ __global__ void __launch_bounds__(1024) item_cum_kernel(DevData d, int k, int pp
 
 // B operand: row 2j+g (g = 0, 1) of SNP j, K byte 32 w + 4 i + b = individual
 // 32 w + 8 b + i (the A producer's order); where the genotype is g the byte
-// is 2^-5 divided by A's weight at that position, else 0.
-__global__ void build_b8_kernel(DevData d, unsigned char *__restrict__ b8)
+// is a power of two, else 0.  The producer's A bytes by position i are 0x10,
+// 0x20, 0x40, 0x08 (twice), and B's are 0x38, 0x28, 0x08, 0x40:
+//   read as E4M3, A = 2^-5, 2^-3, 2^1, 2^-6 and B = 2^0, 2^-2, 2^-6, 2^1, so
+//   every product of two ones is 2^-5 (separate-class variant, case_shift 0);
+//   read as E5M2, A = 2^-11, 2^-7, 2^1, 2^-13 and B = 2^-1, 2^-5, 2^-13,
+//   2^1, so every product is 2^-12; the case words (w < W1) add p to B's
+//   exponent field (case_shift = 4 p, p <= 14 keeps it finite), making their
+//   products 2^(p-12) (combined-class variant).
+__global__ void build_b8_kernel(DevData d, unsigned char *__restrict__ b8, uint32_t case_shift)
 {
-    // E4M3 bytes of B by bit position i: 1.0, 2^-2, 2^-6, 2^1 (A: 2^-5, 2^-3, 2^1, 2^-6)
     const uint32_t bval[8] = {0x38u, 0x28u, 0x08u, 0x40u, 0x38u, 0x28u, 0x08u, 0x40u};
     const int64_t Kt = (int64_t)d.Wt * 32;
     const int64_t per_row = Kt / 16;
@@ -1199,9 +1300,10 @@ __global__ void build_b8_kernel(DevData d, unsigned char *__restrict__ b8)
         const int g = (int)(row & 1);
         const uint32_t word = d.masks[(j * 3 + g) * d.Wt + (q >> 1)];
         const int i0 = (int)(q & 1) * 4;
+        const uint32_t add = (q >> 1) < d.W1 ? case_shift : 0u;
         uint32_t o[4];
 #pragma unroll
-        for (int t = 0; t < 4; t++) o[t] = ((word >> (i0 + t)) & 0x01010101u) * bval[i0 + t];
+        for (int t = 0; t < 4; t++) o[t] = ((word >> (i0 + t)) & 0x01010101u) * (bval[i0 + t] + add);
         reinterpret_cast<uint4 *>(b8)[idx] = make_uint4(o[0], o[1], o[2], o[3]);
     }
 }
@@ -1225,13 +1327,28 @@ static cudaError_t get_encode()
 
 size_t tc_b8_bytes(const DevData &d) { return (size_t)2 * d.n * d.Wt * 32; }
 
-cudaError_t launch_build_b8(const DevData &d, unsigned char *b8, int num_sms, cudaStream_t st)
+cudaError_t launch_build_b8(const DevData &d, unsigned char *b8, int num_sms, cudaStream_t st, int comb_p)
 {
     const int64_t total = 2 * d.n * (int64_t)d.Wt * 2;
     int64_t blocks = (total + 255) / 256;
     if (blocks > (int64_t)num_sms * 16) blocks = (int64_t)num_sms * 16;
-    tc::build_b8_kernel<<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, st>>>(d, b8);
+    tc::build_b8_kernel<<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, st>>>(d, b8, 4u * (uint32_t)comb_p);
     return cudaGetLastError();
+}
+
+// Class shift p of the combined-class variant for an order-k search of d, or
+// 0 where it does not apply: order 3 (at order 4 its single producer group
+// bounds it, measured slower than separate classes); the control count must
+// fit below 2^p and the accumulator value ctrl + case 2^p below 2^23 (the
+// decode's exact range; FP32 accumulation of such integers is exact).
+int tc_comb_shift(const DevData &d, int k)
+{
+    if (k != 3) return 0;
+    int p = 1;
+    while (p < 15 && (1ll << p) <= d.m0) p++;
+    if (p > 14) return 0;
+    if (d.m1 * (1ll << p) + d.m0 >= (1ll << 23)) return 0;
+    return p;
 }
 
 static int tc_pr(int k) { return k == 2 ? 3 : (k == 3 ? 9 : (k == 4 ? 27 : 81)); }
@@ -1245,7 +1362,7 @@ static uint64_t host_subsets_from(int64_t c, int64_t x, int m)
     return c - x >= m ? host_binom(c - x, m) : 0;
 }
 
-uint64_t tc_item_count(int64_t n, int k, int64_t a, int64_t b)
+uint64_t tc_item_count(int64_t n, int k, int64_t a, int64_t b, int kj)
 {
     const uint64_t ppt = (uint64_t)tc_ppt(k);
     uint64_t total = 0, pc = 0;
@@ -1256,12 +1373,12 @@ uint64_t tc_item_count(int64_t n, int k, int64_t a, int64_t b)
         const uint64_t t0 = (pc + ppt - 1) / ppt;
         pc += cnt;
         const uint64_t t1 = (pc + ppt - 1) / ppt;
-        total += (t1 - t0) * (uint64_t)((n - 1 - c + tc::kJ - 1) / tc::kJ);
+        total += (t1 - t0) * (uint64_t)((n - 1 - c + kj - 1) / kj);
     }
     return total;
 }
 
-uint64_t tc_item_count(int64_t n, int k) { return tc_item_count(n, k, 0, n - k); }
+uint64_t tc_item_count(int64_t n, int k) { return tc_item_count(n, k, 0, n - k, tc::Shape<false>::J); }
 
 // First SNP of the combination of lexicographic rank r: the largest s with
 // C(n, k) - C(n - s, k) <= r (the combinations starting below s come first).
@@ -1296,27 +1413,31 @@ int tc_prefixes_per_warp(int k)
 // Candidate buffer entries: the pool plus one check interval (2 chunks of 8
 // last SNPs, both halves, every prefix of the tile; order 2 checks every
 // chunk), rounded up to a power of two for the bitonic sort.
-int tc_cand_p2(int k, int pool)
+int tc_cand_p2(int k, int pool, bool comb)
 {
-    return next_pow2(pool + (k == 2 ? 1 : 2) * 16 * tc_ppt(k));
+    const int groups = comb ? tc::Shape<true>::ColGroups : tc::Shape<false>::ColGroups;
+    return next_pow2(pool + (k == 2 ? 1 : 2) * 8 * groups * tc_ppt(k));
 }
 
-size_t tc_smem_bytes(int cand_p2, int k, bool cand_global)
+size_t tc_smem_bytes(int cand_p2, int k, bool cand_global, bool comb)
 {
-    const size_t transpose = (k == 3 || k == 4) ? (size_t)tc::kEpiWarps * 256 * 4 + 16 : 0;
-    return 1024 + (size_t)(tc::kStagesA + tc::kStagesB) * tc::kTileBytes + (cand_global ? 0 : (size_t)cand_p2 * 12) +
-           2 * 128 * 4 * 4 + tc::kDescDepth * sizeof(tc::Desc) + 64 + transpose;
+    const size_t transpose =
+        (k == 3 || k == 4) ? (size_t)(comb ? tc::Shape<true>::EpiWarps : tc::Shape<false>::EpiWarps) * 256 * 4 + 16 : 0;
+    const size_t rings = comb ? (size_t)tc::Shape<true>::Stages * (tc::kTileBytes + tc::Shape<true>::BBytes)
+                              : (size_t)tc::Shape<false>::Stages * (tc::kTileBytes + tc::Shape<false>::BBytes);
+    return 1024 + rings + (cand_global ? 0 : (size_t)cand_p2 * 12) + 2 * 128 * 4 * 4 +
+           tc::kDescDepth * sizeof(tc::Desc) + 64 + transpose;
 }
 
 
-static cudaError_t encode_map(CUtensorMap *map, const DevData &d, const unsigned char *b8)
+static cudaError_t encode_map(CUtensorMap *map, const DevData &d, const unsigned char *b8, bool comb)
 {
     cudaError_t e = get_encode();
     if (e != cudaSuccess) return e;
     const int64_t Kt = (int64_t)d.Wt * 32;
     cuuint64_t gdim[2] = {(cuuint64_t)Kt, (cuuint64_t)(2 * d.n)};
     cuuint64_t gstride[1] = {(cuuint64_t)Kt};
-    cuuint32_t box[2] = {(cuuint32_t)tc::kKC, 128u};
+    cuuint32_t box[2] = {(cuuint32_t)tc::kKC, comb ? (cuuint32_t)tc::Shape<true>::N : (cuuint32_t)tc::Shape<false>::N};
     cuuint32_t estr[2] = {1u, 1u};
     CUresult cr = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<unsigned char *>(b8), gdim, gstride, box,
                            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -1328,9 +1449,10 @@ static cudaError_t encode_map(CUtensorMap *map, const DevData &d, const unsigned
 // the launch is batched (nullptr: passed as a kernel parameter instead).
 static void fill_ds(tc::DsParams &D, const DevData &d, int k, uint64_t *item_cum, uint32_t *global_thr,
                     uint64_t total, uint64_t rb, uint64_t re, const CUtensorMap *tmap_dev, int cta_begin,
-                    int cta_count)
+                    int cta_count, int comb_p)
 {
     D.d = d;
+    D.comb_p = comb_p;
     D.rank_begin = rb;
     D.rank_end = re;
     D.s1_lo = (int32_t)tc_first_snp(d.n, k, rb);
@@ -1343,7 +1465,7 @@ static void fill_ds(tc::DsParams &D, const DevData &d, int k, uint64_t *item_cum
         else np += host_subsets_from(c, D.s1_lo, k - 2) - host_subsets_from(c, D.s1_hi + 1, k - 2);
     }
     D.n_prefix = np;
-    D.n_items = tc_item_count(d.n, k, D.s1_lo, D.s1_hi);
+    D.n_items = tc_item_count(d.n, k, D.s1_lo, D.s1_hi, comb_p ? tc::Shape<true>::J : tc::Shape<false>::J);
     D.item_cum = item_cum;
     D.pcum = item_cum + d.n + 1;
     const int64_t Kt = (int64_t)d.Wt * 32;
@@ -1370,14 +1492,14 @@ static void fill_ds(tc::DsParams &D, const DevData &d, int k, uint64_t *item_cum
 
 static void fill_launch(tc::Params &P, int k, int pool, float *list_score, uint64_t *list_rank, int32_t *list_count,
                         int32_t *status, uint32_t *dump, unsigned long long *waits, float *cand_g,
-                        uint64_t *rank_g)
+                        uint64_t *rank_g, bool comb)
 {
     P.k = k;
     P.PR = tc_pr(k);
     P.ppw = P.PR > 32 ? 0 : 32 / P.PR;
     P.ppt = tc_ppt(k);
     P.pool = pool;
-    P.cand_p2 = tc_cand_p2(k, pool);
+    P.cand_p2 = tc_cand_p2(k, pool, comb);
     P.cand_score_g = cand_g;
     P.cand_rank_g = rank_g;
     P.wait_ns = 0;
@@ -1389,13 +1511,14 @@ static void fill_launch(tc::Params &P, int k, int pool, float *list_score, uint6
     P.waits = waits;
 }
 
-static cudaError_t launch_kernel(const CUtensorMap &map, const tc::Params &P, int k, int grid, cudaStream_t st)
+static cudaError_t launch_kernel(const CUtensorMap &map, const tc::Params &P, int k, int grid, cudaStream_t st,
+                                 bool comb)
 {
-    const size_t smem = tc_smem_bytes(P.cand_p2, k, P.cand_score_g != nullptr);
-    auto kern = k == 2   ? tc::tc_search_kernel<2>
-                : k == 3 ? tc::tc_search_kernel<3>
-                : k == 4 ? tc::tc_search_kernel<4>
-                         : tc::tc_search_kernel<5>;
+    const size_t smem = tc_smem_bytes(P.cand_p2, k, P.cand_score_g != nullptr, comb);
+    auto kern = k == 2   ? tc::tc_search_kernel<2, false>
+                : k == 3 ? (comb ? tc::tc_search_kernel<3, true> : tc::tc_search_kernel<3, false>)
+                : k == 4 ? tc::tc_search_kernel<4, false>
+                         : tc::tc_search_kernel<5, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, tc::kThreads, smem, st>>>(map, P);
@@ -1403,10 +1526,11 @@ static cudaError_t launch_kernel(const CUtensorMap &map, const tc::Params &P, in
 }
 
 cudaError_t launch_tc_item_cum(const DevData &d, int k, uint64_t rb, uint64_t re, uint64_t *item_cum,
-                               cudaStream_t st)
+                               cudaStream_t st, bool comb)
 {
     const int32_t a = (int32_t)tc_first_snp(d.n, k, rb), b = (int32_t)tc_first_snp(d.n, k, re - 1);
-    tc::item_cum_kernel<<<1, 1024, 0, st>>>(d, k, tc_ppt(k), a, b, item_cum + d.n + 1, item_cum);
+    const int kj = comb ? tc::Shape<true>::J : tc::Shape<false>::J;
+    tc::item_cum_kernel<<<1, 1024, 0, st>>>(d, k, tc_ppt(k), kj, a, b, item_cum + d.n + 1, item_cum);
     return cudaGetLastError();
 }
 
@@ -1414,21 +1538,21 @@ cudaError_t launch_tc_search(const DevData &d, int k, const unsigned char *b8, u
                              uint32_t *global_thr, float *list_score, uint64_t *list_rank, int32_t *list_count,
                              int32_t *status, int grid, uint64_t total, uint64_t rb, uint64_t re, cudaStream_t st,
                              int *cand_p2_out, float *cand_g, uint64_t *rank_g, uint32_t *dump,
-                             unsigned long long *waits, unsigned long long wait_ns)
+                             unsigned long long *waits, unsigned long long wait_ns, int comb_p)
 {
     tc::Params P;
-    fill_ds(P.one, d, k, item_cum, global_thr, total, rb, re, nullptr, 0, grid);
+    fill_ds(P.one, d, k, item_cum, global_thr, total, rb, re, nullptr, 0, grid, comb_p);
     P.many = nullptr;
     P.cta_ds = nullptr;
-    fill_launch(P, k, pool, list_score, list_rank, list_count, status, dump, waits, cand_g, rank_g);
+    fill_launch(P, k, pool, list_score, list_rank, list_count, status, dump, waits, cand_g, rank_g, comb_p != 0);
     P.wait_ns = wait_ns;
     *cand_p2_out = P.cand_p2;
-    cudaError_t e = launch_tc_item_cum(d, k, rb, re, item_cum, st);
+    cudaError_t e = launch_tc_item_cum(d, k, rb, re, item_cum, st, comb_p != 0);
     if (e != cudaSuccess) return e;
     CUtensorMap map;
-    e = encode_map(&map, d, b8);
+    e = encode_map(&map, d, b8, comb_p != 0);
     if (e != cudaSuccess) return e;
-    return launch_kernel(map, P, k, grid, st);
+    return launch_kernel(map, P, k, grid, st, comb_p != 0);
 }
 
 size_t tc_ds_bytes() { return sizeof(tc::DsParams); }
@@ -1438,8 +1562,8 @@ cudaError_t tc_fill_batch_entry(void *ds_host, void *tmap_host, const DevData &d
                                 int cta_begin, int cta_count)
 {
     fill_ds(*static_cast<tc::DsParams *>(ds_host), d, k, item_cum, global_thr, total, 0, total,
-            static_cast<const CUtensorMap *>(tmap_dev), cta_begin, cta_count);
-    return encode_map(static_cast<CUtensorMap *>(tmap_host), d, b8);
+            static_cast<const CUtensorMap *>(tmap_dev), cta_begin, cta_count, 0);
+    return encode_map(static_cast<CUtensorMap *>(tmap_host), d, b8, false);
 }
 
 cudaError_t launch_tc_batch(const void *ds_dev, const int32_t *cta_ds_dev, int k, int pool, float *list_score,
@@ -1450,10 +1574,10 @@ cudaError_t launch_tc_batch(const void *ds_dev, const int32_t *cta_ds_dev, int k
     P.one = tc::DsParams();
     P.many = static_cast<const tc::DsParams *>(ds_dev);
     P.cta_ds = cta_ds_dev;
-    fill_launch(P, k, pool, list_score, list_rank, list_count, status, nullptr, nullptr, cand_g, rank_g);
+    fill_launch(P, k, pool, list_score, list_rank, list_count, status, nullptr, nullptr, cand_g, rank_g, false);
     CUtensorMap unused;
     memset(&unused, 0, sizeof(unused));
-    return launch_kernel(unused, P, k, grid, st);
+    return launch_kernel(unused, P, k, grid, st, false);
 }
 
 }  // namespace epi

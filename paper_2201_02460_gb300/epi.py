@@ -22,6 +22,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "epi.h")
 
 EPI_OK, EPI_EINVAL, EPI_ENOMEM, EPI_ECUDA, EPI_EUNSUPPORTED, EPI_ETIMEOUT, EPI_EOVERFLOW = range(7)
 PATHS = {"auto": 0, "popc": 1, "tc": 2}
+TC_VARIANTS = {"auto": 0, "separate": 1}
 MAX_ORDER = 8
 
 RESULT_DTYPE = np.dtype([("snp", "<u4", (MAX_ORDER,)), ("mi", "<f8"), ("mi_f32", "<f4"),
@@ -179,13 +180,15 @@ def load(path: str | None = None):
         lib.epi_profile_waits.restype = i32
         lib.epi_profile_waits.argtypes = [V, P]
         lib.epi_tc_rate.restype = i32
-        lib.epi_tc_rate.argtypes = [V, i64, P]
+        lib.epi_tc_rate.argtypes = [V, i32, i64, P]
         lib.epi_count_variant.restype = i32
         lib.epi_count_variant.argtypes = [V, i32, i32, P, P, P]
         lib.epi_set_wait_limit.restype = i32
         lib.epi_set_wait_limit.argtypes = [V, u64]
         lib.epi_inject_alloc_failure.restype = i32
         lib.epi_inject_alloc_failure.argtypes = [V, i64]
+        lib.epi_set_tc_variant.restype = i32
+        lib.epi_set_tc_variant.argtypes = [V, i32]
         if path is None:
             _lib = lib
         return lib
@@ -259,11 +262,17 @@ class Context:
         (negative: cancel)."""
         _check(load().epi_inject_alloc_failure(self._h, int(after)))
 
-    def tc_rate(self, stages: int = 1 << 19) -> dict:
-        """Rate of the tensor pipe for the counting path's MMA (FP8 M128 N128
-        K32), measured with one CTA per SM issuing it back to back."""
+    def set_tc_variant(self, variant: str):
+        """Tensor-core counting variant: "auto" (combined classes where they
+        fit) or "separate"."""
+        _check(load().epi_set_tc_variant(self._h, TC_VARIANTS[variant]))
+
+    def tc_rate(self, stages: int = 1 << 19, shape: int = 0) -> dict:
+        """Rate of the tensor pipe for a counting-path MMA (shape 0: E4M3
+        M128 N128 K32; shape 1: E5M2 M128 N256 K32), measured with one CTA
+        per SM issuing it back to back."""
         out = np.zeros(4, dtype=np.float64)
-        _check(load().epi_tc_rate(self._h, int(stages), _np_ptr(out)))
+        _check(load().epi_tc_rate(self._h, int(shape), int(stages), _np_ptr(out)))
         return dict(tflops=float(out[0]), mac_per_clk_sm=float(out[1]), ms=float(out[2]), sm_mhz=float(out[3]))
 
     def close(self):

@@ -31,6 +31,28 @@ def ctx(epi):
     return epi.Context(0)
 
 
+@pytest.fixture(params=["auto", "separate"])
+def tc_variant(request, ctx):
+    """Runs a tensor-path test with the combined-class variant where it
+    applies ("auto") and with separate class accumulators; restores auto."""
+    ctx.set_tc_variant(request.param)
+    yield request.param
+    ctx.set_tc_variant("auto")
+
+
+def comb_shift(m1, m0, k):
+    """The combined-class variant's class shift (0: not applicable), the
+    rule the library documents for EPI_TC_AUTO."""
+    if k != 3:
+        return 0
+    p = 1
+    while p < 15 and (1 << p) <= m0:
+        p += 1
+    if p > 14 or m1 * (1 << p) + m0 >= (1 << 23):
+        return 0
+    return p
+
+
 def _search_both(epi, ctx, geno, pheno, k, top_n, path="popc", rank_range=None):
     ds = epi.Dataset(ctx, geno, pheno)
     r = epi.search(ds, k, top_n, path=path, rank_range=rank_range)
@@ -165,7 +187,7 @@ def test_batched_high_orders(epi, ctx):
 
 
 @pytest.mark.parametrize("path,k,world", [("popc", 3, 3), ("tc", 3, 3), ("tc", 4, 5), ("tc", 2, 4)])
-def test_sharded_ranges_merge_to_the_full_search(epi, ctx, path, k, world):
+def test_sharded_ranges_merge_to_the_full_search(epi, ctx, path, k, world, tc_variant):
     """The sharding hook on the GPU: every range search of a rank split
     against the oracle's search of the same range, and the ranges' records,
     merged by (MI desc, rank asc), against the oracle's whole top-N."""
@@ -205,7 +227,7 @@ def test_search_single_or_nearly_single_class(epi, ctx, m1):
 
 @pytest.mark.parametrize("path", ["popc", "tc"])
 @pytest.mark.parametrize("k", [2, 3, 4, 5])
-def test_search_range(epi, ctx, k, path):
+def test_search_range(epi, ctx, k, path, tc_variant):
     n = {2: 300, 3: 80, 4: 40, 5: 24}[k]
     geno, pheno = random_data(n, 513, seed=11 + k)
     total = O.binom(n, k)
@@ -315,12 +337,20 @@ def test_score_tables_fp32_accuracy(epi, ctx):
 # tensor-core counting path
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("k,n,m", [(2, 50, 300), (3, 24, 700), (3, 40, 129), (4, 14, 1000), (4, 12, 257),
-                                   (3, 70, 2000), (2, 150, 64), (5, 12, 700), (5, 16, 129), (5, 30, 1000)])
-def test_tc_counts_bit_exact(epi, ctx, k, n, m):
+@pytest.mark.parametrize("k,n,m,m1", [(2, 50, 300, None), (3, 24, 700, None), (3, 40, 129, None),
+                                      (4, 14, 1000, None), (4, 12, 257, None), (3, 70, 2000, None),
+                                      (2, 150, 64, None), (5, 12, 700, None), (5, 16, 129, None), (5, 30, 1000, None),
+                                      (3, 100, 4000, None), (3, 150, 700, None), (3, 20, 6000, 1000), (3, 18, 6000, 1020),
+                                      (3, 16, 6000, 1100)])
+def test_tc_counts_bit_exact(epi, ctx, k, n, m, m1, tc_variant):
     """Every combination's table from the tensor-core kernel equals the
-    popcount table kernel's and the oracle's, bit for bit."""
-    geno, pheno = random_data(n, m, seed=300 * k + n + m)
+    popcount table kernel's and the oracle's, bit for bit.  Two order-3
+    cases sit at the combined-class variant's limit: m1 2^13 + m0 just below
+    2^23 (1000 cases over 5000 controls) and just above it (1100 cases: the
+    separate-class variant runs)."""
+    geno, pheno = random_data(n, m, seed=300 * k + n + m, m1=m1)
+    if m1 is not None and tc_variant == "auto" and k == 3:
+        assert (comb_shift(m1, m - m1, k) != 0) == (m1 <= 1020)
     ds = epi.Dataset(ctx, geno, pheno)
     got = epi.debug_counts(ds, k)
     combs = np.array(brute.all_combinations(n, k), dtype=np.uint32)
@@ -333,13 +363,13 @@ def test_tc_counts_bit_exact(epi, ctx, k, n, m):
 @pytest.mark.parametrize("k,n,m,top_n", [(2, 60, 257, 25), (3, 30, 700, 50), (3, 90, 1500, 100),
                                          (4, 22, 1100, 40), (4, 30, 513, 64), (5, 18, 900, 40),
                                          (5, 26, 400, 100)])
-def test_tc_search_small(epi, ctx, k, n, m, top_n):
+def test_tc_search_small(epi, ctx, k, n, m, top_n, tc_variant):
     geno, pheno = random_data(n, m, seed=11 * k + n)
     ds, r, oc, om, _ = _search_both(epi, ctx, geno, pheno, k, top_n, path="tc")
     _check_result(r, geno, pheno, oc, om)
 
 
-def test_tc_matches_popc(epi, ctx):
+def test_tc_matches_popc(epi, ctx, tc_variant):
     geno, pheno = random_data(120, 2000, seed=77)
     geno[50] = geno[7]
     ds = epi.Dataset(ctx, geno, pheno)
@@ -508,11 +538,14 @@ def test_tc_rate_probe(epi, ctx):
     reports, and the count per clock lies below the nominal dense FP8 bound
     (4.5 PFLOP/s at about 1.9 GHz over 152 SMs: under 8 Ki multiply-adds per
     SM clock, with 20 % headroom for clock reporting)."""
-    r = ctx.tc_rate(1 << 14)
-    assert r["ms"] > 0 and r["tflops"] > 0
-    assert 0 < r["mac_per_clk_sm"] <= 1.2 * 8192
-    implied = r["tflops"] * 1e12 / (2 * r["mac_per_clk_sm"] * 152) / 1e6
-    assert 0.8 * r["sm_mhz"] <= implied <= 1.25 * r["sm_mhz"]
+    for shape in (0, 1):
+        r = ctx.tc_rate(1 << 14, shape=shape)
+        assert r["ms"] > 0 and r["tflops"] > 0
+        assert 0 < r["mac_per_clk_sm"] <= 1.2 * 8192
+        implied = r["tflops"] * 1e12 / (2 * r["mac_per_clk_sm"] * 152) / 1e6
+        assert 0.8 * r["sm_mhz"] <= implied <= 1.25 * r["sm_mhz"]
+    with pytest.raises(epi.EpiError):
+        ctx.tc_rate(1 << 14, shape=2)
 
 
 @pytest.mark.parametrize("k,n,m,m1", [(2, 40, 300, 140), (3, 20, 777, 400), (4, 13, 1000, 313), (3, 18, 4100, 2049),
@@ -536,7 +569,7 @@ def test_count_variants_bit_exact(epi, ctx, k, n, m, m1):
 
 
 @pytest.mark.parametrize("k,n", [(3, 60), (4, 26)])
-def test_tc_large_top_n(epi, ctx, k, n):
+def test_tc_large_top_n(epi, ctx, k, n, tc_variant):
     """top_n = 1024: the candidate pool (1088) no longer fits beside the
     operand rings, so the tensor kernel keeps its candidate lists in global
     memory; the result is still the oracle's."""
