@@ -93,6 +93,12 @@ struct Shape {
     static constexpr int EpiThreads = 32 * EpiWarps;
     static constexpr int ProdGroups = ProdWarps / 4;  // one thread per tile row each
     static constexpr int ColGroups = EpiWarps / 4;    // epilogue warps per lane quadrant
+    // chunks of 8 last SNPs per epilogue warp and item, and the chunks
+    // between two candidate-buffer checks (a barrier of the epilogue warps
+    // and maybe a sort): every 2 chunks with separate classes, once per item
+    // with combined classes (its larger buffer then lives in global memory)
+    static constexpr int Iters = (J / 8 + ColGroups - 1) / ColGroups;
+    static constexpr int CheckIters = C ? Iters : 2;
 };
 // Stages are released to the producers in groups: a tcgen05.commit lets the
 // following MMAs start only after the earlier ones finish (about one MMA
@@ -344,36 +350,40 @@ __device__ __forceinline__ int64_t ntiles_of(const DevData &d, int32_t c) { retu
 __device__ __forceinline__ uint32_t f2u_exact(float v) { return __float_as_uint(v + 8388608.0f) & 0x7FFFFFu; }
 
 // Combined-class accumulator x = 2^-12 (ctrl + case 2^p), an integer v
-// below 2^23 times 2^-12: fma(x, 2^12, 2^23) holds v in its 23 mantissa bits
-// (exact), and each class count c becomes the float c / 32 of the separate-
-// class variant by OR-ing its bits under the exponent of 2^23 and removing
-// 2^23 again, scaled by 1/32 in the same fused multiply-add.
-__device__ __forceinline__ void split_classes(uint32_t x, int p, uint32_t &case32, uint32_t &ctrl32)
+// below 2^23 times 2^-12: y = fma(x, 2^12, 2^23) = 2^23 + v holds v in its
+// 23 mantissa bits (exact).  Keeping the low p bits under the exponent of
+// 2^23 gives 2^23 + ctrl, hence ctrl / 32 in one fused multiply-add, and
+// y - (2^23 + ctrl) = case 2^p exactly, hence case / 32 in one multiply by
+// case_scale = 2^-(p+5).  Both come out as the separate-class variant's
+// accumulator values (count / 32).
+__device__ __forceinline__ void split_classes(uint32_t x, uint32_t lo_mask, float case_scale, uint32_t &case32,
+                                              uint32_t &ctrl32)
 {
-    const uint32_t v = __float_as_uint(fmaf(__uint_as_float(x), 4096.0f, 8388608.0f));
-    const uint32_t lo = (v & ((1u << p) - 1u)) | 0x4B000000u;
-    const uint32_t hi = ((v & 0x7FFFFFu) >> p) | 0x4B000000u;
-    ctrl32 = __float_as_uint(fmaf(__uint_as_float(lo), 0.03125f, -262144.0f));
-    case32 = __float_as_uint(fmaf(__uint_as_float(hi), 0.03125f, -262144.0f));
+    const float y = fmaf(__uint_as_float(x), 4096.0f, 8388608.0f);
+    const float lo = __uint_as_float((__float_as_uint(y) & lo_mask) | 0x4B000000u);
+    ctrl32 = __float_as_uint(fmaf(lo, 0.03125f, -262144.0f));
+    case32 = __float_as_uint((y - lo) * case_scale);
 }
 
 // t(x) = x log2 x of an accumulator value x = count / 32 (0 for x = 0)
 __device__ __forceinline__ float tlog32(float x) { return x * __log2f(fmaxf(x, 0.03125f)); }
 
-// sum over the three cells of one tile row of t(a) + t(b) - t(a + b), as
-// one chain of fused multiply-adds (a, b: case and control accumulators)
+// sum over the three cells of one tile row of t(a) + t(b) - t(a + b) (a, b:
+// case and control accumulators): one fused multiply-add chain per cell,
+// the three cells side by side, then two adds
 __device__ __forceinline__ float row_screen(float a0, float a1, float a2, float b0, float b1, float b2)
 {
     const float s0 = a0 + b0, s1 = a1 + b1, s2 = a2 + b2;
-    float v = a0 * __log2f(fmaxf(a0, 0.03125f));
-    v = fmaf(b0, __log2f(fmaxf(b0, 0.03125f)), v);
-    v = fmaf(-s0, __log2f(fmaxf(s0, 0.03125f)), v);
-    v = fmaf(a1, __log2f(fmaxf(a1, 0.03125f)), v);
-    v = fmaf(b1, __log2f(fmaxf(b1, 0.03125f)), v);
-    v = fmaf(-s1, __log2f(fmaxf(s1, 0.03125f)), v);
-    v = fmaf(a2, __log2f(fmaxf(a2, 0.03125f)), v);
-    v = fmaf(b2, __log2f(fmaxf(b2, 0.03125f)), v);
-    return fmaf(-s2, __log2f(fmaxf(s2, 0.03125f)), v);
+    float v0 = a0 * __log2f(fmaxf(a0, 0.03125f));
+    float v1 = a1 * __log2f(fmaxf(a1, 0.03125f));
+    float v2 = a2 * __log2f(fmaxf(a2, 0.03125f));
+    v0 = fmaf(b0, __log2f(fmaxf(b0, 0.03125f)), v0);
+    v1 = fmaf(b1, __log2f(fmaxf(b1, 0.03125f)), v1);
+    v2 = fmaf(b2, __log2f(fmaxf(b2, 0.03125f)), v2);
+    v0 = fmaf(-s0, __log2f(fmaxf(s0, 0.03125f)), v0);
+    v1 = fmaf(-s1, __log2f(fmaxf(s1, 0.03125f)), v1);
+    v2 = fmaf(-s2, __log2f(fmaxf(s2, 0.03125f)), v2);
+    return (v0 + v1) + v2;
 }
 
 __device__ __forceinline__ float warp_sum(float v)
@@ -472,7 +482,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
     // epilogue: the kQC chunks of 8 last SNPs of a lane quadrant go round-
     // robin to its kCG warps, kIters chunks each (the last may be empty)
     constexpr int kQC = kJ / 8;
-    constexpr int kIters = (kQC + kCG - 1) / kCG;
+    constexpr int kIters = S::Iters;
     constexpr int kPR = K == 2 ? 3 : (K == 3 ? 9 : (K == 4 ? 27 : 81));
     // order 5: one prefix per tile, its 81 rows over lane quadrants 0-2 (the
     // epilogue sums a combination across warps through shared memory)
@@ -483,8 +493,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
     constexpr int kWarpTma = kEpiWarps + kProdWarps;
     constexpr int kWarpMma = kWarpTma + 1;
     // candidate-buffer checks (a barrier and maybe a sort) every kJcPerCheck
-    // groups of 8 last SNPs; the buffer holds two intervals' worth
-    constexpr int kJcPerCheck = K == 2 ? 1 : 2;
+    // chunks of 8 last SNPs; the buffer holds the pool and one interval
+    constexpr int kJcPerCheck = K == 2 ? 1 : S::CheckIters;
     static_assert(kIters % kJcPerCheck == 0, "every item ends on a candidate-buffer check");
     constexpr int kRelease = release_group<K, C>();
     // orders 3-4: prefix sums through the shared transpose buffer
@@ -827,6 +837,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
         const bool lane_real = kWide ? r < kPR : l < kPPW * kPR;
         const MiConstF32 mc = make_mi_const(d.m, d.m1, d.m0);
         const float vscale = 32.0f * DS.ln2_over_m, voff = DS.tconst * DS.ln2_over_m;
+        // combined classes: the decode's control-bit mask and 2^-(p+5)
+        const uint32_t lo_mask = (1u << (DS.comb_p & 31)) - 1u;
+        const float case_scale = __uint_as_float((uint32_t)(127 - 5 - DS.comb_p) << 23);
         long long w_epi = 0;
         for (int64_t i = 0; i < n_my; i++) {
             const int dq = (int)(i % kDescDepth);
@@ -926,7 +939,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                         TMEM_LD16(ta, cc);
                         tmem_wait_ld();
 #pragma unroll
-                        for (int q = 0; q < 16; q++) split_classes(cc[q], DS.comb_p, cs[q], cn[q]);
+                        for (int q = 0; q < 16; q++) split_classes(cc[q], lo_mask, case_scale, cs[q], cn[q]);
                     } else {
                         TMEM_LD16(ta, cs);
                         TMEM_LD16(ta + 128, cn);
@@ -1416,7 +1429,8 @@ int tc_prefixes_per_warp(int k)
 int tc_cand_p2(int k, int pool, bool comb)
 {
     const int groups = comb ? tc::Shape<true>::ColGroups : tc::Shape<false>::ColGroups;
-    return next_pow2(pool + (k == 2 ? 1 : 2) * 8 * groups * tc_ppt(k));
+    const int check = k == 2 ? 1 : (comb ? tc::Shape<true>::CheckIters : tc::Shape<false>::CheckIters);
+    return next_pow2(pool + check * 8 * groups * tc_ppt(k));
 }
 
 size_t tc_smem_bytes(int cand_p2, int k, bool cand_global, bool comb)
