@@ -1045,7 +1045,6 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                     float vrow[8];
 #pragma unroll
                     for (int jj = 0; jj < 8; jj++) {
-                        const int32_t j = jb + jj;
                         // accumulator values x = count / 32 (exact); with
                         // t(x) = x log2 x, T(32 x) = 32 t(x) + 160 x and the
                         // linear parts cancel within a cell, so the screen
@@ -1053,7 +1052,16 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                         const float fa0 = __uint_as_float(cs[2 * jj]), fa1 = __uint_as_float(cs[2 * jj + 1]);
                         const float fb0 = __uint_as_float(cn[2 * jj]), fb1 = __uint_as_float(cn[2 * jj + 1]);
                         const float fa2 = fT1 - fa0 - fa1, fb2 = fT0 - fb0 - fb1;
-                        if (P.dump && prow && j >= jlo && j < jhi) {
+                        vrow[jj] = prow ? row_screen(fa0, fa1, fa2, fb0, fb1, fb2) : 0.0f;
+                    }
+                    if (P.dump) {
+                        // validation: every table of the chunk, as counts
+#pragma unroll
+                        for (int jj = 0; jj < 8; jj++) {
+                            const int32_t j = jb + jj;
+                            if (!(prow && j >= jlo && j < jhi)) continue;
+                            const float fa0 = __uint_as_float(cs[2 * jj]), fa1 = __uint_as_float(cs[2 * jj + 1]);
+                            const float fb0 = __uint_as_float(cn[2 * jj]), fb1 = __uint_as_float(cn[2 * jj + 1]);
                             uint64_t rs = 0;
 #pragma unroll
                             for (int tt = 0; tt < km1; tt++) rs += binom_at(d.binom, d.n, d.n - 1 - psnp[tt], K - tt);
@@ -1061,12 +1069,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                             constexpr int cells = kPR * 3;
                             uint32_t *o = P.dump + (DS.total - 1 - rs) * 2 * cells;
                             o[pos * 3 + 0] = f2u_exact(32.0f * fa0); o[pos * 3 + 1] = f2u_exact(32.0f * fa1);
-                            o[pos * 3 + 2] = f2u_exact(32.0f * fa2);
+                            o[pos * 3 + 2] = f2u_exact(32.0f * (fT1 - fa0 - fa1));
                             o[cells + pos * 3 + 0] = f2u_exact(32.0f * fb0);
                             o[cells + pos * 3 + 1] = f2u_exact(32.0f * fb1);
-                            o[cells + pos * 3 + 2] = f2u_exact(32.0f * fb2);
+                            o[cells + pos * 3 + 2] = f2u_exact(32.0f * (fT0 - fb0 - fb1));
                         }
-                        vrow[jj] = prow ? row_screen(fa0, fa1, fa2, fb0, fb1, fb2) : 0.0f;
                     }
                     // transpose: lane l's 8 values at [l][0..7]; the lane of
                     // pair (prefix pp, last SNP jj) reads rows pp*kPR .. of
@@ -1083,9 +1090,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                         bool cand = false;
                         if (pair < kPairs) {
                             const int pp = pair >> 3, jj = pair & 7;
-                            float v = 0.0f;
+                            float v = 0.0f, w2 = 0.0f;
 #pragma unroll
-                            for (int rr = 0; rr < kPR; rr++) v += wb[(pp * kPR + rr) * 8 + jj];
+                            for (int rr = 0; rr < kPR; rr++) {
+                                if (rr & 1) w2 += wb[(pp * kPR + rr) * 8 + jj];
+                                else v += wb[(pp * kPR + rr) * 8 + jj];
+                            }
+                            v += w2;
                             const int32_t j = jb + jj;
                             cand = j >= plo[q] && j < phi[q] && fmaf(v, vscale, voff) >= cut;
                         }

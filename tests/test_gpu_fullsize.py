@@ -8,7 +8,8 @@
   a million samples (counts near 2^18, the largest the API's exactness
   argument covers) with nearly monomorphic SNPs, so that single cells hold
   almost a whole class.
-* The full-size order-3 and order-4 workloads, both counting paths, against
+* The full-size order-3 and order-4 workloads, both counting paths (at
+  order 3 both tensor-core variants), against
   the oracle's exhaustive top-N stored under tests/golden (written by
   tests/golden/make_fullsize.py, which calls only the oracle).
 """
@@ -92,7 +93,13 @@ def _golden_search(epi, ctx, name, paths):
     ds = epi.Dataset(ctx, d.geno, d.pheno)
     m = d.n_samples
     for path in paths:
-        r = epi.search(ds, k, top_n, path=path)
+        # "tc_separate": the tensor path with separate case and control
+        # accumulators (the combined-class variant is the default where it fits)
+        ctx.set_tc_variant("separate" if path == "tc_separate" else "auto")
+        try:
+            r = epi.search(ds, k, top_n, path="tc" if path == "tc_separate" else path)
+        finally:
+            ctx.set_tc_variant("auto")
         check_topn(r.combs, r.mi, want["combs"], want["mi"])
         # every returned table is the oracle's table of that combination, and
         # both scores are those of the table
@@ -108,7 +115,7 @@ def _golden_search(epi, ctx, name, paths):
 
 
 def test_fullsize_order3_2000snp_4000_both_paths(epi, ctx):
-    d = _golden_search(epi, ctx, "order3_2000snp_4000", ("tc", "popc"))
+    d = _golden_search(epi, ctx, "order3_2000snp_4000", ("tc", "tc_separate", "popc"))
     # the planted three-way parity (no marginal or pairwise effect) ranks first
     assert tuple(G.read("order3_2000snp_4000")["combs"][0]) == d.planted
 
