@@ -84,12 +84,25 @@ struct Shape {
     static constexpr int N = 2 * J;                 // tile columns
     static constexpr int Stages = C ? 4 : 6;        // K stages in the rings
     static constexpr int BBytes = N * kKC;          // one B stage
-    // warp roles: the combined variant's producers write each A row once
-    // per 512-cycle stage, so one group of 4 warps keeps up and 12 warps
-    // (3 per TMEM lane quadrant) run the epilogue; the separate variant has
-    // 2 producer groups taking alternate stages and 8 epilogue warps
-    static constexpr int EpiWarps = C ? 12 : 8;
-    static constexpr int ProdWarps = C ? 4 : 8;
+};
+
+// Epilogue warps of the separate-class variant at order 4 (tuning
+// parameter; the other 16 - n warps produce A tiles).  Measured: 8 (two
+// producer groups) 126.5 ms at 300 SNPs x 4000 and 1522 ms at 500 x 8192;
+// 4 (three producer groups) 190 and 1579 ms.
+#ifndef EPI_TC_K4_EPI_WARPS
+#define EPI_TC_K4_EPI_WARPS 8
+#endif
+
+// Warp roles of an order-K launch.  The combined variant's producers write
+// each A row once per 512-cycle stage, so one group of 4 warps keeps up and
+// 12 warps (3 per TMEM lane quadrant) run the epilogue; the separate variant
+// has producer groups of 4 warps taking the ring's stages in turn.
+template <bool C, int K>
+struct Roles {
+    static constexpr int J = Shape<C>::J;
+    static constexpr int EpiWarps = C ? 12 : (K == 4 ? EPI_TC_K4_EPI_WARPS : 8);
+    static constexpr int ProdWarps = 16 - EpiWarps;
     static constexpr int EpiThreads = 32 * EpiWarps;
     static constexpr int ProdGroups = ProdWarps / 4;  // one thread per tile row each
     static constexpr int ColGroups = EpiWarps / 4;    // epilogue warps per lane quadrant
@@ -99,7 +112,19 @@ struct Shape {
     // with combined classes (its larger buffer then lives in global memory)
     static constexpr int Iters = (J / 8 + ColGroups - 1) / ColGroups;
     static constexpr int CheckIters = C ? Iters : 2;
+    static_assert(EpiWarps % 4 == 0 && ProdWarps % 4 == 0, "roles come in whole lane quadrants");
 };
+constexpr int kMaxProdGroups = 3;
+
+// the host's view of the roles of a launch (order k, variant comb)
+inline int roles_epi_warps(bool comb, int k)
+{
+    return comb ? Roles<true, 3>::EpiWarps : (k == 4 ? Roles<false, 4>::EpiWarps : Roles<false, 3>::EpiWarps);
+}
+inline int roles_check_iters(bool comb, int k)
+{
+    return comb ? Roles<true, 3>::CheckIters : (k == 4 ? Roles<false, 4>::CheckIters : Roles<false, 3>::CheckIters);
+}
 // Stages are released to the producers in groups: a tcgen05.commit lets the
 // following MMAs start only after the earlier ones finish (about one MMA
 // latency of idle tensor pipe), so the issuer commits once per group of
@@ -117,9 +142,7 @@ constexpr int release_group()
 }
 constexpr int kDescDepth = 4;
 constexpr int kThreads = 32 * (16 + 2);   // 16 epilogue and producer warps, TMA, MMA
-static_assert(Shape<false>::EpiWarps + Shape<false>::ProdWarps == 16 &&
-                  Shape<true>::EpiWarps + Shape<true>::ProdWarps == 16,
-              "both variants launch 18 warps");
+static_assert(Roles<false, 4>::ProdWarps / 4 <= 3, "at most kMaxProdGroups producer groups");
 constexpr int kTileBytes = 128 * kKC;        // one A tile (and a B tile of the separate-class variant)
 constexpr int kWaitSlots = 8;
 constexpr int kMaxDescSnps = 40;
@@ -474,15 +497,16 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
 {
     static_assert(!C || K == 3, "the combined-class variant serves order 3");
     using S = Shape<C>;
+    using R = Roles<C, K>;
     constexpr int kStages = S::Stages;
     constexpr int kJ = S::J;
     constexpr int kBBytes = S::BBytes;
-    constexpr int kEpiWarps = S::EpiWarps, kProdWarps = S::ProdWarps, kEpiThreads = S::EpiThreads;
-    constexpr int kGroups = S::ProdGroups, kCG = S::ColGroups;
+    constexpr int kEpiWarps = R::EpiWarps, kProdWarps = R::ProdWarps, kEpiThreads = R::EpiThreads;
+    constexpr int kGroups = R::ProdGroups, kCG = R::ColGroups;
     // epilogue: the kQC chunks of 8 last SNPs of a lane quadrant go round-
     // robin to its kCG warps, kIters chunks each (the last may be empty)
     constexpr int kQC = kJ / 8;
-    constexpr int kIters = S::Iters;
+    constexpr int kIters = R::Iters;
     constexpr int kPR = K == 2 ? 3 : (K == 3 ? 9 : (K == 4 ? 27 : 81));
     // order 5: one prefix per tile, its 81 rows over lane quadrants 0-2 (the
     // epilogue sums a combination across warps through shared memory)
@@ -494,7 +518,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
     constexpr int kWarpMma = kWarpTma + 1;
     // candidate-buffer checks (a barrier and maybe a sort) every kJcPerCheck
     // chunks of 8 last SNPs; the buffer holds the pool and one interval
-    constexpr int kJcPerCheck = K == 2 ? 1 : S::CheckIters;
+    constexpr int kJcPerCheck = K == 2 ? 1 : R::CheckIters;
     static_assert(kIters % kJcPerCheck == 0, "every item ends on a candidate-buffer check");
     constexpr int kRelease = release_group<K, C>();
     // orders 3-4: prefix sums through the shared transpose buffer
@@ -508,7 +532,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
     unsigned char *stages_b = smem + kStages * kTileBytes;
     float *sc;
     uint64_t *rk;
-    uint32_t *tot;                                                   // [2][128][2 halves][2 classes]
+    uint32_t *tot;                               // [2][128][kMaxProdGroups][2 classes]
     if (P.cand_score_g) {
         sc = P.cand_score_g + (size_t)blockIdx.x * P.cand_p2;
         rk = P.cand_rank_g + (size_t)blockIdx.x * P.cand_p2;
@@ -518,7 +542,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
         rk = reinterpret_cast<uint64_t *>(sc + P.cand_p2);
         tot = reinterpret_cast<uint32_t *>(rk + P.cand_p2);
     }
-    Desc *desc = reinterpret_cast<Desc *>(tot + 2 * 128 * 4);
+    Desc *desc = reinterpret_cast<Desc *>(tot + 2 * 128 * kMaxProdGroups * 2);
     // orders 3-4: per epilogue warp, the row terms of 8 last SNPs [lane][8]
     // (transposed so that one lane sums one prefix's rows for one last SNP)
     unsigned char *after_desc = reinterpret_cast<unsigned char *>(desc + kDescDepth);
@@ -527,7 +551,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
     // one "stage free" barrier per stage for both operands (the A and B rings
     // advance together), released by one MMA commit
     static_assert(kStages % kRelease == 0, "release groups tile the ring");
-    static_assert(kStages % 2 == 0, "the producer halves take the ring slots of one parity each");
+    static_assert(kStages % kGroups == 0, "each producer group takes every kGroups-th ring slot");
     // full_ab[s]: the A producer warps of the slot's parity and the TMA
     // thread (with its bytes) have filled stage s of both operands
     __shared__ __align__(8) uint64_t full_ab[kStages], empty_ab[kStages / kRelease];
@@ -817,8 +841,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
             const int b = (int)(i & 1);
             const uint32_t ub = (uint32_t)(i >> 1);
             if (!wait_fast(&acc_empty[b], (ub & 1) ^ 1, &abort_flag, w_prod_acc)) break;
-            tot[((b * 128 + r) * 2 + grp) * 2 + 0] = t1;
-            tot[((b * 128 + r) * 2 + grp) * 2 + 1] = t0;
+            tot[((b * 128 + r) * kMaxProdGroups + grp) * 2 + 0] = t1;
+            tot[((b * 128 + r) * kMaxProdGroups + grp) * 2 + 1] = t0;
             __syncwarp();
             if (lane == 0) mbar_arrive(&tot_full[b]);
         }
@@ -908,8 +932,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
             uint32_t T1 = 0, T0 = 0;
 #pragma unroll
             for (int gq = 0; gq < kGroups; gq++) {
-                T1 += tot[((b * 128 + r) * 2 + gq) * 2 + 0];
-                T0 += tot[((b * 128 + r) * 2 + gq) * 2 + 1];
+                T1 += tot[((b * 128 + r) * kMaxProdGroups + gq) * 2 + 0];
+                T0 += tot[((b * 128 + r) * kMaxProdGroups + gq) * 2 + 1];
             }
             // row totals in accumulator units (count / 32, exact)
             const float fT1 = u2f_exact(T1) * 0.03125f, fT0 = u2f_exact(T0) * 0.03125f;
@@ -1439,18 +1463,18 @@ int tc_prefixes_per_warp(int k)
 // chunk), rounded up to a power of two for the bitonic sort.
 int tc_cand_p2(int k, int pool, bool comb)
 {
-    const int groups = comb ? tc::Shape<true>::ColGroups : tc::Shape<false>::ColGroups;
-    const int check = k == 2 ? 1 : (comb ? tc::Shape<true>::CheckIters : tc::Shape<false>::CheckIters);
+    const int groups = tc::roles_epi_warps(comb, k) / 4;
+    const int check = k == 2 ? 1 : tc::roles_check_iters(comb, k);
     return next_pow2(pool + check * 8 * groups * tc_ppt(k));
 }
 
 size_t tc_smem_bytes(int cand_p2, int k, bool cand_global, bool comb)
 {
     const size_t transpose =
-        (k == 3 || k == 4) ? (size_t)(comb ? tc::Shape<true>::EpiWarps : tc::Shape<false>::EpiWarps) * 256 * 4 + 16 : 0;
+        (k == 3 || k == 4) ? (size_t)tc::roles_epi_warps(comb, k) * 256 * 4 + 16 : 0;
     const size_t rings = comb ? (size_t)tc::Shape<true>::Stages * (tc::kTileBytes + tc::Shape<true>::BBytes)
                               : (size_t)tc::Shape<false>::Stages * (tc::kTileBytes + tc::Shape<false>::BBytes);
-    return 1024 + rings + (cand_global ? 0 : (size_t)cand_p2 * 12) + 2 * 128 * 4 * 4 +
+    return 1024 + rings + (cand_global ? 0 : (size_t)cand_p2 * 12) + 2 * 128 * tc::kMaxProdGroups * 2 * 4 +
            tc::kDescDepth * sizeof(tc::Desc) + 64 + transpose;
 }
 
