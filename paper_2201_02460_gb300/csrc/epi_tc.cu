@@ -22,8 +22,10 @@
 //
 // Layout of one tile: M = 128 rows = 4 warps x 32 lanes; each warp holds
 // floor(32 / 3^(k-1)) whole prefixes (prefix rows never straddle a warp, so
-// the epilogue reduces a prefix with warp shuffles); N = 128 columns = 64 last
-// SNPs x genotypes {0, 1}; K = 128 individuals per stage.
+// the epilogue reduces a prefix within a warp); N = 128 columns = 64 last
+// SNPs x genotypes {0, 1}; K = 128 individuals per stage.  At order 3, where
+// the counts fit, the combined-class variant (Shape<true> below) sums both
+// classes into one accumulator with E5M2 operands and uses N = 256 columns.
 // Prefixes are taken in "panel order" (by their last SNP c ascending) so the
 // last SNPs of a tile, j > c, form one contiguous range.  A lexicographic rank
 // range [r0, r1) of combinations covers the first SNPs s1 in [a, b] (those of
@@ -34,15 +36,17 @@
 // SNP, so that is one interval of j).
 //
 // Warp roles (576 threads, one CTA per SM, persistent, a contiguous range of
-// work items per CTA; an item = one M tile x one N tile x the whole K range):
-//   warps 0-7   epilogue: TMEM -> registers, single-precision MI screen,
+// work items per CTA; an item = one M tile x one N tile x the whole K range;
+// the epilogue/producer split is Roles<C, K> below: 8/8, or 12/4 for the
+// combined-class variant):
+//   epilogue warps (first): TMEM -> registers, single-precision MI screen,
 //               exact-margin candidate selection, per-CTA candidate list;
-//               warp w reads TMEM lane quadrant w % 4 for half w / 4 of the
-//               tile's last SNPs
-//   warps 8-15  A producers: prefix rows = AND of the prefix SNPs' bit rows,
-//               expanded to E4M3 bytes in the 128-byte-swizzled K-major
-//               layout; one thread per row and alternate K stages per
-//               half of the producers, own stages prefetched
+//               warp w reads TMEM lane quadrant w % 4 for the chunks of 8
+//               last SNPs w / 4, w / 4 + G, ... (G warps per quadrant)
+//   A producers: prefix rows = AND of the prefix SNPs' bit rows, expanded
+//               to FP8 bytes in the 128-byte-swizzled K-major layout; one
+//               thread per row, groups of 4 warps taking the ring's stages
+//               in turn, own stages prefetched
 //   warp 16     TMA producer of B tiles, and writer of the item descriptors
 //   warp 17     TMEM allocator and MMA issuer (one elected thread)
 // Every mbarrier wait is bounded (about 2 s); a wait that gives up sets
