@@ -525,20 +525,23 @@ __device__ __forceinline__ void pair_of_index(int64_t n, int32_t c, int64_t i, i
     j2 = j1 + 1 + (int32_t)(i - before);
 }
 
-// Single-precision MI of (prefix, j1, j2): lanes take prefix rows lane,
-// lane + 32, lane + 64, lane + 96 (then the next 128), counting per class the
-// joint counts n[g1][g2] (g1, g2 in {0, 1}) and the single counts of the row
-// with j1's and with j2's genotype-0/1 rows over the class's word groups.
+// Sum of the single-precision MI terms (before the division by m) of
+// (prefix, j1, j2) over the prefix rows of blocks part, part + parts, ... of
+// 128 rows: lanes take rows lane, lane + 32, lane + 64, lane + 96 of a block,
+// counting per class the joint counts n[g1][g2] (g1, g2 in {0, 1}) and the
+// single counts of the row with j1's and with j2's genotype-0/1 rows over the
+// class's word groups; each lane sums compensated, the warp as a tree.
 template <int PR>
-__device__ __forceinline__ float score_pair_warp(const uint4 *__restrict__ T, const uint32_t *__restrict__ tot,
-                                                 const uint32_t *__restrict__ mj1, const uint32_t *__restrict__ mj2,
-                                                 int W4, int W14, const MiConstF32 &mc, int lane)
+__device__ __forceinline__ float score_pair_warp_sum(const uint4 *__restrict__ T, const uint32_t *__restrict__ tot,
+                                                     const uint32_t *__restrict__ mj1, const uint32_t *__restrict__ mj2,
+                                                     int W4, int W14, const MiConstF32 &mc, int lane, int part,
+                                                     int parts)
 {
     const uint4 *x0p = reinterpret_cast<const uint4 *>(mj1), *x1p = x0p + W4;
     const uint4 *y0p = reinterpret_cast<const uint4 *>(mj2), *y1p = y0p + W4;
     SumF32 acc;
 #pragma unroll 1
-    for (int r0 = lane; r0 < PR; r0 += 4 * 32) {
+    for (int r0 = lane + 4 * 32 * part; r0 < PR; r0 += 4 * 32 * parts) {
         int rr[4];
 #pragma unroll
         for (int i = 0; i < 4; i++) rr[i] = min(r0 + 32 * i, PR - 1);
@@ -600,7 +603,16 @@ __device__ __forceinline__ float score_pair_warp(const uint4 *__restrict__ T, co
     float v = acc.value();
 #pragma unroll
     for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    return __fdiv_rn(v, mc.fm);
+    return v;
+}
+
+// Single-precision MI of (prefix, j1, j2), one warp over all rows.
+template <int PR>
+__device__ __forceinline__ float score_pair_warp(const uint4 *__restrict__ T, const uint32_t *__restrict__ tot,
+                                                 const uint32_t *__restrict__ mj1, const uint32_t *__restrict__ mj2,
+                                                 int W4, int W14, const MiConstF32 &mc, int lane)
+{
+    return __fdiv_rn(score_pair_warp_sum<PR>(T, tot, mj1, mj2, W4, W14, mc, lane, 0, 1), mc.fm);
 }
 
 template <int K>
@@ -621,6 +633,7 @@ __global__ void __launch_bounds__(kPairThreads, 1) popc_pair_kernel(PopcParams P
     __shared__ SubtileState S;
     __shared__ int32_t pre[kMaxOrderGpu];
     __shared__ int64_t pbase, i_lo, i_hi;
+    __shared__ float partial[kPairThreads / 32];   // few pairs: each warp's share of a pair's sum
 
     const MiConstF32 mc = make_mi_const(d.m, d.m1, d.m0);
     const uint64_t span = D.rank_end - D.rank_begin;
@@ -701,7 +714,41 @@ __global__ void __launch_bounds__(kPairThreads, 1) popc_pair_kernel(PopcParams P
         const int64_t lo = i_lo, hi = i_hi;
         const int32_t cl = pre[km2 - 1];
         const float thr0 = S.thr;
-        for (int64_t c0 = lo; c0 < hi; c0 += kPairChunk) {
+        if (hi - lo < kWarps) {
+            // fewer pairs than warps (the prefixes near the end of the SNP
+            // order): each pair's 128-row blocks are split over kWarps / q
+            // warps, whose sums are added as a tree in a fixed order
+            const int q = (int)(hi - lo);
+            const int parts = q > 0 ? kWarps / q : 1;
+            const int pl = warp / parts, part = warp % parts;
+            float v = 0.0f;
+            if (pl < q) {
+                int32_t j1, j2;
+                pair_of_index(d.n, cl, lo + pl, j1, j2);
+                v = score_pair_warp_sum<PR>(T, tot, d.masks + (int64_t)j1 * 3 * d.Wt, d.masks + (int64_t)j2 * 3 * d.Wt,
+                                            W4, W14, mc, lane, part, parts);
+            }
+            if (lane == 0) partial[warp] = v;
+            __syncthreads();
+            if (threadIdx.x < q) {
+                float t[kWarps];
+#pragma unroll
+                for (int u = 0; u < kWarps; u++) t[u] = u < parts ? partial[threadIdx.x * parts + u] : 0.0f;
+#pragma unroll
+                for (int w2 = kWarps / 2; w2; w2 >>= 1)
+#pragma unroll
+                    for (int u = 0; u < w2; u++) t[u] += t[u + w2];
+                const float score = __fdiv_rn(t[0], mc.fm);
+                if (score >= fmaxf(S.thr, thr0)) {
+                    const int pos = S.list_len + atomicAdd(&S.nbuf, 1);
+                    sc[pos] = score;
+                    rk[pos] = (uint64_t)(pbase + lo + threadIdx.x);
+                }
+            }
+            __syncthreads();
+            if (S.list_len + S.nbuf + kPairChunk > cand_p2) flush_list(S, sc, rk, P.pool, cand_p2, D.global_thr);
+        }
+        for (int64_t c0 = lo; c0 < hi && hi - lo >= kWarps; c0 += kPairChunk) {
             const int64_t c1 = c0 + kPairChunk < hi ? c0 + kPairChunk : hi;
             const int list_len = S.list_len;
             const float thr = S.thr > thr0 ? S.thr : thr0;
