@@ -714,17 +714,38 @@ __global__ void __launch_bounds__(kPairThreads, 1) popc_pair_kernel(PopcParams P
         const int64_t lo = i_lo, hi = i_hi;
         const int32_t cl = pre[km2 - 1];
         const float thr0 = S.thr;
-        if (hi - lo < kWarps) {
-            // fewer pairs than warps (the prefixes near the end of the SNP
-            // order): each pair's 128-row blocks are split over kWarps / q
-            // warps, whose sums are added as a tree in a fixed order
-            const int q = (int)(hi - lo);
+        // whole rounds of kWarps pairs, one warp per pair; the last q <
+        // kWarps pairs (all of them for the prefixes near the end of the SNP
+        // order) split each pair's 128-row blocks over kWarps / q warps,
+        // whose sums are added as a tree in a fixed order
+        const int64_t mid = lo + (hi - lo) / kWarps * kWarps;
+        for (int64_t c0 = lo; c0 < mid; c0 += kPairChunk) {
+            const int64_t c1 = c0 + kPairChunk < mid ? c0 + kPairChunk : mid;
+            const int list_len = S.list_len;
+            const float thr = S.thr > thr0 ? S.thr : thr0;
+            for (int64_t i = c0 + warp; i < c1; i += kWarps) {
+                int32_t j1, j2;
+                pair_of_index(d.n, cl, i, j1, j2);
+                const float score = score_pair_warp<PR>(T, tot, d.masks + (int64_t)j1 * 3 * d.Wt,
+                                                        d.masks + (int64_t)j2 * 3 * d.Wt, W4, W14, mc, lane);
+                if (lane == 0 && score >= thr) {
+                    const int pos = list_len + atomicAdd(&S.nbuf, 1);
+                    sc[pos] = score;
+                    rk[pos] = (uint64_t)(pbase + i);
+                }
+            }
+            __syncthreads();
+            if (S.list_len + S.nbuf + kPairChunk > cand_p2) flush_list(S, sc, rk, P.pool, cand_p2, D.global_thr);
+        }
+        if (mid < hi) {
+            const int64_t lo2 = mid;
+            const int q = (int)(hi - lo2);
             const int parts = q > 0 ? kWarps / q : 1;
             const int pl = warp / parts, part = warp % parts;
             float v = 0.0f;
             if (pl < q) {
                 int32_t j1, j2;
-                pair_of_index(d.n, cl, lo + pl, j1, j2);
+                pair_of_index(d.n, cl, lo2 + pl, j1, j2);
                 v = score_pair_warp_sum<PR>(T, tot, d.masks + (int64_t)j1 * 3 * d.Wt, d.masks + (int64_t)j2 * 3 * d.Wt,
                                             W4, W14, mc, lane, part, parts);
             }
@@ -742,25 +763,7 @@ __global__ void __launch_bounds__(kPairThreads, 1) popc_pair_kernel(PopcParams P
                 if (score >= fmaxf(S.thr, thr0)) {
                     const int pos = S.list_len + atomicAdd(&S.nbuf, 1);
                     sc[pos] = score;
-                    rk[pos] = (uint64_t)(pbase + lo + threadIdx.x);
-                }
-            }
-            __syncthreads();
-            if (S.list_len + S.nbuf + kPairChunk > cand_p2) flush_list(S, sc, rk, P.pool, cand_p2, D.global_thr);
-        }
-        for (int64_t c0 = lo; c0 < hi && hi - lo >= kWarps; c0 += kPairChunk) {
-            const int64_t c1 = c0 + kPairChunk < hi ? c0 + kPairChunk : hi;
-            const int list_len = S.list_len;
-            const float thr = S.thr > thr0 ? S.thr : thr0;
-            for (int64_t i = c0 + warp; i < c1; i += kWarps) {
-                int32_t j1, j2;
-                pair_of_index(d.n, cl, i, j1, j2);
-                const float score = score_pair_warp<PR>(T, tot, d.masks + (int64_t)j1 * 3 * d.Wt,
-                                                        d.masks + (int64_t)j2 * 3 * d.Wt, W4, W14, mc, lane);
-                if (lane == 0 && score >= thr) {
-                    const int pos = list_len + atomicAdd(&S.nbuf, 1);
-                    sc[pos] = score;
-                    rk[pos] = (uint64_t)(pbase + i);
+                    rk[pos] = (uint64_t)(pbase + lo2 + threadIdx.x);
                 }
             }
             __syncthreads();
