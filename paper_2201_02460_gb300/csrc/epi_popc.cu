@@ -486,7 +486,19 @@ __global__ void __launch_bounds__(128) popc_search_kernel(PopcParams P)
 // subtraction (n[g1][2] = row & j1:g1 minus n[g1][0] + n[g1][1], and so on,
 // n[2][2] from the row total).  No table leaves the SM, and every staged
 // table serves C(L, 2) combinations (L = SNPs after the prefix) instead of L.
-constexpr int kPairThreads = 256;
+// threads per CTA and prefix rows per lane and block (tuning parameters;
+// measured on the order-8 Table-2 workload: 4 rows x 256 threads 104 ms
+// (239 registers, 8 warps per SM), 2 x 384 65 ms, 2 x 512 63 ms, 1 x 512
+// 57.6 ms, 1 x 768 52.3 ms, 1 x 1024 52.0 ms (64 registers): the counting
+// loop is latency-bound, and more warps hide it)
+#ifndef EPI_PAIR_THREADS
+#define EPI_PAIR_THREADS 1024
+#endif
+#ifndef EPI_PAIR_ROWS
+#define EPI_PAIR_ROWS 1
+#endif
+constexpr int kPairThreads = EPI_PAIR_THREADS;
+constexpr int kPairRows = EPI_PAIR_ROWS;
 constexpr int kPairChunk = 256;   // pairs counted between candidate-buffer checks
 
 __host__ __device__ inline size_t pair_table_bytes(int k, int32_t Wt)
@@ -527,7 +539,7 @@ __device__ __forceinline__ void pair_of_index(int64_t n, int32_t c, int64_t i, i
 
 // Sum of the single-precision MI terms (before the division by m) of
 // (prefix, j1, j2) over the prefix rows of blocks part, part + parts, ... of
-// 128 rows: lanes take rows lane, lane + 32, lane + 64, lane + 96 of a block,
+// 32 kPairRows rows: lanes take rows lane, lane + 32, ... of a block,
 // counting per class the joint counts n[g1][g2] (g1, g2 in {0, 1}) and the
 // single counts of the row with j1's and with j2's genotype-0/1 rows over the
 // class's word groups; each lane sums compensated, the warp as a tree.
@@ -541,14 +553,14 @@ __device__ __forceinline__ float score_pair_warp_sum(const uint4 *__restrict__ T
     const uint4 *y0p = reinterpret_cast<const uint4 *>(mj2), *y1p = y0p + W4;
     SumF32 acc;
 #pragma unroll 1
-    for (int r0 = lane + 4 * 32 * part; r0 < PR; r0 += 4 * 32 * parts) {
-        int rr[4];
+    for (int r0 = lane + kPairRows * 32 * part; r0 < PR; r0 += kPairRows * 32 * parts) {
+        int rr[kPairRows];
 #pragma unroll
-        for (int i = 0; i < 4; i++) rr[i] = min(r0 + 32 * i, PR - 1);
+        for (int i = 0; i < kPairRows; i++) rr[i] = min(r0 + 32 * i, PR - 1);
         // cnt[i][y][q]: q = n00, n01, n10, n11, j1 g0, j1 g1, j2 g0, j2 g1
-        uint32_t cnt[4][2][8];
+        uint32_t cnt[kPairRows][2][8];
 #pragma unroll
-        for (int i = 0; i < 4; i++)
+        for (int i = 0; i < kPairRows; i++)
 #pragma unroll
             for (int y = 0; y < 2; y++)
 #pragma unroll
@@ -565,7 +577,7 @@ __device__ __forceinline__ float score_pair_warp_sum(const uint4 *__restrict__ T
                 const uint4 j11 = make_uint4(x1.x & y1.x, x1.y & y1.y, x1.z & y1.z, x1.w & y1.w);
                 const size_t off = (size_t)u * PR;
 #pragma unroll
-                for (int i = 0; i < 4; i++) {
+                for (int i = 0; i < kPairRows; i++) {
                     const uint4 p = T[off + rr[i]];
                     cnt[i][y][0] += popc4(p, j00);
                     cnt[i][y][1] += popc4(p, j01);
@@ -579,7 +591,7 @@ __device__ __forceinline__ float score_pair_warp_sum(const uint4 *__restrict__ T
             }
         }
 #pragma unroll
-        for (int i = 0; i < 4; i++) {
+        for (int i = 0; i < kPairRows; i++) {
             if (r0 + 32 * i >= PR) continue;
             uint32_t cell[2][9];
 #pragma unroll
@@ -752,11 +764,12 @@ __global__ void __launch_bounds__(kPairThreads, 1) popc_pair_kernel(PopcParams P
             if (lane == 0) partial[warp] = v;
             __syncthreads();
             if (threadIdx.x < q) {
-                float t[kWarps];
+                constexpr int kT = kWarps <= 8 ? 8 : (kWarps <= 16 ? 16 : 32);   // a power of two >= kWarps
+                float t[kT];
 #pragma unroll
-                for (int u = 0; u < kWarps; u++) t[u] = u < parts ? partial[threadIdx.x * parts + u] : 0.0f;
+                for (int u = 0; u < kT; u++) t[u] = u < parts ? partial[threadIdx.x * parts + u] : 0.0f;
 #pragma unroll
-                for (int w2 = kWarps / 2; w2; w2 >>= 1)
+                for (int w2 = kT / 2; w2; w2 >>= 1)
 #pragma unroll
                     for (int u = 0; u < w2; u++) t[u] += t[u + w2];
                 const float score = __fdiv_rn(t[0], mc.fm);
