@@ -497,6 +497,12 @@ __global__ void __launch_bounds__(128) popc_search_kernel(PopcParams P)
 #ifndef EPI_PAIR_ROWS
 #define EPI_PAIR_ROWS 1
 #endif
+// lowest order searched with the (k-2)-prefix kernel (tuning parameter;
+// order 6, 60 SNPs x 2048: 690 ms against 961 ms for the (k-1)-prefix
+// kernel, whose 243-row tables leave one 4-warp CTA per SM)
+#ifndef EPI_PAIR_MIN_ORDER
+#define EPI_PAIR_MIN_ORDER 6
+#endif
 constexpr int kPairThreads = EPI_PAIR_THREADS;
 constexpr int kPairRows = EPI_PAIR_ROWS;
 constexpr int kPairChunk = 256;   // pairs counted between candidate-buffer checks
@@ -930,15 +936,16 @@ cudaError_t launch_popc_search(const DevData &d, int k, int R, uint64_t rank_beg
     p.list_score = list_score;
     p.list_rank = list_rank;
     p.list_count = list_count;
-    // orders 7-8 with the (k-2)-prefix table in shared memory where it fits
-    // (the searches that return every score keep the (k-1)-prefix kernel)
-    if ((k == 7 || k == 8) && !all_scores) {
+    // orders EPI_PAIR_MIN_ORDER-8 with the (k-2)-prefix table in shared
+    // memory where it fits (the searches that return every score keep the
+    // (k-1)-prefix kernel)
+    if (k >= EPI_PAIR_MIN_ORDER && k <= 8 && !all_scores) {
         int dev = 0, optin = 0;
         if (cudaGetDevice(&dev) == cudaSuccess &&
             cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess) {
             const size_t ps = pair_smem_bytes(k, d.Wt, pool);
             if (ps <= (size_t)optin) {
-                auto kern = k == 7 ? popc_pair_kernel<7> : popc_pair_kernel<8>;
+                auto kern = k == 6 ? popc_pair_kernel<6> : (k == 7 ? popc_pair_kernel<7> : popc_pair_kernel<8>);
                 cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ps);
                 if (e != cudaSuccess) return e;
                 kern<<<grid, kPairThreads, ps, st>>>(p);
