@@ -109,9 +109,10 @@ def test_search_small(epi, ctx, k, n, m, top_n):
 
 
 # Orders 6-8 (popcount path; the tensor path stops at 5).  Single searches
-# keep the order-6 prefix tables in shared memory and the order-7/8 tables in
-# per-CTA global buffers; batched launches keep order-7/8 tables in shared
-# memory where they fit (test_batched_high_orders).
+# stage (k-2)-prefix tables in shared memory and count last pairs (whole
+# rounds of one pair per warp, then the last pairs' rows split over warps);
+# batched launches and the thresholded output keep (k-1)-prefix tables
+# (test_batched_high_orders, test_search_threshold_matches_oracle).
 @pytest.mark.parametrize("k,n,m,m1,top_n", [
     (6, 14, 300, None, 40), (6, 12, 129, 40, 20), (7, 13, 700, None, 30), (7, 11, 3000, 1500, 20),
     (8, 12, 200, None, 25), (8, 11, 1000, 500, 15),
@@ -122,9 +123,9 @@ def test_search_high_orders(epi, ctx, k, n, m, m1, top_n):
     _check_result(r, geno, pheno, oc, om)
 
 
-@pytest.mark.parametrize("k,m,m1", [(7, 3000, 1500), (8, 200, None)])
+@pytest.mark.parametrize("k,m,m1", [(6, 700, None), (7, 3000, 1500), (8, 200, None)])
 def test_search_range_high_orders(epi, ctx, k, m, m1):
-    n = 14 if k == 7 else 13
+    n = {6: 16, 7: 14, 8: 13}[k]
     geno, pheno = random_data(n, m, seed=31 + k, m1=m1)
     total = O.binom(n, k)
     for r0, r1 in [(0, 1), (17, 1000), (total - 100, total + 10)]:
