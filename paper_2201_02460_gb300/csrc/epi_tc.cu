@@ -789,22 +789,46 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
             // this group's first stage of the item and its number of stages
             const int kc0 = (int)(((uint64_t)grp + kGroups - (g % kGroups)) % kGroups);
             const int mine = (chunks - kc0 + kGroups - 1) / kGroups;
-            // this row's words of the next kPf own stages (a register ring
-            // indexed statically: the loop is unrolled by kPf)
+            // the prefix SNPs' words of this row for the next kPf own stages
+            // (a register ring indexed statically: the loop is unrolled by
+            // kPf).  Up to order 3 they are kept as loaded and ANDed only
+            // when their stage is produced, so no instruction waits for a
+            // load issued for a later stage; at orders 4-5 the ring holds the
+            // AND (measured: the raw ring's registers spill there, 1586 vs
+            // 1527 ms at order 4, 500 x 8192, and 1548 ms with one own stage
+            // of prefetch; order 3 combined 94.6 -> 94.0 ms).  EPI_TC_RAW_HI
+            // (a prefetch distance) keeps the raw words at every order.
+#ifdef EPI_TC_RAW_HI
+            constexpr bool kKeepRaw = true;
+            constexpr int kPf = km1 <= 2 ? EPI_TC_PREFETCH : EPI_TC_RAW_HI;
+#else
+            constexpr bool kKeepRaw = km1 <= 2;
             constexpr int kPf = EPI_TC_PREFETCH;
-            uint4 ring[kPf];
-            auto fetch = [&](int kc) {
-                uint4 a = __ldg(rows[0] + kc);
+#endif
+            constexpr int kRaw = kKeepRaw ? km1 : 1;     // words kept per own stage
+            uint4 ring[kPf][kRaw];
+            auto fetch = [&](int kc, uint4 *dst) {
+                if constexpr (kKeepRaw) {
 #pragma unroll
-                for (int tt = 1; tt < km1; tt++) {
-                    const uint4 v = __ldg(rows[tt] + kc);
-                    a.x &= v.x; a.y &= v.y; a.z &= v.z; a.w &= v.w;
+                    for (int tt = 0; tt < km1; tt++) dst[tt] = __ldg(rows[tt] + kc);
+                } else {
+                    uint4 a = __ldg(rows[0] + kc);
+#pragma unroll
+                    for (int tt = 1; tt < km1; tt++) {
+                        const uint4 v = __ldg(rows[tt] + kc);
+                        a.x &= v.x; a.y &= v.y; a.z &= v.z; a.w &= v.w;
+                    }
+                    dst[0] = a;
                 }
-                return a;
             };
 #pragma unroll
-            for (int u = 0; u < kPf; u++)
-                ring[u] = (active && u < mine) ? fetch(kc0 + kGroups * u) : make_uint4(0, 0, 0, 0);
+            for (int u = 0; u < kPf; u++) {
+                if (active && u < mine) fetch(kc0 + kGroups * u, ring[u]);
+                else {
+#pragma unroll
+                    for (int tt = 0; tt < kRaw; tt++) ring[u][tt] = make_uint4(0, 0, 0, 0);
+                }
+            }
             uint64_t gs = g + (uint64_t)kc0;                   // global stage of own stage m
             int s = (int)(gs % kStages);
             uint32_t ph = (uint32_t)((gs / kStages) & 1);
@@ -814,8 +838,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_con
                     const int m = mb + u;
                     if (m >= mine) break;
                     const int kc = kc0 + kGroups * m;
-                    const uint4 cur = ring[u];
-                    if (active && m + kPf < mine) ring[u] = fetch(kc + kGroups * kPf);
+                    uint4 cur = ring[u][0];
+#pragma unroll
+                    for (int tt = 1; tt < kRaw; tt++) {
+                        cur.x &= ring[u][tt].x; cur.y &= ring[u][tt].y; cur.z &= ring[u][tt].z; cur.w &= ring[u][tt].w;
+                    }
+                    if (active && m + kPf < mine) fetch(kc + kGroups * kPf, ring[u]);
                     if (!wait_fast(&empty_ab[s / kRelease], ph ^ 1, &abort_flag, w_prod)) { ok = false; break; }
                     const uint32_t c4 = __popc(cur.x) + __popc(cur.y) + __popc(cur.z) + __popc(cur.w);
                     if (kc < chunks_case) t1 += c4;
