@@ -102,11 +102,23 @@ struct Shape {
 // each A row once per 512-cycle stage, so one group of 4 warps keeps up and
 // 12 warps (3 per TMEM lane quadrant) run the epilogue; the separate variant
 // has producer groups of 4 warps taking the ring's stages in turn.
+// Epilogue and producer warps of the combined-class variant (tuning
+// parameters; the launch's register cap follows from the warps per SM
+// sub-partition.  Order 3, 2000 x 4000: 12 + 4 warps (96 registers) 93.8 ms,
+// 8 + 4 (128 registers) 100.1 ms, 8 + 8 110.8 ms, 4 + 4 133.5 ms)
+#ifndef EPI_TC_C_EPI_WARPS
+#define EPI_TC_C_EPI_WARPS 12
+#endif
+#ifndef EPI_TC_C_PROD_WARPS
+#define EPI_TC_C_PROD_WARPS 4
+#endif
+
 template <bool C, int K>
 struct Roles {
     static constexpr int J = Shape<C>::J;
-    static constexpr int EpiWarps = C ? 12 : (K == 4 ? EPI_TC_K4_EPI_WARPS : 8);
-    static constexpr int ProdWarps = 16 - EpiWarps;
+    static constexpr int EpiWarps = C ? EPI_TC_C_EPI_WARPS : (K == 4 ? EPI_TC_K4_EPI_WARPS : 8);
+    static constexpr int ProdWarps = C ? EPI_TC_C_PROD_WARPS : 16 - EpiWarps;
+    static constexpr int Threads = 32 * (EpiWarps + ProdWarps + 2);   // + the TMA and MMA warps
     static constexpr int EpiThreads = 32 * EpiWarps;
     static constexpr int ProdGroups = ProdWarps / 4;  // one thread per tile row each
     static constexpr int ColGroups = EpiWarps / 4;    // epilogue warps per lane quadrant
@@ -145,7 +157,6 @@ constexpr int release_group()
 #endif
 }
 constexpr int kDescDepth = 4;
-constexpr int kThreads = 32 * (16 + 2);   // 16 epilogue and producer warps, TMA, MMA
 static_assert(Roles<false, 4>::ProdWarps / 4 <= 3, "at most kMaxProdGroups producer groups");
 constexpr int kTileBytes = 128 * kKC;        // one A tile (and a B tile of the separate-class variant)
 constexpr int kWaitSlots = 8;
@@ -496,7 +507,7 @@ __device__ __noinline__ float row_terms_precise(uint32_t a0, uint32_t b0, uint32
                  : "r"(taddr))
 
 template <int K, bool C>
-__global__ void __launch_bounds__(kThreads, 1) tc_search_kernel(const __grid_constant__ CUtensorMap tmap_b,
+__global__ void __launch_bounds__(Roles<C, K>::Threads, 1) tc_search_kernel(const __grid_constant__ CUtensorMap tmap_b,
                                                                 const Params P)
 {
     static_assert(!C || K == 3, "the combined-class variant serves order 3");
@@ -1602,7 +1613,9 @@ static cudaError_t launch_kernel(const CUtensorMap &map, const tc::Params &P, in
                          : tc::tc_search_kernel<5, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid, tc::kThreads, smem, st>>>(map, P);
+    const int threads = comb ? tc::Roles<true, 3>::Threads
+                             : (k == 4 ? tc::Roles<false, 4>::Threads : tc::Roles<false, 3>::Threads);
+    kern<<<grid, threads, smem, st>>>(map, P);
     return cudaGetLastError();
 }
 
