@@ -403,8 +403,18 @@ __device__ __forceinline__ void split_classes(uint32_t x, uint32_t lo_mask, floa
     case32 = __float_as_uint((y - lo) * case_scale);
 }
 
+// Approximate log2 of a normal float (the PTX instruction, flushing
+// subnormal inputs: every argument here is at least 1/32, so the flush never
+// applies and no subnormal handling is emitted around it)
+__device__ __forceinline__ float lg2n(float x)
+{
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // t(x) = x log2 x of an accumulator value x = count / 32 (0 for x = 0)
-__device__ __forceinline__ float tlog32(float x) { return x * __log2f(fmaxf(x, 0.03125f)); }
+__device__ __forceinline__ float tlog32(float x) { return x * lg2n(fmaxf(x, 0.03125f)); }
 
 // sum over the three cells of one tile row of t(a) + t(b) - t(a + b) (a, b:
 // case and control accumulators): one fused multiply-add chain per cell,
@@ -412,15 +422,15 @@ __device__ __forceinline__ float tlog32(float x) { return x * __log2f(fmaxf(x, 0
 __device__ __forceinline__ float row_screen(float a0, float a1, float a2, float b0, float b1, float b2)
 {
     const float s0 = a0 + b0, s1 = a1 + b1, s2 = a2 + b2;
-    float v0 = a0 * __log2f(fmaxf(a0, 0.03125f));
-    float v1 = a1 * __log2f(fmaxf(a1, 0.03125f));
-    float v2 = a2 * __log2f(fmaxf(a2, 0.03125f));
-    v0 = fmaf(b0, __log2f(fmaxf(b0, 0.03125f)), v0);
-    v1 = fmaf(b1, __log2f(fmaxf(b1, 0.03125f)), v1);
-    v2 = fmaf(b2, __log2f(fmaxf(b2, 0.03125f)), v2);
-    v0 = fmaf(-s0, __log2f(fmaxf(s0, 0.03125f)), v0);
-    v1 = fmaf(-s1, __log2f(fmaxf(s1, 0.03125f)), v1);
-    v2 = fmaf(-s2, __log2f(fmaxf(s2, 0.03125f)), v2);
+    float v0 = a0 * lg2n(fmaxf(a0, 0.03125f));
+    float v1 = a1 * lg2n(fmaxf(a1, 0.03125f));
+    float v2 = a2 * lg2n(fmaxf(a2, 0.03125f));
+    v0 = fmaf(b0, lg2n(fmaxf(b0, 0.03125f)), v0);
+    v1 = fmaf(b1, lg2n(fmaxf(b1, 0.03125f)), v1);
+    v2 = fmaf(b2, lg2n(fmaxf(b2, 0.03125f)), v2);
+    v0 = fmaf(-s0, lg2n(fmaxf(s0, 0.03125f)), v0);
+    v1 = fmaf(-s1, lg2n(fmaxf(s1, 0.03125f)), v1);
+    v2 = fmaf(-s2, lg2n(fmaxf(s2, 0.03125f)), v2);
     return (v0 + v1) + v2;
 }
 
