@@ -104,8 +104,10 @@ struct Shape {
 // has producer groups of 4 warps taking the ring's stages in turn.
 // Epilogue and producer warps of the combined-class variant (tuning
 // parameters; the launch's register cap follows from the warps per SM
-// sub-partition.  Order 3, 2000 x 4000: 12 + 4 warps (96 registers) 93.8 ms,
-// 8 + 4 (128 registers) 100.1 ms, 8 + 8 110.8 ms, 4 + 4 133.5 ms)
+// sub-partition.  Order 3, 2000 x 4000: 12 + 4 warps (96 registers) 86.6 ms,
+// 8 + 4 (128 registers) 88.3 ms, 8 + 8 93.6 ms, 12 + 8 (80 registers,
+// spills) 100.6 ms; before the screen's logarithms lost their subnormal
+// handling: 93.8, 100.1, 110.8 ms, and 4 + 4 133.5 ms)
 #ifndef EPI_TC_C_EPI_WARPS
 #define EPI_TC_C_EPI_WARPS 12
 #endif
