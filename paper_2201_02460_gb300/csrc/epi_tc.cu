@@ -35,10 +35,10 @@
 // in [r0, r1) (consecutive ranks share their prefix and differ in the last
 // SNP, so that is one interval of j).
 //
-// Warp roles (576 threads, one CTA per SM, persistent, a contiguous range of
-// work items per CTA; an item = one M tile x one N tile x the whole K range;
-// the epilogue/producer split is Roles<C, K> below: 8/8, or 12/4 for the
-// combined-class variant):
+// Warp roles (by default 576 threads = 18 warps, one CTA per SM, persistent,
+// a contiguous range of work items per CTA; an item = one M tile x one N
+// tile x the whole K range; the epilogue/producer split is Roles<C, K>
+// below: 8/8, or 12/4 for the combined-class variant):
 //   epilogue warps (first): TMEM -> registers, single-precision MI screen,
 //               exact-margin candidate selection, per-CTA candidate list;
 //               warp w reads TMEM lane quadrant w % 4 for the chunks of 8
@@ -47,8 +47,8 @@
 //               to FP8 bytes in the 128-byte-swizzled K-major layout; one
 //               thread per row, groups of 4 warps taking the ring's stages
 //               in turn, own stages prefetched
-//   warp 16     TMA producer of B tiles, and writer of the item descriptors
-//   warp 17     TMEM allocator and MMA issuer (one elected thread)
+//   next warp   TMA producer of B tiles, and writer of the item descriptors
+//   last warp   TMEM allocator and MMA issuer (one elected thread)
 // Every mbarrier wait is bounded (about 2 s); a wait that gives up sets
 // ST_TIMEOUT and all roles leave their loops, drain their own asynchronous
 // work and free tensor memory.
