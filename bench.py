@@ -445,11 +445,28 @@ def roofline(kind, d, k, kern_ms, peaks, tc_rate=None):
     W = ((d.n_cases + 127) // 128 + (d.n_samples - d.n_cases + 127) // 128) * 4
     ops = total * (3 ** k) * W
     achieved = ops / (kern_ms / 1e3) / 1e12
+    executed = popc_executed_ops(d, k, W) / (kern_ms / 1e3) / 1e12
     peak = N_SMS * POPC_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
     return dict(bound="alu", achieved=achieved, peak=peak, unit="Tops/s", frac=achieved / peak, traffic=None,
-                kernel="popc_search_kernel", kernel_ms=kern_ms,
-                note="32-bit AND+POPC word operations, 3^k cells x (W1+W0) words per combination; "
+                kernel="popc_pair_kernel" if k >= 6 else "popc_search_kernel", kernel_ms=kern_ms,
+                executed_tops=executed, executed_frac=executed / peak,
+                note="32-bit AND+POPC word operations, 3^k cells x (W1+W0) words per combination (paper "
+                     "work; executed: the POPCs the kernel issues, the other cells by subtraction); "
                      "peak = 152 SMs x 16 POPC/clk x 2070 MHz")
+
+
+def popc_executed_ops(d, k, W):
+    """32-bit POPC word operations the popcount kernels issue for a whole
+    search: the (k-1)-prefix kernel counts two genotype rows of the last SNP
+    per prefix row (the third by subtraction); the (k-2)-prefix kernel of
+    orders 6-8 counts the four joint rows of the last two SNPs per prefix row,
+    and per prefix its row totals and the single counts of every following
+    SNP's genotype-0/1 rows (rank ranges split between CTAs add a little)."""
+    n, total = d.n_snps, math.comb(d.n_snps, k)
+    if k < 6:
+        return total * 2 * 3 ** (k - 1) * W
+    per_prefix = sum(math.comb(c, k - 3) * (2 * (n - 1 - c) + 1) for c in range(k - 3, n - 2))
+    return 3 ** (k - 2) * W * (4 * total + per_prefix)
 
 
 def run_ours(args):

@@ -194,6 +194,7 @@ struct SearchPlan {
     bool tc = false;
     int comb_p = 0;                // tensor path: class shift of the combined-class variant, 0 = separate classes
     bool global_prefix = false;    // popcount path: prefix tables in a global buffer (orders 7-8)
+    bool pair = false;             // popcount path: the (k-2)-prefix kernel (orders 6-8)
     float *all_scores = nullptr;   // optional: every combination's score (popcount path)
     size_t smem = 0;
     uint64_t rb = 0, re = 0, total = 0;
@@ -277,6 +278,13 @@ epi_status plan_popc(const epi_dataset *ds, SearchPlan &p, int R_req = 0)
         return fail(EPI_EUNSUPPORTED, "order %d with %lld samples: one prefix table does not fit in shared memory",
                     p.k, (long long)ds->m);
     uint64_t grid = (uint64_t)ctx->num_sms * (uint64_t)p.grid;
+    // orders 6-8: the (k-2)-prefix kernel, one 1024-thread CTA per SM, its
+    // own number of waves
+    p.pair = popc_pair_applies(p.k, ds->Wt, p.pool, p.all_scores != nullptr);
+    if (p.pair) {
+        p.global_prefix = false;
+        grid = (uint64_t)popc_pair_grid(ctx->num_sms, p.k, ds->n);
+    }
     const uint64_t by_work = (span + 127) / 128;
     if (grid > by_work) grid = by_work;
     if (grid < 1) grid = 1;
@@ -357,6 +365,7 @@ epi_status queue_search(epi_dataset *ds, const SearchPlan &p, int path, epi_resu
     const size_t o_ic = a.take<uint64_t>(2 * ((size_t)ds->n + 1));
     const size_t o_pre =
         p.global_prefix ? a.take<uint32_t>((size_t)p.grid * p.slots * popc_slot_words(p.k, ds->Wt)) : 0;
+    const size_t o_sing = p.pair ? a.take<uint32_t>((size_t)p.grid * popc_pair_sing_words(p.k, ds->n)) : 0;
     // tensor path: candidate buffers in global memory when they do not fit
     // beside the operand rings in shared memory (large pools)
     const int tc_cp2 = p.tc ? tc_cand_p2(p.k, p.pool, p.comb_p != 0) : 0;
@@ -411,7 +420,8 @@ epi_status queue_search(epi_dataset *ds, const SearchPlan &p, int path, epi_resu
     } else {
         CK(launch_popc_search(d, p.k, p.R, p.rb, p.re, p.tile, p.pool, p.slots, p.cand_p2, thr, ls, lr, lc, p.grid,
                               p.smem, ctx->stream, p.all_scores,
-                              p.global_prefix ? reinterpret_cast<uint32_t *>(base + o_pre) : nullptr));
+                              p.global_prefix ? reinterpret_cast<uint32_t *>(base + o_pre) : nullptr,
+                              p.pair ? reinterpret_cast<uint32_t *>(base + o_sing) : nullptr));
     }
     if (ev1) CK(cudaEventRecord(ev1, ctx->stream));
     CK(launch_merge(ls, lr, lc, p.grid, p.pool, p.pool, cs, cr, cn, ctx->stream));
@@ -1052,9 +1062,9 @@ epi_status epi_search_threshold(epi_dataset *ds, int order, double threshold, in
         // every score of ranks [rb, rb + ch): the popcount path
         SearchPlan p;
         p.k = order; p.top_n = 1; p.pool = initial_pool(1); p.rb = rb; p.re = std::min(total, rb + ch); p.total = total;
+        p.all_scores = scores;
         st = plan_popc(ds, p);
         if (st != EPI_OK) { cleanup(); return st; }
-        p.all_scores = scores;
         int32_t *status = nullptr;
         st = queue_search(ds, p, EPI_PATH_POPC, static_cast<epi_result *>(dout), nullptr,
                           reinterpret_cast<int32_t *>(static_cast<char *>(dout) + 512), &status);
@@ -1138,9 +1148,9 @@ epi_status epi_score_all(epi_dataset *ds, int order, float *out_dev)
         return fail(EPI_EINVAL, "epi_score_all: out must be device memory of device %d", ctx->device);
     SearchPlan p;
     p.k = order; p.top_n = 1; p.pool = initial_pool(1); p.rb = 0; p.re = total; p.total = total;
+    p.all_scores = out_dev;
     st = plan_popc(ds, p);
     if (st != EPI_OK) return st;
-    p.all_scores = out_dev;
     void *dout = nullptr;
     CK(cudaMallocAsync(&dout, 1024, ctx->stream));
     int32_t *status = nullptr;

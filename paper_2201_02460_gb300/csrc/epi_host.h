@@ -44,7 +44,13 @@ int popc_max_active(int k, int R, size_t smem, bool global_prefix = false);
 cudaError_t launch_popc_search(const DevData &d, int k, int R, uint64_t rank_begin, uint64_t rank_end, int tile,
                                int pool, int slots, int cand_p2, uint32_t *global_thr, float *list_score,
                                uint64_t *list_rank, int32_t *list_count, int grid, size_t smem, cudaStream_t st,
-                               float *all_scores = nullptr, uint32_t *pre_global = nullptr);
+                               float *all_scores = nullptr, uint32_t *pre_global = nullptr,
+                               uint32_t *pair_sing = nullptr);
+// orders 6-8: whether a search runs the (k-2)-prefix kernel, and the words of
+// one CTA's single-count table for it (pair_sing above: grid x that many)
+bool popc_pair_applies(int k, int32_t Wt, int pool, bool all_scores);
+int64_t popc_pair_sing_words(int k, int64_t n);
+int popc_pair_grid(int num_sms, int k, int64_t n);
 // batched: one launch over several datasets of order k (descriptors in device memory)
 size_t popc_ds_bytes();
 void popc_fill_ds(void *dst, const DevData &d, uint64_t rank_begin, uint64_t rank_end, int cta_begin, int cta_count,

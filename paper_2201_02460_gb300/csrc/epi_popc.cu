@@ -65,6 +65,8 @@ struct PopcParams {
     float *all_scores;              // optional: every score, [rank - rank_begin] (single dataset)
     uint32_t *pre_global;           // global prefix tables: [grid][pre_cta_words] (global-prefix kernels)
     int64_t pre_cta_words;
+    uint32_t *pair_sing;            // (k-2)-prefix kernel: single-count tables [grid][pair_sing_words], or NULL
+    int64_t pair_sing_words;
 };
 
 struct SlotInfo {
@@ -478,14 +480,17 @@ __global__ void __launch_bounds__(128) popc_search_kernel(PopcParams P)
 // Combinations that share their first k-2 SNPs are consecutive in
 // lexicographic order, their last two SNPs (j1 < j2) running over the pairs
 // after the prefix.  The prefix's table (3^(k-2) = 243 or 729 rows, Section
-// 2.1) is built once in shared memory, transposed by 16-byte words, and each
-// warp counts one pair at a time, lanes over the rows: per row and class the
-// four joint counts n[g1][g2] (g1, g2 in {0, 1}: the prefix row AND both
-// last SNPs' genotype rows) and the four single counts of row & j1's
-// genotype-0/1 rows and row & j2's; the other five cells follow by
-// subtraction (n[g1][2] = row & j1:g1 minus n[g1][0] + n[g1][1], and so on,
-// n[2][2] from the row total).  No table leaves the SM, and every staged
-// table serves C(L, 2) combinations (L = SNPs after the prefix) instead of L.
+// 2.1) is built once in shared memory, transposed by 16-byte words, with its
+// row totals and a single-count table: per row, class and SNP j after the
+// prefix, the counts of row & j's genotype-0 and genotype-1 rows (in a
+// per-CTA global buffer, built once per prefix and shared by the L - 1 pairs
+// that contain j).  Each warp then counts one pair at a time, lanes over the
+// rows: per row and class the four joint counts n[g1][g2] (g1, g2 in {0, 1}:
+// the prefix row AND both last SNPs' genotype rows); the other five cells
+// follow by subtraction (n[g1][2] = row & j1:g1 minus n[g1][0] + n[g1][1],
+// and so on, n[2][2] from the row total).  The prefix table never leaves the
+// SM, and it serves C(L, 2) combinations (L = SNPs after the prefix) instead
+// of L.
 // threads per CTA and prefix rows per lane and block (tuning parameters;
 // measured on the order-8 Table-2 workload: 4 rows x 256 threads 104 ms
 // (239 registers, 8 warps per SM), 2 x 384 65 ms, 2 x 512 63 ms, 1 x 512
@@ -520,6 +525,13 @@ __host__ __device__ inline size_t pair_smem_bytes(int k, int32_t Wt, int pool)
     return ((pair_table_bytes(k, Wt) + 15) & ~(size_t)15) + (size_t)pair_cand_p2(pool) * 12;
 }
 
+// One CTA's single-count table: 4 counts (class x genotype 0/1) per prefix
+// row for each SNP that can follow a (k-2)-prefix (at most n - (k - 2)).
+__host__ __device__ inline int64_t pair_sing_words_of(int k, int64_t n)
+{
+    return n > k - 2 ? (n - (k - 2)) * 4 * (int64_t)ipow3(k - 2) : 0;
+}
+
 // next m-subset of [0, n) in lex order whose last element is at most n - 3
 // (two SNPs must follow); false after the last
 __device__ inline bool next_prefix_pairs(int32_t *p, int m, int64_t n)
@@ -546,14 +558,16 @@ __device__ __forceinline__ void pair_of_index(int64_t n, int32_t c, int64_t i, i
 // Sum of the single-precision MI terms (before the division by m) of
 // (prefix, j1, j2) over the prefix rows of blocks part, part + parts, ... of
 // 32 kPairRows rows: lanes take rows lane, lane + 32, ... of a block,
-// counting per class the joint counts n[g1][g2] (g1, g2 in {0, 1}) and the
-// single counts of the row with j1's and with j2's genotype-0/1 rows over the
-// class's word groups; each lane sums compensated, the warp as a tree.
+// counting per class the joint counts n[g1][g2] (g1, g2 in {0, 1}) over the
+// class's word groups; the single counts of the row with j1's and with j2's
+// genotype-0/1 rows come from the prefix's single-count table (s1, s2: the
+// entries of j1 and j2, [class][genotype][row]).  Each lane sums
+// compensated, the warp as a tree.
 template <int PR>
 __device__ __forceinline__ float score_pair_warp_sum(const uint4 *__restrict__ T, const uint32_t *__restrict__ tot,
                                                      const uint32_t *__restrict__ mj1, const uint32_t *__restrict__ mj2,
-                                                     int W4, int W14, const MiConstF32 &mc, int lane, int part,
-                                                     int parts)
+                                                     const uint32_t *s1, const uint32_t *s2, int W4, int W14,
+                                                     const MiConstF32 &mc, int lane, int part, int parts)
 {
     const uint4 *x0p = reinterpret_cast<const uint4 *>(mj1), *x1p = x0p + W4;
     const uint4 *y0p = reinterpret_cast<const uint4 *>(mj2), *y1p = y0p + W4;
@@ -570,7 +584,7 @@ __device__ __forceinline__ float score_pair_warp_sum(const uint4 *__restrict__ T
 #pragma unroll
             for (int y = 0; y < 2; y++)
 #pragma unroll
-                for (int q = 0; q < 8; q++) cnt[i][y][q] = 0;
+                for (int q = 0; q < 4; q++) cnt[i][y][q] = 0;
 #pragma unroll
         for (int y = 0; y < 2; y++) {
             const int ub = y ? W14 : 0, ue = y ? W4 : W14;
@@ -589,13 +603,20 @@ __device__ __forceinline__ float score_pair_warp_sum(const uint4 *__restrict__ T
                     cnt[i][y][1] += popc4(p, j01);
                     cnt[i][y][2] += popc4(p, j10);
                     cnt[i][y][3] += popc4(p, j11);
-                    cnt[i][y][4] += popc4(p, x0);
-                    cnt[i][y][5] += popc4(p, x1);
-                    cnt[i][y][6] += popc4(p, y0);
-                    cnt[i][y][7] += popc4(p, y1);
                 }
             }
         }
+        // written by this CTA before the barrier that ended the table's
+        // build: read through L2 (never the non-coherent path)
+#pragma unroll
+        for (int i = 0; i < kPairRows; i++)
+#pragma unroll
+            for (int y = 0; y < 2; y++) {
+                cnt[i][y][4] = __ldcg(s1 + (2 * y) * PR + rr[i]);
+                cnt[i][y][5] = __ldcg(s1 + (2 * y + 1) * PR + rr[i]);
+                cnt[i][y][6] = __ldcg(s2 + (2 * y) * PR + rr[i]);
+                cnt[i][y][7] = __ldcg(s2 + (2 * y + 1) * PR + rr[i]);
+            }
 #pragma unroll
         for (int i = 0; i < kPairRows; i++) {
             if (r0 + 32 * i >= PR) continue;
@@ -628,9 +649,10 @@ __device__ __forceinline__ float score_pair_warp_sum(const uint4 *__restrict__ T
 template <int PR>
 __device__ __forceinline__ float score_pair_warp(const uint4 *__restrict__ T, const uint32_t *__restrict__ tot,
                                                  const uint32_t *__restrict__ mj1, const uint32_t *__restrict__ mj2,
-                                                 int W4, int W14, const MiConstF32 &mc, int lane)
+                                                 const uint32_t *s1, const uint32_t *s2, int W4, int W14,
+                                                 const MiConstF32 &mc, int lane)
 {
-    return __fdiv_rn(score_pair_warp_sum<PR>(T, tot, mj1, mj2, W4, W14, mc, lane, 0, 1), mc.fm);
+    return __fdiv_rn(score_pair_warp_sum<PR>(T, tot, mj1, mj2, s1, s2, W4, W14, mc, lane, 0, 1), mc.fm);
 }
 
 template <int K>
@@ -651,7 +673,12 @@ __global__ void __launch_bounds__(kPairThreads, 1) popc_pair_kernel(PopcParams P
     __shared__ SubtileState S;
     __shared__ int32_t pre[kMaxOrderGpu];
     __shared__ int64_t pbase, i_lo, i_hi;
+    __shared__ int32_t jlo;                        // j1 of the CTA's first pair of the prefix
     __shared__ float partial[kPairThreads / 32];   // few pairs: each warp's share of a pair's sum
+    // single counts of the prefix rows with the genotype-0/1 rows of each
+    // SNP j >= jlo: [j - jlo][class][genotype][row], per CTA in global memory
+    uint32_t *sing = P.pair_sing + (size_t)blockIdx.x * (size_t)P.pair_sing_words;
+#define EPI_SING_OF(j) (sing + (size_t)((j) - jlo) * 4 * PR)
 
     const MiConstF32 mc = make_mi_const(d.m, d.m1, d.m0);
     const uint64_t span = D.rank_end - D.rank_begin;
@@ -682,6 +709,11 @@ __global__ void __launch_bounds__(kPairThreads, 1) popc_pair_kernel(PopcParams P
             const int64_t np = L * (L - 1) / 2;
             i_lo = R_b > pbase ? R_b - pbase : 0;
             i_hi = R_e - pbase < np ? R_e - pbase : np;
+            if (i_lo < i_hi) {
+                int32_t j1, j2;
+                pair_of_index(d.n, pre[km2 - 1], i_lo, j1, j2);
+                jlo = j1;
+            }
             const float g = __uint_as_float(*(volatile uint32_t *)D.global_thr);
             if (S.list_len == P.pool || g > 0.0f) S.thr = fmaxf(S.thr, g);
         }
@@ -727,6 +759,29 @@ __global__ void __launch_bounds__(kPairThreads, 1) popc_pair_kernel(PopcParams P
             }
             tot[row * 2 + half] = c;
         }
+        // the single counts of every SNP that a pair of the CTA's range
+        // uses (j1 of its first pair to the last SNP): each serves all
+        // the pairs it is part of instead of being counted for each
+        if (i_lo < i_hi) {
+            const int32_t j0 = jlo;
+            const int nj = d.n - j0;
+            for (int idx = threadIdx.x; idx < nj * PR * 2; idx += blockDim.x) {
+                const int row = idx % PR, rest = idx / PR;
+                const int y = rest & 1, jj = rest >> 1;
+                const int ub = y ? W14 : 0, ue = y ? W4 : W14;
+                const uint4 *g0 = reinterpret_cast<const uint4 *>(d.masks + (int64_t)(j0 + jj) * 3 * d.Wt);
+                const uint4 *g1 = g0 + W4;
+                uint32_t c0 = 0, c1 = 0;
+                for (int u = ub; u < ue; u++) {
+                    const uint4 v = T[(size_t)u * PR + row];
+                    c0 += popc4(v, __ldg(g0 + u));
+                    c1 += popc4(v, __ldg(g1 + u));
+                }
+                uint32_t *o = sing + ((size_t)jj * 4 + 2 * y) * PR + row;
+                __stcg(o, c0);
+                __stcg(o + PR, c1);
+            }
+        }
         __syncthreads();
         // ---- the pairs of this prefix in the CTA's range, in chunks
         const int64_t lo = i_lo, hi = i_hi;
@@ -744,8 +799,9 @@ __global__ void __launch_bounds__(kPairThreads, 1) popc_pair_kernel(PopcParams P
             for (int64_t i = c0 + warp; i < c1; i += kWarps) {
                 int32_t j1, j2;
                 pair_of_index(d.n, cl, i, j1, j2);
-                const float score = score_pair_warp<PR>(T, tot, d.masks + (int64_t)j1 * 3 * d.Wt,
-                                                        d.masks + (int64_t)j2 * 3 * d.Wt, W4, W14, mc, lane);
+                const float score = score_pair_warp<PR>(
+                    T, tot, d.masks + (int64_t)j1 * 3 * d.Wt, d.masks + (int64_t)j2 * 3 * d.Wt,
+                    EPI_SING_OF(j1), EPI_SING_OF(j2), W4, W14, mc, lane);
                 if (lane == 0 && score >= thr) {
                     const int pos = list_len + atomicAdd(&S.nbuf, 1);
                     sc[pos] = score;
@@ -765,7 +821,7 @@ __global__ void __launch_bounds__(kPairThreads, 1) popc_pair_kernel(PopcParams P
                 int32_t j1, j2;
                 pair_of_index(d.n, cl, lo2 + pl, j1, j2);
                 v = score_pair_warp_sum<PR>(T, tot, d.masks + (int64_t)j1 * 3 * d.Wt, d.masks + (int64_t)j2 * 3 * d.Wt,
-                                            W4, W14, mc, lane, part, parts);
+                                            EPI_SING_OF(j1), EPI_SING_OF(j2), W4, W14, mc, lane, part, parts);
             }
             if (lane == 0) partial[warp] = v;
             __syncthreads();
@@ -804,6 +860,7 @@ __global__ void __launch_bounds__(kPairThreads, 1) popc_pair_kernel(PopcParams P
         P.list_rank[(size_t)blockIdx.x * P.pool + i] = rk[i];
     }
     if (threadIdx.x == 0) P.list_count[blockIdx.x] = Lc;
+#undef EPI_SING_OF
 }
 
 template <int K, int R, bool GP>
@@ -911,15 +968,55 @@ static cudaError_t launch_dispatch(const PopcParams &p, int k, int R, int grid, 
     }
 }
 
+bool popc_pair_applies(int k, int32_t Wt, int pool, bool all_scores)
+{
+    if (k < EPI_PAIR_MIN_ORDER || k > 8 || all_scores) return false;
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return false;
+    return pair_smem_bytes(k, Wt, pool) <= (size_t)optin;
+}
+
+int64_t popc_pair_sing_words(int k, int64_t n) { return pair_sing_words_of(k, n); }
+
+// CTAs of a (k-2)-prefix search: waves of one CTA per SM (tuning parameter:
+// equal rank ranges per CTA, so more waves even out prefixes of unequal cost;
+// measured on orders 6-8, 2048-4096 samples: 8 waves 6-15 % faster than 1,
+// 2-8 % faster than 4), fewer where the single-count tables would pass
+// 256 MiB
+#ifndef EPI_PAIR_WAVES
+#define EPI_PAIR_WAVES 8
+#endif
+int popc_pair_grid(int num_sms, int k, int64_t n)
+{
+    const int64_t per_wave = (int64_t)num_sms * pair_sing_words_of(k, n) * 4;
+    int64_t waves = per_wave > 0 ? ((int64_t)256 << 20) / per_wave : EPI_PAIR_WAVES;
+    waves = waves < 1 ? 1 : (waves > EPI_PAIR_WAVES ? EPI_PAIR_WAVES : waves);
+    return num_sms * (int)waves;
+}
+
+template <int K>
+static cudaError_t launch_pair(const PopcParams &p, int grid, size_t smem, cudaStream_t st)
+{
+    auto kern = popc_pair_kernel<K>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, kPairThreads, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_popc_search(const DevData &d, int k, int R, uint64_t rank_begin, uint64_t rank_end, int tile,
                                int pool, int slots, int cand_p2, uint32_t *global_thr, float *list_score,
                                uint64_t *list_rank, int32_t *list_count, int grid, size_t smem, cudaStream_t st,
-                               float *all_scores, uint32_t *pre_global)
+                               float *all_scores, uint32_t *pre_global, uint32_t *pair_sing)
 {
     PopcParams p;
     p.all_scores = all_scores;
     p.pre_global = pre_global;
     p.pre_cta_words = (int64_t)slots * popc_slot_words(k, d.Wt);
+    p.pair_sing = pair_sing;
+    p.pair_sing_words = pair_sing_words_of(k, d.n);
     p.one.d = d;
     p.one.rank_begin = rank_begin;
     p.one.rank_end = rank_end;
@@ -937,22 +1034,15 @@ cudaError_t launch_popc_search(const DevData &d, int k, int R, uint64_t rank_beg
     p.list_rank = list_rank;
     p.list_count = list_count;
     // orders EPI_PAIR_MIN_ORDER-8 with the (k-2)-prefix table in shared
-    // memory where it fits (the searches that return every score keep the
-    // (k-1)-prefix kernel)
-    if (k >= EPI_PAIR_MIN_ORDER && k <= 8 && !all_scores) {
-        int dev = 0, optin = 0;
-        if (cudaGetDevice(&dev) == cudaSuccess &&
-            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess) {
-            const size_t ps = pair_smem_bytes(k, d.Wt, pool);
-            if (ps <= (size_t)optin) {
-                auto kern = k == 6 ? popc_pair_kernel<6> : (k == 7 ? popc_pair_kernel<7> : popc_pair_kernel<8>);
-                cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ps);
-                if (e != cudaSuccess) return e;
-                kern<<<grid, kPairThreads, ps, st>>>(p);
-                return cudaGetLastError();
-            }
-        }
+    // memory where it fits and the caller gives the single-count tables
+    // (grid x popc_pair_sing_words words); the searches that return every
+    // score keep the (k-1)-prefix kernel
+    if (pair_sing && popc_pair_applies(k, d.Wt, pool, all_scores != nullptr)) {
+        const size_t ps = pair_smem_bytes(k, d.Wt, pool);
+        if (k == 6) return launch_pair<6>(p, grid, ps, st);
+        return k == 7 ? launch_pair<7>(p, grid, ps, st) : launch_pair<8>(p, grid, ps, st);
     }
+    p.pair_sing = nullptr;
     return launch_dispatch(p, k, R, grid, smem, st);
 }
 
@@ -978,6 +1068,8 @@ cudaError_t launch_popc_batch(const void *ds_dev, const int32_t *cta_ds_dev, int
     p.all_scores = nullptr;
     p.pre_global = nullptr;
     p.pre_cta_words = 0;
+    p.pair_sing = nullptr;
+    p.pair_sing_words = 0;
     p.one = PopcDs();
     p.many = static_cast<const PopcDs *>(ds_dev);
     p.cta_ds = cta_ds_dev;

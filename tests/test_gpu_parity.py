@@ -109,8 +109,9 @@ def test_search_small(epi, ctx, k, n, m, top_n):
 
 
 # Orders 6-8 (popcount path; the tensor path stops at 5).  Single searches
-# stage (k-2)-prefix tables in shared memory and count last pairs (whole
-# rounds of one pair per warp, then the last pairs' rows split over warps);
+# stage (k-2)-prefix tables in shared memory with a single-count table per
+# prefix and count last pairs (whole rounds of one pair per warp, then the
+# last pairs' rows split over warps);
 # batched launches and the thresholded output keep (k-1)-prefix tables
 # (test_batched_high_orders, test_search_threshold_matches_oracle).
 @pytest.mark.parametrize("k,n,m,m1,top_n", [
