@@ -982,11 +982,11 @@ int64_t popc_pair_sing_words(int k, int64_t n) { return pair_sing_words_of(k, n)
 
 // CTAs of a (k-2)-prefix search: waves of one CTA per SM (tuning parameter:
 // equal rank ranges per CTA, so more waves even out prefixes of unequal cost;
-// measured on orders 6-8, 2048-4096 samples: 8 waves 6-15 % faster than 1,
-// 2-8 % faster than 4), fewer where the single-count tables would pass
-// 256 MiB
+// measured on orders 6-8, 2048-4096 samples: 8 waves 6-15 % faster than 1
+// and 2-8 % faster than 4, 16 waves another 2-5 % where the cap below lets
+// them run), fewer where the single-count tables would pass 256 MiB
 #ifndef EPI_PAIR_WAVES
-#define EPI_PAIR_WAVES 8
+#define EPI_PAIR_WAVES 16
 #endif
 int popc_pair_grid(int num_sms, int k, int64_t n)
 {
