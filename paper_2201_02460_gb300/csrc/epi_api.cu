@@ -421,7 +421,7 @@ epi_status queue_search(epi_dataset *ds, const SearchPlan &p, int path, epi_resu
         CK(launch_popc_search(d, p.k, p.R, p.rb, p.re, p.tile, p.pool, p.slots, p.cand_p2, thr, ls, lr, lc, p.grid,
                               p.smem, ctx->stream, p.all_scores,
                               p.global_prefix ? reinterpret_cast<uint32_t *>(base + o_pre) : nullptr,
-                              p.pair ? reinterpret_cast<uint32_t *>(base + o_sing) : nullptr));
+                              p.pair ? reinterpret_cast<uint32_t *>(base + o_sing) : nullptr, p.top_n));
     }
     if (ev1) CK(cudaEventRecord(ev1, ctx->stream));
     CK(launch_merge(ls, lr, lc, p.grid, p.pool, p.pool, cs, cr, cn, ctx->stream));

@@ -45,7 +45,7 @@ cudaError_t launch_popc_search(const DevData &d, int k, int R, uint64_t rank_beg
                                int pool, int slots, int cand_p2, uint32_t *global_thr, float *list_score,
                                uint64_t *list_rank, int32_t *list_count, int grid, size_t smem, cudaStream_t st,
                                float *all_scores = nullptr, uint32_t *pre_global = nullptr,
-                               uint32_t *pair_sing = nullptr);
+                               uint32_t *pair_sing = nullptr, int top_n = 0);
 // orders 6-8: whether a search runs the (k-2)-prefix kernel, and the words of
 // one CTA's single-count table for it (pair_sing above: grid x that many)
 bool popc_pair_applies(int k, int32_t Wt, int pool, bool all_scores);

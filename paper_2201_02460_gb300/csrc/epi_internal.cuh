@@ -118,6 +118,17 @@ __device__ __forceinline__ double phi_f64(double u)
     return fma(1.0 + u, log1p(u), -u);
 }
 
+// Approximate log2 of a normal float (the PTX instruction, flushing
+// subnormal inputs: the callers' arguments are at least 1/32, so the flush
+// never applies and no subnormal handling is emitted around it).  Error:
+// at most 2^-22 absolute for x in [0.5, 2], 2 ulp of the result elsewhere.
+__device__ __forceinline__ float lg2n(float x)
+{
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Exact float of an integer below 2^23 without a conversion instruction:
 // 2^23 + v has v as its mantissa.
 __device__ __forceinline__ float u2f_exact(uint32_t v)

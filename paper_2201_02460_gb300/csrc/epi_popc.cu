@@ -67,6 +67,7 @@ struct PopcParams {
     int64_t pre_cta_words;
     uint32_t *pair_sing;            // (k-2)-prefix kernel: single-count tables [grid][pair_sing_words], or NULL
     int64_t pair_sing_words;
+    int32_t top_n;                  // (k-2)-prefix kernel: records asked for (0: not known)
 };
 
 struct SlotInfo {
@@ -168,6 +169,25 @@ __device__ inline void flush_list(SubtileState &S, float *sc, uint64_t *rk, int 
         if (S.list_len == pool) {
             const float t = sc[pool - 1];
             S.thr = t;
+            atomicMax(global_thr, __float_as_uint(t));
+        }
+    }
+    __syncthreads();
+}
+
+// A CTA holding at least top_n candidates knows that top_n combinations
+// score at least its top_n-th best s, so none below s can enter the top N:
+// after a flush it lowers s by its single-precision error bound (four times
+// over, so that the final margin check still clears it), and raises its own
+// and the global threshold to it.
+__device__ inline void publish_top_n(SubtileState &S, float *sc, uint64_t *rk, int pool, int cand_p2,
+                                     uint32_t *global_thr, int top_n, int k, int64_t m)
+{
+    flush_list(S, sc, rk, pool, cand_p2, global_thr);
+    if (threadIdx.x == 0 && top_n <= S.list_len) {
+        const float t = sc[top_n - 1] * (float)(1.0 - 4.0 * f32_rel_bound(k, m));
+        if (t > 0.0f) {
+            S.thr = fmaxf(S.thr, t);
             atomicMax(global_thr, __float_as_uint(t));
         }
     }
@@ -555,15 +575,56 @@ __device__ __forceinline__ void pair_of_index(int64_t n, int32_t c, int64_t i, i
     j2 = j1 + 1 + (int32_t)(i - before);
 }
 
+// T(c) = c log2 c of a count below 2^23 with the fast logarithm (0 at c = 0)
+__device__ __forceinline__ float tlog_count(uint32_t c)
+{
+    const float f = u2f_exact(c);
+    return f * lg2n(fmaxf(f, 1.0f));
+}
+
+// Constants of the screen of the (k-2)-prefix kernel.  With T(c) = c log2 c,
+//     m MI / ln 2 = T(m) - T(m1) - T(m0) - sum over cells of
+//                   [T(a + b) - T(a) - T(b)]      (a, b: the cell's classes),
+// every bracket >= 0 (T is superadditive).  Evaluated with the fast log2 its
+// error is bounded by (i) the logarithm: |c (lg2 c - log2 c)| <= 2^-22 (c +
+// T(c)) per term, summed over the 27 terms of a row and all rows: at most
+// 2^-22 (2 m + mag), mag = T(m) + T(m1) + T(m0) >= the sum of all |terms|
+// (superadditivity again); (ii) roundings: the products, a row's chains
+// (depth <= 8), the lane's compensated sum, the warp tree (5), the split
+// pairs' tree (5) and the final subtraction and scaling: at most 26 u mag.
+// The margin doubles that and adds the precise score's own relative bound
+// (MI <= ln 2), so every combination whose precise score reaches the
+// threshold passes the screen.
+struct PairScreen {
+    float tconst;        // T(m) - T(m1) - T(m0)
+    float ln2_over_m;
+    float delta;         // nats
+};
+
+__device__ inline PairScreen make_pair_screen(int k, int64_t m, int64_t m1, int64_t m0)
+{
+    auto T = [](double c) { return c > 0 ? c * log2(c) : 0.0; };
+    const double mag = T((double)m) + T((double)m1) + T((double)m0);
+    const double u = 5.9604644775390625e-8;
+    const double ln2 = 0.6931471805599453;
+    PairScreen p;
+    p.tconst = (float)(T((double)m) - T((double)m1) - T((double)m0));
+    p.ln2_over_m = (float)(ln2 / (double)m);
+    p.delta = (float)(2.0 * (2.384185791015625e-7 * (2.0 * (double)m + mag) + 32.0 * u * mag) * ln2 / (double)m +
+                      f32_rel_bound(k, m) * ln2) + 1e-7f;
+    return p;
+}
+
 // Sum of the single-precision MI terms (before the division by m) of
 // (prefix, j1, j2) over the prefix rows of blocks part, part + parts, ... of
 // 32 kPairRows rows: lanes take rows lane, lane + 32, ... of a block,
 // counting per class the joint counts n[g1][g2] (g1, g2 in {0, 1}) over the
 // class's word groups; the single counts of the row with j1's and with j2's
 // genotype-0/1 rows come from the prefix's single-count table (s1, s2: the
-// entries of j1 and j2, [class][genotype][row]).  Each lane sums
-// compensated, the warp as a tree.
-template <int PR>
+// entries of j1 and j2, [class][genotype][row]).  kScreen: the screen's sum
+// of T(a + b) - T(a) - T(b) over the cells instead (PairScreen).  Each lane
+// sums compensated, the warp as a tree.
+template <int PR, bool kScreen>
 __device__ __forceinline__ float score_pair_warp_sum(const uint4 *__restrict__ T, const uint32_t *__restrict__ tot,
                                                      const uint32_t *__restrict__ mj1, const uint32_t *__restrict__ mj2,
                                                      const uint32_t *s1, const uint32_t *s2, int W4, int W14,
@@ -635,8 +696,16 @@ __device__ __forceinline__ float score_pair_warp_sum(const uint4 *__restrict__ T
                 cell[y][7] = c[7] - c[1] - c[3];         // (2, 1)
                 cell[y][8] = t - c[4] - c[5] - cell[y][6] - cell[y][7];   // (2, 2)
             }
+            if constexpr (kScreen) {
+                float v3[3] = {0.0f, 0.0f, 0.0f};   // three chains of three cells
 #pragma unroll
-            for (int q = 0; q < 9; q++) acc.add(cell_terms_f32(cell[0][q], cell[1][q], mc));
+                for (int q = 0; q < 9; q++)
+                    v3[q % 3] += tlog_count(cell[0][q] + cell[1][q]) - tlog_count(cell[0][q]) - tlog_count(cell[1][q]);
+                acc.add(fmaxf((v3[0] + v3[1]) + v3[2], 0.0f));
+            } else {
+#pragma unroll
+                for (int q = 0; q < 9; q++) acc.add(cell_terms_f32(cell[0][q], cell[1][q], mc));
+            }
         }
     }
     float v = acc.value();
@@ -652,7 +721,7 @@ __device__ __forceinline__ float score_pair_warp(const uint4 *__restrict__ T, co
                                                  const uint32_t *s1, const uint32_t *s2, int W4, int W14,
                                                  const MiConstF32 &mc, int lane)
 {
-    return __fdiv_rn(score_pair_warp_sum<PR>(T, tot, mj1, mj2, s1, s2, W4, W14, mc, lane, 0, 1), mc.fm);
+    return __fdiv_rn(score_pair_warp_sum<PR, false>(T, tot, mj1, mj2, s1, s2, W4, W14, mc, lane, 0, 1), mc.fm);
 }
 
 template <int K>
@@ -675,12 +744,19 @@ __global__ void __launch_bounds__(kPairThreads, 1) popc_pair_kernel(PopcParams P
     __shared__ int64_t pbase, i_lo, i_hi;
     __shared__ int32_t jlo;                        // j1 of the CTA's first pair of the prefix
     __shared__ float partial[kPairThreads / 32];   // few pairs: each warp's share of a pair's sum
+    __shared__ uint32_t tail_mask;                 // few pairs: those that pass the screen
     // single counts of the prefix rows with the genotype-0/1 rows of each
     // SNP j >= jlo: [j - jlo][class][genotype][row], per CTA in global memory
     uint32_t *sing = P.pair_sing + (size_t)blockIdx.x * (size_t)P.pair_sing_words;
 #define EPI_SING_OF(j) (sing + (size_t)((j) - jlo) * 4 * PR)
 
     const MiConstF32 mc = make_mi_const(d.m, d.m1, d.m0);
+    __shared__ PairScreen scr;
+    __shared__ int published;                      // the CTA's top_n-th best went out (publish_top_n)
+    if (threadIdx.x == 0) {
+        scr = make_pair_screen(K, d.m, d.m1, d.m0);
+        published = P.top_n <= 0;
+    }
     const uint64_t span = D.rank_end - D.rank_begin;
     const uint64_t cb = blockIdx.x - (uint64_t)D.cta_begin, cn = (uint64_t)D.cta_count;
     const int64_t R_b = (int64_t)(D.rank_begin + (uint64_t)(((unsigned __int128)span * cb) / cn));
@@ -796,12 +872,22 @@ __global__ void __launch_bounds__(kPairThreads, 1) popc_pair_kernel(PopcParams P
             const int64_t c1 = c0 + kPairChunk < mid ? c0 + kPairChunk : mid;
             const int list_len = S.list_len;
             const float thr = S.thr > thr0 ? S.thr : thr0;
+            const float cut = thr - scr.delta;
             for (int64_t i = c0 + warp; i < c1; i += kWarps) {
                 int32_t j1, j2;
                 pair_of_index(d.n, cl, i, j1, j2);
-                const float score = score_pair_warp<PR>(
-                    T, tot, d.masks + (int64_t)j1 * 3 * d.Wt, d.masks + (int64_t)j2 * 3 * d.Wt,
-                    EPI_SING_OF(j1), EPI_SING_OF(j2), W4, W14, mc, lane);
+                // the screen first (warp-uniform; while there is no
+                // threshold every pair passes it), the precise score for the
+                // pairs within its margin of the threshold
+                if (cut > 0.0f) {
+                    const float sv = score_pair_warp_sum<PR, true>(
+                        T, tot, d.masks + (int64_t)j1 * 3 * d.Wt, d.masks + (int64_t)j2 * 3 * d.Wt, EPI_SING_OF(j1),
+                        EPI_SING_OF(j2), W4, W14, mc, lane, 0, 1);
+                    if ((scr.tconst - sv) * scr.ln2_over_m < cut) continue;
+                }
+                const float score = score_pair_warp<PR>(T, tot, d.masks + (int64_t)j1 * 3 * d.Wt,
+                                                        d.masks + (int64_t)j2 * 3 * d.Wt, EPI_SING_OF(j1),
+                                                        EPI_SING_OF(j2), W4, W14, mc, lane);
                 if (lane == 0 && score >= thr) {
                     const int pos = list_len + atomicAdd(&S.nbuf, 1);
                     sc[pos] = score;
@@ -810,39 +896,74 @@ __global__ void __launch_bounds__(kPairThreads, 1) popc_pair_kernel(PopcParams P
             }
             __syncthreads();
             if (S.list_len + S.nbuf + kPairChunk > cand_p2) flush_list(S, sc, rk, P.pool, cand_p2, D.global_thr);
+            if (!published && S.list_len + S.nbuf >= P.top_n) {
+                publish_top_n(S, sc, rk, P.pool, cand_p2, D.global_thr, P.top_n, K, d.m);
+                if (threadIdx.x == 0) published = 1;
+                __syncthreads();
+            }
         }
         if (mid < hi) {
             const int64_t lo2 = mid;
             const int q = (int)(hi - lo2);
             const int parts = q > 0 ? kWarps / q : 1;
             const int pl = warp / parts, part = warp % parts;
-            float v = 0.0f;
-            if (pl < q) {
-                int32_t j1, j2;
-                pair_of_index(d.n, cl, lo2 + pl, j1, j2);
-                v = score_pair_warp_sum<PR>(T, tot, d.masks + (int64_t)j1 * 3 * d.Wt, d.masks + (int64_t)j2 * 3 * d.Wt,
-                                            EPI_SING_OF(j1), EPI_SING_OF(j2), W4, W14, mc, lane, part, parts);
-            }
-            if (lane == 0) partial[warp] = v;
-            __syncthreads();
-            if (threadIdx.x < q) {
+            int32_t j1 = 0, j2 = 0;
+            if (pl < q) pair_of_index(d.n, cl, lo2 + pl, j1, j2);
+            const uint32_t *m1p = d.masks + (int64_t)j1 * 3 * d.Wt, *m2p = d.masks + (int64_t)j2 * 3 * d.Wt;
+            // a pair's sum over its warps' parts, as a tree in a fixed order
+            auto tree = [&](int pair) {
                 constexpr int kT = kWarps <= 8 ? 8 : (kWarps <= 16 ? 16 : 32);   // a power of two >= kWarps
                 float t[kT];
 #pragma unroll
-                for (int u = 0; u < kT; u++) t[u] = u < parts ? partial[threadIdx.x * parts + u] : 0.0f;
+                for (int u = 0; u < kT; u++) t[u] = u < parts ? partial[pair * parts + u] : 0.0f;
 #pragma unroll
                 for (int w2 = kT / 2; w2; w2 >>= 1)
 #pragma unroll
                     for (int u = 0; u < w2; u++) t[u] += t[u + w2];
-                const float score = __fdiv_rn(t[0], mc.fm);
-                if (score >= fmaxf(S.thr, thr0)) {
-                    const int pos = S.list_len + atomicAdd(&S.nbuf, 1);
-                    sc[pos] = score;
-                    rk[pos] = (uint64_t)(pbase + lo2 + threadIdx.x);
+                return t[0];
+            };
+            // the screen of the q pairs (skipped while there is no
+            // threshold), then the precise scores of those within its margin
+            // of the threshold (a block-uniform mask)
+            const float thr_t = fmaxf(S.thr, thr0);
+            float v = 0.0f;
+            if (thr_t - scr.delta > 0.0f) {
+                if (pl < q)
+                    v = score_pair_warp_sum<PR, true>(T, tot, m1p, m2p, EPI_SING_OF(j1), EPI_SING_OF(j2), W4, W14, mc,
+                                                      lane, part, parts);
+                if (lane == 0) partial[warp] = v;
+                if (threadIdx.x == 0) tail_mask = 0;
+                __syncthreads();
+                if (threadIdx.x < q && (scr.tconst - tree(threadIdx.x)) * scr.ln2_over_m >= thr_t - scr.delta)
+                    atomicOr(&tail_mask, 1u << threadIdx.x);
+            } else if (threadIdx.x == 0) {
+                tail_mask = q >= 32 ? ~0u : (1u << q) - 1u;
+            }
+            __syncthreads();
+            const uint32_t mask = tail_mask;
+            if (mask) {
+                v = 0.0f;
+                if (pl < q && ((mask >> pl) & 1u))
+                    v = score_pair_warp_sum<PR, false>(T, tot, m1p, m2p, EPI_SING_OF(j1), EPI_SING_OF(j2), W4, W14, mc,
+                                                       lane, part, parts);
+                if (lane == 0) partial[warp] = v;
+                __syncthreads();
+                if (threadIdx.x < q && ((mask >> threadIdx.x) & 1u)) {
+                    const float score = __fdiv_rn(tree(threadIdx.x), mc.fm);
+                    if (score >= thr_t) {
+                        const int pos = S.list_len + atomicAdd(&S.nbuf, 1);
+                        sc[pos] = score;
+                        rk[pos] = (uint64_t)(pbase + lo2 + threadIdx.x);
+                    }
                 }
             }
             __syncthreads();
             if (S.list_len + S.nbuf + kPairChunk > cand_p2) flush_list(S, sc, rk, P.pool, cand_p2, D.global_thr);
+            if (!published && S.list_len + S.nbuf >= P.top_n) {
+                publish_top_n(S, sc, rk, P.pool, cand_p2, D.global_thr, P.top_n, K, d.m);
+                if (threadIdx.x == 0) published = 1;
+                __syncthreads();
+            }
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -1009,9 +1130,10 @@ static cudaError_t launch_pair(const PopcParams &p, int grid, size_t smem, cudaS
 cudaError_t launch_popc_search(const DevData &d, int k, int R, uint64_t rank_begin, uint64_t rank_end, int tile,
                                int pool, int slots, int cand_p2, uint32_t *global_thr, float *list_score,
                                uint64_t *list_rank, int32_t *list_count, int grid, size_t smem, cudaStream_t st,
-                               float *all_scores, uint32_t *pre_global, uint32_t *pair_sing)
+                               float *all_scores, uint32_t *pre_global, uint32_t *pair_sing, int top_n)
 {
     PopcParams p;
+    p.top_n = top_n;
     p.all_scores = all_scores;
     p.pre_global = pre_global;
     p.pre_cta_words = (int64_t)slots * popc_slot_words(k, d.Wt);
@@ -1070,6 +1192,7 @@ cudaError_t launch_popc_batch(const void *ds_dev, const int32_t *cta_ds_dev, int
     p.pre_cta_words = 0;
     p.pair_sing = nullptr;
     p.pair_sing_words = 0;
+    p.top_n = 0;
     p.one = PopcDs();
     p.many = static_cast<const PopcDs *>(ds_dev);
     p.cta_ds = cta_ds_dev;

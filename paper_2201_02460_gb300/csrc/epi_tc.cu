@@ -405,16 +405,6 @@ __device__ __forceinline__ void split_classes(uint32_t x, uint32_t lo_mask, floa
     case32 = __float_as_uint((y - lo) * case_scale);
 }
 
-// Approximate log2 of a normal float (the PTX instruction, flushing
-// subnormal inputs: every argument here is at least 1/32, so the flush never
-// applies and no subnormal handling is emitted around it)
-__device__ __forceinline__ float lg2n(float x)
-{
-    float y;
-    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
 // t(x) = x log2 x of an accumulator value x = count / 32 (0 for x = 0)
 __device__ __forceinline__ float tlog32(float x) { return x * lg2n(fmaxf(x, 0.03125f)); }
 
