@@ -115,11 +115,21 @@ __device__ inline float table_mi_f32(const DevData &d, const uint32_t *ct, int c
     return __fdiv_rn(acc.value(), mc.fm);
 }
 
-__global__ void __launch_bounds__(256) rescore_kernel(DevData d, int k, const uint64_t *__restrict__ cand_rank,
-                                                      const int32_t *__restrict__ cand_n, uint32_t *__restrict__ counts,
-                                                      double *__restrict__ mi64, int32_t *__restrict__ combs)
+constexpr int kRescoreThreads = 256;
+
+// One pooled combination per block: its table, then its double-precision MI
+// with the cells shared out over the block (thread t takes cells t, t + 256,
+// ...) and the threads' sums added as a tree in a fixed order, so the value
+// is the same on every run (the 13,122 terms of an order-8 table took one
+// thread 4.8 ms of double-precision divisions and logarithms).
+__global__ void __launch_bounds__(kRescoreThreads) rescore_kernel(DevData d, int k,
+                                                                  const uint64_t *__restrict__ cand_rank,
+                                                                  const int32_t *__restrict__ cand_n,
+                                                                  uint32_t *__restrict__ counts,
+                                                                  double *__restrict__ mi64, int32_t *__restrict__ combs)
 {
     __shared__ int32_t comb[EPI_MAX_ORDER];
+    __shared__ double part[kRescoreThreads];
     const int c = blockIdx.x;
     if (c >= *cand_n) return;
     int cells = 1;
@@ -132,7 +142,19 @@ __global__ void __launch_bounds__(256) rescore_kernel(DevData d, int k, const ui
     uint32_t *ct = counts + (int64_t)c * 2 * cells;
     count_cells(d, k, comb, ct);
     __syncthreads();
-    if (threadIdx.x == 0) mi64[c] = table_mi_f64(d, ct, cells);
+    double acc = 0.0;
+    for (int x = threadIdx.x; x < cells; x += kRescoreThreads) {
+        const uint32_t a = ct[x], b = ct[cells + x];
+        acc += mi_term_f64(a, a + b, d.m1, d.m);
+        acc += mi_term_f64(b, a + b, d.m0, d.m);
+    }
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = kRescoreThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) mi64[c] = part[0] / (double)d.m;
 }
 
 __device__ __forceinline__ bool final_better(double ma, uint64_t ra, double mb, uint64_t rb)
@@ -291,7 +313,7 @@ cudaError_t launch_merge(const float *ls, const uint64_t *lr, const int32_t *lc,
 cudaError_t launch_rescore(const DevData &d, int k, int pool, const uint64_t *cand_r, const int32_t *cand_n,
                            uint32_t *counts, double *mi64, int32_t *combs, cudaStream_t st)
 {
-    rescore_kernel<<<pool, 256, 0, st>>>(d, k, cand_r, cand_n, counts, mi64, combs);
+    rescore_kernel<<<pool, kRescoreThreads, 0, st>>>(d, k, cand_r, cand_n, counts, mi64, combs);
     return cudaGetLastError();
 }
 
