@@ -1104,15 +1104,16 @@ int64_t popc_pair_sing_words(int k, int64_t n) { return pair_sing_words_of(k, n)
 // CTAs of a (k-2)-prefix search: waves of one CTA per SM (tuning parameter:
 // equal rank ranges per CTA, so more waves even out prefixes of unequal cost;
 // measured on orders 6-8, 2048-4096 samples: 8 waves 6-15 % faster than 1
-// and 2-8 % faster than 4, 16 waves another 2-5 % where the cap below lets
-// them run), fewer where the single-count tables would pass 256 MiB
+// and 2-8 % faster than 4, 16 waves another 2-5 %; with the screen 2, 4 and
+// 8 waves took 42.2, 38.8 and 34.7 ms at order 8, 23 x 2048), fewer where
+// the single-count tables would pass 512 MiB
 #ifndef EPI_PAIR_WAVES
 #define EPI_PAIR_WAVES 16
 #endif
 int popc_pair_grid(int num_sms, int k, int64_t n)
 {
     const int64_t per_wave = (int64_t)num_sms * pair_sing_words_of(k, n) * 4;
-    int64_t waves = per_wave > 0 ? ((int64_t)256 << 20) / per_wave : EPI_PAIR_WAVES;
+    int64_t waves = per_wave > 0 ? ((int64_t)512 << 20) / per_wave : EPI_PAIR_WAVES;
     waves = waves < 1 ? 1 : (waves > EPI_PAIR_WAVES ? EPI_PAIR_WAVES : waves);
     return num_sms * (int)waves;
 }
