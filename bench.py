@@ -461,7 +461,8 @@ def popc_executed_ops(d, k, W):
     per prefix row (the third by subtraction); the (k-2)-prefix kernel of
     orders 6-8 counts the four joint rows of the last two SNPs per prefix row,
     and per prefix its row totals and the single counts of every following
-    SNP's genotype-0/1 rows (rank ranges split between CTAs add a little)."""
+    SNP's genotype-0/1 rows (rank ranges split between CTAs add a little, and
+    the pairs its screen passes are counted a second time, not included)."""
     n, total = d.n_snps, math.comb(d.n_snps, k)
     if k < 6:
         return total * 2 * 3 ** (k - 1) * W
